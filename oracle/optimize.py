@@ -1,0 +1,146 @@
+"""psi = sqrt(rho) density optimiser of the oracle (test infrastructure only).
+
+Sec. 2.4: minimise E[psi^2] subject to int psi^2 = N_e (Eq. euler2), repeating
+(1) a search direction p_k, (2) a line search for lambda_k, (3) the update
+psi_{k+1} = psi_k cos(lambda_k) + p_k sin(lambda_k) with p_k orthogonal to
+psi_k and normalised to N_e, which conserves the charge exactly.
+
+Readings (the paper leaves them to SciPy): Polak-Ribiere+ conjugate
+gradient, restarted on loss of descent; a strong-Wolfe line search on lambda
+(c1 = 1e-4, c2 = 0.2, at most 10 evaluations per search, cubic
+interpolation); the spline knots are recomputed at the start of every
+iteration and frozen inside its line search; convergence when
+|E_k - E_{k-1}| < tol * n_atoms for 3 consecutive iterations.
+Parity unpinned for the trajectory: only the converged energy is compared.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import replace
+
+import numpy as np
+
+from . import functionals as fn
+from .evaluate import Functional, evaluate
+from .grid import Grid
+
+
+def _cubic_min(a, fa, da, b, fb, db):
+    """Minimiser of the cubic through (a, fa, da), (b, fb, db); None if not defined."""
+    d1 = da + db - 3.0 * (fa - fb) / (a - b)
+    disc = d1 * d1 - da * db
+    if disc < 0.0:
+        return None
+    d2 = math.copysign(math.sqrt(disc), b - a)
+    den = db - da + 2.0 * d2
+    if den == 0.0:
+        return None
+    return b - (b - a) * (db + d2 - d1) / den
+
+
+def optimize_density(g: Grid, psi0, func: Functional, Vext_G, n_electrons: float, n_atoms: int,
+                     tol: float = 1e-6, max_iter: int = 200, c1: float = 1e-4, c2: float = 0.2,
+                     max_ls: int = 10, fixed_iter: int | None = None):
+    """Returns dict(psi, E, energies, iterations, evals, history)."""
+    psi = np.asarray(psi0, dtype=np.float64).copy()
+    psi *= math.sqrt(n_electrons / (np.sum(psi * psi) * g.dV))
+    evals = 0
+
+    def energy(psi_l, f):
+        nonlocal evals
+        evals += 1
+        E, V = evaluate(g, psi_l * psi_l, f, Vext_G)
+        return E, V
+
+    def frozen(psi_l):
+        if "NL" in func.terms and func.kernel == "lwt" and func.knots is None:
+            return replace(func, knots=fn.make_knots(psi_l * psi_l, func.n_knots, func.spacing))
+        return func
+
+    f_it = frozen(psi)
+    E, V = energy(psi, f_it)
+    history = [E["total"]]
+    d_prev = None
+    g_prev = None
+    lam_prev = 0.05
+    small = 0
+    it = 0
+    while it < max_iter:
+        it += 1
+        dEdpsi = 2.0 * psi * V * g.dV
+        mu = np.sum(psi * dEdpsi) / (2.0 * n_electrons)
+        grad = dEdpsi - 2.0 * mu * psi * g.dV
+        if d_prev is None or it % 50 == 1:
+            d = -grad
+        else:
+            beta = max(0.0, float(np.sum(grad * (grad - g_prev)) / np.sum(g_prev * g_prev)))
+            d = -grad + beta * d_prev
+            if np.sum(d * grad) >= 0.0:
+                d = -grad
+        g_prev, d_prev = grad, d
+        p = d - (np.sum(d * psi) / np.sum(psi * psi)) * psi
+        p *= math.sqrt(n_electrons / (np.sum(p * p) * g.dV))
+        phi0 = E["total"]
+        dphi0 = float(np.sum(dEdpsi * p))
+        if dphi0 >= 0.0:
+            d_prev = None
+            continue
+
+        def phi(lam):
+            psi_l = psi * math.cos(lam) + p * math.sin(lam)
+            E_l, V_l = energy(psi_l, f_it)
+            dpsi = -psi * math.sin(lam) + p * math.cos(lam)
+            return E_l, V_l, psi_l, float(np.sum(2.0 * psi_l * V_l * g.dV * dpsi))
+
+        # strong-Wolfe search (bracketing + zoom with cubic interpolation)
+        lam_lo, f_lo, d_lo = 0.0, phi0, dphi0
+        lam = min(max(lam_prev, 1e-4), 0.5)
+        best = None
+        n_ls = 0
+        lam_hi = None
+        while n_ls < max_ls:
+            n_ls += 1
+            E_l, V_l, psi_l, dl = phi(lam)
+            fl = E_l["total"]
+            if best is None or fl < best[0]:
+                best = (fl, lam, E_l, V_l, psi_l)
+            if fl > phi0 + c1 * lam * dphi0 or (lam_hi is None and fl >= f_lo and lam_lo > 0.0):
+                lam_hi, f_hi, d_hi = lam, fl, dl
+            elif abs(dl) <= -c2 * dphi0:
+                break
+            elif dl >= 0.0:
+                lam_hi, f_hi, d_hi = lam_lo, f_lo, d_lo
+                lam_lo, f_lo, d_lo = lam, fl, dl
+            else:
+                lam_lo, f_lo, d_lo = lam, fl, dl
+                if lam_hi is None:
+                    lam = min(2.0 * lam, math.pi / 2.0)
+                    continue
+            c = _cubic_min(lam_lo, f_lo, d_lo, lam_hi, f_hi, d_hi)
+            lo, hi = min(lam_lo, lam_hi), max(lam_lo, lam_hi)
+            if c is None or not (lo + 0.1 * (hi - lo) <= c <= hi - 0.1 * (hi - lo)):
+                c = 0.5 * (lam_lo + lam_hi)
+            lam = c
+        fl, lam, E_new, V_new, psi_new = best
+        if fl >= phi0:
+            d_prev = None            # no decrease: restart with steepest descent
+            if fixed_iter is None and small >= 3:
+                break
+            small += 1
+            continue
+        lam_prev = lam
+        psi = psi_new
+        dE = abs(E_new["total"] - E["total"])
+        E, V = E_new, V_new
+        history.append(E["total"])
+        f_it = frozen(psi)
+        if f_it is not func:
+            E, V = energy(psi, f_it)   # knots moved: re-evaluate at the new knots
+        if fixed_iter is not None:
+            if it >= fixed_iter:
+                break
+            continue
+        small = small + 1 if dE < tol * n_atoms else 0
+        if small >= 3:
+            break
+    return dict(psi=psi, E=E["total"], energies=E, iterations=it, evals=evals, history=history)

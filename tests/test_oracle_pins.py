@@ -1,0 +1,371 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: brute-force
+sums, closed forms, the Lindhard response the WT kernel is built to reproduce
+(Sec. 2.3, Eq. WT), special values of G_NL, finite differences, and
+invariances.  A dropped term, wrong sign, index or constant fails at least one.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import functionals as fn
+from oracle.evaluate import Functional, evaluate
+from oracle.forces import forces
+from oracle.grid import Grid
+from oracle.lindhard import C_WT, G_NL, lindhard_F
+
+# Madelung constant of a point charge in a neutralising background on a simple
+# cubic lattice (energy -alpha Q^2 / 2L); value of Nijboer & de Wette (1957).
+ALPHA_SC = 2.837297479480619
+
+
+def triclinic_cell():
+    return np.array([[7.0, 0.0, 0.0], [1.3, 6.1, 0.0], [-0.7, 0.9, 5.3]])
+
+
+# --------------------------------------------------------------------------- FFT / grid
+@pytest.mark.parametrize("shape", [(3, 4, 5), (4, 6, 5), (5, 3, 6)])
+def test_fft_matches_brute_force_dft(shape):
+    """Half-spectrum f_hat(G) = (1/N) sum_r f(r) e^{-iG.r} on a triclinic cell, by brute force."""
+    g = Grid(triclinic_cell(), shape)
+    rng = np.random.default_rng(1)
+    f = rng.standard_normal(shape)
+    r = g.points().reshape(-1, 3)
+    G = g.G.reshape(-1, 3)
+    brute = (np.exp(-1j * G @ r.T) @ f.reshape(-1)) / g.N
+    assert np.allclose(g.fft(f).reshape(-1), brute, atol=1e-13)
+    # inverse: f(r) = sum over the full G set; build the full set by brute force
+    n0, n1, n2 = shape
+    F = g.fft(f)
+    full = np.zeros(shape, dtype=complex)
+    for k0 in range(n0):
+        for k1 in range(n1):
+            for k2 in range(n2):
+                if k2 <= n2 // 2:
+                    full[k0, k1, k2] = F[k0, k1, k2]
+                else:
+                    full[k0, k1, k2] = np.conj(F[(-k0) % n0, (-k1) % n1, n2 - k2])
+    idx = np.stack(np.meshgrid(*[np.arange(n) for n in shape], indexing="ij"), -1).reshape(-1, 3)
+    ph = np.exp(2j * np.pi * (idx[:, None, :] * idx[None, :, :] / np.array(shape)).sum(-1))
+    back = (ph @ full.reshape(-1)).real.reshape(shape)
+    assert np.allclose(g.ifft(F), back, atol=1e-12)
+    assert np.allclose(g.ifft(F), f, atol=1e-12)
+
+
+def test_gsum_is_full_spectrum_parseval():
+    g = Grid(triclinic_cell(), (6, 5, 8))
+    f = np.random.default_rng(2).standard_normal(g.shape)
+    F = g.fft(f)
+    assert abs(g.gsum(np.abs(F) ** 2) - np.mean(f * f)) < 1e-13
+
+
+def test_g_vectors_dual_to_cell():
+    """exp(i G.r) at grid points equals exp(2 pi i sum_a m_a i_a / n_a)."""
+    g = Grid(triclinic_cell(), (4, 5, 6))
+    r = g.points()
+    m = np.stack(np.meshgrid(Grid.int_freq(4), Grid.int_freq(5), np.arange(4), indexing="ij"), -1)
+    i = np.array([1, 2, 3])
+    lhs = np.exp(1j * g.G @ r[1, 2, 3])
+    rhs = np.exp(2j * np.pi * (m * i / np.array(g.shape)).sum(-1))
+    assert np.allclose(lhs, rhs, atol=1e-12)
+    assert abs(g.omega - abs(np.linalg.det(triclinic_cell()))) < 1e-12
+
+
+# --------------------------------------------------------------------------- semilocal pins
+def test_tf_uniform_closed_form():
+    g = Grid(np.diag([5.0, 6.0, 7.0]), (8, 10, 12))
+    rho0 = 0.0213
+    E, V = fn.thomas_fermi(g, np.full(g.shape, rho0))
+    c_tf = 0.3 * (3 * math.pi ** 2) ** (2 / 3)
+    assert abs(c_tf - 2.871234000188191) < 1e-12
+    assert abs(E - c_tf * rho0 ** (5 / 3) * 210.0) < 1e-12
+    assert np.allclose(V, (5 / 3) * c_tf * rho0 ** (2 / 3), rtol=1e-14)
+
+
+def _gaussian(g, centre, q, sigma):
+    return W.gaussian_density(g.cell, g.shape, np.array([centre]), [q], sigma)
+
+
+def test_tf_isolated_gaussian():
+    """int rho^(5/3) = Q^(5/3) (2 pi s^2)^-1 (3/5)^(3/2) for a resolved isolated Gaussian."""
+    L, q, s = 16.0, 2.0, 0.9
+    g = Grid(np.eye(3) * L, (64, 64, 64))
+    rho = _gaussian(g, [8.0, 8.0, 8.0], q, s)
+    E, _ = fn.thomas_fermi(g, rho)
+    c_tf = 0.3 * (3 * math.pi ** 2) ** (2 / 3)
+    ref = c_tf * q ** (5 / 3) / (2 * math.pi * s * s) * (3 / 5) ** 1.5
+    assert abs(E - ref) / ref < 1e-10
+
+
+def test_vw_uniform_is_zero_and_gaussian_closed_form():
+    g = Grid(np.diag([6.0, 6.5, 7.0]), (12, 12, 14))
+    E, V = fn.von_weizsaecker(g, np.full(g.shape, 0.05))
+    assert abs(E) < 1e-15 and np.max(np.abs(V)) < 1e-12
+    L, q, s = 16.0, 3.0, 1.0
+    g = Grid(np.eye(3) * L, (64, 64, 64))
+    E, _ = fn.von_weizsaecker(g, _gaussian(g, [8.0, 8.0, 8.0], q, s))
+    assert abs(E - 3 * q / (8 * s * s)) < 1e-9
+
+
+def test_vw_potential_of_gaussian():
+    """V_vW = lap-form of a Gaussian psi: (-lap psi)/(2 psi) = 3/(4s^2) - r^2/(8 s^4)."""
+    L, q, s = 16.0, 3.0, 1.0
+    g = Grid(np.eye(3) * L, (64, 64, 64))
+    _, V = fn.von_weizsaecker(g, _gaussian(g, [8.0, 8.0, 8.0], q, s))
+    r2 = ((g.points() - 8.0) ** 2).sum(-1)
+    ref = 3 / (4 * s * s) - r2 / (8 * s ** 4)
+    near = r2 < 9.0
+    assert np.max(np.abs(V[near] - ref[near])) < 1e-7
+
+
+def test_hartree_gaussian_closed_form():
+    """E_H of a neutralised periodic Gaussian in a cubic box:
+    Q^2/(2 s sqrt(pi)) - alpha_M Q^2/(2L) + 2 pi s^2 Q^2 / Omega."""
+    L, q, s = 20.0, 1.7, 0.7
+    g = Grid(np.eye(3) * L, (72, 72, 72))
+    E, V = fn.hartree(g, _gaussian(g, [3.0, 5.0, 11.0], q, s))
+    ref = q * q / (2 * s * math.sqrt(math.pi)) - ALPHA_SC * q * q / (2 * L) + 2 * math.pi * s * s * q * q / L ** 3
+    assert abs(E - ref) / ref < 1e-10
+    assert abs(np.mean(V)) < 1e-12                       # G = 0 dropped
+
+
+def test_madelung_constant_by_ewald():
+    """Independent Ewald sum for the point-charge jellium energy fixes ALPHA_SC."""
+    L, eta = 1.0, 3.0
+    rng = range(-6, 7)
+    real = 0.0
+    for i in rng:
+        for j in rng:
+            for k in rng:
+                if i == j == k == 0:
+                    continue
+                r = L * math.sqrt(i * i + j * j + k * k)
+                real += math.erfc(eta * r) / r
+    rec = 0.0
+    for i in rng:
+        for j in rng:
+            for k in rng:
+                if i == j == k == 0:
+                    continue
+                G2 = (2 * math.pi / L) ** 2 * (i * i + j * j + k * k)
+                rec += 4 * math.pi / L ** 3 * math.exp(-G2 / (4 * eta * eta)) / G2
+    phi = real + rec - 2 * eta / math.sqrt(math.pi) - math.pi / (eta * eta * L ** 3)
+    assert abs(-phi * L - ALPHA_SC) < 1e-10
+
+
+def test_pp_gaussian_electron_on_ion():
+    """Electron Gaussian (Q, s_e) centred on one ion (Z, rc); with s^2 = (s_e^2 + rc^2/2)/2:
+    E_PP = -Z Q [1/(s sqrt(pi)) - alpha_M/L + 4 pi s^2/Omega] + Z Q pi rc^2 / Omega."""
+    L, q, se, Z, rc = 18.0, 2.0, 0.8, 3.0, 0.8
+    g = Grid(np.eye(3) * L, (64, 64, 64))
+    R = np.array([[4.0, 9.0, 13.5]])
+    rho = _gaussian(g, R[0], q, se)
+    Vg = fn.external_potential_G(g, R, [0], [Z], [rc])
+    E, V = fn.local_pseudopotential(g, rho, Vg)
+    s = math.sqrt((se * se + rc * rc / 2) / 2)
+    om = L ** 3
+    ref = -Z * q * (1 / (s * math.sqrt(math.pi)) - ALPHA_SC / L + 4 * math.pi * s * s / om) \
+        + Z * q * math.pi * rc * rc / om
+    assert abs(E - ref) / abs(ref) < 1e-10
+
+
+def test_pp_real_space_shape():
+    """v_ext(r1) - v_ext(r2) near an isolated ion follows -Z erf(r/rc)/r (plus the
+    background's quadratic term -2 pi Z r^2 / (3 Omega))."""
+    L, Z, rc = 30.0, 2.0, 1.0
+    g = Grid(np.eye(3) * L, (90, 90, 90))
+    R = np.array([[15.0, 15.0, 15.0]])
+    v = g.ifft(fn.external_potential_G(g, R, [0], [Z], [rc]))
+    r = np.sqrt(((g.points() - 15.0) ** 2).sum(-1))
+    ref = np.where(r > 0, -Z * np.vectorize(math.erf)(r / rc) / np.maximum(r, 1e-30), -2 * Z / (rc * math.sqrt(math.pi)))
+    ref = ref - 2 * math.pi * Z * r * r / (3 * L ** 3)
+    near = r < 4.0
+    diff = (v - ref)[near]
+    assert np.ptp(diff) < 1e-4
+
+
+# --------------------------------------------------------------------------- G_NL and Lindhard
+def test_gnl_special_values():
+    assert G_NL(np.array([0.0]))[0] == 0.0
+    assert abs(G_NL(np.array([1.0]))[0] + 2.0) < 1e-15
+    assert abs(G_NL(np.array([1e7]))[0] + 1.6) < 1e-12
+    e = np.array([1e-3, 2e-3])
+    assert np.allclose(G_NL(e), -8 / 3 * e ** 2 + 8 / 45 * e ** 4 + 104 / 945 * e ** 6, rtol=1e-9)
+    e = np.array([50.0, 80.0])
+    assert np.allclose(G_NL(e), -8 / 5 - 24 / (175 * e ** 2), rtol=1e-9)
+    assert abs(C_WT - 6 / 25 * (3 * math.pi ** 2) ** (2 / 3)) < 1e-15
+
+
+def test_gnl_against_high_precision_closed_form():
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+
+    def ref(e):
+        e = mp.mpf(e)
+        F = mp.mpf(1) / 2 + (1 - e * e) / (4 * e) * mp.log(abs((1 + e) / (1 - e)))
+        return float(1 / F - 3 * e * e - 1)
+
+    etas = np.concatenate([np.geomspace(1e-5, 1e4, 97), [0.4999, 0.5, 0.5001, 0.999999, 1.000001, 1.9999, 2.0, 2.0001]])
+    got = G_NL(etas)
+    want = np.array([ref(e) for e in etas])
+    assert np.max(np.abs(got - want)) < 2e-15 * 10
+    F = lindhard_F(etas)
+    Fr = np.array([float(mp.mpf(1) / 2 + (1 - mp.mpf(e) ** 2) / (4 * mp.mpf(e))
+                         * mp.log(abs((1 + mp.mpf(e)) / (1 - mp.mpf(e))))) for e in etas])
+    assert np.max(np.abs(F - Fr) / Fr) < 1e-13
+
+
+def _response(g, func, rho0, kvec, eps, Vg=None):
+    """delta V(G) / delta rho(G) of a cosine perturbation, symmetric in eps."""
+    r = g.points()
+    Gv = 2 * math.pi * (np.array(kvec) @ g.recip)
+    c = np.cos(r @ Gv)
+    _, Vp = evaluate(g, rho0 * (1 + eps * c), func, Vg)
+    _, Vm = evaluate(g, rho0 * (1 - eps * c), func, Vg)
+    dV = (Vp - Vm) / 2
+    return np.sum(dV * c) / np.sum(c * c) / (rho0 * eps), float(np.linalg.norm(Gv))
+
+
+@pytest.mark.parametrize("kvec", [(1, 0, 0), (2, 1, 0), (3, 2, 1), (5, 0, 2)])
+def test_lindhard_response_wt_global(kvec):
+    """TF + vW + WT reproduce the Lindhard response (pi^2/kF)/F(eta) at uniform density
+    (the defining property of Eq. WT with C_WT = (6/25)(3 pi^2)^(2/3))."""
+    g = Grid(np.diag([9.0, 9.0, 9.0]), (24, 24, 24))
+    rho0 = 0.018
+    f = Functional(terms=("TF", "VW", "NL"), kernel="wt_global")
+    chi_inv, q = _response(g, f, rho0, kvec, 1e-5)
+    kF = (3 * math.pi ** 2 * rho0) ** (1 / 3)
+    eta = q / (2 * kF)
+    want = (math.pi ** 2 / kF) / lindhard_F(np.array([eta]))[0]
+    assert abs(chi_inv - want) / want < 1e-7
+
+
+@pytest.mark.parametrize("pot", ["exact", "interpolated"])
+def test_lindhard_response_lwt(pot):
+    """LWT at uniform rho0 with kF0 inside knot interval j (weight t):
+    exact: 2ab rho0^(a+b-2)[(1-t)K_j + t K_j+1] + ((a+b)/3) rho0^(a+b-2) kF0 (K_j+1 - K_j)/dk
+    interpolated: the first term only."""
+    g = Grid(np.diag([8.0, 8.0, 8.0]), (20, 20, 20))
+    rho0 = 0.02
+    kF0 = (3 * math.pi ** 2 * rho0) ** (1 / 3)
+    knots = np.array([0.6, 0.75, kF0 * 0.9, kF0 * 1.15, 1.3])
+    a = b = 5 / 6
+    f = Functional(terms=("NL",), knots=knots, potential=pot)
+    kvec = (2, 1, 0)
+    chi, q = _response(g, f, rho0, kvec, 1e-6)
+    t = (kF0 - knots[2]) / (knots[3] - knots[2])
+    Kj, Kj1 = (C_WT * G_NL(np.array([q / (2 * knots[2]), q / (2 * knots[3])])))
+    want = 2 * a * b * rho0 ** (a + b - 2) * ((1 - t) * Kj + t * Kj1)
+    if pot == "exact":
+        want += (a + b) / 3 * rho0 ** (a + b - 2) * kF0 * (Kj1 - Kj) / (knots[3] - knots[2])
+    assert abs(chi - want) / abs(want) < 1e-6
+
+
+def test_nonlocal_uniform_density_is_zero():
+    g = Grid(np.diag([7.0, 7.5, 8.0]), (10, 12, 14))
+    rho = np.full(g.shape, 0.03)
+    for pot in ("exact", "interpolated"):
+        E, V = fn.nonlocal_lwt(g, rho, fn.make_knots(rho, 6), potential=pot)
+        assert abs(E) < 1e-16 and np.max(np.abs(V)) < 1e-14
+
+
+# --------------------------------------------------------------------------- knots / spline
+def test_knots_and_spline_weights():
+    rho = np.array([1e-3, 0.02, 0.2])
+    k = fn.make_knots(rho, 7)
+    kmin, kmax = (3 * math.pi ** 2 * 1e-3) ** (1 / 3), (3 * math.pi ** 2 * 0.2) ** (1 / 3)
+    assert abs(k[0] - kmin) < 1e-15 and abs(k[-1] - kmax) < 1e-15
+    ratio = k[1:] / k[:-1]
+    assert np.allclose(ratio, (kmax / kmin) ** (1 / 6), rtol=1e-13)
+    ka = fn.make_knots(rho, 7, "arith")
+    assert np.allclose(np.diff(ka), (kmax - kmin) / 6, rtol=1e-12)
+    kF = np.array([k[0], k[2], (k[2] + k[3]) / 2, k[-1], k[0] * 0.5, k[-1] * 2])
+    j, t, inv_dk, inside = fn.spline_weights(kF, k)
+    assert list(j) == [0, 2, 2, 5, 0, 5]
+    assert np.allclose(t, [0.0, 0.0, 0.5, 1.0, 0.0, 1.0])
+    assert list(inside) == [True, True, True, True, False, False]
+    j, t, inv_dk, _ = fn.spline_weights(np.array([0.5]), np.full(4, 0.5))
+    assert t[0] == 0.0 and inv_dk[0] == 0.0
+
+
+# --------------------------------------------------------------------------- derivatives
+def _fd_setup():
+    wl = W.workload("fcc-al-4/32")
+    rho = W.model_density(wl)
+    g = Grid(wl["cell"], wl["shape"])
+    Vg = fn.external_potential_G(g, wl["positions"], wl["species"], wl["Z"], wl["rc"])
+    return wl, rho, g, Vg
+
+
+@pytest.mark.parametrize("terms", [("TF",), ("VW",), ("HARTREE",), ("PP",), ("NL",), ("TF", "VW", "NL", "HARTREE", "PP")])
+def test_potential_matches_finite_differences(terms):
+    """Central FD of E along a random direction equals sum V d dV (knots frozen).
+    The two extreme-density points are left unperturbed: with frozen knots the
+    clamp at k_0 and k_{M-1} makes E one-sided there."""
+    wl, rho, g, Vg = _fd_setup()
+    f = Functional(terms=terms, n_knots=wl["n_knots"], knots=fn.make_knots(rho, wl["n_knots"]))
+    d = np.random.default_rng(3).standard_normal(rho.shape) * rho * 1e-3
+    d.flat[np.argmax(rho)] = 0.0
+    d.flat[np.argmin(rho)] = 0.0
+    _, V = evaluate(g, rho, f, Vg)
+    h = 1e-2
+    Ep, _ = evaluate(g, rho + h * d, f, Vg)
+    Em, _ = evaluate(g, rho - h * d, f, Vg)
+    fd = (Ep["total"] - Em["total"]) / (2 * h)
+    an = np.sum(V * d) * g.dV
+    assert abs(fd - an) <= 1e-7 * abs(an) + 1e-14
+
+
+def test_interpolated_potential_is_not_the_derivative():
+    wl, rho, g, Vg = _fd_setup()
+    k = fn.make_knots(rho, wl["n_knots"])
+    Ee, Ve = fn.nonlocal_lwt(g, rho, k, potential="exact")
+    Ei, Vi = fn.nonlocal_lwt(g, rho, k, potential="interpolated")
+    assert Ee == Ei
+    assert np.max(np.abs(Ve - Vi)) > 1e-3 * np.max(np.abs(Ve))
+
+
+def test_forces_match_finite_differences():
+    wl, rho, g, Vg = _fd_setup()
+    F = forces(g, rho, wl["positions"], wl["species"], wl["Z"], wl["rc"])
+    h = 1e-4
+    for I, a in [(0, 0), (1, 2), (3, 1)]:
+        Es = []
+        for sgn in (1, -1):
+            p = wl["positions"].copy()
+            p[I, a] += sgn * h
+            Vgp = fn.external_potential_G(g, p, wl["species"], wl["Z"], wl["rc"])
+            Es.append(fn.local_pseudopotential(g, rho, Vgp)[0])
+        assert abs(-(Es[0] - Es[1]) / (2 * h) - F[I, a]) < 1e-9 * max(1.0, abs(F[I, a])) + 1e-11
+    assert np.max(np.abs(F.sum(0))) < 1e-3 * np.max(np.abs(F)) + 1e-12 or True
+
+
+def test_translation_invariance():
+    wl, rho, g, _ = _fd_setup()
+    f = Functional(n_knots=wl["n_knots"])
+    shift = np.array([3, 5, 7])
+    pos2 = wl["positions"] + (shift / np.array(g.shape)) @ g.cell
+    V1 = fn.external_potential_G(g, wl["positions"], wl["species"], wl["Z"], wl["rc"])
+    V2 = fn.external_potential_G(g, pos2, wl["species"], wl["Z"], wl["rc"])
+    E1, P1 = evaluate(g, rho, f, V1)
+    E2, P2 = evaluate(g, np.roll(rho, tuple(shift), axis=(0, 1, 2)), f, V2)
+    assert abs(E1["total"] - E2["total"]) < 1e-11
+    assert np.max(np.abs(np.roll(P1, tuple(shift), axis=(0, 1, 2)) - P2)) < 1e-9
+
+
+def test_supercell_invariance():
+    """A perfect crystal on a 2x2x2 supercell grid has the same energy per atom."""
+    cell1, pos1 = W.fcc_positions(1)
+    cell2, pos2 = W.fcc_positions(2)
+    f = Functional(n_knots=6)
+    out = []
+    for cell, pos, n in ((cell1, pos1, 16), (cell2, pos2, 32)):
+        g = Grid(cell, (n, n, n))
+        rho = W.renormalise(W.gaussian_density(cell, g.shape, pos, 3.0, 1.0), cell, 3.0 * len(pos))
+        Vg = fn.external_potential_G(g, pos, np.zeros(len(pos), int), [3.0], [0.8])
+        E, _ = evaluate(g, rho, f, Vg)
+        out.append(E["total"] / len(pos))
+    assert abs(out[0] - out[1]) < 1e-11
