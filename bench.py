@@ -1,0 +1,346 @@
+"""Benchmark of the OFDFT energy + potential evaluation on GB300.
+
+Workload (default): FCC Al, 4x4x4 conventional cells (256 atoms, a = 7.65 bohr),
+128^3 grid, analytic local PP (Z = 3, rc = 0.8), TF + vW + Hartree + PP + LWT
+nonlocal KEDF with 16 log-spaced kF knots, exact potential, FP32-mixed
+(FP32 FFT/pointwise, FP64 energies/knots).  One step = one full E+V
+evaluation (all kernels of the path) of one density; the density is resident
+in HBM when the timed region starts.  L2 is flushed (a 512 MB write) before
+every timed step and the flush is outside the timed events.
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead
+(a bounded sample of the same workload on the host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "OFDFT E+V evals: grid points/s, FP32-mixed vs FP64 on GB300 at ≤1e-6 Ha/atom"
+UNIT = "grid points/s"
+WORKLOAD = "fcc-al-256/128"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            for k in ("hbm_gbs", "hbm_GBps", "hbm"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return 6800.0, "fallback"
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.p = None
+        self.out = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        try:
+            os.makedirs(os.path.dirname(self.out), exist_ok=True)
+            self.f = open(self.out, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.out):
+            c = [x.strip() for x in line.split(",")]
+            if len(c) < 9:
+                continue
+            try:
+                sm.append(float(c[1]))
+                mx = float(c[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, c[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_input(wl):
+    import workloads as W
+    return W.model_density(wl)
+
+
+def run_gpu(args):
+    import torch
+    import paper_2002_02985_gb300 as ofd
+    import workloads as W
+    from paper_2002_02985_gb300 import _lib as L
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    wl = W.workload(WORKLOAD)
+    rho64 = make_input(wl)
+    N = rho64.size
+    stream = torch.cuda.current_stream()
+    g = ofd.Grid(wl["cell"], wl["shape"], stream=stream)
+    g.set_ions(wl["positions"], wl["species"], wl["Z"], wl["rc"])
+    f32 = ofd.Functional(n_knots=wl["n_knots"], precision=L.FP32_MIXED)
+    f64 = ofd.Functional(n_knots=wl["n_knots"], precision=L.FP64)
+    rho = torch.from_numpy(rho64.astype(np.float32)).to(dev)
+    V = torch.empty_like(rho)
+    E_dev = torch.zeros(8, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(func, r, v):
+        g.energy_potential_async(r, func, E_dev, v)
+
+    # correctness snapshot (FP32-mixed and FP64) vs each other before timing
+    E32, _ = g.energy_potential(rho, f32)
+    rho_d = rho.double()
+    E64, _ = g.energy_potential(rho_d, f64)
+
+    for _ in range(args.warmup):
+        step(f32, rho, V)
+    torch.cuda.synchronize()
+
+    def timed(func, r, v, steps, profile=False):
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        if profile:
+            g.profile_reset()
+            g.profile(True)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(steps):
+            flush.fill_(float(i))                     # evict L2 (untimed)
+            starts[i].record(stream)
+            step(func, r, v)
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        if profile:
+            g.profile(False)
+        ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        return ms, wall
+
+    clk = Clocks(local)
+    ms32, wall32 = timed(f32, rho, V, args.steps, profile=True)
+    clocks = clk.stop()
+    prof = g.profile_read()
+    t_step = sum(ms32) / len(ms32)
+    t_max = t_step
+    if dist:
+        t = torch.tensor([t_step], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t)
+    value = N * world / (t_max * 1e-3)
+
+    # FP64 path (the speed-up denominator), fewer steps
+    V64 = torch.empty_like(rho_d)
+    for _ in range(2):
+        step(f64, rho_d, V64)
+    ms64, _ = timed(f64, rho_d, V64, max(3, args.steps // 4))
+    t64 = sum(ms64) / len(ms64)
+
+    # end to end through the public API: H2D of rho from pinned host memory,
+    # evaluation, D2H of V and the energies, every step
+    host_rho = torch.from_numpy(rho64.astype(np.float32)).pin_memory()
+    host_V = torch.empty(rho.shape, dtype=torch.float32).pin_memory()
+    rho_e = torch.empty_like(rho)
+    for _ in range(2):
+        rho_e.copy_(host_rho, non_blocking=True)
+        E_, V_ = g.energy_potential(rho_e, f32)
+        host_V.copy_(V_, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_steps = max(3, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        rho_e.copy_(host_rho, non_blocking=True)
+        E_, V_ = g.energy_potential(rho_e, f32)      # synchronises and reads E to the host
+        host_V.copy_(V_, non_blocking=True)
+    torch.cuda.synchronize()
+    t_e2e = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": N * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(N * 4),
+           "d2h_bytes_per_step": int(N * 4 + 48)}
+
+    # roofline of the dominant kernel (largest total time)
+    top = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (launches, tot_ms) = top
+    alg = algorithmic_bytes(name, wl, 4)
+    avg_s = tot_ms / max(1, launches) * 1e-3
+    peak, kind = peaks()
+    achieved = alg / avg_s / 1e9
+    traffic = measured_traffic(name)
+    roof = {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1), "peak": peak, "peak_kind": kind,
+            "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+            "algorithmic_bytes_per_launch": alg, "avg_launch_ms": round(avg_s * 1e3, 5)}
+    kernels = {k: {"launches": n, "avg_ms": round(t / max(1, n), 5), "share": round(t / max(1e-12, sum(
+        v[1] for v in prof.values())), 4)} for k, (n, t) in prof.items()}
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t_max, 5), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": list(wl["shape"]), "atoms": wl["n_atoms"],
+                   "n_knots": wl["n_knots"], "functional": "TF+vW+H+PP+LWT(exact V)",
+                   "reductions": "f64", "l2": "flushed (512 MB write) before every timed step",
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "fp64": {"value": round(N * world / (t64 * 1e-3), 1), "ms_per_step": round(t64, 4),
+                 "speedup_fp32_mixed": round(t64 / t_max, 2)},
+        "energy_check": {"fp32_mixed_total": E32["total"], "fp64_total": E64["total"],
+                         "fp32_vs_fp64_Ha_per_atom": abs(E32["total"] - E64["total"]) / wl["n_atoms"]},
+        "roofline": roof, "kernels": kernels,
+        "gpu_launches": int(sum(n for n, _ in prof.values())),
+        "e2e": e2e, "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, rho64, args.cpu_budget)
+        eo = line["cpu_baseline"].get("E_total")
+        if eo is not None:
+            line["energy_check"]["fp32_vs_oracle_Ha_per_atom"] = abs(E32["total"] - eo) / wl["n_atoms"]
+            line["energy_check"]["fp64_vs_oracle_Ha_per_atom"] = abs(E64["total"] - eo) / wl["n_atoms"]
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def algorithmic_bytes(kernel, wl, esize):
+    """Bytes a kernel must move per launch: its channel half-spectra in and out (complex of
+    2*esize bytes), the density in and the potential out, as the pipeline defines them."""
+    n0, n1, n2 = wl["shape"]
+    N = n0 * n1 * n2
+    NH = n0 * n1 * (n2 // 2 + 1)
+    M = wl["n_knots"]
+    ch = 3 + M                    # Hartree+PP, vW, rho^beta/T2, M knots (exact potential)
+    c = 2 * esize
+    table = {
+        "stats": N * esize,
+        "row_fwd": N * esize + ch * NH * c,
+        "pencil_fwd": 2 * ch * NH * c,
+        "axis0_recip": 2 * ch * NH * c + NH * c,      # + V_ext(G)
+        "pencil_inv": 2 * ch * NH * c,
+        "row_inv": ch * NH * c + 2 * N * esize,
+    }
+    return int(table.get(kernel, 0))
+
+
+def measured_traffic(kernel):
+    """dram bytes per launch from the committed ncu summary of the same kernel, if any."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            if kernel in d:
+                return d[kernel]
+        except Exception:
+            pass
+    return None
+
+
+def cpu_baseline(wl, rho64, budget_s):
+    """The FP64 oracle as it stands on the host cores: whole E+V evaluations of the same
+    workload until ~budget_s seconds have passed (at least one)."""
+    from oracle import functionals as ofn
+    from oracle.evaluate import Functional as OF, evaluate
+    from oracle.grid import Grid as OG
+    og = OG(wl["cell"], wl["shape"])
+    Vg = ofn.external_potential_G(og, wl["positions"], wl["species"], wl["Z"], wl["rc"])
+    rho = rho64.astype(np.float32).astype(np.float64)
+    of = OF(n_knots=wl["n_knots"])
+    t0 = time.perf_counter()
+    n = 0
+    E = None
+    while True:
+        E, _ = evaluate(og, rho, of, Vg)
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": round(rho.size * n / dt, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} full E+V evaluation(s) of {WORKLOAD} (numpy FP64, single thread)",
+            "seconds": round(dt, 2), "E_total": E["total"]}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import workloads as W
+    wl = W.workload(WORKLOAD)
+    rho64 = make_input(wl)
+    per = []
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        cpu_baseline(wl, rho64, 0.0)
+    res = None
+    for _ in range(args.steps):
+        res = cpu_baseline(wl, rho64, 0.0)
+        per.append(rho64.size / res["value"])
+    t = sum(per) / len(per)
+    v = rho64.size / t
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t * 1e3, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "grid": list(wl["shape"]),
+                                            "n_knots": wl["n_knots"]},
+            "cpu_baseline": {"value": round(v, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} full E+V evaluations of {WORKLOAD}"},
+            "e2e": {"value": round(v, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

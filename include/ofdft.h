@@ -1,0 +1,183 @@
+/*
+ * ofdft.h -- C ABI of the GB300 orbital-free DFT energy/potential library.
+ *
+ * The library evaluates, for an electron density rho on a periodic 3-D grid,
+ * the energy E[rho] = T_TF + T_vW + T_NL + E_H + E_PP and its functional
+ * derivative V = dE/drho (arXiv:2002.02985, Sec. 1 Eqs. efunc and euler),
+ * the ionic forces of the electron-ion term, and the psi = sqrt(rho) density
+ * optimisation of Sec. 2.4 (Eq. euler2).  T_NL is the density-dependent-kernel
+ * nonlocal KEDF (LWT) evaluated with linear splines over a set of kF knots,
+ * steps s1-s4 of Sec. 2.3 (Eqs. nl2, WT and the G_NL definition).
+ *
+ * Conventions (all entry points)
+ *   - Units: Hartree atomic units; lengths in bohr, energies in Ha.
+ *   - Cell: cell[9] holds the lattice vectors a_0, a_1, a_2 as rows (bohr),
+ *     row-major.  Grid shape[3] = {n0, n1, n2}; fields are contiguous C-order
+ *     arrays [n0][n1][n2] (n2 fastest) of float (OFDFT_FP32_MIXED) or double
+ *     (OFDFT_FP64) in DEVICE memory owned by the caller.  Each n_a must be
+ *     of the form 2^a 3^b 5^c with 2 <= n_a <= 1024.
+ *   - Fourier convention: f_hat(G) = (1/N) sum_r f(r) e^{-iG.r}; the integer
+ *     frequency of index k on an axis of n points is k for k <= n/2, else k-n.
+ *   - V is the functional derivative in Ha/e: dE/drho_r = V_r * Omega/N.
+ *   - All device work is enqueued on the stream given to ofdft_grid_create.
+ *     Calls that return host values synchronise that stream.
+ *
+ * Ownership: the caller owns every density/potential buffer.  The library
+ * owns the grid handle and its workspace (allocated with cudaMalloc on first
+ * use for a precision and freed by ofdft_grid_destroy).  Nothing returned
+ * needs freeing except the handle.  A handle must not be used from two host
+ * threads at once.
+ *
+ * Errors: every entry point returns an int status; 0 = OFDFT_OK.  On error the
+ * handle keeps a message readable with ofdft_last_error().  No C++ exception
+ * crosses the ABI.
+ */
+#ifndef OFDFT_H
+#define OFDFT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define OFDFT_OK                    0
+#define OFDFT_ERR_INVALID_ARG      -1  /* null pointer, bad shape, singular cell, bad knot count */
+#define OFDFT_ERR_UNSUPPORTED_SIZE -2  /* a grid dimension not 2^a3^b5^c or outside [2, 1024] */
+#define OFDFT_ERR_BAD_DENSITY      -3  /* NaN/Inf or negative density found */
+#define OFDFT_ERR_OOM              -4  /* cudaMalloc failed */
+#define OFDFT_ERR_CUDA             -5  /* any other CUDA error (message kept in the handle) */
+#define OFDFT_ERR_NOT_CONVERGED    -6  /* optimiser reached max_iter */
+#define OFDFT_ERR_NO_IONS          -7  /* a call needs ions but ofdft_set_ions was not called */
+
+/* ---- functional description ----------------------------------------- */
+#define OFDFT_TERM_TF       1u   /* Thomas-Fermi  C_TF int rho^(5/3)             */
+#define OFDFT_TERM_VW       2u   /* von Weizsaecker, psi = sqrt(rho) form          */
+#define OFDFT_TERM_NL       4u   /* nonlocal KEDF (LWT spline or global-kF WT)    */
+#define OFDFT_TERM_HARTREE  8u   /* Hartree, G = 0 dropped                        */
+#define OFDFT_TERM_PP      16u   /* local pseudopotential of the ions             */
+#define OFDFT_TERMS_ALL    31u
+
+#define OFDFT_KNOTS_LOG     0    /* geometric progression of kF knots (s1)        */
+#define OFDFT_KNOTS_ARITH   1    /* arithmetic progression                        */
+
+#define OFDFT_NLPOT_EXACT   0    /* V = exact derivative of the spline energy     */
+#define OFDFT_NLPOT_INTERP  1    /* V = 2 alpha rho^(alpha-1) Phi (s3->s4 blend)  */
+
+#define OFDFT_KERNEL_LWT        0  /* kernel at the local kF(r) via the knots      */
+#define OFDFT_KERNEL_WT_GLOBAL  1  /* one WT kernel at kF(N_e/Omega)               */
+
+#define OFDFT_FP64        0      /* fields double, all arithmetic FP64            */
+#define OFDFT_FP32_MIXED  1      /* fields float, FFT/pointwise FP32, energies,
+                                    knots and optimiser scalars FP64             */
+
+typedef struct {
+    unsigned terms;        /* OR of OFDFT_TERM_* */
+    double alpha, beta;    /* exponents of Eq. nl2 (5/6, 5/6) */
+    int n_knots;           /* M >= 2, <= 64 */
+    int knot_spacing;      /* OFDFT_KNOTS_LOG | OFDFT_KNOTS_ARITH */
+    const double *knots;   /* optional HOST array of n_knots frozen knots (ascending);
+                              NULL = recompute from min/max rho on every call (s1) */
+    int nl_potential;      /* OFDFT_NLPOT_EXACT | OFDFT_NLPOT_INTERP (needs alpha == beta) */
+    int kernel;            /* OFDFT_KERNEL_LWT | OFDFT_KERNEL_WT_GLOBAL */
+    int precision;         /* OFDFT_FP64 | OFDFT_FP32_MIXED */
+    double rho_floor;      /* guard for rho^(alpha-1), 1/psi, kF (<= 0 means 1e-20) */
+} ofdft_functional;
+
+/* Analytic local pseudopotential per species: v(q) = -4 pi Z exp(-(q rc)^2/4) / q^2,
+ * i.e. -Z erf(r/rc)/r in real space; the q = 0 term is pi Z rc^2. */
+typedef struct {
+    int n_species;
+    const double *Z;       /* [n_species] valence charge */
+    const double *rc;      /* [n_species] core radius, bohr */
+} ofdft_species;
+
+typedef struct {
+    int n;                 /* number of ions */
+    const double *pos;     /* HOST [n][3] Cartesian positions, bohr */
+    const int *species;    /* HOST [n] species index */
+} ofdft_ions;
+
+typedef struct {
+    int iterations;        /* CG iterations done */
+    int evaluations;       /* energy/potential evaluations done */
+    double energy;         /* final total energy, Ha */
+    double energies[6];    /* total, TF, vW, NL, H, PP */
+    double mu;             /* chemical potential int rho V / N_e */
+    double residual;       /* || (V - mu) psi ||_2 (with dV weight) at the end */
+    double last_dE;        /* |E_k - E_{k-1}| of the last iteration */
+} ofdft_opt_report;
+
+typedef struct ofdft_grid ofdft_grid;   /* opaque */
+
+/* Create a grid for the periodic cell (cell[9], rows = lattice vectors, bohr)
+ * sampled on shape[3] points; work is enqueued on cuda_stream (a cudaStream_t,
+ * NULL = legacy default stream) of the current device.  No device memory is
+ * allocated until the first call that needs it.  Defines the Grid of Sec. 2.1. */
+int ofdft_grid_create(const double cell[9], const int shape[3], void *cuda_stream, ofdft_grid **out);
+int ofdft_grid_destroy(ofdft_grid *g);
+
+/* Set the ions and build the external potential V_ext(G) = (1/Omega) sum_I
+ * v(|G|) e^{-iG.R_I} on the half spectrum by the direct structure factor
+ * (Sec. 2.5).  Copies the host arrays; may be called again for new positions. */
+int ofdft_set_ions(ofdft_grid *g, const ofdft_ions *ions, const ofdft_species *sp);
+
+/* One energy + potential evaluation (Eq. efunc; Eq. euler for V; Sec. 2.3 s1-s4).
+ * rho_dev: device [N] float/double (precision of f), >= 0.
+ * E_out:   HOST double[6] = {total, TF, vW, NL, H, PP} (Ha); may be NULL.
+ * V_dev:   device [N] output potential (Ha/e), same precision; may be NULL.
+ * Synchronises the stream when E_out is not NULL. */
+int ofdft_energy_potential(ofdft_grid *g, const void *rho_dev, const ofdft_functional *f,
+                           double *E_out, void *V_dev);
+
+/* Same evaluation, fully asynchronous: energies are written to E_dev (DEVICE
+ * double[6]) on the stream; nothing is synchronised and no host memory is
+ * touched, so the call can be captured in a CUDA graph once the workspace
+ * exists (make one ordinary call first). */
+int ofdft_energy_potential_async(ofdft_grid *g, const void *rho_dev, const ofdft_functional *f,
+                                 double *E_dev, void *V_dev);
+
+/* Ionic forces F_I = -dE/dR_I of the electron-ion term (the only term of
+ * Eq. efunc that depends on R_I): F_I = -sum_G G v(|G|) Im[conj(rho_hat) e^{-iG.R_I}].
+ * F_out: HOST double[n_ions][3] (Ha/bohr).  precision selects the rho dtype. */
+int ofdft_forces(ofdft_grid *g, const void *rho_dev, int precision, double *F_out);
+
+/* psi = sqrt(rho) CG density optimisation (Sec. 2.4, Eq. euler2):
+ * psi_dev (device [N], precision of f) holds the initial psi and receives the
+ * result; int psi^2 = N_e is imposed first and then conserved by the
+ * psi cos(l) + p sin(l) update.  Stops when |E_k - E_{k-1}| < tol_E_per_atom *
+ * n_ions for 3 consecutive iterations (returns OFDFT_OK) or after max_iter
+ * iterations (returns OFDFT_ERR_NOT_CONVERGED with the report filled).
+ * rep may be NULL. */
+int ofdft_optimize_density(ofdft_grid *g, void *psi_dev, const ofdft_functional *f,
+                           double N_e, double tol_E_per_atom, int max_iter,
+                           ofdft_opt_report *rep);
+
+/* Batched evaluation of n independent grids (snapshots), possibly of different
+ * shapes: E_out HOST [n][6]; V_dev[i] and F_out[i] may be NULL (F_out needs ions).
+ * All grids must share one stream; the batch is enqueued back to back and
+ * synchronised once. */
+int ofdft_energy_potential_batched(int n, ofdft_grid *const *grids, const void *const *rho_dev,
+                                   const ofdft_functional *f, double *E_out,
+                                   void *const *V_dev, double *const *F_out);
+
+/* Per-kernel device timing of the evaluation pipeline (tracing aid, results
+ * unchanged).  While enabled, every kernel launch of an evaluation is bracketed
+ * by two CUDA events on the grid's stream.  ofdft_profile_read synchronises
+ * the stream, folds the finished events into running totals and returns, for
+ * kernel index idx in [0, 8), its name, launch count and total time in ms
+ * (OFDFT_ERR_INVALID_ARG for other idx).  ofdft_profile_reset zeroes the totals. */
+int ofdft_profile_enable(ofdft_grid *g, int enable);
+int ofdft_profile_reset(ofdft_grid *g);
+int ofdft_profile_read(ofdft_grid *g, int idx, const char **name, int *launches, double *total_ms);
+
+/* Human-readable text of a status code, and the handle's last error message. */
+const char *ofdft_status_string(int status);
+const char *ofdft_last_error(const ofdft_grid *g);
+
+/* Library version string. */
+const char *ofdft_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OFDFT_H */

@@ -1,0 +1,252 @@
+"""GB300-native orbital-free DFT energy/potential engine (arXiv:2002.02985 hot path).
+
+Thin Python binding over the C ABI of libofdft.so (include/ofdft.h).  PyTorch
+supplies device memory and the CUDA stream; all arithmetic of the path runs in
+the library's hand-written sm_103a kernels.  There is no CPU fallback: if the
+library is missing or no GPU is present the calls raise.
+
+    from paper_2002_02985_gb300 import Grid, Functional
+    g = Grid(cell, (128, 128, 128))
+    g.set_ions(positions, species, Z=[3.0], rc=[0.8])
+    E, V = g.energy_potential(rho, Functional(n_knots=16))
+"""
+from __future__ import annotations
+
+import ctypes as ct
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _lib as L
+
+__all__ = ["Grid", "Functional", "OFDFTError", "OFDFTEnergy", "energy_potential_batched", "library"]
+
+ENERGY_KEYS = ("total", "TF", "vW", "NL", "H", "PP")
+
+
+class OFDFTError(RuntimeError):
+    def __init__(self, status: int, message: str = ""):
+        self.status = status
+        super().__init__(f"{L.STATUS.get(status, status)}: {message}")
+
+
+def library():
+    return L.load()
+
+
+@dataclass
+class Functional:
+    """Mirror of ofdft_functional (include/ofdft.h)."""
+    terms: int = L.TERMS_ALL
+    alpha: float = 5.0 / 6.0
+    beta: float = 5.0 / 6.0
+    n_knots: int = 10
+    knot_spacing: int = L.KNOTS_LOG
+    knots: object = None            # optional frozen knots (sequence of floats)
+    nl_potential: int = L.NLPOT_EXACT
+    kernel: int = L.KERNEL_LWT
+    precision: int = L.FP32_MIXED
+    rho_floor: float = 1e-20
+
+    def to_c(self):
+        c = L.CFunctional()
+        c.terms = self.terms
+        c.alpha = self.alpha
+        c.beta = self.beta
+        c.n_knots = self.n_knots
+        c.knot_spacing = self.knot_spacing
+        keep = None
+        if self.knots is not None:
+            keep = np.ascontiguousarray(np.asarray(self.knots, dtype=np.float64))
+            c.knots = keep.ctypes.data_as(ct.POINTER(ct.c_double))
+            c.n_knots = len(keep)
+        c.nl_potential = self.nl_potential
+        c.kernel = self.kernel
+        c.precision = self.precision
+        c.rho_floor = self.rho_floor
+        return c, keep
+
+    @property
+    def torch_dtype(self):
+        import torch
+        return torch.float64 if self.precision == L.FP64 else torch.float32
+
+
+def _check(lib, status, handle=None):
+    if status != L.OFDFT_OK:
+        msg = lib.ofdft_last_error(handle).decode() if handle else lib.ofdft_status_string(status).decode()
+        raise OFDFTError(status, msg)
+
+
+def _ptr(t):
+    return ct.c_void_p(t.data_ptr())
+
+
+class Grid:
+    """A periodic cell sampled on n0 x n1 x n2 points (the paper's Grid class, Sec. 2.1)."""
+
+    def __init__(self, cell, shape, stream=None):
+        import torch
+        self.lib = library()
+        self.cell = np.ascontiguousarray(np.asarray(cell, dtype=np.float64).reshape(3, 3))
+        self.shape = tuple(int(n) for n in shape)
+        self.N = int(np.prod(self.shape))
+        self.omega = abs(float(np.linalg.det(self.cell)))
+        self.dV = self.omega / self.N
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self.device = stream.device
+        h = ct.c_void_p()
+        sh = (ct.c_int * 3)(*self.shape)
+        st = self.lib.ofdft_grid_create(self.cell.ctypes.data_as(ct.POINTER(ct.c_double)), sh,
+                                        ct.c_void_p(stream.cuda_stream), ct.byref(h))
+        _check(self.lib, st)
+        self.h = h
+        self.n_ions = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ofdft_grid_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_ions(self, positions, species, Z, rc):
+        pos = np.ascontiguousarray(np.asarray(positions, dtype=np.float64).reshape(-1, 3))
+        spc = np.ascontiguousarray(np.asarray(species, dtype=np.int32).reshape(-1))
+        Zs = np.ascontiguousarray(np.asarray(Z, dtype=np.float64).reshape(-1))
+        rcs = np.ascontiguousarray(np.asarray(rc, dtype=np.float64).reshape(-1))
+        ions = L.CIons(len(pos), pos.ctypes.data_as(ct.POINTER(ct.c_double)), spc.ctypes.data_as(ct.POINTER(ct.c_int)))
+        sp = L.CSpecies(len(Zs), Zs.ctypes.data_as(ct.POINTER(ct.c_double)), rcs.ctypes.data_as(ct.POINTER(ct.c_double)))
+        _check(self.lib, self.lib.ofdft_set_ions(self.h, ct.byref(ions), ct.byref(sp)), self.h)
+        self.n_ions = len(pos)
+
+    def _field(self, t, func: Functional):
+        import torch
+        if not (t.is_cuda and t.is_contiguous() and t.dtype == func.torch_dtype and t.numel() == self.N):
+            raise ValueError(f"expected a contiguous CUDA {func.torch_dtype} tensor of {self.N} elements")
+        return t
+
+    def energy_potential(self, rho, func: Functional, want_potential: bool = True):
+        """Returns (dict of energies in Ha, V tensor or None)."""
+        import torch
+        rho = self._field(rho, func)
+        V = torch.empty_like(rho) if want_potential else None
+        E = (ct.c_double * 6)()
+        c, keep = func.to_c()
+        st = self.lib.ofdft_energy_potential(self.h, _ptr(rho), ct.byref(c), E, _ptr(V) if V is not None else None)
+        _check(self.lib, st, self.h)
+        del keep
+        return dict(zip(ENERGY_KEYS, list(E))), V
+
+    def energy_potential_async(self, rho, func: Functional, E_dev, V=None):
+        """Enqueue one evaluation; energies go to the device tensor E_dev (float64, 6)."""
+        c, keep = func.to_c()
+        st = self.lib.ofdft_energy_potential_async(self.h, _ptr(rho), ct.byref(c), _ptr(E_dev),
+                                                   _ptr(V) if V is not None else None)
+        _check(self.lib, st, self.h)
+        del keep
+
+    def profile(self, enable: bool = True):
+        """Start/stop per-kernel CUDA-event timing of evaluations on this grid."""
+        _check(self.lib, self.lib.ofdft_profile_enable(self.h, int(enable)), self.h)
+
+    def profile_reset(self):
+        _check(self.lib, self.lib.ofdft_profile_reset(self.h), self.h)
+
+    def profile_read(self):
+        """{kernel name: (launches, total ms)} since the last reset."""
+        out = {}
+        for i in range(8):
+            nm, n, ms = ct.c_char_p(), ct.c_int(), ct.c_double()
+            _check(self.lib, self.lib.ofdft_profile_read(self.h, i, ct.byref(nm), ct.byref(n), ct.byref(ms)), self.h)
+            out[nm.value.decode()] = (n.value, ms.value)
+        return out
+
+    def forces(self, rho, precision: int = L.FP32_MIXED):
+        F = np.zeros((self.n_ions, 3))
+        st = self.lib.ofdft_forces(self.h, _ptr(rho), precision, F.ctypes.data_as(ct.POINTER(ct.c_double)))
+        _check(self.lib, st, self.h)
+        return F
+
+    def optimize_density(self, psi, func: Functional, n_electrons: float, tol_per_atom: float = 1e-6,
+                         max_iter: int = 200, raise_on_not_converged: bool = False):
+        rep = L.COptReport()
+        c, keep = func.to_c()
+        st = self.lib.ofdft_optimize_density(self.h, _ptr(self._field(psi, func)), ct.byref(c), n_electrons,
+                                             tol_per_atom, max_iter, ct.byref(rep))
+        if st != L.OFDFT_OK and not (st == -6 and not raise_on_not_converged):
+            _check(self.lib, st, self.h)
+        del keep
+        return dict(converged=(st == 0), iterations=rep.iterations, evaluations=rep.evaluations,
+                    energy=rep.energy, energies=dict(zip(ENERGY_KEYS, list(rep.energies))), mu=rep.mu,
+                    residual=rep.residual, last_dE=rep.last_dE)
+
+
+def energy_potential_batched(grids, rhos, func: Functional, want_potential=True, want_forces=False):
+    """Evaluate many snapshots (grids may differ in shape) with one synchronisation."""
+    import torch
+    lib = library()
+    n = len(grids)
+    hs = (ct.c_void_p * n)(*[g.h for g in grids])
+    rp = (ct.c_void_p * n)(*[r.data_ptr() for r in rhos])
+    Vs = [torch.empty_like(r) for r in rhos] if want_potential else None
+    vp = (ct.c_void_p * n)(*[v.data_ptr() for v in Vs]) if want_potential else None
+    E = np.zeros((n, 6))
+    Fs = [np.zeros((g.n_ions, 3)) for g in grids] if want_forces else None
+    fp = (ct.POINTER(ct.c_double) * n)(*[f.ctypes.data_as(ct.POINTER(ct.c_double)) for f in Fs]) if want_forces else None
+    c, keep = func.to_c()
+    st = lib.ofdft_energy_potential_batched(n, hs, rp, ct.byref(c), E.ctypes.data_as(ct.POINTER(ct.c_double)),
+                                            vp, fp)
+    _check(lib, st, grids[0].h if n else None)
+    del keep
+    return E, Vs, Fs
+
+
+def _autograd():
+    import torch
+
+    class OFDFTEnergy(torch.autograd.Function):
+        """E[rho, R] with a hand-written backward: dE/drho_r = V_r dV, dE/dR_I = -F_I.
+
+        The ions' positions are a float64 CPU tensor (n, 3); species/Z/rc are
+        fixed attributes of `grid` set before the call through `spec`."""
+
+        @staticmethod
+        def forward(ctx, rho, positions, grid, func, spec):
+            species, Z, rc = spec
+            grid.set_ions(positions.detach().cpu().numpy(), species, Z, rc)
+            E, V = grid.energy_potential(rho.detach(), func, want_potential=True)
+            ctx.grid, ctx.func = grid, func
+            ctx.save_for_backward(rho, V)
+            ctx.need_forces = positions.requires_grad
+            return rho.new_tensor(E["total"], dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, gout):
+            rho, V = ctx.saved_tensors
+            g_rho = (V * ctx.grid.dV) * gout.to(V.dtype)
+            g_pos = None
+            if ctx.need_forces:
+                F = ctx.grid.forces(rho.detach(), ctx.func.precision)
+                g_pos = -torch.from_numpy(F) * float(gout)
+            return g_rho, g_pos, None, None, None
+
+    return OFDFTEnergy
+
+
+class _Lazy:
+    _cls = None
+
+    def __getattr__(self, k):
+        if _Lazy._cls is None:
+            _Lazy._cls = _autograd()
+        return getattr(_Lazy._cls, k)
+
+
+OFDFTEnergy = _Lazy()

@@ -1,0 +1,89 @@
+"""ctypes declarations of the C ABI in include/ofdft.h (argument marshalling only).
+
+Loads the in-tree libofdft.so and raises if it is missing: there is no CPU
+fallback; every step of the evaluation runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libofdft.so")
+
+OFDFT_OK = 0
+STATUS = {0: "OFDFT_OK", -1: "OFDFT_ERR_INVALID_ARG", -2: "OFDFT_ERR_UNSUPPORTED_SIZE",
+          -3: "OFDFT_ERR_BAD_DENSITY", -4: "OFDFT_ERR_OOM", -5: "OFDFT_ERR_CUDA",
+          -6: "OFDFT_ERR_NOT_CONVERGED", -7: "OFDFT_ERR_NO_IONS"}
+
+TERM_TF, TERM_VW, TERM_NL, TERM_HARTREE, TERM_PP = 1, 2, 4, 8, 16
+TERMS_ALL = 31
+KNOTS_LOG, KNOTS_ARITH = 0, 1
+NLPOT_EXACT, NLPOT_INTERP = 0, 1
+KERNEL_LWT, KERNEL_WT_GLOBAL = 0, 1
+FP64, FP32_MIXED = 0, 1
+
+# symbols declared in include/ofdft.h (checked by the CPU test suite)
+EXPORTS = (
+    "ofdft_grid_create", "ofdft_grid_destroy", "ofdft_set_ions", "ofdft_energy_potential",
+    "ofdft_energy_potential_async", "ofdft_forces", "ofdft_optimize_density",
+    "ofdft_energy_potential_batched", "ofdft_status_string", "ofdft_last_error", "ofdft_version",
+    "ofdft_profile_enable", "ofdft_profile_reset", "ofdft_profile_read",
+)
+
+
+class CFunctional(ct.Structure):
+    _fields_ = [("terms", ct.c_uint), ("alpha", ct.c_double), ("beta", ct.c_double),
+                ("n_knots", ct.c_int), ("knot_spacing", ct.c_int), ("knots", ct.POINTER(ct.c_double)),
+                ("nl_potential", ct.c_int), ("kernel", ct.c_int), ("precision", ct.c_int),
+                ("rho_floor", ct.c_double)]
+
+
+class CSpecies(ct.Structure):
+    _fields_ = [("n_species", ct.c_int), ("Z", ct.POINTER(ct.c_double)), ("rc", ct.POINTER(ct.c_double))]
+
+
+class CIons(ct.Structure):
+    _fields_ = [("n", ct.c_int), ("pos", ct.POINTER(ct.c_double)), ("species", ct.POINTER(ct.c_int))]
+
+
+class COptReport(ct.Structure):
+    _fields_ = [("iterations", ct.c_int), ("evaluations", ct.c_int), ("energy", ct.c_double),
+                ("energies", ct.c_double * 6), ("mu", ct.c_double), ("residual", ct.c_double),
+                ("last_dE", ct.c_double)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ct.CDLL:
+    """Load libofdft.so (raises OSError with a clear message when it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"{path} not found: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ct.CDLL(path)
+    P, I, D, V = ct.c_void_p, ct.c_int, ct.c_double, ct.c_void_p
+    lib.ofdft_grid_create.argtypes = [ct.POINTER(D), ct.POINTER(I), P, ct.POINTER(P)]
+    lib.ofdft_grid_destroy.argtypes = [P]
+    lib.ofdft_set_ions.argtypes = [P, ct.POINTER(CIons), ct.POINTER(CSpecies)]
+    lib.ofdft_energy_potential.argtypes = [P, V, ct.POINTER(CFunctional), ct.POINTER(D), V]
+    lib.ofdft_energy_potential_async.argtypes = [P, V, ct.POINTER(CFunctional), V, V]
+    lib.ofdft_forces.argtypes = [P, V, I, ct.POINTER(D)]
+    lib.ofdft_optimize_density.argtypes = [P, V, ct.POINTER(CFunctional), D, D, I, ct.POINTER(COptReport)]
+    lib.ofdft_energy_potential_batched.argtypes = [I, ct.POINTER(P), ct.POINTER(V), ct.POINTER(CFunctional),
+                                                   ct.POINTER(D), ct.POINTER(V), ct.POINTER(ct.POINTER(D))]
+    lib.ofdft_profile_enable.argtypes = [P, I]
+    lib.ofdft_profile_reset.argtypes = [P]
+    lib.ofdft_profile_read.argtypes = [P, I, ct.POINTER(ct.c_char_p), ct.POINTER(I), ct.POINTER(D)]
+    lib.ofdft_status_string.argtypes = [I]
+    lib.ofdft_status_string.restype = ct.c_char_p
+    lib.ofdft_last_error.argtypes = [P]
+    lib.ofdft_last_error.restype = ct.c_char_p
+    lib.ofdft_version.restype = ct.c_char_p
+    for name in EXPORTS:
+        if name not in ("ofdft_status_string", "ofdft_last_error", "ofdft_version"):
+            getattr(lib, name).restype = ct.c_int
+    _lib = lib
+    return lib

@@ -1,0 +1,900 @@
+// C ABI of the OFDFT library: grid handle, planning, workspace, evaluation,
+// forces, batched evaluation and the psi = sqrt(rho) CG optimiser.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/ofdft.h"
+#include "eval.cuh"
+#include "misc.cuh"
+
+using namespace ofdft;
+
+namespace {
+
+
+bool factor_235(int n, std::vector<int> &radix) {
+    radix.clear();
+    int m = n, p2 = 0;
+    while (m % 2 == 0) { m /= 2; p2++; }
+    while (p2 >= 3) { radix.push_back(8); p2 -= 3; }
+    if (p2 == 2) radix.push_back(4);
+    if (p2 == 1) radix.push_back(2);
+    while (m % 5 == 0) { m /= 5; radix.push_back(5); }
+    while (m % 3 == 0) { m /= 3; radix.push_back(3); }
+    return m == 1;
+}
+
+FFTPlan make_plan(int n) {
+    FFTPlan p;
+    std::memset(&p, 0, sizeof(p));
+    std::vector<int> r;
+    factor_235(n, r);
+    p.n = n;
+    p.npass = (int)r.size();
+    int ns = 1;
+    for (int i = 0; i < p.npass; i++) {
+        p.radix[i] = r[i];
+        p.ns[i] = ns;
+        ns *= r[i];
+    }
+    return p;
+}
+
+// smallest multiple-of-32 thread count that keeps every pass within cap staged values
+int threads_for(const FFTPlan &p, int B, int cap, int lo = 64) {
+    int need = lo;
+    for (int i = 0; i < p.npass; i++) {
+        const int R = p.radix[i], mb = cap / R;
+        const int total = (p.n / R) * B;
+        const int t = (total + mb - 1) / mb;
+        if (t > need) need = t;
+    }
+    need = (need + 31) / 32 * 32;
+    return need;
+}
+
+template <typename T> struct Workspace {
+    typedef typename Vec2<T>::type C;
+    bool ready = false;
+    int nslots = 0;
+    C *chan = nullptr;
+    C *tw[3] = {nullptr, nullptr, nullptr};
+    C *vext = nullptr;
+    double *scal = nullptr, *energies = nullptr, *knots_d = nullptr;
+    T *knots_t = nullptr, *invdk_t = nullptr, *part_minmax = nullptr;
+    double *part_stats = nullptr, *part_ax0 = nullptr, *part_row = nullptr, *part_misc = nullptr;
+    T *opt = nullptr;                 // optimiser fields (8 * N), allocated on demand
+    int Brow = 0, thr_rowf = 0, thr_rowi = 0, TW1 = 0, thr_p1 = 0, TW0 = 0, thr_ax0 = 0, nb_row = 0, nb_ax0 = 0;
+};
+
+}  // namespace
+
+struct ofdft_grid {
+    int n[3];
+    int n2h;
+    long long N, NH;
+    double cell[9], recip[9], omega, dV;
+    cudaStream_t stream;
+    int device;
+    int nsm;
+    FFTPlan plan[3];
+    Workspace<float> w32;
+    Workspace<double> w64;
+    // ions
+    int n_ions = 0, n_species = 0;
+    std::vector<double> pos, Z, rc;
+    std::vector<int> species;
+    bool have_ions = false;
+    bool vext_fresh32 = false, vext_fresh64 = false;
+    double2 *ph = nullptr;       // phase tables [n_ions][n0 + n1 + n2h]
+    int *d_species = nullptr;
+    double *d_Z = nullptr, *d_rc = nullptr;
+    double *h_pinned = nullptr;  // 64 doubles of pinned host memory
+    std::string err;
+    // per-kernel CUDA-event timing (ofdft_profile_*)
+    bool prof_on = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<cudaEvent_t> ev_pending = std::vector<cudaEvent_t>(K_NKERNEL, nullptr);
+    struct Rec { int id; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    double prof_ms[K_NKERNEL] = {0};
+    int prof_n[K_NKERNEL] = {0};
+};
+
+namespace {
+
+int fail(ofdft_grid *g, int code, const char *what, cudaError_t e = cudaSuccess) {
+    if (g) {
+        char buf[512];
+        if (e != cudaSuccess) std::snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+        else std::snprintf(buf, sizeof(buf), "%s", what);
+        g->err = buf;
+    }
+    return code;
+}
+
+#define CK(call, what)                                                                       \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(g, e_ == cudaErrorMemoryAllocation ? OFDFT_ERR_OOM : OFDFT_ERR_CUDA, \
+                        what, e_);                                                           \
+    } while (0)
+
+template <typename T> Workspace<T> &ws(ofdft_grid *g);
+template <> Workspace<float> &ws<float>(ofdft_grid *g) { return g->w32; }
+template <> Workspace<double> &ws<double>(ofdft_grid *g) { return g->w64; }
+
+template <typename T> int choose_launch(ofdft_grid *g, Workspace<T> &w) {
+    typedef typename Vec2<T>::type C;
+    const size_t row_budget = 110 * 1024;
+    EvalArgs<T> probe;
+    std::memset(&probe, 0, sizeof(probe));
+    probe.n2 = g->n[2];
+    const int cap = Cap<T>::value, tmax = kMaxThreads;
+    int B = 16;
+    for (; B >= 1; B /= 2) {
+        probe.Brow = B;
+        if (row_inv_smem(probe) <= row_budget && threads_for(g->plan[2], B, cap) <= tmax) break;
+    }
+    if (B < 1) return fail(g, OFDFT_ERR_UNSUPPORTED_SIZE, "row transform does not fit in shared memory");
+    w.Brow = B;
+    w.thr_rowf = w.thr_rowi = std::min(std::max(threads_for(g->plan[2], B, cap), 128), tmax);
+    int TW = 16;
+    while (TW > 1 && ((size_t)g->n[1] * TW * sizeof(C) > 64 * 1024 || threads_for(g->plan[1], TW, cap) > tmax)) TW /= 2;
+    w.TW1 = TW;
+    w.thr_p1 = std::min(std::max(threads_for(g->plan[1], TW, cap), 128), tmax);
+    TW = 16;
+    while (TW > 1 && (axis0_smem<T>(g->n[0], TW) > 200 * 1024 || threads_for(g->plan[0], TW, cap) > tmax)) TW /= 2;
+    w.TW0 = TW;
+    w.thr_ax0 = std::min(std::max(threads_for(g->plan[0], TW, cap), 128), tmax);
+    const long long R = (long long)g->n[0] * g->n[1];
+    w.nb_row = (int)(((R + 1) / 2 + B - 1) / B);
+    const long long P = (long long)g->n[1] * g->n2h;
+    w.nb_ax0 = (int)((P + w.TW0 - 1) / w.TW0);
+    return OFDFT_OK;
+}
+
+template <typename T> int ensure_ws(ofdft_grid *g, int nslots) {
+    typedef typename Vec2<T>::type C;
+    Workspace<T> &w = ws<T>(g);
+    if (!w.ready) {
+        int rc = choose_launch<T>(g, w);
+        if (rc) return rc;
+        for (int a = 0; a < 3; a++) {
+            const int n = g->n[a];
+            std::vector<C> h(n);
+            for (int k = 0; k < n; k++) {
+                const double ang = -2.0 * kPi * (double)k / (double)n;
+                h[k].x = (T)std::cos(ang);
+                h[k].y = (T)std::sin(ang);
+            }
+            CK(cudaMalloc(&w.tw[a], n * sizeof(C)), "cudaMalloc twiddles");
+            CK(cudaMemcpy(w.tw[a], h.data(), n * sizeof(C), cudaMemcpyHostToDevice), "upload twiddles");
+        }
+        CK(cudaMalloc(&w.scal, 64 * sizeof(double)), "cudaMalloc scalars");
+        CK(cudaMemset(w.scal, 0, 64 * sizeof(double)), "memset");
+        CK(cudaMalloc(&w.energies, 8 * sizeof(double)), "cudaMalloc energies");
+        CK(cudaMalloc(&w.knots_d, OFDFT_MAX_KNOTS * sizeof(double)), "cudaMalloc knots");
+        CK(cudaMalloc(&w.knots_t, OFDFT_MAX_KNOTS * sizeof(T)), "cudaMalloc knots");
+        CK(cudaMalloc(&w.invdk_t, OFDFT_MAX_KNOTS * sizeof(T)), "cudaMalloc knots");
+        const int nbs = 2 * g->nsm;
+        CK(cudaMalloc(&w.part_stats, 2 * nbs * sizeof(double)), "cudaMalloc partials");
+        CK(cudaMalloc(&w.part_minmax, 2 * nbs * sizeof(T)), "cudaMalloc partials");
+        CK(cudaMalloc(&w.part_ax0, 3 * (size_t)w.nb_ax0 * sizeof(double)), "cudaMalloc partials");
+        CK(cudaMalloc(&w.part_row, (size_t)w.nb_row * sizeof(double)), "cudaMalloc partials");
+        CK(cudaMalloc(&w.part_misc, 4096 * sizeof(double)), "cudaMalloc partials");
+        w.ready = true;
+    }
+    if (nslots > w.nslots) {
+        if (w.chan) cudaFree(w.chan);
+        w.chan = nullptr;
+        w.nslots = 0;
+        CK(cudaMalloc(&w.chan, (size_t)nslots * g->NH * sizeof(C)), "cudaMalloc channel workspace");
+        w.nslots = nslots;
+    }
+    return OFDFT_OK;
+}
+
+template <typename T> void free_ws(Workspace<T> &w) {
+    cudaFree(w.chan);
+    for (int a = 0; a < 3; a++) cudaFree(w.tw[a]);
+    cudaFree(w.vext);
+    cudaFree(w.scal);
+    cudaFree(w.energies);
+    cudaFree(w.knots_d);
+    cudaFree(w.knots_t);
+    cudaFree(w.invdk_t);
+    cudaFree(w.part_minmax);
+    cudaFree(w.part_stats);
+    cudaFree(w.part_ax0);
+    cudaFree(w.part_row);
+    cudaFree(w.part_misc);
+    cudaFree(w.opt);
+    w = Workspace<T>();
+}
+
+IonArgs ion_args(ofdft_grid *g) {
+    IonArgs a;
+    a.n0 = g->n[0];
+    a.n1 = g->n[1];
+    a.n2 = g->n[2];
+    a.n2h = g->n2h;
+    a.n_ions = g->n_ions;
+    a.n_species = g->n_species;
+    a.omega = g->omega;
+    for (int i = 0; i < 9; i++) a.bvec[i] = 2.0 * kPi * g->recip[i];
+    a.ph0 = g->ph;
+    a.ph1 = g->ph + (size_t)g->n_ions * g->n[0];
+    a.ph2 = a.ph1 + (size_t)g->n_ions * g->n[1];
+    a.species = g->d_species;
+    a.Z = g->d_Z;
+    a.rc = g->d_rc;
+    return a;
+}
+
+template <typename T> int ensure_vext(ofdft_grid *g) {
+    typedef typename Vec2<T>::type C;
+    Workspace<T> &w = ws<T>(g);
+    bool &fresh = sizeof(T) == 4 ? g->vext_fresh32 : g->vext_fresh64;
+    if (fresh) return OFDFT_OK;
+    if (!w.vext) CK(cudaMalloc(&w.vext, g->NH * sizeof(C)), "cudaMalloc V_ext(G)");
+    IonArgs a = ion_args(g);
+    cudaError_t e;
+    if (sizeof(T) == 4) e = launch_vext(a, nullptr, (float2 *)w.vext, g->stream);
+    else e = launch_vext(a, (double2 *)w.vext, nullptr, g->stream);
+    CK(e, "structure factor kernel");
+    fresh = true;
+    return OFDFT_OK;
+}
+
+int check_functional(ofdft_grid *g, const ofdft_functional *f) {
+    if (!f) return fail(g, OFDFT_ERR_INVALID_ARG, "functional is NULL");
+    if (f->precision != OFDFT_FP64 && f->precision != OFDFT_FP32_MIXED)
+        return fail(g, OFDFT_ERR_INVALID_ARG, "unknown precision");
+    if (f->terms & ~OFDFT_TERMS_ALL) return fail(g, OFDFT_ERR_INVALID_ARG, "unknown term bits");
+    if (f->terms & OFDFT_TERM_NL) {
+        if (f->kernel == OFDFT_KERNEL_LWT && (f->n_knots < 2 || f->n_knots > OFDFT_MAX_KNOTS))
+            return fail(g, OFDFT_ERR_INVALID_ARG, "n_knots must be in [2, 64]");
+        if (f->nl_potential == OFDFT_NLPOT_INTERP && f->alpha != f->beta)
+            return fail(g, OFDFT_ERR_INVALID_ARG, "interpolated potential needs alpha == beta");
+        if (f->kernel != OFDFT_KERNEL_LWT && f->kernel != OFDFT_KERNEL_WT_GLOBAL)
+            return fail(g, OFDFT_ERR_INVALID_ARG, "unknown kernel");
+        if (f->knots && f->kernel == OFDFT_KERNEL_LWT)
+            for (int m = 0; m + 1 < f->n_knots; m++)
+                if (!(f->knots[m + 1] >= f->knots[m]) || !(f->knots[0] > 0.0))
+                    return fail(g, OFDFT_ERR_INVALID_ARG, "knots must be positive and ascending");
+    }
+    if ((f->terms & OFDFT_TERM_PP) && !g->have_ions) return fail(g, OFDFT_ERR_NO_IONS, "PP term needs ions");
+    return OFDFT_OK;
+}
+
+cudaEvent_t take_event(ofdft_grid *g) {
+    if (!g->ev_pool.empty()) {
+        cudaEvent_t e = g->ev_pool.back();
+        g->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void prof_record(void *ctx, int id, int phase, cudaStream_t s) {
+    ofdft_grid *g = (ofdft_grid *)ctx;
+    cudaEvent_t e = take_event(g);
+    cudaEventRecord(e, s);
+    if (phase == 0) g->ev_pending[id] = e;
+    else g->recs.push_back({id, g->ev_pending[id], e});
+}
+
+void prof_collect(ofdft_grid *g) {
+    cudaStreamSynchronize(g->stream);
+    for (auto &r : g->recs) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            g->prof_ms[r.id] += ms;
+            g->prof_n[r.id] += 1;
+        }
+        g->ev_pool.push_back(r.a);
+        g->ev_pool.push_back(r.b);
+    }
+    g->recs.clear();
+}
+
+const char *kKernelNames[K_NKERNEL] = {"stats", "knots", "row_fwd", "pencil_fwd", "axis0_recip",
+                                       "pencil_inv", "row_inv", "finalize"};
+
+// Fill the evaluation arguments and enqueue one evaluation.
+template <typename T>
+int enqueue_eval(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, double *E_dev_out) {
+    const bool nl = f->terms & OFDFT_TERM_NL;
+    const bool lwt = nl && f->kernel == OFDFT_KERNEL_LWT;
+    const int M = lwt ? f->n_knots : 0;
+    const int nslots = nl ? (lwt ? 3 + M : 4) : 3;
+    int rc = ensure_ws<T>(g, nslots);
+    if (rc) return rc;
+    Workspace<T> &w = ws<T>(g);
+    if (f->terms & OFDFT_TERM_PP) {
+        rc = ensure_vext<T>(g);
+        if (rc) return rc;
+    }
+    EvalArgs<T> a;
+    std::memset(&a, 0, sizeof(a));
+    a.n0 = g->n[0];
+    a.n1 = g->n[1];
+    a.n2 = g->n[2];
+    a.n2h = g->n2h;
+    a.N = g->N;
+    a.NH = g->NH;
+    a.omega = g->omega;
+    a.dV = g->dV;
+    for (int i = 0; i < 9; i++) a.bvec[i] = 2.0 * kPi * g->recip[i];
+    a.rho = rho;
+    a.V = V;
+    a.chan = w.chan;
+    a.vext = w.vext;
+    a.terms = f->terms;
+    a.kernel = f->kernel;
+    a.nlpot = f->nl_potential;
+    a.M = M;
+    a.alpha = (T)f->alpha;
+    a.beta = (T)f->beta;
+    const double fl = f->rho_floor > 0.0 ? f->rho_floor : 1e-20;
+    a.floor_ = (T)(sizeof(T) == 4 && fl < 1e-30 ? 1e-30 : fl);
+    a.scal = w.scal;
+    a.knots_d = w.knots_d;
+    a.knots_t = w.knots_t;
+    a.invdk_t = w.invdk_t;
+    a.frozen = (lwt && f->knots) ? 1 : 0;
+    a.knot_spacing = f->knot_spacing;
+    a.part_stats = w.part_stats;
+    a.part_minmax = w.part_minmax;
+    a.part_ax0 = w.part_ax0;
+    a.part_row = w.part_row;
+    a.energies = E_dev_out ? E_dev_out : w.energies;
+    a.nb_stats = 2 * g->nsm;
+    a.nb_ax0 = w.nb_ax0;
+    a.nb_row = w.nb_row;
+    a.p0 = g->plan[0];
+    a.p1 = g->plan[1];
+    a.p2 = g->plan[2];
+    a.tw0 = w.tw[0];
+    a.tw1 = w.tw[1];
+    a.tw2 = w.tw[2];
+    a.Brow = w.Brow;
+    a.thr_rowf = w.thr_rowf;
+    a.thr_rowi = w.thr_rowi;
+    a.TW1 = w.TW1;
+    a.thr_p1 = w.thr_p1;
+    a.TW0 = w.TW0;
+    a.thr_ax0 = w.thr_ax0;
+    // channel lists
+    const bool hpp = f->terms & (OFDFT_TERM_HARTREE | OFDFT_TERM_PP);
+    const bool vw = f->terms & OFDFT_TERM_VW;
+    const bool exact = f->nl_potential == OFDFT_NLPOT_EXACT;
+    if (hpp) { a.fwd_ch[a.nfwd++] = CH_HPP; }
+    if (vw) { a.fwd_ch[a.nfwd++] = CH_VW; }
+    if (nl) {
+        a.fwd_ch[a.nfwd++] = CH_NL;
+        if (!lwt) a.fwd_ch[a.nfwd++] = CH_KNOT0;
+        else if (exact)
+            for (int m = 0; m < M; m++) a.fwd_ch[a.nfwd++] = CH_KNOT0 + m;
+    }
+    // forward and inverse passes along n1: every channel that exists in G space
+    if (hpp) a.col_ch[a.ncol++] = CH_HPP;
+    if (vw) a.col_ch[a.ncol++] = CH_VW;
+    if (nl) {
+        a.col_ch[a.ncol++] = CH_NL;   // (interp: the forward pass needs it; the inverse is unused)
+        if (!lwt) a.col_ch[a.ncol++] = CH_KNOT0;
+        else
+            for (int m = 0; m < M; m++) a.col_ch[a.ncol++] = CH_KNOT0 + m;
+    }
+    for (int i = 0; i < a.ncol; i++)
+        if (!(lwt && !exact && a.col_ch[i] == CH_NL)) a.col_inv_ch[a.ncol_inv++] = a.col_ch[i];
+    if (hpp) { a.inv_ch[a.ninv] = CH_HPP; a.inv_kind[a.ninv++] = CONS_ADD; }
+    if (vw) { a.inv_ch[a.ninv] = CH_VW; a.inv_kind[a.ninv++] = CONS_VW; }
+    if (nl) {
+        if (!lwt) {
+            a.inv_ch[a.ninv] = CH_NL; a.inv_kind[a.ninv++] = CONS_WT_A;
+            a.inv_ch[a.ninv] = CH_KNOT0; a.inv_kind[a.ninv++] = CONS_WT_B;
+        } else {
+            if (exact) { a.inv_ch[a.ninv] = CH_NL; a.inv_kind[a.ninv++] = CONS_T2; }
+            for (int m = 0; m < M; m++) {
+                a.inv_ch[a.ninv] = CH_KNOT0 + m;
+                a.inv_kind[a.ninv] = CONS_KNOT;
+                a.inv_knot[a.ninv++] = m;
+            }
+        }
+    }
+    CK(cudaMemsetAsync(w.scal + S_BAD, 0, sizeof(double), g->stream), "memset flag");
+    if (a.frozen) CK(cudaMemcpyAsync(w.knots_d, f->knots, M * sizeof(double), cudaMemcpyHostToDevice, g->stream),
+                     "upload knots");
+    ProfHook hook{prof_record, g};
+    CK(launch_eval<T>(a, g->stream, g->prof_on ? &hook : nullptr), "evaluation kernels");
+    return OFDFT_OK;
+}
+
+template <typename T>
+int eval_sync(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, double *E_out) {
+    int rc = enqueue_eval<T>(g, rho, f, V, nullptr);
+    if (rc) return rc;
+    Workspace<T> &w = ws<T>(g);
+    CK(cudaMemcpyAsync(g->h_pinned, w.energies, 6 * sizeof(double), cudaMemcpyDeviceToHost, g->stream), "copy E");
+    CK(cudaMemcpyAsync(g->h_pinned + 8, w.scal, S_NSCAL * sizeof(double), cudaMemcpyDeviceToHost, g->stream),
+       "copy scalars");
+    CK(cudaStreamSynchronize(g->stream), "stream synchronize");
+    if (g->h_pinned[8 + S_BAD] != 0.0) return fail(g, OFDFT_ERR_BAD_DENSITY, "density has NaN/Inf or negative values");
+    if (E_out) std::memcpy(E_out, g->h_pinned, 6 * sizeof(double));
+    return OFDFT_OK;
+}
+
+// ---------------------------------------------------------------- forces
+template <typename T> int forces_impl(ofdft_grid *g, const T *rho, double *F) {
+    typedef typename Vec2<T>::type C;
+    int rc = ensure_ws<T>(g, 3);
+    if (rc) return rc;
+    Workspace<T> &w = ws<T>(g);
+    EvalArgs<T> a;
+    std::memset(&a, 0, sizeof(a));
+    a.n0 = g->n[0]; a.n1 = g->n[1]; a.n2 = g->n[2]; a.n2h = g->n2h; a.N = g->N; a.NH = g->NH;
+    a.omega = g->omega; a.dV = g->dV;
+    a.rho = rho; a.chan = w.chan; a.terms = OFDFT_TERM_HARTREE; a.floor_ = (T)1e-30;
+    a.scal = w.scal; a.knots_d = w.knots_d; a.knots_t = w.knots_t; a.invdk_t = w.invdk_t;
+    a.part_stats = w.part_stats; a.part_minmax = w.part_minmax; a.energies = w.energies;
+    a.nb_stats = 2 * g->nsm;
+    a.p0 = g->plan[0]; a.p1 = g->plan[1]; a.p2 = g->plan[2];
+    a.tw0 = w.tw[0]; a.tw1 = w.tw[1]; a.tw2 = w.tw[2];
+    a.Brow = w.Brow; a.thr_rowf = w.thr_rowf; a.TW1 = w.TW1; a.thr_p1 = w.thr_p1;
+    a.nfwd = 1; a.fwd_ch[0] = CH_HPP; a.ncol = 1; a.col_ch[0] = CH_HPP;
+    CK(launch_forward_rows_cols<T>(a, g->stream), "forward transform");
+    CK(launch_axis0_fft<T>(w.chan, g->n[0], (long long)g->n[1] * g->n2h, g->plan[0], w.tw[0], w.TW0, w.thr_ax0,
+                           1.0 / (double)g->N, g->stream),
+       "forward transform along n0");
+    const int nchunk = 16;
+    std::vector<double> part((size_t)g->n_ions * nchunk * 3);
+    double *dpart = w.part_misc;
+    bool own = false;
+    if ((size_t)g->n_ions * nchunk * 3 > 4096) {
+        CK(cudaMalloc(&dpart, part.size() * sizeof(double)), "cudaMalloc force partials");
+        own = true;
+    }
+    IonArgs ia = ion_args(g);
+    CK(launch_forces<C>(ia, w.chan, dpart, nchunk, g->stream), "forces kernel");
+    CK(cudaMemcpyAsync(part.data(), dpart, part.size() * sizeof(double), cudaMemcpyDeviceToHost, g->stream),
+       "copy forces");
+    CK(cudaStreamSynchronize(g->stream), "stream synchronize");
+    if (own) cudaFree(dpart);
+    for (int I = 0; I < g->n_ions; I++)
+        for (int d = 0; d < 3; d++) {
+            double s = 0.0;
+            for (int c = 0; c < nchunk; c++) s += part[((size_t)I * nchunk + c) * 3 + d];
+            F[3 * I + d] = s;
+        }
+    return OFDFT_OK;
+}
+
+// ---------------------------------------------------------------- optimiser
+template <typename T> struct Dev {
+    ofdft_grid *g;
+    Workspace<T> *w;
+    double dot(const T *a, const T *b, const T *c = nullptr) {
+        launch_dot<T>(a, b, c, g->N, w->part_misc, 1024, w->part_misc + 2048, g->stream);
+        double r = 0.0;
+        cudaMemcpyAsync(g->h_pinned + 40, w->part_misc + 2048, sizeof(double), cudaMemcpyDeviceToHost, g->stream);
+        cudaStreamSynchronize(g->stream);
+        r = g->h_pinned[40];
+        return r;
+    }
+};
+
+double cubic_min(double a, double fa, double da, double b, double fb, double db, bool &ok) {
+    const double d1 = da + db - 3.0 * (fa - fb) / (a - b);
+    const double disc = d1 * d1 - da * db;
+    ok = false;
+    if (disc < 0.0) return 0.0;
+    const double d2 = std::copysign(std::sqrt(disc), b - a);
+    const double den = db - da + 2.0 * d2;
+    if (den == 0.0) return 0.0;
+    ok = true;
+    return b - (b - a) * (db + d2 - d1) / den;
+}
+
+template <typename T>
+int optimize_impl(ofdft_grid *g, T *psi, const ofdft_functional *f0, double Ne, double tol, int max_iter,
+                  ofdft_opt_report *rep) {
+    const long long N = g->N;
+    int rc = ensure_ws<T>(g, 3);
+    if (rc) return rc;
+    Workspace<T> &w = ws<T>(g);
+    if (!w.opt) CK(cudaMalloc(&w.opt, 8 * (size_t)N * sizeof(T)), "cudaMalloc optimiser fields");
+    T *rho = w.opt, *V = rho + N, *grad = V + N, *gprev = grad + N, *d = gprev + N, *p = d + N, *psil = p + N;
+    T *tmp = psil + N;
+    Dev<T> dv{g, &w};
+    cudaStream_t s = g->stream;
+    const bool lwt_auto = (f0->terms & OFDFT_TERM_NL) && f0->kernel == OFDFT_KERNEL_LWT && !f0->knots;
+    ofdft_functional f = *f0;
+    std::vector<double> knots(OFDFT_MAX_KNOTS);
+    double E[6], Enew[6];
+    int evals = 0;
+    // normalise psi to N_e
+    const double nrm = dv.dot(psi, psi) * g->dV;
+    if (!(nrm > 0.0)) return fail(g, OFDFT_ERR_BAD_DENSITY, "initial psi is zero");
+    CK(launch_square<T>(rho, psi, std::sqrt(Ne / nrm), N, s), "square");
+    auto refresh_knots = [&]() -> int {
+        if (!lwt_auto) return OFDFT_OK;
+        f.knots = nullptr;
+        int r = eval_sync<T>(g, rho, &f, V, E);
+        evals++;
+        if (r) return r;
+        cudaMemcpy(knots.data(), w.knots_d, f.n_knots * sizeof(double), cudaMemcpyDeviceToHost);
+        f.knots = knots.data();
+        return OFDFT_OK;
+    };
+    if ((rc = refresh_knots())) return rc;
+    if (!lwt_auto) {
+        if ((rc = eval_sync<T>(g, rho, &f, V, E))) return rc;
+        evals++;
+    }
+    double lam_prev = 0.05;
+    int small = 0, it = 0, restarts = 0;
+    bool have_dir = false;
+    double last_dE = 0.0, mu = 0.0;
+    const double c1 = 1e-4, c2 = 0.2;
+    while (it < max_iter) {
+        it++;
+        // g = 2 psi (V - mu) dV, mu = int rho V / N_e
+        mu = dv.dot(psi, psi, V) * g->dV / Ne;
+        CK(launch_grad<T>(grad, psi, V, mu, g->dV, N, s), "grad");
+        double beta = 0.0;
+        if (have_dir && (it % 50) != 1) {
+            const double gg = dv.dot(grad, grad), ggp = dv.dot(grad, gprev), gpgp = dv.dot(gprev, gprev);
+            beta = std::max(0.0, (gg - ggp) / gpgp);
+        }
+        // d = -g + beta d
+        if (have_dir && beta > 0.0) CK(launch_axpby<T>(d, grad, -1.0, beta, N, s), "axpby");
+        else CK(launch_axpby<T>(d, grad, -1.0, 0.0, N, s), "axpby");
+        if (dv.dot(d, grad) >= 0.0) CK(launch_axpby<T>(d, grad, -1.0, 0.0, N, s), "axpby");
+        CK(launch_copy<T>(gprev, grad, N, s), "copy");
+        have_dir = true;
+        // p = d - (<d,psi>/<psi,psi>) psi, normalised to N_e
+        CK(launch_copy<T>(p, d, N, s), "copy");
+        const double dpsi = dv.dot(d, psi), pp = dv.dot(psi, psi);
+        CK(launch_axpby<T>(p, psi, -dpsi / pp, 1.0, N, s), "axpby");
+        const double pn = dv.dot(p, p) * g->dV;
+        if (!(pn > 0.0)) break;
+        CK(launch_axpby<T>(p, psi, 0.0, std::sqrt(Ne / pn), N, s), "axpby");
+        const double phi0 = E[0];
+        // dE/dlambda at 0 = sum dE/dpsi p = sum 2 psi V dV p
+        const double dphi0 = 2.0 * g->dV * dv.dot(psi, V, p);
+        if (dphi0 >= 0.0) {
+            have_dir = false;
+            if (++restarts > 3) break;
+            continue;
+        }
+        auto phi = [&](double lam, double *El, double &dl) -> int {
+            CK(launch_rotate<T>(psil, rho, psi, p, std::cos(lam), std::sin(lam), N, s), "rotate");
+            int r = eval_sync<T>(g, rho, &f, V, El);
+            evals++;
+            if (r) return r;
+            // dpsi/dlambda = -psi sin + p cos into tmp (grad is free scratch here)
+            CK(launch_rotate<T>(tmp, grad, psi, p, -std::sin(lam), std::cos(lam), N, s), "rotate");
+            dl = 2.0 * g->dV * dv.dot(psil, V, tmp);
+            return OFDFT_OK;
+        };
+        double lam_lo = 0.0, f_lo = phi0, d_lo = dphi0, lam_hi = -1.0, f_hi = 0.0, d_hi = 0.0;
+        double lam = std::min(std::max(lam_prev, 1e-4), 0.5);
+        double best_f = 1e300, best_lam = 0.0;
+        for (int ls = 0; ls < 10; ls++) {
+            double El[6], dl;
+            if ((rc = phi(lam, El, dl))) return rc;
+            const double fl = El[0];
+            if (fl < best_f) { best_f = fl; best_lam = lam; std::memcpy(Enew, El, sizeof(El)); }
+            if (fl > phi0 + c1 * lam * dphi0 || (lam_hi < 0.0 && fl >= f_lo && lam_lo > 0.0)) {
+                lam_hi = lam; f_hi = fl; d_hi = dl;
+            } else if (std::fabs(dl) <= -c2 * dphi0) {
+                break;
+            } else if (dl >= 0.0) {
+                lam_hi = lam_lo; f_hi = f_lo; d_hi = d_lo;
+                lam_lo = lam; f_lo = fl; d_lo = dl;
+            } else {
+                lam_lo = lam; f_lo = fl; d_lo = dl;
+                if (lam_hi < 0.0) { lam = std::min(2.0 * lam, 1.5707963267948966); continue; }
+            }
+            bool ok;
+            double c = cubic_min(lam_lo, f_lo, d_lo, lam_hi, f_hi, d_hi, ok);
+            const double lo = std::min(lam_lo, lam_hi), hi = std::max(lam_lo, lam_hi);
+            if (!ok || !(c >= lo + 0.1 * (hi - lo) && c <= hi - 0.1 * (hi - lo))) c = 0.5 * (lam_lo + lam_hi);
+            lam = c;
+        }
+        if (!(best_f < phi0)) {
+            have_dir = false;
+            if (++restarts > 3) break;
+            // restore V at psi for the next gradient
+            CK(launch_square<T>(rho, psi, 1.0, N, s), "square");
+            if ((rc = eval_sync<T>(g, rho, &f, V, E))) return rc;
+            evals++;
+            continue;
+        }
+        restarts = 0;
+        lam_prev = best_lam;
+        // accept: psi <- psi cos + p sin, and V at the accepted point
+        CK(launch_rotate<T>(psil, rho, psi, p, std::cos(best_lam), std::sin(best_lam), N, s), "rotate");
+        CK(launch_copy<T>(psi, psil, N, s), "copy");
+        last_dE = std::fabs(Enew[0] - E[0]);
+        if (lwt_auto) {
+            if ((rc = refresh_knots())) return rc;
+        } else {
+            if ((rc = eval_sync<T>(g, rho, &f, V, E))) return rc;
+            evals++;
+        }
+        small = (last_dE < tol * std::max(1, g->n_ions)) ? small + 1 : 0;
+        if (small >= 3) break;
+    }
+    if (rep) {
+        rep->iterations = it;
+        rep->evaluations = evals;
+        rep->energy = E[0];
+        std::memcpy(rep->energies, E, sizeof(E));
+        rep->mu = dv.dot(psi, psi, V) * g->dV / Ne;
+        // residual ||(V - mu) psi|| with dV weight: sum psi^2 (V-mu)^2 dV
+        CK(launch_grad<T>(grad, psi, V, rep->mu, 0.5, N, s), "grad");   // grad = psi (V - mu)
+        rep->residual = std::sqrt(dv.dot(grad, grad) * g->dV);
+        rep->last_dE = last_dE;
+    }
+    return small >= 3 ? OFDFT_OK : OFDFT_ERR_NOT_CONVERGED;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+const char *ofdft_version(void) { return "ofdft-gb300 0.1 (sm_103a)"; }
+
+const char *ofdft_status_string(int s) {
+    switch (s) {
+        case OFDFT_OK: return "ok";
+        case OFDFT_ERR_INVALID_ARG: return "invalid argument";
+        case OFDFT_ERR_UNSUPPORTED_SIZE: return "unsupported grid size (need 2^a 3^b 5^c in [2, 1024])";
+        case OFDFT_ERR_BAD_DENSITY: return "bad density (NaN, Inf or negative)";
+        case OFDFT_ERR_OOM: return "out of device memory";
+        case OFDFT_ERR_CUDA: return "CUDA error";
+        case OFDFT_ERR_NOT_CONVERGED: return "optimiser did not converge";
+        case OFDFT_ERR_NO_IONS: return "no ions set";
+        default: return "unknown status";
+    }
+}
+
+const char *ofdft_last_error(const ofdft_grid *g) { return g ? g->err.c_str() : "null handle"; }
+
+int ofdft_grid_create(const double cell[9], const int shape[3], void *cuda_stream, ofdft_grid **out) {
+    if (!cell || !shape || !out) return OFDFT_ERR_INVALID_ARG;
+    *out = nullptr;
+    for (int a = 0; a < 3; a++) {
+        std::vector<int> r;
+        if (shape[a] < 2 || shape[a] > 1024 || !factor_235(shape[a], r)) return OFDFT_ERR_UNSUPPORTED_SIZE;
+    }
+    const double *A = cell;
+    const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                       A[2] * (A[3] * A[7] - A[4] * A[6]);
+    if (!(std::fabs(det) > 1e-12)) return OFDFT_ERR_INVALID_ARG;
+    static bool tables = false;
+    if (!tables) {
+        if (upload_gnl_tables() != cudaSuccess) return OFDFT_ERR_CUDA;
+        tables = true;
+    }
+    ofdft_grid *g = new (std::nothrow) ofdft_grid();
+    if (!g) return OFDFT_ERR_OOM;
+    for (int a = 0; a < 3; a++) g->n[a] = shape[a];
+    g->n2h = shape[2] / 2 + 1;
+    g->N = (long long)shape[0] * shape[1] * shape[2];
+    g->NH = (long long)shape[0] * shape[1] * g->n2h;
+    std::memcpy(g->cell, cell, 9 * sizeof(double));
+    // recip rows b_i = rows of inv(A)^T: b_i . a_j = delta_ij; inv(A)^T = cofactor(A) / det
+    const double inv[9] = {(A[4] * A[8] - A[5] * A[7]) / det, -(A[1] * A[8] - A[2] * A[7]) / det,
+                           (A[1] * A[5] - A[2] * A[4]) / det, -(A[3] * A[8] - A[5] * A[6]) / det,
+                           (A[0] * A[8] - A[2] * A[6]) / det, -(A[0] * A[5] - A[2] * A[3]) / det,
+                           (A[3] * A[7] - A[4] * A[6]) / det, -(A[0] * A[7] - A[1] * A[6]) / det,
+                           (A[0] * A[4] - A[1] * A[3]) / det};
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) g->recip[3 * i + j] = inv[3 * j + i];
+    g->omega = std::fabs(det);
+    g->dV = g->omega / (double)g->N;
+    g->stream = (cudaStream_t)cuda_stream;
+    for (int a = 0; a < 3; a++) g->plan[a] = make_plan(shape[a]);
+    cudaError_t e = cudaGetDevice(&g->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->nsm, cudaDevAttrMultiProcessorCount, g->device);
+    if (e == cudaSuccess) e = cudaMallocHost(&g->h_pinned, 64 * sizeof(double));
+    if (e != cudaSuccess) {
+        delete g;
+        return e == cudaErrorMemoryAllocation ? OFDFT_ERR_OOM : OFDFT_ERR_CUDA;
+    }
+    *out = g;
+    return OFDFT_OK;
+}
+
+int ofdft_profile_enable(ofdft_grid *g, int enable) {
+    if (!g) return OFDFT_ERR_INVALID_ARG;
+    g->prof_on = enable != 0;
+    return OFDFT_OK;
+}
+
+int ofdft_profile_reset(ofdft_grid *g) {
+    if (!g) return OFDFT_ERR_INVALID_ARG;
+    prof_collect(g);
+    for (int i = 0; i < K_NKERNEL; i++) {
+        g->prof_ms[i] = 0.0;
+        g->prof_n[i] = 0;
+    }
+    return OFDFT_OK;
+}
+
+int ofdft_profile_read(ofdft_grid *g, int idx, const char **name, int *launches, double *total_ms) {
+    if (!g || idx < 0 || idx >= K_NKERNEL) return OFDFT_ERR_INVALID_ARG;
+    prof_collect(g);
+    if (name) *name = kKernelNames[idx];
+    if (launches) *launches = g->prof_n[idx];
+    if (total_ms) *total_ms = g->prof_ms[idx];
+    return OFDFT_OK;
+}
+
+int ofdft_grid_destroy(ofdft_grid *g) {
+    if (!g) return OFDFT_ERR_INVALID_ARG;
+    cudaStreamSynchronize(g->stream);
+    prof_collect(g);
+    for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
+    free_ws(g->w32);
+    free_ws(g->w64);
+    cudaFree(g->ph);
+    cudaFree(g->d_species);
+    cudaFree(g->d_Z);
+    cudaFree(g->d_rc);
+    cudaFreeHost(g->h_pinned);
+    delete g;
+    return OFDFT_OK;
+}
+
+int ofdft_set_ions(ofdft_grid *g, const ofdft_ions *ions, const ofdft_species *sp) {
+    if (!g) return OFDFT_ERR_INVALID_ARG;
+    if (!ions || !sp || ions->n < 1 || !ions->pos || !ions->species || sp->n_species < 1 || !sp->Z || !sp->rc)
+        return fail(g, OFDFT_ERR_INVALID_ARG, "ions/species");
+    for (int i = 0; i < ions->n; i++)
+        if (ions->species[i] < 0 || ions->species[i] >= sp->n_species)
+            return fail(g, OFDFT_ERR_INVALID_ARG, "species index out of range");
+    CK(cudaStreamSynchronize(g->stream), "stream synchronize");
+    const int n = ions->n;
+    if (n != g->n_ions || sp->n_species != g->n_species) {
+        cudaFree(g->ph);
+        cudaFree(g->d_species);
+        cudaFree(g->d_Z);
+        cudaFree(g->d_rc);
+        g->ph = nullptr;
+        g->d_species = nullptr;
+        g->d_Z = g->d_rc = nullptr;
+        CK(cudaMalloc(&g->ph, (size_t)n * (g->n[0] + g->n[1] + g->n2h) * sizeof(double2)), "cudaMalloc phases");
+        CK(cudaMalloc(&g->d_species, n * sizeof(int)), "cudaMalloc species");
+        CK(cudaMalloc(&g->d_Z, sp->n_species * sizeof(double)), "cudaMalloc Z");
+        CK(cudaMalloc(&g->d_rc, sp->n_species * sizeof(double)), "cudaMalloc rc");
+    }
+    g->n_ions = n;
+    g->n_species = sp->n_species;
+    g->pos.assign(ions->pos, ions->pos + 3 * n);
+    g->species.assign(ions->species, ions->species + n);
+    g->Z.assign(sp->Z, sp->Z + sp->n_species);
+    g->rc.assign(sp->rc, sp->rc + sp->n_species);
+    // per-axis phase tables e^{-2 pi i m_a f_a}, f = R . inv(cell) (fractional)
+    const int na[3] = {g->n[0], g->n[1], g->n2h};
+    std::vector<double2> ph((size_t)n * (na[0] + na[1] + na[2]));
+    size_t off = 0;
+    for (int ax = 0; ax < 3; ax++) {
+        for (int I = 0; I < n; I++) {
+            const double *R = &g->pos[3 * I];
+            // fractional coordinate along a_ax: R . b_ax
+            const double fr = R[0] * g->recip[3 * ax] + R[1] * g->recip[3 * ax + 1] + R[2] * g->recip[3 * ax + 2];
+            for (int k = 0; k < na[ax]; k++) {
+                const int nn = g->n[ax];
+                const double m = (ax == 2) ? k : ((k <= nn / 2) ? k : k - nn);
+                double t = m * fr;
+                t -= std::floor(t);
+                const double ang = -2.0 * kPi * t;
+                ph[off + (size_t)I * na[ax] + k] = make_double2(std::cos(ang), std::sin(ang));
+            }
+        }
+        off += (size_t)n * na[ax];
+    }
+    CK(cudaMemcpy(g->ph, ph.data(), ph.size() * sizeof(double2), cudaMemcpyHostToDevice), "upload phases");
+    CK(cudaMemcpy(g->d_species, g->species.data(), n * sizeof(int), cudaMemcpyHostToDevice), "upload species");
+    CK(cudaMemcpy(g->d_Z, g->Z.data(), g->n_species * sizeof(double), cudaMemcpyHostToDevice), "upload Z");
+    CK(cudaMemcpy(g->d_rc, g->rc.data(), g->n_species * sizeof(double), cudaMemcpyHostToDevice), "upload rc");
+    g->have_ions = true;
+    g->vext_fresh32 = g->vext_fresh64 = false;
+    return OFDFT_OK;
+}
+
+int ofdft_energy_potential(ofdft_grid *g, const void *rho_dev, const ofdft_functional *f, double *E_out,
+                           void *V_dev) {
+    if (!g) return OFDFT_ERR_INVALID_ARG;
+    if (!rho_dev) return fail(g, OFDFT_ERR_INVALID_ARG, "rho is NULL");
+    int rc = check_functional(g, f);
+    if (rc) return rc;
+    if (f->precision == OFDFT_FP64) return eval_sync<double>(g, (const double *)rho_dev, f, (double *)V_dev, E_out);
+    return eval_sync<float>(g, (const float *)rho_dev, f, (float *)V_dev, E_out);
+}
+
+int ofdft_energy_potential_async(ofdft_grid *g, const void *rho_dev, const ofdft_functional *f, double *E_dev,
+                                 void *V_dev) {
+    if (!g) return OFDFT_ERR_INVALID_ARG;
+    if (!rho_dev || !E_dev) return fail(g, OFDFT_ERR_INVALID_ARG, "rho or E_dev is NULL");
+    int rc = check_functional(g, f);
+    if (rc) return rc;
+    if (f->precision == OFDFT_FP64) return enqueue_eval<double>(g, (const double *)rho_dev, f, (double *)V_dev, E_dev);
+    return enqueue_eval<float>(g, (const float *)rho_dev, f, (float *)V_dev, E_dev);
+}
+
+int ofdft_forces(ofdft_grid *g, const void *rho_dev, int precision, double *F_out) {
+    if (!g) return OFDFT_ERR_INVALID_ARG;
+    if (!rho_dev || !F_out) return fail(g, OFDFT_ERR_INVALID_ARG, "rho or F_out is NULL");
+    if (!g->have_ions) return fail(g, OFDFT_ERR_NO_IONS, "forces need ions");
+    if (precision == OFDFT_FP64) return forces_impl<double>(g, (const double *)rho_dev, F_out);
+    if (precision == OFDFT_FP32_MIXED) return forces_impl<float>(g, (const float *)rho_dev, F_out);
+    return fail(g, OFDFT_ERR_INVALID_ARG, "unknown precision");
+}
+
+int ofdft_optimize_density(ofdft_grid *g, void *psi_dev, const ofdft_functional *f, double N_e,
+                           double tol_E_per_atom, int max_iter, ofdft_opt_report *rep) {
+    if (!g) return OFDFT_ERR_INVALID_ARG;
+    if (!psi_dev || !(N_e > 0.0) || max_iter < 1) return fail(g, OFDFT_ERR_INVALID_ARG, "psi, N_e or max_iter");
+    int rc = check_functional(g, f);
+    if (rc) return rc;
+    if (f->precision == OFDFT_FP64)
+        return optimize_impl<double>(g, (double *)psi_dev, f, N_e, tol_E_per_atom, max_iter, rep);
+    return optimize_impl<float>(g, (float *)psi_dev, f, N_e, tol_E_per_atom, max_iter, rep);
+}
+
+int ofdft_energy_potential_batched(int n, ofdft_grid *const *grids, const void *const *rho_dev,
+                                   const ofdft_functional *f, double *E_out, void *const *V_dev,
+                                   double *const *F_out) {
+    if (n < 0 || (n > 0 && (!grids || !rho_dev || !E_out))) return OFDFT_ERR_INVALID_ARG;
+    for (int i = 0; i < n; i++) {
+        if (!grids[i]) return OFDFT_ERR_INVALID_ARG;
+        int rc = check_functional(grids[i], f);
+        if (rc) return rc;
+        if (grids[i]->stream != grids[0]->stream) return fail(grids[i], OFDFT_ERR_INVALID_ARG, "streams differ");
+    }
+    // enqueue every evaluation back to back; energies land in each grid's device slot
+    for (int i = 0; i < n; i++) {
+        ofdft_grid *g = grids[i];
+        void *V = V_dev ? V_dev[i] : nullptr;
+        int rc = (f->precision == OFDFT_FP64)
+                     ? enqueue_eval<double>(g, (const double *)rho_dev[i], f, (double *)V, nullptr)
+                     : enqueue_eval<float>(g, (const float *)rho_dev[i], f, (float *)V, nullptr);
+        if (rc) return rc;
+        double *Ed = (f->precision == OFDFT_FP64) ? g->w64.energies : g->w32.energies;
+        double *Sd = (f->precision == OFDFT_FP64) ? g->w64.scal : g->w32.scal;
+        CK(cudaMemcpyAsync(g->h_pinned, Ed, 6 * sizeof(double), cudaMemcpyDeviceToHost, g->stream), "copy E");
+        CK(cudaMemcpyAsync(g->h_pinned + 8, Sd, S_NSCAL * sizeof(double), cudaMemcpyDeviceToHost, g->stream),
+           "copy scalars");
+    }
+    if (n > 0) {
+        ofdft_grid *g = grids[0];
+        CK(cudaStreamSynchronize(g->stream), "stream synchronize");
+    }
+    for (int i = 0; i < n; i++) {
+        ofdft_grid *g = grids[i];
+        if (g->h_pinned[8 + S_BAD] != 0.0) return fail(g, OFDFT_ERR_BAD_DENSITY, "bad density in batch");
+        std::memcpy(E_out + 6 * i, g->h_pinned, 6 * sizeof(double));
+    }
+    for (int i = 0; i < n; i++) {
+        if (!F_out || !F_out[i]) continue;
+        int rc = ofdft_forces(grids[i], rho_dev[i], f->precision, F_out[i]);
+        if (rc) return rc;
+    }
+    return OFDFT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,104 @@
+// Shared device/host definitions of the OFDFT CUDA library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define OFDFT_MAX_KNOTS 64
+#define OFDFT_MAX_PASS 12
+
+namespace ofdft {
+
+// Allow a kernel the largest dynamic shared memory the device permits next to
+// its own static shared memory.
+template <typename K> inline cudaError_t allow_max_dynamic_smem(K kernel) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
+// --------------------------------------------------------------- physical constants
+// C_TF = (3/10)(3 pi^2)^(2/3) and C_WT = (6/25)(3 pi^2)^(2/3) (Sec. 2.3, Eq. WT).
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kThreePi2 = 29.608813203268074;     // 3 pi^2
+constexpr double kCTF = 2.871234000188191;           // 0.3 (3 pi^2)^(2/3)
+constexpr double kCWT = 2.2969872001505527;          // 0.24 (3 pi^2)^(2/3)
+
+// --------------------------------------------------------------- complex helpers
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { typedef float2 type; };
+template <> struct Vec2<double> { typedef double2 type; };
+
+template <typename C> __host__ __device__ __forceinline__ C cmake(decltype(C::x) a, decltype(C::x) b) {
+    C c; c.x = a; c.y = b; return c;
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return cmake<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return cmake<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+    return cmake<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C::x) s) { return cmake<C>(a.x * s, a.y * s); }
+// multiply by (s i) with s = -1 (forward) or +1 (inverse)
+template <int DIR, typename C> __device__ __forceinline__ C cmul_si(C a) {
+    return DIR < 0 ? cmake<C>(a.y, -a.x) : cmake<C>(-a.y, a.x);
+}
+
+// --------------------------------------------------------------- math wrappers
+__device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float dcbrt(float x) { return cbrtf(x); }
+__device__ __forceinline__ double dcbrt(double x) { return cbrt(x); }
+__device__ __forceinline__ float dpow(float x, float y) { return powf(x, y); }
+__device__ __forceinline__ double dpow(double x, double y) { return pow(x, y); }
+__device__ __forceinline__ float dlog(float x) { return logf(x); }
+__device__ __forceinline__ double dlog(double x) { return log(x); }
+__device__ __forceinline__ float dabs(float x) { return fabsf(x); }
+__device__ __forceinline__ double dabs(double x) { return fabs(x); }
+
+// --------------------------------------------------------------- reductions
+// Deterministic block sum of a double: warp shuffles, then warp 0 over the
+// per-warp partials.  Every thread of the block must call it; result valid in
+// thread 0.  scratch: >= 32 doubles of shared memory.
+__device__ __forceinline__ double block_sum(double v, double *scratch) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) scratch[warp] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    v = (threadIdx.x < nw) ? scratch[threadIdx.x] : 0.0;
+    if (warp == 0)
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename T> __device__ __forceinline__ T block_min(T v, T *scratch) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) { T w = __shfl_down_sync(0xffffffffu, v, o); v = w < v ? w : v; }
+    __syncthreads();
+    if (lane == 0) scratch[warp] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    v = (threadIdx.x < nw) ? scratch[threadIdx.x] : scratch[0];
+    if (warp == 0)
+        for (int o = 16; o > 0; o >>= 1) { T w = __shfl_down_sync(0xffffffffu, v, o); v = w < v ? w : v; }
+    return v;
+}
+template <typename T> __device__ __forceinline__ T block_max(T v, T *scratch) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) { T w = __shfl_down_sync(0xffffffffu, v, o); v = w > v ? w : v; }
+    __syncthreads();
+    if (lane == 0) scratch[warp] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    v = (threadIdx.x < nw) ? scratch[threadIdx.x] : scratch[0];
+    if (warp == 0)
+        for (int o = 16; o > 0; o >>= 1) { T w = __shfl_down_sync(0xffffffffu, v, o); v = w > v ? w : v; }
+    return v;
+}
+
+}  // namespace ofdft

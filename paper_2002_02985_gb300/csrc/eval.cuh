@@ -1,0 +1,95 @@
+// Parameters and launch entry points of the energy/potential pipeline.
+//
+// One evaluation (Sec. 2.3 steps s1-s4 plus the semilocal terms) runs as:
+//   stats     one pass over rho: sum rho, sum rho^(5/3), min/max rho, bad-value flag
+//   knots     1 block: FP64 reduction of the stats, mean density, kF knots (s1)
+//   row_fwd   per pair of rows: forms each channel field from rho and does the
+//             real-to-complex FFT along n2
+//   pencil    complex FFT along n1 for all channels
+//   axis0     FFT along n0, the reciprocal-space products (Hartree, PP, vW,
+//             per-knot kernels K_j(G), s2 and s3), FP64 energy partials, and
+//             the inverse FFT along n0
+//   pencil    inverse complex FFT along n1
+//   row_inv   complex-to-real FFT along n2 fused with the s4 spline blend and
+//             the assembly of V; FP64 partial of E_NL
+//   finalize  1 block: FP64 energies in a fixed order
+#pragma once
+
+#include "fft.cuh"
+
+namespace ofdft {
+
+// channel slots of the workspace (each one half spectrum n0*n1*(n2/2+1))
+enum { CH_HPP = 0, CH_VW = 1, CH_NL = 2, CH_KNOT0 = 3 };
+
+// row_inv consumer kinds
+enum { CONS_ADD = 0, CONS_VW = 1, CONS_T2 = 2, CONS_KNOT = 3, CONS_WT_A = 4, CONS_WT_B = 5 };
+
+// scalar slots (double) in the workspace
+enum {
+    S_SUM_RHO = 0, S_SUM_TF = 1, S_RHO_MIN = 2, S_RHO_MAX = 3, S_RHO_MEAN = 4, S_BAD = 5,
+    S_KF_WT = 6, S_NSCAL = 8
+};
+// energy slots: total, TF, vW, NL, H, PP
+enum { E_TOT = 0, E_TF = 1, E_VW = 2, E_NL = 3, E_H = 4, E_PP = 5 };
+
+constexpr int kMaxChan = 3 + OFDFT_MAX_KNOTS;
+constexpr int kMaxThreads = 512;     // block size bound of the FFT kernels
+
+// complex values a thread stages per FFT pass (register budget per precision)
+template <typename T> struct Cap { static constexpr int value = sizeof(T) == 4 ? 16 : 8; };
+
+template <typename T> struct EvalArgs {
+    typedef typename Vec2<T>::type C;
+    int n0, n1, n2, n2h;
+    long long N, NH;
+    double omega, dV;
+    double bvec[9];          // 2 pi b_i (rows), b = inv(cell)^T
+    const T *rho;
+    T *V;                    // may be null
+    C *chan;                 // workspace channels, slot c at chan + c * NH
+    const C *vext;           // V_ext(G) half spectrum, null if no PP
+    unsigned terms;
+    int kernel, nlpot, M;    // kernel: 0 LWT, 1 WT global
+    T alpha, beta, floor_;
+    double *scal;            // S_* slots
+    double *knots_d;         // [M] FP64 knots
+    T *knots_t;              // [M] knots rounded to T
+    T *invdk_t;              // [M-1] 1/(k_{j+1}-k_j), 0 for a zero-width interval
+    int frozen;              // knots supplied by the caller
+    int knot_spacing;
+    double *part_stats;      // [nb_stats * 2]
+    T *part_minmax;          // [nb_stats * 2]
+    double *part_ax0;        // [nb_ax0 * 3]: S_H, S_vW, S_PP
+    double *part_row;        // [nb_row]: S_NL
+    double *energies;        // [6] device output
+    int nb_stats, nb_ax0, nb_row;
+    FFTPlan p0, p1, p2;
+    const C *tw0, *tw1, *tw2;
+    int Brow, thr_rowf, thr_rowi, TW1, thr_p1, TW0, thr_ax0;
+    int nfwd, fwd_ch[kMaxChan];          // channels formed by row_fwd (slot ids)
+    int ncol, col_ch[kMaxChan];          // channels transformed forward along n1
+    int ncol_inv, col_inv_ch[kMaxChan];  // channels transformed back along n1
+    int ninv, inv_ch[kMaxChan], inv_kind[kMaxChan], inv_knot[kMaxChan];
+};
+
+// Optional per-kernel timing: record(ctx, kernel_id, phase) is called with
+// phase 0 just before and phase 1 just after each launch (ids: KernelId).
+enum KernelId { K_STATS = 0, K_KNOTS, K_ROW_FWD, K_PENCIL_FWD, K_AXIS0, K_PENCIL_INV, K_ROW_INV, K_FINALIZE, K_NKERNEL };
+struct ProfHook {
+    void (*record)(void *ctx, int kernel_id, int phase, cudaStream_t s);
+    void *ctx;
+};
+
+template <typename T> cudaError_t launch_eval(const EvalArgs<T> &a, cudaStream_t s, const ProfHook *prof = nullptr);
+// stats + knots + row_fwd + forward pencil along n1 only (the channels of a.fwd_ch / a.col_ch)
+template <typename T> cudaError_t launch_forward_rows_cols(const EvalArgs<T> &a, cudaStream_t s);
+template <typename T> size_t row_fwd_smem(const EvalArgs<T> &a);
+template <typename T> size_t row_inv_smem(const EvalArgs<T> &a);
+template <typename T> size_t pencil_smem(int n, int TW);
+template <typename T> size_t axis0_smem(int n, int TW);
+
+// series tables of the Lindhard kernel (set once per process)
+cudaError_t upload_gnl_tables();
+
+}  // namespace ofdft

@@ -1,0 +1,52 @@
+// Per-geometry kernels (structure factor, forces) and optimiser vector kernels.
+#pragma once
+
+#include "fft.cuh"
+
+namespace ofdft {
+
+// V_ext(G) = (1/Omega) sum_s v_s(|G|) S_s(G), S_s(G) = sum_{I in s} e^{-iG.R_I}
+// with the phase of each ion factorised per axis: e^{-iG.R} = P0[k0] P1[k1] P2[k2],
+// P_a[k] = e^{-2 pi i m_a(k) f_a} (f = fractional coordinates).  FP64 throughout.
+struct IonArgs {
+    int n0, n1, n2, n2h, n_ions, n_species;
+    double omega;
+    double bvec[9];                  // 2 pi b_i
+    const double2 *ph0, *ph1, *ph2;  // [n_ions][n0], [n_ions][n1], [n_ions][n2h]
+    const int *species;              // [n_ions]
+    const double *Z, *rc;            // [n_species]
+};
+
+cudaError_t launch_vext(const IonArgs &a, double2 *vext64, float2 *vext32, cudaStream_t s);
+
+// forces from the normalised half spectrum rho_hat (FP64 or FP32 complex)
+template <typename C>
+cudaError_t launch_forces(const IonArgs &a, const C *rhohat, double *partials, int nchunk, cudaStream_t s);
+
+// plain forward FFT along n0 of a half spectrum (in place), used by forces
+template <typename T>
+cudaError_t launch_axis0_fft(typename Vec2<T>::type *data, int n0, long long P, const FFTPlan &p,
+                             const typename Vec2<T>::type *tw, int TW, int thr, double scale, cudaStream_t s);
+
+// ---- optimiser vector kernels (all reductions FP64, fixed order) ----------
+// out[slot] = sum_i a_i b_i (c_i if c != null)
+template <typename T>
+cudaError_t launch_dot(const T *a, const T *b, const T *c, long long N, double *partials, int nblk,
+                       double *out, cudaStream_t s);
+// y = alpha * x + beta * y (scalars read from device double pointers when given)
+template <typename T>
+cudaError_t launch_axpby(T *y, const T *x, double alpha, double beta, long long N, cudaStream_t s);
+// psi_l = psi cos(l) + p sin(l);  rho = psi_l^2
+template <typename T>
+cudaError_t launch_rotate(T *psi_l, T *rho, const T *psi, const T *p, double c, double sn, long long N,
+                          cudaStream_t s);
+// g = 2 psi (V - mu) dV
+template <typename T>
+cudaError_t launch_grad(T *g, const T *psi, const T *V, double mu, double dV, long long N, cudaStream_t s);
+// rho = psi^2 (and optional scale of psi)
+template <typename T>
+cudaError_t launch_square(T *rho, T *psi, double scale, long long N, cudaStream_t s);
+// d = -g + beta d ; dot partial <d, g> computed by launch_dot afterwards
+template <typename T> cudaError_t launch_copy(T *dst, const T *src, long long N, cudaStream_t s);
+
+}  // namespace ofdft

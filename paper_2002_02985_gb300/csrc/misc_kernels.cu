@@ -1,0 +1,253 @@
+// Structure factor, forces and optimiser vector kernels (see misc.cuh).
+#include "misc.cuh"
+
+namespace ofdft {
+
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__device__ __forceinline__ void gvec_of(const IonArgs &a, long long e, double &gx, double &gy, double &gz, int &k0,
+                                        int &k1, int &k2) {
+    k2 = (int)(e % a.n2h);
+    const long long r = e / a.n2h;
+    k1 = (int)(r % a.n1);
+    k0 = (int)(r / a.n1);
+    const double m0 = (k0 <= a.n0 / 2) ? k0 : k0 - a.n0;
+    const double m1 = (k1 <= a.n1 / 2) ? k1 : k1 - a.n1;
+    const double m2 = k2;
+    gx = m0 * a.bvec[0] + m1 * a.bvec[3] + m2 * a.bvec[6];
+    gy = m0 * a.bvec[1] + m1 * a.bvec[4] + m2 * a.bvec[7];
+    gz = m0 * a.bvec[2] + m1 * a.bvec[5] + m2 * a.bvec[8];
+}
+
+// v(q) = -4 pi Z exp(-(q rc)^2/4)/q^2, v(0) = pi Z rc^2 (finite part, Coulomb tail neutralised)
+__device__ __forceinline__ double pp_form(double q2, double Z, double rc) {
+    if (q2 <= 0.0) return kPi * Z * rc * rc;
+    return -4.0 * kPi * Z * exp(-q2 * rc * rc * 0.25) / q2;
+}
+
+__global__ void __launch_bounds__(256) vext_kernel(IonArgs a, double2 *v64, float2 *v32) {
+    const long long NH = (long long)a.n0 * a.n1 * a.n2h;
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= NH) return;
+    double gx, gy, gz;
+    int k0, k1, k2;
+    gvec_of(a, e, gx, gy, gz, k0, k1, k2);
+    const double q2 = gx * gx + gy * gy + gz * gz;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int s = 0; s < a.n_species; s++) {
+        double2 S = make_double2(0.0, 0.0);
+        for (int I = 0; I < a.n_ions; I++) {
+            if (a.species[I] != s) continue;
+            const double2 p = zmul(zmul(a.ph0[(size_t)I * a.n0 + k0], a.ph1[(size_t)I * a.n1 + k1]),
+                                   a.ph2[(size_t)I * a.n2h + k2]);
+            S.x += p.x;
+            S.y += p.y;
+        }
+        const double v = pp_form(q2, a.Z[s], a.rc[s]) / a.omega;
+        acc.x += v * S.x;
+        acc.y += v * S.y;
+    }
+    if (v64) v64[e] = acc;
+    if (v32) v32[e] = make_float2((float)acc.x, (float)acc.y);
+}
+
+cudaError_t launch_vext(const IonArgs &a, double2 *vext64, float2 *vext32, cudaStream_t s) {
+    const long long NH = (long long)a.n0 * a.n1 * a.n2h;
+    vext_kernel<<<(unsigned)((NH + 255) / 256), 256, 0, s>>>(a, vext64, vext32);
+    return cudaGetLastError();
+}
+
+// F_I = -sum_G w G v(|G|) Im[conj(rho_hat) e^{-iG.R_I}]; block (I, chunk) sums a
+// contiguous range of the half spectrum and writes one partial per component.
+template <typename C>
+__global__ void __launch_bounds__(256) forces_kernel(IonArgs a, const C *rh, double *part, int nchunk) {
+    __shared__ double sd[32];
+    const int I = blockIdx.x, chunk = blockIdx.y;
+    const long long NH = (long long)a.n0 * a.n1 * a.n2h;
+    const long long per = (NH + nchunk - 1) / nchunk;
+    const long long e0 = chunk * per, e1 = (e0 + per < NH) ? e0 + per : NH;
+    const int s = a.species[I];
+    const double Z = a.Z[s], rc = a.rc[s];
+    double fx = 0.0, fy = 0.0, fz = 0.0;
+    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        double gx, gy, gz;
+        int k0, k1, k2;
+        gvec_of(a, e, gx, gy, gz, k0, k1, k2);
+        const double q2 = gx * gx + gy * gy + gz * gz;
+        if (q2 <= 0.0) continue;
+        const double w = (k2 == 0 || (a.n2 % 2 == 0 && 2 * k2 == a.n2)) ? 1.0 : 2.0;
+        const double2 p = zmul(zmul(a.ph0[(size_t)I * a.n0 + k0], a.ph1[(size_t)I * a.n1 + k1]),
+                               a.ph2[(size_t)I * a.n2h + k2]);
+        const C r = rh[e];
+        // Im[conj(r) p] = r.x p.y - r.y p.x
+        const double im = (double)r.x * p.y - (double)r.y * p.x;
+        const double f = -w * pp_form(q2, Z, rc) * im;
+        fx += f * gx;
+        fy += f * gy;
+        fz += f * gz;
+    }
+    fx = block_sum(fx, sd);
+    if (threadIdx.x == 0) part[((size_t)I * nchunk + chunk) * 3 + 0] = fx;
+    fy = block_sum(fy, sd);
+    if (threadIdx.x == 0) part[((size_t)I * nchunk + chunk) * 3 + 1] = fy;
+    fz = block_sum(fz, sd);
+    if (threadIdx.x == 0) part[((size_t)I * nchunk + chunk) * 3 + 2] = fz;
+}
+
+template <typename C>
+cudaError_t launch_forces(const IonArgs &a, const C *rhohat, double *partials, int nchunk, cudaStream_t s) {
+    dim3 g(a.n_ions, nchunk);
+    forces_kernel<C><<<g, 256, 0, s>>>(a, rhohat, partials, nchunk);
+    return cudaGetLastError();
+}
+template cudaError_t launch_forces<float2>(const IonArgs &, const float2 *, double *, int, cudaStream_t);
+template cudaError_t launch_forces<double2>(const IonArgs &, const double2 *, double *, int, cudaStream_t);
+
+// ---------------------------------------------------------------- plain FFT along n0
+template <typename T, int CAP>
+__global__ void __launch_bounds__(512) axis0_fft_kernel(typename Vec2<T>::type *data, int n0, long long P, FFTPlan p,
+                                 const typename Vec2<T>::type *twg, int TW, T scale) {
+    typedef typename Vec2<T>::type C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tw = (C *)smem_raw;
+    C *buf = tw + n0;
+    for (int i = threadIdx.x; i < n0; i += blockDim.x) tw[i] = twg[i];
+    const long long c0 = (long long)blockIdx.x * TW;
+    for (int idx = threadIdx.x; idx < n0 * TW; idx += blockDim.x) {
+        const int w = idx % TW, i = idx / TW;
+        buf[idx] = (c0 + w < P) ? data[(size_t)i * P + c0 + w] : cmake<C>((T)0, (T)0);
+    }
+    __syncthreads();
+    fft_smem<-1, CAP>(buf, TW, TW, p, tw);
+    for (int idx = threadIdx.x; idx < n0 * TW; idx += blockDim.x) {
+        const int w = idx % TW, i = idx / TW;
+        if (c0 + w < P) data[(size_t)i * P + c0 + w] = cscale(buf[idx], scale);
+    }
+}
+
+template <typename T>
+cudaError_t launch_axis0_fft(typename Vec2<T>::type *data, int n0, long long P, const FFTPlan &p,
+                             const typename Vec2<T>::type *tw, int TW, int thr, double scale, cudaStream_t s) {
+    typedef typename Vec2<T>::type C;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = allow_max_dynamic_smem(axis0_fft_kernel<T, (sizeof(T) == 4 ? 16 : 8)>);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const size_t sm = (size_t)n0 * sizeof(C) * (1 + TW);
+    const unsigned nb = (unsigned)((P + TW - 1) / TW);
+    axis0_fft_kernel<T, (sizeof(T) == 4 ? 16 : 8)><<<nb, thr, sm, s>>>(data, n0, P, p, tw, TW, (T)scale);
+    return cudaGetLastError();
+}
+template cudaError_t launch_axis0_fft<float>(float2 *, int, long long, const FFTPlan &, const float2 *, int, int,
+                                             double, cudaStream_t);
+template cudaError_t launch_axis0_fft<double>(double2 *, int, long long, const FFTPlan &, const double2 *, int, int,
+                                              double, cudaStream_t);
+
+// ---------------------------------------------------------------- optimiser vectors
+template <typename T>
+__global__ void __launch_bounds__(256) dot_kernel(const T *a, const T *b, const T *c, long long N, double *part) {
+    __shared__ double sd[32];
+    double acc = 0.0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += stride) {
+        double v = (double)a[i] * (double)b[i];
+        if (c) v *= (double)c[i];
+        acc += v;
+    }
+    acc = block_sum(acc, sd);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(256) sum_partials_kernel(const double *part, int n, double *out) {
+    __shared__ double sd[32];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += part[i];
+    acc = block_sum(acc, sd);
+    if (threadIdx.x == 0) *out = acc;
+}
+
+template <typename T>
+cudaError_t launch_dot(const T *a, const T *b, const T *c, long long N, double *partials, int nblk, double *out,
+                       cudaStream_t s) {
+    dot_kernel<T><<<nblk, 256, 0, s>>>(a, b, c, N, partials);
+    sum_partials_kernel<<<1, 256, 0, s>>>(partials, nblk, out);
+    return cudaGetLastError();
+}
+
+template <typename T> __global__ void axpby_kernel(T *y, const T *x, T al, T be, long long N) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += stride)
+        y[i] = al * x[i] + be * y[i];
+}
+template <typename T>
+cudaError_t launch_axpby(T *y, const T *x, double alpha, double beta, long long N, cudaStream_t s) {
+    axpby_kernel<T><<<1216, 256, 0, s>>>(y, x, (T)alpha, (T)beta, N);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void rotate_kernel(T *psl, T *rho, const T *psi, const T *p, T c, T sn, long long N) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += stride) {
+        const T v = psi[i] * c + p[i] * sn;
+        psl[i] = v;
+        rho[i] = v * v;
+    }
+}
+template <typename T>
+cudaError_t launch_rotate(T *psi_l, T *rho, const T *psi, const T *p, double c, double sn, long long N,
+                          cudaStream_t s) {
+    rotate_kernel<T><<<1216, 256, 0, s>>>(psi_l, rho, psi, p, (T)c, (T)sn, N);
+    return cudaGetLastError();
+}
+
+template <typename T> __global__ void grad_kernel(T *g, const T *psi, const T *V, T mu, T dV2, long long N) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += stride)
+        g[i] = dV2 * psi[i] * (V[i] - mu);
+}
+template <typename T>
+cudaError_t launch_grad(T *g, const T *psi, const T *V, double mu, double dV, long long N, cudaStream_t s) {
+    grad_kernel<T><<<1216, 256, 0, s>>>(g, psi, V, (T)mu, (T)(2.0 * dV), N);
+    return cudaGetLastError();
+}
+
+template <typename T> __global__ void square_kernel(T *rho, T *psi, T scale, long long N) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += stride) {
+        const T v = psi[i] * scale;
+        psi[i] = v;
+        rho[i] = v * v;
+    }
+}
+template <typename T> cudaError_t launch_square(T *rho, T *psi, double scale, long long N, cudaStream_t s) {
+    square_kernel<T><<<1216, 256, 0, s>>>(rho, psi, (T)scale, N);
+    return cudaGetLastError();
+}
+
+template <typename T> __global__ void copy_kernel(T *d, const T *s, long long N) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += stride) d[i] = s[i];
+}
+template <typename T> cudaError_t launch_copy(T *dst, const T *src, long long N, cudaStream_t s) {
+    copy_kernel<T><<<1216, 256, 0, s>>>(dst, src, N);
+    return cudaGetLastError();
+}
+
+#define INST(T)                                                                                              \
+    template cudaError_t launch_dot<T>(const T *, const T *, const T *, long long, double *, int, double *,    \
+                                       cudaStream_t);                                                        \
+    template cudaError_t launch_axpby<T>(T *, const T *, double, double, long long, cudaStream_t);           \
+    template cudaError_t launch_rotate<T>(T *, T *, const T *, const T *, double, double, long long,         \
+                                          cudaStream_t);                                                     \
+    template cudaError_t launch_grad<T>(T *, const T *, const T *, double, double, long long, cudaStream_t);  \
+    template cudaError_t launch_square<T>(T *, T *, double, long long, cudaStream_t);                        \
+    template cudaError_t launch_copy<T>(T *, const T *, long long, cudaStream_t);
+INST(float)
+INST(double)
+
+}  // namespace ofdft

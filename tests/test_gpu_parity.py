@@ -1,0 +1,183 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances
+  FP64 path : energy <= 1e-10 relative (per term), V <= 1e-9 Ha max abs.
+  FP32 path : energy <= 1e-6 Ha/atom; V: ||dV||_2 / ||V||_2 <= 1e-4, at points
+              whose kF is not within 1e-5 (relative) of a knot (there FP32 and
+              FP64 may legitimately pick neighbouring spline intervals; the
+              interval is a floating-point decision taken in each side's own
+              precision).
+Both sides read the same float32 density (the oracle upcasts it exactly).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import functionals as ofn
+from oracle.evaluate import Functional as OFunc, evaluate
+from oracle.forces import forces as oforces
+from oracle.grid import Grid as OGrid
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2002_02985_gb300 as ofd  # noqa: E402
+from paper_2002_02985_gb300 import _lib as L  # noqa: E402
+
+TERM_BITS = {"TF": L.TERM_TF, "VW": L.TERM_VW, "NL": L.TERM_NL, "HARTREE": L.TERM_HARTREE, "PP": L.TERM_PP}
+KEYMAP = {"TF": "TF", "VW": "vW", "NL": "NL", "HARTREE": "H", "PP": "PP"}
+
+
+def triclinic():
+    return np.array([[9.0, 0.0, 0.0], [1.1, 8.2, 0.0], [-0.6, 0.8, 7.7]])
+
+
+def small_case(shape, cell=None, natoms=3, seed=0, noise=0.1):
+    cell = triclinic() if cell is None else cell
+    rng = np.random.default_rng(seed)
+    pos = rng.uniform(0, 1, (natoms, 3)) @ cell
+    rho = W.gaussian_density(cell, shape, pos, 2.0, 0.9)
+    rho = W.apply_noise(rho + 1e-3, noise, seed + 1)
+    rho = W.renormalise(rho, cell, 2.0 * natoms)
+    return cell, pos, rho
+
+
+def run_both(cell, shape, pos, rho64, func_kw, precision, species=None, Z=(2.0,), rc=(0.9,)):
+    species = np.zeros(len(pos), np.int32) if species is None else species
+    dt = torch.float64 if precision == L.FP64 else torch.float32
+    rho_in = rho64 if precision == L.FP64 else rho64.astype(np.float32)
+    g = ofd.Grid(cell, shape)
+    g.set_ions(pos, species, Z, rc)
+    f = ofd.Functional(precision=precision, **func_kw)
+    E, V = g.energy_potential(torch.from_numpy(np.ascontiguousarray(rho_in)).to("cuda", dt), f)
+    og = OGrid(cell, shape)
+    Vg = ofn.external_potential_G(og, pos, species, list(Z), list(rc))
+    terms = tuple(k for k, b in TERM_BITS.items() if f.terms & b)
+    of = OFunc(terms=terms, alpha=f.alpha, beta=f.beta, n_knots=f.n_knots,
+               spacing="log" if f.knot_spacing == L.KNOTS_LOG else "arith",
+               knots=None if f.knots is None else np.asarray(f.knots),
+               potential="exact" if f.nl_potential == L.NLPOT_EXACT else "interpolated",
+               kernel="lwt" if f.kernel == L.KERNEL_LWT else "wt_global")
+    Eo, Vo = evaluate(og, rho_in.astype(np.float64), of, Vg)
+    return E, V.double().cpu().numpy(), Eo, Vo, og, g
+
+
+def knot_mask(rho, n_knots, rtol=1e-5, knots=None):
+    k = ofn.make_knots(rho, n_knots) if knots is None else np.asarray(knots)
+    kF = ofn.fermi_wavevector(rho)
+    d = np.min(np.abs(kF[..., None] / k[None] - 1.0), axis=-1)
+    return d > rtol
+
+
+FP64_CASES = [
+    ((12, 10, 15), dict(n_knots=5)),
+    ((16, 18, 20), dict(n_knots=6, knot_spacing=L.KNOTS_ARITH)),
+    ((30, 24, 27), dict(n_knots=8, nl_potential=L.NLPOT_INTERP)),
+    ((20, 20, 20), dict(n_knots=4, kernel=L.KERNEL_WT_GLOBAL)),
+    ((25, 32, 18), dict(n_knots=7)),
+]
+
+
+@pytest.mark.parametrize("shape,kw", FP64_CASES)
+def test_fp64_energy_potential_matches_oracle(shape, kw):
+    cell, pos, rho = small_case(shape)
+    E, V, Eo, Vo, og, _ = run_both(cell, shape, pos, rho, kw, L.FP64)
+    for k in ("TF", "vW", "NL", "H", "PP", "total"):
+        assert abs(E[k] - Eo[k]) <= 1e-10 * max(1.0, abs(Eo[k])), (k, E[k], Eo[k])
+    assert np.max(np.abs(V - Vo)) <= 1e-9 * max(1.0, np.max(np.abs(Vo))), np.max(np.abs(V - Vo))
+
+
+@pytest.mark.parametrize("term", ["TF", "VW", "NL", "HARTREE", "PP"])
+def test_fp64_single_terms(term):
+    shape = (18, 20, 16)
+    cell, pos, rho = small_case(shape, seed=3)
+    E, V, Eo, Vo, og, _ = run_both(cell, shape, pos, rho, dict(terms=TERM_BITS[term], n_knots=6), L.FP64)
+    k = KEYMAP[term]
+    assert abs(E[k] - Eo[k]) <= 1e-10 * max(1.0, abs(Eo[k])), (E[k], Eo[k])
+    assert np.max(np.abs(V - Vo)) <= 1e-9 * max(1.0, np.max(np.abs(Vo)))
+
+
+FP32_CASES = [
+    ("fcc-al-4/32", dict()),
+    ("fcc-al-4/32", dict(nl_potential=L.NLPOT_INTERP)),
+]
+
+
+@pytest.mark.parametrize("name,kw", FP32_CASES)
+def test_fp32_mixed_workload_matches_oracle(name, kw):
+    wl = W.workload(name)
+    rho = W.model_density(wl)
+    E, V, Eo, Vo, og, _ = run_both(wl["cell"], wl["shape"], wl["positions"], rho,
+                                   dict(n_knots=wl["n_knots"], **kw), L.FP32_MIXED, wl["species"],
+                                   tuple(wl["Z"]), tuple(wl["rc"]))
+    assert abs(E["total"] - Eo["total"]) / wl["n_atoms"] <= 1e-6, (E["total"], Eo["total"])
+    for k in ("TF", "vW", "NL", "H", "PP"):
+        assert abs(E[k] - Eo[k]) / wl["n_atoms"] <= 1e-6, (k, E[k], Eo[k])
+    m = knot_mask(rho.astype(np.float32).astype(np.float64), wl["n_knots"])
+    rel = np.linalg.norm((V - Vo)[m]) / np.linalg.norm(Vo[m])
+    assert rel <= 1e-4, rel
+
+
+def test_fp32_mixed_ragged_triclinic():
+    shape = (30, 24, 25)
+    cell, pos, rho = small_case(shape, seed=5)
+    E, V, Eo, Vo, og, _ = run_both(cell, shape, pos, rho, dict(n_knots=8), L.FP32_MIXED)
+    assert abs(E["total"] - Eo["total"]) <= 1e-6 * 3, (E, Eo)
+    m = knot_mask(rho.astype(np.float32).astype(np.float64), 8)
+    assert np.linalg.norm((V - Vo)[m]) / np.linalg.norm(Vo[m]) <= 1e-4
+
+
+@pytest.mark.parametrize("precision,tol", [(L.FP64, 1e-10), (L.FP32_MIXED, 2e-6)])
+def test_forces_match_oracle(precision, tol):
+    wl = W.workload("fcc-al-4/32")
+    rho = W.model_density(wl)
+    rin = rho if precision == L.FP64 else rho.astype(np.float32)
+    dt = torch.float64 if precision == L.FP64 else torch.float32
+    g = ofd.Grid(wl["cell"], wl["shape"])
+    g.set_ions(wl["positions"], wl["species"], wl["Z"], wl["rc"])
+    F = g.forces(torch.from_numpy(np.ascontiguousarray(rin)).to("cuda", dt), precision)
+    og = OGrid(wl["cell"], wl["shape"])
+    Fo = oforces(og, rin.astype(np.float64), wl["positions"], wl["species"], wl["Z"], wl["rc"])
+    assert np.max(np.abs(F - Fo)) <= tol * max(1.0, np.max(np.abs(Fo))), np.max(np.abs(F - Fo))
+
+
+def test_frozen_knots_fp64():
+    shape = (16, 16, 16)
+    cell, pos, rho = small_case(shape, seed=9)
+    knots = ofn.make_knots(rho, 6) * np.array([0.9, 1, 1, 1, 1, 1.1])
+    E, V, Eo, Vo, og, _ = run_both(cell, shape, pos, rho, dict(n_knots=6, knots=knots), L.FP64)
+    assert abs(E["NL"] - Eo["NL"]) <= 1e-10 * abs(Eo["NL"])
+    assert np.max(np.abs(V - Vo)) <= 1e-9
+
+
+def test_bad_density_and_unsupported_size_are_errors():
+    cell = np.eye(3) * 8.0
+    with pytest.raises(ofd.OFDFTError) as e:
+        ofd.Grid(cell, (14, 16, 16))        # 14 = 2 * 7
+    assert e.value.status == -2
+    g = ofd.Grid(cell, (16, 16, 16))
+    rho = torch.full((16, 16, 16), 0.01, device="cuda")
+    rho[3, 4, 5] = float("nan")
+    with pytest.raises(ofd.OFDFTError) as e:
+        g.energy_potential(rho, ofd.Functional(terms=L.TERM_TF | L.TERM_VW))
+    assert e.value.status == -3
+    rho[3, 4, 5] = -1.0
+    with pytest.raises(ofd.OFDFTError) as e:
+        g.energy_potential(rho, ofd.Functional(terms=L.TERM_TF))
+    assert e.value.status == -3
+    with pytest.raises(ofd.OFDFTError) as e:
+        g.energy_potential(rho.abs(), ofd.Functional(terms=L.TERM_PP))   # no ions set
+    assert e.value.status == -7
+
+
+def test_repeated_runs_are_bit_identical():
+    wl = W.workload("fcc-al-4/32")
+    rho = torch.from_numpy(W.model_density(wl).astype(np.float32)).cuda()
+    g = ofd.Grid(wl["cell"], wl["shape"])
+    g.set_ions(wl["positions"], wl["species"], wl["Z"], wl["rc"])
+    f = ofd.Functional(n_knots=10)
+    E0, V0 = g.energy_potential(rho, f)
+    for _ in range(5):
+        E1, V1 = g.energy_potential(rho, f)
+        assert E1 == E0
+        assert torch.equal(V0, V1)
