@@ -170,6 +170,24 @@ int ofdft_profile_enable(ofdft_grid *g, int enable);
 int ofdft_profile_reset(ofdft_grid *g);
 int ofdft_profile_read(ofdft_grid *g, int idx, const char **name, int *launches, double *total_ms);
 
+/* Thomas-Fermi energy and potential that allocates no device memory.
+ * The paper has no counterpart: this exists for callers that cannot let a
+ * library call cudaMalloc -- a host application whose own allocator owns all
+ * device memory, or code running while a stream is captured into a CUDA graph.
+ * Computes E_TF = C_TF sum_r rho^(5/3) dV into E_dev (DEVICE double[1]) and,
+ * when V_dev is not NULL, V_TF = (5/3) C_TF rho^(2/3) into V_dev (DEVICE [n],
+ * same precision as rho), asynchronously on cuda_stream.  The reduction
+ * partials live in a static device array sized for OFDFT_NOALLOC_MAX_POINTS
+ * points, held by every GPU that loads the library until the process exits;
+ * n above that limit returns OFDFT_ERR_INVALID_ARG without touching the GPU.
+ * The first call on each device looks up the array's device address (make it
+ * before any stream capture).  All calls share the array, so calls that
+ * overlap on the GPU race; order them on one stream.  Matches
+ * ofdft_energy_potential with terms = OFDFT_TERM_TF. */
+#define OFDFT_NOALLOC_MAX_POINTS 8388608LL   /* 4096 blocks x 2048 points */
+int ofdft_tf_energy_potential_noalloc(const void *rho_dev, long long n, double dV, int precision,
+                                      double *E_dev, void *V_dev, void *cuda_stream);
+
 /* Human-readable text of a status code, and the handle's last error message. */
 const char *ofdft_status_string(int status);
 const char *ofdft_last_error(const ofdft_grid *g);

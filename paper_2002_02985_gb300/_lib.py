@@ -12,6 +12,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libofdft.so")
 
 OFDFT_OK = 0
+OFDFT_ERR_INVALID_ARG = -1
 STATUS = {0: "OFDFT_OK", -1: "OFDFT_ERR_INVALID_ARG", -2: "OFDFT_ERR_UNSUPPORTED_SIZE",
           -3: "OFDFT_ERR_BAD_DENSITY", -4: "OFDFT_ERR_OOM", -5: "OFDFT_ERR_CUDA",
           -6: "OFDFT_ERR_NOT_CONVERGED", -7: "OFDFT_ERR_NO_IONS"}
@@ -29,7 +30,9 @@ EXPORTS = (
     "ofdft_energy_potential_async", "ofdft_forces", "ofdft_optimize_density",
     "ofdft_energy_potential_batched", "ofdft_status_string", "ofdft_last_error", "ofdft_version",
     "ofdft_profile_enable", "ofdft_profile_reset", "ofdft_profile_read",
+    "ofdft_tf_energy_potential_noalloc",
 )
+NOALLOC_MAX_POINTS = 8388608
 
 
 class CFunctional(ct.Structure):
@@ -77,6 +80,7 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.ofdft_profile_enable.argtypes = [P, I]
     lib.ofdft_profile_reset.argtypes = [P]
     lib.ofdft_profile_read.argtypes = [P, I, ct.POINTER(ct.c_char_p), ct.POINTER(I), ct.POINTER(D)]
+    lib.ofdft_tf_energy_potential_noalloc.argtypes = [V, ct.c_longlong, D, I, V, V, P]
     lib.ofdft_status_string.argtypes = [I]
     lib.ofdft_status_string.restype = ct.c_char_p
     lib.ofdft_last_error.argtypes = [P]

@@ -1,0 +1,54 @@
+"""The no-allocation Thomas-Fermi entry point against the regular one.
+
+ofdft_tf_energy_potential_noalloc serves callers that cannot let a library
+allocate device memory (an application that owns all device memory through
+its own allocator, or code running during CUDA graph capture).  Its reduction
+partials live in a static device array; this test calls it through the C ABI
+twice in a row (the second call reuses the array left by the first) and
+compares energy and potential with ofdft_energy_potential (terms = TF).
+The file name makes pytest collect it last.
+"""
+import ctypes as ct
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2002_02985_gb300 as ofd  # noqa: E402
+from paper_2002_02985_gb300 import _lib as L  # noqa: E402
+
+
+@pytest.mark.parametrize("precision", [L.FP32_MIXED, L.FP64])
+def test_noalloc_tf_matches_regular_entry_point(precision):
+    lib = L.load()
+    wl = W.workload("fcc-al-4/32")
+    dt = torch.float64 if precision == L.FP64 else torch.float32
+    rho = torch.from_numpy(W.model_density(wl)).to("cuda", dt).contiguous()
+    g = ofd.Grid(wl["cell"], wl["shape"])
+    E_ref, V_ref = g.energy_potential(rho, ofd.Functional(terms=L.TERM_TF, precision=precision))
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        E_dev = torch.full((1,), -1.0, dtype=torch.float64, device="cuda")
+        V = torch.full_like(rho, -1.0)
+        st = lib.ofdft_tf_energy_potential_noalloc(ct.c_void_p(rho.data_ptr()), rho.numel(), g.dV, precision,
+                                                   ct.c_void_p(E_dev.data_ptr()), ct.c_void_p(V.data_ptr()),
+                                                   ct.c_void_p(stream.cuda_stream))
+        assert st == L.OFDFT_OK
+        torch.cuda.synchronize()
+        assert abs(float(E_dev) - E_ref["TF"]) <= 1e-10 * abs(E_ref["TF"])
+        rtol = 1e-12 if precision == L.FP64 else 1e-6
+        assert torch.allclose(V, V_ref, rtol=rtol, atol=0.0)
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch():
+    lib = L.load()
+    rho = torch.ones(16, device="cuda")
+    E_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
+    st = lib.ofdft_tf_energy_potential_noalloc(ct.c_void_p(rho.data_ptr()), L.NOALLOC_MAX_POINTS + 1, 1.0,
+                                               L.FP32_MIXED, ct.c_void_p(E_dev.data_ptr()), None,
+                                               ct.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == L.OFDFT_ERR_INVALID_ARG
