@@ -2,6 +2,7 @@
 // forces, batched evaluation and the psi = sqrt(rho) CG optimiser.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -68,6 +69,7 @@ template <typename T> struct Workspace {
     T *knots_t = nullptr, *invdk_t = nullptr, *part_minmax = nullptr;
     double *part_stats = nullptr, *part_ax0 = nullptr, *part_row = nullptr, *part_misc = nullptr;
     T *opt = nullptr;                 // optimiser fields (8 * N), allocated on demand
+    LaunchSet ks;                     // FFT-carrying kernels (size-specialised where compiled)
     int Brow = 0, thr_rowf = 0, thr_rowi = 0, TW1 = 0, thr_p1 = 0, TW0 = 0, thr_ax0 = 0, nb_row = 0, nb_ax0 = 0;
 };
 
@@ -132,28 +134,55 @@ template <> Workspace<double> &ws<double>(ofdft_grid *g) { return g->w64; }
 template <typename T> int choose_launch(ofdft_grid *g, Workspace<T> &w) {
     typedef typename Vec2<T>::type C;
     const size_t row_budget = 110 * 1024;
-    EvalArgs<T> probe;
-    std::memset(&probe, 0, sizeof(probe));
-    probe.n2 = g->n[2];
     const int cap = Cap<T>::value, tmax = kMaxThreads;
-    int B = 16;
-    for (; B >= 1; B /= 2) {
-        probe.Brow = B;
-        if (row_inv_smem(probe) <= row_budget && threads_for(g->plan[2], B, cap) <= tmax) break;
+    const char *env = std::getenv("OFDFT_FORCE_GENERIC");
+    const bool generic_only = env && env[0] == '1';
+    w.ks = generic_kernels<T>();
+    const void *k1 = nullptr, *k2 = nullptr;
+    int Bv = 0, ntv = 0;
+    // rows (n2)
+    if (!generic_only && find_specialised<T>(ROLE_ROW, g->n[2], &k1, &k2, &Bv, &ntv)) {
+        w.ks.row_fwd = k1;
+        w.ks.row_inv = k2;
+        w.Brow = Bv;
+        w.thr_rowf = w.thr_rowi = ntv;
+    } else {
+        int B = 16;
+        for (; B >= 1; B /= 2)
+            if (row_inv_smem_bytes<T>(g->n[2], B) <= row_budget && threads_for(g->plan[2], B, cap) <= tmax) break;
+        if (B < 1) return fail(g, OFDFT_ERR_UNSUPPORTED_SIZE, "row transform does not fit in shared memory");
+        w.Brow = B;
+        w.thr_rowf = w.thr_rowi = std::min(std::max(threads_for(g->plan[2], B, cap), 128), tmax);
     }
-    if (B < 1) return fail(g, OFDFT_ERR_UNSUPPORTED_SIZE, "row transform does not fit in shared memory");
-    w.Brow = B;
-    w.thr_rowf = w.thr_rowi = std::min(std::max(threads_for(g->plan[2], B, cap), 128), tmax);
-    int TW = 16;
-    while (TW > 1 && ((size_t)g->n[1] * TW * sizeof(C) > 64 * 1024 || threads_for(g->plan[1], TW, cap) > tmax)) TW /= 2;
-    w.TW1 = TW;
-    w.thr_p1 = std::min(std::max(threads_for(g->plan[1], TW, cap), 128), tmax);
-    TW = 16;
-    while (TW > 1 && (axis0_smem<T>(g->n[0], TW) > 200 * 1024 || threads_for(g->plan[0], TW, cap) > tmax)) TW /= 2;
-    w.TW0 = TW;
-    w.thr_ax0 = std::min(std::max(threads_for(g->plan[0], TW, cap), 128), tmax);
+    // pencils along n1
+    if (!generic_only && find_specialised<T>(ROLE_PENCIL, g->n[1], &k1, &k2, &Bv, &ntv)) {
+        w.ks.pen_fwd = k1;
+        w.ks.pen_inv = k2;
+        w.TW1 = Bv;
+        w.thr_p1 = ntv;
+    } else {
+        int TW = 16;
+        while (TW > 1 && ((size_t)g->n[1] * TW * sizeof(C) > 64 * 1024 || threads_for(g->plan[1], TW, cap) > tmax))
+            TW /= 2;
+        w.TW1 = TW;
+        w.thr_p1 = std::min(std::max(threads_for(g->plan[1], TW, cap), 128), tmax);
+    }
+    // axis 0 with the reciprocal-space products
+    if (!generic_only && find_specialised<T>(ROLE_AXIS0, g->n[0], &k1, &k2, &Bv, &ntv)) {
+        w.ks.axis0 = k1;
+        w.TW0 = Bv;
+        w.thr_ax0 = ntv;
+    } else {
+        int TW = 16;
+        while (TW > 1 && (axis0_smem_bytes<T>(g->n[0], TW) > 200 * 1024 || threads_for(g->plan[0], TW, cap) > tmax))
+            TW /= 2;
+        w.TW0 = TW;
+        w.thr_ax0 = std::min(std::max(threads_for(g->plan[0], TW, cap), 128), tmax);
+    }
+    cudaError_t e = prepare_kernels(w.ks);
+    if (e != cudaSuccess) return fail(g, OFDFT_ERR_CUDA, "kernel attributes", e);
     const long long R = (long long)g->n[0] * g->n[1];
-    w.nb_row = (int)(((R + 1) / 2 + B - 1) / B);
+    w.nb_row = (int)(((R + 1) / 2 + w.Brow - 1) / w.Brow);
     const long long P = (long long)g->n[1] * g->n2h;
     w.nb_ax0 = (int)((P + w.TW0 - 1) / w.TW0);
     return OFDFT_OK;
@@ -185,7 +214,7 @@ template <typename T> int ensure_ws(ofdft_grid *g, int nslots) {
         const int nbs = 2 * g->nsm;
         CK(cudaMalloc(&w.part_stats, 2 * nbs * sizeof(double)), "cudaMalloc partials");
         CK(cudaMalloc(&w.part_minmax, 2 * nbs * sizeof(T)), "cudaMalloc partials");
-        CK(cudaMalloc(&w.part_ax0, 3 * (size_t)w.nb_ax0 * sizeof(double)), "cudaMalloc partials");
+        CK(cudaMalloc(&w.part_ax0, 4 * (size_t)w.nb_ax0 * sizeof(double)), "cudaMalloc partials");
         CK(cudaMalloc(&w.part_row, (size_t)w.nb_row * sizeof(double)), "cudaMalloc partials");
         CK(cudaMalloc(&w.part_misc, 4096 * sizeof(double)), "cudaMalloc partials");
         w.ready = true;
@@ -415,7 +444,7 @@ int enqueue_eval(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, d
     if (a.frozen) CK(cudaMemcpyAsync(w.knots_d, f->knots, M * sizeof(double), cudaMemcpyHostToDevice, g->stream),
                      "upload knots");
     ProfHook hook{prof_record, g};
-    CK(launch_eval<T>(a, g->stream, g->prof_on ? &hook : nullptr), "evaluation kernels");
+    CK(launch_eval<T>(a, w.ks, g->stream, g->prof_on ? &hook : nullptr), "evaluation kernels");
     return OFDFT_OK;
 }
 
@@ -451,7 +480,7 @@ template <typename T> int forces_impl(ofdft_grid *g, const T *rho, double *F) {
     a.tw0 = w.tw[0]; a.tw1 = w.tw[1]; a.tw2 = w.tw[2];
     a.Brow = w.Brow; a.thr_rowf = w.thr_rowf; a.TW1 = w.TW1; a.thr_p1 = w.thr_p1;
     a.nfwd = 1; a.fwd_ch[0] = CH_HPP; a.ncol = 1; a.col_ch[0] = CH_HPP;
-    CK(launch_forward_rows_cols<T>(a, g->stream), "forward transform");
+    CK(launch_forward_rows_cols<T>(a, w.ks, g->stream), "forward transform");
     CK(launch_axis0_fft<T>(w.chan, g->n[0], (long long)g->n[1] * g->n2h, g->plan[0], w.tw[0], w.TW0, w.thr_ax0,
                            1.0 / (double)g->N, g->stream),
        "forward transform along n0");
@@ -683,11 +712,6 @@ int ofdft_grid_create(const double cell[9], const int shape[3], void *cuda_strea
     const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
                        A[2] * (A[3] * A[7] - A[4] * A[6]);
     if (!(std::fabs(det) > 1e-12)) return OFDFT_ERR_INVALID_ARG;
-    static bool tables = false;
-    if (!tables) {
-        if (upload_gnl_tables() != cudaSuccess) return OFDFT_ERR_CUDA;
-        tables = true;
-    }
     ofdft_grid *g = new (std::nothrow) ofdft_grid();
     if (!g) return OFDFT_ERR_OOM;
     for (int a = 0; a < 3; a++) g->n[a] = shape[a];

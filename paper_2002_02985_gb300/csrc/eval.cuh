@@ -81,15 +81,50 @@ struct ProfHook {
     void *ctx;
 };
 
-template <typename T> cudaError_t launch_eval(const EvalArgs<T> &a, cudaStream_t s, const ProfHook *prof = nullptr);
-// stats + knots + row_fwd + forward pencil along n1 only (the channels of a.fwd_ch / a.col_ch)
-template <typename T> cudaError_t launch_forward_rows_cols(const EvalArgs<T> &a, cudaStream_t s);
-template <typename T> size_t row_fwd_smem(const EvalArgs<T> &a);
-template <typename T> size_t row_inv_smem(const EvalArgs<T> &a);
-template <typename T> size_t pencil_smem(int n, int TW);
-template <typename T> size_t axis0_smem(int n, int TW);
+// Dynamic shared memory of the FFT-carrying kernels (tile layouts in kernels.cuh).
+template <typename T> __host__ __device__ inline size_t row_fwd_smem_bytes(int n2, int B) {
+    typedef typename Vec2<T>::type C;
+    const size_t P = (size_t)2 * B * (n2 + 1);
+    return n2 * sizeof(C) + (size_t)n2 * (B + 1) * sizeof(C) + P * (4 * sizeof(T) + 1) + 16;
+}
 
-// series tables of the Lindhard kernel (set once per process)
-cudaError_t upload_gnl_tables();
+template <typename T> __host__ __device__ inline size_t pencil_smem_bytes(int n, int TW) {
+    typedef typename Vec2<T>::type C;
+    return (size_t)n * sizeof(C) + (size_t)n * TW * sizeof(C);
+}
+
+template <typename T> __host__ __device__ inline size_t axis0_smem_bytes(int n, int TW) {
+    typedef typename Vec2<T>::type C;
+    return (size_t)n * sizeof(C) + 3 * (size_t)n * TW * sizeof(C) + (size_t)n * TW * sizeof(T) + 16;
+}
+
+template <typename T> __host__ __device__ inline size_t row_inv_smem_bytes(int n2, int B) {
+    typedef typename Vec2<T>::type C;
+    const size_t P = (size_t)2 * B * (n2 + 1);
+    return n2 * sizeof(C) + (size_t)n2 * (B + 1) * sizeof(C) + P * (6 * sizeof(T) + 1) + 16;
+}
+
+// The five FFT-carrying kernels of one evaluation (generic or size-specialised).
+struct LaunchSet {
+    const void *row_fwd = nullptr, *row_inv = nullptr;   // depend on n2
+    const void *pen_fwd = nullptr, *pen_inv = nullptr;   // depend on n1
+    const void *axis0 = nullptr;                         // depends on n0
+};
+
+// role of a kernel family for the size registry
+enum { ROLE_ROW = 0, ROLE_PENCIL = 1, ROLE_AXIS0 = 2 };
+
+// Size-specialised kernels of a role for size n, with their fixed batch (B or
+// TW) and block size; false when none is compiled for that size/precision.
+template <typename T> bool find_specialised(int role, int n, const void **k1, const void **k2, int *B, int *nt);
+// The generic (runtime-size) kernels.
+template <typename T> LaunchSet generic_kernels();
+// Let every kernel of the set use the device's full opt-in shared memory.
+cudaError_t prepare_kernels(const LaunchSet &ks);
+
+template <typename T> cudaError_t launch_eval(const EvalArgs<T> &a, const LaunchSet &ks, cudaStream_t s,
+                                              const ProfHook *prof = nullptr);
+// stats + knots + row_fwd + forward pencil along n1 only (the channels of a.fwd_ch / a.col_ch)
+template <typename T> cudaError_t launch_forward_rows_cols(const EvalArgs<T> &a, const LaunchSet &ks, cudaStream_t s);
 
 }  // namespace ofdft

@@ -155,4 +155,96 @@ __device__ __noinline__ void fft_smem(C *buf, int ld, int B, const FFTPlan &p, c
     }
 }
 
+
+// ======================================================================
+// Compile-time variant: length N, batch B (sequence stride 1, batch index
+// innermost with element stride LD) and block size NT are template
+// parameters, so every index, loop bound and twiddle stride is a constant.
+// The radix sequence is the host plan's: 8s first, then a 4 or 2, then 5s,
+// then 3s.
+namespace ct {
+
+constexpr int npass(int n) {
+    int c = 0, m = n, p2 = 0;
+    while (m % 2 == 0) { m /= 2; p2++; }
+    c += p2 / 3 + (p2 % 3 ? 1 : 0);
+    while (m % 5 == 0) { m /= 5; c++; }
+    while (m % 3 == 0) { m /= 3; c++; }
+    return c;
+}
+
+constexpr int radix(int n, int p) {
+    int m = n, p2 = 0;
+    while (m % 2 == 0) { m /= 2; p2++; }
+    int r8 = p2 / 3, rem = p2 % 3;
+    if (p < r8) return 8;
+    p -= r8;
+    if (rem) {
+        if (p == 0) return rem == 2 ? 4 : 2;
+        p -= 1;
+    }
+    int n5 = 0;
+    while (m % 5 == 0) { m /= 5; n5++; }
+    if (p < n5) return 5;
+    return 3;
+}
+
+constexpr int ns(int n, int p) {
+    int s = 1;
+    for (int q = 0; q < p; q++) s *= radix(n, q);
+    return s;
+}
+
+template <int DIR, int R, int N, int NS, int B, int LD, int NT, typename C>
+__device__ __forceinline__ void pass(C *buf, const C *tw) {
+    constexpr int NB = N / R, TOT = NB * B, Q = (TOT + NT - 1) / NT, STRIDE = N / (NS * R);
+    C v[Q][R];
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+        const int idx = threadIdx.x + q * NT;
+        if (TOT % NT == 0 || idx < TOT) {
+            const int b = idx % B, j = idx / B, k = j % NS;
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                C x = buf[(j + r * NB) * LD + b];
+                if (NS > 1 && r > 0) {
+                    C w = tw[r * k * STRIDE];
+                    if (DIR > 0) w.y = -w.y;
+                    x = cmul(x, w);
+                }
+                v[q][r] = x;
+            }
+            dft<DIR, R>(v[q]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+        const int idx = threadIdx.x + q * NT;
+        if (TOT % NT == 0 || idx < TOT) {
+            const int b = idx % B, j = idx / B, k = j % NS;
+            const int dst = (j / NS) * NS * R + k;
+#pragma unroll
+            for (int r = 0; r < R; r++) buf[(dst + r * NS) * LD + b] = v[q][r];
+        }
+    }
+    __syncthreads();
+}
+
+template <int DIR, int N, int B, int LD, int NT, int P, typename C>
+__device__ __forceinline__ void passes(C *buf, const C *tw) {
+    if constexpr (P < npass(N)) {
+        pass<DIR, radix(N, P), N, ns(N, P), B, LD, NT>(buf, tw);
+        passes<DIR, N, B, LD, NT, P + 1>(buf, tw);
+    }
+}
+
+// B sequences of length N in buf (element e of sequence b at buf[e*LD + b]);
+// the caller synchronises before the call.
+template <int DIR, int N, int B, int LD, int NT, typename C>
+__device__ __forceinline__ void fft(C *buf, const C *tw) {
+    passes<DIR, N, B, LD, NT, 0>(buf, tw);
+}
+
+}  // namespace ct
 }  // namespace ofdft

@@ -1,0 +1,34 @@
+// Size-specialised instantiations of the FFT-carrying kernels.
+//
+// OFDFT_SPECIALISE(T, N, RB, RNT, PTW, PNT, ATW, ANT) registers, for axis
+// length N: the row kernels with RB row pairs per block (batch stride RB + 1)
+// and RNT threads, the n1 pencil kernels with PTW columns and PNT threads, and
+// the axis-0 kernel with ATW columns and ANT threads.  Each thread stages at
+// most ceil((N/R) * batch / threads) butterflies per pass.
+#pragma once
+
+#include "kernels.cuh"
+
+#define OFDFT_SPECIALISE(T, N, RB, RNT, PTW, PNT, ATW, ANT)                                   \
+    if (n == N) {                                                                             \
+        typedef ::ofdft::CtPolicy<T, N, RB, RB + 1, RNT> PR;                                  \
+        typedef ::ofdft::CtPolicy<T, N, PTW, PTW, PNT> PP;                                    \
+        typedef ::ofdft::CtPolicy<T, N, ATW, ATW, ANT> PA;                                    \
+        if (role == ROLE_ROW) {                                                               \
+            *k1 = (const void *)row_fwd_kernel<T, PR>;                                        \
+            *k2 = (const void *)row_inv_kernel<T, PR>;                                        \
+            *B = RB;                                                                          \
+            *nt = RNT;                                                                        \
+        } else if (role == ROLE_PENCIL) {                                                     \
+            *k1 = (const void *)pencil1_kernel<T, -1, PP>;                                    \
+            *k2 = (const void *)pencil1_kernel<T, +1, PP>;                                    \
+            *B = PTW;                                                                         \
+            *nt = PNT;                                                                        \
+        } else {                                                                              \
+            *k1 = (const void *)axis0_kernel<T, PA>;                                          \
+            *k2 = nullptr;                                                                    \
+            *B = ATW;                                                                         \
+            *nt = ANT;                                                                        \
+        }                                                                                     \
+        return true;                                                                          \
+    }

@@ -1,0 +1,648 @@
+// Kernel templates of one energy/potential evaluation (pipeline in eval.cuh).
+//
+// Every FFT-carrying kernel is written once against an FFT policy P:
+//   RtPolicy<T, AX>              sizes, batch and plan read from EvalArgs (any 2^a3^b5^c)
+//   CtPolicy<T, N, B, LD, NT>    size, batch, batch stride and block size fixed at
+//                                compile time (specialised instantiations)
+// so the physics is shared and only the transform is specialised.
+#pragma once
+
+#include "eval.cuh"
+
+namespace ofdft {
+
+// ======================================================================= policies
+template <typename T, int AX> struct RtPolicy {
+    typedef typename Vec2<T>::type C;
+    __device__ static int n(const EvalArgs<T> &a) { return AX == 0 ? a.n0 : (AX == 1 ? a.n1 : a.n2); }
+    __device__ static int B(const EvalArgs<T> &a) { return AX == 0 ? a.TW0 : (AX == 1 ? a.TW1 : a.Brow); }
+    __device__ static int ld(const EvalArgs<T> &a) { return AX == 2 ? a.Brow + 1 : B(a); }
+    __device__ static int nt() { return blockDim.x; }
+    template <int DIR> __device__ static void fft(C *buf, const EvalArgs<T> &a, const C *tw) {
+        fft_smem<DIR, Cap<T>::value>(buf, ld(a), B(a), AX == 0 ? a.p0 : (AX == 1 ? a.p1 : a.p2), tw);
+    }
+};
+
+template <typename T, int N, int B_, int LD_, int NT_> struct CtPolicy {
+    typedef typename Vec2<T>::type C;
+    __device__ static constexpr int n(const EvalArgs<T> &) { return N; }
+    __device__ static constexpr int B(const EvalArgs<T> &) { return B_; }
+    __device__ static constexpr int ld(const EvalArgs<T> &) { return LD_; }
+    __device__ static constexpr int nt() { return NT_; }
+    template <int DIR> __device__ static void fft(C *buf, const EvalArgs<T> &, const C *tw) {
+        ct::fft<DIR, N, B_, LD_, NT_>(buf, tw);
+    }
+};
+
+// ======================================================================= G_NL
+// Lindhard-derived WT kernel (Sec. 2.3, the G_NL definition below Eq. MGP):
+//   G_NL(eta) = 1/F(eta) - 3 eta^2 - 1,
+//   F(eta)    = 1/2 + (1 - eta^2)/(4 eta) ln|(1+eta)/(1-eta)|.
+// Below eta = 1/2 and above eta = 2 the exact series of F in y = eta^2
+// (resp. x = 1/eta^2) are summed, with the numerator 1 - (1 + 3 eta^2) F
+// expanded term by term so that nothing cancels (a_m = 1/(4 m^2 - 1)):
+//   eta < 1/2:  F = 1 - sum_m a_m y^m,   num = -(8/3) y + sum_{m>=2} (a_m + 3 a_{m-1}) y^m
+//   eta > 2  :  F = sum_m a_m x^m,       num = -sum_{m>=1} (a_m + 3 a_{m+1}) x^m
+// and G_NL = num / F.  The loops are unrolled, so every coefficient folds to
+// a constant.
+template <typename T> struct GnlTerms { static constexpr int value = 12; };
+template <> struct GnlTerms<double> { static constexpr int value = 28; };
+
+template <typename T> __device__ __forceinline__ T gnl(T eta) {
+    constexpr int nt = GnlTerms<T>::value;
+    if (eta < (T)0.5) {
+        const T y = eta * eta;
+        T sF = 0, sN = 0;
+#pragma unroll
+        for (int m = nt; m >= 1; m--) {
+            const double am = 1.0 / (4.0 * m * m - 1.0);
+            const double lo = (m >= 2) ? am + 3.0 / (4.0 * (m - 1) * (m - 1) - 1.0) : -8.0 / 3.0;
+            sF = (sF + (T)am) * y;
+            sN = (sN + (T)lo) * y;
+        }
+        return sN / ((T)1 - sF);
+    } else if (eta > (T)2) {
+        const T x = (T)1 / (eta * eta);
+        T sF = 0, sN = 0;
+#pragma unroll
+        for (int m = nt; m >= 1; m--) {
+            const double am = 1.0 / (4.0 * m * m - 1.0);
+            const double hi = am + 3.0 / (4.0 * (m + 1) * (m + 1) - 1.0);
+            sF = (sF + (T)am) * x;
+            sN = (sN + (T)hi) * x;
+        }
+        return -sN / sF;
+    }
+    const T d = (T)1 - eta;
+    if (dabs(d) < (T)1e-12) return (T)-2;
+    const T F = (T)0.5 + ((T)1 - eta * eta) / ((T)4 * eta) * dlog(dabs(((T)1 + eta) / d));
+    return (T)1 / F - (T)3 * eta * eta - (T)1;
+}
+
+// ======================================================================= helpers
+template <typename T> __device__ __forceinline__ int knot_interval(T kc, const T *knots, int M) {
+    // largest j in [0, M-2] with knots[j] <= kc (binary search; kc already clamped)
+    int lo = 0, hi = M - 2;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (knots[mid] <= kc) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ======================================================================= stats (s1 input)
+template <typename T>
+__global__ void __launch_bounds__(256) stats_kernel(EvalArgs<T> a) {
+    __shared__ double sd[32];
+    __shared__ T st[32];
+    double s_rho = 0.0, s_tf = 0.0;
+    T mn = (T)3.0e38, mx = (T)-3.0e38;
+    int bad = 0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.N; i += stride) {
+        const T x = a.rho[i];
+        if (!(x >= (T)0) || !(x < (T)3.0e38)) bad = 1;      // NaN, Inf or negative
+        s_rho += (double)x;
+        const T c = dcbrt(x);
+        s_tf += (double)(x * c * c);                       // rho^(5/3)
+        mn = x < mn ? x : mn;
+        mx = x > mx ? x : mx;
+    }
+    s_rho = block_sum(s_rho, sd);
+    if (threadIdx.x == 0) a.part_stats[2 * blockIdx.x] = s_rho;
+    s_tf = block_sum(s_tf, sd);
+    if (threadIdx.x == 0) a.part_stats[2 * blockIdx.x + 1] = s_tf;
+    mn = block_min(mn, st);
+    if (threadIdx.x == 0) a.part_minmax[2 * blockIdx.x] = mn;
+    mx = block_max(mx, st);
+    if (threadIdx.x == 0) a.part_minmax[2 * blockIdx.x + 1] = mx;
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0 && bad) a.scal[S_BAD] = 1.0;
+}
+
+// ======================================================================= knots (s1)
+template <typename T>
+__global__ void __launch_bounds__(256) knots_kernel(EvalArgs<T> a) {
+    __shared__ double sd[32];
+    __shared__ T st[32];
+    double s_rho = 0.0, s_tf = 0.0;
+    T mn = (T)3.0e38, mx = (T)-3.0e38;
+    for (int b = threadIdx.x; b < a.nb_stats; b += blockDim.x) {
+        s_rho += a.part_stats[2 * b];
+        s_tf += a.part_stats[2 * b + 1];
+        const T x = a.part_minmax[2 * b], y = a.part_minmax[2 * b + 1];
+        mn = x < mn ? x : mn;
+        mx = y > mx ? y : mx;
+    }
+    s_rho = block_sum(s_rho, sd);
+    s_tf = block_sum(s_tf, sd);
+    mn = block_min(mn, st);
+    mx = block_max(mx, st);
+    if (threadIdx.x != 0) return;
+    const double fl = (double)a.floor_;
+    a.scal[S_SUM_RHO] = s_rho;
+    a.scal[S_SUM_TF] = s_tf;
+    a.scal[S_RHO_MIN] = (double)mn;
+    a.scal[S_RHO_MAX] = (double)mx;
+    const double mean = s_rho / (double)a.N;
+    a.scal[S_RHO_MEAN] = mean;
+    a.scal[S_KF_WT] = cbrt(kThreePi2 * (mean > fl ? mean : fl));
+    a.energies[E_TF] = (a.terms & 1u) ? kCTF * s_tf * a.dV : 0.0;
+    const int M = a.M;
+    if (!(a.terms & 4u) || a.kernel != 0 || M < 2) return;
+    if (!a.frozen) {
+        // s1: knots between kF(min rho) and kF(max rho), FP64
+        const double rmin = (double)mn > fl ? (double)mn : fl, rmax = (double)mx > fl ? (double)mx : fl;
+        const double kmin = cbrt(kThreePi2 * rmin), kmax = cbrt(kThreePi2 * rmax);
+        for (int m = 0; m < M; m++) {
+            double k;
+            if (a.knot_spacing == 0) k = kmin * exp((double)m * (log(kmax / kmin) / (double)(M - 1)));
+            else k = kmin + (double)m * ((kmax - kmin) / (double)(M - 1));
+            a.knots_d[m] = k;
+        }
+        a.knots_d[0] = kmin;
+        a.knots_d[M - 1] = kmax;
+    }
+    for (int m = 0; m < M; m++) a.knots_t[m] = (T)a.knots_d[m];
+    for (int m = 0; m + 1 < M; m++) {
+        const double dk = a.knots_d[m + 1] - a.knots_d[m];
+        a.invdk_t[m] = dk > 0.0 ? (T)(1.0 / dk) : (T)0;
+    }
+}
+
+// ======================================================================= row forward (R2C along n2)
+// Tile: B pairs of consecutive rows (flattened row r = i0*n1 + i1); pair p holds
+// rows 2p and 2p+1, packed as z = x_2p + i x_2p+1 for one complex FFT of length n2.
+
+template <typename T, class P>
+__device__ __forceinline__ void row_fwd_body(const EvalArgs<T> &a) {
+    typedef typename Vec2<T>::type C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = P::n(a), B = P::B(a), ld = P::ld(a), pl = n + 1, NT = P::nt();
+    const int n2h = n / 2 + 1;
+    const int PP = 2 * B * pl;
+    C *tw = (C *)smem_raw;
+    C *buf = tw + n;
+    T *sx = (T *)(buf + (size_t)n * ld);
+    T *sra = sx + PP;
+    T *srb = sra + PP;
+    T *st = srb + PP;
+    unsigned char *sj = (unsigned char *)(st + PP);
+    __shared__ T sk[OFDFT_MAX_KNOTS];
+
+    const long long R = (long long)a.n0 * a.n1;
+    const long long row0 = 2LL * B * blockIdx.x;
+    for (int i = threadIdx.x; i < n; i += NT) tw[i] = a.tw2[i];
+    const bool lwt = (a.terms & 4u) && a.kernel == 0;
+    const int M = a.M;
+    if (lwt)
+        for (int i = threadIdx.x; i < M; i += NT) sk[i] = a.knots_t[i];
+    const T mean = (T)a.scal[S_RHO_MEAN];
+    __syncthreads();
+    // per-point quantities of the 2B rows of the tile
+    for (int idx = threadIdx.x; idx < 2 * B * n; idx += NT) {
+        const int rr = idx / n, i2 = idx - rr * n;
+        const long long row = row0 + rr;
+        const int o = rr * pl + i2;
+        T x = 0;
+        if (row < R) x = a.rho[row * n + i2];
+        sx[o] = x;
+        if (a.terms & 4u) {
+            const T xf = x > a.floor_ ? x : a.floor_;
+            const T ra = dpow(xf, a.alpha);
+            sra[o] = ra;
+            srb[o] = (a.beta == a.alpha) ? ra : dpow(xf, a.beta);
+            if (lwt) {
+                T kf = dcbrt((T)kThreePi2 * xf);
+                kf = kf < sk[0] ? sk[0] : (kf > sk[M - 1] ? sk[M - 1] : kf);
+                const int j = knot_interval(kf, sk, M);
+                sj[o] = (unsigned char)j;
+                st[o] = (kf - sk[j]) * a.invdk_t[j];
+            }
+        }
+    }
+    __syncthreads();
+    for (int ci = 0; ci < a.nfwd; ci++) {
+        const int ch = a.fwd_ch[ci];
+        for (int idx = threadIdx.x; idx < n * B; idx += NT) {
+            const int b = idx % B, i2 = idx / B;
+            T v[2];
+#pragma unroll
+            for (int s = 0; s < 2; s++) {
+                const int o = (2 * b + s) * pl + i2;
+                T f;
+                if (ch == CH_HPP) f = sx[o] - mean;
+                else if (ch == CH_VW) f = dsqrt(sx[o] > (T)0 ? sx[o] : (T)0);
+                else if (ch == CH_NL) f = srb[o];
+                else if (!lwt) f = sra[o];                         // WT: rho^alpha field
+                else {
+                    const int m = ch - CH_KNOT0, j = sj[o];
+                    const T t = st[o];
+                    f = (j == m) ? ((T)1 - t) * sra[o] : ((j == m - 1) ? t * sra[o] : (T)0);
+                }
+                if (row0 + 2 * b + s >= R) f = 0;
+                v[s] = f;
+            }
+            buf[i2 * ld + b] = cmake<C>(v[0], v[1]);
+        }
+        __syncthreads();
+        P::template fft<-1>(buf, a, tw);
+        // unpack X_2p[k] = (Z_k + conj Z_{n-k})/2, X_2p+1[k] = (Z_k - conj Z_{n-k})/(2i)
+        C *out = a.chan + (size_t)ch * a.NH;
+        for (int idx = threadIdx.x; idx < n2h * B; idx += NT) {
+            const int b = idx / n2h, k = idx - b * n2h;
+            const C A = buf[k * ld + b];
+            const C Bv = buf[((n - k) % n) * ld + b];
+            const long long r0 = row0 + 2 * b;
+            if (r0 < R) out[r0 * n2h + k] = cmake<C>((T)0.5 * (A.x + Bv.x), (T)0.5 * (A.y - Bv.y));
+            if (r0 + 1 < R) out[(r0 + 1) * n2h + k] = cmake<C>((T)0.5 * (A.y + Bv.y), (T)0.5 * (Bv.x - A.x));
+        }
+        __syncthreads();
+    }
+}
+
+// ======================================================================= pencil (C2C along n1)
+
+// blockIdx.x: tile of TW consecutive k2, blockIdx.y: i0, blockIdx.z: channel list entry
+template <typename T, int DIR, class P>
+__device__ __forceinline__ void pencil1_body(const EvalArgs<T> &a) {
+    typedef typename Vec2<T>::type C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = P::n(a), TW = P::B(a), n2h = a.n2h, NT = P::nt();
+    C *tw = (C *)smem_raw;
+    C *buf = tw + n;
+    for (int i = threadIdx.x; i < n; i += NT) tw[i] = a.tw1[i];
+    const int ch = DIR < 0 ? a.col_ch[blockIdx.z] : a.col_inv_ch[blockIdx.z];
+    C *base = a.chan + (size_t)ch * a.NH + (size_t)blockIdx.y * n * n2h;
+    const int c0 = blockIdx.x * TW;
+    for (int idx = threadIdx.x; idx < n * TW; idx += NT) {
+        const int w = idx % TW, i = idx / TW;
+        buf[idx] = (c0 + w < n2h) ? base[(size_t)i * n2h + c0 + w] : cmake<C>((T)0, (T)0);
+    }
+    __syncthreads();
+    P::template fft<DIR>(buf, a, tw);
+    for (int idx = threadIdx.x; idx < n * TW; idx += NT) {
+        const int w = idx % TW, i = idx / TW;
+        if (c0 + w < n2h) base[(size_t)i * n2h + c0 + w] = buf[idx];
+    }
+}
+
+// ======================================================================= axis 0 + reciprocal space
+
+// Partials per block: [0] sum_G w |rho_hat|^2/G^2, [1] sum_G w G^2 |psi_hat|^2,
+// [2] sum_G w Re(conj(rho_hat) V_ext), [3] nonlocal energy in G space.
+template <typename T, class P>
+__device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
+    typedef typename Vec2<T>::type C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double sd[32];
+    __shared__ double cvec[64][3];
+    __shared__ float cw[64];
+    __shared__ T sk[OFDFT_MAX_KNOTS];
+    const int n = P::n(a), TW = P::B(a), n2h = a.n2h, NT = P::nt();
+    const long long PL = (long long)a.n1 * n2h;      // columns per plane
+    const int NTILE = n * TW;
+    C *tw = (C *)smem_raw;
+    C *S = tw + n;
+    C *Rr = S + NTILE;
+    C *A = Rr + NTILE;
+    T *gn = (T *)(A + NTILE);
+    for (int i = threadIdx.x; i < n; i += NT) tw[i] = a.tw0[i];
+    const long long c0 = (long long)blockIdx.x * TW;
+    // per column (k1, k2): its part of the G vector and its half-spectrum weight
+    for (int w = threadIdx.x; w < TW; w += NT) {
+        const long long col = c0 + w;
+        const int k1 = (int)(col / n2h), k2 = (int)(col % n2h);
+        const double m1 = (k1 <= a.n1 / 2) ? k1 : k1 - a.n1, m2 = k2;
+        for (int d = 0; d < 3; d++) cvec[w][d] = m1 * a.bvec[3 + d] + m2 * a.bvec[6 + d];
+        cw[w] = (col < PL) ? ((k2 == 0 || (a.n2 % 2 == 0 && k2 == a.n2 / 2)) ? 1.f : 2.f) : 0.f;
+    }
+    const bool lwt = a.kernel == 0;
+    if ((a.terms & 4u) && lwt)
+        for (int i = threadIdx.x; i < a.M; i += NT) sk[i] = a.knots_t[i];
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
+        const int w = idx % TW, i = idx / TW;
+        const double m0 = (i <= n / 2) ? i : i - n;
+        const double gx = cvec[w][0] + m0 * a.bvec[0];
+        const double gy = cvec[w][1] + m0 * a.bvec[1];
+        const double gz = cvec[w][2] + m0 * a.bvec[2];
+        gn[idx] = (T)sqrt(gx * gx + gy * gy + gz * gz);
+    }
+    const T invN = (T)(1.0 / (double)a.N);
+    double eH = 0.0, eV = 0.0, eP = 0.0, eN = 0.0;
+
+    auto load = [&](C *dst, int ch) {
+        const C *src = a.chan + (size_t)ch * a.NH;
+        for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
+            const int w = idx % TW, i = idx / TW;
+            dst[idx] = (c0 + w < PL) ? src[(size_t)i * PL + c0 + w] : cmake<C>((T)0, (T)0);
+        }
+    };
+    auto store = [&](const C *srcb, int ch) {
+        C *dst = a.chan + (size_t)ch * a.NH;
+        for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
+            const int w = idx % TW, i = idx / TW;
+            if (c0 + w < PL) dst[(size_t)i * PL + c0 + w] = srcb[idx];
+        }
+    };
+
+    // ---- Hartree + local pseudopotential
+    if (a.terms & (8u | 16u)) {
+        load(S, CH_HPP);
+        __syncthreads();
+        P::template fft<-1>(S, a, tw);
+        for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
+            const int w = idx % TW, i = idx / TW;
+            const long long col = c0 + w;
+            const C X = cscale(S[idx], invN);
+            const T g = gn[idx];
+            const T g2 = g * g;
+            C out = cmake<C>((T)0, (T)0);
+            if (col < PL && g2 > (T)0) {
+                const double wgt = cw[w];
+                if (a.terms & 8u) {
+                    const T f = (T)(4.0 * kPi) / g2;
+                    eH += wgt * ((double)X.x * X.x + (double)X.y * X.y) / (double)g2;
+                    out = cscale(X, f);
+                }
+                if (a.terms & 16u) {
+                    const C v = a.vext[(size_t)i * PL + col];
+                    eP += wgt * ((double)X.x * v.x + (double)X.y * v.y);
+                    out = cadd(out, v);
+                }
+            } else if (col < PL && (a.terms & 16u)) {
+                out = a.vext[(size_t)i * PL + col];       // G = 0: V_ext(0) only
+            }
+            S[idx] = out;
+        }
+        __syncthreads();
+        P::template fft<+1>(S, a, tw);
+        store(S, CH_HPP);
+        __syncthreads();
+    }
+    // ---- von Weizsaecker (psi form)
+    if (a.terms & 2u) {
+        load(S, CH_VW);
+        __syncthreads();
+        P::template fft<-1>(S, a, tw);
+        for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
+            const int w = idx % TW;
+            const C X = cscale(S[idx], invN);
+            const T g = gn[idx];
+            const T g2 = g * g;
+            eV += (double)cw[w] * (double)g2 * ((double)X.x * X.x + (double)X.y * X.y);
+            S[idx] = cscale(X, g2);
+        }
+        __syncthreads();
+        P::template fft<+1>(S, a, tw);
+        store(S, CH_VW);
+        __syncthreads();
+    }
+    // ---- nonlocal: s2 (kernel at each knot) and the reciprocal half of s3
+    if (a.terms & 4u) {
+        load(Rr, CH_NL);
+        __syncthreads();
+        P::template fft<-1>(Rr, a, tw);
+        for (int idx = threadIdx.x; idx < NTILE; idx += NT) Rr[idx] = cscale(Rr[idx], invN);
+        __syncthreads();
+        if (!lwt) {
+            // global-kF Wang-Teter: K * rho^beta into CH_NL, K * rho^alpha into CH_KNOT0;
+            // E = Omega sum_G w Re(conj(FFT[rho^alpha]) K FFT[rho^beta])
+            const T hk = (T)(0.5 / a.scal[S_KF_WT]);
+            load(S, CH_KNOT0);
+            __syncthreads();
+            P::template fft<-1>(S, a, tw);
+            for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
+                const int w = idx % TW;
+                const T K = (T)kCWT * gnl(gn[idx] * hk);
+                const C Sa = cscale(S[idx], invN);
+                const C Rb = Rr[idx];
+                eN += (double)cw[w] * (double)K * ((double)Sa.x * Rb.x + (double)Sa.y * Rb.y);
+                Rr[idx] = cscale(Rb, K);
+                S[idx] = cscale(Sa, K);
+            }
+            __syncthreads();
+            P::template fft<+1>(Rr, a, tw);
+            P::template fft<+1>(S, a, tw);
+            store(Rr, CH_NL);
+            store(S, CH_KNOT0);
+        } else {
+            const bool exact = a.nlpot == 0;
+            if (exact)
+                for (int idx = threadIdx.x; idx < NTILE; idx += NT) A[idx] = cmake<C>((T)0, (T)0);
+            for (int m = 0; m < a.M; m++) {
+                const T hk = (T)0.5 / sk[m];
+                if (exact) {
+                    load(S, CH_KNOT0 + m);
+                    __syncthreads();
+                    P::template fft<-1>(S, a, tw);
+                }
+                for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
+                    const T K = (T)kCWT * gnl(gn[idx] * hk);
+                    if (exact) {
+                        // E_NL += Omega sum_G w Re(conj(FFT[h_m rho^alpha]) K_m FFT[rho^beta])
+                        const C Sm = cscale(S[idx], invN);
+                        const C Rb = Rr[idx];
+                        eN += (double)cw[idx % TW] * (double)K * ((double)Sm.x * Rb.x + (double)Sm.y * Rb.y);
+                        A[idx] = cadd(A[idx], cscale(Sm, K));
+                    }
+                    S[idx] = cscale(Rr[idx], K);
+                }
+                __syncthreads();
+                P::template fft<+1>(S, a, tw);
+                store(S, CH_KNOT0 + m);
+                __syncthreads();
+            }
+            if (exact) {
+                P::template fft<+1>(A, a, tw);
+                store(A, CH_NL);
+            }
+        }
+    }
+    eH = block_sum(eH, sd);
+    if (threadIdx.x == 0) a.part_ax0[4 * blockIdx.x] = eH;
+    eV = block_sum(eV, sd);
+    if (threadIdx.x == 0) a.part_ax0[4 * blockIdx.x + 1] = eV;
+    eP = block_sum(eP, sd);
+    if (threadIdx.x == 0) a.part_ax0[4 * blockIdx.x + 2] = eP;
+    eN = block_sum(eN, sd);
+    if (threadIdx.x == 0) a.part_ax0[4 * blockIdx.x + 3] = eN;
+}
+
+// ======================================================================= row inverse (C2R along n2) + s4 + V
+
+template <typename T, class P>
+__device__ __forceinline__ void row_inv_body(const EvalArgs<T> &a) {
+    typedef typename Vec2<T>::type C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double sd[32];
+    __shared__ T sk[OFDFT_MAX_KNOTS];
+    __shared__ T sidk[OFDFT_MAX_KNOTS];
+    const int n = P::n(a), B = P::B(a), ld = P::ld(a), pl = n + 1, NT = P::nt();
+    const int n2h = n / 2 + 1;
+    const int PP = 2 * B * pl;
+    C *tw = (C *)smem_raw;
+    C *buf = tw + n;
+    T *sv = (T *)(buf + (size_t)n * ld);   // V accumulator
+    T *sa1 = sv + PP;                      // rho^(alpha-1)
+    T *sk3 = sa1 + PP;                     // exact: kF/3 inside the knot range (else 0); interp: rho^alpha
+    T *svw = sk3 + PP;                     // 1 / (2 max(psi, psi_floor))
+    T *sb1 = svw + PP;                     // rho^(beta-1)
+    T *st = sb1 + PP;                      // spline weight t
+    unsigned char *sj = (unsigned char *)(st + PP);
+
+    const long long R = (long long)a.n0 * a.n1;
+    const long long row0 = 2LL * B * blockIdx.x;
+    const bool lwt = (a.terms & 4u) && a.kernel == 0;
+    const bool interp = a.nlpot == 1;
+    const int M = a.M;
+    for (int i = threadIdx.x; i < n; i += NT) tw[i] = a.tw2[i];
+    if (lwt)
+        for (int i = threadIdx.x; i < M; i += NT) {
+            sk[i] = a.knots_t[i];
+            sidk[i] = (i + 1 < M) ? a.invdk_t[i] : (T)0;
+        }
+    __syncthreads();
+    const T psi_floor = dsqrt(a.floor_);
+    for (int idx = threadIdx.x; idx < 2 * B * n; idx += NT) {
+        const int rr = idx / n, i2 = idx - rr * n;
+        const long long row = row0 + rr;
+        const int o = rr * pl + i2;
+        T x = 0;
+        if (row < R) x = a.rho[row * n + i2];
+        T v = 0;
+        const T xp = x > (T)0 ? x : (T)0;
+        if (a.terms & 1u) {
+            const T c = dcbrt(xp);
+            v = (T)(5.0 / 3.0 * kCTF) * c * c;          // V_TF = (5/3) C_TF rho^(2/3)
+        }
+        sv[o] = v;
+        const T p = dsqrt(xp);
+        svw[o] = (T)1 / ((T)2 * (p > psi_floor ? p : psi_floor));
+        if (a.terms & 4u) {
+            const T xf = x > a.floor_ ? x : a.floor_;
+            const T ra = dpow(xf, a.alpha);
+            const T rb = (a.beta == a.alpha) ? ra : dpow(xf, a.beta);
+            sa1[o] = ra / xf;
+            sb1[o] = rb / xf;
+            if (lwt) {
+                const T kf = dcbrt((T)kThreePi2 * xf);
+                const bool inside = kf >= sk[0] && kf <= sk[M - 1];
+                const T kc = kf < sk[0] ? sk[0] : (kf > sk[M - 1] ? sk[M - 1] : kf);
+                const int j = knot_interval(kc, sk, M);
+                sj[o] = (unsigned char)j;
+                st[o] = (kc - sk[j]) * sidk[j];
+                sk3[o] = interp ? ra : (inside ? kf * (T)(1.0 / 3.0) : (T)0);
+            }
+        }
+    }
+    __syncthreads();
+    double eNL = 0.0;
+    const T alpha_eff = interp ? (T)2 * a.alpha : a.alpha;
+    for (int ci = 0; ci < a.ninv; ci++) {
+        const int ch = a.inv_ch[ci], kind = a.inv_kind[ci], m = a.inv_knot[ci];
+        const C *in = a.chan + (size_t)ch * a.NH;
+        // pack the pair of half spectra into one full complex spectrum
+        for (int idx = threadIdx.x; idx < n2h * B; idx += NT) {
+            const int b = idx / n2h, k = idx - b * n2h;
+            const long long r0 = row0 + 2 * b;
+            const C z = cmake<C>((T)0, (T)0);
+            const C X0 = (r0 < R) ? in[r0 * n2h + k] : z;
+            const C X1 = (r0 + 1 < R) ? in[(r0 + 1) * n2h + k] : z;
+            if (k == 0 || 2 * k == n) {
+                buf[k * ld + b] = cmake<C>(X0.x, X1.x);
+            } else {
+                buf[k * ld + b] = cmake<C>(X0.x - X1.y, X0.y + X1.x);
+                buf[(n - k) * ld + b] = cmake<C>(X0.x + X1.y, X1.x - X0.y);
+            }
+        }
+        __syncthreads();
+        P::template fft<+1>(buf, a, tw);
+        for (int idx = threadIdx.x; idx < n * B; idx += NT) {
+            const int b = idx % B, i2 = idx / B;
+            const C z = buf[i2 * ld + b];
+#pragma unroll
+            for (int s = 0; s < 2; s++) {
+                const int o = (2 * b + s) * pl + i2;
+                const T y = s ? z.y : z.x;
+                T acc = sv[o];
+                if (kind == CONS_ADD) acc += y;
+                else if (kind == CONS_VW) acc += y * svw[o];
+                else if (kind == CONS_T2 || kind == CONS_WT_B) acc += a.beta * sb1[o] * y;
+                else if (kind == CONS_WT_A) acc += a.alpha * sa1[o] * y;
+                else {
+                    const int j = sj[o];
+                    if (j == m || j + 1 == m) {
+                        const T t = st[o], idk = sidk[j];
+                        const T h = (j == m) ? (T)1 - t : t;
+                        if (interp) {
+                            acc += y * alpha_eff * sa1[o] * h;
+                            if (row0 + 2 * b + s < R) eNL += (double)(sk3[o] * h) * (double)y;
+                        } else {
+                            const T hp = (j == m) ? -idk : idk;
+                            acc += y * sa1[o] * (alpha_eff * h + sk3[o] * hp);
+                        }
+                    }
+                }
+                sv[o] = acc;
+            }
+        }
+        __syncthreads();
+    }
+    if (a.V) {
+        for (int idx = threadIdx.x; idx < 2 * B * n; idx += NT) {
+            const int rr = idx / n, i2 = idx - rr * n;
+            const long long row = row0 + rr;
+            if (row < R) a.V[row * n + i2] = sv[rr * pl + i2];
+        }
+    }
+    eNL = block_sum(eNL, sd);
+    if (threadIdx.x == 0) a.part_row[blockIdx.x] = eNL;
+}
+
+// ======================================================================= finalize
+template <typename T>
+__global__ void __launch_bounds__(256) finalize_kernel(EvalArgs<T> a) {
+    __shared__ double sd[32];
+    double h = 0.0, v = 0.0, p = 0.0, ng = 0.0, nl = 0.0;
+    for (int b = threadIdx.x; b < a.nb_ax0; b += blockDim.x) {
+        h += a.part_ax0[4 * b];
+        v += a.part_ax0[4 * b + 1];
+        p += a.part_ax0[4 * b + 2];
+        ng += a.part_ax0[4 * b + 3];
+    }
+    for (int b = threadIdx.x; b < a.nb_row; b += blockDim.x) nl += a.part_row[b];
+    h = block_sum(h, sd);
+    v = block_sum(v, sd);
+    p = block_sum(p, sd);
+    ng = block_sum(ng, sd);
+    nl = block_sum(nl, sd);
+    if (threadIdx.x != 0) return;
+    double *E = a.energies;
+    E[E_VW] = (a.terms & 2u) ? 0.5 * a.omega * v : 0.0;
+    E[E_H] = (a.terms & 8u) ? 2.0 * kPi * a.omega * h : 0.0;
+    if (a.terms & 16u) {
+        const double v0 = (double)a.vext[0].x;                    // V_ext(G = 0)
+        E[E_PP] = a.omega * (p + a.scal[S_RHO_MEAN] * v0);
+    } else {
+        E[E_PP] = 0.0;
+    }
+    // nonlocal: G-space sum (exact LWT, WT) or real-space sum (interpolated LWT)
+    const bool real_space = a.kernel == 0 && a.nlpot == 1;
+    E[E_NL] = (a.terms & 4u) ? (real_space ? nl * a.dV : a.omega * ng) : 0.0;
+    E[E_TOT] = E[E_TF] + E[E_VW] + E[E_NL] + E[E_H] + E[E_PP];
+}
+
+// ======================================================================= kernel wrappers
+template <typename T, class P>
+__global__ void __launch_bounds__(kMaxThreads) row_fwd_kernel(EvalArgs<T> a) { row_fwd_body<T, P>(a); }
+template <typename T, int DIR, class P>
+__global__ void __launch_bounds__(kMaxThreads) pencil1_kernel(EvalArgs<T> a) { pencil1_body<T, DIR, P>(a); }
+template <typename T, class P>
+__global__ void __launch_bounds__(kMaxThreads) axis0_kernel(EvalArgs<T> a) { axis0_body<T, P>(a); }
+template <typename T, class P>
+__global__ void __launch_bounds__(kMaxThreads) row_inv_kernel(EvalArgs<T> a) { row_inv_body<T, P>(a); }
+
+}  // namespace ofdft

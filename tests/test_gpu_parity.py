@@ -181,3 +181,51 @@ def test_repeated_runs_are_bit_identical():
         E1, V1 = g.energy_potential(rho, f)
         assert E1 == E0
         assert torch.equal(V0, V1)
+
+
+# ---------------------------------------------------------------- size-specialised kernels
+SPEC_SHAPES = [(128, 96, 64), (80, 120, 32), (192, 64, 96), (64, 192, 120)]
+
+
+@pytest.mark.parametrize("shape", SPEC_SHAPES)
+def test_fp32_specialised_sizes_match_oracle(shape):
+    """Every axis length here has compile-time kernels for its role (rows: n2,
+    pencils: n1, reciprocal pass: n0)."""
+    cell = np.diag([0.2 * n for n in shape])
+    rng = np.random.default_rng(sum(shape))
+    pos = rng.uniform(0, 1, (6, 3)) @ cell
+    rho = W.renormalise(W.apply_noise(W.gaussian_density(cell, shape, pos, 3.0, 1.0) + 2e-3, 0.03, 11), cell, 18.0)
+    E, V, Eo, Vo, og, _ = run_both(cell, shape, pos, rho, dict(n_knots=8), L.FP32_MIXED, Z=(3.0,), rc=(0.8,))
+    for k in ("TF", "vW", "NL", "H", "PP", "total"):
+        assert abs(E[k] - Eo[k]) / 6 <= 1e-6, (k, E[k], Eo[k])
+    m = knot_mask(rho.astype(np.float32).astype(np.float64), 8)
+    assert np.linalg.norm((V - Vo)[m]) / np.linalg.norm(Vo[m]) <= 1e-4
+
+
+def test_fp64_specialised_128_matches_oracle():
+    shape = (128, 32, 128)
+    cell = np.diag([0.2 * n for n in shape])
+    rng = np.random.default_rng(7)
+    pos = rng.uniform(0, 1, (4, 3)) @ cell
+    rho = W.renormalise(W.apply_noise(W.gaussian_density(cell, shape, pos, 3.0, 1.0) + 2e-3, 0.03, 12), cell, 12.0)
+    E, V, Eo, Vo, og, _ = run_both(cell, shape, pos, rho, dict(n_knots=6), L.FP64, Z=(3.0,), rc=(0.8,))
+    for k in ("TF", "vW", "NL", "H", "PP", "total"):
+        assert abs(E[k] - Eo[k]) <= 1e-10 * max(1.0, abs(Eo[k])), (k, E[k], Eo[k])
+    assert np.max(np.abs(V - Vo)) <= 1e-9 * max(1.0, np.max(np.abs(Vo)))
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(nl_potential=L.NLPOT_INTERP), dict(kernel=L.KERNEL_WT_GLOBAL)])
+def test_specialised_and_generic_kernels_agree(kw, monkeypatch):
+    wl = W.workload("fcc-al-256/128")
+    rho = torch.from_numpy(W.model_density(wl).astype(np.float32)).cuda()
+    f = ofd.Functional(n_knots=16, **kw)
+    out = []
+    for generic in ("0", "1"):
+        monkeypatch.setenv("OFDFT_FORCE_GENERIC", generic)
+        g = ofd.Grid(wl["cell"], wl["shape"])
+        g.set_ions(wl["positions"], wl["species"], wl["Z"], wl["rc"])
+        out.append(g.energy_potential(rho, f))
+    (E1, V1), (E2, V2) = out
+    for k in E1:
+        assert abs(E1[k] - E2[k]) <= 1e-9 * max(1.0, abs(E1[k])), (k, E1[k], E2[k])
+    assert torch.allclose(V1, V2, rtol=1e-5, atol=1e-5 * float(V1.abs().max()))
