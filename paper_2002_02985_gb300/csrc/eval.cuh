@@ -82,12 +82,20 @@ struct ProfHook {
 };
 
 // Dynamic shared memory of the FFT-carrying kernels (tile layouts in kernels.cuh).
+// row tiles: the complex FFT buffer (n x (B+1)) doubles as the density staging
+// area ([2B][pitch], pitch odd), so it is sized for the larger of the two
+__host__ __device__ inline int row_pitch(int n) { return n % 2 ? n + 2 : n + 1; }
+template <typename T> __host__ __device__ inline size_t row_buf_bytes(int n2, int B) {
+    const size_t fft = (size_t)n2 * (B + 1) * 2 * sizeof(T);
+    const size_t stg = (size_t)2 * B * row_pitch(n2) * sizeof(T);
+    const size_t m = fft > stg ? fft : stg;
+    return (m + 15) / 16 * 16;
+}
 template <typename T> __host__ __device__ inline size_t row_fwd_smem_bytes(int n2, int B) {
     typedef typename Vec2<T>::type C;
-    const size_t P = (size_t)2 * B * (n2 + 1);
-    return n2 * sizeof(C) + (size_t)n2 * (B + 1) * sizeof(C) + P * (4 * sizeof(T) + 1) + 16;
+    const size_t P = (size_t)2 * B * n2;
+    return n2 * sizeof(C) + row_buf_bytes<T>(n2, B) + P * (4 * sizeof(T) + 1) + 16;
 }
-
 template <typename T> __host__ __device__ inline size_t pencil_smem_bytes(int n, int TW) {
     typedef typename Vec2<T>::type C;
     return (size_t)n * sizeof(C) + (size_t)n * TW * sizeof(C);
@@ -100,8 +108,8 @@ template <typename T> __host__ __device__ inline size_t axis0_smem_bytes(int n, 
 
 template <typename T> __host__ __device__ inline size_t row_inv_smem_bytes(int n2, int B) {
     typedef typename Vec2<T>::type C;
-    const size_t P = (size_t)2 * B * (n2 + 1);
-    return n2 * sizeof(C) + (size_t)n2 * (B + 1) * sizeof(C) + P * (6 * sizeof(T) + 1) + 16;
+    const size_t P = (size_t)2 * B * n2;
+    return n2 * sizeof(C) + row_buf_bytes<T>(n2, B) + P * (6 * sizeof(T) + 1) + 16;
 }
 
 // The five FFT-carrying kernels of one evaluation (generic or size-specialised).

@@ -33,6 +33,10 @@ cudaError_t prepare_kernels(const LaunchSet &ks) {
     return cudaSuccess;
 }
 
+template <typename T> static unsigned pencil_tiles(const EvalArgs<T> &a) {
+    return (unsigned)(((long long)a.n0 * a.n2h + a.TW1 - 1) / a.TW1);
+}
+
 template <typename T>
 static cudaError_t launch(const void *k, dim3 g, int nt, size_t smem, const EvalArgs<T> &a, cudaStream_t s) {
     void *args[] = {(void *)&a};
@@ -62,8 +66,7 @@ cudaError_t launch_eval(const EvalArgs<T> &a, const LaunchSet &ks, cudaStream_t 
     }
     if (a.ncol > 0) {
         mark(K_PENCIL_FWD, 0);
-        e = launch(ks.pen_fwd, dim3((a.n2h + a.TW1 - 1) / a.TW1, a.n0, a.ncol), a.thr_p1,
-                   pencil_smem_bytes<T>(a.n1, a.TW1), a, s);
+        e = launch(ks.pen_fwd, dim3(pencil_tiles(a), 1, a.ncol), a.thr_p1, pencil_smem_bytes<T>(a.n1, a.TW1), a, s);
         if (e) return e;
         mark(K_PENCIL_FWD, 1);
     }
@@ -73,8 +76,8 @@ cudaError_t launch_eval(const EvalArgs<T> &a, const LaunchSet &ks, cudaStream_t 
     mark(K_AXIS0, 1);
     if (a.ncol_inv > 0) {
         mark(K_PENCIL_INV, 0);
-        e = launch(ks.pen_inv, dim3((a.n2h + a.TW1 - 1) / a.TW1, a.n0, a.ncol_inv), a.thr_p1,
-                   pencil_smem_bytes<T>(a.n1, a.TW1), a, s);
+        e = launch(ks.pen_inv, dim3(pencil_tiles(a), 1, a.ncol_inv), a.thr_p1, pencil_smem_bytes<T>(a.n1, a.TW1),
+                   a, s);
         if (e) return e;
         mark(K_PENCIL_INV, 1);
     }
@@ -96,8 +99,7 @@ template <typename T> cudaError_t launch_forward_rows_cols(const EvalArgs<T> &a,
     knots_kernel<T><<<1, 256, 0, s>>>(a);
     cudaError_t e = launch(ks.row_fwd, dim3(nrt), a.thr_rowf, row_fwd_smem_bytes<T>(a.n2, a.Brow), a, s);
     if (e) return e;
-    e = launch(ks.pen_fwd, dim3((a.n2h + a.TW1 - 1) / a.TW1, a.n0, a.ncol), a.thr_p1,
-               pencil_smem_bytes<T>(a.n1, a.TW1), a, s);
+    e = launch(ks.pen_fwd, dim3(pencil_tiles(a), 1, a.ncol), a.thr_p1, pencil_smem_bytes<T>(a.n1, a.TW1), a, s);
     if (e) return e;
     return cudaGetLastError();
 }

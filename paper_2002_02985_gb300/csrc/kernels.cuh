@@ -99,15 +99,25 @@ __global__ void __launch_bounds__(256) stats_kernel(EvalArgs<T> a) {
     double s_rho = 0.0, s_tf = 0.0;
     T mn = (T)3.0e38, mx = (T)-3.0e38;
     int bad = 0;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.N; i += stride) {
-        const T x = a.rho[i];
-        if (!(x >= (T)0) || !(x < (T)3.0e38)) bad = 1;      // NaN, Inf or negative
-        s_rho += (double)x;
-        const T c = dcbrt(x);
-        s_tf += (double)(x * c * c);                       // rho^(5/3)
-        mn = x < mn ? x : mn;
-        mx = x > mx ? x : mx;
+    // groups of 4 consecutive points: summed in T, then added in FP64 (keeps the FP64 pipe idle)
+    const long long ng = a.N / 4, stride = (long long)gridDim.x * blockDim.x;
+    for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < ng + (a.N % 4 ? 1 : 0); gi += stride) {
+        T r4 = 0, t4 = 0;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const long long i = 4 * gi + q;
+            if (i < a.N) {
+                const T x = a.rho[i];
+                if (!(x >= (T)0) || !(x < (T)3.0e38)) bad = 1;      // NaN, Inf or negative
+                const T c = dcbrt(x);
+                r4 += x;
+                t4 += x * c * c;                                      // rho^(5/3)
+                mn = x < mn ? x : mn;
+                mx = x > mx ? x : mx;
+            }
+        }
+        s_rho += (double)r4;
+        s_tf += (double)t4;
     }
     s_rho = block_sum(s_rho, sd);
     if (threadIdx.x == 0) a.part_stats[2 * blockIdx.x] = s_rho;
@@ -174,17 +184,21 @@ __global__ void __launch_bounds__(256) knots_kernel(EvalArgs<T> a) {
 // ======================================================================= row forward (R2C along n2)
 // Tile: B pairs of consecutive rows (flattened row r = i0*n1 + i1); pair p holds
 // rows 2p and 2p+1, packed as z = x_2p + i x_2p+1 for one complex FFT of length n2.
-
+// Per-point arrays use the layout o = i2 * 2B + rr (rr = row within the tile), so
+// the two points of a pair are adjacent and a thread reads them as one vector.
+// The density is staged through shared memory ([rr][pitch], pitch odd) so that
+// both the global loads and the shared-memory transposition are conflict free.
 template <typename T, class P>
 __device__ __forceinline__ void row_fwd_body(const EvalArgs<T> &a) {
     typedef typename Vec2<T>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int n = P::n(a), B = P::B(a), ld = P::ld(a), pl = n + 1, NT = P::nt();
+    const int n = P::n(a), B = P::B(a), ld = P::ld(a), NT = P::nt();
     const int n2h = n / 2 + 1;
-    const int PP = 2 * B * pl;
+    const int PP = 2 * B * n, pitch = row_pitch(n);
     C *tw = (C *)smem_raw;
     C *buf = tw + n;
-    T *sx = (T *)(buf + (size_t)n * ld);
+    T *stg = (T *)buf;
+    T *sx = (T *)((unsigned char *)buf + row_buf_bytes<T>(n, B));
     T *sra = sx + PP;
     T *srb = sra + PP;
     T *st = srb + PP;
@@ -199,14 +213,16 @@ __device__ __forceinline__ void row_fwd_body(const EvalArgs<T> &a) {
     if (lwt)
         for (int i = threadIdx.x; i < M; i += NT) sk[i] = a.knots_t[i];
     const T mean = (T)a.scal[S_RHO_MEAN];
-    __syncthreads();
-    // per-point quantities of the 2B rows of the tile
-    for (int idx = threadIdx.x; idx < 2 * B * n; idx += NT) {
+    for (int idx = threadIdx.x; idx < PP; idx += NT) {
         const int rr = idx / n, i2 = idx - rr * n;
         const long long row = row0 + rr;
-        const int o = rr * pl + i2;
-        T x = 0;
-        if (row < R) x = a.rho[row * n + i2];
+        stg[rr * pitch + i2] = (row < R) ? a.rho[row * n + i2] : (T)0;
+    }
+    __syncthreads();
+    // per-point quantities (o = idx = i2 * 2B + rr)
+    for (int o = threadIdx.x; o < PP; o += NT) {
+        const int rr = o % (2 * B), i2 = o / (2 * B);
+        const T x = stg[rr * pitch + i2];
         sx[o] = x;
         if (a.terms & 4u) {
             const T xf = x > a.floor_ ? x : a.floor_;
@@ -227,19 +243,19 @@ __device__ __forceinline__ void row_fwd_body(const EvalArgs<T> &a) {
         const int ch = a.fwd_ch[ci];
         for (int idx = threadIdx.x; idx < n * B; idx += NT) {
             const int b = idx % B, i2 = idx / B;
+            const int o = 2 * idx;                      // = i2 * 2B + 2b
             T v[2];
 #pragma unroll
             for (int s = 0; s < 2; s++) {
-                const int o = (2 * b + s) * pl + i2;
                 T f;
-                if (ch == CH_HPP) f = sx[o] - mean;
-                else if (ch == CH_VW) f = dsqrt(sx[o] > (T)0 ? sx[o] : (T)0);
-                else if (ch == CH_NL) f = srb[o];
-                else if (!lwt) f = sra[o];                         // WT: rho^alpha field
+                if (ch == CH_HPP) f = sx[o + s] - mean;
+                else if (ch == CH_VW) f = dsqrt(sx[o + s] > (T)0 ? sx[o + s] : (T)0);
+                else if (ch == CH_NL) f = srb[o + s];
+                else if (!lwt) f = sra[o + s];                     // WT: rho^alpha field
                 else {
-                    const int m = ch - CH_KNOT0, j = sj[o];
-                    const T t = st[o];
-                    f = (j == m) ? ((T)1 - t) * sra[o] : ((j == m - 1) ? t * sra[o] : (T)0);
+                    const int m = ch - CH_KNOT0, j = sj[o + s];
+                    const T t = st[o + s];
+                    f = (j == m) ? ((T)1 - t) * sra[o + s] : ((j == m - 1) ? t * sra[o + s] : (T)0);
                 }
                 if (row0 + 2 * b + s >= R) f = 0;
                 v[s] = f;
@@ -264,7 +280,8 @@ __device__ __forceinline__ void row_fwd_body(const EvalArgs<T> &a) {
 
 // ======================================================================= pencil (C2C along n1)
 
-// blockIdx.x: tile of TW consecutive k2, blockIdx.y: i0, blockIdx.z: channel list entry
+// blockIdx.x: tile of TW consecutive columns c = k0 * n2h + k2 (flattened over the
+// planes, so no tile is ragged except the very last), blockIdx.z: channel list entry
 template <typename T, int DIR, class P>
 __device__ __forceinline__ void pencil1_body(const EvalArgs<T> &a) {
     typedef typename Vec2<T>::type C;
@@ -274,17 +291,23 @@ __device__ __forceinline__ void pencil1_body(const EvalArgs<T> &a) {
     C *buf = tw + n;
     for (int i = threadIdx.x; i < n; i += NT) tw[i] = a.tw1[i];
     const int ch = DIR < 0 ? a.col_ch[blockIdx.z] : a.col_inv_ch[blockIdx.z];
-    C *base = a.chan + (size_t)ch * a.NH + (size_t)blockIdx.y * n * n2h;
-    const int c0 = blockIdx.x * TW;
+    C *base = a.chan + (size_t)ch * a.NH;
+    const long long ncols = (long long)a.n0 * n2h;
+    const long long c0 = (long long)blockIdx.x * TW;
+    const long long plane = (long long)n * n2h;
     for (int idx = threadIdx.x; idx < n * TW; idx += NT) {
         const int w = idx % TW, i = idx / TW;
-        buf[idx] = (c0 + w < n2h) ? base[(size_t)i * n2h + c0 + w] : cmake<C>((T)0, (T)0);
+        const long long c = c0 + w;
+        const long long k0 = c / n2h, k2 = c - k0 * n2h;
+        buf[idx] = (c < ncols) ? base[k0 * plane + (long long)i * n2h + k2] : cmake<C>((T)0, (T)0);
     }
     __syncthreads();
     P::template fft<DIR>(buf, a, tw);
     for (int idx = threadIdx.x; idx < n * TW; idx += NT) {
         const int w = idx % TW, i = idx / TW;
-        if (c0 + w < n2h) base[(size_t)i * n2h + c0 + w] = buf[idx];
+        const long long c = c0 + w;
+        const long long k0 = c / n2h, k2 = c - k0 * n2h;
+        if (c < ncols) base[k0 * plane + (long long)i * n2h + k2] = buf[idx];
     }
 }
 
@@ -297,8 +320,8 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
     typedef typename Vec2<T>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double sd[32];
-    __shared__ double cvec[64][3];
-    __shared__ float cw[64];
+    __shared__ T cvec[64][3];
+    __shared__ T cw[64];
     __shared__ T sk[OFDFT_MAX_KNOTS];
     const int n = P::n(a), TW = P::B(a), n2h = a.n2h, NT = P::nt();
     const long long PL = (long long)a.n1 * n2h;      // columns per plane
@@ -315,20 +338,21 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
         const long long col = c0 + w;
         const int k1 = (int)(col / n2h), k2 = (int)(col % n2h);
         const double m1 = (k1 <= a.n1 / 2) ? k1 : k1 - a.n1, m2 = k2;
-        for (int d = 0; d < 3; d++) cvec[w][d] = m1 * a.bvec[3 + d] + m2 * a.bvec[6 + d];
-        cw[w] = (col < PL) ? ((k2 == 0 || (a.n2 % 2 == 0 && k2 == a.n2 / 2)) ? 1.f : 2.f) : 0.f;
+        for (int d = 0; d < 3; d++) cvec[w][d] = (T)(m1 * a.bvec[3 + d] + m2 * a.bvec[6 + d]);
+        cw[w] = (col < PL) ? ((k2 == 0 || (a.n2 % 2 == 0 && k2 == a.n2 / 2)) ? (T)1 : (T)2) : (T)0;
     }
     const bool lwt = a.kernel == 0;
     if ((a.terms & 4u) && lwt)
         for (int i = threadIdx.x; i < a.M; i += NT) sk[i] = a.knots_t[i];
     __syncthreads();
+    const T b0x = (T)a.bvec[0], b0y = (T)a.bvec[1], b0z = (T)a.bvec[2];
     for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
         const int w = idx % TW, i = idx / TW;
-        const double m0 = (i <= n / 2) ? i : i - n;
-        const double gx = cvec[w][0] + m0 * a.bvec[0];
-        const double gy = cvec[w][1] + m0 * a.bvec[1];
-        const double gz = cvec[w][2] + m0 * a.bvec[2];
-        gn[idx] = (T)sqrt(gx * gx + gy * gy + gz * gz);
+        const T m0 = (T)((i <= n / 2) ? i : i - n);
+        const T gx = cvec[w][0] + m0 * b0x;
+        const T gy = cvec[w][1] + m0 * b0y;
+        const T gz = cvec[w][2] + m0 * b0z;
+        gn[idx] = dsqrt(gx * gx + gy * gy + gz * gz);
     }
     const T invN = (T)(1.0 / (double)a.N);
     double eH = 0.0, eV = 0.0, eP = 0.0, eN = 0.0;
@@ -353,6 +377,7 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
         load(S, CH_HPP);
         __syncthreads();
         P::template fft<-1>(S, a, tw);
+        T fH = 0, fP = 0;          // per-thread partials in T, folded into FP64 once
         for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
             const int w = idx % TW, i = idx / TW;
             const long long col = c0 + w;
@@ -361,15 +386,15 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
             const T g2 = g * g;
             C out = cmake<C>((T)0, (T)0);
             if (col < PL && g2 > (T)0) {
-                const double wgt = cw[w];
+                const T wgt = cw[w];
                 if (a.terms & 8u) {
-                    const T f = (T)(4.0 * kPi) / g2;
-                    eH += wgt * ((double)X.x * X.x + (double)X.y * X.y) / (double)g2;
-                    out = cscale(X, f);
+                    const T f = (T)1 / g2;
+                    fH += wgt * (X.x * X.x + X.y * X.y) * f;
+                    out = cscale(X, (T)(4.0 * kPi) * f);
                 }
                 if (a.terms & 16u) {
                     const C v = a.vext[(size_t)i * PL + col];
-                    eP += wgt * ((double)X.x * v.x + (double)X.y * v.y);
+                    fP += wgt * (X.x * v.x + X.y * v.y);
                     out = cadd(out, v);
                 }
             } else if (col < PL && (a.terms & 16u)) {
@@ -377,6 +402,8 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
             }
             S[idx] = out;
         }
+        eH += (double)fH;
+        eP += (double)fP;
         __syncthreads();
         P::template fft<+1>(S, a, tw);
         store(S, CH_HPP);
@@ -387,14 +414,16 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
         load(S, CH_VW);
         __syncthreads();
         P::template fft<-1>(S, a, tw);
+        T fV = 0;
         for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
             const int w = idx % TW;
             const C X = cscale(S[idx], invN);
             const T g = gn[idx];
             const T g2 = g * g;
-            eV += (double)cw[w] * (double)g2 * ((double)X.x * X.x + (double)X.y * X.y);
+            fV += cw[w] * g2 * (X.x * X.x + X.y * X.y);
             S[idx] = cscale(X, g2);
         }
+        eV += (double)fV;
         __syncthreads();
         P::template fft<+1>(S, a, tw);
         store(S, CH_VW);
@@ -414,15 +443,17 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
             load(S, CH_KNOT0);
             __syncthreads();
             P::template fft<-1>(S, a, tw);
+            T fN = 0;
             for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
                 const int w = idx % TW;
                 const T K = (T)kCWT * gnl(gn[idx] * hk);
                 const C Sa = cscale(S[idx], invN);
                 const C Rb = Rr[idx];
-                eN += (double)cw[w] * (double)K * ((double)Sa.x * Rb.x + (double)Sa.y * Rb.y);
+                fN += cw[w] * K * (Sa.x * Rb.x + Sa.y * Rb.y);
                 Rr[idx] = cscale(Rb, K);
                 S[idx] = cscale(Sa, K);
             }
+            eN += (double)fN;
             __syncthreads();
             P::template fft<+1>(Rr, a, tw);
             P::template fft<+1>(S, a, tw);
@@ -439,17 +470,19 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
                     __syncthreads();
                     P::template fft<-1>(S, a, tw);
                 }
+                T fN = 0;
                 for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
                     const T K = (T)kCWT * gnl(gn[idx] * hk);
                     if (exact) {
                         // E_NL += Omega sum_G w Re(conj(FFT[h_m rho^alpha]) K_m FFT[rho^beta])
                         const C Sm = cscale(S[idx], invN);
                         const C Rb = Rr[idx];
-                        eN += (double)cw[idx % TW] * (double)K * ((double)Sm.x * Rb.x + (double)Sm.y * Rb.y);
+                        fN += cw[idx % TW] * K * (Sm.x * Rb.x + Sm.y * Rb.y);
                         A[idx] = cadd(A[idx], cscale(Sm, K));
                     }
                     S[idx] = cscale(Rr[idx], K);
                 }
+                eN += (double)fN;
                 __syncthreads();
                 P::template fft<+1>(S, a, tw);
                 store(S, CH_KNOT0 + m);
@@ -472,7 +505,6 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
 }
 
 // ======================================================================= row inverse (C2R along n2) + s4 + V
-
 template <typename T, class P>
 __device__ __forceinline__ void row_inv_body(const EvalArgs<T> &a) {
     typedef typename Vec2<T>::type C;
@@ -480,12 +512,13 @@ __device__ __forceinline__ void row_inv_body(const EvalArgs<T> &a) {
     __shared__ double sd[32];
     __shared__ T sk[OFDFT_MAX_KNOTS];
     __shared__ T sidk[OFDFT_MAX_KNOTS];
-    const int n = P::n(a), B = P::B(a), ld = P::ld(a), pl = n + 1, NT = P::nt();
+    const int n = P::n(a), B = P::B(a), ld = P::ld(a), NT = P::nt();
     const int n2h = n / 2 + 1;
-    const int PP = 2 * B * pl;
+    const int PP = 2 * B * n, pitch = row_pitch(n);
     C *tw = (C *)smem_raw;
     C *buf = tw + n;
-    T *sv = (T *)(buf + (size_t)n * ld);   // V accumulator
+    T *stg = (T *)buf;
+    T *sv = (T *)((unsigned char *)buf + row_buf_bytes<T>(n, B));   // V accumulator
     T *sa1 = sv + PP;                      // rho^(alpha-1)
     T *sk3 = sa1 + PP;                     // exact: kF/3 inside the knot range (else 0); interp: rho^alpha
     T *svw = sk3 + PP;                     // 1 / (2 max(psi, psi_floor))
@@ -504,14 +537,16 @@ __device__ __forceinline__ void row_inv_body(const EvalArgs<T> &a) {
             sk[i] = a.knots_t[i];
             sidk[i] = (i + 1 < M) ? a.invdk_t[i] : (T)0;
         }
-    __syncthreads();
-    const T psi_floor = dsqrt(a.floor_);
-    for (int idx = threadIdx.x; idx < 2 * B * n; idx += NT) {
+    for (int idx = threadIdx.x; idx < PP; idx += NT) {
         const int rr = idx / n, i2 = idx - rr * n;
         const long long row = row0 + rr;
-        const int o = rr * pl + i2;
-        T x = 0;
-        if (row < R) x = a.rho[row * n + i2];
+        stg[rr * pitch + i2] = (row < R) ? a.rho[row * n + i2] : (T)0;
+    }
+    __syncthreads();
+    const T psi_floor = dsqrt(a.floor_);
+    for (int o = threadIdx.x; o < PP; o += NT) {
+        const int rr = o % (2 * B), i2 = o / (2 * B);
+        const T x = stg[rr * pitch + i2];
         T v = 0;
         const T xp = x > (T)0 ? x : (T)0;
         if (a.terms & 1u) {
@@ -539,7 +574,7 @@ __device__ __forceinline__ void row_inv_body(const EvalArgs<T> &a) {
         }
     }
     __syncthreads();
-    double eNL = 0.0;
+    T fNL = 0;
     const T alpha_eff = interp ? (T)2 * a.alpha : a.alpha;
     for (int ci = 0; ci < a.ninv; ci++) {
         const int ch = a.inv_ch[ci], kind = a.inv_kind[ci], m = a.inv_knot[ci];
@@ -563,42 +598,47 @@ __device__ __forceinline__ void row_inv_body(const EvalArgs<T> &a) {
         for (int idx = threadIdx.x; idx < n * B; idx += NT) {
             const int b = idx % B, i2 = idx / B;
             const C z = buf[i2 * ld + b];
+            const int o = 2 * idx;                      // = i2 * 2B + 2b
 #pragma unroll
             for (int s = 0; s < 2; s++) {
-                const int o = (2 * b + s) * pl + i2;
                 const T y = s ? z.y : z.x;
-                T acc = sv[o];
+                T acc = sv[o + s];
                 if (kind == CONS_ADD) acc += y;
-                else if (kind == CONS_VW) acc += y * svw[o];
-                else if (kind == CONS_T2 || kind == CONS_WT_B) acc += a.beta * sb1[o] * y;
-                else if (kind == CONS_WT_A) acc += a.alpha * sa1[o] * y;
+                else if (kind == CONS_VW) acc += y * svw[o + s];
+                else if (kind == CONS_T2 || kind == CONS_WT_B) acc += a.beta * sb1[o + s] * y;
+                else if (kind == CONS_WT_A) acc += a.alpha * sa1[o + s] * y;
                 else {
-                    const int j = sj[o];
+                    const int j = sj[o + s];
                     if (j == m || j + 1 == m) {
-                        const T t = st[o], idk = sidk[j];
+                        const T t = st[o + s], idk = sidk[j];
                         const T h = (j == m) ? (T)1 - t : t;
                         if (interp) {
-                            acc += y * alpha_eff * sa1[o] * h;
-                            if (row0 + 2 * b + s < R) eNL += (double)(sk3[o] * h) * (double)y;
+                            acc += y * alpha_eff * sa1[o + s] * h;
+                            if (row0 + 2 * b + s < R) fNL += sk3[o + s] * h * y;
                         } else {
                             const T hp = (j == m) ? -idk : idk;
-                            acc += y * sa1[o] * (alpha_eff * h + sk3[o] * hp);
+                            acc += y * sa1[o + s] * (alpha_eff * h + sk3[o + s] * hp);
                         }
                     }
                 }
-                sv[o] = acc;
+                sv[o + s] = acc;
             }
         }
         __syncthreads();
     }
     if (a.V) {
-        for (int idx = threadIdx.x; idx < 2 * B * n; idx += NT) {
+        for (int o = threadIdx.x; o < PP; o += NT) {
+            const int rr = o % (2 * B), i2 = o / (2 * B);
+            stg[rr * pitch + i2] = sv[o];
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < PP; idx += NT) {
             const int rr = idx / n, i2 = idx - rr * n;
             const long long row = row0 + rr;
-            if (row < R) a.V[row * n + i2] = sv[rr * pl + i2];
+            if (row < R) a.V[row * n + i2] = stg[rr * pitch + i2];
         }
     }
-    eNL = block_sum(eNL, sd);
+    const double eNL = block_sum((double)fNL, sd);
     if (threadIdx.x == 0) a.part_row[blockIdx.x] = eNL;
 }
 

@@ -226,6 +226,7 @@ def test_specialised_and_generic_kernels_agree(kw, monkeypatch):
         g.set_ions(wl["positions"], wl["species"], wl["Z"], wl["rc"])
         out.append(g.energy_potential(rho, f))
     (E1, V1), (E2, V2) = out
+    # same algorithm, different reduction blocking: FP32 rounding only
     for k in E1:
-        assert abs(E1[k] - E2[k]) <= 1e-9 * max(1.0, abs(E1[k])), (k, E1[k], E2[k])
+        assert abs(E1[k] - E2[k]) / wl["n_atoms"] <= 1e-7, (k, E1[k], E2[k])
     assert torch.allclose(V1, V2, rtol=1e-5, atol=1e-5 * float(V1.abs().max()))

@@ -39,7 +39,10 @@ def test_noalloc_tf_matches_regular_entry_point(precision):
                                                    ct.c_void_p(stream.cuda_stream))
         assert st == L.OFDFT_OK
         torch.cuda.synchronize()
-        assert abs(float(E_dev) - E_ref["TF"]) <= 1e-10 * abs(E_ref["TF"])
+        # FP64: 1e-10 relative; FP32-mixed: the reductions group points differently
+        # (FP32 partials of 4 points in the regular path), so FP32 rounding only
+        etol = 1e-10 if precision == L.FP64 else 1e-7
+        assert abs(float(E_dev) - E_ref["TF"]) <= etol * abs(E_ref["TF"])
         rtol = 1e-12 if precision == L.FP64 else 1e-6
         assert torch.allclose(V, V_ref, rtol=rtol, atol=0.0)
 
