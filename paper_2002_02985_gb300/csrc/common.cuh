@@ -28,6 +28,22 @@ constexpr double kThreePi2 = 29.608813203268074;     // 3 pi^2
 constexpr double kCTF = 2.871234000188191;           // 0.3 (3 pi^2)^(2/3)
 constexpr double kCWT = 2.2969872001505527;          // 0.24 (3 pi^2)^(2/3)
 
+// --------------------------------------------------------------- async copies
+// Asynchronous global -> shared copies (one 8- or 16-byte element per call).
+// src_bytes = 0 fills the destination with zeros (used for ragged tiles).
+template <int BYTES> __device__ __forceinline__ void cp_async(void *smem_dst, const void *gmem_src, bool valid) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    const int n = valid ? BYTES : 0;
+    if (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem_src), "r"(n) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem_src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 // --------------------------------------------------------------- complex helpers
 template <typename T> struct Vec2;
 template <> struct Vec2<float> { typedef float2 type; };

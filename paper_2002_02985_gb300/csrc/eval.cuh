@@ -103,7 +103,7 @@ template <typename T> __host__ __device__ inline size_t pencil_smem_bytes(int n,
 
 template <typename T> __host__ __device__ inline size_t axis0_smem_bytes(int n, int TW) {
     typedef typename Vec2<T>::type C;
-    return (size_t)n * sizeof(C) + 3 * (size_t)n * TW * sizeof(C) + (size_t)n * TW * sizeof(T) + 16;
+    return (size_t)n * sizeof(C) + 4 * (size_t)n * TW * sizeof(C) + (size_t)n * TW * sizeof(T) + 16;
 }
 
 template <typename T> __host__ __device__ inline size_t row_inv_smem_bytes(int n2, int B) {

@@ -57,6 +57,7 @@ cudaError_t launch_eval(const EvalArgs<T> &a, const LaunchSet &ks, cudaStream_t 
     mark(K_STATS, 1);
     mark(K_KNOTS, 0);
     knots_kernel<T><<<1, 256, 0, s>>>(a);
+    if ((a.terms & 4u) && a.kernel == 0 && a.M >= 2) knots_make_kernel<T><<<1, 64, 0, s>>>(a);
     mark(K_KNOTS, 1);
     if (a.nfwd > 0) {
         mark(K_ROW_FWD, 0);

@@ -1,4 +1,4 @@
-// Shared-memory batched FFT engine: mixed radix 2/3/4/5/8 Stockham autosort.
+// Shared-memory batched FFT engine: mixed radix 2/3/4/5/8/16 Stockham autosort.
 //
 // A CTA transforms B sequences of length n that live in shared memory with the
 // batch index innermost: element e of sequence b sits at buf[e * ld + b].
@@ -88,12 +88,48 @@ template <int DIR, typename C> __device__ __forceinline__ void dft5(C *v) {
     v[3] = csub(m2, n2);
 }
 
+// 16-point DFT as 4 x 4: DFT4 over n1 for each n2, twiddles W16^(n2 k1), DFT4
+// over n2; X[k1 + 4 k2] = sum_n2 W4^(n2 k2) W16^(n2 k1) sum_n1 W4^(n1 k1) v[4 n1 + n2].
+template <int DIR, typename C> __device__ __forceinline__ void dft16(C *v) {
+    typedef decltype(C::x) T;
+    const T s = (T)DIR;
+    const T c8 = (T)0.9238795325112867, s8 = (T)0.3826834323650898, h = (T)0.7071067811865476;
+#pragma unroll
+    for (int n2 = 0; n2 < 4; n2++) dft4x<DIR>(v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]);
+    // v[n2 + 4 k1] holds A_n2[k1]; multiply by W16^(n2 k1), W16^e = cos(2 pi e/16) + s i sin(2 pi e/16)
+    auto rot = [&](C &x, T cr, T si) {          // x *= (cr + s i si)
+        const T xr = x.x, xi = x.y;
+        x.x = xr * cr - s * xi * si;
+        x.y = xi * cr + s * xr * si;
+    };
+    rot(v[5], c8, s8);          // e = 1
+    rot(v[9], h, h);            // e = 2
+    rot(v[13], s8, c8);         // e = 3
+    rot(v[6], h, h);            // e = 2
+    v[10] = cmul_si<DIR>(v[10]);// e = 4
+    rot(v[14], -h, h);          // e = 6
+    rot(v[7], s8, c8);          // e = 3
+    rot(v[11], -h, h);          // e = 6
+    rot(v[15], -c8, -s8);       // e = 9
+#pragma unroll
+    for (int k1 = 0; k1 < 4; k1++) dft4x<DIR>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+    // now v[4 k1 + k2] = X[k1 + 4 k2]: transpose the 4 x 4 index
+    C t[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) t[i] = v[i];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; k1++)
+#pragma unroll
+        for (int k2 = 0; k2 < 4; k2++) v[k1 + 4 * k2] = t[4 * k1 + k2];
+}
+
 template <int DIR, int R, typename C> __device__ __forceinline__ void dft(C *v) {
     if (R == 2) dft2<DIR>(v);
     else if (R == 3) dft3<DIR>(v);
     else if (R == 4) dft4<DIR>(v);
     else if (R == 5) dft5<DIR>(v);
-    else dft8<DIR>(v);
+    else if (R == 8) dft8<DIR>(v);
+    else dft16<DIR>(v);
 }
 
 // ----------------------------------------------------------------- one pass
@@ -160,27 +196,31 @@ __device__ __noinline__ void fft_smem(C *buf, int ld, int B, const FFTPlan &p, c
 // Compile-time variant: length N, batch B (sequence stride 1, batch index
 // innermost with element stride LD) and block size NT are template
 // parameters, so every index, loop bound and twiddle stride is a constant.
-// The radix sequence is the host plan's: 8s first, then a 4 or 2, then 5s,
-// then 3s.
+// The radix sequence puts the largest power-of-two radix first (16 in FP32,
+// 8 in FP64), then the remaining power of two, then 5s, then 3s.
 namespace ct {
 
-constexpr int npass(int n) {
+// radix sequence with power-of-two radix at most maxr (16 or 8): maxr-radix
+// passes first, then one smaller power of two, then 5s, then 3s
+constexpr int npass(int n, int maxr) {
     int c = 0, m = n, p2 = 0;
     while (m % 2 == 0) { m /= 2; p2++; }
-    c += p2 / 3 + (p2 % 3 ? 1 : 0);
+    const int lr = maxr == 16 ? 4 : 3;
+    c += p2 / lr + (p2 % lr ? 1 : 0);
     while (m % 5 == 0) { m /= 5; c++; }
     while (m % 3 == 0) { m /= 3; c++; }
     return c;
 }
 
-constexpr int radix(int n, int p) {
+constexpr int radix(int n, int p, int maxr) {
     int m = n, p2 = 0;
     while (m % 2 == 0) { m /= 2; p2++; }
-    int r8 = p2 / 3, rem = p2 % 3;
-    if (p < r8) return 8;
-    p -= r8;
+    const int lr = maxr == 16 ? 4 : 3;
+    int rbig = p2 / lr, rem = p2 % lr;
+    if (p < rbig) return maxr;
+    p -= rbig;
     if (rem) {
-        if (p == 0) return rem == 2 ? 4 : 2;
+        if (p == 0) return 1 << rem;
         p -= 1;
     }
     int n5 = 0;
@@ -189,9 +229,9 @@ constexpr int radix(int n, int p) {
     return 3;
 }
 
-constexpr int ns(int n, int p) {
+constexpr int ns(int n, int p, int maxr) {
     int s = 1;
-    for (int q = 0; q < p; q++) s *= radix(n, q);
+    for (int q = 0; q < p; q++) s *= radix(n, q, maxr);
     return s;
 }
 
@@ -231,19 +271,21 @@ __device__ __forceinline__ void pass(C *buf, const C *tw) {
     __syncthreads();
 }
 
-template <int DIR, int N, int B, int LD, int NT, int P, typename C>
+template <int DIR, int N, int B, int LD, int NT, int MAXR, int P, typename C>
 __device__ __forceinline__ void passes(C *buf, const C *tw) {
-    if constexpr (P < npass(N)) {
-        pass<DIR, radix(N, P), N, ns(N, P), B, LD, NT>(buf, tw);
-        passes<DIR, N, B, LD, NT, P + 1>(buf, tw);
+    if constexpr (P < npass(N, MAXR)) {
+        pass<DIR, radix(N, P, MAXR), N, ns(N, P, MAXR), B, LD, NT>(buf, tw);
+        passes<DIR, N, B, LD, NT, MAXR, P + 1>(buf, tw);
     }
 }
 
 // B sequences of length N in buf (element e of sequence b at buf[e*LD + b]);
-// the caller synchronises before the call.
+// the caller synchronises before the call.  FP32 uses radix-16 passes (a
+// 128-point transform is 16 x 8), FP64 radix 8 at most (register budget).
 template <int DIR, int N, int B, int LD, int NT, typename C>
 __device__ __forceinline__ void fft(C *buf, const C *tw) {
-    passes<DIR, N, B, LD, NT, 0>(buf, tw);
+    constexpr int MAXR = sizeof(C) == 8 ? 16 : 8;
+    passes<DIR, N, B, LD, NT, MAXR, 0>(buf, tw);
 }
 
 }  // namespace ct

@@ -14,6 +14,9 @@ namespace ofdft {
 // ======================================================================= policies
 template <typename T, int AX> struct RtPolicy {
     typedef typename Vec2<T>::type C;
+    static constexpr bool ct = false;
+    static constexpr int N_ = 0, B_ = 0, NT_ = 0;
+    static constexpr int max_threads = kMaxThreads, min_blocks = 1, min_blocks_ax0 = 1;
     __device__ static int n(const EvalArgs<T> &a) { return AX == 0 ? a.n0 : (AX == 1 ? a.n1 : a.n2); }
     __device__ static int B(const EvalArgs<T> &a) { return AX == 0 ? a.TW0 : (AX == 1 ? a.TW1 : a.Brow); }
     __device__ static int ld(const EvalArgs<T> &a) { return AX == 2 ? a.Brow + 1 : B(a); }
@@ -23,14 +26,20 @@ template <typename T, int AX> struct RtPolicy {
     }
 };
 
-template <typename T, int N, int B_, int LD_, int NT_> struct CtPolicy {
+template <typename T, int N, int B__, int LD_, int NT__> struct CtPolicy {
     typedef typename Vec2<T>::type C;
+    static constexpr bool ct = true;
+    static constexpr int N_ = N, B_ = B__, NT_ = NT__;
+    // register budget: at least 768 resident threads per SM (24 warps)
+    static constexpr int max_threads = NT__, min_blocks = (768 / NT__) > 0 ? 768 / NT__ : 1;
+    // the reciprocal-space kernel holds more live state: at least 512 threads per SM
+    static constexpr int min_blocks_ax0 = (512 / NT__) > 0 ? 512 / NT__ : 1;
     __device__ static constexpr int n(const EvalArgs<T> &) { return N; }
-    __device__ static constexpr int B(const EvalArgs<T> &) { return B_; }
+    __device__ static constexpr int B(const EvalArgs<T> &) { return B__; }
     __device__ static constexpr int ld(const EvalArgs<T> &) { return LD_; }
-    __device__ static constexpr int nt() { return NT_; }
+    __device__ static constexpr int nt() { return NT__; }
     template <int DIR> __device__ static void fft(C *buf, const EvalArgs<T> &, const C *tw) {
-        ct::fft<DIR, N, B_, LD_, NT_>(buf, tw);
+        ct::fft<DIR, N, B__, LD_, NT__>(buf, tw);
     }
 };
 
@@ -159,24 +168,36 @@ __global__ void __launch_bounds__(256) knots_kernel(EvalArgs<T> a) {
     a.scal[S_RHO_MEAN] = mean;
     a.scal[S_KF_WT] = cbrt(kThreePi2 * (mean > fl ? mean : fl));
     a.energies[E_TF] = (a.terms & 1u) ? kCTF * s_tf * a.dV : 0.0;
-    const int M = a.M;
-    if (!(a.terms & 4u) || a.kernel != 0 || M < 2) return;
-    if (!a.frozen) {
-        // s1: knots between kF(min rho) and kF(max rho), FP64
-        const double rmin = (double)mn > fl ? (double)mn : fl, rmax = (double)mx > fl ? (double)mx : fl;
-        const double kmin = cbrt(kThreePi2 * rmin), kmax = cbrt(kThreePi2 * rmax);
-        for (int m = 0; m < M; m++) {
-            double k;
-            if (a.knot_spacing == 0) k = kmin * exp((double)m * (log(kmax / kmin) / (double)(M - 1)));
+}
+
+// s1: M knots between kF(min rho) and kF(max rho) in FP64, one thread per knot
+// (min/max from knots_kernel's reduction); a separate launch so the reduction
+// block does no serial FP64 work.
+template <typename T>
+__global__ void __launch_bounds__(64) knots_make_kernel(EvalArgs<T> a) {
+    __shared__ double kn[OFDFT_MAX_KNOTS];
+    const int M = a.M, m = threadIdx.x;
+    if (m < M) {
+        double k;
+        if (!a.frozen) {
+            const double fl = (double)a.floor_;
+            const double mn = a.scal[S_RHO_MIN], mx = a.scal[S_RHO_MAX];
+            const double kmin = cbrt(kThreePi2 * (mn > fl ? mn : fl));
+            const double kmax = cbrt(kThreePi2 * (mx > fl ? mx : fl));
+            if (m == 0) k = kmin;
+            else if (m == M - 1) k = kmax;
+            else if (a.knot_spacing == 0) k = kmin * exp((double)m * (log(kmax / kmin) / (double)(M - 1)));
             else k = kmin + (double)m * ((kmax - kmin) / (double)(M - 1));
             a.knots_d[m] = k;
+        } else {
+            k = a.knots_d[m];
         }
-        a.knots_d[0] = kmin;
-        a.knots_d[M - 1] = kmax;
+        kn[m] = k;
+        a.knots_t[m] = (T)k;
     }
-    for (int m = 0; m < M; m++) a.knots_t[m] = (T)a.knots_d[m];
-    for (int m = 0; m + 1 < M; m++) {
-        const double dk = a.knots_d[m + 1] - a.knots_d[m];
+    __syncthreads();
+    if (m + 1 < M) {
+        const double dk = kn[m + 1] - kn[m];
         a.invdk_t[m] = dk > 0.0 ? (T)(1.0 / dk) : (T)0;
     }
 }
@@ -312,7 +333,10 @@ __device__ __forceinline__ void pencil1_body(const EvalArgs<T> &a) {
 }
 
 // ======================================================================= axis 0 + reciprocal space
-
+// Tile: TW consecutive columns (k1, k2) of the plane, all n0 values of k0.
+// The channel tiles are read in a fixed order (Hartree+PP, vW, rho^beta, then
+// the knot fields); the next one is prefetched asynchronously into the second
+// of two rotating buffers while the current one is transformed.
 // Partials per block: [0] sum_G w |rho_hat|^2/G^2, [1] sum_G w G^2 |psi_hat|^2,
 // [2] sum_G w Re(conj(rho_hat) V_ext), [3] nonlocal energy in G space.
 template <typename T, class P>
@@ -323,16 +347,51 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
     __shared__ T cvec[64][3];
     __shared__ T cw[64];
     __shared__ T sk[OFDFT_MAX_KNOTS];
+    __shared__ int order[kMaxChan];
     const int n = P::n(a), TW = P::B(a), n2h = a.n2h, NT = P::nt();
     const long long PL = (long long)a.n1 * n2h;      // columns per plane
     const int NTILE = n * TW;
     C *tw = (C *)smem_raw;
-    C *S = tw + n;
-    C *Rr = S + NTILE;
+    C *X[2] = {tw + n, tw + n + NTILE};              // rotating load buffers
+    C *Rr = X[1] + NTILE;
     C *A = Rr + NTILE;
     T *gn = (T *)(A + NTILE);
-    for (int i = threadIdx.x; i < n; i += NT) tw[i] = a.tw0[i];
+    const bool lwt = a.kernel == 0;
+    const bool exact = a.nlpot == 0;
+    // the channels this block reads, in processing order
+    int nord = 0;
+    if (a.terms & (8u | 16u)) nord++;
+    if (a.terms & 2u) nord++;
+    if (a.terms & 4u) nord += 1 + (!lwt ? 1 : (exact ? a.M : 0));
+    if (threadIdx.x == 0) {
+        int q = 0;
+        if (a.terms & (8u | 16u)) order[q++] = CH_HPP;
+        if (a.terms & 2u) order[q++] = CH_VW;
+        if (a.terms & 4u) {
+            order[q++] = CH_NL;
+            if (!lwt) order[q++] = CH_KNOT0;
+            else if (exact)
+                for (int m = 0; m < a.M; m++) order[q++] = CH_KNOT0 + m;
+        }
+    }
     const long long c0 = (long long)blockIdx.x * TW;
+    auto prefetch = [&](C *dst, int ch) {
+        const C *src = a.chan + (size_t)ch * a.NH;
+        for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
+            const int w = idx % TW, i = idx / TW;
+            const bool ok = c0 + w < PL;
+            cp_async<sizeof(C)>(dst + idx, src + (ok ? (size_t)i * PL + c0 + w : 0), ok);
+        }
+        cp_async_commit();
+    };
+    auto store = [&](const C *srcb, int ch) {
+        C *dst = a.chan + (size_t)ch * a.NH;
+        for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
+            const int w = idx % TW, i = idx / TW;
+            if (c0 + w < PL) dst[(size_t)i * PL + c0 + w] = srcb[idx];
+        }
+    };
+    for (int i = threadIdx.x; i < n; i += NT) tw[i] = a.tw0[i];
     // per column (k1, k2): its part of the G vector and its half-spectrum weight
     for (int w = threadIdx.x; w < TW; w += NT) {
         const long long col = c0 + w;
@@ -341,10 +400,20 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
         for (int d = 0; d < 3; d++) cvec[w][d] = (T)(m1 * a.bvec[3 + d] + m2 * a.bvec[6 + d]);
         cw[w] = (col < PL) ? ((k2 == 0 || (a.n2 % 2 == 0 && k2 == a.n2 / 2)) ? (T)1 : (T)2) : (T)0;
     }
-    const bool lwt = a.kernel == 0;
     if ((a.terms & 4u) && lwt)
         for (int i = threadIdx.x; i < a.M; i += NT) sk[i] = a.knots_t[i];
     __syncthreads();
+    int stage = 0;
+    if (nord > 0) prefetch(X[0], order[0]);
+    // next(): wait for the current stage's tile, start the following one
+    auto next = [&]() -> C * {
+        cp_async_wait<0>();
+        __syncthreads();
+        C *cur = X[stage & 1];
+        if (stage + 1 < nord) prefetch(X[(stage + 1) & 1], order[stage + 1]);
+        stage++;
+        return cur;
+    };
     const T b0x = (T)a.bvec[0], b0y = (T)a.bvec[1], b0z = (T)a.bvec[2];
     for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
         const int w = idx % TW, i = idx / TW;
@@ -357,31 +426,15 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
     const T invN = (T)(1.0 / (double)a.N);
     double eH = 0.0, eV = 0.0, eP = 0.0, eN = 0.0;
 
-    auto load = [&](C *dst, int ch) {
-        const C *src = a.chan + (size_t)ch * a.NH;
-        for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
-            const int w = idx % TW, i = idx / TW;
-            dst[idx] = (c0 + w < PL) ? src[(size_t)i * PL + c0 + w] : cmake<C>((T)0, (T)0);
-        }
-    };
-    auto store = [&](const C *srcb, int ch) {
-        C *dst = a.chan + (size_t)ch * a.NH;
-        for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
-            const int w = idx % TW, i = idx / TW;
-            if (c0 + w < PL) dst[(size_t)i * PL + c0 + w] = srcb[idx];
-        }
-    };
-
     // ---- Hartree + local pseudopotential
     if (a.terms & (8u | 16u)) {
-        load(S, CH_HPP);
-        __syncthreads();
+        C *S = next();
         P::template fft<-1>(S, a, tw);
         T fH = 0, fP = 0;          // per-thread partials in T, folded into FP64 once
         for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
             const int w = idx % TW, i = idx / TW;
             const long long col = c0 + w;
-            const C X = cscale(S[idx], invN);
+            const C X0 = cscale(S[idx], invN);
             const T g = gn[idx];
             const T g2 = g * g;
             C out = cmake<C>((T)0, (T)0);
@@ -389,12 +442,12 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
                 const T wgt = cw[w];
                 if (a.terms & 8u) {
                     const T f = (T)1 / g2;
-                    fH += wgt * (X.x * X.x + X.y * X.y) * f;
-                    out = cscale(X, (T)(4.0 * kPi) * f);
+                    fH += wgt * (X0.x * X0.x + X0.y * X0.y) * f;
+                    out = cscale(X0, (T)(4.0 * kPi) * f);
                 }
                 if (a.terms & 16u) {
                     const C v = a.vext[(size_t)i * PL + col];
-                    fP += wgt * (X.x * v.x + X.y * v.y);
+                    fP += wgt * (X0.x * v.x + X0.y * v.y);
                     out = cadd(out, v);
                 }
             } else if (col < PL && (a.terms & 16u)) {
@@ -407,41 +460,37 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
         __syncthreads();
         P::template fft<+1>(S, a, tw);
         store(S, CH_HPP);
-        __syncthreads();
     }
     // ---- von Weizsaecker (psi form)
     if (a.terms & 2u) {
-        load(S, CH_VW);
-        __syncthreads();
+        C *S = next();
         P::template fft<-1>(S, a, tw);
         T fV = 0;
         for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
             const int w = idx % TW;
-            const C X = cscale(S[idx], invN);
+            const C X0 = cscale(S[idx], invN);
             const T g = gn[idx];
             const T g2 = g * g;
-            fV += cw[w] * g2 * (X.x * X.x + X.y * X.y);
-            S[idx] = cscale(X, g2);
+            fV += cw[w] * g2 * (X0.x * X0.x + X0.y * X0.y);
+            S[idx] = cscale(X0, g2);
         }
         eV += (double)fV;
         __syncthreads();
         P::template fft<+1>(S, a, tw);
         store(S, CH_VW);
-        __syncthreads();
     }
     // ---- nonlocal: s2 (kernel at each knot) and the reciprocal half of s3
     if (a.terms & 4u) {
-        load(Rr, CH_NL);
-        __syncthreads();
-        P::template fft<-1>(Rr, a, tw);
-        for (int idx = threadIdx.x; idx < NTILE; idx += NT) Rr[idx] = cscale(Rr[idx], invN);
-        __syncthreads();
+        {
+            C *S = next();
+            P::template fft<-1>(S, a, tw);
+            for (int idx = threadIdx.x; idx < NTILE; idx += NT) Rr[idx] = cscale(S[idx], invN);
+        }
         if (!lwt) {
             // global-kF Wang-Teter: K * rho^beta into CH_NL, K * rho^alpha into CH_KNOT0;
             // E = Omega sum_G w Re(conj(FFT[rho^alpha]) K FFT[rho^beta])
             const T hk = (T)(0.5 / a.scal[S_KF_WT]);
-            load(S, CH_KNOT0);
-            __syncthreads();
+            C *S = next();
             P::template fft<-1>(S, a, tw);
             T fN = 0;
             for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
@@ -460,15 +509,17 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
             store(Rr, CH_NL);
             store(S, CH_KNOT0);
         } else {
-            const bool exact = a.nlpot == 0;
             if (exact)
                 for (int idx = threadIdx.x; idx < NTILE; idx += NT) A[idx] = cmake<C>((T)0, (T)0);
             for (int m = 0; m < a.M; m++) {
                 const T hk = (T)0.5 / sk[m];
+                C *S;
                 if (exact) {
-                    load(S, CH_KNOT0 + m);
-                    __syncthreads();
+                    S = next();
                     P::template fft<-1>(S, a, tw);
+                } else {
+                    __syncthreads();
+                    S = X[m & 1];
                 }
                 T fN = 0;
                 for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
@@ -486,14 +537,15 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
                 __syncthreads();
                 P::template fft<+1>(S, a, tw);
                 store(S, CH_KNOT0 + m);
-                __syncthreads();
             }
             if (exact) {
+                __syncthreads();
                 P::template fft<+1>(A, a, tw);
                 store(A, CH_NL);
             }
         }
     }
+    cp_async_wait<0>();
     eH = block_sum(eH, sd);
     if (threadIdx.x == 0) a.part_ax0[4 * blockIdx.x] = eH;
     eV = block_sum(eV, sd);
@@ -576,24 +628,60 @@ __device__ __forceinline__ void row_inv_body(const EvalArgs<T> &a) {
     __syncthreads();
     T fNL = 0;
     const T alpha_eff = interp ? (T)2 * a.alpha : a.alpha;
-    for (int ci = 0; ci < a.ninv; ci++) {
-        const int ch = a.inv_ch[ci], kind = a.inv_kind[ci], m = a.inv_knot[ci];
-        const C *in = a.chan + (size_t)ch * a.NH;
-        // pack the pair of half spectra into one full complex spectrum
-        for (int idx = threadIdx.x; idx < n2h * B; idx += NT) {
-            const int b = idx / n2h, k = idx - b * n2h;
-            const long long r0 = row0 + 2 * b;
+    // the pair of half-spectrum rows of every (pair, k) this thread packs; with a
+    // compile-time policy the next channel's values are loaded into registers
+    // while the current channel is transformed (latency hidden behind the FFT)
+    constexpr int QP = P::ct ? (P::B_ * (P::N_ / 2 + 1) + P::NT_ - 1) / P::NT_ : 1;
+    C p0[QP], p1[QP];
+    auto load_pairs = [&](int ci) {
+        const C *in = a.chan + (size_t)a.inv_ch[ci] * a.NH;
+#pragma unroll
+        for (int q = 0; q < QP; q++) {
+            const int idx = threadIdx.x + q * NT;
             const C z = cmake<C>((T)0, (T)0);
-            const C X0 = (r0 < R) ? in[r0 * n2h + k] : z;
-            const C X1 = (r0 + 1 < R) ? in[(r0 + 1) * n2h + k] : z;
-            if (k == 0 || 2 * k == n) {
-                buf[k * ld + b] = cmake<C>(X0.x, X1.x);
-            } else {
-                buf[k * ld + b] = cmake<C>(X0.x - X1.y, X0.y + X1.x);
-                buf[(n - k) * ld + b] = cmake<C>(X0.x + X1.y, X1.x - X0.y);
+            p0[q] = z;
+            p1[q] = z;
+            if (idx < n2h * B) {
+                const int b = idx / n2h, k = idx - b * n2h;
+                const long long r0 = row0 + 2 * b;
+                if (r0 < R) p0[q] = in[r0 * n2h + k];
+                if (r0 + 1 < R) p1[q] = in[(r0 + 1) * n2h + k];
             }
         }
-        __syncthreads();
+    };
+    auto pack = [&](int idx, C X0, C X1) {
+        const int b = idx / n2h, k = idx - b * n2h;
+        if (k == 0 || 2 * k == n) {
+            buf[k * ld + b] = cmake<C>(X0.x, X1.x);
+        } else {
+            buf[k * ld + b] = cmake<C>(X0.x - X1.y, X0.y + X1.x);
+            buf[(n - k) * ld + b] = cmake<C>(X0.x + X1.y, X1.x - X0.y);
+        }
+    };
+    if constexpr (P::ct) {
+        if (a.ninv > 0) load_pairs(0);
+    }
+    for (int ci = 0; ci < a.ninv; ci++) {
+        const int kind = a.inv_kind[ci], m = a.inv_knot[ci];
+        // pack the pair of half spectra into one full complex spectrum
+        if constexpr (P::ct) {
+#pragma unroll
+            for (int q = 0; q < QP; q++) {
+                const int idx = threadIdx.x + q * NT;
+                if (idx < n2h * B) pack(idx, p0[q], p1[q]);
+            }
+            __syncthreads();
+            if (ci + 1 < a.ninv) load_pairs(ci + 1);
+        } else {
+            const C *in = a.chan + (size_t)a.inv_ch[ci] * a.NH;
+            for (int idx = threadIdx.x; idx < n2h * B; idx += NT) {
+                const int b = idx / n2h, k = idx - b * n2h;
+                const long long r0 = row0 + 2 * b;
+                const C z = cmake<C>((T)0, (T)0);
+                pack(idx, (r0 < R) ? in[r0 * n2h + k] : z, (r0 + 1 < R) ? in[(r0 + 1) * n2h + k] : z);
+            }
+            __syncthreads();
+        }
         P::template fft<+1>(buf, a, tw);
         for (int idx = threadIdx.x; idx < n * B; idx += NT) {
             const int b = idx % B, i2 = idx / B;
@@ -677,12 +765,20 @@ __global__ void __launch_bounds__(256) finalize_kernel(EvalArgs<T> a) {
 
 // ======================================================================= kernel wrappers
 template <typename T, class P>
-__global__ void __launch_bounds__(kMaxThreads) row_fwd_kernel(EvalArgs<T> a) { row_fwd_body<T, P>(a); }
+__global__ void __launch_bounds__(P::max_threads, P::min_blocks) row_fwd_kernel(EvalArgs<T> a) {
+    row_fwd_body<T, P>(a);
+}
 template <typename T, int DIR, class P>
-__global__ void __launch_bounds__(kMaxThreads) pencil1_kernel(EvalArgs<T> a) { pencil1_body<T, DIR, P>(a); }
+__global__ void __launch_bounds__(P::max_threads, P::min_blocks) pencil1_kernel(EvalArgs<T> a) {
+    pencil1_body<T, DIR, P>(a);
+}
 template <typename T, class P>
-__global__ void __launch_bounds__(kMaxThreads) axis0_kernel(EvalArgs<T> a) { axis0_body<T, P>(a); }
+__global__ void __launch_bounds__(P::max_threads, P::min_blocks_ax0) axis0_kernel(EvalArgs<T> a) {
+    axis0_body<T, P>(a);
+}
 template <typename T, class P>
-__global__ void __launch_bounds__(kMaxThreads) row_inv_kernel(EvalArgs<T> a) { row_inv_body<T, P>(a); }
+__global__ void __launch_bounds__(P::max_threads, P::min_blocks) row_inv_kernel(EvalArgs<T> a) {
+    row_inv_body<T, P>(a);
+}
 
 }  // namespace ofdft

@@ -226,7 +226,9 @@ def test_specialised_and_generic_kernels_agree(kw, monkeypatch):
         g.set_ions(wl["positions"], wl["species"], wl["Z"], wl["rc"])
         out.append(g.energy_potential(rho, f))
     (E1, V1), (E2, V2) = out
-    # same algorithm, different reduction blocking: FP32 rounding only
+    # same method; the specialised FP32 plans use radix-16 passes and other
+    # reduction blocking, so the two differ by FP32 rounding: bound it by half
+    # the oracle tolerance (each side is checked against the oracle elsewhere)
     for k in E1:
-        assert abs(E1[k] - E2[k]) / wl["n_atoms"] <= 1e-7, (k, E1[k], E2[k])
+        assert abs(E1[k] - E2[k]) / wl["n_atoms"] <= 5e-7, (k, E1[k], E2[k])
     assert torch.allclose(V1, V2, rtol=1e-5, atol=1e-5 * float(V1.abs().max()))
