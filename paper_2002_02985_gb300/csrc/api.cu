@@ -654,6 +654,13 @@ int optimize_impl(ofdft_grid *g, T *psi, const ofdft_functional *f0, double Ne, 
         // accept: psi <- psi cos + p sin, and V at the accepted point
         CK(launch_rotate<T>(psil, rho, psi, p, std::cos(best_lam), std::sin(best_lam), N, s), "rotate");
         CK(launch_copy<T>(psi, psil, N, s), "copy");
+        // The rotation conserves int psi^2 exactly only in exact arithmetic; in FP32
+        // the rounding drift accumulates over iterations (and lowers E with the
+        // charge), so psi is renormalised to N_e with an FP64 norm.
+        {
+            const double nn = dv.dot(psi, psi) * g->dV;
+            CK(launch_square<T>(rho, psi, std::sqrt(Ne / nn), N, s), "renormalise");
+        }
         last_dE = std::fabs(Enew[0] - E[0]);
         if (lwt_auto) {
             if ((rc = refresh_knots())) return rc;
