@@ -101,7 +101,57 @@ def make_input(wl):
     return W.model_density(wl)
 
 
+def run_batch(args):
+    """64 snapshots of jittered 108-atom FCC Al on grids drawn from {64,80,96,120}^3:
+    one batched E+V+forces call per step (inputs resident, V_ext(G) built per geometry
+    beforehand and timed separately)."""
+    import torch
+    import paper_2002_02985_gb300 as ofd
+    import workloads as W
+    from paper_2002_02985_gb300 import _lib as L
+    torch.cuda.set_device(0)
+    nsnap = args.snapshots
+    grids, rhos, npts = [], [], 0
+    f = ofd.Functional(n_knots=16, precision=L.FP32_MIXED)
+    t_ions = 0.0
+    for s in range(nsnap):
+        wl = W.workload("fcc-al-108-snap", s)
+        rho = W.model_density(wl)
+        g = ofd.Grid(wl["cell"], wl["shape"])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.set_ions(wl["positions"], wl["species"], wl["Z"], wl["rc"])
+        g.energy_potential(torch.from_numpy(rho.astype(np.float32)).cuda(), f)   # builds V_ext(G), workspace
+        torch.cuda.synchronize()
+        t_ions += time.perf_counter() - t0
+        grids.append(g)
+        rhos.append(torch.from_numpy(rho.astype(np.float32)).cuda())
+        npts += rho.size
+    for _ in range(args.warmup):
+        ofd.energy_potential_batched(grids, rhos, f, want_potential=True, want_forces=True)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.steps):
+        st, en = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st.record()
+        ofd.energy_potential_batched(grids, rhos, f, want_potential=True, want_forces=True)
+        en.record()
+        torch.cuda.synchronize()
+        ms.append(st.elapsed_time(en))
+    t = sum(ms) / len(ms)
+    line = {"metric": METRIC, "value": round(npts / (t * 1e-3), 1), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "fcc-al-108-snap x%d" % nsnap, "grid_points": npts, "n_knots": 16,
+                       "step": "batched E+V+forces of all snapshots",
+                       "l2": "inputs %.0f MB + workspaces > L2" % (npts * 4 / 1e6)},
+            "per_geometry_setup_ms": round(t_ions * 1e3 / nsnap, 3)}
+    print(json.dumps(line), flush=True)
+
+
 def run_gpu(args):
+    if args.workload == "fcc-al-108-batch":
+        return run_batch(args)
     import torch
     import paper_2002_02985_gb300 as ofd
     import workloads as W
@@ -114,7 +164,7 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
-    wl = W.workload(WORKLOAD)
+    wl = W.workload(args.workload)
     rho64 = make_input(wl)
     N = rho64.size
     stream = torch.cuda.current_stream()
@@ -218,7 +268,7 @@ def run_gpu(args):
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t_max, 5), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": list(wl["shape"]), "atoms": wl["n_atoms"],
+        "config": {"workload": args.workload, "grid": list(wl["shape"]), "atoms": wl["n_atoms"],
                    "n_knots": wl["n_knots"], "functional": "TF+vW+H+PP+LWT(exact V)",
                    "reductions": "f64", "l2": "flushed (512 MB write) before every timed step",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
@@ -230,7 +280,7 @@ def run_gpu(args):
         "gpu_launches": int(sum(n for n, _ in prof.values())),
         "e2e": e2e, "clocks": clocks,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == WORKLOAD:
         line["cpu_baseline"] = cpu_baseline(wl, rho64, args.cpu_budget)
         eo = line["cpu_baseline"].get("E_total")
         if eo is not None:
@@ -335,6 +385,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="fcc-al-256/128 (default), fcc-al-4/32, mg147/192, fcc-al-108-batch")
+    ap.add_argument("--snapshots", type=int, default=64)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

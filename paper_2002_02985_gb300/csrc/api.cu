@@ -93,6 +93,9 @@ struct ofdft_grid {
     bool have_ions = false;
     bool vext_fresh32 = false, vext_fresh64 = false;
     double2 *ph = nullptr;       // phase tables [n_ions][n0 + n1 + n2h]
+    float2 *ph32 = nullptr;      // the same rounded to FP32 (FP32-mixed kernels)
+    float4 *gc = nullptr;        // per-G scratch of the FP32-mixed force kernel
+    long long gc_len = 0;
     int *d_species = nullptr;
     double *d_Z = nullptr, *d_rc = nullptr;
     double *h_pinned = nullptr;  // 64 doubles of pinned host memory
@@ -274,7 +277,7 @@ template <typename T> int ensure_vext(ofdft_grid *g) {
     if (!w.vext) CK(cudaMalloc(&w.vext, g->NH * sizeof(C)), "cudaMalloc V_ext(G)");
     IonArgs a = ion_args(g);
     cudaError_t e;
-    if (sizeof(T) == 4) e = launch_vext(a, nullptr, (float2 *)w.vext, g->stream);
+    if (sizeof(T) == 4) e = launch_vext(a, nullptr, (float2 *)w.vext, g->stream, g->ph32);
     else e = launch_vext(a, (double2 *)w.vext, nullptr, g->stream);
     CK(e, "structure factor kernel");
     fresh = true;
@@ -484,25 +487,41 @@ template <typename T> int forces_impl(ofdft_grid *g, const T *rho, double *F) {
     CK(launch_axis0_fft<T>(w.chan, g->n[0], (long long)g->n[1] * g->n2h, g->plan[0], w.tw[0], w.TW0, w.thr_ax0,
                            1.0 / (double)g->N, g->stream),
        "forward transform along n0");
-    const int nchunk = 16;
-    std::vector<double> part((size_t)g->n_ions * nchunk * 3);
+    // FP32-mixed: FP32 phase products with FP64 accumulation (per-G scratch of
+    // 32 bytes per half-spectrum point, allowed up to 2 GB); FP64: all-FP64 kernel
+    const bool fast = sizeof(T) == 4 && g->NH <= (64LL << 20);
+    const int nchunk = fast ? std::max(16, 1024 / ((g->n_ions + 7) / 8)) : 16;
+    const int nsp = fast ? g->n_species : 1;
+    std::vector<double> part((size_t)nsp * g->n_ions * nchunk * 3);
     double *dpart = w.part_misc;
     bool own = false;
-    if ((size_t)g->n_ions * nchunk * 3 > 4096) {
+    if (part.size() > 4096) {
         CK(cudaMalloc(&dpart, part.size() * sizeof(double)), "cudaMalloc force partials");
         own = true;
     }
     IonArgs ia = ion_args(g);
-    CK(launch_forces<C>(ia, w.chan, dpart, nchunk, g->stream), "forces kernel");
+    if (fast) {
+        if (g->gc_len < g->NH) {
+            cudaFree(g->gc);
+            g->gc = nullptr;
+            g->gc_len = 0;
+            CK(cudaMalloc(&g->gc, 2 * (size_t)g->NH * sizeof(float4)), "cudaMalloc force scratch");
+            g->gc_len = g->NH;
+        }
+        CK(launch_forces_fast(ia, (const float2 *)w.chan, g->ph32, g->gc, dpart, nchunk, g->stream), "forces kernel");
+    } else {
+        CK(launch_forces<C>(ia, w.chan, dpart, nchunk, g->stream), "forces kernel");
+    }
     CK(cudaMemcpyAsync(part.data(), dpart, part.size() * sizeof(double), cudaMemcpyDeviceToHost, g->stream),
        "copy forces");
     CK(cudaStreamSynchronize(g->stream), "stream synchronize");
     if (own) cudaFree(dpart);
     for (int I = 0; I < g->n_ions; I++)
         for (int d = 0; d < 3; d++) {
-            double s = 0.0;
-            for (int c = 0; c < nchunk; c++) s += part[((size_t)I * nchunk + c) * 3 + d];
-            F[3 * I + d] = s;
+            double sum = 0.0;
+            for (int sp = 0; sp < nsp; sp++)
+                for (int c = 0; c < nchunk; c++) sum += part[(((size_t)sp * g->n_ions + I) * nchunk + c) * 3 + d];
+            F[3 * I + d] = sum;
         }
     return OFDFT_OK;
 }
@@ -782,6 +801,8 @@ int ofdft_grid_destroy(ofdft_grid *g) {
     free_ws(g->w32);
     free_ws(g->w64);
     cudaFree(g->ph);
+    cudaFree(g->ph32);
+    cudaFree(g->gc);
     cudaFree(g->d_species);
     cudaFree(g->d_Z);
     cudaFree(g->d_rc);
@@ -801,13 +822,16 @@ int ofdft_set_ions(ofdft_grid *g, const ofdft_ions *ions, const ofdft_species *s
     const int n = ions->n;
     if (n != g->n_ions || sp->n_species != g->n_species) {
         cudaFree(g->ph);
+        cudaFree(g->ph32);
         cudaFree(g->d_species);
         cudaFree(g->d_Z);
         cudaFree(g->d_rc);
         g->ph = nullptr;
+        g->ph32 = nullptr;
         g->d_species = nullptr;
         g->d_Z = g->d_rc = nullptr;
         CK(cudaMalloc(&g->ph, (size_t)n * (g->n[0] + g->n[1] + g->n2h) * sizeof(double2)), "cudaMalloc phases");
+        CK(cudaMalloc(&g->ph32, (size_t)n * (g->n[0] + g->n[1] + g->n2h) * sizeof(float2)), "cudaMalloc phases");
         CK(cudaMalloc(&g->d_species, n * sizeof(int)), "cudaMalloc species");
         CK(cudaMalloc(&g->d_Z, sp->n_species * sizeof(double)), "cudaMalloc Z");
         CK(cudaMalloc(&g->d_rc, sp->n_species * sizeof(double)), "cudaMalloc rc");
@@ -839,6 +863,7 @@ int ofdft_set_ions(ofdft_grid *g, const ofdft_ions *ions, const ofdft_species *s
         off += (size_t)n * na[ax];
     }
     CK(cudaMemcpy(g->ph, ph.data(), ph.size() * sizeof(double2), cudaMemcpyHostToDevice), "upload phases");
+    CK(launch_round_phases(g->ph, g->ph32, (long long)ph.size(), g->stream), "round phases");
     CK(cudaMemcpy(g->d_species, g->species.data(), n * sizeof(int), cudaMemcpyHostToDevice), "upload species");
     CK(cudaMemcpy(g->d_Z, g->Z.data(), g->n_species * sizeof(double), cudaMemcpyHostToDevice), "upload Z");
     CK(cudaMemcpy(g->d_rc, g->rc.data(), g->n_species * sizeof(double), cudaMemcpyHostToDevice), "upload rc");

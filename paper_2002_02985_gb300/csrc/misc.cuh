@@ -17,7 +17,14 @@ struct IonArgs {
     const double *Z, *rc;            // [n_species]
 };
 
-cudaError_t launch_vext(const IonArgs &a, double2 *vext64, float2 *vext32, cudaStream_t s);
+// vext64 != null: FP64 build; otherwise the FP32 copy from FP32 phase products
+// (ph32 = FP32 copy of the phase tables) with FP64 accumulation of 8-ion groups
+cudaError_t launch_vext(const IonArgs &a, double2 *vext64, float2 *vext32, cudaStream_t s,
+                        const float2 *ph32 = nullptr);
+cudaError_t launch_round_phases(const double2 *in, float2 *out, long long n, cudaStream_t s);
+// FP32-mixed forces: gc scratch of 2 NH float4; partials [n_species][n_ions][nchunk][3]
+cudaError_t launch_forces_fast(const IonArgs &a, const float2 *rhohat, const float2 *ph32, float4 *gc,
+                               double *partials, int nchunk, cudaStream_t st);
 
 // forces from the normalised half spectrum rho_hat (FP64 or FP32 complex)
 template <typename C>

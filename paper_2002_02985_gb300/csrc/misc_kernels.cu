@@ -53,14 +53,66 @@ __global__ void __launch_bounds__(256) vext_kernel(IonArgs a, double2 *v64, floa
     if (v32) v32[e] = make_float2((float)acc.x, (float)acc.y);
 }
 
-cudaError_t launch_vext(const IonArgs &a, double2 *vext64, float2 *vext32, cudaStream_t s) {
+// FP32-mixed variant: the per-ion phase products e^{-iG.R} = P0 P1 P2 are formed
+// in FP32 from the FP64 tables rounded once; groups of 8 ions are summed in
+// FP32 and the groups in FP64 (GB300's FP64 rate is a small fraction of FP32's).
+__global__ void __launch_bounds__(256) vext_fast_kernel(IonArgs a, const float2 *ph32, float2 *v32) {
     const long long NH = (long long)a.n0 * a.n1 * a.n2h;
-    vext_kernel<<<(unsigned)((NH + 255) / 256), 256, 0, s>>>(a, vext64, vext32);
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= NH) return;
+    double gx, gy, gz;
+    int k0, k1, k2;
+    gvec_of(a, e, gx, gy, gz, k0, k1, k2);
+    const double q2 = gx * gx + gy * gy + gz * gz;
+    const float2 *P0 = ph32, *P1 = ph32 + (size_t)a.n_ions * a.n0, *P2 = P1 + (size_t)a.n_ions * a.n1;
+    double ax = 0.0, ay = 0.0;
+    for (int s = 0; s < a.n_species; s++) {
+        double Sx = 0.0, Sy = 0.0;
+        float gxs = 0.f, gys = 0.f;
+        int cnt = 0;
+        for (int I = 0; I < a.n_ions; I++) {
+            if (a.species[I] != s) continue;
+            const float2 p0 = P0[(size_t)I * a.n0 + k0], p1 = P1[(size_t)I * a.n1 + k1], p2 = P2[(size_t)I * a.n2h + k2];
+            const float rx = p0.x * p1.x - p0.y * p1.y, ry = p0.x * p1.y + p0.y * p1.x;
+            gxs += rx * p2.x - ry * p2.y;
+            gys += rx * p2.y + ry * p2.x;
+            if (++cnt == 8) {
+                Sx += (double)gxs;
+                Sy += (double)gys;
+                gxs = gys = 0.f;
+                cnt = 0;
+            }
+        }
+        Sx += (double)gxs;
+        Sy += (double)gys;
+        const double v = pp_form(q2, a.Z[s], a.rc[s]) / a.omega;
+        ax += v * Sx;
+        ay += v * Sy;
+    }
+    v32[e] = make_float2((float)ax, (float)ay);
+}
+
+cudaError_t launch_vext(const IonArgs &a, double2 *vext64, float2 *vext32, cudaStream_t s, const float2 *ph32) {
+    const long long NH = (long long)a.n0 * a.n1 * a.n2h;
+    if (ph32 && vext32 && !vext64)
+        vext_fast_kernel<<<(unsigned)((NH + 255) / 256), 256, 0, s>>>(a, ph32, vext32);
+    else
+        vext_kernel<<<(unsigned)((NH + 255) / 256), 256, 0, s>>>(a, vext64, vext32);
     return cudaGetLastError();
 }
 
-// F_I = -sum_G w G v(|G|) Im[conj(rho_hat) e^{-iG.R_I}]; block (I, chunk) sums a
-// contiguous range of the half spectrum and writes one partial per component.
+// FP32 copy of the FP64 phase tables
+__global__ void round_phases_kernel(const double2 *in, float2 *out, long long n) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+cudaError_t launch_round_phases(const double2 *in, float2 *out, long long n, cudaStream_t s) {
+    round_phases_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+// Forces, FP64 path: F_I = -sum_G w G v(|G|) Im[conj(rho_hat) e^{-iG.R_I}]; block
+// (I, chunk) sums a contiguous range of the half spectrum, one partial per component.
 template <typename C>
 __global__ void __launch_bounds__(256) forces_kernel(IonArgs a, const C *rh, double *part, int nchunk) {
     __shared__ double sd[32];
@@ -104,6 +156,95 @@ cudaError_t launch_forces(const IonArgs &a, const C *rhohat, double *partials, i
 }
 template cudaError_t launch_forces<float2>(const IonArgs &, const float2 *, double *, int, cudaStream_t);
 template cudaError_t launch_forces<double2>(const IonArgs &, const double2 *, double *, int, cudaStream_t);
+
+// Forces, FP32-mixed path.  Per G (once, not per ion): c(G) = -w v_s(|G|) conj(rho_hat)
+// and G itself in FP32.  Then block (chunk, ion group of 8): each thread walks its
+// G values, forms e^{-iG.R_I} from the FP32 phase tables and accumulates
+// G Im[c e^{-iG.R}] in FP32 over 8 consecutive G before adding to FP64.
+__global__ void __launch_bounds__(256) force_gprep_kernel(IonArgs a, const float2 *rh, float4 *gc, int s) {
+    const long long NH = (long long)a.n0 * a.n1 * a.n2h;
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= NH) return;
+    double gx, gy, gz;
+    int k0, k1, k2;
+    gvec_of(a, e, gx, gy, gz, k0, k1, k2);
+    const double q2 = gx * gx + gy * gy + gz * gz;
+    float cr = 0.f, ci = 0.f;
+    if (q2 > 0.0) {
+        const double w = (k2 == 0 || (a.n2 % 2 == 0 && 2 * k2 == a.n2)) ? 1.0 : 2.0;
+        const double f = -w * pp_form(q2, a.Z[s], a.rc[s]);
+        cr = (float)(f * rh[e].x);
+        ci = (float)(-f * rh[e].y);          // c = f conj(rho_hat)
+    }
+    gc[2 * e] = make_float4((float)gx, (float)gy, (float)gz, 0.f);
+    gc[2 * e + 1] = make_float4(cr, ci, 0.f, 0.f);
+}
+
+__global__ void __launch_bounds__(256) forces_fast_kernel(IonArgs a, const float2 *ph32, const float4 *gc, int s,
+                                                           double *part, int nchunk) {
+    __shared__ double sd[32];
+    const int chunk = blockIdx.x, g0 = blockIdx.y * 8;
+    const long long NH = (long long)a.n0 * a.n1 * a.n2h;
+    const long long per = (NH + nchunk - 1) / nchunk;
+    const long long e0 = chunk * per, e1 = (e0 + per < NH) ? e0 + per : NH;
+    const float2 *P0 = ph32, *P1 = ph32 + (size_t)a.n_ions * a.n0, *P2 = P1 + (size_t)a.n_ions * a.n1;
+    double F[8][3];
+    float f32[8][3];
+#pragma unroll
+    for (int q = 0; q < 8; q++)
+#pragma unroll
+        for (int d = 0; d < 3; d++) F[q][d] = 0.0, f32[q][d] = 0.f;
+    int cnt = 0;
+    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const int k2 = (int)(e % a.n2h);
+        const long long r = e / a.n2h;
+        const int k1 = (int)(r % a.n1), k0 = (int)(r / a.n1);
+        const float4 G = gc[2 * e], c4 = gc[2 * e + 1];
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const int I = g0 + q;
+            if (I >= a.n_ions || a.species[I] != s) continue;
+            const float2 p0 = P0[(size_t)I * a.n0 + k0], p1 = P1[(size_t)I * a.n1 + k1],
+                         p2 = P2[(size_t)I * a.n2h + k2];
+            const float rx = p0.x * p1.x - p0.y * p1.y, ry = p0.x * p1.y + p0.y * p1.x;
+            const float px = rx * p2.x - ry * p2.y, py = rx * p2.y + ry * p2.x;
+            const float im = c4.x * py + c4.y * px;            // Im(c p)
+            f32[q][0] += im * G.x;
+            f32[q][1] += im * G.y;
+            f32[q][2] += im * G.z;
+        }
+        if (++cnt == 8) {
+            cnt = 0;
+#pragma unroll
+            for (int q = 0; q < 8; q++)
+#pragma unroll
+                for (int d = 0; d < 3; d++) F[q][d] += (double)f32[q][d], f32[q][d] = 0.f;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; q++)
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            const double v = block_sum(F[q][d] + (double)f32[q][d], sd);
+            if (threadIdx.x == 0 && g0 + q < a.n_ions)
+                part[(((size_t)(g0 + q)) * nchunk + chunk) * 3 + d] = v;
+        }
+}
+
+cudaError_t launch_forces_fast(const IonArgs &a, const float2 *rhohat, const float2 *ph32, float4 *gc,
+                               double *partials, int nchunk, cudaStream_t st) {
+    const long long NH = (long long)a.n0 * a.n1 * a.n2h;
+    cudaError_t e = cudaSuccess;
+    for (int s = 0; s < a.n_species; s++) {
+        force_gprep_kernel<<<(unsigned)((NH + 255) / 256), 256, 0, st>>>(a, rhohat, gc, s);
+        // ions of other species write nothing for this species: their partials come from
+        // their own species' pass (the kernel skips them)
+        dim3 g(nchunk, (a.n_ions + 7) / 8);
+        forces_fast_kernel<<<g, 256, 0, st>>>(a, ph32, gc, s, partials + (size_t)s * a.n_ions * nchunk * 3, nchunk);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return e;
+}
 
 // ---------------------------------------------------------------- plain FFT along n0
 template <typename T, int CAP>
