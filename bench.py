@@ -258,7 +258,7 @@ def run_gpu(args):
     avg_s = tot_ms / max(1, launches) * 1e-3
     peak, kind = peaks()
     achieved = alg / avg_s / 1e9
-    traffic = measured_traffic(name)
+    traffic = measured_traffic(name, args.workload)
     roof = {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1), "peak": peak, "peak_kind": kind,
             "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
             "algorithmic_bytes_per_launch": alg, "avg_launch_ms": round(avg_s * 1e3, 5)}
@@ -313,17 +313,30 @@ def algorithmic_bytes(kernel, wl, esize):
     return int(table.get(kernel, 0))
 
 
-def measured_traffic(kernel):
-    """dram bytes per launch from the committed ncu summary of the same kernel, if any."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(p):
-        try:
-            d = json.load(open(p))
-            if kernel in d:
-                return d[kernel]
-        except Exception:
-            pass
-    return None
+def kernel_source_sha():
+    import hashlib
+    d = os.path.join(ROOT, "paper_2002_02985_gb300", "csrc")
+    names = sorted(f for f in os.listdir(d) if f.endswith(".cu")) + sorted(f for f in os.listdir(d) if f.endswith(".cuh"))
+    h = hashlib.sha256()
+    for f in names:
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel, workload):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
+    committed ncu summary profiles/<kernel>_<workload>.md; None when the kernel
+    sources changed since that capture (its kernel_source_sha differs)."""
+    p = os.path.join(ROOT, "profiles", "%s_%s.md" % (kernel, workload.replace("/", "-")))
+    if not os.path.exists(p):
+        return None
+    sha, traffic = None, None
+    for line in open(p):
+        if line.startswith("kernel_source_sha:"):
+            sha = line.split(":", 1)[1].strip()
+        if line.startswith("| traffic_bytes_per_launch |") and traffic is None:
+            traffic = int(line.split("|")[2].strip())
+    return traffic if sha == kernel_source_sha() else None
 
 
 def cpu_baseline(wl, rho64, budget_s):
