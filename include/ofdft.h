@@ -121,6 +121,14 @@ int ofdft_grid_destroy(ofdft_grid *g);
  * (Sec. 2.5).  Copies the host arrays; may be called again for new positions. */
 int ofdft_set_ions(ofdft_grid *g, const ofdft_ions *ions, const ofdft_species *sp);
 
+/* Same as ofdft_set_ions, but the structure factor is the smooth particle-mesh
+ * Ewald approximation of even B-spline order `order` (4..16), as the paper uses
+ * for more than ~1000 ions (Sec. 2.5; Essmann et al. 1995):
+ *   S(G) ~ prod_a conj(b_a(m_a)) sum_k Q(k) e^{-iG.r_k},  Q(k) = sum_I prod_a M_p(u_aI - k_a),
+ * spread with fixed-point atomics (bit-reproducible).  Forces are then the exact
+ * derivative of the PME energy (B-spline gather).  Needs every n_a >= order. */
+int ofdft_set_ions_pme(ofdft_grid *g, const ofdft_ions *ions, const ofdft_species *sp, int order);
+
 /* One energy + potential evaluation (Eq. efunc; Eq. euler for V; Sec. 2.3 s1-s4).
  * rho_dev: device [N] float/double (precision of f), >= 0.
  * E_out:   HOST double[6] = {total, TF, vW, NL, H, PP} (Ha); may be NULL.

@@ -116,14 +116,20 @@ class Grid:
         except Exception:
             pass
 
-    def set_ions(self, positions, species, Z, rc):
+    def set_ions(self, positions, species, Z, rc, pme_order: int = 0):
+        """Ions and their analytic local PP; pme_order > 0 (even, 4..16) selects the
+        smooth-PME structure factor instead of the direct sum."""
         pos = np.ascontiguousarray(np.asarray(positions, dtype=np.float64).reshape(-1, 3))
         spc = np.ascontiguousarray(np.asarray(species, dtype=np.int32).reshape(-1))
         Zs = np.ascontiguousarray(np.asarray(Z, dtype=np.float64).reshape(-1))
         rcs = np.ascontiguousarray(np.asarray(rc, dtype=np.float64).reshape(-1))
         ions = L.CIons(len(pos), pos.ctypes.data_as(ct.POINTER(ct.c_double)), spc.ctypes.data_as(ct.POINTER(ct.c_int)))
         sp = L.CSpecies(len(Zs), Zs.ctypes.data_as(ct.POINTER(ct.c_double)), rcs.ctypes.data_as(ct.POINTER(ct.c_double)))
-        _check(self.lib, self.lib.ofdft_set_ions(self.h, ct.byref(ions), ct.byref(sp)), self.h)
+        if pme_order:
+            st = self.lib.ofdft_set_ions_pme(self.h, ct.byref(ions), ct.byref(sp), int(pme_order))
+        else:
+            st = self.lib.ofdft_set_ions(self.h, ct.byref(ions), ct.byref(sp))
+        _check(self.lib, st, self.h)
         self.n_ions = len(pos)
 
     def _field(self, t, func: Functional):

@@ -30,7 +30,7 @@ EXPORTS = (
     "ofdft_energy_potential_async", "ofdft_forces", "ofdft_optimize_density",
     "ofdft_energy_potential_batched", "ofdft_status_string", "ofdft_last_error", "ofdft_version",
     "ofdft_profile_enable", "ofdft_profile_reset", "ofdft_profile_read",
-    "ofdft_tf_energy_potential_noalloc",
+    "ofdft_tf_energy_potential_noalloc", "ofdft_set_ions_pme",
 )
 NOALLOC_MAX_POINTS = 8388608
 
@@ -71,6 +71,7 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.ofdft_grid_create.argtypes = [ct.POINTER(D), ct.POINTER(I), P, ct.POINTER(P)]
     lib.ofdft_grid_destroy.argtypes = [P]
     lib.ofdft_set_ions.argtypes = [P, ct.POINTER(CIons), ct.POINTER(CSpecies)]
+    lib.ofdft_set_ions_pme.argtypes = [P, ct.POINTER(CIons), ct.POINTER(CSpecies), I]
     lib.ofdft_energy_potential.argtypes = [P, V, ct.POINTER(CFunctional), ct.POINTER(D), V]
     lib.ofdft_energy_potential_async.argtypes = [P, V, ct.POINTER(CFunctional), V, V]
     lib.ofdft_forces.argtypes = [P, V, I, ct.POINTER(D)]

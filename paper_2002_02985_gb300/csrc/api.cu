@@ -11,6 +11,7 @@
 #include "../../include/ofdft.h"
 #include "eval.cuh"
 #include "misc.cuh"
+#include "pme.cuh"
 
 using namespace ofdft;
 
@@ -96,6 +97,14 @@ struct ofdft_grid {
     float2 *ph32 = nullptr;      // the same rounded to FP32 (FP32-mixed kernels)
     float4 *gc = nullptr;        // per-G scratch of the FP32-mixed force kernel
     long long gc_len = 0;
+    // smooth PME (ofdft_set_ions_pme): order > 0 selects it for V_ext(G) and forces
+    int pme_order = 0;
+    double2 *pmeB = nullptr;               // conj b_a tables [n0 | n1 | n2h]
+    double *d_pos = nullptr;               // device positions
+    unsigned long long *Qfix = nullptr;    // fixed-point charge grid (N)
+    void *pme_real = nullptr;              // real field scratch (N, largest precision used)
+    size_t pme_real_bytes = 0;
+    std::vector<int> species_count;
     int *d_species = nullptr;
     double *d_Z = nullptr, *d_rc = nullptr;
     double *h_pinned = nullptr;  // 64 doubles of pinned host memory
@@ -269,12 +278,20 @@ IonArgs ion_args(ofdft_grid *g) {
     return a;
 }
 
+template <typename T> int build_vext_pme(ofdft_grid *g, Workspace<T> &w);
+
 template <typename T> int ensure_vext(ofdft_grid *g) {
     typedef typename Vec2<T>::type C;
     Workspace<T> &w = ws<T>(g);
     bool &fresh = sizeof(T) == 4 ? g->vext_fresh32 : g->vext_fresh64;
     if (fresh) return OFDFT_OK;
     if (!w.vext) CK(cudaMalloc(&w.vext, g->NH * sizeof(C)), "cudaMalloc V_ext(G)");
+    if (g->pme_order > 0) {
+        int rc = build_vext_pme<T>(g, w);
+        if (rc) return rc;
+        fresh = true;
+        return OFDFT_OK;
+    }
     IonArgs a = ion_args(g);
     cudaError_t e;
     if (sizeof(T) == 4) e = launch_vext(a, nullptr, (float2 *)w.vext, g->stream, g->ph32);
@@ -465,12 +482,128 @@ int eval_sync(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, doub
     return OFDFT_OK;
 }
 
+// ---------------------------------------------------------------- plain transforms
+// EvalArgs for a plain transform of one real field through slot CH_HPP (forward:
+// stats + rows + n1 pencils; the n0 pass is done by launch_axis0_fft).
+template <typename T> EvalArgs<T> plain_args(ofdft_grid *g, Workspace<T> &w, const T *field) {
+    EvalArgs<T> a;
+    std::memset(&a, 0, sizeof(a));
+    a.n0 = g->n[0]; a.n1 = g->n[1]; a.n2 = g->n[2]; a.n2h = g->n2h; a.N = g->N; a.NH = g->NH;
+    a.omega = g->omega; a.dV = g->dV;
+    a.rho = field; a.chan = w.chan; a.terms = OFDFT_TERM_HARTREE; a.floor_ = (T)1e-30;
+    a.scal = w.scal; a.knots_d = w.knots_d; a.knots_t = w.knots_t; a.invdk_t = w.invdk_t;
+    a.part_stats = w.part_stats; a.part_minmax = w.part_minmax; a.energies = w.energies;
+    a.part_ax0 = w.part_ax0; a.part_row = w.part_row;
+    a.nb_stats = 2 * g->nsm; a.nb_ax0 = w.nb_ax0; a.nb_row = w.nb_row;
+    a.p0 = g->plan[0]; a.p1 = g->plan[1]; a.p2 = g->plan[2];
+    a.tw0 = w.tw[0]; a.tw1 = w.tw[1]; a.tw2 = w.tw[2];
+    a.Brow = w.Brow; a.thr_rowf = w.thr_rowf; a.thr_rowi = w.thr_rowi;
+    a.TW1 = w.TW1; a.thr_p1 = w.thr_p1; a.TW0 = w.TW0; a.thr_ax0 = w.thr_ax0;
+    a.nfwd = 1; a.fwd_ch[0] = CH_HPP; a.ncol = 1; a.col_ch[0] = CH_HPP;
+    return a;
+}
+
+// normalised half spectrum (1/N) of a real field into slot CH_HPP (G = 0 is not kept)
+template <typename T> int forward_plain(ofdft_grid *g, Workspace<T> &w, const T *field) {
+    EvalArgs<T> a = plain_args<T>(g, w, field);
+    CK(launch_forward_rows_cols<T>(a, w.ks, g->stream), "forward transform");
+    CK(launch_axis0_fft<T>(w.chan, g->n[0], (long long)g->n[1] * g->n2h, g->plan[0], w.tw[0], w.TW0, w.thr_ax0,
+                           1.0 / (double)g->N, g->stream, -1),
+       "forward transform along n0");
+    return OFDFT_OK;
+}
+
+// real field out = sum_G F(G) e^{iG.r} of the half spectrum F in slot `slot` (destroys it)
+template <typename T> int inverse_plain(ofdft_grid *g, Workspace<T> &w, int slot, T *out, const T *any_field) {
+    typedef typename Vec2<T>::type C;
+    EvalArgs<T> a = plain_args<T>(g, w, any_field);
+    a.terms = 0;
+    a.V = out;
+    a.ncol_inv = 1;
+    a.col_inv_ch[0] = slot;
+    a.ninv = 1;
+    a.inv_ch[0] = slot;
+    a.inv_kind[0] = CONS_ADD;
+    CK(launch_axis0_fft<T>((C *)w.chan + (size_t)slot * g->NH, g->n[0], (long long)g->n[1] * g->n2h, g->plan[0],
+                           w.tw[0], w.TW0, w.thr_ax0, 1.0, g->stream, +1),
+       "inverse transform along n0");
+    CK(launch_inverse_cols_rows<T>(a, w.ks, g->stream), "inverse transform");
+    return OFDFT_OK;
+}
+
+template <typename T> int ensure_pme_buffers(ofdft_grid *g) {
+    if (!g->Qfix) CK(cudaMalloc(&g->Qfix, (size_t)g->N * sizeof(unsigned long long)), "cudaMalloc PME grid");
+    if (g->pme_real_bytes < (size_t)g->N * sizeof(T)) {
+        cudaFree(g->pme_real);
+        g->pme_real = nullptr;
+        g->pme_real_bytes = 0;
+        CK(cudaMalloc(&g->pme_real, (size_t)g->N * sizeof(T)), "cudaMalloc PME field");
+        g->pme_real_bytes = (size_t)g->N * sizeof(T);
+    }
+    return OFDFT_OK;
+}
+
+PmeArgs pme_args(ofdft_grid *g, int s) {
+    PmeArgs a;
+    a.n0 = g->n[0];
+    a.n1 = g->n[1];
+    a.n2 = g->n[2];
+    a.n2h = g->n2h;
+    a.n_ions = g->n_ions;
+    a.p = g->pme_order;
+    a.s = s;
+    for (int i = 0; i < 9; i++) a.recip[i] = g->recip[i];
+    a.pos = g->d_pos;
+    a.species = g->d_species;
+    return a;
+}
+
+// V_ext(G) = (1/Omega) sum_s v_s(|G|) S_s(G) with the PME structure factor
+template <typename T> int build_vext_pme(ofdft_grid *g, Workspace<T> &w) {
+    typedef typename Vec2<T>::type C;
+    int rc = ensure_pme_buffers<T>(g);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(g->Qfix, 0, (size_t)g->N * sizeof(unsigned long long), g->stream), "memset");
+    for (int s = 0; s < g->n_species; s++) {
+        PmeArgs pa = pme_args(g, s);
+        CK(pme_spread(pa, g->Qfix, g->stream), "PME spread");
+        CK(pme_fixed_to_real<T>(g->Qfix, (T *)g->pme_real, g->N, g->stream), "PME grid");
+        if ((rc = forward_plain<T>(g, w, (const T *)g->pme_real))) return rc;
+        CK(pme_vext<C>(pa, (const C *)w.chan, g->pmeB, g->Z[s], g->rc[s], (double)g->species_count[s],
+                       (double)g->N, g->omega, (C *)w.vext, s == 0, g->stream),
+           "PME V_ext");
+    }
+    return OFDFT_OK;
+}
+
+template <typename T> int forces_pme(ofdft_grid *g, Workspace<T> &w, const T *rho, double *F) {
+    typedef typename Vec2<T>::type C;
+    int rc = ensure_pme_buffers<T>(g);
+    if (rc) return rc;
+    if ((rc = forward_plain<T>(g, w, rho))) return rc;                  // rho_hat in slot 0
+    double *dF = nullptr;
+    CK(cudaMalloc(&dF, (size_t)3 * g->n_ions * sizeof(double)), "cudaMalloc forces");
+    for (int s = 0; s < g->n_species; s++) {
+        PmeArgs pa = pme_args(g, s);
+        C *slot1 = (C *)w.chan + g->NH;
+        CK(pme_force_field<C>(pa, (const C *)w.chan, g->pmeB, g->Z[s], g->rc[s], slot1, g->stream), "PME field");
+        if ((rc = inverse_plain<T>(g, w, 1, (T *)g->pme_real, rho))) { cudaFree(dF); return rc; }
+        CK(pme_gather<T>(pa, (const T *)g->pme_real, dF, g->stream), "PME gather");
+    }
+    cudaError_t e = cudaMemcpyAsync(F, dF, (size_t)3 * g->n_ions * sizeof(double), cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    cudaFree(dF);
+    CK(e, "copy forces");
+    return OFDFT_OK;
+}
+
 // ---------------------------------------------------------------- forces
 template <typename T> int forces_impl(ofdft_grid *g, const T *rho, double *F) {
     typedef typename Vec2<T>::type C;
     int rc = ensure_ws<T>(g, 3);
     if (rc) return rc;
     Workspace<T> &w = ws<T>(g);
+    if (g->pme_order > 0) return forces_pme<T>(g, w, rho, F);
     EvalArgs<T> a;
     std::memset(&a, 0, sizeof(a));
     a.n0 = g->n[0]; a.n1 = g->n[1]; a.n2 = g->n[2]; a.n2h = g->n2h; a.N = g->N; a.NH = g->NH;
@@ -803,6 +936,10 @@ int ofdft_grid_destroy(ofdft_grid *g) {
     cudaFree(g->ph);
     cudaFree(g->ph32);
     cudaFree(g->gc);
+    cudaFree(g->pmeB);
+    cudaFree(g->d_pos);
+    cudaFree(g->Qfix);
+    cudaFree(g->pme_real);
     cudaFree(g->d_species);
     cudaFree(g->d_Z);
     cudaFree(g->d_rc);
@@ -811,8 +948,12 @@ int ofdft_grid_destroy(ofdft_grid *g) {
     return OFDFT_OK;
 }
 
-int ofdft_set_ions(ofdft_grid *g, const ofdft_ions *ions, const ofdft_species *sp) {
-    if (!g) return OFDFT_ERR_INVALID_ARG;
+}  // extern "C"
+
+namespace {
+
+// common part of both ion set-ups: validation, host copies, device species/Z/rc
+int store_ions(ofdft_grid *g, const ofdft_ions *ions, const ofdft_species *sp) {
     if (!ions || !sp || ions->n < 1 || !ions->pos || !ions->species || sp->n_species < 1 || !sp->Z || !sp->rc)
         return fail(g, OFDFT_ERR_INVALID_ARG, "ions/species");
     for (int i = 0; i < ions->n; i++)
@@ -823,32 +964,56 @@ int ofdft_set_ions(ofdft_grid *g, const ofdft_ions *ions, const ofdft_species *s
     if (n != g->n_ions || sp->n_species != g->n_species) {
         cudaFree(g->ph);
         cudaFree(g->ph32);
+        cudaFree(g->d_pos);
         cudaFree(g->d_species);
         cudaFree(g->d_Z);
         cudaFree(g->d_rc);
         g->ph = nullptr;
         g->ph32 = nullptr;
+        g->d_pos = nullptr;
         g->d_species = nullptr;
         g->d_Z = g->d_rc = nullptr;
-        CK(cudaMalloc(&g->ph, (size_t)n * (g->n[0] + g->n[1] + g->n2h) * sizeof(double2)), "cudaMalloc phases");
-        CK(cudaMalloc(&g->ph32, (size_t)n * (g->n[0] + g->n[1] + g->n2h) * sizeof(float2)), "cudaMalloc phases");
         CK(cudaMalloc(&g->d_species, n * sizeof(int)), "cudaMalloc species");
         CK(cudaMalloc(&g->d_Z, sp->n_species * sizeof(double)), "cudaMalloc Z");
         CK(cudaMalloc(&g->d_rc, sp->n_species * sizeof(double)), "cudaMalloc rc");
     }
     g->n_ions = n;
     g->n_species = sp->n_species;
-    g->pos.assign(ions->pos, ions->pos + 3 * n);
+    g->pos.assign(ions->pos, ions->pos + 3 * (size_t)n);
     g->species.assign(ions->species, ions->species + n);
     g->Z.assign(sp->Z, sp->Z + sp->n_species);
     g->rc.assign(sp->rc, sp->rc + sp->n_species);
+    g->species_count.assign(sp->n_species, 0);
+    for (int i = 0; i < n; i++) g->species_count[g->species[i]]++;
+    CK(cudaMemcpy(g->d_species, g->species.data(), n * sizeof(int), cudaMemcpyHostToDevice), "upload species");
+    CK(cudaMemcpy(g->d_Z, g->Z.data(), g->n_species * sizeof(double), cudaMemcpyHostToDevice), "upload Z");
+    CK(cudaMemcpy(g->d_rc, g->rc.data(), g->n_species * sizeof(double), cudaMemcpyHostToDevice), "upload rc");
+    g->have_ions = true;
+    g->vext_fresh32 = g->vext_fresh64 = false;
+    return OFDFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ofdft_set_ions(ofdft_grid *g, const ofdft_ions *ions, const ofdft_species *sp) {
+    if (!g) return OFDFT_ERR_INVALID_ARG;
+    int rc = store_ions(g, ions, sp);
+    if (rc) return rc;
+    g->pme_order = 0;
+    const int n = g->n_ions;
+    if (!g->ph) {
+        CK(cudaMalloc(&g->ph, (size_t)n * (g->n[0] + g->n[1] + g->n2h) * sizeof(double2)), "cudaMalloc phases");
+        CK(cudaMalloc(&g->ph32, (size_t)n * (g->n[0] + g->n[1] + g->n2h) * sizeof(float2)), "cudaMalloc phases");
+    }
     // per-axis phase tables e^{-2 pi i m_a f_a}, f = R . inv(cell) (fractional)
     const int na[3] = {g->n[0], g->n[1], g->n2h};
     std::vector<double2> ph((size_t)n * (na[0] + na[1] + na[2]));
     size_t off = 0;
     for (int ax = 0; ax < 3; ax++) {
         for (int I = 0; I < n; I++) {
-            const double *R = &g->pos[3 * I];
+            const double *R = &g->pos[3 * (size_t)I];
             // fractional coordinate along a_ax: R . b_ax
             const double fr = R[0] * g->recip[3 * ax] + R[1] * g->recip[3 * ax + 1] + R[2] * g->recip[3 * ax + 2];
             for (int k = 0; k < na[ax]; k++) {
@@ -864,11 +1029,55 @@ int ofdft_set_ions(ofdft_grid *g, const ofdft_ions *ions, const ofdft_species *s
     }
     CK(cudaMemcpy(g->ph, ph.data(), ph.size() * sizeof(double2), cudaMemcpyHostToDevice), "upload phases");
     CK(launch_round_phases(g->ph, g->ph32, (long long)ph.size(), g->stream), "round phases");
-    CK(cudaMemcpy(g->d_species, g->species.data(), n * sizeof(int), cudaMemcpyHostToDevice), "upload species");
-    CK(cudaMemcpy(g->d_Z, g->Z.data(), g->n_species * sizeof(double), cudaMemcpyHostToDevice), "upload Z");
-    CK(cudaMemcpy(g->d_rc, g->rc.data(), g->n_species * sizeof(double), cudaMemcpyHostToDevice), "upload rc");
-    g->have_ions = true;
-    g->vext_fresh32 = g->vext_fresh64 = false;
+    return OFDFT_OK;
+}
+
+int ofdft_set_ions_pme(ofdft_grid *g, const ofdft_ions *ions, const ofdft_species *sp, int order) {
+    if (!g) return OFDFT_ERR_INVALID_ARG;
+    if (order < 4 || order > kPmeMaxOrder || order % 2) return fail(g, OFDFT_ERR_INVALID_ARG, "PME order must be even, 4..16");
+    for (int a = 0; a < 3; a++)
+        if (g->n[a] < order) return fail(g, OFDFT_ERR_INVALID_ARG, "grid smaller than the PME stencil");
+    int rc = store_ions(g, ions, sp);
+    if (rc) return rc;
+    g->pme_order = order;
+    if (!g->d_pos) CK(cudaMalloc(&g->d_pos, (size_t)3 * g->n_ions * sizeof(double)), "cudaMalloc positions");
+    CK(cudaMemcpy(g->d_pos, g->pos.data(), (size_t)3 * g->n_ions * sizeof(double), cudaMemcpyHostToDevice),
+       "upload positions");
+    // conj b_a(k) = conj( e^{2 pi i (p-1) k/n} / sum_{j=0}^{p-2} M_p(j+1) e^{2 pi i k j/n} )
+    std::vector<double> Mp(order + 1, 0.0);   // M_p at the integers 1..p-1
+    {
+        std::vector<double> w(order, 0.0);
+        w[0] = 0.0;
+        w[1] = 1.0;                            // order 2 at x = 0: M_2(0) = 0, M_2(1) = 1
+        for (int k = 3; k <= order; k++)
+            for (int i = k - 1; i >= 0; i--) {
+                const double a = (i >= 1) ? w[i - 1] : 0.0;
+                w[i] = ((double)i * w[i] + (double)(k - i) * a) / (double)(k - 1);
+            }
+        for (int i = 0; i < order; i++) Mp[i] = w[i];      // Mp[i] = M_p(i)
+    }
+    const int na[3] = {g->n[0], g->n[1], g->n2h};
+    std::vector<double2> B((size_t)na[0] + na[1] + na[2]);
+    size_t off = 0;
+    for (int ax = 0; ax < 3; ax++) {
+        const int n = g->n[ax];
+        for (int k = 0; k < na[ax]; k++) {
+            double dr = 0.0, di = 0.0;
+            for (int j = 0; j <= order - 2; j++) {
+                const double ang = 2.0 * kPi * (double)k * j / n;
+                dr += Mp[j + 1] * std::cos(ang);
+                di += Mp[j + 1] * std::sin(ang);
+            }
+            const double ang = 2.0 * kPi * (double)(order - 1) * k / n;
+            const double nr = std::cos(ang), ni = std::sin(ang);
+            const double den = dr * dr + di * di;
+            const double br = (nr * dr + ni * di) / den, bi = (ni * dr - nr * di) / den;
+            B[off + k] = make_double2(br, -bi);    // conjugate
+        }
+        off += na[ax];
+    }
+    if (!g->pmeB) CK(cudaMalloc(&g->pmeB, B.size() * sizeof(double2)), "cudaMalloc PME factors");
+    CK(cudaMemcpy(g->pmeB, B.data(), B.size() * sizeof(double2), cudaMemcpyHostToDevice), "upload PME factors");
     return OFDFT_OK;
 }
 

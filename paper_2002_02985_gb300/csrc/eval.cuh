@@ -132,6 +132,8 @@ cudaError_t prepare_kernels(const LaunchSet &ks);
 
 template <typename T> cudaError_t launch_eval(const EvalArgs<T> &a, const LaunchSet &ks, cudaStream_t s,
                                               const ProfHook *prof = nullptr);
+// inverse pencil along n1 + C2R rows of the channels in a.col_inv_ch / a.inv_ch (CONS_ADD), V = result
+template <typename T> cudaError_t launch_inverse_cols_rows(const EvalArgs<T> &a, const LaunchSet &ks, cudaStream_t s);
 // stats + knots + row_fwd + forward pencil along n1 only (the channels of a.fwd_ch / a.col_ch)
 template <typename T> cudaError_t launch_forward_rows_cols(const EvalArgs<T> &a, const LaunchSet &ks, cudaStream_t s);
 

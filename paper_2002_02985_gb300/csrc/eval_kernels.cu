@@ -105,11 +105,25 @@ template <typename T> cudaError_t launch_forward_rows_cols(const EvalArgs<T> &a,
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_inverse_cols_rows(const EvalArgs<T> &a, const LaunchSet &ks, cudaStream_t s) {
+    const long long R = (long long)a.n0 * a.n1;
+    const long long pairs = (R + 1) / 2;
+    const int nrt = (int)((pairs + a.Brow - 1) / a.Brow);
+    cudaError_t e = launch(ks.pen_inv, dim3(pencil_tiles(a), 1, a.ncol_inv), a.thr_p1,
+                           pencil_smem_bytes<T>(a.n1, a.TW1), a, s);
+    if (e) return e;
+    e = launch(ks.row_inv, dim3(nrt), a.thr_rowi, row_inv_smem_bytes<T>(a.n2, a.Brow), a, s);
+    if (e) return e;
+    return cudaGetLastError();
+}
+
 #define INST(T)                                                                                              \
     template bool find_specialised<T>(int, int, const void **, const void **, int *, int *);                 \
     template LaunchSet generic_kernels<T>();                                                                 \
     template cudaError_t launch_eval<T>(const EvalArgs<T> &, const LaunchSet &, cudaStream_t, const ProfHook *); \
-    template cudaError_t launch_forward_rows_cols<T>(const EvalArgs<T> &, const LaunchSet &, cudaStream_t);
+    template cudaError_t launch_forward_rows_cols<T>(const EvalArgs<T> &, const LaunchSet &, cudaStream_t); \
+    template cudaError_t launch_inverse_cols_rows<T>(const EvalArgs<T> &, const LaunchSet &, cudaStream_t);
 INST(float)
 INST(double)
 

@@ -33,7 +33,8 @@ cudaError_t launch_forces(const IonArgs &a, const C *rhohat, double *partials, i
 // plain forward FFT along n0 of a half spectrum (in place), used by forces
 template <typename T>
 cudaError_t launch_axis0_fft(typename Vec2<T>::type *data, int n0, long long P, const FFTPlan &p,
-                             const typename Vec2<T>::type *tw, int TW, int thr, double scale, cudaStream_t s);
+                             const typename Vec2<T>::type *tw, int TW, int thr, double scale, cudaStream_t s,
+                             int dir = -1);
 
 // ---- optimiser vector kernels (all reductions FP64, fixed order) ----------
 // out[slot] = sum_i a_i b_i (c_i if c != null)

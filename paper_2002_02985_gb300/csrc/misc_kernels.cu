@@ -247,7 +247,7 @@ cudaError_t launch_forces_fast(const IonArgs &a, const float2 *rhohat, const flo
 }
 
 // ---------------------------------------------------------------- plain FFT along n0
-template <typename T, int CAP>
+template <typename T, int CAP, int DIR>
 __global__ void __launch_bounds__(512) axis0_fft_kernel(typename Vec2<T>::type *data, int n0, long long P, FFTPlan p,
                                  const typename Vec2<T>::type *twg, int TW, T scale) {
     typedef typename Vec2<T>::type C;
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(512) axis0_fft_kernel(typename Vec2<T>::type *
         buf[idx] = (c0 + w < P) ? data[(size_t)i * P + c0 + w] : cmake<C>((T)0, (T)0);
     }
     __syncthreads();
-    fft_smem<-1, CAP>(buf, TW, TW, p, tw);
+    fft_smem<DIR, CAP>(buf, TW, TW, p, tw);
     for (int idx = threadIdx.x; idx < n0 * TW; idx += blockDim.x) {
         const int w = idx % TW, i = idx / TW;
         if (c0 + w < P) data[(size_t)i * P + c0 + w] = cscale(buf[idx], scale);
@@ -270,23 +270,26 @@ __global__ void __launch_bounds__(512) axis0_fft_kernel(typename Vec2<T>::type *
 
 template <typename T>
 cudaError_t launch_axis0_fft(typename Vec2<T>::type *data, int n0, long long P, const FFTPlan &p,
-                             const typename Vec2<T>::type *tw, int TW, int thr, double scale, cudaStream_t s) {
+                             const typename Vec2<T>::type *tw, int TW, int thr, double scale, cudaStream_t s, int dir) {
     typedef typename Vec2<T>::type C;
+    constexpr int CAP = sizeof(T) == 4 ? 16 : 8;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = allow_max_dynamic_smem(axis0_fft_kernel<T, (sizeof(T) == 4 ? 16 : 8)>);
+        cudaError_t e = allow_max_dynamic_smem(axis0_fft_kernel<T, CAP, -1>);
+        if (e == cudaSuccess) e = allow_max_dynamic_smem(axis0_fft_kernel<T, CAP, 1>);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     const size_t sm = (size_t)n0 * sizeof(C) * (1 + TW);
     const unsigned nb = (unsigned)((P + TW - 1) / TW);
-    axis0_fft_kernel<T, (sizeof(T) == 4 ? 16 : 8)><<<nb, thr, sm, s>>>(data, n0, P, p, tw, TW, (T)scale);
+    if (dir < 0) axis0_fft_kernel<T, CAP, -1><<<nb, thr, sm, s>>>(data, n0, P, p, tw, TW, (T)scale);
+    else axis0_fft_kernel<T, CAP, 1><<<nb, thr, sm, s>>>(data, n0, P, p, tw, TW, (T)scale);
     return cudaGetLastError();
 }
 template cudaError_t launch_axis0_fft<float>(float2 *, int, long long, const FFTPlan &, const float2 *, int, int,
-                                             double, cudaStream_t);
+                                             double, cudaStream_t, int);
 template cudaError_t launch_axis0_fft<double>(double2 *, int, long long, const FFTPlan &, const double2 *, int, int,
-                                              double, cudaStream_t);
+                                              double, cudaStream_t, int);
 
 // ---------------------------------------------------------------- optimiser vectors
 template <typename T>

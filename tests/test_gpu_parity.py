@@ -232,3 +232,19 @@ def test_specialised_and_generic_kernels_agree(kw, monkeypatch):
     for k in E1:
         assert abs(E1[k] - E2[k]) / wl["n_atoms"] <= 5e-7, (k, E1[k], E2[k])
     assert float((V1 - V2).norm() / V1.norm()) <= 1e-5
+
+
+@pytest.mark.parametrize("shape", [(1024, 12, 20), (16, 1024, 18), (20, 12, 1024)])
+def test_length_1024_axes_match_oracle(shape):
+    """1024-point axes in each role (generic kernels), FP32-mixed and FP64."""
+    cell = np.diag([0.25 * n for n in shape])
+    rng = np.random.default_rng(shape[0] + 7)
+    pos = rng.uniform(0, 1, (3, 3)) @ cell
+    rho = W.renormalise(W.apply_noise(W.gaussian_density(cell, shape, pos, 3.0, 1.0) + 2e-3, 0.03, 5), cell, 9.0)
+    E, V, Eo, Vo, og, _ = run_both(cell, shape, pos, rho, dict(n_knots=6), L.FP64, Z=(3.0,), rc=(0.8,))
+    assert abs(E["total"] - Eo["total"]) <= 1e-10 * abs(Eo["total"])
+    assert np.max(np.abs(V - Vo)) <= 1e-9 * max(1.0, np.max(np.abs(Vo)))
+    E, V, Eo, Vo, og, _ = run_both(cell, shape, pos, rho, dict(n_knots=6), L.FP32_MIXED, Z=(3.0,), rc=(0.8,))
+    assert abs(E["total"] - Eo["total"]) / 3 <= 1e-6
+    m = knot_mask(rho.astype(np.float32).astype(np.float64), 6)
+    assert np.linalg.norm((V - Vo)[m]) / np.linalg.norm(Vo[m]) <= 1e-4
