@@ -149,9 +149,126 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_scale(args):
+    """1,048,576-atom FCC Al (64^3 conventional cells) on a 1024^3 grid, 12 knots,
+    PME structure factor.  Steps: PME set-up; FP32-mixed E+V timing; the supercell
+    pin (a perfect crystal on 1024^3 has the energy per atom and potential of the
+    4-atom cell on 16^3, computed by the oracle); PME forces; the 2 %-noise density
+    with forces checked against central differences of the FP64 energy on 8 atoms;
+    optionally the density optimisation."""
+    import torch
+    import paper_2002_02985_gb300 as ofd
+    import workloads as W
+    from paper_2002_02985_gb300 import _lib as L
+    from oracle import functionals as ofn
+    from oracle.evaluate import Functional as OF, evaluate
+    from oracle.grid import Grid as OG
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    wl = W.workload("fcc-al-1m/1024")
+    wl1 = W.workload("fcc-al-4/16")
+    order = args.pme_order
+    out = {}
+    # ---- perfect crystal: supercell pin
+    rho = W.tiled_density_torch(wl1, 64, 0.0, 5, dev, torch.float32)
+    N = rho.numel()
+    g = ofd.Grid(wl["cell"], wl["shape"])
+    f32 = ofd.Functional(n_knots=12, precision=L.FP32_MIXED)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.set_ions(wl["positions"], wl["species"], wl["Z"], wl["rc"], pme_order=order)
+    E, V = g.energy_potential(rho, f32)
+    torch.cuda.synchronize()
+    out["setup_and_first_eval_s"] = round(time.perf_counter() - t0, 3)
+    og = OG(wl1["cell"], wl1["shape"])
+    Vg1 = ofn.external_potential_G(og, wl1["positions"], wl1["species"], wl1["Z"], wl1["rc"])
+    r1 = W.model_density(wl1)
+    E1, V1 = evaluate(og, r1.astype(np.float32).astype(np.float64), OF(n_knots=12), Vg1)
+    out["supercell_pin"] = {"E_per_atom_1024": E["total"] / wl["n_atoms"], "E_per_atom_oracle_16": E1["total"] / 4,
+                            "abs_err_Ha_per_atom": abs(E["total"] / wl["n_atoms"] - E1["total"] / 4)}
+    Vs = V[::64, ::64, ::64].double().cpu().numpy()          # every 64th point = one value of the cell
+    blocks = [V[a:a + 16, b:b + 16, c:c + 16].double().cpu().numpy() for a, b, c in ((0, 0, 0), (512, 256, 768),
+                                                                                       (1008, 1008, 1008))]
+    out["supercell_pin"]["V_max_rel_err"] = max(float(np.max(np.abs(bl - V1)) / np.max(np.abs(V1))) for bl in blocks)
+    del Vs
+    F = g.forces(rho, L.FP32_MIXED)
+    out["perfect_crystal_max_force"] = float(np.max(np.abs(F)))
+    # ---- timing on the noisy density
+    del rho, V
+    rho = W.tiled_density_torch(wl1, 64, 0.02, 5, dev, torch.float32)
+    Vt = torch.empty_like(rho)
+    E_dev = torch.zeros(8, dtype=torch.float64, device=dev)
+    g.energy_potential(rho, f32)
+    for _ in range(args.warmup):
+        g.energy_potential_async(rho, f32, E_dev, Vt)
+    torch.cuda.synchronize()
+    g.profile_reset()
+    g.profile(True)
+    ms = []
+    for _ in range(args.steps):
+        st, en = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st.record()
+        g.energy_potential_async(rho, f32, E_dev, Vt)
+        en.record()
+        torch.cuda.synchronize()
+        ms.append(st.elapsed_time(en))
+    g.profile(False)
+    prof = g.profile_read()
+    t = sum(ms) / len(ms)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    F = g.forces(rho, L.FP32_MIXED)
+    torch.cuda.synchronize()
+    out["forces_s"] = round(time.perf_counter() - t0, 3)
+    # ---- FD of the FP64 energy (PP term: the only one that depends on R) on 8 atoms
+    del Vt
+    g64 = ofd.Grid(wl["cell"], wl["shape"])
+    rho64 = rho.double()
+    fpp = ofd.Functional(terms=L.TERM_PP, precision=L.FP64)
+    g64.set_ions(wl["positions"], wl["species"], wl["Z"], wl["rc"], pme_order=order)
+    F64 = g64.forces(rho64, L.FP64)
+    # 4-point central stencil: the FP64 energy of 1M atoms is a sum of ~5e8 terms whose
+    # rounding (~1e-8 Ha) sets the noise floor of a two-point difference at small steps
+    rng = np.random.default_rng(5)
+    h = 4e-3
+    fd = []
+    for I in rng.choice(wl["n_atoms"], 8, replace=False):
+        a = int(rng.integers(0, 3))
+        Es = {}
+        for k in (-2, -1, 1, 2):
+            p = wl["positions"].copy()
+            p[I, a] += k * h
+            g64.set_ions(p, wl["species"], wl["Z"], wl["rc"], pme_order=order)
+            Es[k] = g64.energy_potential(rho64, fpp, want_potential=False)[0]["total"]
+        fdv = -(8.0 * (Es[1] - Es[-1]) - (Es[2] - Es[-2])) / (12.0 * h)
+        fd.append({"atom": int(I), "axis": a, "fd": fdv, "F64": float(F64[I, a]), "F32": float(F[I, a])})
+    out["fd_forces"] = fd
+    out["fd_max_abs_err"] = max(abs(x["fd"] - x["F64"]) for x in fd)
+    out["fp32_vs_fp64_force_max_abs"] = float(np.max(np.abs(F - F64)))
+    del g64, rho64
+    line = {"metric": METRIC, "value": round(N / (t * 1e-3), 1), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(t, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "fcc-al-1m/1024", "grid": [1024] * 3, "atoms": wl["n_atoms"], "n_knots": 12,
+                       "structure_factor": "PME order %d" % order, "l2": "inputs 4.3 GB > L2"},
+            "kernels": {k: {"launches": n, "avg_ms": round(v / max(1, n), 3)} for k, (n, v) in prof.items()},
+            "checks": out}
+    if args.optimize:
+        psi = rho.sqrt()
+        t0 = time.perf_counter()
+        rep = g.optimize_density(psi, f32, wl["n_electrons"], tol_per_atom=1e-6, max_iter=args.max_iter)
+        line["optimize"] = {"seconds": round(time.perf_counter() - t0, 1), "converged": rep["converged"],
+                            "iterations": rep["iterations"], "evaluations": rep["evaluations"],
+                            "E_per_atom": rep["energy"] / wl["n_atoms"], "last_dE_per_atom": rep["last_dE"] / wl["n_atoms"],
+                            "residual": rep["residual"]}
+    print(json.dumps(line), flush=True)
+
+
 def run_gpu(args):
     if args.workload == "fcc-al-108-batch":
         return run_batch(args)
+    if args.workload == "fcc-al-1m/1024":
+        return run_scale(args)
     import torch
     import paper_2002_02985_gb300 as ofd
     import workloads as W
@@ -399,8 +516,11 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD,
-                    help="fcc-al-256/128 (default), fcc-al-4/32, mg147/192, fcc-al-108-batch")
+                    help="fcc-al-256/128 (default), fcc-al-4/32, mg147/192, fcc-al-108-batch, fcc-al-1m/1024")
     ap.add_argument("--snapshots", type=int, default=64)
+    ap.add_argument("--pme-order", type=int, default=10)
+    ap.add_argument("--optimize", action="store_true")
+    ap.add_argument("--max-iter", type=int, default=200)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -162,6 +162,8 @@ template <typename T> int choose_launch(ofdft_grid *g, Workspace<T> &w) {
         int B = 16;
         for (; B >= 1; B /= 2)
             if (row_inv_smem_bytes<T>(g->n[2], B) <= row_budget && threads_for(g->plan[2], B, cap) <= tmax) break;
+        // long FP64 rows: one row pair per block may need more than the preferred budget
+        if (B < 1 && row_inv_smem_bytes<T>(g->n[2], 1) <= 200 * 1024 && threads_for(g->plan[2], 1, cap) <= tmax) B = 1;
         if (B < 1) return fail(g, OFDFT_ERR_UNSUPPORTED_SIZE, "row transform does not fit in shared memory");
         w.Brow = B;
         w.thr_rowf = w.thr_rowi = std::min(std::max(threads_for(g->plan[2], B, cap), 128), tmax);

@@ -245,6 +245,8 @@ def test_length_1024_axes_match_oracle(shape):
     assert abs(E["total"] - Eo["total"]) <= 1e-10 * abs(Eo["total"])
     assert np.max(np.abs(V - Vo)) <= 1e-9 * max(1.0, np.max(np.abs(Vo)))
     E, V, Eo, Vo, og, _ = run_both(cell, shape, pos, rho, dict(n_knots=6), L.FP32_MIXED, Z=(3.0,), rc=(0.8,))
-    assert abs(E["total"] - Eo["total"]) / 3 <= 1e-6
+    # these boxes are dominated by the background density (|E| ~ 200 Ha for 3 atoms):
+    # FP32 rounding is bounded per atom or relative to |E|, whichever is larger
+    assert abs(E["total"] - Eo["total"]) <= max(3 * 1e-6, 2e-7 * abs(Eo["total"]))
     m = knot_mask(rho.astype(np.float32).astype(np.float64), 6)
     assert np.linalg.norm((V - Vo)[m]) / np.linalg.norm(Vo[m]) <= 1e-4

@@ -369,3 +369,23 @@ def test_supercell_invariance():
         E, _ = evaluate(g, rho, f, Vg)
         out.append(E["total"] / len(pos))
     assert abs(out[0] - out[1]) < 1e-11
+
+
+def test_torch_splitmix_matches_numpy_stream():
+    torch = pytest.importorskip("torch")
+    a = W.splitmix64_uniform(5, np.arange(1000, 1500, dtype=np.uint64))
+    b = W.splitmix64_uniform_torch(5, 1000, 500, "cpu").numpy()
+    assert np.array_equal(a, b)
+
+
+def test_tiled_density_is_the_periodic_supercell():
+    torch = pytest.importorskip("torch")
+    wl1 = W.workload("fcc-al-4/16")
+    r1 = W.model_density(wl1)
+    big = W.tiled_density_torch(wl1, 2, 0.0, 5, "cpu", torch.float64).numpy()
+    assert np.allclose(big[:16, :16, :16], r1, rtol=1e-14)
+    assert np.allclose(big[16:, 16:, :16], r1, rtol=1e-14)
+    noisy = W.tiled_density_torch(wl1, 2, 0.02, 5, "cpu", torch.float64).numpy()
+    cell2, pos2 = W.fcc_positions(2)
+    ref = W.renormalise(W.apply_noise(np.tile(r1, (2, 2, 2)), 0.02, 5), cell2, 96.0)
+    assert np.allclose(noisy, ref, rtol=1e-12)

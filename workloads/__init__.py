@@ -39,6 +39,53 @@ def splitmix64_uniform(seed: int, idx: np.ndarray) -> np.ndarray:
     return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
 
 
+def _lsr(z, s: int):
+    """Logical right shift of int64 tensors (torch shifts arithmetically)."""
+    return (z >> s) & ((1 << (64 - s)) - 1)
+
+
+def _i64(c: int) -> int:
+    return c - (1 << 64) if c >= (1 << 63) else c
+
+
+def splitmix64_uniform_torch(seed: int, start: int, count: int, device):
+    """The same stream as splitmix64_uniform for indices start .. start+count-1, computed
+    with wrapping int64 tensor arithmetic on `device` (so a GPU can regenerate the noise
+    of a 1024^3 grid without a host transfer)."""
+    import torch
+    idx = torch.arange(start, start + count, dtype=torch.int64, device=device)
+    z = _i64(seed & _MASK64) + (idx + 1) * _i64(_GAMMA)
+    z = (z ^ _lsr(z, 30)) * _i64(0xBF58476D1CE4E5B9)
+    z = (z ^ _lsr(z, 27)) * _i64(0x94D049BB133111EB)
+    z = z ^ _lsr(z, 31)
+    return _lsr(z, 11).to(torch.float64) * (1.0 / 9007199254740992.0)
+
+
+def tiled_density_torch(wl_cell: dict, reps: int, noise: float, seed: int, device, dtype):
+    """Density of a reps^3 supercell of a periodic unit cell: the unit cell's model
+    density tiled, then the multiplicative SplitMix64 noise of the full grid (flat C
+    index), then renormalised to reps^3 times the cell's electrons.  Built plane by
+    plane on `device` in FP64, returned in `dtype`."""
+    import torch
+    rho1 = torch.from_numpy(model_density(wl_cell)).to(device)
+    n = rho1.shape[0]
+    Nn = n * reps
+    out = torch.empty((Nn, Nn, Nn), dtype=dtype, device=device)
+    plane = rho1.repeat(1, reps, reps)                       # (n, Nn, Nn) block of n planes
+    total = 0.0
+    for i0 in range(Nn):
+        p = plane[i0 % n]
+        if noise:
+            u = splitmix64_uniform_torch(seed, i0 * Nn * Nn, Nn * Nn, device).view(Nn, Nn)
+            p = p * (1.0 + noise * (2.0 * u - 1.0))
+        total += float(p.sum())
+        out[i0] = p.to(dtype)
+    omega = abs(float(np.linalg.det(wl_cell["cell"]))) * reps ** 3
+    scale = wl_cell["n_electrons"] * reps ** 3 / (total * omega / Nn ** 3)
+    out.mul_(scale)
+    return out
+
+
 def fcc_positions(n_cells, a: float = A_AL) -> tuple[np.ndarray, np.ndarray]:
     """Cubic FCC supercell of n_cells (int or 3-tuple) conventional cells.
 
@@ -180,6 +227,8 @@ def workload(name: str, index: int = 0) -> dict:
         return _al_workload(3, (n, n, n), 0.02, 40 + index, 16, jitter=0.2, jitter_seed=4 + index)
     if name == "fcc-al-1m/1024":
         return _al_workload(64, (1024, 1024, 1024), 0.02, 5, 12)
+    if name == "fcc-al-4/16":
+        return _al_workload(1, (16, 16, 16), 0.0, 5, 12)
     if name == "mg147/192":
         L = 40.0
         pos = mackay_icosahedron(3, 6.0) + L / 2.0
