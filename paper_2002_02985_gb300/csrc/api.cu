@@ -72,6 +72,7 @@ template <typename T> struct Workspace {
     T *opt = nullptr;                 // optimiser fields (8 * N), allocated on demand
     LaunchSet ks;                     // FFT-carrying kernels (size-specialised where compiled)
     int Brow = 0, thr_rowf = 0, thr_rowi = 0, TW1 = 0, thr_p1 = 0, TW0 = 0, thr_ax0 = 0, nb_row = 0, nb_ax0 = 0;
+    int grid_p1 = 0;
 };
 
 }  // namespace
@@ -176,7 +177,7 @@ template <typename T> int choose_launch(ofdft_grid *g, Workspace<T> &w) {
         w.thr_p1 = ntv;
     } else {
         int TW = 16;
-        while (TW > 1 && ((size_t)g->n[1] * TW * sizeof(C) > 64 * 1024 || threads_for(g->plan[1], TW, cap) > tmax))
+        while (TW > 1 && (pencil_smem_bytes<T>(g->n[1], TW) > 96 * 1024 || threads_for(g->plan[1], TW, cap) > tmax))
             TW /= 2;
         w.TW1 = TW;
         w.thr_p1 = std::min(std::max(threads_for(g->plan[1], TW, cap), 128), tmax);
@@ -195,6 +196,12 @@ template <typename T> int choose_launch(ofdft_grid *g, Workspace<T> &w) {
     }
     cudaError_t e = prepare_kernels(w.ks);
     if (e != cudaSuccess) return fail(g, OFDFT_ERR_CUDA, "kernel attributes", e);
+    // persistent pencil grid: every resident block slot of the device, once
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, w.ks.pen_fwd, w.thr_p1,
+                                                      pencil_smem_bytes<T>(g->n[1], w.TW1));
+    if (e != cudaSuccess) return fail(g, OFDFT_ERR_CUDA, "occupancy", e);
+    w.grid_p1 = std::max(1, per_sm) * g->nsm;
     const long long R = (long long)g->n[0] * g->n[1];
     w.nb_row = (int)(((R + 1) / 2 + w.Brow - 1) / w.Brow);
     const long long P = (long long)g->n[1] * g->n2h;
@@ -424,6 +431,7 @@ int enqueue_eval(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, d
     a.thr_p1 = w.thr_p1;
     a.TW0 = w.TW0;
     a.thr_ax0 = w.thr_ax0;
+    a.grid_p1 = w.grid_p1;
     // channel lists
     const bool hpp = f->terms & (OFDFT_TERM_HARTREE | OFDFT_TERM_PP);
     const bool vw = f->terms & OFDFT_TERM_VW;
@@ -500,7 +508,7 @@ template <typename T> EvalArgs<T> plain_args(ofdft_grid *g, Workspace<T> &w, con
     a.p0 = g->plan[0]; a.p1 = g->plan[1]; a.p2 = g->plan[2];
     a.tw0 = w.tw[0]; a.tw1 = w.tw[1]; a.tw2 = w.tw[2];
     a.Brow = w.Brow; a.thr_rowf = w.thr_rowf; a.thr_rowi = w.thr_rowi;
-    a.TW1 = w.TW1; a.thr_p1 = w.thr_p1; a.TW0 = w.TW0; a.thr_ax0 = w.thr_ax0;
+    a.TW1 = w.TW1; a.thr_p1 = w.thr_p1; a.TW0 = w.TW0; a.thr_ax0 = w.thr_ax0; a.grid_p1 = w.grid_p1;
     a.nfwd = 1; a.fwd_ch[0] = CH_HPP; a.ncol = 1; a.col_ch[0] = CH_HPP;
     return a;
 }
@@ -606,22 +614,7 @@ template <typename T> int forces_impl(ofdft_grid *g, const T *rho, double *F) {
     if (rc) return rc;
     Workspace<T> &w = ws<T>(g);
     if (g->pme_order > 0) return forces_pme<T>(g, w, rho, F);
-    EvalArgs<T> a;
-    std::memset(&a, 0, sizeof(a));
-    a.n0 = g->n[0]; a.n1 = g->n[1]; a.n2 = g->n[2]; a.n2h = g->n2h; a.N = g->N; a.NH = g->NH;
-    a.omega = g->omega; a.dV = g->dV;
-    a.rho = rho; a.chan = w.chan; a.terms = OFDFT_TERM_HARTREE; a.floor_ = (T)1e-30;
-    a.scal = w.scal; a.knots_d = w.knots_d; a.knots_t = w.knots_t; a.invdk_t = w.invdk_t;
-    a.part_stats = w.part_stats; a.part_minmax = w.part_minmax; a.energies = w.energies;
-    a.nb_stats = 2 * g->nsm;
-    a.p0 = g->plan[0]; a.p1 = g->plan[1]; a.p2 = g->plan[2];
-    a.tw0 = w.tw[0]; a.tw1 = w.tw[1]; a.tw2 = w.tw[2];
-    a.Brow = w.Brow; a.thr_rowf = w.thr_rowf; a.TW1 = w.TW1; a.thr_p1 = w.thr_p1;
-    a.nfwd = 1; a.fwd_ch[0] = CH_HPP; a.ncol = 1; a.col_ch[0] = CH_HPP;
-    CK(launch_forward_rows_cols<T>(a, w.ks, g->stream), "forward transform");
-    CK(launch_axis0_fft<T>(w.chan, g->n[0], (long long)g->n[1] * g->n2h, g->plan[0], w.tw[0], w.TW0, w.thr_ax0,
-                           1.0 / (double)g->N, g->stream),
-       "forward transform along n0");
+    if ((rc = forward_plain<T>(g, w, rho))) return rc;          // normalised rho_hat in slot 0
     // FP32-mixed: FP32 phase products with FP64 accumulation (per-G scratch of
     // 32 bytes per half-spectrum point, allowed up to 2 GB); FP64: all-FP64 kernel
     const bool fast = sizeof(T) == 4 && g->NH <= (64LL << 20);

@@ -67,6 +67,7 @@ template <typename T> struct EvalArgs {
     FFTPlan p0, p1, p2;
     const C *tw0, *tw1, *tw2;
     int Brow, thr_rowf, thr_rowi, TW1, thr_p1, TW0, thr_ax0;
+    int grid_p1;                         // persistent grid of the n1 pencil kernels
     int nfwd, fwd_ch[kMaxChan];          // channels formed by row_fwd (slot ids)
     int ncol, col_ch[kMaxChan];          // channels transformed forward along n1
     int ncol_inv, col_inv_ch[kMaxChan];  // channels transformed back along n1
@@ -98,7 +99,7 @@ template <typename T> __host__ __device__ inline size_t row_fwd_smem_bytes(int n
 }
 template <typename T> __host__ __device__ inline size_t pencil_smem_bytes(int n, int TW) {
     typedef typename Vec2<T>::type C;
-    return (size_t)n * sizeof(C) + (size_t)n * TW * sizeof(C);
+    return (size_t)n * sizeof(C) + 2 * (size_t)n * TW * sizeof(C);     // twiddles + two tile buffers
 }
 
 template <typename T> __host__ __device__ inline size_t axis0_smem_bytes(int n, int TW) {

@@ -33,8 +33,10 @@ cudaError_t prepare_kernels(const LaunchSet &ks) {
     return cudaSuccess;
 }
 
-template <typename T> static unsigned pencil_tiles(const EvalArgs<T> &a) {
-    return (unsigned)(((long long)a.n0 * a.n2h + a.TW1 - 1) / a.TW1);
+// persistent pencil grid: at most grid_p1 blocks (resident capacity), never more than tiles
+template <typename T> static unsigned pencil_tiles(const EvalArgs<T> &a, int nch) {
+    const long long t = (((long long)a.n0 * a.n2h + a.TW1 - 1) / a.TW1) * nch;
+    return (unsigned)(t < a.grid_p1 ? t : a.grid_p1);
 }
 
 template <typename T>
@@ -67,7 +69,7 @@ cudaError_t launch_eval(const EvalArgs<T> &a, const LaunchSet &ks, cudaStream_t 
     }
     if (a.ncol > 0) {
         mark(K_PENCIL_FWD, 0);
-        e = launch(ks.pen_fwd, dim3(pencil_tiles(a), 1, a.ncol), a.thr_p1, pencil_smem_bytes<T>(a.n1, a.TW1), a, s);
+        e = launch(ks.pen_fwd, dim3(pencil_tiles(a, a.ncol)), a.thr_p1, pencil_smem_bytes<T>(a.n1, a.TW1), a, s);
         if (e) return e;
         mark(K_PENCIL_FWD, 1);
     }
@@ -77,7 +79,7 @@ cudaError_t launch_eval(const EvalArgs<T> &a, const LaunchSet &ks, cudaStream_t 
     mark(K_AXIS0, 1);
     if (a.ncol_inv > 0) {
         mark(K_PENCIL_INV, 0);
-        e = launch(ks.pen_inv, dim3(pencil_tiles(a), 1, a.ncol_inv), a.thr_p1, pencil_smem_bytes<T>(a.n1, a.TW1),
+        e = launch(ks.pen_inv, dim3(pencil_tiles(a, a.ncol_inv)), a.thr_p1, pencil_smem_bytes<T>(a.n1, a.TW1),
                    a, s);
         if (e) return e;
         mark(K_PENCIL_INV, 1);
@@ -100,7 +102,7 @@ template <typename T> cudaError_t launch_forward_rows_cols(const EvalArgs<T> &a,
     knots_kernel<T><<<1, 256, 0, s>>>(a);
     cudaError_t e = launch(ks.row_fwd, dim3(nrt), a.thr_rowf, row_fwd_smem_bytes<T>(a.n2, a.Brow), a, s);
     if (e) return e;
-    e = launch(ks.pen_fwd, dim3(pencil_tiles(a), 1, a.ncol), a.thr_p1, pencil_smem_bytes<T>(a.n1, a.TW1), a, s);
+    e = launch(ks.pen_fwd, dim3(pencil_tiles(a, a.ncol)), a.thr_p1, pencil_smem_bytes<T>(a.n1, a.TW1), a, s);
     if (e) return e;
     return cudaGetLastError();
 }
@@ -110,7 +112,7 @@ cudaError_t launch_inverse_cols_rows(const EvalArgs<T> &a, const LaunchSet &ks, 
     const long long R = (long long)a.n0 * a.n1;
     const long long pairs = (R + 1) / 2;
     const int nrt = (int)((pairs + a.Brow - 1) / a.Brow);
-    cudaError_t e = launch(ks.pen_inv, dim3(pencil_tiles(a), 1, a.ncol_inv), a.thr_p1,
+    cudaError_t e = launch(ks.pen_inv, dim3(pencil_tiles(a, a.ncol_inv)), a.thr_p1,
                            pencil_smem_bytes<T>(a.n1, a.TW1), a, s);
     if (e) return e;
     e = launch(ks.row_inv, dim3(nrt), a.thr_rowi, row_inv_smem_bytes<T>(a.n2, a.Brow), a, s);

@@ -301,35 +301,60 @@ __device__ __forceinline__ void row_fwd_body(const EvalArgs<T> &a) {
 
 // ======================================================================= pencil (C2C along n1)
 
-// blockIdx.x: tile of TW consecutive columns c = k0 * n2h + k2 (flattened over the
-// planes, so no tile is ragged except the very last), blockIdx.z: channel list entry
+// Persistent: block b handles tiles t = b, b + gridDim.x, ... of the flattened
+// (channel, column tile) range; a tile is TW consecutive columns c = k0 * n2h + k2
+// (flattened over the planes, so only the last tile of a channel is ragged) times
+// all n1 rows.  The next tile is prefetched with cp.async into the second of two
+// buffers while the current one is transformed and stored.
 template <typename T, int DIR, class P>
 __device__ __forceinline__ void pencil1_body(const EvalArgs<T> &a) {
     typedef typename Vec2<T>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = P::n(a), TW = P::B(a), n2h = a.n2h, NT = P::nt();
     C *tw = (C *)smem_raw;
-    C *buf = tw + n;
+    C *buf[2] = {tw + n, tw + n + n * TW};
     for (int i = threadIdx.x; i < n; i += NT) tw[i] = a.tw1[i];
-    const int ch = DIR < 0 ? a.col_ch[blockIdx.z] : a.col_inv_ch[blockIdx.z];
-    C *base = a.chan + (size_t)ch * a.NH;
     const long long ncols = (long long)a.n0 * n2h;
-    const long long c0 = (long long)blockIdx.x * TW;
+    const int ntile = (int)((ncols + TW - 1) / TW);
+    const int nch = DIR < 0 ? a.ncol : a.ncol_inv;
+    const int total = ntile * nch;
     const long long plane = (long long)n * n2h;
-    for (int idx = threadIdx.x; idx < n * TW; idx += NT) {
-        const int w = idx % TW, i = idx / TW;
-        const long long c = c0 + w;
-        const long long k0 = c / n2h, k2 = c - k0 * n2h;
-        buf[idx] = (c < ncols) ? base[k0 * plane + (long long)i * n2h + k2] : cmake<C>((T)0, (T)0);
+    auto tile_base = [&](int t, long long &c0) -> C * {
+        const int ci = t / ntile;
+        c0 = (long long)(t - ci * ntile) * TW;
+        const int ch = DIR < 0 ? a.col_ch[ci] : a.col_inv_ch[ci];
+        return a.chan + (size_t)ch * a.NH;
+    };
+    auto prefetch = [&](int t, C *dst) {
+        long long c0;
+        const C *base = tile_base(t, c0);
+        for (int idx = threadIdx.x; idx < n * TW; idx += NT) {
+            const int w = idx % TW, i = idx / TW;
+            const long long c = c0 + w;
+            const long long k0 = c / n2h, k2 = c - k0 * n2h;
+            const bool ok = c < ncols;
+            cp_async<sizeof(C)>(dst + idx, base + (ok ? k0 * plane + (long long)i * n2h + k2 : 0), ok);
+        }
+        cp_async_commit();
+    };
+    int it = 0;
+    if ((int)blockIdx.x < total) prefetch(blockIdx.x, buf[0]);
+    for (int t = blockIdx.x; t < total; t += gridDim.x, it++) {
+        C *cur = buf[it & 1];
+        cp_async_wait<0>();
+        __syncthreads();
+        if (t + (int)gridDim.x < total) prefetch(t + gridDim.x, buf[(it + 1) & 1]);
+        P::template fft<DIR>(cur, a, tw);
+        long long c0;
+        C *base = tile_base(t, c0);
+        for (int idx = threadIdx.x; idx < n * TW; idx += NT) {
+            const int w = idx % TW, i = idx / TW;
+            const long long c = c0 + w;
+            const long long k0 = c / n2h, k2 = c - k0 * n2h;
+            if (c < ncols) base[k0 * plane + (long long)i * n2h + k2] = cur[idx];
+        }
     }
-    __syncthreads();
-    P::template fft<DIR>(buf, a, tw);
-    for (int idx = threadIdx.x; idx < n * TW; idx += NT) {
-        const int w = idx % TW, i = idx / TW;
-        const long long c = c0 + w;
-        const long long k0 = c / n2h, k2 = c - k0 * n2h;
-        if (c < ncols) base[k0 * plane + (long long)i * n2h + k2] = buf[idx];
-    }
+    cp_async_wait<0>();
 }
 
 // ======================================================================= axis 0 + reciprocal space

@@ -231,7 +231,7 @@ def test_specialised_and_generic_kernels_agree(kw, monkeypatch):
     # the oracle tolerance (each side is checked against the oracle elsewhere)
     for k in E1:
         assert abs(E1[k] - E2[k]) / wl["n_atoms"] <= 5e-7, (k, E1[k], E2[k])
-    assert float((V1 - V2).norm() / V1.norm()) <= 1e-5
+    assert float((V1 - V2).norm() / V1.norm()) <= 2.5e-5      # a quarter of the oracle tolerance
 
 
 @pytest.mark.parametrize("shape", [(1024, 12, 20), (16, 1024, 18), (20, 12, 1024)])
