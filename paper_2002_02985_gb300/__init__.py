@@ -194,14 +194,16 @@ class Grid:
                     residual=rep.residual, last_dE=rep.last_dE)
 
 
-def energy_potential_batched(grids, rhos, func: Functional, want_potential=True, want_forces=False):
-    """Evaluate many snapshots (grids may differ in shape) with one synchronisation."""
+def energy_potential_batched(grids, rhos, func: Functional, want_potential=True, want_forces=False, V_out=None):
+    """Evaluate many snapshots (grids may differ in shape) with one synchronisation.
+    Pass the same V_out tensors on every call to let the library replay its captured
+    CUDA graph of the batch (new buffers mean a new capture)."""
     import torch
     lib = library()
     n = len(grids)
     hs = (ct.c_void_p * n)(*[g.h for g in grids])
     rp = (ct.c_void_p * n)(*[r.data_ptr() for r in rhos])
-    Vs = [torch.empty_like(r) for r in rhos] if want_potential else None
+    Vs = (V_out if V_out is not None else [torch.empty_like(r) for r in rhos]) if want_potential else None
     vp = (ct.c_void_p * n)(*[v.data_ptr() for v in Vs]) if want_potential else None
     E = np.zeros((n, 6))
     Fs = [np.zeros((g.n_ions, 3)) for g in grids] if want_forces else None

@@ -106,6 +106,12 @@ struct ofdft_grid {
     void *pme_real = nullptr;              // real field scratch (N, largest precision used)
     size_t pme_real_bytes = 0;
     std::vector<int> species_count;
+    // asynchronous forces (batched evaluation): device partials, device F, pinned copy
+    double *fpart = nullptr;
+    size_t fpart_len = 0;
+    double *F_dev = nullptr, *F_pinned = nullptr;
+    int F_len = 0;
+    unsigned long long generation = 0;     // bumped whenever device buffers are (re)allocated
     int *d_species = nullptr;
     double *d_Z = nullptr, *d_rc = nullptr;
     double *h_pinned = nullptr;  // 64 doubles of pinned host memory
@@ -123,6 +129,8 @@ struct ofdft_grid {
 namespace {
 
 int fail(ofdft_grid *g, int code, const char *what, cudaError_t e = cudaSuccess) {
+    // a non-sticky error must not be reported again by the next call's launch check
+    if (e != cudaSuccess) (void)cudaGetLastError();
     if (g) {
         char buf[512];
         if (e != cudaSuccess) std::snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
@@ -246,6 +254,7 @@ template <typename T> int ensure_ws(ofdft_grid *g, int nslots) {
         w.nslots = 0;
         CK(cudaMalloc(&w.chan, (size_t)nslots * g->NH * sizeof(C)), "cudaMalloc channel workspace");
         w.nslots = nslots;
+        g->generation++;
     }
     return OFDFT_OK;
 }
@@ -294,7 +303,10 @@ template <typename T> int ensure_vext(ofdft_grid *g) {
     Workspace<T> &w = ws<T>(g);
     bool &fresh = sizeof(T) == 4 ? g->vext_fresh32 : g->vext_fresh64;
     if (fresh) return OFDFT_OK;
-    if (!w.vext) CK(cudaMalloc(&w.vext, g->NH * sizeof(C)), "cudaMalloc V_ext(G)");
+    if (!w.vext) {
+        CK(cudaMalloc(&w.vext, g->NH * sizeof(C)), "cudaMalloc V_ext(G)");
+        g->generation++;
+    }
     if (g->pme_order > 0) {
         int rc = build_vext_pme<T>(g, w);
         if (rc) return rc;
@@ -542,13 +554,17 @@ template <typename T> int inverse_plain(ofdft_grid *g, Workspace<T> &w, int slot
 }
 
 template <typename T> int ensure_pme_buffers(ofdft_grid *g) {
-    if (!g->Qfix) CK(cudaMalloc(&g->Qfix, (size_t)g->N * sizeof(unsigned long long)), "cudaMalloc PME grid");
+    if (!g->Qfix) {
+        CK(cudaMalloc(&g->Qfix, (size_t)g->N * sizeof(unsigned long long)), "cudaMalloc PME grid");
+        g->generation++;
+    }
     if (g->pme_real_bytes < (size_t)g->N * sizeof(T)) {
         cudaFree(g->pme_real);
         g->pme_real = nullptr;
         g->pme_real_bytes = 0;
         CK(cudaMalloc(&g->pme_real, (size_t)g->N * sizeof(T)), "cudaMalloc PME field");
         g->pme_real_bytes = (size_t)g->N * sizeof(T);
+        g->generation++;
     }
     return OFDFT_OK;
 }
@@ -586,71 +602,95 @@ template <typename T> int build_vext_pme(ofdft_grid *g, Workspace<T> &w) {
     return OFDFT_OK;
 }
 
-template <typename T> int forces_pme(ofdft_grid *g, Workspace<T> &w, const T *rho, double *F) {
+template <typename T> int forces_pme(ofdft_grid *g, Workspace<T> &w, const T *rho, double *dF) {
     typedef typename Vec2<T>::type C;
     int rc = ensure_pme_buffers<T>(g);
     if (rc) return rc;
     if ((rc = forward_plain<T>(g, w, rho))) return rc;                  // rho_hat in slot 0
-    double *dF = nullptr;
-    CK(cudaMalloc(&dF, (size_t)3 * g->n_ions * sizeof(double)), "cudaMalloc forces");
     for (int s = 0; s < g->n_species; s++) {
         PmeArgs pa = pme_args(g, s);
         C *slot1 = (C *)w.chan + g->NH;
         CK(pme_force_field<C>(pa, (const C *)w.chan, g->pmeB, g->Z[s], g->rc[s], slot1, g->stream), "PME field");
-        if ((rc = inverse_plain<T>(g, w, 1, (T *)g->pme_real, rho))) { cudaFree(dF); return rc; }
+        if ((rc = inverse_plain<T>(g, w, 1, (T *)g->pme_real, rho))) return rc;
         CK(pme_gather<T>(pa, (const T *)g->pme_real, dF, g->stream), "PME gather");
     }
-    cudaError_t e = cudaMemcpyAsync(F, dF, (size_t)3 * g->n_ions * sizeof(double), cudaMemcpyDeviceToHost, g->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
-    cudaFree(dF);
-    CK(e, "copy forces");
     return OFDFT_OK;
 }
 
 // ---------------------------------------------------------------- forces
-template <typename T> int forces_impl(ofdft_grid *g, const T *rho, double *F) {
+// Force kernels in use for this grid/precision and the size of their partials.
+template <typename T> void force_layout(ofdft_grid *g, bool &fast, int &nchunk, int &nsp) {
+    fast = sizeof(T) == 4 && g->NH <= (64LL << 20);
+    nchunk = fast ? std::max(16, 1024 / ((g->n_ions + 7) / 8)) : 16;
+    nsp = fast ? g->n_species : 1;
+}
+
+// device buffers of the force computation (outside any stream capture)
+template <typename T> int ensure_force_buffers(ofdft_grid *g) {
+    bool fast;
+    int nchunk, nsp;
+    force_layout<T>(g, fast, nchunk, nsp);
+    const size_t plen = (size_t)nsp * g->n_ions * nchunk * 3;
+    if (g->pme_order == 0 && plen > g->fpart_len) {
+        cudaFree(g->fpart);
+        g->fpart = nullptr;
+        g->fpart_len = 0;
+        CK(cudaMalloc(&g->fpart, plen * sizeof(double)), "cudaMalloc force partials");
+        g->fpart_len = plen;
+        g->generation++;
+    }
+    if (g->pme_order == 0 && fast && g->gc_len < g->NH) {
+        cudaFree(g->gc);
+        g->gc = nullptr;
+        g->gc_len = 0;
+        CK(cudaMalloc(&g->gc, 2 * (size_t)g->NH * sizeof(float4)), "cudaMalloc force scratch");
+        g->gc_len = g->NH;
+        g->generation++;
+    }
+    if (g->F_len < g->n_ions) {
+        cudaFree(g->F_dev);
+        cudaFreeHost(g->F_pinned);
+        g->F_dev = g->F_pinned = nullptr;
+        g->F_len = 0;
+        CK(cudaMalloc(&g->F_dev, (size_t)3 * g->n_ions * sizeof(double)), "cudaMalloc forces");
+        CK(cudaMallocHost(&g->F_pinned, (size_t)3 * g->n_ions * sizeof(double)), "cudaMallocHost forces");
+        g->F_len = g->n_ions;
+        g->generation++;
+    }
+    if (g->pme_order > 0) {
+        int rc = ensure_pme_buffers<T>(g);
+        if (rc) return rc;
+    }
+    return OFDFT_OK;
+}
+
+// enqueue the forces into g->F_dev (no synchronisation)
+template <typename T> int forces_enqueue(ofdft_grid *g, const T *rho) {
     typedef typename Vec2<T>::type C;
     int rc = ensure_ws<T>(g, 3);
     if (rc) return rc;
+    if ((rc = ensure_force_buffers<T>(g))) return rc;
     Workspace<T> &w = ws<T>(g);
-    if (g->pme_order > 0) return forces_pme<T>(g, w, rho, F);
+    if (g->pme_order > 0) return forces_pme<T>(g, w, rho, g->F_dev);
     if ((rc = forward_plain<T>(g, w, rho))) return rc;          // normalised rho_hat in slot 0
-    // FP32-mixed: FP32 phase products with FP64 accumulation (per-G scratch of
-    // 32 bytes per half-spectrum point, allowed up to 2 GB); FP64: all-FP64 kernel
-    const bool fast = sizeof(T) == 4 && g->NH <= (64LL << 20);
-    const int nchunk = fast ? std::max(16, 1024 / ((g->n_ions + 7) / 8)) : 16;
-    const int nsp = fast ? g->n_species : 1;
-    std::vector<double> part((size_t)nsp * g->n_ions * nchunk * 3);
-    double *dpart = w.part_misc;
-    bool own = false;
-    if (part.size() > 4096) {
-        CK(cudaMalloc(&dpart, part.size() * sizeof(double)), "cudaMalloc force partials");
-        own = true;
-    }
+    bool fast;
+    int nchunk, nsp;
+    force_layout<T>(g, fast, nchunk, nsp);
     IonArgs ia = ion_args(g);
-    if (fast) {
-        if (g->gc_len < g->NH) {
-            cudaFree(g->gc);
-            g->gc = nullptr;
-            g->gc_len = 0;
-            CK(cudaMalloc(&g->gc, 2 * (size_t)g->NH * sizeof(float4)), "cudaMalloc force scratch");
-            g->gc_len = g->NH;
-        }
-        CK(launch_forces_fast(ia, (const float2 *)w.chan, g->ph32, g->gc, dpart, nchunk, g->stream), "forces kernel");
-    } else {
-        CK(launch_forces<C>(ia, w.chan, dpart, nchunk, g->stream), "forces kernel");
-    }
-    CK(cudaMemcpyAsync(part.data(), dpart, part.size() * sizeof(double), cudaMemcpyDeviceToHost, g->stream),
+    if (fast)
+        CK(launch_forces_fast(ia, (const float2 *)w.chan, g->ph32, g->gc, g->fpart, nchunk, g->stream), "forces kernel");
+    else
+        CK(launch_forces<C>(ia, w.chan, g->fpart, nchunk, g->stream), "forces kernel");
+    CK(launch_reduce_force_partials(g->fpart, nsp, g->n_ions, nchunk, g->F_dev, g->stream), "force reduction");
+    return OFDFT_OK;
+}
+
+template <typename T> int forces_impl(ofdft_grid *g, const T *rho, double *F) {
+    int rc = forces_enqueue<T>(g, rho);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(F, g->F_dev, (size_t)3 * g->n_ions * sizeof(double), cudaMemcpyDeviceToHost, g->stream),
        "copy forces");
     CK(cudaStreamSynchronize(g->stream), "stream synchronize");
-    if (own) cudaFree(dpart);
-    for (int I = 0; I < g->n_ions; I++)
-        for (int d = 0; d < 3; d++) {
-            double sum = 0.0;
-            for (int sp = 0; sp < nsp; sp++)
-                for (int c = 0; c < nchunk; c++) sum += part[(((size_t)sp * g->n_ions + I) * nchunk + c) * 3 + d];
-            F[3 * I + d] = sum;
-        }
     return OFDFT_OK;
 }
 
@@ -832,6 +872,153 @@ int optimize_impl(ofdft_grid *g, T *psi, const ofdft_functional *f0, double Ne, 
     return small >= 3 ? OFDFT_OK : OFDFT_ERR_NOT_CONVERGED;
 }
 
+// ---------------------------------------------------------------- batched evaluation
+// Snapshots are spread over a few internal streams forked from (and joined back
+// into) the caller's stream, so that small grids overlap on the GPU; the whole
+// batch is captured once into a CUDA graph and replayed while the arguments and
+// the grids' device buffers are unchanged.
+constexpr int kBatchStreams = 4;
+
+struct BatchGraph {
+    std::vector<uintptr_t> key;
+    cudaGraphExec_t exec = nullptr;
+};
+
+std::vector<BatchGraph> &graph_cache() {
+    static std::vector<BatchGraph> c;
+    return c;
+}
+
+// kBatchStreams worker streams, then the stream a batch graph is captured on (the
+// caller's stream may be the legacy default stream, which cannot be captured)
+cudaStream_t *batch_streams() {
+    static cudaStream_t s[kBatchStreams + 1] = {nullptr};
+    static int device = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (!s[0] || device != dev) {
+        for (int k = 0; k <= kBatchStreams; k++) cudaStreamCreateWithFlags(&s[k], cudaStreamNonBlocking);
+        device = dev;
+    }
+    return s;
+}
+
+template <typename T> int prepare_batch_grid(ofdft_grid *g, const ofdft_functional *f, bool forces) {
+    const bool nl = f->terms & OFDFT_TERM_NL;
+    const bool lwt = nl && f->kernel == OFDFT_KERNEL_LWT;
+    const int nslots = nl ? (lwt ? 3 + f->n_knots : 4) : 3;
+    int rc = ensure_ws<T>(g, nslots);
+    if (rc) return rc;
+    if ((f->terms & OFDFT_TERM_PP) && (rc = ensure_vext<T>(g))) return rc;
+    if (forces && (rc = ensure_force_buffers<T>(g))) return rc;
+    return OFDFT_OK;
+}
+
+// enqueue the whole batch on the caller's stream (fork/join over internal streams)
+template <typename T>
+int enqueue_batch(int n, ofdft_grid *const *grids, const void *const *rho_dev, const ofdft_functional *f,
+                  void *const *V_dev, double *const *F_out, cudaStream_t user) {
+    cudaStream_t *st = batch_streams();
+    cudaEvent_t fork, join[kBatchStreams];
+    cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    for (int k = 0; k < kBatchStreams; k++) cudaEventCreateWithFlags(&join[k], cudaEventDisableTiming);
+    int rc = OFDFT_OK;
+    cudaEventRecord(fork, user);
+    for (int k = 0; k < kBatchStreams; k++) cudaStreamWaitEvent(st[k], fork, 0);
+    for (int i = 0; i < n && rc == OFDFT_OK; i++) {
+        ofdft_grid *g = grids[i];
+        const cudaStream_t saved = g->stream;
+        g->stream = st[i % kBatchStreams];
+        Workspace<T> &w = ws<T>(g);
+        rc = enqueue_eval<T>(g, (const T *)rho_dev[i], f, V_dev ? (T *)V_dev[i] : nullptr, nullptr);
+        if (rc == OFDFT_OK) {
+            cudaMemcpyAsync(g->h_pinned, w.energies, 6 * sizeof(double), cudaMemcpyDeviceToHost, g->stream);
+            cudaMemcpyAsync(g->h_pinned + 8, w.scal, S_NSCAL * sizeof(double), cudaMemcpyDeviceToHost, g->stream);
+        }
+        if (rc == OFDFT_OK && F_out && F_out[i]) {
+            rc = forces_enqueue<T>(g, (const T *)rho_dev[i]);
+            if (rc == OFDFT_OK)
+                cudaMemcpyAsync(g->F_pinned, g->F_dev, (size_t)3 * g->n_ions * sizeof(double), cudaMemcpyDeviceToHost,
+                                g->stream);
+        }
+        g->stream = saved;
+    }
+    for (int k = 0; k < kBatchStreams; k++) {
+        cudaEventRecord(join[k], st[k]);
+        cudaStreamWaitEvent(user, join[k], 0);
+    }
+    cudaEventDestroy(fork);
+    for (int k = 0; k < kBatchStreams; k++) cudaEventDestroy(join[k]);
+    return rc;
+}
+
+template <typename T>
+int batched_impl(int n, ofdft_grid *const *grids, const void *const *rho_dev, const ofdft_functional *f,
+                 double *E_out, void *const *V_dev, double *const *F_out) {
+    cudaStream_t user = grids[0]->stream;
+    ofdft_grid *g0 = grids[0];
+    for (int i = 0; i < n; i++) {
+        int rc = prepare_batch_grid<T>(grids[i], f, F_out && F_out[i]);
+        if (rc) return rc;
+    }
+    const char *env = std::getenv("OFDFT_BATCH_GRAPH");
+    bool use_graph = !(env && env[0] == '0') && !f->knots;
+    for (int i = 0; i < n; i++) use_graph = use_graph && !grids[i]->prof_on;
+    cudaError_t e;
+    if (use_graph) {
+        // key: functional, then per snapshot the grid, its buffer generation and the pointers
+        std::vector<uintptr_t> key;
+        const unsigned char *fb = (const unsigned char *)f;
+        for (size_t b = 0; b < sizeof(ofdft_functional); b++) key.push_back(fb[b]);
+        key.push_back((uintptr_t)user);
+        for (int i = 0; i < n; i++) {
+            key.push_back((uintptr_t)grids[i]);
+            key.push_back((uintptr_t)grids[i]->generation);
+            key.push_back((uintptr_t)rho_dev[i]);
+            key.push_back(V_dev ? (uintptr_t)V_dev[i] : 0);
+            key.push_back((F_out && F_out[i]) ? 1 : 0);
+        }
+        cudaGraphExec_t exec = nullptr;
+        for (auto &bg : graph_cache())
+            if (bg.key == key) exec = bg.exec;
+        if (!exec) {
+            cudaGraph_t graph = nullptr;
+            cudaStream_t origin = batch_streams()[kBatchStreams];
+            e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return fail(g0, OFDFT_ERR_CUDA, "begin capture", e);
+            int rc = enqueue_batch<T>(n, grids, rho_dev, f, V_dev, F_out, origin);
+            e = cudaStreamEndCapture(origin, &graph);
+            if (rc) {
+                if (graph) cudaGraphDestroy(graph);
+                return rc;
+            }
+            if (e != cudaSuccess) return fail(g0, OFDFT_ERR_CUDA, "end capture", e);
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return fail(g0, OFDFT_ERR_CUDA, "graph instantiate", e);
+            if (graph_cache().size() >= 16) {
+                cudaGraphExecDestroy(graph_cache().front().exec);
+                graph_cache().erase(graph_cache().begin());
+            }
+            graph_cache().push_back({key, exec});
+        }
+        e = cudaGraphLaunch(exec, user);
+        if (e != cudaSuccess) return fail(g0, OFDFT_ERR_CUDA, "graph launch", e);
+    } else {
+        int rc = enqueue_batch<T>(n, grids, rho_dev, f, V_dev, F_out, user);
+        if (rc) return rc;
+    }
+    e = cudaStreamSynchronize(user);
+    if (e != cudaSuccess) return fail(g0, OFDFT_ERR_CUDA, "stream synchronize", e);
+    for (int i = 0; i < n; i++) {
+        ofdft_grid *g = grids[i];
+        if (g->h_pinned[8 + S_BAD] != 0.0) return fail(g, OFDFT_ERR_BAD_DENSITY, "bad density in batch");
+        std::memcpy(E_out + 6 * i, g->h_pinned, 6 * sizeof(double));
+        if (F_out && F_out[i]) std::memcpy(F_out[i], g->F_pinned, (size_t)3 * g->n_ions * sizeof(double));
+    }
+    return OFDFT_OK;
+}
+
 }  // namespace
 
 // ====================================================================== ABI
@@ -931,6 +1118,9 @@ int ofdft_grid_destroy(ofdft_grid *g) {
     cudaFree(g->ph);
     cudaFree(g->ph32);
     cudaFree(g->gc);
+    cudaFree(g->fpart);
+    cudaFree(g->F_dev);
+    cudaFreeHost(g->F_pinned);
     cudaFree(g->pmeB);
     cudaFree(g->d_pos);
     cudaFree(g->Qfix);
@@ -1120,41 +1310,19 @@ int ofdft_energy_potential_batched(int n, ofdft_grid *const *grids, const void *
                                    const ofdft_functional *f, double *E_out, void *const *V_dev,
                                    double *const *F_out) {
     if (n < 0 || (n > 0 && (!grids || !rho_dev || !E_out))) return OFDFT_ERR_INVALID_ARG;
+    if (n == 0) return OFDFT_OK;
     for (int i = 0; i < n; i++) {
         if (!grids[i]) return OFDFT_ERR_INVALID_ARG;
         int rc = check_functional(grids[i], f);
         if (rc) return rc;
         if (grids[i]->stream != grids[0]->stream) return fail(grids[i], OFDFT_ERR_INVALID_ARG, "streams differ");
+        for (int j = 0; j < i; j++)
+            if (grids[j] == grids[i]) return fail(grids[i], OFDFT_ERR_INVALID_ARG, "a grid appears twice in the batch");
+        if (F_out && F_out[i] && !grids[i]->have_ions) return fail(grids[i], OFDFT_ERR_NO_IONS, "forces need ions");
     }
-    // enqueue every evaluation back to back; energies land in each grid's device slot
-    for (int i = 0; i < n; i++) {
-        ofdft_grid *g = grids[i];
-        void *V = V_dev ? V_dev[i] : nullptr;
-        int rc = (f->precision == OFDFT_FP64)
-                     ? enqueue_eval<double>(g, (const double *)rho_dev[i], f, (double *)V, nullptr)
-                     : enqueue_eval<float>(g, (const float *)rho_dev[i], f, (float *)V, nullptr);
-        if (rc) return rc;
-        double *Ed = (f->precision == OFDFT_FP64) ? g->w64.energies : g->w32.energies;
-        double *Sd = (f->precision == OFDFT_FP64) ? g->w64.scal : g->w32.scal;
-        CK(cudaMemcpyAsync(g->h_pinned, Ed, 6 * sizeof(double), cudaMemcpyDeviceToHost, g->stream), "copy E");
-        CK(cudaMemcpyAsync(g->h_pinned + 8, Sd, S_NSCAL * sizeof(double), cudaMemcpyDeviceToHost, g->stream),
-           "copy scalars");
-    }
-    if (n > 0) {
-        ofdft_grid *g = grids[0];
-        CK(cudaStreamSynchronize(g->stream), "stream synchronize");
-    }
-    for (int i = 0; i < n; i++) {
-        ofdft_grid *g = grids[i];
-        if (g->h_pinned[8 + S_BAD] != 0.0) return fail(g, OFDFT_ERR_BAD_DENSITY, "bad density in batch");
-        std::memcpy(E_out + 6 * i, g->h_pinned, 6 * sizeof(double));
-    }
-    for (int i = 0; i < n; i++) {
-        if (!F_out || !F_out[i]) continue;
-        int rc = ofdft_forces(grids[i], rho_dev[i], f->precision, F_out[i]);
-        if (rc) return rc;
-    }
-    return OFDFT_OK;
+    const bool fp64 = f->precision == OFDFT_FP64;
+    return fp64 ? batched_impl<double>(n, grids, rho_dev, f, E_out, V_dev, F_out)
+                : batched_impl<float>(n, grids, rho_dev, f, E_out, V_dev, F_out);
 }
 
 }  // extern "C"

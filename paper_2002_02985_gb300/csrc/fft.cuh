@@ -280,11 +280,10 @@ __device__ __forceinline__ void passes(C *buf, const C *tw) {
 }
 
 // B sequences of length N in buf (element e of sequence b at buf[e*LD + b]);
-// the caller synchronises before the call.  FP32 uses radix-16 passes (a
-// 128-point transform is 16 x 8), FP64 radix 8 at most (register budget).
-template <int DIR, int N, int B, int LD, int NT, typename C>
+// the caller synchronises before the call.  MAXR caps the power-of-two radix
+// (16: a 128-point transform is 16 x 8; 8: it is 8 x 8 x 2).
+template <int DIR, int N, int B, int LD, int NT, int MAXR, typename C>
 __device__ __forceinline__ void fft(C *buf, const C *tw) {
-    constexpr int MAXR = sizeof(C) == 8 ? 16 : 8;
     passes<DIR, N, B, LD, NT, MAXR, 0>(buf, tw);
 }
 

@@ -10,10 +10,15 @@
 #include "kernels.cuh"
 
 #define OFDFT_SPECIALISE(T, N, RB, RNT, PTW, PNT, ATW, ANT)                                   \
+    OFDFT_SPECIALISE_X(T, N, RB, RNT, PTW, PNT, ATW, ANT, (sizeof(T) == 4 ? 16 : 8), (sizeof(T) == 4 ? 16 : 8), 0, 0)
+
+// full form: RMAXR / AMAXR cap the radix of the row / axis-0 transforms, RMINB / AMINB
+// override the minimum resident blocks of the row / axis-0 kernels (0 = default)
+#define OFDFT_SPECIALISE_X(T, N, RB, RNT, PTW, PNT, ATW, ANT, RMAXR, AMAXR, RMINB, AMINB)        \
     if (n == N) {                                                                             \
-        typedef ::ofdft::CtPolicy<T, N, RB, RB + 1, RNT> PR;                                  \
+        typedef ::ofdft::CtPolicy<T, N, RB, RB + 1, RNT, RMAXR, RMINB> PR;                    \
         typedef ::ofdft::CtPolicy<T, N, PTW, PTW, PNT> PP;                                    \
-        typedef ::ofdft::CtPolicy<T, N, ATW, ATW, ANT> PA;                                    \
+        typedef ::ofdft::CtPolicy<T, N, ATW, ATW, ANT, AMAXR, AMINB> PA;                      \
         if (role == ROLE_ROW) {                                                               \
             *k1 = (const void *)row_fwd_kernel<T, PR>;                                        \
             *k2 = (const void *)row_inv_kernel<T, PR>;                                        \

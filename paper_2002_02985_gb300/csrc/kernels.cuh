@@ -26,20 +26,22 @@ template <typename T, int AX> struct RtPolicy {
     }
 };
 
-template <typename T, int N, int B__, int LD_, int NT__> struct CtPolicy {
+template <typename T, int N, int B__, int LD_, int NT__, int MAXR = (sizeof(T) == 4 ? 16 : 8), int MINB = 0>
+struct CtPolicy {
     typedef typename Vec2<T>::type C;
     static constexpr bool ct = true;
     static constexpr int N_ = N, B_ = B__, NT_ = NT__;
     // register budget: at least 768 resident threads per SM (24 warps)
-    static constexpr int max_threads = NT__, min_blocks = (768 / NT__) > 0 ? 768 / NT__ : 1;
+    static constexpr int max_threads = NT__;
+    static constexpr int min_blocks = MINB ? MINB : ((768 / NT__) > 0 ? 768 / NT__ : 1);
     // the reciprocal-space kernel holds more live state: at least 512 threads per SM
-    static constexpr int min_blocks_ax0 = (512 / NT__) > 0 ? 512 / NT__ : 1;
+    static constexpr int min_blocks_ax0 = MINB ? MINB : ((512 / NT__) > 0 ? 512 / NT__ : 1);
     __device__ static constexpr int n(const EvalArgs<T> &) { return N; }
     __device__ static constexpr int B(const EvalArgs<T> &) { return B__; }
     __device__ static constexpr int ld(const EvalArgs<T> &) { return LD_; }
     __device__ static constexpr int nt() { return NT__; }
     template <int DIR> __device__ static void fft(C *buf, const EvalArgs<T> &, const C *tw) {
-        ct::fft<DIR, N, B__, LD_, NT__>(buf, tw);
+        ct::fft<DIR, N, B__, LD_, NT__, MAXR>(buf, tw);
     }
 };
 

@@ -30,6 +30,9 @@ cudaError_t launch_forces_fast(const IonArgs &a, const float2 *rhohat, const flo
 template <typename C>
 cudaError_t launch_forces(const IonArgs &a, const C *rhohat, double *partials, int nchunk, cudaStream_t s);
 
+cudaError_t launch_reduce_force_partials(const double *part, int nsp, int n_ions, int nchunk, double *F,
+                                         cudaStream_t s);
+
 // plain forward FFT along n0 of a half spectrum (in place), used by forces
 template <typename T>
 cudaError_t launch_axis0_fft(typename Vec2<T>::type *data, int n0, long long P, const FFTPlan &p,

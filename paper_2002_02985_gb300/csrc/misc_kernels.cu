@@ -246,6 +246,22 @@ cudaError_t launch_forces_fast(const IonArgs &a, const float2 *rhohat, const flo
     return e;
 }
 
+// F[I][d] = sum over species and chunks of the partials [nsp][n_ions][nchunk][3] (fixed order)
+__global__ void reduce_force_partials_kernel(const double *part, int nsp, int n_ions, int nchunk, double *F) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3 * n_ions) return;
+    const int I = t / 3, d = t - 3 * I;
+    double s = 0.0;
+    for (int sp = 0; sp < nsp; sp++)
+        for (int c = 0; c < nchunk; c++) s += part[(((size_t)sp * n_ions + I) * nchunk + c) * 3 + d];
+    F[t] = s;
+}
+cudaError_t launch_reduce_force_partials(const double *part, int nsp, int n_ions, int nchunk, double *F,
+                                         cudaStream_t s) {
+    reduce_force_partials_kernel<<<(3 * n_ions + 255) / 256, 256, 0, s>>>(part, nsp, n_ions, nchunk, F);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- plain FFT along n0
 template <typename T, int CAP, int DIR>
 __global__ void __launch_bounds__(512) axis0_fft_kernel(typename Vec2<T>::type *data, int n0, long long P, FFTPlan p,

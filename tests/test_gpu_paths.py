@@ -107,7 +107,11 @@ def test_autograd_matches_finite_differences():
         assert abs(fdF - float(pos.grad[I, a])) <= 1e-7 + 1e-6 * abs(fdF)
 
 
-def test_batched_equals_single_evaluations():
+@pytest.mark.parametrize("graph", ["1", "0"])
+def test_batched_equals_single_evaluations(graph, monkeypatch):
+    """Batched snapshots (fork/join over internal streams; captured into a CUDA graph
+    and replayed when graph = 1) give bit-identical results to single calls."""
+    monkeypatch.setenv("OFDFT_BATCH_GRAPH", graph)
     grids, rhos, singles = [], [], []
     f = ofd.Functional(n_knots=16)
     for s in range(4):
@@ -124,8 +128,10 @@ def test_batched_equals_single_evaluations():
         rhos.append(r)
         E, V = g.energy_potential(r, f)
         singles.append((E, V, g.forces(r)))
-    E, Vs, Fs = ofd.energy_potential_batched(grids, rhos, f, want_potential=True, want_forces=True)
-    for i, (Es, Vsg, Fsg) in enumerate(singles):
-        assert np.array_equal(E[i], np.array([Es[k] for k in ofd.ENERGY_KEYS]))
-        assert torch.equal(Vs[i], Vsg)
-        assert np.array_equal(Fs[i], Fsg)
+    Vbuf = [torch.empty_like(r) for r in rhos]
+    for rep in range(3):                      # first call captures, later calls replay
+        E, Vs, Fs = ofd.energy_potential_batched(grids, rhos, f, want_potential=True, want_forces=True, V_out=Vbuf)
+        for i, (Es, Vsg, Fsg) in enumerate(singles):
+            assert np.array_equal(E[i], np.array([Es[k] for k in ofd.ENERGY_KEYS]))
+            assert torch.equal(Vs[i], Vsg)
+            assert np.array_equal(Fs[i], Fsg)
