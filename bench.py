@@ -63,8 +63,12 @@ class Clocks:
             os.makedirs(os.path.dirname(self.out), exist_ok=True)
             self.f = open(self.out, "w")
             self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
+            # start timing only once the sampler is producing lines (nvidia-smi takes a moment)
+            t0 = time.time()
+            while time.time() - t0 < 5.0 and os.path.getsize(self.out) == 0 and self.p.poll() is None:
+                time.sleep(0.02)
         except Exception:
             self.p = None
 
@@ -518,7 +522,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
