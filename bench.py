@@ -263,7 +263,7 @@ def run_scale(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "fcc-al-1m/1024", "grid": [1024] * 3, "atoms": wl["n_atoms"], "n_knots": 12,
                        "structure_factor": "PME order %d" % order, "l2": "inputs 4.3 GB > L2"},
-            "kernels": {k: {"launches": n, "avg_ms": round(v / max(1, n), 3)} for k, (n, v) in prof.items()},
+            "kernels": {k: {"launches": n, "avg_ms": round(v / max(1, n), 3)} for k, (n, v) in prof.items() if n},
             "checks": out}
     if args.optimize:
         psi = rho.sqrt()
@@ -392,7 +392,7 @@ def run_gpu(args):
             "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
             "algorithmic_bytes_per_launch": alg, "avg_launch_ms": round(avg_s * 1e3, 5)}
     kernels = {k: {"launches": n, "avg_ms": round(t / max(1, n), 5), "share": round(t / max(1e-12, sum(
-        v[1] for v in prof.values())), 4)} for k, (n, t) in prof.items()}
+        v[1] for v in prof.values())), 4)} for k, (n, t) in prof.items() if n}
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t_max, 5), "higher_is_better": True, "scaling": "weak",

@@ -69,10 +69,12 @@ template <typename T> struct Workspace {
     double *scal = nullptr, *energies = nullptr, *knots_d = nullptr;
     T *knots_t = nullptr, *invdk_t = nullptr, *part_minmax = nullptr;
     double *part_stats = nullptr, *part_ax0 = nullptr, *part_row = nullptr, *part_misc = nullptr;
+    unsigned *ticket = nullptr;       // stats completion counter
     T *opt = nullptr;                 // optimiser fields (8 * N), allocated on demand
     LaunchSet ks;                     // FFT-carrying kernels (size-specialised where compiled)
     int Brow = 0, thr_rowf = 0, thr_rowi = 0, TW1 = 0, thr_p1 = 0, TW0 = 0, thr_ax0 = 0, nb_row = 0, nb_ax0 = 0;
     int grid_p1 = 0;
+    int row2_G = 0;                   // channel-batched row kernels in use: channels per group
 };
 
 }  // namespace
@@ -161,8 +163,18 @@ template <typename T> int choose_launch(ofdft_grid *g, Workspace<T> &w) {
     w.ks = generic_kernels<T>();
     const void *k1 = nullptr, *k2 = nullptr;
     int Bv = 0, ntv = 0;
-    // rows (n2)
-    if (!generic_only && find_specialised<T>(ROLE_ROW, g->n[2], &k1, &k2, &Bv, &ntv)) {
+    // rows (n2): the channel-batched form where compiled (OFDFT_ROW_PER_CHANNEL=1 keeps the
+    // per-channel form, for comparison), else the per-channel form
+    const char *env_rows = std::getenv("OFDFT_ROW_PER_CHANNEL");
+    const bool per_channel = env_rows && env_rows[0] == '1';
+    w.row2_G = 0;
+    if (!generic_only && !per_channel && find_specialised<T>(ROLE_ROW2, g->n[2], &k1, &k2, &Bv, &ntv)) {
+        w.ks.row_fwd = k1;
+        w.ks.row_inv = k2;
+        w.Brow = 1;
+        w.row2_G = Bv;
+        w.thr_rowf = w.thr_rowi = ntv;
+    } else if (!generic_only && find_specialised<T>(ROLE_ROW, g->n[2], &k1, &k2, &Bv, &ntv)) {
         w.ks.row_fwd = k1;
         w.ks.row_inv = k2;
         w.Brow = Bv;
@@ -246,6 +258,8 @@ template <typename T> int ensure_ws(ofdft_grid *g, int nslots) {
         CK(cudaMalloc(&w.part_ax0, 4 * (size_t)w.nb_ax0 * sizeof(double)), "cudaMalloc partials");
         CK(cudaMalloc(&w.part_row, (size_t)w.nb_row * sizeof(double)), "cudaMalloc partials");
         CK(cudaMalloc(&w.part_misc, 4096 * sizeof(double)), "cudaMalloc partials");
+        CK(cudaMalloc(&w.ticket, sizeof(unsigned)), "cudaMalloc ticket");
+        CK(cudaMemset(w.ticket, 0, sizeof(unsigned)), "memset ticket");
         w.ready = true;
     }
     if (nslots > w.nslots) {
@@ -273,6 +287,7 @@ template <typename T> void free_ws(Workspace<T> &w) {
     cudaFree(w.part_ax0);
     cudaFree(w.part_row);
     cudaFree(w.part_misc);
+    cudaFree(w.ticket);
     cudaFree(w.opt);
     w = Workspace<T>();
 }
@@ -427,6 +442,7 @@ int enqueue_eval(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, d
     a.part_ax0 = w.part_ax0;
     a.part_row = w.part_row;
     a.energies = E_dev_out ? E_dev_out : w.energies;
+    a.ticket = w.ticket;
     a.nb_stats = 2 * g->nsm;
     a.nb_ax0 = w.nb_ax0;
     a.nb_row = w.nb_row;
@@ -444,6 +460,7 @@ int enqueue_eval(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, d
     a.TW0 = w.TW0;
     a.thr_ax0 = w.thr_ax0;
     a.grid_p1 = w.grid_p1;
+    a.row2_G = w.row2_G;
     // channel lists
     const bool hpp = f->terms & (OFDFT_TERM_HARTREE | OFDFT_TERM_PP);
     const bool vw = f->terms & OFDFT_TERM_VW;
@@ -514,13 +531,14 @@ template <typename T> EvalArgs<T> plain_args(ofdft_grid *g, Workspace<T> &w, con
     a.omega = g->omega; a.dV = g->dV;
     a.rho = field; a.chan = w.chan; a.terms = OFDFT_TERM_HARTREE; a.floor_ = (T)1e-30;
     a.scal = w.scal; a.knots_d = w.knots_d; a.knots_t = w.knots_t; a.invdk_t = w.invdk_t;
-    a.part_stats = w.part_stats; a.part_minmax = w.part_minmax; a.energies = w.energies;
+    a.part_stats = w.part_stats; a.part_minmax = w.part_minmax; a.energies = w.energies; a.ticket = w.ticket;
     a.part_ax0 = w.part_ax0; a.part_row = w.part_row;
     a.nb_stats = 2 * g->nsm; a.nb_ax0 = w.nb_ax0; a.nb_row = w.nb_row;
     a.p0 = g->plan[0]; a.p1 = g->plan[1]; a.p2 = g->plan[2];
     a.tw0 = w.tw[0]; a.tw1 = w.tw[1]; a.tw2 = w.tw[2];
     a.Brow = w.Brow; a.thr_rowf = w.thr_rowf; a.thr_rowi = w.thr_rowi;
     a.TW1 = w.TW1; a.thr_p1 = w.thr_p1; a.TW0 = w.TW0; a.thr_ax0 = w.thr_ax0; a.grid_p1 = w.grid_p1;
+    a.row2_G = w.row2_G;
     a.nfwd = 1; a.fwd_ch[0] = CH_HPP; a.ncol = 1; a.col_ch[0] = CH_HPP;
     return a;
 }

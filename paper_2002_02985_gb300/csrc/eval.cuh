@@ -1,8 +1,8 @@
 // Parameters and launch entry points of the energy/potential pipeline.
 //
 // One evaluation (Sec. 2.3 steps s1-s4 plus the semilocal terms) runs as:
-//   stats     one pass over rho: sum rho, sum rho^(5/3), min/max rho, bad-value flag
-//   knots     1 block: FP64 reduction of the stats, mean density, kF knots (s1)
+//   stats     one pass over rho: sum rho, sum rho^(5/3), min/max rho, bad-value flag;
+//             its last block reduces the partials in FP64: mean density, kF knots (s1)
 //   row_fwd   per pair of rows: forms each channel field from rho and does the
 //             real-to-complex FFT along n2
 //   pencil    complex FFT along n1 for all channels
@@ -63,11 +63,13 @@ template <typename T> struct EvalArgs {
     double *part_ax0;        // [nb_ax0 * 3]: S_H, S_vW, S_PP
     double *part_row;        // [nb_row]: S_NL
     double *energies;        // [6] device output
+    unsigned *ticket;        // completion counter of the stats blocks (zero between launches)
     int nb_stats, nb_ax0, nb_row;
     FFTPlan p0, p1, p2;
     const C *tw0, *tw1, *tw2;
     int Brow, thr_rowf, thr_rowi, TW1, thr_p1, TW0, thr_ax0;
     int grid_p1;                         // persistent grid of the n1 pencil kernels
+    int row2_G;                          // channel-batched row kernels: channels per group (0: per-channel form)
     int nfwd, fwd_ch[kMaxChan];          // channels formed by row_fwd (slot ids)
     int ncol, col_ch[kMaxChan];          // channels transformed forward along n1
     int ncol_inv, col_inv_ch[kMaxChan];  // channels transformed back along n1
@@ -113,6 +115,20 @@ template <typename T> __host__ __device__ inline size_t row_inv_smem_bytes(int n
     return n2 * sizeof(C) + row_buf_bytes<T>(n2, B) + P * (6 * sizeof(T) + 1) + 16;
 }
 
+// channel-batched row kernels: twiddles + two n2 x LD complex buffers (LD = G, or G + 1 if G
+// is even): the batch and the scratch of the out-of-place transform
+template <typename T> __host__ __device__ inline size_t row2_smem_bytes(int n2, int G) {
+    typedef typename Vec2<T>::type C;
+    const int ld = (G % 2) ? G : G + 1;
+    return (size_t)n2 * sizeof(C) + 2 * (size_t)n2 * ld * sizeof(C) + 16;
+}
+template <typename T> __host__ __device__ inline size_t rowf_smem(const EvalArgs<T> &a) {
+    return a.row2_G ? row2_smem_bytes<T>(a.n2, a.row2_G) : row_fwd_smem_bytes<T>(a.n2, a.Brow);
+}
+template <typename T> __host__ __device__ inline size_t rowi_smem(const EvalArgs<T> &a) {
+    return a.row2_G ? row2_smem_bytes<T>(a.n2, a.row2_G) : row_inv_smem_bytes<T>(a.n2, a.Brow);
+}
+
 // The five FFT-carrying kernels of one evaluation (generic or size-specialised).
 struct LaunchSet {
     const void *row_fwd = nullptr, *row_inv = nullptr;   // depend on n2
@@ -121,7 +137,7 @@ struct LaunchSet {
 };
 
 // role of a kernel family for the size registry
-enum { ROLE_ROW = 0, ROLE_PENCIL = 1, ROLE_AXIS0 = 2 };
+enum { ROLE_ROW = 0, ROLE_PENCIL = 1, ROLE_AXIS0 = 2, ROLE_ROW2 = 3 };
 
 // Size-specialised kernels of a role for size n, with their fixed batch (B or
 // TW) and block size; false when none is compiled for that size/precision.

@@ -55,15 +55,11 @@ cudaError_t launch_eval(const EvalArgs<T> &a, const LaunchSet &ks, cudaStream_t 
         if (ph) ph->record(ph->ctx, id, phase, s);
     };
     mark(K_STATS, 0);
-    stats_kernel<T><<<a.nb_stats, 256, 0, s>>>(a);
+    stats_kernel<T><<<a.nb_stats, 256, 0, s>>>(a);        // (its last block makes the knots)
     mark(K_STATS, 1);
-    mark(K_KNOTS, 0);
-    knots_kernel<T><<<1, 256, 0, s>>>(a);
-    if ((a.terms & 4u) && a.kernel == 0 && a.M >= 2) knots_make_kernel<T><<<1, 64, 0, s>>>(a);
-    mark(K_KNOTS, 1);
     if (a.nfwd > 0) {
         mark(K_ROW_FWD, 0);
-        e = launch(ks.row_fwd, dim3(nrt), a.thr_rowf, row_fwd_smem_bytes<T>(a.n2, a.Brow), a, s);
+        e = launch(ks.row_fwd, dim3(nrt), a.thr_rowf, rowf_smem<T>(a), a, s);
         if (e) return e;
         mark(K_ROW_FWD, 1);
     }
@@ -85,11 +81,11 @@ cudaError_t launch_eval(const EvalArgs<T> &a, const LaunchSet &ks, cudaStream_t 
         mark(K_PENCIL_INV, 1);
     }
     mark(K_ROW_INV, 0);
-    e = launch(ks.row_inv, dim3(nrt), a.thr_rowi, row_inv_smem_bytes<T>(a.n2, a.Brow), a, s);
+    e = launch(ks.row_inv, dim3(nrt), a.thr_rowi, rowi_smem<T>(a), a, s);
     if (e) return e;
     mark(K_ROW_INV, 1);
     mark(K_FINALIZE, 0);
-    finalize_kernel<T><<<1, 256, 0, s>>>(a);
+    finalize_kernel<T><<<1, 1024, 0, s>>>(a);
     mark(K_FINALIZE, 1);
     return cudaGetLastError();
 }
@@ -99,8 +95,7 @@ template <typename T> cudaError_t launch_forward_rows_cols(const EvalArgs<T> &a,
     const long long pairs = (R + 1) / 2;
     const int nrt = (int)((pairs + a.Brow - 1) / a.Brow);
     stats_kernel<T><<<a.nb_stats, 256, 0, s>>>(a);
-    knots_kernel<T><<<1, 256, 0, s>>>(a);
-    cudaError_t e = launch(ks.row_fwd, dim3(nrt), a.thr_rowf, row_fwd_smem_bytes<T>(a.n2, a.Brow), a, s);
+    cudaError_t e = launch(ks.row_fwd, dim3(nrt), a.thr_rowf, rowf_smem<T>(a), a, s);
     if (e) return e;
     e = launch(ks.pen_fwd, dim3(pencil_tiles(a, a.ncol)), a.thr_p1, pencil_smem_bytes<T>(a.n1, a.TW1), a, s);
     if (e) return e;
@@ -115,7 +110,7 @@ cudaError_t launch_inverse_cols_rows(const EvalArgs<T> &a, const LaunchSet &ks, 
     cudaError_t e = launch(ks.pen_inv, dim3(pencil_tiles(a, a.ncol_inv)), a.thr_p1,
                            pencil_smem_bytes<T>(a.n1, a.TW1), a, s);
     if (e) return e;
-    e = launch(ks.row_inv, dim3(nrt), a.thr_rowi, row_inv_smem_bytes<T>(a.n2, a.Brow), a, s);
+    e = launch(ks.row_inv, dim3(nrt), a.thr_rowi, rowi_smem<T>(a), a, s);
     if (e) return e;
     return cudaGetLastError();
 }

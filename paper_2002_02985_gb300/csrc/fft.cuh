@@ -287,5 +287,54 @@ __device__ __forceinline__ void fft(C *buf, const C *tw) {
     passes<DIR, N, B, LD, NT, MAXR, 0>(buf, tw);
 }
 
+// Out-of-place form of the same passes: each butterfly reads its R inputs from
+// `in` and writes its outputs to `out` at once, so nothing is held across a
+// barrier (registers: one butterfly at a time) and a pass needs one barrier.
+template <int DIR, int R, int N, int NS, int B, int LD, int NT, typename C>
+__device__ __forceinline__ void pass_oop(const C *in, C *out, const C *tw) {
+    constexpr int NB = N / R, TOT = NB * B, STRIDE = N / (NS * R);
+#pragma unroll
+    for (int idx0 = 0; idx0 < TOT; idx0 += NT) {
+        const int idx = idx0 + threadIdx.x;
+        if (TOT % NT == 0 || idx < TOT) {
+            const int b = idx % B, j = idx / B, k = j % NS;
+            C v[R];
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                C x = in[(j + r * NB) * LD + b];
+                if (NS > 1 && r > 0) {
+                    C w = tw[r * k * STRIDE];
+                    if (DIR > 0) w.y = -w.y;
+                    x = cmul(x, w);
+                }
+                v[r] = x;
+            }
+            dft<DIR, R>(v);
+            const int dst = (j / NS) * NS * R + k;
+#pragma unroll
+            for (int r = 0; r < R; r++) out[(dst + r * NS) * LD + b] = v[r];
+        }
+    }
+    __syncthreads();
+}
+
+template <int DIR, int N, int B, int LD, int NT, int MAXR, int P, typename C>
+__device__ __forceinline__ C *passes_oop(C *x, C *y, const C *tw) {
+    if constexpr (P < npass(N, MAXR)) {
+        pass_oop<DIR, radix(N, P, MAXR), N, ns(N, P, MAXR), B, LD, NT>(x, y, tw);
+        return passes_oop<DIR, N, B, LD, NT, MAXR, P + 1>(y, x, tw);
+    } else {
+        return x;
+    }
+}
+
+// B sequences of length N in x (layout as fft above), y a scratch buffer of the
+// same size; returns the buffer that holds the transform (x or y by the parity
+// of the pass count).  The caller synchronises before the call.
+template <int DIR, int N, int B, int LD, int NT, int MAXR, typename C>
+__device__ __forceinline__ C *fft_oop(C *x, C *y, const C *tw) {
+    return passes_oop<DIR, N, B, LD, NT, MAXR, 0>(x, y, tw);
+}
+
 }  // namespace ct
 }  // namespace ofdft

@@ -15,7 +15,7 @@
 // full form: RMAXR / AMAXR cap the radix of the row / axis-0 transforms, RMINB / AMINB
 // override the minimum resident blocks of the row / axis-0 kernels (0 = default)
 #define OFDFT_SPECIALISE_X(T, N, RB, RNT, PTW, PNT, ATW, ANT, RMAXR, AMAXR, RMINB, AMINB)        \
-    if (n == N) {                                                                             \
+    if (n == N && role != ROLE_ROW2) {                                                        \
         typedef ::ofdft::CtPolicy<T, N, RB, RB + 1, RNT, RMAXR, RMINB> PR;                    \
         typedef ::ofdft::CtPolicy<T, N, PTW, PTW, PNT> PP;                                    \
         typedef ::ofdft::CtPolicy<T, N, ATW, ATW, ANT, AMAXR, AMINB> PA;                      \
@@ -35,5 +35,18 @@
             *B = ATW;                                                                         \
             *nt = ANT;                                                                        \
         }                                                                                     \
+        return true;                                                                          \
+    }
+
+// OFDFT_SPECIALISE_ROW2(T, N, G, NT, MAXR, MINB): the channel-batched row kernels
+// for n2 = N (one pair of rows per block, G channels per transform, NT threads,
+// at least MINB resident blocks per SM).
+#define OFDFT_SPECIALISE_ROW2(T, N, G, NT, MAXR, MINB)                                        \
+    if (role == ROLE_ROW2 && n == N) {                                                        \
+        typedef ::ofdft::RowPolicy2<T, N, G, NT, MAXR, MINB> PQ;                              \
+        *k1 = (const void *)row_fwd2_kernel<T, PQ>;                                           \
+        *k2 = (const void *)row_inv2_kernel<T, PQ>;                                           \
+        *B = G;                                                                               \
+        *nt = NT;                                                                             \
         return true;                                                                          \
     }

@@ -15,6 +15,10 @@ static bool variant_128(int v, int role, int n, const void **k1, const void **k2
         case 2: OFDFT_SPECIALISE_X(float, 128, 8, 128, 16, 256, 8, 128, 8, 16, 0, 5) break;
         case 3: OFDFT_SPECIALISE_X(float, 128, 16, 256, 16, 256, 16, 256, 8, 8, 0, 0) break;
         case 4: OFDFT_SPECIALISE_X(float, 128, 4, 128, 16, 256, 8, 256, 8, 8, 0, 0) break;
+        case 5: OFDFT_SPECIALISE_ROW2(float, 128, 20, 160, 16, 4) break;
+        case 6: OFDFT_SPECIALISE_X(float, 128, 8, 256, 16, 256, 8, 64, 16, 16, 0, 0) break;
+        case 7: OFDFT_SPECIALISE_X(float, 128, 8, 256, 16, 256, 16, 128, 16, 16, 0, 2) break;
+        case 8: OFDFT_SPECIALISE_X(float, 128, 8, 256, 16, 256, 8, 128, 16, 8, 0, 0) break;
         default: break;
     }
     return false;
@@ -26,7 +30,9 @@ template <> bool find_specialised_a<float>(int role, int n, const void **k1, con
         const int v = env ? std::atoi(env) : 0;
         if (v > 0 && variant_128(v, role, n, k1, k2, B, nt)) return true;
     }
+    OFDFT_SPECIALISE_ROW2(float, 128, 20, 160, 16, 5)
     OFDFT_SPECIALISE(float, 128, 8, 256, 16, 256, 8, 128)
+    OFDFT_SPECIALISE_ROW2(float, 32, 16, 64, 16, 10)
     OFDFT_SPECIALISE(float, 32, 16, 128, 16, 128, 16, 128)
     return false;
 }

@@ -102,6 +102,67 @@ template <typename T> __device__ __forceinline__ int knot_interval(T kc, const T
     return lo;
 }
 
+// ======================================================================= knots (s1)
+// FP64 reduction of the stats partials (read through L2: they were written by
+// other blocks of the same launch), the mean density, E_TF, and the M knots
+// between kF(min rho) and kF(max rho).  Called by the last stats block.
+template <typename T>
+__device__ __forceinline__ void knots_from_partials(const EvalArgs<T> &a, double *sd, T *st) {
+    __shared__ double kn[OFDFT_MAX_KNOTS];
+    __shared__ double smm[2];
+    double s_rho = 0.0, s_tf = 0.0;
+    T mn = (T)3.0e38, mx = (T)-3.0e38;
+    for (int b = threadIdx.x; b < a.nb_stats; b += blockDim.x) {
+        s_rho += __ldcg(a.part_stats + 2 * b);
+        s_tf += __ldcg(a.part_stats + 2 * b + 1);
+        const T x = __ldcg(a.part_minmax + 2 * b), y = __ldcg(a.part_minmax + 2 * b + 1);
+        mn = x < mn ? x : mn;
+        mx = y > mx ? y : mx;
+    }
+    s_rho = block_sum(s_rho, sd);
+    s_tf = block_sum(s_tf, sd);
+    mn = block_min(mn, st);
+    mx = block_max(mx, st);
+    const double fl = (double)a.floor_;
+    if (threadIdx.x == 0) {
+        a.scal[S_SUM_RHO] = s_rho;
+        a.scal[S_SUM_TF] = s_tf;
+        a.scal[S_RHO_MIN] = (double)mn;
+        a.scal[S_RHO_MAX] = (double)mx;
+        const double mean = s_rho / (double)a.N;
+        a.scal[S_RHO_MEAN] = mean;
+        a.scal[S_KF_WT] = cbrt(kThreePi2 * (mean > fl ? mean : fl));
+        a.energies[E_TF] = (a.terms & 1u) ? kCTF * s_tf * a.dV : 0.0;
+        smm[0] = (double)mn;
+        smm[1] = (double)mx;
+    }
+    __syncthreads();
+    if (!((a.terms & 4u) && a.kernel == 0 && a.M >= 2)) return;
+    // s1: one thread per knot, in FP64
+    const int M = a.M, m = threadIdx.x;
+    if (m < M) {
+        double k;
+        if (!a.frozen) {
+            const double kmin = cbrt(kThreePi2 * (smm[0] > fl ? smm[0] : fl));
+            const double kmax = cbrt(kThreePi2 * (smm[1] > fl ? smm[1] : fl));
+            if (m == 0) k = kmin;
+            else if (m == M - 1) k = kmax;
+            else if (a.knot_spacing == 0) k = kmin * exp((double)m * (log(kmax / kmin) / (double)(M - 1)));
+            else k = kmin + (double)m * ((kmax - kmin) / (double)(M - 1));
+            a.knots_d[m] = k;
+        } else {
+            k = a.knots_d[m];
+        }
+        kn[m] = k;
+        a.knots_t[m] = (T)k;
+    }
+    __syncthreads();
+    if (m + 1 < M) {
+        const double dk = kn[m + 1] - kn[m];
+        a.invdk_t[m] = dk > 0.0 ? (T)(1.0 / dk) : (T)0;
+    }
+}
+
 // ======================================================================= stats (s1 input)
 template <typename T>
 __global__ void __launch_bounds__(256) stats_kernel(EvalArgs<T> a) {
@@ -140,68 +201,15 @@ __global__ void __launch_bounds__(256) stats_kernel(EvalArgs<T> a) {
     if (threadIdx.x == 0) a.part_minmax[2 * blockIdx.x + 1] = mx;
     bad = __syncthreads_or(bad);
     if (threadIdx.x == 0 && bad) a.scal[S_BAD] = 1.0;
-}
-
-// ======================================================================= knots (s1)
-template <typename T>
-__global__ void __launch_bounds__(256) knots_kernel(EvalArgs<T> a) {
-    __shared__ double sd[32];
-    __shared__ T st[32];
-    double s_rho = 0.0, s_tf = 0.0;
-    T mn = (T)3.0e38, mx = (T)-3.0e38;
-    for (int b = threadIdx.x; b < a.nb_stats; b += blockDim.x) {
-        s_rho += a.part_stats[2 * b];
-        s_tf += a.part_stats[2 * b + 1];
-        const T x = a.part_minmax[2 * b], y = a.part_minmax[2 * b + 1];
-        mn = x < mn ? x : mn;
-        mx = y > mx ? y : mx;
-    }
-    s_rho = block_sum(s_rho, sd);
-    s_tf = block_sum(s_tf, sd);
-    mn = block_min(mn, st);
-    mx = block_max(mx, st);
-    if (threadIdx.x != 0) return;
-    const double fl = (double)a.floor_;
-    a.scal[S_SUM_RHO] = s_rho;
-    a.scal[S_SUM_TF] = s_tf;
-    a.scal[S_RHO_MIN] = (double)mn;
-    a.scal[S_RHO_MAX] = (double)mx;
-    const double mean = s_rho / (double)a.N;
-    a.scal[S_RHO_MEAN] = mean;
-    a.scal[S_KF_WT] = cbrt(kThreePi2 * (mean > fl ? mean : fl));
-    a.energies[E_TF] = (a.terms & 1u) ? kCTF * s_tf * a.dV : 0.0;
-}
-
-// s1: M knots between kF(min rho) and kF(max rho) in FP64, one thread per knot
-// (min/max from knots_kernel's reduction); a separate launch so the reduction
-// block does no serial FP64 work.
-template <typename T>
-__global__ void __launch_bounds__(64) knots_make_kernel(EvalArgs<T> a) {
-    __shared__ double kn[OFDFT_MAX_KNOTS];
-    const int M = a.M, m = threadIdx.x;
-    if (m < M) {
-        double k;
-        if (!a.frozen) {
-            const double fl = (double)a.floor_;
-            const double mn = a.scal[S_RHO_MIN], mx = a.scal[S_RHO_MAX];
-            const double kmin = cbrt(kThreePi2 * (mn > fl ? mn : fl));
-            const double kmax = cbrt(kThreePi2 * (mx > fl ? mx : fl));
-            if (m == 0) k = kmin;
-            else if (m == M - 1) k = kmax;
-            else if (a.knot_spacing == 0) k = kmin * exp((double)m * (log(kmax / kmin) / (double)(M - 1)));
-            else k = kmin + (double)m * ((kmax - kmin) / (double)(M - 1));
-            a.knots_d[m] = k;
-        } else {
-            k = a.knots_d[m];
-        }
-        kn[m] = k;
-        a.knots_t[m] = (T)k;
-    }
+    // the last block to finish reduces every block's partials and makes the knots
+    __shared__ bool last;
+    __threadfence();
+    if (threadIdx.x == 0) last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
     __syncthreads();
-    if (m + 1 < M) {
-        const double dk = kn[m + 1] - kn[m];
-        a.invdk_t[m] = dk > 0.0 ? (T)(1.0 / dk) : (T)0;
-    }
+    if (!last) return;
+    __threadfence();
+    knots_from_partials(a, sd, st);
+    if (threadIdx.x == 0) *a.ticket = 0u;           // ready for the next evaluation
 }
 
 // ======================================================================= row forward (R2C along n2)
@@ -327,6 +335,7 @@ __device__ __forceinline__ void pencil1_body(const EvalArgs<T> &a) {
         const int ch = DIR < 0 ? a.col_ch[ci] : a.col_inv_ch[ci];
         return a.chan + (size_t)ch * a.NH;
     };
+    // (NT is a multiple of TW, so a thread's column w, hence the division, is loop invariant)
     auto prefetch = [&](int t, C *dst) {
         long long c0;
         const C *base = tile_base(t, c0);
@@ -757,9 +766,305 @@ __device__ __forceinline__ void row_inv_body(const EvalArgs<T> &a) {
     if (threadIdx.x == 0) a.part_row[blockIdx.x] = eNL;
 }
 
+// ======================================================================= rows, channel-batched form
+// One pair of rows (2p, 2p+1) per block.  Instead of transforming the channels
+// one after another, all channels of a group of up to G are formed and
+// transformed together: the batch index of the shared-memory FFT is the channel
+// slot, so every pass has work for every thread and one transform per group
+// replaces one per channel.  Each thread owns fixed points of the pair (element
+// e of the packed sequence = points (2p, e) and (2p+1, e)) for the whole
+// kernel, so the per-point quantities (rho^alpha, knot interval, spline
+// weights) live in registers and a point reads only the channels it needs: the
+// semilocal ones and the two knots that bracket its kF.
+template <typename T, int N, int G, int NT, int MAXR, int MINB>
+struct RowPolicy2 {
+    typedef typename Vec2<T>::type C;
+    static constexpr int N_ = N, G_ = G, NT_ = NT, LD = (G % 2) ? G : G + 1;
+    static constexpr int E = (N + NT - 1) / NT;      // elements (pairs of points) per thread
+    static constexpr int min_blocks = MINB;
+    template <int DIR> __device__ static C *fft(C *x, C *y, const C *tw) {
+        return ct::fft_oop<DIR, N, G, LD, NT, MAXR>(x, y, tw);
+    }
+};
+
+template <typename T, class Q>
+__device__ __forceinline__ void row_fwd2_body(const EvalArgs<T> &a) {
+    typedef typename Vec2<T>::type C;
+    constexpr int n = Q::N_, G = Q::G_, LD = Q::LD, NT = Q::NT_, E = Q::E, n2h = n / 2 + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tw = (C *)smem_raw;
+    C *buf = tw + n;                 // the channel batch, formed here
+    C *scr = buf + n * LD;           // scratch of the out-of-place transform
+    __shared__ T sk[OFDFT_MAX_KNOTS], sdk[OFDFT_MAX_KNOTS];
+    __shared__ int sch[kMaxChan], skpos;
+    const long long R = (long long)a.n0 * a.n1;
+    const long long row0 = 2LL * blockIdx.x;
+    const bool has1 = row0 + 1 < R;
+    const bool nl = a.terms & 4u, lwt = nl && a.kernel == 0;
+    const int M = a.M, nf = a.nfwd;
+    for (int i = threadIdx.x; i < n; i += NT) tw[i] = a.tw2[i];
+    if (lwt)
+        for (int i = threadIdx.x; i < M; i += NT) {
+            sk[i] = a.knots_t[i];
+            sdk[i] = a.invdk_t[i];
+        }
+    for (int i = threadIdx.x; i < nf; i += NT) sch[i] = a.fwd_ch[i];
+    if (threadIdx.x == 0) {
+        // list position of the first knot field h_0 rho^alpha (the knots follow in order)
+        int k = nf;
+        if (lwt)
+            for (int i = nf - 1; i >= 0; i--)
+                if (a.fwd_ch[i] >= CH_KNOT0) k = i;
+        skpos = k;
+    }
+    __syncthreads();
+    const int kpos = skpos;
+    const T mean = (T)a.scal[S_RHO_MEAN];
+    // per-point channel values: vh = rho - mean, vv = psi, vb = rho^beta,
+    // fa/fb = (1 - t) rho^alpha / t rho^alpha for knots j/j+1 (WT: fa = rho^alpha)
+    T vh[E][2], vv[E][2], vb[E][2], fa[E][2], fb[E][2];
+    int jj[E][2];
+#pragma unroll
+    for (int q = 0; q < E; q++) {
+        const int e = threadIdx.x + q * NT;
+#pragma unroll
+        for (int s = 0; s < 2; s++) {
+            vh[q][s] = vv[q][s] = vb[q][s] = fa[q][s] = fb[q][s] = (T)0;
+            jj[q][s] = 0;
+            if (e < n && (s == 0 || has1)) {
+                const T x = a.rho[(row0 + s) * n + e];
+                vh[q][s] = x - mean;
+                vv[q][s] = dsqrt(x > (T)0 ? x : (T)0);
+                if (nl) {
+                    const T xf = x > a.floor_ ? x : a.floor_;
+                    const T ra = dpow(xf, a.alpha);
+                    vb[q][s] = (a.beta == a.alpha) ? ra : dpow(xf, a.beta);
+                    if (lwt) {
+                        T kf = dcbrt((T)kThreePi2 * xf);
+                        kf = kf < sk[0] ? sk[0] : (kf > sk[M - 1] ? sk[M - 1] : kf);
+                        const int j = knot_interval(kf, sk, M);
+                        const T t = (kf - sk[j]) * sdk[j];
+                        jj[q][s] = j;
+                        fa[q][s] = ((T)1 - t) * ra;
+                        fb[q][s] = t * ra;
+                    } else {
+                        fa[q][s] = ra;
+                    }
+                }
+            }
+        }
+    }
+    for (int g0 = 0; g0 < nf; g0 += G) {
+        const int gact = nf - g0 < G ? nf - g0 : G;
+        // form: every slot of the element (knot slots zero), then the two knot values of each point
+#pragma unroll
+        for (int q = 0; q < E; q++) {
+            const int e = threadIdx.x + q * NT;
+            if (e < n) {
+                C *row = buf + e * LD;
+#pragma unroll
+                for (int s = 0; s < G; s++) {
+                    const int ci = g0 + s;
+                    C v = cmake<C>((T)0, (T)0);
+                    if (ci < kpos && ci < nf) {
+                        const int ch = sch[ci];
+                        if (ch == CH_HPP) v = cmake<C>(vh[q][0], vh[q][1]);
+                        else if (ch == CH_VW) v = cmake<C>(vv[q][0], vv[q][1]);
+                        else if (ch == CH_NL) v = cmake<C>(vb[q][0], vb[q][1]);
+                        else v = cmake<C>(fa[q][0], fa[q][1]);          // WT: rho^alpha
+                    }
+                    row[s] = v;
+                }
+                if (kpos < nf) {
+#pragma unroll
+                    for (int s = 0; s < 2; s++) {
+                        const int ca = kpos + jj[q][s] - g0;
+                        if (ca >= 0 && ca < gact) ((T *)(row + ca))[s] = fa[q][s];
+                        if (ca + 1 >= 0 && ca + 1 < gact) ((T *)(row + ca + 1))[s] = fb[q][s];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        const C *Z = Q::template fft<-1>(buf, scr, tw);
+        // unpack X_2p[k] = (Z_k + conj Z_{n-k})/2, X_2p+1[k] = (Z_k - conj Z_{n-k})/(2i)
+        for (int idx = threadIdx.x; idx < gact * n2h; idx += NT) {
+            const int s = idx / n2h, k = idx - s * n2h;
+            const C A = Z[k * LD + s];
+            const C Bv = Z[((n - k) % n) * LD + s];
+            C *out = a.chan + (size_t)sch[g0 + s] * a.NH + row0 * n2h + k;
+            out[0] = cmake<C>((T)0.5 * (A.x + Bv.x), (T)0.5 * (A.y - Bv.y));
+            if (has1) out[n2h] = cmake<C>((T)0.5 * (A.y + Bv.y), (T)0.5 * (Bv.x - A.x));
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T, class Q>
+__device__ __forceinline__ void row_inv2_body(const EvalArgs<T> &a) {
+    typedef typename Vec2<T>::type C;
+    constexpr int n = Q::N_, G = Q::G_, LD = Q::LD, NT = Q::NT_, E = Q::E, n2h = n / 2 + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tw = (C *)smem_raw;
+    C *buf = tw + n;                 // the packed channel batch
+    C *scr = buf + n * LD;           // scratch of the out-of-place transform
+    __shared__ double sd[32];
+    __shared__ T sk[OFDFT_MAX_KNOTS], sdk[OFDFT_MAX_KNOTS];
+    __shared__ int sch[kMaxChan], skind[kMaxChan], skpos;
+    const long long R = (long long)a.n0 * a.n1;
+    const long long row0 = 2LL * blockIdx.x;
+    const bool has1 = row0 + 1 < R;
+    const bool nl = a.terms & 4u, lwt = nl && a.kernel == 0, interp = a.nlpot == 1;
+    const int M = a.M, ni = a.ninv;
+    for (int i = threadIdx.x; i < n; i += NT) tw[i] = a.tw2[i];
+    if (lwt)
+        for (int i = threadIdx.x; i < M; i += NT) {
+            sk[i] = a.knots_t[i];
+            sdk[i] = (i + 1 < M) ? a.invdk_t[i] : (T)0;
+        }
+    for (int i = threadIdx.x; i < ni; i += NT) {
+        sch[i] = a.inv_ch[i];
+        skind[i] = a.inv_kind[i];
+    }
+    if (threadIdx.x == 0) {
+        // list position of the first knot field y_0 (the knots follow in order)
+        int k = ni;
+        for (int i = ni - 1; i >= 0; i--)
+            if (a.inv_kind[i] == CONS_KNOT) k = i;
+        skpos = k;
+    }
+    __syncthreads();
+    const int kpos = skpos;
+    const T psi_floor = dsqrt(a.floor_);
+    const T alpha_eff = interp ? (T)2 * a.alpha : a.alpha;
+    // per point: V accumulator (starts at V_TF), factors of the semilocal channels,
+    // and the knot interval with the weights of its two knots in V (wa, wb) and,
+    // interpolated mode, in the real-space E_NL (ea, eb)
+    T acc[E][2], fvw[E][2], fa1[E][2], fb1[E][2], wa[E][2], wb[E][2], ea[E][2], eb[E][2];
+    int jj[E][2];
+#pragma unroll
+    for (int q = 0; q < E; q++) {
+        const int e = threadIdx.x + q * NT;
+#pragma unroll
+        for (int s = 0; s < 2; s++) {
+            acc[q][s] = fvw[q][s] = fa1[q][s] = fb1[q][s] = wa[q][s] = wb[q][s] = ea[q][s] = eb[q][s] = (T)0;
+            jj[q][s] = 0;
+            if (e < n) {
+                const bool valid = s == 0 || has1;
+                const T x = valid ? a.rho[(row0 + s) * n + e] : (T)0;
+                const T xp = x > (T)0 ? x : (T)0;
+                if (a.terms & 1u) {
+                    const T c = dcbrt(xp);
+                    acc[q][s] = (T)(5.0 / 3.0 * kCTF) * c * c;        // V_TF = (5/3) C_TF rho^(2/3)
+                }
+                const T p = dsqrt(xp);
+                fvw[q][s] = (T)1 / ((T)2 * (p > psi_floor ? p : psi_floor));
+                if (nl) {
+                    const T xf = x > a.floor_ ? x : a.floor_;
+                    const T ra = dpow(xf, a.alpha);
+                    const T rb = (a.beta == a.alpha) ? ra : dpow(xf, a.beta);
+                    const T sa1 = ra / xf;
+                    fa1[q][s] = a.alpha * sa1;
+                    fb1[q][s] = a.beta * (rb / xf);
+                    if (lwt) {
+                        const T kf = dcbrt((T)kThreePi2 * xf);
+                        const bool inside = kf >= sk[0] && kf <= sk[M - 1];
+                        const T kc = kf < sk[0] ? sk[0] : (kf > sk[M - 1] ? sk[M - 1] : kf);
+                        const int j = knot_interval(kc, sk, M);
+                        const T t = (kc - sk[j]) * sdk[j], idk = sdk[j];
+                        jj[q][s] = j;
+                        if (interp) {
+                            wa[q][s] = alpha_eff * sa1 * ((T)1 - t);
+                            wb[q][s] = alpha_eff * sa1 * t;
+                            if (valid) {
+                                ea[q][s] = ra * ((T)1 - t);
+                                eb[q][s] = ra * t;
+                            }
+                        } else {
+                            const T k3 = inside ? kf * (T)(1.0 / 3.0) : (T)0;
+                            wa[q][s] = sa1 * (alpha_eff * ((T)1 - t) - k3 * idk);
+                            wb[q][s] = sa1 * (alpha_eff * t + k3 * idk);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    T fNL = 0;
+    for (int g0 = 0; g0 < ni; g0 += G) {
+        const int gact = ni - g0 < G ? ni - g0 : G;
+        // pack each pair of half-spectrum rows into one full complex spectrum
+        for (int idx = threadIdx.x; idx < gact * n2h; idx += NT) {
+            const int s = idx / n2h, k = idx - s * n2h;
+            const C *in = a.chan + (size_t)sch[g0 + s] * a.NH + row0 * n2h + k;
+            const C X0 = in[0];
+            const C X1 = has1 ? in[n2h] : cmake<C>((T)0, (T)0);
+            if (k == 0 || 2 * k == n) {
+                buf[k * LD + s] = cmake<C>(X0.x, X1.x);
+            } else {
+                buf[k * LD + s] = cmake<C>(X0.x - X1.y, X0.y + X1.x);
+                buf[(n - k) * LD + s] = cmake<C>(X0.x + X1.y, X1.x - X0.y);
+            }
+        }
+        __syncthreads();
+        const C *Z = Q::template fft<+1>(buf, scr, tw);
+#pragma unroll
+        for (int q = 0; q < E; q++) {
+            const int e = threadIdx.x + q * NT;
+            if (e < n) {
+                const C *row = Z + e * LD;
+                const int pend = kpos < g0 + gact ? kpos : g0 + gact;
+                for (int ci = g0; ci < pend; ci++) {
+                    const C z = row[ci - g0];
+                    const int kind = skind[ci];
+#pragma unroll
+                    for (int s = 0; s < 2; s++) {
+                        const T y = s ? z.y : z.x;
+                        if (kind == CONS_ADD) acc[q][s] += y;
+                        else if (kind == CONS_VW) acc[q][s] += y * fvw[q][s];
+                        else if (kind == CONS_T2 || kind == CONS_WT_B) acc[q][s] += fb1[q][s] * y;
+                        else if (kind == CONS_WT_A) acc[q][s] += fa1[q][s] * y;
+                    }
+                }
+                if (kpos < ni) {
+#pragma unroll
+                    for (int s = 0; s < 2; s++) {
+                        const int ca = kpos + jj[q][s] - g0;
+                        if (ca >= 0 && ca < gact) {
+                            const T y = ((const T *)(row + ca))[s];
+                            acc[q][s] += y * wa[q][s];
+                            fNL += ea[q][s] * y;
+                        }
+                        if (ca + 1 >= 0 && ca + 1 < gact) {
+                            const T y = ((const T *)(row + ca + 1))[s];
+                            acc[q][s] += y * wb[q][s];
+                            fNL += eb[q][s] * y;
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (a.V) {
+#pragma unroll
+        for (int q = 0; q < E; q++) {
+            const int e = threadIdx.x + q * NT;
+            if (e < n) {
+                a.V[row0 * n + e] = acc[q][0];
+                if (has1) a.V[(row0 + 1) * n + e] = acc[q][1];
+            }
+        }
+    }
+    if (lwt && interp) {                     // the only mode with a real-space E_NL
+        const double eNL = block_sum((double)fNL, sd);
+        if (threadIdx.x == 0) a.part_row[blockIdx.x] = eNL;
+    }
+}
+
 // ======================================================================= finalize
 template <typename T>
-__global__ void __launch_bounds__(256) finalize_kernel(EvalArgs<T> a) {
+__global__ void __launch_bounds__(1024) finalize_kernel(EvalArgs<T> a) {
     __shared__ double sd[32];
     double h = 0.0, v = 0.0, p = 0.0, ng = 0.0, nl = 0.0;
     for (int b = threadIdx.x; b < a.nb_ax0; b += blockDim.x) {
@@ -768,7 +1073,10 @@ __global__ void __launch_bounds__(256) finalize_kernel(EvalArgs<T> a) {
         p += a.part_ax0[4 * b + 2];
         ng += a.part_ax0[4 * b + 3];
     }
-    for (int b = threadIdx.x; b < a.nb_row; b += blockDim.x) nl += a.part_row[b];
+    // the row partials hold the real-space E_NL of the interpolated LWT mode only
+    const bool real_space = a.kernel == 0 && a.nlpot == 1;
+    if ((a.terms & 4u) && real_space)
+        for (int b = threadIdx.x; b < a.nb_row; b += blockDim.x) nl += a.part_row[b];
     h = block_sum(h, sd);
     v = block_sum(v, sd);
     p = block_sum(p, sd);
@@ -785,7 +1093,6 @@ __global__ void __launch_bounds__(256) finalize_kernel(EvalArgs<T> a) {
         E[E_PP] = 0.0;
     }
     // nonlocal: G-space sum (exact LWT, WT) or real-space sum (interpolated LWT)
-    const bool real_space = a.kernel == 0 && a.nlpot == 1;
     E[E_NL] = (a.terms & 4u) ? (real_space ? nl * a.dV : a.omega * ng) : 0.0;
     E[E_TOT] = E[E_TF] + E[E_VW] + E[E_NL] + E[E_H] + E[E_PP];
 }
@@ -806,6 +1113,14 @@ __global__ void __launch_bounds__(P::max_threads, P::min_blocks_ax0) axis0_kerne
 template <typename T, class P>
 __global__ void __launch_bounds__(P::max_threads, P::min_blocks) row_inv_kernel(EvalArgs<T> a) {
     row_inv_body<T, P>(a);
+}
+template <typename T, class Q>
+__global__ void __launch_bounds__(Q::NT_, Q::min_blocks) row_fwd2_kernel(EvalArgs<T> a) {
+    row_fwd2_body<T, Q>(a);
+}
+template <typename T, class Q>
+__global__ void __launch_bounds__(Q::NT_, Q::min_blocks) row_inv2_kernel(EvalArgs<T> a) {
+    row_inv2_body<T, Q>(a);
 }
 
 }  // namespace ofdft
