@@ -64,6 +64,15 @@ template <int DIR, typename C> __device__ __forceinline__ C cmul_si(C a) {
 }
 
 // --------------------------------------------------------------- math wrappers
+// four consecutive values from a 16-byte (float) / 32-byte (double) aligned address
+__device__ __forceinline__ void load4(const float *p, float v[4]) {
+    const float4 q = *reinterpret_cast<const float4 *>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void load4(const double *p, double v[4]) {
+    const double2 q0 = reinterpret_cast<const double2 *>(p)[0], q1 = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+}
 __device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float dcbrt(float x) { return cbrtf(x); }

@@ -56,8 +56,16 @@ struct CtPolicy {
 //   eta > 2  :  F = sum_m a_m x^m,       num = -sum_{m>=1} (a_m + 3 a_{m+1}) x^m
 // and G_NL = num / F.  The loops are unrolled, so every coefficient folds to
 // a constant.
-template <typename T> struct GnlTerms { static constexpr int value = 12; };
+template <typename T> struct GnlTerms { static constexpr int value = 10; };
 template <> struct GnlTerms<double> { static constexpr int value = 28; };
+
+// Divisions and the logarithm of the kernel: in the FP32-mixed path the fast
+// intrinsics (at most 2 ulp for these operand ranges, against the few ulp the
+// FP32 sums already carry); FP64 keeps IEEE division and log.
+__device__ __forceinline__ float gdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double gdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float glog(float x) { return __logf(x); }
+__device__ __forceinline__ double glog(double x) { return log(x); }
 
 template <typename T> __device__ __forceinline__ T gnl(T eta) {
     constexpr int nt = GnlTerms<T>::value;
@@ -71,9 +79,9 @@ template <typename T> __device__ __forceinline__ T gnl(T eta) {
             sF = (sF + (T)am) * y;
             sN = (sN + (T)lo) * y;
         }
-        return sN / ((T)1 - sF);
+        return gdiv(sN, (T)1 - sF);
     } else if (eta > (T)2) {
-        const T x = (T)1 / (eta * eta);
+        const T x = gdiv((T)1, eta * eta);
         T sF = 0, sN = 0;
 #pragma unroll
         for (int m = nt; m >= 1; m--) {
@@ -82,12 +90,12 @@ template <typename T> __device__ __forceinline__ T gnl(T eta) {
             sF = (sF + (T)am) * x;
             sN = (sN + (T)hi) * x;
         }
-        return -sN / sF;
+        return -gdiv(sN, sF);
     }
     const T d = (T)1 - eta;
     if (dabs(d) < (T)1e-12) return (T)-2;
-    const T F = (T)0.5 + ((T)1 - eta * eta) / ((T)4 * eta) * dlog(dabs(((T)1 + eta) / d));
-    return (T)1 / F - (T)3 * eta * eta - (T)1;
+    const T F = (T)0.5 + gdiv((T)1 - eta * eta, (T)4 * eta) * glog(dabs(gdiv((T)1 + eta, d)));
+    return gdiv((T)1, F) - (T)3 * eta * eta - (T)1;
 }
 
 // ======================================================================= helpers
@@ -171,25 +179,42 @@ __global__ void __launch_bounds__(256) stats_kernel(EvalArgs<T> a) {
     double s_rho = 0.0, s_tf = 0.0;
     T mn = (T)3.0e38, mx = (T)-3.0e38;
     int bad = 0;
-    // groups of 4 consecutive points: summed in T, then added in FP64 (keeps the FP64 pipe idle)
-    const long long ng = a.N / 4, stride = (long long)gridDim.x * blockDim.x;
-    for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < ng + (a.N % 4 ? 1 : 0); gi += stride) {
-        T r4 = 0, t4 = 0;
+    // groups of 4 consecutive points: summed in T, then added in FP64 (keeps the FP64 pipe
+    // idle); U groups a grid stride apart per iteration, all loaded before any is used
+    constexpr int U = 4;
+    const long long ng = (a.N + 3) / 4, stride = (long long)gridDim.x * blockDim.x;
+    const bool vec = (reinterpret_cast<uintptr_t>(a.rho) % (4 * sizeof(T)) == 0) && (a.N % 4 == 0);
+    for (long long g0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; g0 < ng; g0 += U * stride) {
+        T x[U][4];
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const long long i = 4 * gi + q;
-            if (i < a.N) {
-                const T x = a.rho[i];
-                if (!(x >= (T)0) || !(x < (T)3.0e38)) bad = 1;      // NaN, Inf or negative
-                const T c = dcbrt(x);
-                r4 += x;
-                t4 += x * c * c;                                      // rho^(5/3)
-                mn = x < mn ? x : mn;
-                mx = x > mx ? x : mx;
+        for (int u = 0; u < U; u++) {
+            const long long gi = g0 + u * stride;
+            if (vec && gi < ng) {
+                load4(a.rho + 4 * gi, x[u]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; q++) x[u][q] = (4 * gi + q < a.N) ? a.rho[4 * gi + q] : (T)0;
             }
         }
-        s_rho += (double)r4;
-        s_tf += (double)t4;
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const long long gi = g0 + u * stride;
+            T r4 = 0, t4 = 0;
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                if (4 * gi + q < a.N) {
+                    const T xv = x[u][q];
+                    if (!(xv >= (T)0) || !(xv < (T)3.0e38)) bad = 1;      // NaN, Inf or negative
+                    const T c = dcbrt(xv);
+                    r4 += xv;
+                    t4 += xv * c * c;                                      // rho^(5/3)
+                    mn = xv < mn ? xv : mn;
+                    mx = xv > mx ? xv : mx;
+                }
+            }
+            s_rho += (double)r4;
+            s_tf += (double)t4;
+        }
     }
     s_rho = block_sum(s_rho, sd);
     if (threadIdx.x == 0) a.part_stats[2 * blockIdx.x] = s_rho;
