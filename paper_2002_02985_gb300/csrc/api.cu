@@ -75,6 +75,7 @@ template <typename T> struct Workspace {
     int Brow = 0, thr_rowf = 0, thr_rowi = 0, TW1 = 0, thr_p1 = 0, TW0 = 0, thr_ax0 = 0, nb_row = 0, nb_ax0 = 0;
     int grid_p1 = 0;
     int row2_G = 0;                   // channel-batched row kernels in use: channels per group
+    int ax0_scr = 0;                  // the reciprocal-space kernel transforms out of place
 };
 
 }  // namespace
@@ -207,9 +208,11 @@ template <typename T> int choose_launch(ofdft_grid *g, Workspace<T> &w) {
         w.ks.axis0 = k1;
         w.TW0 = Bv;
         w.thr_ax0 = ntv;
+        w.ax0_scr = axis0_oop<T>(g->n[0]) ? 1 : 0;
     } else {
         int TW = 16;
-        while (TW > 1 && (axis0_smem_bytes<T>(g->n[0], TW) > 200 * 1024 || threads_for(g->plan[0], TW, cap) > tmax))
+        w.ax0_scr = 0;
+        while (TW > 1 && (axis0_smem_bytes<T>(g->n[0], TW, false) > 200 * 1024 || threads_for(g->plan[0], TW, cap) > tmax))
             TW /= 2;
         w.TW0 = TW;
         w.thr_ax0 = std::min(std::max(threads_for(g->plan[0], TW, cap), 128), tmax);
@@ -461,6 +464,7 @@ int enqueue_eval(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, d
     a.thr_ax0 = w.thr_ax0;
     a.grid_p1 = w.grid_p1;
     a.row2_G = w.row2_G;
+    a.ax0_scr = w.ax0_scr;
     // channel lists
     const bool hpp = f->terms & (OFDFT_TERM_HARTREE | OFDFT_TERM_PP);
     const bool vw = f->terms & OFDFT_TERM_VW;
@@ -538,7 +542,7 @@ template <typename T> EvalArgs<T> plain_args(ofdft_grid *g, Workspace<T> &w, con
     a.tw0 = w.tw[0]; a.tw1 = w.tw[1]; a.tw2 = w.tw[2];
     a.Brow = w.Brow; a.thr_rowf = w.thr_rowf; a.thr_rowi = w.thr_rowi;
     a.TW1 = w.TW1; a.thr_p1 = w.thr_p1; a.TW0 = w.TW0; a.thr_ax0 = w.thr_ax0; a.grid_p1 = w.grid_p1;
-    a.row2_G = w.row2_G;
+    a.row2_G = w.row2_G; a.ax0_scr = w.ax0_scr;
     a.nfwd = 1; a.fwd_ch[0] = CH_HPP; a.ncol = 1; a.col_ch[0] = CH_HPP;
     return a;
 }

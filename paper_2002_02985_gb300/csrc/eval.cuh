@@ -70,6 +70,7 @@ template <typename T> struct EvalArgs {
     int Brow, thr_rowf, thr_rowi, TW1, thr_p1, TW0, thr_ax0;
     int grid_p1;                         // persistent grid of the n1 pencil kernels
     int row2_G;                          // channel-batched row kernels: channels per group (0: per-channel form)
+    int ax0_scr;                         // the reciprocal-space kernel has a scratch tile (out-of-place transforms)
     int nfwd, fwd_ch[kMaxChan];          // channels formed by row_fwd (slot ids)
     int ncol, col_ch[kMaxChan];          // channels transformed forward along n1
     int ncol_inv, col_inv_ch[kMaxChan];  // channels transformed back along n1
@@ -101,12 +102,19 @@ template <typename T> __host__ __device__ inline size_t row_fwd_smem_bytes(int n
 }
 template <typename T> __host__ __device__ inline size_t pencil_smem_bytes(int n, int TW) {
     typedef typename Vec2<T>::type C;
-    return (size_t)n * sizeof(C) + 2 * (size_t)n * TW * sizeof(C);     // twiddles + two tile buffers
+    // twiddles + two tile buffers (prefetch ping-pong) + the transform's scratch
+    return (size_t)n * sizeof(C) + 3 * (size_t)n * TW * sizeof(C);
 }
 
-template <typename T> __host__ __device__ inline size_t axis0_smem_bytes(int n, int TW) {
+// Whether the size-specialised reciprocal-space kernel for n0 = n transforms out of place
+// (in place measured faster for the FP32 128-point tiles).
+template <typename T> __host__ __device__ constexpr bool axis0_oop(int n) { return !(sizeof(T) == 4 && n == 128); }
+
+template <typename T> __host__ __device__ inline size_t axis0_smem_bytes(int n, int TW, bool scratch) {
     typedef typename Vec2<T>::type C;
-    return (size_t)n * sizeof(C) + 4 * (size_t)n * TW * sizeof(C) + (size_t)n * TW * sizeof(T) + 16;
+    // twiddles, two load buffers, rho^beta, the term-2 accumulator, the out-of-place
+    // transforms' scratch (if any), |G|
+    return (size_t)n * sizeof(C) + (scratch ? 5 : 4) * (size_t)n * TW * sizeof(C) + (size_t)n * TW * sizeof(T) + 16;
 }
 
 template <typename T> __host__ __device__ inline size_t row_inv_smem_bytes(int n2, int B) {

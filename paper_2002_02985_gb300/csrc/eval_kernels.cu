@@ -70,7 +70,7 @@ cudaError_t launch_eval(const EvalArgs<T> &a, const LaunchSet &ks, cudaStream_t 
         mark(K_PENCIL_FWD, 1);
     }
     mark(K_AXIS0, 0);
-    e = launch(ks.axis0, dim3(a.nb_ax0), a.thr_ax0, axis0_smem_bytes<T>(a.n0, a.TW0), a, s);
+    e = launch(ks.axis0, dim3(a.nb_ax0), a.thr_ax0, axis0_smem_bytes<T>(a.n0, a.TW0, a.ax0_scr), a, s);
     if (e) return e;
     mark(K_AXIS0, 1);
     if (a.ncol_inv > 0) {

@@ -18,7 +18,7 @@
     if (n == N && role != ROLE_ROW2) {                                                        \
         typedef ::ofdft::CtPolicy<T, N, RB, RB + 1, RNT, RMAXR, RMINB> PR;                    \
         typedef ::ofdft::CtPolicy<T, N, PTW, PTW, PNT> PP;                                    \
-        typedef ::ofdft::CtPolicy<T, N, ATW, ATW, ANT, AMAXR, AMINB> PA;                      \
+        typedef ::ofdft::CtPolicy<T, N, ATW, ATW, ANT, AMAXR, AMINB, ::ofdft::axis0_oop<T>(N)> PA; \
         if (role == ROLE_ROW) {                                                               \
             *k1 = (const void *)row_fwd_kernel<T, PR>;                                        \
             *k2 = (const void *)row_inv_kernel<T, PR>;                                        \
@@ -50,3 +50,16 @@
         *nt = NT;                                                                             \
         return true;                                                                          \
     }
+
+// OFDFT_SPECIALISE_PENCIL(T, N, TW, NT, MINB): only the n1 pencil kernels for n1 = N, with at
+// least MINB resident blocks per SM (tuning variants).
+#define OFDFT_SPECIALISE_PENCIL(T, N, TW, NT, MINB)                                           \
+    if (role == ROLE_PENCIL && n == N) {                                                      \
+        typedef ::ofdft::CtPolicy<T, N, TW, TW, NT, (sizeof(T) == 4 ? 16 : 8), MINB> PP;      \
+        *k1 = (const void *)pencil1_kernel<T, -1, PP>;                                        \
+        *k2 = (const void *)pencil1_kernel<T, +1, PP>;                                        \
+        *B = TW;                                                                              \
+        *nt = NT;                                                                             \
+        return true;                                                                          \
+    }
+

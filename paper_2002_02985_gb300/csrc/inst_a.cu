@@ -19,6 +19,9 @@ static bool variant_128(int v, int role, int n, const void **k1, const void **k2
         case 6: OFDFT_SPECIALISE_X(float, 128, 8, 256, 16, 256, 8, 64, 16, 16, 0, 0) break;
         case 7: OFDFT_SPECIALISE_X(float, 128, 8, 256, 16, 256, 16, 128, 16, 16, 0, 2) break;
         case 8: OFDFT_SPECIALISE_X(float, 128, 8, 256, 16, 256, 8, 128, 16, 8, 0, 0) break;
+        case 9: OFDFT_SPECIALISE_PENCIL(float, 128, 16, 256, 4) break;
+        case 10: OFDFT_SPECIALISE_PENCIL(float, 128, 16, 128, 8) break;
+        case 11: OFDFT_SPECIALISE_PENCIL(float, 128, 8, 128, 8) break;
         default: break;
     }
     return false;

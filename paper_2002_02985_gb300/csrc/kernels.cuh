@@ -14,7 +14,7 @@ namespace ofdft {
 // ======================================================================= policies
 template <typename T, int AX> struct RtPolicy {
     typedef typename Vec2<T>::type C;
-    static constexpr bool ct = false;
+    static constexpr bool ct = false, oop = false;
     static constexpr int N_ = 0, B_ = 0, NT_ = 0;
     static constexpr int max_threads = kMaxThreads, min_blocks = 1, min_blocks_ax0 = 1;
     __device__ static int n(const EvalArgs<T> &a) { return AX == 0 ? a.n0 : (AX == 1 ? a.n1 : a.n2); }
@@ -24,12 +24,18 @@ template <typename T, int AX> struct RtPolicy {
     template <int DIR> __device__ static void fft(C *buf, const EvalArgs<T> &a, const C *tw) {
         fft_smem<DIR, Cap<T>::value>(buf, ld(a), B(a), AX == 0 ? a.p0 : (AX == 1 ? a.p1 : a.p2), tw);
     }
+    // transform of x with y as scratch; returns the buffer holding the result (here x)
+    template <int DIR> __device__ static C *fft2(C *x, C *, const EvalArgs<T> &a, const C *tw) {
+        fft<DIR>(x, a, tw);
+        return x;
+    }
 };
 
-template <typename T, int N, int B__, int LD_, int NT__, int MAXR = (sizeof(T) == 4 ? 16 : 8), int MINB = 0>
+template <typename T, int N, int B__, int LD_, int NT__, int MAXR = (sizeof(T) == 4 ? 16 : 8), int MINB = 0,
+          bool OOP = true>
 struct CtPolicy {
     typedef typename Vec2<T>::type C;
-    static constexpr bool ct = true;
+    static constexpr bool ct = true, oop = OOP;
     static constexpr int N_ = N, B_ = B__, NT_ = NT__;
     // register budget: at least 768 resident threads per SM (24 warps)
     static constexpr int max_threads = NT__;
@@ -42,6 +48,16 @@ struct CtPolicy {
     __device__ static constexpr int nt() { return NT__; }
     template <int DIR> __device__ static void fft(C *buf, const EvalArgs<T> &, const C *tw) {
         ct::fft<DIR, N, B__, LD_, NT__, MAXR>(buf, tw);
+    }
+    // x transformed with y as scratch (out of place unless OOP is false); returns the
+    // buffer holding the result
+    template <int DIR> __device__ static C *fft2(C *x, C *y, const EvalArgs<T> &, const C *tw) {
+        if constexpr (OOP) {
+            return ct::fft_oop<DIR, N, B__, LD_, NT__, MAXR>(x, y, tw);
+        } else {
+            ct::fft<DIR, N, B__, LD_, NT__, MAXR>(x, tw);
+            return x;
+        }
     }
 };
 
@@ -347,7 +363,8 @@ __device__ __forceinline__ void pencil1_body(const EvalArgs<T> &a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = P::n(a), TW = P::B(a), n2h = a.n2h, NT = P::nt();
     C *tw = (C *)smem_raw;
-    C *buf[2] = {tw + n, tw + n + n * TW};
+    C *const b0 = tw + n, *const b1 = tw + n + n * TW;   // prefetch ping-pong (no indexed array:
+    C *scr = tw + n + 2 * n * TW;                        // it would live in local memory); scratch
     for (int i = threadIdx.x; i < n; i += NT) tw[i] = a.tw1[i];
     const long long ncols = (long long)a.n0 * n2h;
     const int ntile = (int)((ncols + TW - 1) / TW);
@@ -374,20 +391,20 @@ __device__ __forceinline__ void pencil1_body(const EvalArgs<T> &a) {
         cp_async_commit();
     };
     int it = 0;
-    if ((int)blockIdx.x < total) prefetch(blockIdx.x, buf[0]);
+    if ((int)blockIdx.x < total) prefetch(blockIdx.x, b0);
     for (int t = blockIdx.x; t < total; t += gridDim.x, it++) {
-        C *cur = buf[it & 1];
+        C *cur = (it & 1) ? b1 : b0;
         cp_async_wait<0>();
         __syncthreads();
-        if (t + (int)gridDim.x < total) prefetch(t + gridDim.x, buf[(it + 1) & 1]);
-        P::template fft<DIR>(cur, a, tw);
+        if (t + (int)gridDim.x < total) prefetch(t + gridDim.x, (it & 1) ? b0 : b1);
+        const C *res = P::template fft2<DIR>(cur, scr, a, tw);
         long long c0;
         C *base = tile_base(t, c0);
         for (int idx = threadIdx.x; idx < n * TW; idx += NT) {
             const int w = idx % TW, i = idx / TW;
             const long long c = c0 + w;
             const long long k0 = c / n2h, k2 = c - k0 * n2h;
-            if (c < ncols) base[k0 * plane + (long long)i * n2h + k2] = cur[idx];
+            if (c < ncols) base[k0 * plane + (long long)i * n2h + k2] = res[idx];
         }
     }
     cp_async_wait<0>();
@@ -413,10 +430,11 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
     const long long PL = (long long)a.n1 * n2h;      // columns per plane
     const int NTILE = n * TW;
     C *tw = (C *)smem_raw;
-    C *X[2] = {tw + n, tw + n + NTILE};              // rotating load buffers
-    C *Rr = X[1] + NTILE;
+    C *xa = tw + n, *xb = tw + n + NTILE;            // rotating load buffers (slots 0, 1)
+    C *Rr = xb + NTILE;
     C *A = Rr + NTILE;
-    T *gn = (T *)(A + NTILE);
+    C *scr = A + NTILE;                              // scratch of the out-of-place transforms
+    T *gn = (T *)(scr + (P::oop ? NTILE : 0));
     const bool lwt = a.kernel == 0;
     const bool exact = a.nlpot == 0;
     // the channels this block reads, in processing order
@@ -465,15 +483,32 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
         for (int i = threadIdx.x; i < a.M; i += NT) sk[i] = a.knots_t[i];
     __syncthreads();
     int stage = 0;
-    if (nord > 0) prefetch(X[0], order[0]);
-    // next(): wait for the current stage's tile, start the following one
-    auto next = [&]() -> C * {
+    if (nord > 0) prefetch(xa, order[0]);
+    // next(): wait for the current stage's tile, start the following one; returns its slot
+    auto next = [&]() -> int {
         cp_async_wait<0>();
         __syncthreads();
-        C *cur = X[stage & 1];
-        if (stage + 1 < nord) prefetch(X[(stage + 1) & 1], order[stage + 1]);
+        const int cur = stage & 1;
+        if (stage + 1 < nord) prefetch(((stage + 1) & 1) ? xb : xa, order[stage + 1]);
         stage++;
         return cur;
+    };
+    // transforms of the tile in buffer x, returning the buffer that holds the result; when
+    // that is the scratch buffer, x becomes the scratch (callers re-point the tile's slot)
+    auto fwd = [&](C *x) -> C * {
+        C *r = P::template fft2<-1>(x, scr, a, tw);
+        if (r != x) scr = x;
+        return r;
+    };
+    auto inv = [&](C *x) -> C * {
+        C *r = P::template fft2<+1>(x, scr, a, tw);
+        if (r != x) scr = x;
+        return r;
+    };
+    auto slot = [&](int sl) -> C * { return sl ? xb : xa; };
+    auto set_slot = [&](int sl, C *p) {
+        if (sl) xb = p;
+        else xa = p;
     };
     const T b0x = (T)a.bvec[0], b0y = (T)a.bvec[1], b0z = (T)a.bvec[2];
     for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
@@ -489,8 +524,9 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
 
     // ---- Hartree + local pseudopotential
     if (a.terms & (8u | 16u)) {
-        C *S = next();
-        P::template fft<-1>(S, a, tw);
+        const int sl = next();
+        C *S = fwd(slot(sl));
+        set_slot(sl, S);
         T fH = 0, fP = 0;          // per-thread partials in T, folded into FP64 once
         for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
             const int w = idx % TW, i = idx / TW;
@@ -519,13 +555,15 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
         eH += (double)fH;
         eP += (double)fP;
         __syncthreads();
-        P::template fft<+1>(S, a, tw);
+        S = inv(S);
+        set_slot(sl, S);
         store(S, CH_HPP);
     }
     // ---- von Weizsaecker (psi form)
     if (a.terms & 2u) {
-        C *S = next();
-        P::template fft<-1>(S, a, tw);
+        const int sl = next();
+        C *S = fwd(slot(sl));
+        set_slot(sl, S);
         T fV = 0;
         for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
             const int w = idx % TW;
@@ -537,22 +575,25 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
         }
         eV += (double)fV;
         __syncthreads();
-        P::template fft<+1>(S, a, tw);
+        S = inv(S);
+        set_slot(sl, S);
         store(S, CH_VW);
     }
     // ---- nonlocal: s2 (kernel at each knot) and the reciprocal half of s3
     if (a.terms & 4u) {
         {
-            C *S = next();
-            P::template fft<-1>(S, a, tw);
+            const int sl = next();
+            C *S = fwd(slot(sl));
+            set_slot(sl, S);
             for (int idx = threadIdx.x; idx < NTILE; idx += NT) Rr[idx] = cscale(S[idx], invN);
         }
         if (!lwt) {
             // global-kF Wang-Teter: K * rho^beta into CH_NL, K * rho^alpha into CH_KNOT0;
             // E = Omega sum_G w Re(conj(FFT[rho^alpha]) K FFT[rho^beta])
             const T hk = (T)(0.5 / a.scal[S_KF_WT]);
-            C *S = next();
-            P::template fft<-1>(S, a, tw);
+            const int sl = next();
+            C *S = fwd(slot(sl));
+            set_slot(sl, S);
             T fN = 0;
             for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
                 const int w = idx % TW;
@@ -565,8 +606,9 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
             }
             eN += (double)fN;
             __syncthreads();
-            P::template fft<+1>(Rr, a, tw);
-            P::template fft<+1>(S, a, tw);
+            Rr = inv(Rr);
+            S = inv(S);
+            set_slot(sl, S);
             store(Rr, CH_NL);
             store(S, CH_KNOT0);
         } else {
@@ -574,13 +616,16 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
                 for (int idx = threadIdx.x; idx < NTILE; idx += NT) A[idx] = cmake<C>((T)0, (T)0);
             for (int m = 0; m < a.M; m++) {
                 const T hk = (T)0.5 / sk[m];
+                int sl;
                 C *S;
                 if (exact) {
-                    S = next();
-                    P::template fft<-1>(S, a, tw);
+                    sl = next();
+                    S = fwd(slot(sl));
+                    set_slot(sl, S);
                 } else {
                     __syncthreads();
-                    S = X[m & 1];
+                    sl = m & 1;
+                    S = slot(sl);
                 }
                 T fN = 0;
                 for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
@@ -596,12 +641,13 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
                 }
                 eN += (double)fN;
                 __syncthreads();
-                P::template fft<+1>(S, a, tw);
+                S = inv(S);
+                set_slot(sl, S);
                 store(S, CH_KNOT0 + m);
             }
             if (exact) {
                 __syncthreads();
-                P::template fft<+1>(A, a, tw);
+                A = inv(A);
                 store(A, CH_NL);
             }
         }
