@@ -48,6 +48,7 @@ extern "C" {
 #define OFDFT_ERR_CUDA             -5  /* any other CUDA error (message kept in the handle) */
 #define OFDFT_ERR_NOT_CONVERGED    -6  /* optimiser reached max_iter */
 #define OFDFT_ERR_NO_IONS          -7  /* a call needs ions but ofdft_set_ions was not called */
+#define OFDFT_ERR_TIMEOUT          -8  /* a bounded device-side wait expired (the results are not valid) */
 
 /* ---- functional description ----------------------------------------- */
 #define OFDFT_TERM_TF       1u   /* Thomas-Fermi  C_TF int rho^(5/3)             */

@@ -15,7 +15,7 @@ OFDFT_OK = 0
 OFDFT_ERR_INVALID_ARG = -1
 STATUS = {0: "OFDFT_OK", -1: "OFDFT_ERR_INVALID_ARG", -2: "OFDFT_ERR_UNSUPPORTED_SIZE",
           -3: "OFDFT_ERR_BAD_DENSITY", -4: "OFDFT_ERR_OOM", -5: "OFDFT_ERR_CUDA",
-          -6: "OFDFT_ERR_NOT_CONVERGED", -7: "OFDFT_ERR_NO_IONS"}
+          -6: "OFDFT_ERR_NOT_CONVERGED", -7: "OFDFT_ERR_NO_IONS", -8: "OFDFT_ERR_TIMEOUT"}
 
 TERM_TF, TERM_VW, TERM_NL, TERM_HARTREE, TERM_PP = 1, 2, 4, 8, 16
 TERMS_ALL = 31

@@ -503,7 +503,9 @@ int enqueue_eval(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, d
             }
         }
     }
-    CK(cudaMemsetAsync(w.scal + S_BAD, 0, sizeof(double), g->stream), "memset flag");
+    // clears the bad-density flag, the WT kF (recomputed) and the device-wait timeout flag
+    static_assert(S_TIMEOUT == S_BAD + 2, "flag slots");
+    CK(cudaMemsetAsync(w.scal + S_BAD, 0, 3 * sizeof(double), g->stream), "memset flags");
     if (a.frozen) CK(cudaMemcpyAsync(w.knots_d, f->knots, M * sizeof(double), cudaMemcpyHostToDevice, g->stream),
                      "upload knots");
     ProfHook hook{prof_record, g};
@@ -520,6 +522,7 @@ int eval_sync(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, doub
     CK(cudaMemcpyAsync(g->h_pinned + 8, w.scal, S_NSCAL * sizeof(double), cudaMemcpyDeviceToHost, g->stream),
        "copy scalars");
     CK(cudaStreamSynchronize(g->stream), "stream synchronize");
+    if (g->h_pinned[8 + S_TIMEOUT] != 0.0) return fail(g, OFDFT_ERR_TIMEOUT, "a bounded device wait expired");
     if (g->h_pinned[8 + S_BAD] != 0.0) return fail(g, OFDFT_ERR_BAD_DENSITY, "density has NaN/Inf or negative values");
     if (E_out) std::memcpy(E_out, g->h_pinned, 6 * sizeof(double));
     return OFDFT_OK;
@@ -1034,6 +1037,7 @@ int batched_impl(int n, ofdft_grid *const *grids, const void *const *rho_dev, co
     if (e != cudaSuccess) return fail(g0, OFDFT_ERR_CUDA, "stream synchronize", e);
     for (int i = 0; i < n; i++) {
         ofdft_grid *g = grids[i];
+        if (g->h_pinned[8 + S_TIMEOUT] != 0.0) return fail(g, OFDFT_ERR_TIMEOUT, "a bounded device wait expired");
         if (g->h_pinned[8 + S_BAD] != 0.0) return fail(g, OFDFT_ERR_BAD_DENSITY, "bad density in batch");
         std::memcpy(E_out + 6 * i, g->h_pinned, 6 * sizeof(double));
         if (F_out && F_out[i]) std::memcpy(F_out[i], g->F_pinned, (size_t)3 * g->n_ions * sizeof(double));
@@ -1058,6 +1062,7 @@ const char *ofdft_status_string(int s) {
         case OFDFT_ERR_CUDA: return "CUDA error";
         case OFDFT_ERR_NOT_CONVERGED: return "optimiser did not converge";
         case OFDFT_ERR_NO_IONS: return "no ions set";
+        case OFDFT_ERR_TIMEOUT: return "a bounded device wait expired";
         default: return "unknown status";
     }
 }

@@ -28,7 +28,7 @@ enum { CONS_ADD = 0, CONS_VW = 1, CONS_T2 = 2, CONS_KNOT = 3, CONS_WT_A = 4, CON
 // scalar slots (double) in the workspace
 enum {
     S_SUM_RHO = 0, S_SUM_TF = 1, S_RHO_MIN = 2, S_RHO_MAX = 3, S_RHO_MEAN = 4, S_BAD = 5,
-    S_KF_WT = 6, S_NSCAL = 8
+    S_KF_WT = 6, S_TIMEOUT = 7, S_NSCAL = 8
 };
 // energy slots: total, TF, vW, NL, H, PP
 enum { E_TOT = 0, E_TF = 1, E_VW = 2, E_NL = 3, E_H = 4, E_PP = 5 };
@@ -123,12 +123,14 @@ template <typename T> __host__ __device__ inline size_t row_inv_smem_bytes(int n
     return n2 * sizeof(C) + row_buf_bytes<T>(n2, B) + P * (6 * sizeof(T) + 1) + 16;
 }
 
-// channel-batched row kernels: twiddles + two n2 x LD complex buffers (LD = G, or G + 1 if G
-// is even): the batch and the scratch of the out-of-place transform
+// channel-batched row kernels: twiddles and two buffers, each of max(n2 x LD, G (n2 + 2))
+// complex (LD = G, or G + 1 if G is even): the batch and the transform's scratch, which also
+// stage G pairs of half-spectrum rows
 template <typename T> __host__ __device__ inline size_t row2_smem_bytes(int n2, int G) {
     typedef typename Vec2<T>::type C;
     const int ld = (G % 2) ? G : G + 1;
-    return (size_t)n2 * sizeof(C) + 2 * (size_t)n2 * ld * sizeof(C) + 16;
+    const size_t scr = ((size_t)n2 * ld > (size_t)G * (n2 + 2)) ? (size_t)n2 * ld : (size_t)G * (n2 + 2);
+    return (size_t)n2 * sizeof(C) + 2 * scr * sizeof(C) + 16;
 }
 template <typename T> __host__ __device__ inline size_t rowf_smem(const EvalArgs<T> &a) {
     return a.row2_G ? row2_smem_bytes<T>(a.n2, a.row2_G) : row_fwd_smem_bytes<T>(a.n2, a.Brow);

@@ -851,6 +851,9 @@ template <typename T, int N, int G, int NT, int MAXR, int MINB>
 struct RowPolicy2 {
     typedef typename Vec2<T>::type C;
     static constexpr int N_ = N, G_ = G, NT_ = NT, LD = (G % 2) ? G : G + 1;
+    // each of the two buffers (the batch and the out-of-place transform's scratch) holds
+    // N x LD elements and, when used as staging, G pairs of half-spectrum rows
+    static constexpr int SCR = (N * LD > G * (N + 2)) ? N * LD : G * (N + 2);
     static constexpr int E = (N + NT - 1) / NT;      // elements (pairs of points) per thread
     static constexpr int min_blocks = MINB;
     template <int DIR> __device__ static C *fft(C *x, C *y, const C *tw) {
@@ -865,7 +868,7 @@ __device__ __forceinline__ void row_fwd2_body(const EvalArgs<T> &a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *tw = (C *)smem_raw;
     C *buf = tw + n;                 // the channel batch, formed here
-    C *scr = buf + n * LD;           // scratch of the out-of-place transform
+    C *scr = buf + Q::SCR;           // scratch of the out-of-place transform
     __shared__ T sk[OFDFT_MAX_KNOTS], sdk[OFDFT_MAX_KNOTS];
     __shared__ int sch[kMaxChan], skpos;
     const long long R = (long long)a.n0 * a.n1;
@@ -959,6 +962,7 @@ __device__ __forceinline__ void row_fwd2_body(const EvalArgs<T> &a) {
         __syncthreads();
         const C *Z = Q::template fft<-1>(buf, scr, tw);
         // unpack X_2p[k] = (Z_k + conj Z_{n-k})/2, X_2p+1[k] = (Z_k - conj Z_{n-k})/(2i)
+        // (plain stores: staging for bulk stores measured slower here)
         for (int idx = threadIdx.x; idx < gact * n2h; idx += NT) {
             const int s = idx / n2h, k = idx - s * n2h;
             const C A = Z[k * LD + s];
@@ -978,8 +982,10 @@ __device__ __forceinline__ void row_inv2_body(const EvalArgs<T> &a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *tw = (C *)smem_raw;
     C *buf = tw + n;                 // the packed channel batch
-    C *scr = buf + n * LD;           // scratch of the out-of-place transform
+    C *scr = buf + Q::SCR;           // scratch of the out-of-place transform; stages the raw rows
     __shared__ double sd[32];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ int s_ok;
     __shared__ T sk[OFDFT_MAX_KNOTS], sdk[OFDFT_MAX_KNOTS];
     __shared__ int sch[kMaxChan], skind[kMaxChan], skpos;
     const long long R = (long long)a.n0 * a.n1;
@@ -1004,8 +1010,15 @@ __device__ __forceinline__ void row_inv2_body(const EvalArgs<T> &a) {
             if (a.inv_kind[i] == CONS_KNOT) k = i;
         skpos = k;
     }
+    // bulk (TMA) loads need 16-byte aligned rows: an even channel stride, both rows present
+    const bool bulk = has1 && (a.NH % 2 == 0) && (smem_u32(scr) % 16 == 0);
+    if (bulk && threadIdx.x == 0) {
+        mbar_init(&mbar, 1);
+        fence_proxy_async_smem();
+    }
     __syncthreads();
     const int kpos = skpos;
+    unsigned phase = 0;
     const T psi_floor = dsqrt(a.floor_);
     const T alpha_eff = interp ? (T)2 * a.alpha : a.alpha;
     // per point: V accumulator (starts at V_TF), factors of the semilocal channels,
@@ -1064,12 +1077,46 @@ __device__ __forceinline__ void row_inv2_body(const EvalArgs<T> &a) {
     T fNL = 0;
     for (int g0 = 0; g0 < ni; g0 += G) {
         const int gact = ni - g0 < G ? ni - g0 : G;
+        // the two half-spectrum rows of each channel (contiguous in memory) are copied
+        // asynchronously into the scratch buffer, so that all of a block's loads are in
+        // flight at once: one bulk copy per channel, else element copies (a missing
+        // second row reads as zeros)
+        if (bulk) {
+            if (threadIdx.x == 0) {
+                const unsigned bytes = (unsigned)(2 * n2h * sizeof(C));
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&mbar, bytes * (unsigned)gact);
+                for (int s = 0; s < gact; s++)
+                    bulk_g2s(scr + 2 * s * n2h, a.chan + (size_t)sch[g0 + s] * a.NH + row0 * n2h, bytes, &mbar);
+                s_ok = mbar_wait_bounded(&mbar, phase, 1u << 22) ? 1 : 0;
+            }
+            __syncthreads();
+            if (!s_ok) {
+                // the copies did not arrive in time: flag it, give them one more bounded
+                // wait (they target this block's shared memory) and stop
+                if (threadIdx.x == 0) {
+                    a.scal[S_TIMEOUT] = 1.0;
+                    mbar_wait_bounded(&mbar, phase, 1u << 22);
+                }
+                return;
+            }
+            mbar_wait_bounded(&mbar, phase, 1u << 22);      // completed: makes the data visible here
+            phase ^= 1u;
+        } else {
+            for (int idx = threadIdx.x; idx < gact * 2 * n2h; idx += NT) {
+                const int s = idx / (2 * n2h), j = idx - s * 2 * n2h;
+                const bool ok = j < n2h || has1;
+                cp_async<sizeof(C)>(scr + idx, a.chan + (size_t)sch[g0 + s] * a.NH + (ok ? row0 * n2h + j : 0), ok);
+            }
+            cp_async_commit();
+            cp_async_wait<0>();
+            __syncthreads();
+        }
         // pack each pair of half-spectrum rows into one full complex spectrum
         for (int idx = threadIdx.x; idx < gact * n2h; idx += NT) {
             const int s = idx / n2h, k = idx - s * n2h;
-            const C *in = a.chan + (size_t)sch[g0 + s] * a.NH + row0 * n2h + k;
-            const C X0 = in[0];
-            const C X1 = has1 ? in[n2h] : cmake<C>((T)0, (T)0);
+            const C X0 = scr[2 * s * n2h + k];
+            const C X1 = scr[(2 * s + 1) * n2h + k];
             if (k == 0 || 2 * k == n) {
                 buf[k * LD + s] = cmake<C>(X0.x, X1.x);
             } else {
