@@ -242,10 +242,13 @@ __global__ void __launch_bounds__(256) stats_kernel(EvalArgs<T> a) {
     if (threadIdx.x == 0) a.part_minmax[2 * blockIdx.x + 1] = mx;
     bad = __syncthreads_or(bad);
     if (threadIdx.x == 0 && bad) a.scal[S_BAD] = 1.0;
-    // the last block to finish reduces every block's partials and makes the knots
+    // the last block to finish reduces every block's partials and makes the knots (thread 0
+    // wrote this block's partials and flag, so only it orders them before the ticket)
     __shared__ bool last;
-    __threadfence();
-    if (threadIdx.x == 0) last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
+    }
     __syncthreads();
     if (!last) return;
     __threadfence();
@@ -1075,6 +1078,7 @@ __device__ __forceinline__ void row_inv2_body(const EvalArgs<T> &a) {
         }
     }
     T fNL = 0;
+    bool alive = true;
     for (int g0 = 0; g0 < ni; g0 += G) {
         const int gact = ni - g0 < G ? ni - g0 : G;
         // the two half-spectrum rows of each channel (contiguous in memory) are copied
@@ -1093,12 +1097,13 @@ __device__ __forceinline__ void row_inv2_body(const EvalArgs<T> &a) {
             __syncthreads();
             if (!s_ok) {
                 // the copies did not arrive in time: flag it, give them one more bounded
-                // wait (they target this block's shared memory) and stop
+                // wait (they target this block's shared memory) and stop working
                 if (threadIdx.x == 0) {
                     a.scal[S_TIMEOUT] = 1.0;
                     mbar_wait_bounded(&mbar, phase, 1u << 22);
                 }
-                return;
+                alive = false;
+                break;
             }
             mbar_wait_bounded(&mbar, phase, 1u << 22);      // completed: makes the data visible here
             phase ^= 1u;
@@ -1164,7 +1169,7 @@ __device__ __forceinline__ void row_inv2_body(const EvalArgs<T> &a) {
         }
         __syncthreads();
     }
-    if (a.V) {
+    if (alive && a.V) {
 #pragma unroll
         for (int q = 0; q < E; q++) {
             const int e = threadIdx.x + q * NT;
@@ -1181,6 +1186,8 @@ __device__ __forceinline__ void row_inv2_body(const EvalArgs<T> &a) {
 }
 
 // ======================================================================= finalize
+// FP64 energies from the per-block partials of the reciprocal-space kernel (and, for
+// the interpolated LWT mode, of the row kernel), summed in a fixed order.
 template <typename T>
 __global__ void __launch_bounds__(1024) finalize_kernel(EvalArgs<T> a) {
     __shared__ double sd[32];

@@ -308,12 +308,13 @@ def test_channel_batched_and_per_channel_rows_agree(kw, monkeypatch):
         out.append(g.energy_potential(rho, f))
     (E1, V1), (E2, V2) = out
     # the forward rows do the same arithmetic per sequence in both forms, so every
-    # G-space energy is bit-identical; the spline blend of the inverse rows groups
+    # G-space energy agrees to the FP64 rounding of the final sums (whose tree follows
+    # the inverse row kernel's block size); the spline blend of the inverse rows groups
     # its products differently, so V (and the real-space E_NL of the interpolated
     # mode) differ by FP32 rounding (each side is checked against the oracle elsewhere)
     for k in E1:
         if kw.get("nl_potential") == L.NLPOT_INTERP and k in ("NL", "total"):
             assert abs(E1[k] - E2[k]) / wl["n_atoms"] <= 5e-7, (k, E1[k], E2[k])
         else:
-            assert E1[k] == E2[k], (k, E1[k], E2[k])
+            assert abs(E1[k] - E2[k]) <= 1e-13 * max(1.0, abs(E1[k])), (k, E1[k], E2[k])
     assert float((V1 - V2).norm() / V1.norm()) <= 2.5e-5
