@@ -85,28 +85,32 @@ __device__ __forceinline__ double glog(double x) { return log(x); }
 
 template <typename T> __device__ __forceinline__ T gnl(T eta) {
     constexpr int nt = GnlTerms<T>::value;
+    // both series are sums sum_{m=1}^{nt} c_m z^m, evaluated by Horner's rule with fused
+    // multiply-adds: p = c_nt, p = p z + c_m (m = nt-1..1), sum = p z
     if (eta < (T)0.5) {
         const T y = eta * eta;
-        T sF = 0, sN = 0;
+        T pF = (T)(1.0 / (4.0 * nt * nt - 1.0));
+        T pN = (T)(1.0 / (4.0 * nt * nt - 1.0) + 3.0 / (4.0 * (nt - 1) * (nt - 1) - 1.0));
 #pragma unroll
-        for (int m = nt; m >= 1; m--) {
+        for (int m = nt - 1; m >= 1; m--) {
             const double am = 1.0 / (4.0 * m * m - 1.0);
             const double lo = (m >= 2) ? am + 3.0 / (4.0 * (m - 1) * (m - 1) - 1.0) : -8.0 / 3.0;
-            sF = (sF + (T)am) * y;
-            sN = (sN + (T)lo) * y;
+            pF = pF * y + (T)am;
+            pN = pN * y + (T)lo;
         }
-        return gdiv(sN, (T)1 - sF);
+        return gdiv(pN * y, (T)1 - pF * y);
     } else if (eta > (T)2) {
         const T x = gdiv((T)1, eta * eta);
-        T sF = 0, sN = 0;
+        T pF = (T)(1.0 / (4.0 * nt * nt - 1.0));
+        T pN = (T)(1.0 / (4.0 * nt * nt - 1.0) + 3.0 / (4.0 * (nt + 1) * (nt + 1) - 1.0));
 #pragma unroll
-        for (int m = nt; m >= 1; m--) {
+        for (int m = nt - 1; m >= 1; m--) {
             const double am = 1.0 / (4.0 * m * m - 1.0);
             const double hi = am + 3.0 / (4.0 * (m + 1) * (m + 1) - 1.0);
-            sF = (sF + (T)am) * x;
-            sN = (sN + (T)hi) * x;
+            pF = pF * x + (T)am;
+            pN = pN * x + (T)hi;
         }
-        return -gdiv(sN, sF);
+        return -gdiv(pN, pF);          // the common factor x of both sums cancels
     }
     const T d = (T)1 - eta;
     if (dabs(d) < (T)1e-12) return (T)-2;
