@@ -1,7 +1,8 @@
 """Total energy and potential of the oracle (test infrastructure only).
 
-E[rho] = T_TF + T_vW + T_NL + E_H + E_PP   (Eq. efunc without E_xc)
-V      = dE/drho                            (Eq. euler)
+E[rho] = T_TF + T_vW + T_NL + E_H + E_PP (+ E_xc)   (Eq. efunc)
+V      = dE/drho                                     (Eq. euler)
+E_xc (LDA, Perdew-Zunger) is included when "XC" is among the terms.
 """
 from __future__ import annotations
 
@@ -10,6 +11,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import functionals as fn
+from . import xc as fxc
 from .grid import Grid
 
 TERMS_ALL = ("TF", "VW", "NL", "HARTREE", "PP")
@@ -30,9 +32,9 @@ class Functional:
 
 
 def evaluate(g: Grid, rho, func: Functional, Vext_G=None):
-    """Returns (energies dict with keys total, TF, vW, NL, H, PP;  V on the grid)."""
+    """Returns (energies dict with keys total, TF, vW, NL, H, PP, XC;  V on the grid)."""
     rho = np.asarray(rho, dtype=np.float64)
-    E = dict(TF=0.0, vW=0.0, NL=0.0, H=0.0, PP=0.0)
+    E = dict(TF=0.0, vW=0.0, NL=0.0, H=0.0, PP=0.0, XC=0.0)
     V = np.zeros_like(rho)
     if "TF" in func.terms:
         e, v = fn.thomas_fermi(g, rho)
@@ -59,5 +61,9 @@ def evaluate(g: Grid, rho, func: Functional, Vext_G=None):
         e, v = fn.local_pseudopotential(g, rho, Vext_G)
         E["PP"] = e
         V += v
-    E["total"] = E["TF"] + E["vW"] + E["NL"] + E["H"] + E["PP"]
+    if "XC" in func.terms:
+        e, v = fxc.lda_xc(g, rho)
+        E["XC"] = e
+        V += v
+    E["total"] = E["TF"] + E["vW"] + E["NL"] + E["H"] + E["PP"] + E["XC"]
     return E, V

@@ -300,7 +300,8 @@ def _fd_setup():
     return wl, rho, g, Vg
 
 
-@pytest.mark.parametrize("terms", [("TF",), ("VW",), ("HARTREE",), ("PP",), ("NL",), ("TF", "VW", "NL", "HARTREE", "PP")])
+@pytest.mark.parametrize("terms", [("TF",), ("VW",), ("HARTREE",), ("PP",), ("NL",), ("XC",),
+                                   ("TF", "VW", "NL", "HARTREE", "PP"), ("TF", "VW", "NL", "HARTREE", "PP", "XC")])
 def test_potential_matches_finite_differences(terms):
     """Central FD of E along a random direction equals sum V d dV (knots frozen).
     The two extreme-density points are left unperturbed: with frozen knots the
