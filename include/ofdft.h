@@ -56,7 +56,14 @@ extern "C" {
 #define OFDFT_TERM_NL       4u   /* nonlocal KEDF (LWT spline or global-kF WT)    */
 #define OFDFT_TERM_HARTREE  8u   /* Hartree, G = 0 dropped                        */
 #define OFDFT_TERM_PP      16u   /* local pseudopotential of the ions             */
-#define OFDFT_TERMS_ALL    31u
+#define OFDFT_TERM_XC      32u   /* LDA exchange-correlation: Dirac exchange and the
+                                    Perdew-Zunger (1981) correlation the paper's
+                                    benchmarks use (Sec. 3.1)                      */
+#define OFDFT_TERMS_ALL    31u   /* the kinetic + electrostatic functional (no xc)   */
+#define OFDFT_TERMS_VALID  63u   /* every defined term bit                          */
+
+/* Energies returned by the evaluation calls, in this order (Ha). */
+#define OFDFT_N_ENERGIES 7      /* total, TF, vW, NL, H, PP, XC */
 
 #define OFDFT_KNOTS_LOG     0    /* geometric progression of kF knots (s1)        */
 #define OFDFT_KNOTS_ARITH   1    /* arithmetic progression                        */
@@ -102,7 +109,7 @@ typedef struct {
     int iterations;        /* CG iterations done */
     int evaluations;       /* energy/potential evaluations done */
     double energy;         /* final total energy, Ha */
-    double energies[6];    /* total, TF, vW, NL, H, PP */
+    double energies[OFDFT_N_ENERGIES];    /* total, TF, vW, NL, H, PP, XC */
     double mu;             /* chemical potential int rho V / N_e */
     double residual;       /* || (V - mu) psi ||_2 (with dV weight) at the end */
     double last_dE;        /* |E_k - E_{k-1}| of the last iteration */
@@ -132,14 +139,14 @@ int ofdft_set_ions_pme(ofdft_grid *g, const ofdft_ions *ions, const ofdft_specie
 
 /* One energy + potential evaluation (Eq. efunc; Eq. euler for V; Sec. 2.3 s1-s4).
  * rho_dev: device [N] float/double (precision of f), >= 0.
- * E_out:   HOST double[6] = {total, TF, vW, NL, H, PP} (Ha); may be NULL.
+ * E_out:   HOST double[OFDFT_N_ENERGIES] = {total, TF, vW, NL, H, PP, XC} (Ha); may be NULL.
  * V_dev:   device [N] output potential (Ha/e), same precision; may be NULL.
  * Synchronises the stream when E_out is not NULL. */
 int ofdft_energy_potential(ofdft_grid *g, const void *rho_dev, const ofdft_functional *f,
                            double *E_out, void *V_dev);
 
 /* Same evaluation, fully asynchronous: energies are written to E_dev (DEVICE
- * double[6]) on the stream; nothing is synchronised and no host memory is
+ * double[OFDFT_N_ENERGIES]) on the stream; nothing is synchronised and no host memory is
  * touched, so the call can be captured in a CUDA graph once the workspace
  * exists (make one ordinary call first). */
 int ofdft_energy_potential_async(ofdft_grid *g, const void *rho_dev, const ofdft_functional *f,
@@ -162,7 +169,7 @@ int ofdft_optimize_density(ofdft_grid *g, void *psi_dev, const ofdft_functional 
                            ofdft_opt_report *rep);
 
 /* Batched evaluation of n independent grids (snapshots), possibly of different
- * shapes: E_out HOST [n][6]; V_dev[i] and F_out[i] may be NULL (F_out needs ions).
+ * shapes: E_out HOST [n][OFDFT_N_ENERGIES]; V_dev[i] and F_out[i] may be NULL (F_out needs ions).
  * All grids must share one stream; the batch is enqueued back to back and
  * synchronised once. */
 int ofdft_energy_potential_batched(int n, ofdft_grid *const *grids, const void *const *rho_dev,

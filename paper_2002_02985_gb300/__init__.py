@@ -21,7 +21,7 @@ from . import _lib as L
 
 __all__ = ["Grid", "Functional", "OFDFTError", "OFDFTEnergy", "energy_potential_batched", "library"]
 
-ENERGY_KEYS = ("total", "TF", "vW", "NL", "H", "PP")
+ENERGY_KEYS = ("total", "TF", "vW", "NL", "H", "PP", "XC")
 
 
 class OFDFTError(RuntimeError):
@@ -143,7 +143,7 @@ class Grid:
         import torch
         rho = self._field(rho, func)
         V = torch.empty_like(rho) if want_potential else None
-        E = (ct.c_double * 6)()
+        E = (ct.c_double * L.N_ENERGIES)()
         c, keep = func.to_c()
         st = self.lib.ofdft_energy_potential(self.h, _ptr(rho), ct.byref(c), E, _ptr(V) if V is not None else None)
         _check(self.lib, st, self.h)
@@ -151,7 +151,7 @@ class Grid:
         return dict(zip(ENERGY_KEYS, list(E))), V
 
     def energy_potential_async(self, rho, func: Functional, E_dev, V=None):
-        """Enqueue one evaluation; energies go to the device tensor E_dev (float64, 6)."""
+        """Enqueue one evaluation; energies go to the device tensor E_dev (float64, at least 7)."""
         c, keep = func.to_c()
         st = self.lib.ofdft_energy_potential_async(self.h, _ptr(rho), ct.byref(c), _ptr(E_dev),
                                                    _ptr(V) if V is not None else None)
@@ -205,7 +205,7 @@ def energy_potential_batched(grids, rhos, func: Functional, want_potential=True,
     rp = (ct.c_void_p * n)(*[r.data_ptr() for r in rhos])
     Vs = (V_out if V_out is not None else [torch.empty_like(r) for r in rhos]) if want_potential else None
     vp = (ct.c_void_p * n)(*[v.data_ptr() for v in Vs]) if want_potential else None
-    E = np.zeros((n, 6))
+    E = np.zeros((n, L.N_ENERGIES))
     Fs = [np.zeros((g.n_ions, 3)) for g in grids] if want_forces else None
     fp = (ct.POINTER(ct.c_double) * n)(*[f.ctypes.data_as(ct.POINTER(ct.c_double)) for f in Fs]) if want_forces else None
     c, keep = func.to_c()

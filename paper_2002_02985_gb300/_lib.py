@@ -17,8 +17,10 @@ STATUS = {0: "OFDFT_OK", -1: "OFDFT_ERR_INVALID_ARG", -2: "OFDFT_ERR_UNSUPPORTED
           -3: "OFDFT_ERR_BAD_DENSITY", -4: "OFDFT_ERR_OOM", -5: "OFDFT_ERR_CUDA",
           -6: "OFDFT_ERR_NOT_CONVERGED", -7: "OFDFT_ERR_NO_IONS", -8: "OFDFT_ERR_TIMEOUT"}
 
-TERM_TF, TERM_VW, TERM_NL, TERM_HARTREE, TERM_PP = 1, 2, 4, 8, 16
-TERMS_ALL = 31
+TERM_TF, TERM_VW, TERM_NL, TERM_HARTREE, TERM_PP, TERM_XC = 1, 2, 4, 8, 16, 32
+TERMS_ALL = 31          # kinetic + electrostatic functional (the benchmark's)
+TERMS_VALID = 63
+N_ENERGIES = 7          # total, TF, vW, NL, H, PP, XC
 KNOTS_LOG, KNOTS_ARITH = 0, 1
 NLPOT_EXACT, NLPOT_INTERP = 0, 1
 KERNEL_LWT, KERNEL_WT_GLOBAL = 0, 1
@@ -52,7 +54,7 @@ class CIons(ct.Structure):
 
 class COptReport(ct.Structure):
     _fields_ = [("iterations", ct.c_int), ("evaluations", ct.c_int), ("energy", ct.c_double),
-                ("energies", ct.c_double * 6), ("mu", ct.c_double), ("residual", ct.c_double),
+                ("energies", ct.c_double * N_ENERGIES), ("mu", ct.c_double), ("residual", ct.c_double),
                 ("last_dE", ct.c_double)]
 
 

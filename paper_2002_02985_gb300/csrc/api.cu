@@ -151,6 +151,8 @@ int fail(ofdft_grid *g, int code, const char *what, cudaError_t e = cudaSuccess)
                         what, e_);                                                           \
     } while (0)
 
+static_assert(E_NUM == OFDFT_N_ENERGIES, "energy slots");
+
 template <typename T> Workspace<T> &ws(ofdft_grid *g);
 template <> Workspace<float> &ws<float>(ofdft_grid *g) { return g->w32; }
 template <> Workspace<double> &ws<double>(ofdft_grid *g) { return g->w64; }
@@ -256,7 +258,7 @@ template <typename T> int ensure_ws(ofdft_grid *g, int nslots) {
         CK(cudaMalloc(&w.knots_t, OFDFT_MAX_KNOTS * sizeof(T)), "cudaMalloc knots");
         CK(cudaMalloc(&w.invdk_t, OFDFT_MAX_KNOTS * sizeof(T)), "cudaMalloc knots");
         const int nbs = 2 * g->nsm;
-        CK(cudaMalloc(&w.part_stats, 2 * nbs * sizeof(double)), "cudaMalloc partials");
+        CK(cudaMalloc(&w.part_stats, 3 * nbs * sizeof(double)), "cudaMalloc partials");
         CK(cudaMalloc(&w.part_minmax, 2 * nbs * sizeof(T)), "cudaMalloc partials");
         CK(cudaMalloc(&w.part_ax0, 4 * (size_t)w.nb_ax0 * sizeof(double)), "cudaMalloc partials");
         CK(cudaMalloc(&w.part_row, (size_t)w.nb_row * sizeof(double)), "cudaMalloc partials");
@@ -344,7 +346,7 @@ int check_functional(ofdft_grid *g, const ofdft_functional *f) {
     if (!f) return fail(g, OFDFT_ERR_INVALID_ARG, "functional is NULL");
     if (f->precision != OFDFT_FP64 && f->precision != OFDFT_FP32_MIXED)
         return fail(g, OFDFT_ERR_INVALID_ARG, "unknown precision");
-    if (f->terms & ~OFDFT_TERMS_ALL) return fail(g, OFDFT_ERR_INVALID_ARG, "unknown term bits");
+    if (f->terms & ~OFDFT_TERMS_VALID) return fail(g, OFDFT_ERR_INVALID_ARG, "unknown term bits");
     if (f->terms & OFDFT_TERM_NL) {
         if (f->kernel == OFDFT_KERNEL_LWT && (f->n_knots < 2 || f->n_knots > OFDFT_MAX_KNOTS))
             return fail(g, OFDFT_ERR_INVALID_ARG, "n_knots must be in [2, 64]");
@@ -518,13 +520,13 @@ int eval_sync(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, doub
     int rc = enqueue_eval<T>(g, rho, f, V, nullptr);
     if (rc) return rc;
     Workspace<T> &w = ws<T>(g);
-    CK(cudaMemcpyAsync(g->h_pinned, w.energies, 6 * sizeof(double), cudaMemcpyDeviceToHost, g->stream), "copy E");
+    CK(cudaMemcpyAsync(g->h_pinned, w.energies, E_NUM * sizeof(double), cudaMemcpyDeviceToHost, g->stream), "copy E");
     CK(cudaMemcpyAsync(g->h_pinned + 8, w.scal, S_NSCAL * sizeof(double), cudaMemcpyDeviceToHost, g->stream),
        "copy scalars");
     CK(cudaStreamSynchronize(g->stream), "stream synchronize");
     if (g->h_pinned[8 + S_TIMEOUT] != 0.0) return fail(g, OFDFT_ERR_TIMEOUT, "a bounded device wait expired");
     if (g->h_pinned[8 + S_BAD] != 0.0) return fail(g, OFDFT_ERR_BAD_DENSITY, "density has NaN/Inf or negative values");
-    if (E_out) std::memcpy(E_out, g->h_pinned, 6 * sizeof(double));
+    if (E_out) std::memcpy(E_out, g->h_pinned, E_NUM * sizeof(double));
     return OFDFT_OK;
 }
 
@@ -760,7 +762,7 @@ int optimize_impl(ofdft_grid *g, T *psi, const ofdft_functional *f0, double Ne, 
     const bool lwt_auto = (f0->terms & OFDFT_TERM_NL) && f0->kernel == OFDFT_KERNEL_LWT && !f0->knots;
     ofdft_functional f = *f0;
     std::vector<double> knots(OFDFT_MAX_KNOTS);
-    double E[6], Enew[6];
+    double E[E_NUM], Enew[E_NUM];
     int evals = 0;
     // normalise psi to N_e
     const double nrm = dv.dot(psi, psi) * g->dV;
@@ -831,7 +833,7 @@ int optimize_impl(ofdft_grid *g, T *psi, const ofdft_functional *f0, double Ne, 
         double lam = std::min(std::max(lam_prev, 1e-4), 0.5);
         double best_f = 1e300, best_lam = 0.0;
         for (int ls = 0; ls < 10; ls++) {
-            double El[6], dl;
+            double El[E_NUM], dl;
             if ((rc = phi(lam, El, dl))) return rc;
             const double fl = El[0];
             if (fl < best_f) { best_f = fl; best_lam = lam; std::memcpy(Enew, El, sizeof(El)); }
@@ -957,7 +959,7 @@ int enqueue_batch(int n, ofdft_grid *const *grids, const void *const *rho_dev, c
         Workspace<T> &w = ws<T>(g);
         rc = enqueue_eval<T>(g, (const T *)rho_dev[i], f, V_dev ? (T *)V_dev[i] : nullptr, nullptr);
         if (rc == OFDFT_OK) {
-            cudaMemcpyAsync(g->h_pinned, w.energies, 6 * sizeof(double), cudaMemcpyDeviceToHost, g->stream);
+            cudaMemcpyAsync(g->h_pinned, w.energies, E_NUM * sizeof(double), cudaMemcpyDeviceToHost, g->stream);
             cudaMemcpyAsync(g->h_pinned + 8, w.scal, S_NSCAL * sizeof(double), cudaMemcpyDeviceToHost, g->stream);
         }
         if (rc == OFDFT_OK && F_out && F_out[i]) {
@@ -1039,7 +1041,7 @@ int batched_impl(int n, ofdft_grid *const *grids, const void *const *rho_dev, co
         ofdft_grid *g = grids[i];
         if (g->h_pinned[8 + S_TIMEOUT] != 0.0) return fail(g, OFDFT_ERR_TIMEOUT, "a bounded device wait expired");
         if (g->h_pinned[8 + S_BAD] != 0.0) return fail(g, OFDFT_ERR_BAD_DENSITY, "bad density in batch");
-        std::memcpy(E_out + 6 * i, g->h_pinned, 6 * sizeof(double));
+        std::memcpy(E_out + E_NUM * i, g->h_pinned, E_NUM * sizeof(double));
         if (F_out && F_out[i]) std::memcpy(F_out[i], g->F_pinned, (size_t)3 * g->n_ions * sizeof(double));
     }
     return OFDFT_OK;

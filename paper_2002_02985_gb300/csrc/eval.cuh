@@ -30,8 +30,8 @@ enum {
     S_SUM_RHO = 0, S_SUM_TF = 1, S_RHO_MIN = 2, S_RHO_MAX = 3, S_RHO_MEAN = 4, S_BAD = 5,
     S_KF_WT = 6, S_TIMEOUT = 7, S_NSCAL = 8
 };
-// energy slots: total, TF, vW, NL, H, PP
-enum { E_TOT = 0, E_TF = 1, E_VW = 2, E_NL = 3, E_H = 4, E_PP = 5 };
+// energy slots: total, TF, vW, NL, H, PP, XC
+enum { E_TOT = 0, E_TF = 1, E_VW = 2, E_NL = 3, E_H = 4, E_PP = 5, E_XC = 6, E_NUM = 7 };
 
 constexpr int kMaxChan = 3 + OFDFT_MAX_KNOTS;
 constexpr int kMaxThreads = 512;     // block size bound of the FFT kernels
@@ -58,7 +58,7 @@ template <typename T> struct EvalArgs {
     T *invdk_t;              // [M-1] 1/(k_{j+1}-k_j), 0 for a zero-width interval
     int frozen;              // knots supplied by the caller
     int knot_spacing;
-    double *part_stats;      // [nb_stats * 2]
+    double *part_stats;      // [nb_stats * 3]: sum rho, sum rho^(5/3), sum rho eps_xc
     T *part_minmax;          // [nb_stats * 2]
     double *part_ax0;        // [nb_ax0 * 3]: S_H, S_vW, S_PP
     double *part_row;        // [nb_row]: S_NL

@@ -118,6 +118,38 @@ template <typename T> __device__ __forceinline__ T gnl(T eta) {
     return gdiv((T)1, F) - (T)3 * eta * eta - (T)1;
 }
 
+// ======================================================================= LDA exchange-correlation
+// Dirac exchange and the Perdew-Zunger (1981) fit of the Ceperley-Alder correlation,
+// spin unpolarised (the xc of the paper's benchmarks, Sec. 3.1), with
+// r_s = (3 / (4 pi rho))^(1/3):
+//   eps_x = -(3/4) (3/pi)^(1/3) rho^(1/3),  V_x = (4/3) eps_x
+//   r_s >= 1: eps_c = g / (1 + b1 sqrt(r_s) + b2 r_s),
+//             V_c = eps_c (1 + (7/6) b1 sqrt(r_s) + (4/3) b2 r_s) / (1 + b1 sqrt(r_s) + b2 r_s)
+//   r_s <  1: eps_c = A ln r_s + B + C r_s ln r_s + D r_s,
+//             V_c = A ln r_s + (B - A/3) + (2/3) C r_s ln r_s + ((2 D - C)/3) r_s
+// (V = d(rho eps)/d rho).  Returns rho eps_xc; v receives V_xc.
+template <typename T> __device__ __forceinline__ T lda_xc(T rho, T &v) {
+    constexpr double g = -0.1423, b1 = 1.0529, b2 = 0.3334, A = 0.0311, B = -0.048, C = 0.0020, D = -0.0116;
+    constexpr double cx = 0.7385587663820224;                 // (3/4) (3/pi)^(1/3)
+    constexpr double crs = 0.6203504908994001;                // (3 / (4 pi))^(1/3)
+    const T c = dcbrt(rho);
+    const T ex = -(T)cx * c;
+    const T rs = (T)crs / c;
+    T ec, vc;
+    if (rs >= (T)1) {
+        const T sq = dsqrt(rs);
+        const T den = (T)1 + (T)b1 * sq + (T)b2 * rs;
+        ec = (T)g / den;
+        vc = ec * ((T)1 + (T)(7.0 / 6.0 * b1) * sq + (T)(4.0 / 3.0 * b2) * rs) / den;
+    } else {
+        const T l = dlog(rs);
+        ec = (T)A * l + (T)B + (T)C * rs * l + (T)D * rs;
+        vc = (T)A * l + (T)(B - A / 3.0) + (T)(2.0 / 3.0 * C) * rs * l + (T)((2.0 * D - C) / 3.0) * rs;
+    }
+    v = (T)(4.0 / 3.0) * ex + vc;
+    return rho * (ex + ec);
+}
+
 // ======================================================================= helpers
 template <typename T> __device__ __forceinline__ int knot_interval(T kc, const T *knots, int M) {
     // largest j in [0, M-2] with knots[j] <= kc (binary search; kc already clamped)
@@ -138,17 +170,19 @@ template <typename T>
 __device__ __forceinline__ void knots_from_partials(const EvalArgs<T> &a, double *sd, T *st) {
     __shared__ double kn[OFDFT_MAX_KNOTS];
     __shared__ double smm[2];
-    double s_rho = 0.0, s_tf = 0.0;
+    double s_rho = 0.0, s_tf = 0.0, s_xc = 0.0;
     T mn = (T)3.0e38, mx = (T)-3.0e38;
     for (int b = threadIdx.x; b < a.nb_stats; b += blockDim.x) {
-        s_rho += __ldcg(a.part_stats + 2 * b);
-        s_tf += __ldcg(a.part_stats + 2 * b + 1);
+        s_rho += __ldcg(a.part_stats + 3 * b);
+        s_tf += __ldcg(a.part_stats + 3 * b + 1);
+        s_xc += __ldcg(a.part_stats + 3 * b + 2);
         const T x = __ldcg(a.part_minmax + 2 * b), y = __ldcg(a.part_minmax + 2 * b + 1);
         mn = x < mn ? x : mn;
         mx = y > mx ? y : mx;
     }
     s_rho = block_sum(s_rho, sd);
     s_tf = block_sum(s_tf, sd);
+    s_xc = block_sum(s_xc, sd);
     mn = block_min(mn, st);
     mx = block_max(mx, st);
     const double fl = (double)a.floor_;
@@ -161,6 +195,7 @@ __device__ __forceinline__ void knots_from_partials(const EvalArgs<T> &a, double
         a.scal[S_RHO_MEAN] = mean;
         a.scal[S_KF_WT] = cbrt(kThreePi2 * (mean > fl ? mean : fl));
         a.energies[E_TF] = (a.terms & 1u) ? kCTF * s_tf * a.dV : 0.0;
+        a.energies[E_XC] = (a.terms & 32u) ? s_xc * a.dV : 0.0;
         smm[0] = (double)mn;
         smm[1] = (double)mx;
     }
@@ -196,9 +231,10 @@ template <typename T>
 __global__ void __launch_bounds__(256) stats_kernel(EvalArgs<T> a) {
     __shared__ double sd[32];
     __shared__ T st[32];
-    double s_rho = 0.0, s_tf = 0.0;
+    double s_rho = 0.0, s_tf = 0.0, s_xc = 0.0;
     T mn = (T)3.0e38, mx = (T)-3.0e38;
     int bad = 0;
+    const bool xc = a.terms & 32u;
     // groups of 4 consecutive points: summed in T, then added in FP64 (keeps the FP64 pipe
     // idle); U groups a grid stride apart per iteration, all loaded before any is used
     constexpr int U = 4;
@@ -219,7 +255,7 @@ __global__ void __launch_bounds__(256) stats_kernel(EvalArgs<T> a) {
 #pragma unroll
         for (int u = 0; u < U; u++) {
             const long long gi = g0 + u * stride;
-            T r4 = 0, t4 = 0;
+            T r4 = 0, t4 = 0, x4 = 0;
 #pragma unroll
             for (int q = 0; q < 4; q++) {
                 if (4 * gi + q < a.N) {
@@ -228,18 +264,25 @@ __global__ void __launch_bounds__(256) stats_kernel(EvalArgs<T> a) {
                     const T c = dcbrt(xv);
                     r4 += xv;
                     t4 += xv * c * c;                                      // rho^(5/3)
+                    if (xc) {
+                        T vxc;
+                        x4 += lda_xc(xv > a.floor_ ? xv : a.floor_, vxc);  // rho eps_xc
+                    }
                     mn = xv < mn ? xv : mn;
                     mx = xv > mx ? xv : mx;
                 }
             }
             s_rho += (double)r4;
             s_tf += (double)t4;
+            s_xc += (double)x4;
         }
     }
     s_rho = block_sum(s_rho, sd);
-    if (threadIdx.x == 0) a.part_stats[2 * blockIdx.x] = s_rho;
+    if (threadIdx.x == 0) a.part_stats[3 * blockIdx.x] = s_rho;
     s_tf = block_sum(s_tf, sd);
-    if (threadIdx.x == 0) a.part_stats[2 * blockIdx.x + 1] = s_tf;
+    if (threadIdx.x == 0) a.part_stats[3 * blockIdx.x + 1] = s_tf;
+    if (xc) s_xc = block_sum(s_xc, sd);
+    if (threadIdx.x == 0) a.part_stats[3 * blockIdx.x + 2] = s_xc;
     mn = block_min(mn, st);
     if (threadIdx.x == 0) a.part_minmax[2 * blockIdx.x] = mn;
     mx = block_max(mx, st);
@@ -719,6 +762,11 @@ __device__ __forceinline__ void row_inv_body(const EvalArgs<T> &a) {
             const T c = dcbrt(xp);
             v = (T)(5.0 / 3.0 * kCTF) * c * c;          // V_TF = (5/3) C_TF rho^(2/3)
         }
+        if (a.terms & 32u) {
+            T vxc;
+            lda_xc(x > a.floor_ ? x : a.floor_, vxc);
+            v += vxc;
+        }
         sv[o] = v;
         const T p = dsqrt(xp);
         svw[o] = (T)1 / ((T)2 * (p > psi_floor ? p : psi_floor));
@@ -1048,6 +1096,11 @@ __device__ __forceinline__ void row_inv2_body(const EvalArgs<T> &a) {
                     const T c = dcbrt(xp);
                     acc[q][s] = (T)(5.0 / 3.0 * kCTF) * c * c;        // V_TF = (5/3) C_TF rho^(2/3)
                 }
+                if (a.terms & 32u) {
+                    T vxc;
+                    lda_xc(x > a.floor_ ? x : a.floor_, vxc);
+                    acc[q][s] += vxc;
+                }
                 const T p = dsqrt(xp);
                 fvw[q][s] = (T)1 / ((T)2 * (p > psi_floor ? p : psi_floor));
                 if (nl) {
@@ -1223,7 +1276,7 @@ __global__ void __launch_bounds__(1024) finalize_kernel(EvalArgs<T> a) {
     }
     // nonlocal: G-space sum (exact LWT, WT) or real-space sum (interpolated LWT)
     E[E_NL] = (a.terms & 4u) ? (real_space ? nl * a.dV : a.omega * ng) : 0.0;
-    E[E_TOT] = E[E_TF] + E[E_VW] + E[E_NL] + E[E_H] + E[E_PP];
+    E[E_TOT] = E[E_TF] + E[E_VW] + E[E_NL] + E[E_H] + E[E_PP] + E[E_XC];
 }
 
 // ======================================================================= kernel wrappers

@@ -24,8 +24,9 @@ pytestmark = pytest.mark.gpu
 import paper_2002_02985_gb300 as ofd  # noqa: E402
 from paper_2002_02985_gb300 import _lib as L  # noqa: E402
 
-TERM_BITS = {"TF": L.TERM_TF, "VW": L.TERM_VW, "NL": L.TERM_NL, "HARTREE": L.TERM_HARTREE, "PP": L.TERM_PP}
-KEYMAP = {"TF": "TF", "VW": "vW", "NL": "NL", "HARTREE": "H", "PP": "PP"}
+TERM_BITS = {"TF": L.TERM_TF, "VW": L.TERM_VW, "NL": L.TERM_NL, "HARTREE": L.TERM_HARTREE, "PP": L.TERM_PP,
+             "XC": L.TERM_XC}
+KEYMAP = {"TF": "TF", "VW": "vW", "NL": "NL", "HARTREE": "H", "PP": "PP", "XC": "XC"}
 
 
 def triclinic():
@@ -75,6 +76,7 @@ FP64_CASES = [
     ((30, 24, 27), dict(n_knots=8, nl_potential=L.NLPOT_INTERP)),
     ((20, 20, 20), dict(n_knots=4, kernel=L.KERNEL_WT_GLOBAL)),
     ((25, 32, 18), dict(n_knots=7)),
+    ((18, 16, 20), dict(n_knots=6, terms=L.TERMS_VALID)),            # with LDA xc
 ]
 
 
@@ -82,12 +84,12 @@ FP64_CASES = [
 def test_fp64_energy_potential_matches_oracle(shape, kw):
     cell, pos, rho = small_case(shape)
     E, V, Eo, Vo, og, _ = run_both(cell, shape, pos, rho, kw, L.FP64)
-    for k in ("TF", "vW", "NL", "H", "PP", "total"):
+    for k in ("TF", "vW", "NL", "H", "PP", "XC", "total"):
         assert abs(E[k] - Eo[k]) <= 1e-10 * max(1.0, abs(Eo[k])), (k, E[k], Eo[k])
     assert np.max(np.abs(V - Vo)) <= 1e-9 * max(1.0, np.max(np.abs(Vo))), np.max(np.abs(V - Vo))
 
 
-@pytest.mark.parametrize("term", ["TF", "VW", "NL", "HARTREE", "PP"])
+@pytest.mark.parametrize("term", ["TF", "VW", "NL", "HARTREE", "PP", "XC"])
 def test_fp64_single_terms(term):
     shape = (18, 20, 16)
     cell, pos, rho = small_case(shape, seed=3)
@@ -100,6 +102,7 @@ def test_fp64_single_terms(term):
 FP32_CASES = [
     ("fcc-al-4/32", dict()),
     ("fcc-al-4/32", dict(nl_potential=L.NLPOT_INTERP)),
+    ("fcc-al-4/32", dict(terms=L.TERMS_VALID)),                        # with LDA xc
 ]
 
 
@@ -111,7 +114,7 @@ def test_fp32_mixed_workload_matches_oracle(name, kw):
                                    dict(n_knots=wl["n_knots"], **kw), L.FP32_MIXED, wl["species"],
                                    tuple(wl["Z"]), tuple(wl["rc"]))
     assert abs(E["total"] - Eo["total"]) / wl["n_atoms"] <= 1e-6, (E["total"], Eo["total"])
-    for k in ("TF", "vW", "NL", "H", "PP"):
+    for k in ("TF", "vW", "NL", "H", "PP", "XC"):
         assert abs(E[k] - Eo[k]) / wl["n_atoms"] <= 1e-6, (k, E[k], Eo[k])
     m = knot_mask(rho.astype(np.float32).astype(np.float64), wl["n_knots"])
     rel = np.linalg.norm((V - Vo)[m]) / np.linalg.norm(Vo[m])
@@ -272,15 +275,15 @@ def test_fp32_channel_batched_rows_match_oracle(kw):
     # 4 atoms carry E_H ~ 44 Ha here: FP32 rounding (~1e-7 of each term's magnitude) is
     # bounded per atom or relative to the terms, whichever is larger (the total is a sum
     # of large terms of both signs, so its bound uses the sum of their magnitudes)
-    scale = {k: abs(Eo[k]) for k in ("TF", "vW", "NL", "H", "PP")}
+    scale = {k: abs(Eo[k]) for k in ("TF", "vW", "NL", "H", "PP", "XC")}
     scale["total"] = sum(scale.values())
-    for k in ("TF", "vW", "NL", "H", "PP", "total"):
+    for k in ("TF", "vW", "NL", "H", "PP", "XC", "total"):
         assert abs(E[k] - Eo[k]) <= max(4 * 1e-6, 2e-7 * scale[k]), (k, E[k], Eo[k])
     m = knot_mask(rho.astype(np.float32).astype(np.float64), kw["n_knots"])
     assert np.linalg.norm((V - Vo)[m]) / np.linalg.norm(Vo[m]) <= 1e-4
 
 
-@pytest.mark.parametrize("term", ["TF", "VW", "NL", "HARTREE", "PP"])
+@pytest.mark.parametrize("term", ["TF", "VW", "NL", "HARTREE", "PP", "XC"])
 def test_fp32_channel_batched_rows_single_terms(term):
     shape = (8, 5, 128)
     cell = np.diag([4.0, 3.0, 25.0])
