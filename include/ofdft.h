@@ -157,6 +157,19 @@ int ofdft_energy_potential_async(ofdft_grid *g, const void *rho_dev, const ofdft
  * F_out: HOST double[n_ions][3] (Ha/bohr).  precision selects the rho dtype. */
 int ofdft_forces(ofdft_grid *g, const void *rho_dev, int precision, double *F_out);
 
+/* Ion-ion electrostatic energy and forces of the ions given to ofdft_set_ions or
+ * ofdft_set_ions_pme: point charges Z_s in a uniform neutralising background, by
+ * Ewald summation.  The paper's Eq. efunc has no ion-ion term; with it (and
+ * OFDFT_TERM_XC) the energy becomes a total energy for structures and forces.
+ * The reciprocal sum runs over the grid's G vectors (the split parameter is set
+ * from the grid so that the neglected terms are below 1e-16; with
+ * ofdft_set_ions_pme the structure factor is the PME one), the real-space sum
+ * over a cell list; FP64 throughout.  Independent of the density.
+ * E_out: HOST double[1] (Ha) or NULL; F_out: HOST double[n][3] (Ha/bohr) or NULL
+ * (not both NULL).  Synchronises the handle's stream.
+ * Errors: OFDFT_ERR_NO_IONS, OFDFT_ERR_INVALID_ARG, OFDFT_ERR_OOM, OFDFT_ERR_CUDA. */
+int ofdft_ewald(ofdft_grid *g, double *E_out, double *F_out);
+
 /* psi = sqrt(rho) CG density optimisation (Sec. 2.4, Eq. euler2):
  * psi_dev (device [N], precision of f) holds the initial psi and receives the
  * result; int psi^2 = N_e is imposed first and then conserved by the

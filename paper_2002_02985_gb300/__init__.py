@@ -174,6 +174,15 @@ class Grid:
             out[nm.value.decode()] = (n.value, ms.value)
         return out
 
+    def ewald(self, want_forces: bool = True):
+        """Ion-ion Ewald energy (Ha) and forces (Ha/bohr, [n][3] or None) of the ions set."""
+        E = ct.c_double()
+        F = np.zeros((self.n_ions, 3)) if want_forces else None
+        st = self.lib.ofdft_ewald(self.h, ct.byref(E), F.ctypes.data_as(ct.POINTER(ct.c_double)) if want_forces
+                                  else None)
+        _check(self.lib, st, self.h)
+        return E.value, F
+
     def forces(self, rho, precision: int = L.FP32_MIXED):
         F = np.zeros((self.n_ions, 3))
         st = self.lib.ofdft_forces(self.h, _ptr(rho), precision, F.ctypes.data_as(ct.POINTER(ct.c_double)))

@@ -10,6 +10,7 @@
 
 #include "../../include/ofdft.h"
 #include "eval.cuh"
+#include "ewald.cuh"
 #include "misc.cuh"
 #include "pme.cuh"
 
@@ -115,6 +116,11 @@ struct ofdft_grid {
     double *F_dev = nullptr, *F_pinned = nullptr;
     int F_len = 0;
     unsigned long long generation = 0;     // bumped whenever device buffers are (re)allocated
+    // ion-ion Ewald sum: sorted ions, cell list, results
+    double4 *ew_p = nullptr;
+    int *ew_cell = nullptr, *ew_orig = nullptr, *ew_cstart = nullptr;
+    double *ew_F = nullptr, *ew_e = nullptr, *ew_part = nullptr;
+    int ew_n = 0, ew_ncell = 0;
     int *d_species = nullptr;
     double *d_Z = nullptr, *d_rc = nullptr;
     double *h_pinned = nullptr;  // 64 doubles of pinned host memory
@@ -721,6 +727,171 @@ template <typename T> int forces_impl(ofdft_grid *g, const T *rho, double *F) {
     return OFDFT_OK;
 }
 
+// ---------------------------------------------------------------- ion-ion Ewald sum
+constexpr double kEwaldCut = 6.0;      // erfc(6) ~ 2e-17, exp(-36) ~ 2e-16
+constexpr int kEwaldBlocks = 512;
+
+int ewald_impl(ofdft_grid *g, double *E_out, double *F_out) {
+    typedef double2 C;
+    const int n = g->n_ions;
+    // split parameter: the grid's half spectrum holds every G inside the sphere of radius
+    // min_a pi n_a / |a_a|; at its surface exp(-G^2/(4 eta^2)) = exp(-36)
+    const double *A = g->cell;
+    double gs = 1e300;
+    for (int a = 0; a < 3; a++) {
+        const double len = std::sqrt(A[3 * a] * A[3 * a] + A[3 * a + 1] * A[3 * a + 1] + A[3 * a + 2] * A[3 * a + 2]);
+        gs = std::min(gs, kPi * g->n[a] / len);
+    }
+    const double eta = gs / (2.0 * kEwaldCut), rcut = kEwaldCut / eta;
+    // ---- real space: cell list over the lattice planes (host counting sort)
+    EwaldReal er;
+    er.n = n;
+    er.eta = eta;
+    er.rc2 = rcut * rcut;
+    for (int i = 0; i < 9; i++) er.A[i] = A[i];
+    long long ncell = 1;
+    for (int a = 0; a < 3; a++) {
+        const int b = (a + 1) % 3, c = (a + 2) % 3;
+        const double cx = A[3 * b + 1] * A[3 * c + 2] - A[3 * b + 2] * A[3 * c + 1];
+        const double cy = A[3 * b + 2] * A[3 * c + 0] - A[3 * b + 0] * A[3 * c + 2];
+        const double cz = A[3 * b + 0] * A[3 * c + 1] - A[3 * b + 1] * A[3 * c + 0];
+        const double width = g->omega / std::sqrt(cx * cx + cy * cy + cz * cz);      // plane spacing
+        er.nc[a] = (int)std::max(1.0, std::min(256.0, std::floor(width / rcut)));
+        er.kr[a] = (int)std::ceil(rcut / (width / er.nc[a]));
+        ncell *= er.nc[a];
+    }
+    std::vector<int> cell(n), cnt(ncell + 1, 0), orig(n), scell(n);
+    std::vector<double4> wp(n), sp(n);
+    for (int I = 0; I < n; I++) {
+        const double *R = &g->pos[3 * (size_t)I];
+        double f[3];
+        int ci[3];
+        for (int a = 0; a < 3; a++) {
+            f[a] = R[0] * g->recip[3 * a] + R[1] * g->recip[3 * a + 1] + R[2] * g->recip[3 * a + 2];
+            f[a] -= std::floor(f[a]);
+            ci[a] = std::min(er.nc[a] - 1, (int)(f[a] * er.nc[a]));
+        }
+        wp[I] = make_double4(f[0] * A[0] + f[1] * A[3] + f[2] * A[6], f[0] * A[1] + f[1] * A[4] + f[2] * A[7],
+                             f[0] * A[2] + f[1] * A[5] + f[2] * A[8], g->Z[g->species[I]]);
+        cell[I] = (ci[0] * er.nc[1] + ci[1]) * er.nc[2] + ci[2];
+        cnt[cell[I] + 1]++;
+    }
+    for (long long c = 0; c < ncell; c++) cnt[c + 1] += cnt[c];
+    std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+    for (int I = 0; I < n; I++) {
+        const int k = fill[cell[I]]++;
+        sp[k] = wp[I];
+        orig[k] = I;
+        scell[k] = cell[I];
+    }
+    if (n > g->ew_n || ncell > g->ew_ncell) {
+        cudaFree(g->ew_p);
+        cudaFree(g->ew_cell);
+        cudaFree(g->ew_orig);
+        cudaFree(g->ew_F);
+        cudaFree(g->ew_e);
+        cudaFree(g->ew_cstart);
+        g->ew_p = nullptr;
+        g->ew_cell = g->ew_orig = g->ew_cstart = nullptr;
+        g->ew_F = g->ew_e = nullptr;
+        g->ew_n = g->ew_ncell = 0;
+        CK(cudaMalloc(&g->ew_p, (size_t)n * sizeof(double4)), "cudaMalloc Ewald ions");
+        CK(cudaMalloc(&g->ew_cell, (size_t)n * sizeof(int)), "cudaMalloc Ewald ions");
+        CK(cudaMalloc(&g->ew_orig, (size_t)n * sizeof(int)), "cudaMalloc Ewald ions");
+        CK(cudaMalloc(&g->ew_F, (size_t)6 * n * sizeof(double)), "cudaMalloc Ewald forces");
+        CK(cudaMalloc(&g->ew_e, (size_t)n * sizeof(double)), "cudaMalloc Ewald energies");
+        CK(cudaMalloc(&g->ew_cstart, (size_t)(ncell + 1) * sizeof(int)), "cudaMalloc Ewald cells");
+        g->ew_n = n;
+        g->ew_ncell = (int)ncell;
+    }
+    if (!g->ew_part) CK(cudaMalloc(&g->ew_part, (kEwaldBlocks + 8) * sizeof(double)), "cudaMalloc Ewald partials");
+    cudaStream_t st = g->stream;
+    CK(cudaMemcpyAsync(g->ew_p, sp.data(), (size_t)n * sizeof(double4), cudaMemcpyHostToDevice, st), "upload");
+    CK(cudaMemcpyAsync(g->ew_cell, scell.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice, st), "upload");
+    CK(cudaMemcpyAsync(g->ew_orig, orig.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice, st), "upload");
+    CK(cudaMemcpyAsync(g->ew_cstart, cnt.data(), (size_t)(ncell + 1) * sizeof(int), cudaMemcpyHostToDevice, st),
+       "upload");
+    er.p = g->ew_p;
+    er.cell = g->ew_cell;
+    er.cstart = g->ew_cstart;
+    er.orig = g->ew_orig;
+    er.F = g->ew_F;                                   // [n][3] real space, then [n][3] reciprocal
+    er.e = g->ew_e;
+    CK(ewald_real(er, st), "Ewald real space");
+    double *sums = g->ew_part + kEwaldBlocks;         // [0] real-space sum, [1] reciprocal sum
+    CK(ewald_sum(g->ew_e, n, g->ew_part, kEwaldBlocks, sums, st), "Ewald sum");
+    // ---- reciprocal space on the grid: S_Z(G), its energy, then its forces
+    int rc = ensure_ws<double>(g, 3);
+    if (rc) return rc;
+    Workspace<double> &w = g->w64;
+    C *sz;
+    if (g->pme_order > 0) {
+        if ((rc = ensure_pme_buffers<double>(g))) return rc;
+        sz = (C *)w.chan + 2 * g->NH;
+        CK(cudaMemsetAsync(g->Qfix, 0, (size_t)g->N * sizeof(unsigned long long), st), "memset");
+        for (int s = 0; s < g->n_species; s++) {
+            PmeArgs pa = pme_args(g, s);
+            pa.charge_ff = 1;
+            CK(pme_spread(pa, g->Qfix, st), "PME spread");
+            CK(pme_fixed_to_real<double>(g->Qfix, (double *)g->pme_real, g->N, st), "PME grid");
+            if ((rc = forward_plain<double>(g, w, (const double *)g->pme_real))) return rc;
+            CK(pme_vext<C>(pa, (const C *)w.chan, g->pmeB, g->Z[s], g->rc[s], (double)g->species_count[s],
+                           (double)g->N, g->omega, sz, s == 0, st),
+               "PME charge structure factor");
+        }
+    } else {
+        sz = (C *)w.chan;
+        IonArgs ia = ion_args(g);
+        ia.charge_ff = 1;
+        CK(launch_vext(ia, sz, nullptr, st), "charge structure factor");
+    }
+    double bv[9];
+    for (int i = 0; i < 9; i++) bv[i] = 2.0 * kPi * g->recip[i];
+    CK(ewald_recip(g->n[0], g->n[1], g->n[2], bv, eta, g->omega, sz, g->ew_part, kEwaldBlocks, st), "Ewald G sum");
+    CK(ewald_sum(g->ew_part, kEwaldBlocks, g->ew_part + kEwaldBlocks + 2, 1, sums + 1, st), "Ewald sum");
+    double *Frec = g->ew_F + 3 * (size_t)n;
+    if (F_out) {
+        if ((rc = ensure_force_buffers<double>(g))) return rc;
+        if (g->pme_order > 0) {
+            for (int s = 0; s < g->n_species; s++) {
+                PmeArgs pa = pme_args(g, s);
+                pa.charge_ff = 1;
+                C *slot1 = (C *)w.chan + g->NH;
+                CK(pme_force_field<C>(pa, sz, g->pmeB, g->Z[s], g->rc[s], slot1, st), "PME field");
+                // (the last argument is any N-point real field the inverse rows may read; slot 0 is free)
+                if ((rc = inverse_plain<double>(g, w, 1, (double *)g->pme_real, (const double *)w.chan))) return rc;
+                CK(pme_gather<double>(pa, (const double *)g->pme_real, Frec, st), "PME gather");
+            }
+        } else {
+            bool fast;
+            int nchunk, nsp;
+            force_layout<double>(g, fast, nchunk, nsp);
+            IonArgs ia = ion_args(g);
+            ia.charge_ff = 1;
+            CK(launch_forces<C>(ia, sz, g->fpart, nchunk, st), "Ewald forces");
+            CK(launch_reduce_force_partials(g->fpart, nsp, n, nchunk, Frec, st), "force reduction");
+        }
+    }
+    std::vector<double> F2(F_out ? 6 * (size_t)n : 0);
+    double hs[2];
+    CK(cudaMemcpyAsync(hs, sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, st), "copy energies");
+    if (F_out) CK(cudaMemcpyAsync(F2.data(), g->ew_F, 6 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, st),
+                  "copy forces");
+    CK(cudaStreamSynchronize(st), "stream synchronize");
+    double zz = 0.0, zs = 0.0;
+    for (int I = 0; I < n; I++) {
+        const double z = g->Z[g->species[I]];
+        zz += z * z;
+        zs += z;
+    }
+    const double E = hs[0] + 2.0 * kPi / g->omega * hs[1] - eta / std::sqrt(kPi) * zz -
+                     kPi * zs * zs / (2.0 * g->omega * eta * eta);
+    if (E_out) *E_out = E;
+    if (F_out)
+        for (size_t k = 0; k < 3 * (size_t)n; k++) F_out[k] = F2[k] + F2[3 * (size_t)n + k];
+    return OFDFT_OK;
+}
+
 // ---------------------------------------------------------------- optimiser
 template <typename T> struct Dev {
     ofdft_grid *g;
@@ -1157,6 +1328,13 @@ int ofdft_grid_destroy(ofdft_grid *g) {
     cudaFree(g->d_species);
     cudaFree(g->d_Z);
     cudaFree(g->d_rc);
+    cudaFree(g->ew_p);
+    cudaFree(g->ew_cell);
+    cudaFree(g->ew_orig);
+    cudaFree(g->ew_cstart);
+    cudaFree(g->ew_F);
+    cudaFree(g->ew_e);
+    cudaFree(g->ew_part);
     cudaFreeHost(g->h_pinned);
     delete g;
     return OFDFT_OK;
@@ -1322,6 +1500,13 @@ int ofdft_forces(ofdft_grid *g, const void *rho_dev, int precision, double *F_ou
     if (precision == OFDFT_FP64) return forces_impl<double>(g, (const double *)rho_dev, F_out);
     if (precision == OFDFT_FP32_MIXED) return forces_impl<float>(g, (const float *)rho_dev, F_out);
     return fail(g, OFDFT_ERR_INVALID_ARG, "unknown precision");
+}
+
+int ofdft_ewald(ofdft_grid *g, double *E_out, double *F_out) {
+    if (!g) return OFDFT_ERR_INVALID_ARG;
+    if (!E_out && !F_out) return fail(g, OFDFT_ERR_INVALID_ARG, "E_out and F_out are both NULL");
+    if (!g->have_ions) return fail(g, OFDFT_ERR_NO_IONS, "the Ewald sum needs ions");
+    return ewald_impl(g, E_out, F_out);
 }
 
 int ofdft_optimize_density(ofdft_grid *g, void *psi_dev, const ofdft_functional *f, double N_e,

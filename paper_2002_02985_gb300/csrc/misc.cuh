@@ -6,6 +6,7 @@
 namespace ofdft {
 
 // V_ext(G) = (1/Omega) sum_s v_s(|G|) S_s(G), S_s(G) = sum_{I in s} e^{-iG.R_I}
+// (with charge_ff: S_Z(G) = sum_s Z_s S_s(G) instead, for the ion-ion Ewald sum)
 // with the phase of each ion factorised per axis: e^{-iG.R} = P0[k0] P1[k1] P2[k2],
 // P_a[k] = e^{-2 pi i m_a(k) f_a} (f = fractional coordinates).  FP64 throughout.
 struct IonArgs {
@@ -15,6 +16,7 @@ struct IonArgs {
     const double2 *ph0, *ph1, *ph2;  // [n_ions][n0], [n_ions][n1], [n_ions][n2h]
     const int *species;              // [n_ions]
     const double *Z, *rc;            // [n_species]
+    int charge_ff = 0;               // 1: form factor Z_s instead of v_s (Ewald: S_Z(G) and its forces)
 };
 
 // vext64 != null: FP64 build; otherwise the FP32 copy from FP32 phase products

@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(256) vext_kernel(IonArgs a, double2 *v64, floa
             S.x += p.x;
             S.y += p.y;
         }
-        const double v = pp_form(q2, a.Z[s], a.rc[s]) / a.omega;
+        const double v = a.charge_ff ? a.Z[s] : pp_form(q2, a.Z[s], a.rc[s]) / a.omega;
         acc.x += v * S.x;
         acc.y += v * S.y;
     }
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(256) forces_kernel(IonArgs a, const C *rh, dou
         const C r = rh[e];
         // Im[conj(r) p] = r.x p.y - r.y p.x
         const double im = (double)r.x * p.y - (double)r.y * p.x;
-        const double f = -w * pp_form(q2, Z, rc) * im;
+        const double f = -w * (a.charge_ff ? Z : pp_form(q2, Z, rc)) * im;
         fx += f * gx;
         fy += f * gy;
         fz += f * gz;

@@ -122,7 +122,7 @@ __global__ void pme_vext_kernel(PmeArgs a, const C *qhat, const double2 *B, doub
         sx = count;
         sy = 0.0;
     }
-    const double v = pme_pp_form(q2, Z, rc) / omega;
+    const double v = a.charge_ff ? Z : pme_pp_form(q2, Z, rc) / omega;
     C out;
     out.x = (decltype(out.x))(v * sx);
     out.y = (decltype(out.y))(v * sy);
@@ -150,7 +150,7 @@ __global__ void pme_force_field_kernel(PmeArgs a, const C *rhohat, const double2
         const double2 b0 = B[k0], b1 = B[a.n0 + k1], b2 = B[a.n0 + a.n1 + k2];
         const double rx = b0.x * b1.x - b0.y * b1.y, ry = b0.x * b1.y + b0.y * b1.x;
         const double bx = rx * b2.x - ry * b2.y, by = -(rx * b2.y + ry * b2.x);   // conj of the product
-        const double v = pme_pp_form(q2, Z, rc);
+        const double v = a.charge_ff ? Z : pme_pp_form(q2, Z, rc);
         const double hx = rhohat[e].x, hy = rhohat[e].y;
         out.x = (decltype(out.x))(v * (hx * bx - hy * by));
         out.y = (decltype(out.y))(v * (hx * by + hy * bx));

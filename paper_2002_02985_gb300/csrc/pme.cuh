@@ -12,6 +12,7 @@ struct PmeArgs {
     double recip[9];                     // rows b_a (a_i . b_j = delta_ij), no 2 pi
     const double *pos;                   // device [n_ions][3]
     const int *species;                  // device [n_ions]
+    int charge_ff = 0;                   // 1: form factor Z_s instead of v_s (Ewald sum)
 };
 
 // Q (fixed point, scale 2^40) += B-spline stencils of the ions of species a.s
