@@ -7,10 +7,11 @@ namespace ofdft {
 template <typename T> bool find_specialised_a(int, int, const void **, const void **, int *, int *);
 template <typename T> bool find_specialised_b(int, int, const void **, const void **, int *, int *);
 template <typename T> bool find_specialised_c(int, int, const void **, const void **, int *, int *);
+template <typename T> bool find_specialised_d(int, int, const void **, const void **, int *, int *);
 
 template <typename T> bool find_specialised(int role, int n, const void **k1, const void **k2, int *B, int *nt) {
     return find_specialised_a<T>(role, n, k1, k2, B, nt) || find_specialised_b<T>(role, n, k1, k2, B, nt) ||
-           find_specialised_c<T>(role, n, k1, k2, B, nt);
+           find_specialised_c<T>(role, n, k1, k2, B, nt) || find_specialised_d<T>(role, n, k1, k2, B, nt);
 }
 
 template <typename T> LaunchSet generic_kernels() {

@@ -63,3 +63,15 @@
         return true;                                                                          \
     }
 
+
+// OFDFT_SPECIALISE_AXIS0(T, N, TW, NT, MAXR, MINB): only the reciprocal-space kernel for n0 = N
+// (out of place or in place as axis0_oop<T>(N) says, which the host also uses for its scratch).
+#define OFDFT_SPECIALISE_AXIS0(T, N, TW, NT, MAXR, MINB)                                      \
+    if (role == ROLE_AXIS0 && n == N) {                                                       \
+        typedef ::ofdft::CtPolicy<T, N, TW, TW, NT, MAXR, MINB, ::ofdft::axis0_oop<T>(N)> PA;  \
+        *k1 = (const void *)axis0_kernel<T, PA>;                                              \
+        *k2 = nullptr;                                                                        \
+        *B = TW;                                                                              \
+        *nt = NT;                                                                             \
+        return true;                                                                          \
+    }
