@@ -930,6 +930,30 @@ int optimize_impl(ofdft_grid *g, T *psi, const ofdft_functional *f0, double Ne, 
     T *tmp = psil + N;
     Dev<T> dv{g, &w};
     cudaStream_t s = g->stream;
+    // Preconditioner of the gradient, P(G) = a G^2 / (G^4 + a G^2 + b), the inverse of a model
+    // Hessian in psi about the mean density rho_m: G^2 from the von Weizsaecker term (it
+    // grows with the grid's cut-off, so plain CG needs ever more iterations on finer grids),
+    // a = (70/9) C_TF rho_m^(2/3) from the local terms, b/G^2 = 16 pi rho_m / G^2 from Hartree
+    // (stiff long-wavelength charge moves; a kinetic-only preconditioner amplifies exactly
+    // those and stalls).  OFDFT_OPT_PRECOND=0 turns it off.
+    typedef typename Vec2<T>::type C;
+    const char *env_pc = std::getenv("OFDFT_OPT_PRECOND");
+    const bool precond = !(env_pc && env_pc[0] == '0');
+    const double rho_m = Ne / g->omega;
+    const double pa = 70.0 / 9.0 * kCTF * std::pow(rho_m, 2.0 / 3.0), pb = 16.0 * kPi * rho_m;
+    double bv[9];
+    for (int i = 0; i < 9; i++) bv[i] = 2.0 * kPi * g->recip[i];
+    T *z = tmp;                        // preconditioned gradient (tmp is free until the line search)
+    double zg_prev = 0.0;
+    auto apply_precond = [&](const T *x, T *out) -> int {
+        // the plain forward transform drops the mean (kept in the scalars); P(0) = 1 adds it back
+        int r = forward_plain<T>(g, w, x);
+        if (r) return r;
+        CK(launch_precond<C>((C *)w.chan, g->n[0], g->n[1], g->n[2], bv, pa, pb, s), "preconditioner");
+        if ((r = inverse_plain<T>(g, w, 0, out, x))) return r;
+        CK(launch_add_scalar<T>(out, w.scal + S_RHO_MEAN, N, s), "preconditioner mean");
+        return OFDFT_OK;
+    };
     const bool lwt_auto = (f0->terms & OFDFT_TERM_NL) && f0->kernel == OFDFT_KERNEL_LWT && !f0->knots;
     ofdft_functional f = *f0;
     std::vector<double> knots(OFDFT_MAX_KNOTS);
@@ -964,16 +988,28 @@ int optimize_impl(ofdft_grid *g, T *psi, const ofdft_functional *f0, double Ne, 
         // g = 2 psi (V - mu) dV, mu = int rho V / N_e
         mu = dv.dot(psi, psi, V) * g->dV / Ne;
         CK(launch_grad<T>(grad, psi, V, mu, g->dV, N, s), "grad");
-        double beta = 0.0;
-        if (have_dir && (it % 50) != 1) {
-            const double gg = dv.dot(grad, grad), ggp = dv.dot(grad, gprev), gpgp = dv.dot(gprev, gprev);
-            beta = std::max(0.0, (gg - ggp) / gpgp);
+        double beta = 0.0, zg = 0.0;
+        const T *src = grad;           // the (preconditioned) steepest-descent direction
+        if (precond) {
+            if ((rc = apply_precond(grad, z))) return rc;
+            src = z;
+            zg = dv.dot(z, grad);
         }
-        // d = -g + beta d
-        if (have_dir && beta > 0.0) CK(launch_axpby<T>(d, grad, -1.0, beta, N, s), "axpby");
-        else CK(launch_axpby<T>(d, grad, -1.0, 0.0, N, s), "axpby");
-        if (dv.dot(d, grad) >= 0.0) CK(launch_axpby<T>(d, grad, -1.0, 0.0, N, s), "axpby");
+        if (have_dir && (it % 50) != 1) {
+            if (precond) {
+                // preconditioned PR+: beta = <z, g - g_prev> / <z_prev, g_prev>
+                beta = zg_prev > 0.0 ? std::max(0.0, (zg - dv.dot(z, gprev)) / zg_prev) : 0.0;
+            } else {
+                const double gg = dv.dot(grad, grad), ggp = dv.dot(grad, gprev), gpgp = dv.dot(gprev, gprev);
+                beta = std::max(0.0, (gg - ggp) / gpgp);
+            }
+        }
+        // d = -src + beta d
+        if (have_dir && beta > 0.0) CK(launch_axpby<T>(d, src, -1.0, beta, N, s), "axpby");
+        else CK(launch_axpby<T>(d, src, -1.0, 0.0, N, s), "axpby");
+        if (dv.dot(d, grad) >= 0.0) CK(launch_axpby<T>(d, src, -1.0, 0.0, N, s), "axpby");
         CK(launch_copy<T>(gprev, grad, N, s), "copy");
+        zg_prev = zg;
         have_dir = true;
         // p = d - (<d,psi>/<psi,psi>) psi, normalised to N_e
         CK(launch_copy<T>(p, d, N, s), "copy");

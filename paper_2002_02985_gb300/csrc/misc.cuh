@@ -61,5 +61,10 @@ template <typename T>
 cudaError_t launch_square(T *rho, T *psi, double scale, long long N, cudaStream_t s);
 // d = -g + beta d ; dot partial <d, g> computed by launch_dot afterwards
 template <typename T> cudaError_t launch_copy(T *dst, const T *src, long long N, cudaStream_t s);
+// x += c[0] (c a device scalar)
+template <typename T> cudaError_t launch_add_scalar(T *x, const double *c, long long N, cudaStream_t s);
+// optimiser preconditioner on a normalised half spectrum: h(G) *= a G^2 / (G^4 + a G^2 + b), h(0) kept
+template <typename C>
+cudaError_t launch_precond(C *h, int n0, int n1, int n2, const double *bvec, double a, double b, cudaStream_t s);
 
 }  // namespace ofdft

@@ -398,7 +398,46 @@ template <typename T> cudaError_t launch_copy(T *dst, const T *src, long long N,
     return cudaGetLastError();
 }
 
+template <typename T> __global__ void add_scalar_kernel(T *x, const double *c, long long N) {
+    const T v = (T)c[0];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += stride) x[i] += v;
+}
+template <typename T> cudaError_t launch_add_scalar(T *x, const double *c, long long N, cudaStream_t s) {
+    add_scalar_kernel<T><<<1216, 256, 0, s>>>(x, c, N);
+    return cudaGetLastError();
+}
+
+template <typename C>
+__global__ void precond_kernel(C *h, int n0, int n1, int n2, double b0, double b1, double b2, double b3,
+                               double b4, double b5, double b6, double b7, double b8, double pa, double pb) {
+    const int n2h = n2 / 2 + 1;
+    const long long NH = (long long)n0 * n1 * n2h, stride = (long long)gridDim.x * blockDim.x;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < NH; e += stride) {
+        const int k2 = (int)(e % n2h);
+        const long long r = e / n2h;
+        const int k1 = (int)(r % n1), k0 = (int)(r / n1);
+        const double m0 = (k0 <= n0 / 2) ? k0 : k0 - n0, m1 = (k1 <= n1 / 2) ? k1 : k1 - n1, m2 = k2;
+        const double gx = m0 * b0 + m1 * b3 + m2 * b6, gy = m0 * b1 + m1 * b4 + m2 * b7, gz = m0 * b2 + m1 * b5 + m2 * b8;
+        const double q2 = gx * gx + gy * gy + gz * gz;
+        const double f = (q2 > 0.0) ? pa * q2 / (q2 * q2 + pa * q2 + pb) : 1.0;
+        C v = h[e];
+        v.x = (decltype(v.x))(v.x * f);
+        v.y = (decltype(v.y))(v.y * f);
+        h[e] = v;
+    }
+}
+template <typename C>
+cudaError_t launch_precond(C *h, int n0, int n1, int n2, const double *bv, double a, double b, cudaStream_t s) {
+    precond_kernel<C><<<1216, 256, 0, s>>>(h, n0, n1, n2, bv[0], bv[1], bv[2], bv[3], bv[4], bv[5], bv[6], bv[7],
+                                           bv[8], a, b);
+    return cudaGetLastError();
+}
+template cudaError_t launch_precond<float2>(float2 *, int, int, int, const double *, double, double, cudaStream_t);
+template cudaError_t launch_precond<double2>(double2 *, int, int, int, const double *, double, double, cudaStream_t);
+
 #define INST(T)                                                                                              \
+    template cudaError_t launch_add_scalar<T>(T *, const double *, long long, cudaStream_t);                  \
     template cudaError_t launch_dot<T>(const T *, const T *, const T *, long long, double *, int, double *,    \
                                        cudaStream_t);                                                        \
     template cudaError_t launch_axpby<T>(T *, const T *, double, double, long long, cudaStream_t);           \
