@@ -218,6 +218,19 @@ def run_scale(args):
                     "abs_err_Ha_per_atom": abs(Eii / wl["n_atoms"] + 0.895873615195 * z * z / rs),
                     "max_force": float(np.max(np.abs(Fii)))}
     del Fii
+    # ---- E, V and forces through the autograd function (forward + backward) on the perfect crystal
+    rg = rho.clone().requires_grad_(True)
+    pos_t = torch.from_numpy(np.asarray(wl["positions"], dtype=np.float64).copy()).requires_grad_(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    E_ag = ofd.OFDFTEnergy.apply(rg, pos_t, g, f32, (wl["species"], wl["Z"], wl["rc"], order))
+    E_ag.backward()
+    torch.cuda.synchronize()
+    out["autograd"] = {"forward_backward_s": round(time.perf_counter() - t0, 3),
+                       "E_per_atom": float(E_ag.detach()) / wl["n_atoms"],
+                       "grad_rho_vs_V_dV_max": float((rg.grad - V * g.dV).abs().max()),
+                       "grad_R_vs_minus_F_max": float((pos_t.grad.numpy() + F).__abs__().max())}
+    del rg, pos_t
     # ---- timing on the noisy density
     del rho, V
     rho = W.tiled_density_torch(wl1, 64, 0.02, 5, dev, torch.float32)

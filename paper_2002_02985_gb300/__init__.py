@@ -231,13 +231,14 @@ def _autograd():
     class OFDFTEnergy(torch.autograd.Function):
         """E[rho, R] with a hand-written backward: dE/drho_r = V_r dV, dE/dR_I = -F_I.
 
-        The ions' positions are a float64 CPU tensor (n, 3); species/Z/rc are
-        fixed attributes of `grid` set before the call through `spec`."""
+        The ions' positions are a float64 CPU tensor (n, 3); `spec` = (species, Z, rc) or
+        (species, Z, rc, pme_order) describes the ions (pme_order > 0: PME structure factor)."""
 
         @staticmethod
         def forward(ctx, rho, positions, grid, func, spec):
-            species, Z, rc = spec
-            grid.set_ions(positions.detach().cpu().numpy(), species, Z, rc)
+            species, Z, rc = spec[:3]
+            order = spec[3] if len(spec) > 3 else 0
+            grid.set_ions(positions.detach().cpu().numpy(), species, Z, rc, pme_order=order)
             E, V = grid.energy_potential(rho.detach(), func, want_potential=True)
             ctx.grid, ctx.func = grid, func
             ctx.save_for_backward(rho, V)
