@@ -673,6 +673,7 @@ template <typename T> int ensure_force_buffers(ofdft_grid *g) {
         g->generation++;
     }
     if (g->pme_order == 0 && fast && g->gc_len < g->NH) {
+        CK(prepare_force_kernels(), "force kernel attributes");
         cudaFree(g->gc);
         g->gc = nullptr;
         g->gc_len = 0;

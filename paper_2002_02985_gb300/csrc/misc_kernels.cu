@@ -160,7 +160,7 @@ template cudaError_t launch_forces<double2>(const IonArgs &, const double2 *, do
 // Forces, FP32-mixed path.  Per G (once, not per ion): c(G) = -w v_s(|G|) conj(rho_hat)
 // and G itself in FP32.  Then block (chunk, ion group of 8): each thread walks its
 // G values, forms e^{-iG.R_I} from the FP32 phase tables and accumulates
-// G Im[c e^{-iG.R}] in FP32 over 8 consecutive G before adding to FP64.
+// G Im[c e^{-iG.R}] in FP32 over 16 consecutive G before adding to FP64.
 __global__ void __launch_bounds__(256) force_gprep_kernel(IonArgs a, const float2 *rh, float4 *gc, int s) {
     const long long NH = (long long)a.n0 * a.n1 * a.n2h;
     const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -180,14 +180,31 @@ __global__ void __launch_bounds__(256) force_gprep_kernel(IonArgs a, const float
     gc[2 * e + 1] = make_float4(cr, ci, 0.f, 0.f);
 }
 
+// STAGE: the block's 8 ions' phase tables are first copied into shared memory
+// ([8][n0 + n1 + n2h]), so the G loop reads them there instead of from L2.
+template <bool STAGE>
 __global__ void __launch_bounds__(256) forces_fast_kernel(IonArgs a, const float2 *ph32, const float4 *gc, int s,
                                                            double *part, int nchunk) {
-    __shared__ double sd[32];
+    extern __shared__ float2 sph[];
     const int chunk = blockIdx.x, g0 = blockIdx.y * 8;
     const long long NH = (long long)a.n0 * a.n1 * a.n2h;
     const long long per = (NH + nchunk - 1) / nchunk;
     const long long e0 = chunk * per, e1 = (e0 + per < NH) ? e0 + per : NH;
     const float2 *P0 = ph32, *P1 = ph32 + (size_t)a.n_ions * a.n0, *P2 = P1 + (size_t)a.n_ions * a.n1;
+    const int Lt = a.n0 + a.n1 + a.n2h;
+    if (STAGE) {
+        for (int t = threadIdx.x; t < 8 * Lt; t += blockDim.x) {
+            const int q = t / Lt, k = t - q * Lt, I = g0 + q;
+            float2 v = make_float2(0.f, 0.f);
+            if (I < a.n_ions) {
+                if (k < a.n0) v = P0[(size_t)I * a.n0 + k];
+                else if (k < a.n0 + a.n1) v = P1[(size_t)I * a.n1 + (k - a.n0)];
+                else v = P2[(size_t)I * a.n2h + (k - a.n0 - a.n1)];
+            }
+            sph[t] = v;
+        }
+        __syncthreads();
+    }
     double F[8][3];
     float f32[8][3];
 #pragma unroll
@@ -204,8 +221,17 @@ __global__ void __launch_bounds__(256) forces_fast_kernel(IonArgs a, const float
         for (int q = 0; q < 8; q++) {
             const int I = g0 + q;
             if (I >= a.n_ions || a.species[I] != s) continue;
-            const float2 p0 = P0[(size_t)I * a.n0 + k0], p1 = P1[(size_t)I * a.n1 + k1],
-                         p2 = P2[(size_t)I * a.n2h + k2];
+            float2 p0, p1, p2;
+            if (STAGE) {
+                const float2 *row = sph + q * Lt;
+                p0 = row[k0];
+                p1 = row[a.n0 + k1];
+                p2 = row[a.n0 + a.n1 + k2];
+            } else {
+                p0 = P0[(size_t)I * a.n0 + k0];
+                p1 = P1[(size_t)I * a.n1 + k1];
+                p2 = P2[(size_t)I * a.n2h + k2];
+            }
             const float rx = p0.x * p1.x - p0.y * p1.y, ry = p0.x * p1.y + p0.y * p1.x;
             const float px = rx * p2.x - ry * p2.y, py = rx * p2.y + ry * p2.x;
             const float im = c4.x * py + c4.y * px;            // Im(c p)
@@ -213,7 +239,7 @@ __global__ void __launch_bounds__(256) forces_fast_kernel(IonArgs a, const float
             f32[q][1] += im * G.y;
             f32[q][2] += im * G.z;
         }
-        if (++cnt == 8) {
+        if (++cnt == 16) {                               // FP32 over 16 G, then FP64
             cnt = 0;
 #pragma unroll
             for (int q = 0; q < 8; q++)
@@ -221,14 +247,29 @@ __global__ void __launch_bounds__(256) forces_fast_kernel(IonArgs a, const float
                 for (int d = 0; d < 3; d++) F[q][d] += (double)f32[q][d], f32[q][d] = 0.f;
         }
     }
+    // block sums: warp sums in FP32 (32 values each), then the warps in FP64 -- 24 full FP64
+    // block reductions per block had kept the FP64 pipe half busy
+    __shared__ double wsum[24][8];                     // (blocks of 256 threads: 8 warps)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
     for (int q = 0; q < 8; q++)
 #pragma unroll
         for (int d = 0; d < 3; d++) {
-            const double v = block_sum(F[q][d] + (double)f32[q][d], sd);
-            if (threadIdx.x == 0 && g0 + q < a.n_ions)
-                part[(((size_t)(g0 + q)) * nchunk + chunk) * 3 + d] = v;
+            float v = (float)F[q][d] + f32[q][d];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) wsum[q * 3 + d][warp] = (double)v;
         }
+    __syncthreads();
+    if (threadIdx.x < 24) {
+        const int q = threadIdx.x / 3, d = threadIdx.x - 3 * q;
+        double t = 0.0;
+        for (int w = 0; w < nw; w++) t += wsum[threadIdx.x][w];
+        if (g0 + q < a.n_ions) part[(((size_t)(g0 + q)) * nchunk + chunk) * 3 + d] = t;
+    }
+}
+
+cudaError_t prepare_force_kernels() {
+    return cudaFuncSetAttribute(forces_fast_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
 }
 
 cudaError_t launch_forces_fast(const IonArgs &a, const float2 *rhohat, const float2 *ph32, float4 *gc,
@@ -240,7 +281,13 @@ cudaError_t launch_forces_fast(const IonArgs &a, const float2 *rhohat, const flo
         // ions of other species write nothing for this species: their partials come from
         // their own species' pass (the kernel skips them)
         dim3 g(nchunk, (a.n_ions + 7) / 8);
-        forces_fast_kernel<<<g, 256, 0, st>>>(a, ph32, gc, s, partials + (size_t)s * a.n_ions * nchunk * 3, nchunk);
+        const size_t smem = (size_t)8 * (a.n0 + a.n1 + a.n2h) * sizeof(float2);
+        double *ps = partials + (size_t)s * a.n_ions * nchunk * 3;
+        if (smem <= 96 * 1024) {          // (prepare_force_kernels raised the kernel's limit to 96 KB)
+            forces_fast_kernel<true><<<g, 256, smem, st>>>(a, ph32, gc, s, ps, nchunk);
+        } else {
+            forces_fast_kernel<false><<<g, 256, 0, st>>>(a, ph32, gc, s, ps, nchunk);
+        }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return e;
