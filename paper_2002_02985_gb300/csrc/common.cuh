@@ -152,6 +152,29 @@ __device__ __forceinline__ double block_sum(double v, double *scratch) {
     return v;
 }
 
+// K sums at once (same shuffle tree per value as block_sum, one pair of barriers for
+// all): the totals are valid in thread 0.  scratch: 32 K doubles.
+template <int K> __device__ __forceinline__ void block_sum_n(double (&v)[K], double *scratch) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < K; k++) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; k++) scratch[k * 32 + warp] = v[k];
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < K; k++) v[k] = (threadIdx.x < nw) ? scratch[k * 32 + threadIdx.x] : 0.0;
+    if (warp == 0)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int k = 0; k < K; k++) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+}
+
 template <typename T> __device__ __forceinline__ T block_min(T v, T *scratch) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int o = 16; o > 0; o >>= 1) { T w = __shfl_down_sync(0xffffffffu, v, o); v = w < v ? w : v; }

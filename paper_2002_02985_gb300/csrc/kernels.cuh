@@ -180,9 +180,11 @@ __device__ __forceinline__ void knots_from_partials(const EvalArgs<T> &a, double
         mn = x < mn ? x : mn;
         mx = y > mx ? y : mx;
     }
-    s_rho = block_sum(s_rho, sd);
-    s_tf = block_sum(s_tf, sd);
-    s_xc = block_sum(s_xc, sd);
+    double r[3] = {s_rho, s_tf, s_xc};
+    block_sum_n<3>(r, sd);
+    s_rho = r[0];
+    s_tf = r[1];
+    s_xc = r[2];
     mn = block_min(mn, st);
     mx = block_max(mx, st);
     const double fl = (double)a.floor_;
@@ -229,7 +231,7 @@ __device__ __forceinline__ void knots_from_partials(const EvalArgs<T> &a, double
 // ======================================================================= stats (s1 input)
 template <typename T>
 __global__ void __launch_bounds__(256) stats_kernel(EvalArgs<T> a) {
-    __shared__ double sd[32];
+    __shared__ double sd[3 * 32];
     __shared__ T st[32];
     double s_rho = 0.0, s_tf = 0.0, s_xc = 0.0;
     T mn = (T)3.0e38, mx = (T)-3.0e38;
@@ -277,12 +279,10 @@ __global__ void __launch_bounds__(256) stats_kernel(EvalArgs<T> a) {
             s_xc += (double)x4;
         }
     }
-    s_rho = block_sum(s_rho, sd);
-    if (threadIdx.x == 0) a.part_stats[3 * blockIdx.x] = s_rho;
-    s_tf = block_sum(s_tf, sd);
-    if (threadIdx.x == 0) a.part_stats[3 * blockIdx.x + 1] = s_tf;
-    if (xc) s_xc = block_sum(s_xc, sd);
-    if (threadIdx.x == 0) a.part_stats[3 * blockIdx.x + 2] = s_xc;
+    double r[3] = {s_rho, s_tf, s_xc};
+    block_sum_n<3>(r, sd);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 3; k++) a.part_stats[3 * blockIdx.x + k] = r[k];
     mn = block_min(mn, st);
     if (threadIdx.x == 0) a.part_minmax[2 * blockIdx.x] = mn;
     mx = block_max(mx, st);
@@ -471,7 +471,7 @@ template <typename T, class P>
 __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
     typedef typename Vec2<T>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double sd[32];
+    __shared__ double sd[4 * 32];
     __shared__ T cvec[64][3];
     __shared__ T cw[64];
     __shared__ T sk[OFDFT_MAX_KNOTS];
@@ -703,14 +703,10 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
         }
     }
     cp_async_wait<0>();
-    eH = block_sum(eH, sd);
-    if (threadIdx.x == 0) a.part_ax0[4 * blockIdx.x] = eH;
-    eV = block_sum(eV, sd);
-    if (threadIdx.x == 0) a.part_ax0[4 * blockIdx.x + 1] = eV;
-    eP = block_sum(eP, sd);
-    if (threadIdx.x == 0) a.part_ax0[4 * blockIdx.x + 2] = eP;
-    eN = block_sum(eN, sd);
-    if (threadIdx.x == 0) a.part_ax0[4 * blockIdx.x + 3] = eN;
+    double r[4] = {eH, eV, eP, eN};
+    block_sum_n<4>(r, sd);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 4; k++) a.part_ax0[4 * blockIdx.x + k] = r[k];
 }
 
 // ======================================================================= row inverse (C2R along n2) + s4 + V
@@ -1247,7 +1243,7 @@ __device__ __forceinline__ void row_inv2_body(const EvalArgs<T> &a) {
 // the interpolated LWT mode, of the row kernel), summed in a fixed order.
 template <typename T>
 __global__ void __launch_bounds__(1024) finalize_kernel(EvalArgs<T> a) {
-    __shared__ double sd[32];
+    __shared__ double sd[5 * 32];
     double h = 0.0, v = 0.0, p = 0.0, ng = 0.0, nl = 0.0;
     for (int b = threadIdx.x; b < a.nb_ax0; b += blockDim.x) {
         h += a.part_ax0[4 * b];
@@ -1259,12 +1255,14 @@ __global__ void __launch_bounds__(1024) finalize_kernel(EvalArgs<T> a) {
     const bool real_space = a.kernel == 0 && a.nlpot == 1;
     if ((a.terms & 4u) && real_space)
         for (int b = threadIdx.x; b < a.nb_row; b += blockDim.x) nl += a.part_row[b];
-    h = block_sum(h, sd);
-    v = block_sum(v, sd);
-    p = block_sum(p, sd);
-    ng = block_sum(ng, sd);
-    nl = block_sum(nl, sd);
+    double r[5] = {h, v, p, ng, nl};
+    block_sum_n<5>(r, sd);
     if (threadIdx.x != 0) return;
+    h = r[0];
+    v = r[1];
+    p = r[2];
+    ng = r[3];
+    nl = r[4];
     double *E = a.energies;
     E[E_VW] = (a.terms & 2u) ? 0.5 * a.omega * v : 0.0;
     E[E_H] = (a.terms & 8u) ? 2.0 * kPi * a.omega * h : 0.0;
