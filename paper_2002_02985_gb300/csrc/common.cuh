@@ -175,6 +175,35 @@ template <int K> __device__ __forceinline__ void block_sum_n(double (&v)[K], dou
             for (int k = 0; k < K; k++) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
 }
 
+// K sums where the per-thread values need only FP32 within a warp (the FP32-mixed
+// path): warp sums in FP32, the warps' sums in FP64 by thread 0 (GB300 does two FP64
+// operations per clock per SM, so FP64 shuffle trees dominate small kernels).  The
+// totals are valid in thread 0.  scratch: 32 K doubles.
+template <int K> __device__ __forceinline__ void block_sum_n_f32warp(double (&v)[K], double *scratch) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float f[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) f[k] = (float)v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < K; k++) f[k] += __shfl_down_sync(0xffffffffu, f[k], o);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; k++) scratch[k * 32 + warp] = (double)f[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            double t = 0.0;
+            for (int w = 0; w < nw; w++) t += scratch[k * 32 + w];
+            v[k] = t;
+        }
+    }
+}
+
 template <typename T> __device__ __forceinline__ T block_min(T v, T *scratch) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int o = 16; o > 0; o >>= 1) { T w = __shfl_down_sync(0xffffffffu, v, o); v = w < v ? w : v; }

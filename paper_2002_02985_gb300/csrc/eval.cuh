@@ -28,7 +28,8 @@ enum { CONS_ADD = 0, CONS_VW = 1, CONS_T2 = 2, CONS_KNOT = 3, CONS_WT_A = 4, CON
 // scalar slots (double) in the workspace
 enum {
     S_SUM_RHO = 0, S_SUM_TF = 1, S_RHO_MIN = 2, S_RHO_MAX = 3, S_RHO_MEAN = 4, S_BAD = 5,
-    S_KF_WT = 6, S_TIMEOUT = 7, S_NSCAL = 8
+    S_KF_WT = 6, S_TIMEOUT = 7, S_NSCAL = 8,
+    S_FIN = 16                 // [16, 21): the finalize blocks' five sums
 };
 // energy slots: total, TF, vW, NL, H, PP, XC
 enum { E_TOT = 0, E_TF = 1, E_VW = 2, E_NL = 3, E_H = 4, E_PP = 5, E_XC = 6, E_NUM = 7 };

@@ -86,7 +86,7 @@ cudaError_t launch_eval(const EvalArgs<T> &a, const LaunchSet &ks, cudaStream_t 
     if (e) return e;
     mark(K_ROW_INV, 1);
     mark(K_FINALIZE, 0);
-    finalize_kernel<T><<<1, 1024, 0, s>>>(a);
+    finalize_kernel<T><<<5, 256, 0, s>>>(a);
     mark(K_FINALIZE, 1);
     return cudaGetLastError();
 }

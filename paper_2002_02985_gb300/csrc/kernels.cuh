@@ -254,6 +254,8 @@ __global__ void __launch_bounds__(256) stats_kernel(EvalArgs<T> a) {
                 for (int q = 0; q < 4; q++) x[u][q] = (4 * gi + q < a.N) ? a.rho[4 * gi + q] : (T)0;
             }
         }
+        // FP32-mixed: the U groups are summed in FP32 too (one FP64 add per sum per iteration)
+        T r16 = 0, t16 = 0, x16 = 0;
 #pragma unroll
         for (int u = 0; u < U; u++) {
             const long long gi = g0 + u * stride;
@@ -274,13 +276,25 @@ __global__ void __launch_bounds__(256) stats_kernel(EvalArgs<T> a) {
                     mx = xv > mx ? xv : mx;
                 }
             }
-            s_rho += (double)r4;
-            s_tf += (double)t4;
-            s_xc += (double)x4;
+            if (sizeof(T) == 4) {
+                r16 += r4;
+                t16 += t4;
+                x16 += x4;
+            } else {
+                s_rho += (double)r4;
+                s_tf += (double)t4;
+                s_xc += (double)x4;
+            }
+        }
+        if (sizeof(T) == 4) {
+            s_rho += (double)r16;
+            s_tf += (double)t16;
+            s_xc += (double)x16;
         }
     }
     double r[3] = {s_rho, s_tf, s_xc};
-    block_sum_n<3>(r, sd);
+    if constexpr (sizeof(T) == 4) block_sum_n_f32warp<3>(r, sd);
+    else block_sum_n<3>(r, sd);
     if (threadIdx.x == 0)
         for (int k = 0; k < 3; k++) a.part_stats[3 * blockIdx.x + k] = r[k];
     mn = block_min(mn, st);
@@ -1242,27 +1256,32 @@ __device__ __forceinline__ void row_inv2_body(const EvalArgs<T> &a) {
 // FP64 energies from the per-block partials of the reciprocal-space kernel (and, for
 // the interpolated LWT mode, of the row kernel), summed in a fixed order.
 template <typename T>
-__global__ void __launch_bounds__(1024) finalize_kernel(EvalArgs<T> a) {
-    __shared__ double sd[5 * 32];
-    double h = 0.0, v = 0.0, p = 0.0, ng = 0.0, nl = 0.0;
-    for (int b = threadIdx.x; b < a.nb_ax0; b += blockDim.x) {
-        h += a.part_ax0[4 * b];
-        v += a.part_ax0[4 * b + 1];
-        p += a.part_ax0[4 * b + 2];
-        ng += a.part_ax0[4 * b + 3];
-    }
-    // the row partials hold the real-space E_NL of the interpolated LWT mode only
+__global__ void __launch_bounds__(256) finalize_kernel(EvalArgs<T> a) {
+    // block k sums one kind of partial (0..3: the reciprocal-space kernel's E_H, E_vW,
+    // E_PP and G-space E_NL sums; 4: the rows' real-space E_NL), so the FP64 work is
+    // spread over five SMs; the last block to finish assembles the energies
+    __shared__ double sd[32];
+    __shared__ bool last;
+    const int k = blockIdx.x;
     const bool real_space = a.kernel == 0 && a.nlpot == 1;
-    if ((a.terms & 4u) && real_space)
-        for (int b = threadIdx.x; b < a.nb_row; b += blockDim.x) nl += a.part_row[b];
-    double r[5] = {h, v, p, ng, nl};
-    block_sum_n<5>(r, sd);
-    if (threadIdx.x != 0) return;
-    h = r[0];
-    v = r[1];
-    p = r[2];
-    ng = r[3];
-    nl = r[4];
+    double acc = 0.0;
+    if (k < 4) {
+        for (int b = threadIdx.x; b < a.nb_ax0; b += blockDim.x) acc += a.part_ax0[4 * b + k];
+    } else if ((a.terms & 4u) && real_space) {
+        for (int b = threadIdx.x; b < a.nb_row; b += blockDim.x) acc += a.part_row[b];
+    }
+    acc = block_sum(acc, sd);
+    double *sums = a.scal + S_FIN;
+    if (threadIdx.x == 0) {
+        sums[k] = acc;
+        __threadfence();
+        last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    const double h = __ldcg(sums), v = __ldcg(sums + 1), p = __ldcg(sums + 2), ng = __ldcg(sums + 3),
+                 nl = __ldcg(sums + 4);
     double *E = a.energies;
     E[E_VW] = (a.terms & 2u) ? 0.5 * a.omega * v : 0.0;
     E[E_H] = (a.terms & 8u) ? 2.0 * kPi * a.omega * h : 0.0;
@@ -1275,6 +1294,7 @@ __global__ void __launch_bounds__(1024) finalize_kernel(EvalArgs<T> a) {
     // nonlocal: G-space sum (exact LWT, WT) or real-space sum (interpolated LWT)
     E[E_NL] = (a.terms & 4u) ? (real_space ? nl * a.dV : a.omega * ng) : 0.0;
     E[E_TOT] = E[E_TF] + E[E_VW] + E[E_NL] + E[E_H] + E[E_PP] + E[E_XC];
+    *a.ticket = 0u;                                   // ready for the next evaluation
 }
 
 // ======================================================================= kernel wrappers
