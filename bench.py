@@ -49,6 +49,19 @@ def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def job_throughput(points_per_rank, t_ms_local, dist=None, device=None):
+    """Whole-job throughput of independent replicas (one per rank, no data-path
+    collective): the step time is the MAX over ranks (the slowest replica bounds the
+    job) and the value counts the points of all ranks.  Returns (value, t_max_ms)."""
+    t_max, world = t_ms_local, 1
+    if dist is not None:
+        import torch
+        t = torch.tensor([t_ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max, world = float(t), dist.get_world_size()
+    return points_per_rank * world / (t_max * 1e-3), t_max
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -376,12 +389,7 @@ def run_gpu(args):
     prof = g.profile_read()
     t_step = sum(ms32) / len(ms32)
     t_step_instr = sum(ms32p) / len(ms32p)
-    t_max = t_step
-    if dist:
-        t = torch.tensor([t_step], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t)
-    value = N * world / (t_max * 1e-3)
+    value, t_max = job_throughput(N, t_step, dist, dev)
 
     # FP64 path (the speed-up denominator), fewer steps
     V64 = torch.empty_like(rho_d)
