@@ -144,3 +144,22 @@ def optimize_density(g: Grid, psi0, func: Functional, Vext_G, n_electrons: float
         if small >= 3:
             break
     return dict(psi=psi, E=E["total"], energies=E, iterations=it, evals=evals, history=history)
+
+
+def optimize_multistep(grids, psi0, func: Functional, Vext_list, n_electrons: float, n_atoms: int,
+                       tol: float = 1e-6, max_iter: int = 200):
+    """Sec. 2.4's multi-step scheme: psi0 (on the finest grid, grids[-1]) is carried to
+    the coarsest grid, optimised there, and each converged psi is interpolated
+    (oracle.interp) to the next finer grid and optimised again.  Returns the finest
+    level's result dict (with 'levels': the per-level iteration counts)."""
+    from .interp import fourier_interpolate
+    psi = fourier_interpolate(psi0, grids[0].shape)
+    levels = []
+    res = None
+    for li, (g, Vg) in enumerate(zip(grids, Vext_list)):
+        if li > 0:
+            psi = fourier_interpolate(res["psi"], g.shape)
+        res = optimize_density(g, psi, func, Vg, n_electrons, n_atoms, tol=tol, max_iter=max_iter)
+        levels.append(res["iterations"])
+    res["levels"] = levels
+    return res

@@ -51,3 +51,20 @@ def test_orthogonal_update_is_exactly_norm_preserving():
     for lam in (0.01, 0.3, 1.2):
         q = psi * math.cos(lam) + p * math.sin(lam)
         assert abs(np.sum(q * q) * g.dV - 12.0) < 1e-11
+
+
+def test_multistep_reaches_the_single_level_minimum():
+    """Coarse (16^3) then fine (32^3): the fine level ends at the minimum a direct fine
+    optimisation reaches (knots frozen, so both minimise the same functional)."""
+    from oracle.optimize import optimize_multistep
+    wl = W.workload("fcc-al-4/32")
+    rho = W.model_density(wl)
+    gf, gc = Grid(wl["cell"], wl["shape"]), Grid(wl["cell"], (16, 16, 16))
+    Vf = fn.external_potential_G(gf, wl["positions"], wl["species"], wl["Z"], wl["rc"])
+    Vc = fn.external_potential_G(gc, wl["positions"], wl["species"], wl["Z"], wl["rc"])
+    f = Functional(n_knots=wl["n_knots"], knots=fn.make_knots(rho, wl["n_knots"]))
+    direct = optimize_density(gf, np.sqrt(rho), f, Vf, wl["n_electrons"], wl["n_atoms"], tol=1e-10, max_iter=400)
+    multi = optimize_multistep([gc, gf], np.sqrt(rho), f, [Vc, Vf], wl["n_electrons"], wl["n_atoms"],
+                               tol=1e-10, max_iter=400)
+    assert abs(multi["E"] - direct["E"]) / wl["n_atoms"] < 1e-8
+    assert multi["levels"][1] < direct["iterations"]
