@@ -181,6 +181,28 @@ int ofdft_optimize_density(ofdft_grid *g, void *psi_dev, const ofdft_functional 
                            double N_e, double tol_E_per_atom, int max_iter,
                            ofdft_opt_report *rep);
 
+/* Fourier (band-limited) interpolation of a real periodic field between two grids of
+ * one cell, the step that carries a converged density to a finer grid in the paper's
+ * multi-step optimisation (Sec. 2.4).  Frequencies present on both grids are copied;
+ * a Nyquist term of the smaller grid is shared between +-n/2 of the larger (so the
+ * interpolant passes through the coarse samples) or, going down, formed from both.
+ * src_dev: DEVICE [from's N], dst_dev: DEVICE [to's N], both float (OFDFT_FP32_MIXED)
+ * or double (OFDFT_FP64).  Runs on the grids' streams and synchronises `to`'s stream.
+ * Errors: OFDFT_ERR_INVALID_ARG (NULL, different cells, unknown precision), OFDFT_ERR_CUDA. */
+int ofdft_interpolate(ofdft_grid *from, const void *src_dev, ofdft_grid *to, void *dst_dev, int precision);
+
+/* Multi-step density optimisation (Sec. 2.4): grids[0..n_levels-1] share one cell,
+ * coarsest first; psi_dev (DEVICE, on the finest grid, grids[n_levels-1]) holds the
+ * initial psi and receives the result.  The initial psi is interpolated to the coarsest
+ * grid and optimised there (as ofdft_optimize_density, max_iter iterations at most per
+ * level); each level's result is interpolated to the next finer grid and optimised
+ * again.  Each grid needs its ions when f has the PP term.  rep (may be NULL) describes
+ * the finest level; a coarse level that stops at max_iter still seeds the next.
+ * Allocates one psi buffer per coarse level for the duration of the call. */
+int ofdft_optimize_density_multistep(int n_levels, ofdft_grid *const *grids, void *psi_dev,
+                                     const ofdft_functional *f, double N_e, double tol_E_per_atom,
+                                     int max_iter, ofdft_opt_report *rep);
+
 /* Batched evaluation of n independent grids (snapshots), possibly of different
  * shapes: E_out HOST [n][OFDFT_N_ENERGIES]; V_dev[i] and F_out[i] may be NULL (F_out needs ions).
  * All grids must share one stream; the batch is enqueued back to back and

@@ -19,7 +19,8 @@ import numpy as np
 
 from . import _lib as L
 
-__all__ = ["Grid", "Functional", "OFDFTError", "OFDFTEnergy", "energy_potential_batched", "library"]
+__all__ = ["Grid", "Functional", "OFDFTError", "OFDFTEnergy", "energy_potential_batched",
+           "optimize_density_multistep", "library"]
 
 ENERGY_KEYS = ("total", "TF", "vW", "NL", "H", "PP", "XC")
 
@@ -183,6 +184,15 @@ class Grid:
         _check(self.lib, st, self.h)
         return E.value, F
 
+    def interpolate(self, field, to):
+        """Fourier interpolation of `field` (a tensor on this grid) onto the grid `to`
+        (same cell); returns a new tensor of `to`'s shape and the field's dtype."""
+        import torch
+        out = torch.empty(tuple(to.shape), dtype=field.dtype, device=field.device)
+        prec = L.FP64 if field.dtype == torch.float64 else L.FP32_MIXED
+        _check(self.lib, self.lib.ofdft_interpolate(self.h, _ptr(field), to.h, _ptr(out), prec), to.h)
+        return out
+
     def forces(self, rho, precision: int = L.FP32_MIXED):
         F = np.zeros((self.n_ions, 3))
         st = self.lib.ofdft_forces(self.h, _ptr(rho), precision, F.ctypes.data_as(ct.POINTER(ct.c_double)))
@@ -201,6 +211,24 @@ class Grid:
         return dict(converged=(st == 0), iterations=rep.iterations, evaluations=rep.evaluations,
                     energy=rep.energy, energies=dict(zip(ENERGY_KEYS, list(rep.energies))), mu=rep.mu,
                     residual=rep.residual, last_dE=rep.last_dE)
+
+
+def optimize_density_multistep(grids, psi, func: Functional, n_electrons: float, tol_per_atom: float = 1e-6,
+                               max_iter: int = 200):
+    """Sec. 2.4's multi-step optimisation over `grids` (coarsest first, one cell); psi lives
+    on the finest grid and is overwritten with the result.  Returns the finest level's report."""
+    lib = library()
+    rep = L.COptReport()
+    c, keep = func.to_c()
+    hs = (ct.c_void_p * len(grids))(*[g.h for g in grids])
+    st = lib.ofdft_optimize_density_multistep(len(grids), hs, _ptr(psi), ct.byref(c), n_electrons, tol_per_atom,
+                                              max_iter, ct.byref(rep))
+    if st != L.OFDFT_OK and st != -6:
+        _check(lib, st, grids[-1].h)
+    del keep
+    return dict(converged=(st == 0), iterations=rep.iterations, evaluations=rep.evaluations, energy=rep.energy,
+                energies=dict(zip(ENERGY_KEYS, list(rep.energies))), mu=rep.mu, residual=rep.residual,
+                last_dE=rep.last_dE)
 
 
 def energy_potential_batched(grids, rhos, func: Functional, want_potential=True, want_forces=False, V_out=None):

@@ -32,7 +32,8 @@ EXPORTS = (
     "ofdft_energy_potential_async", "ofdft_forces", "ofdft_optimize_density",
     "ofdft_energy_potential_batched", "ofdft_status_string", "ofdft_last_error", "ofdft_version",
     "ofdft_profile_enable", "ofdft_profile_reset", "ofdft_profile_read",
-    "ofdft_tf_energy_potential_noalloc", "ofdft_set_ions_pme", "ofdft_ewald",
+    "ofdft_tf_energy_potential_noalloc", "ofdft_set_ions_pme", "ofdft_ewald", "ofdft_interpolate",
+    "ofdft_optimize_density_multistep",
 )
 NOALLOC_MAX_POINTS = 8388608
 
@@ -78,6 +79,9 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.ofdft_energy_potential_async.argtypes = [P, V, ct.POINTER(CFunctional), V, V]
     lib.ofdft_forces.argtypes = [P, V, I, ct.POINTER(D)]
     lib.ofdft_ewald.argtypes = [P, ct.POINTER(D), ct.POINTER(D)]
+    lib.ofdft_interpolate.argtypes = [P, V, P, V, I]
+    lib.ofdft_optimize_density_multistep.argtypes = [I, ct.POINTER(P), V, ct.POINTER(CFunctional), D, D, I,
+                                                     ct.POINTER(COptReport)]
     lib.ofdft_optimize_density.argtypes = [P, V, ct.POINTER(CFunctional), D, D, I, ct.POINTER(COptReport)]
     lib.ofdft_energy_potential_batched.argtypes = [I, ct.POINTER(P), ct.POINTER(V), ct.POINTER(CFunctional),
                                                    ct.POINTER(D), ct.POINTER(V), ct.POINTER(ct.POINTER(D))]

@@ -893,6 +893,68 @@ int ewald_impl(ofdft_grid *g, double *E_out, double *F_out) {
     return OFDFT_OK;
 }
 
+template <typename T>
+int optimize_impl(ofdft_grid *g, T *psi, const ofdft_functional *f0, double Ne, double tol, int max_iter,
+                  ofdft_opt_report *rep);
+
+// ---------------------------------------------------------------- Fourier interpolation between grids
+bool same_cell(const ofdft_grid *a, const ofdft_grid *b) {
+    for (int i = 0; i < 9; i++)
+        if (std::fabs(a->cell[i] - b->cell[i]) > 1e-12 * (1.0 + std::fabs(a->cell[i]))) return false;
+    return true;
+}
+
+template <typename T> int interpolate_impl(ofdft_grid *from, const T *src, ofdft_grid *to, T *dst) {
+    typedef typename Vec2<T>::type C;
+    ofdft_grid *g = to;                 // errors are reported on the target grid
+    int rc = ensure_ws<T>(from, 3);
+    if (rc) return rc;
+    if ((rc = ensure_ws<T>(to, 3))) return rc;
+    Workspace<T> &wf = ws<T>(from), &wt = ws<T>(to);
+    if ((rc = forward_plain<T>(from, wf, src))) return rc;     // normalised spectrum, mean in the scalars
+    if (from->stream != to->stream) {
+        cudaEvent_t ev;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
+        cudaEventRecord(ev, from->stream);
+        cudaStreamWaitEvent(to->stream, ev, 0);
+        cudaEventDestroy(ev);
+    }
+    CK(launch_spectral_map<C>((const C *)wf.chan, from->n[0], from->n[1], from->n[2], (C *)wt.chan, to->n[0],
+                              to->n[1], to->n[2], to->stream),
+       "spectral map");
+    if ((rc = inverse_plain<T>(to, wt, 0, dst, dst))) return rc;
+    CK(launch_add_scalar<T>(dst, wf.scal + S_RHO_MEAN, to->N, to->stream), "mean");
+    return OFDFT_OK;
+}
+
+template <typename T>
+int multistep_impl(int nlev, ofdft_grid *const *grids, T *psi, const ofdft_functional *f, double Ne, double tol,
+                   int max_iter, ofdft_opt_report *rep) {
+    ofdft_grid *fine = grids[nlev - 1], *g = fine;
+    std::vector<T *> lev(nlev, nullptr);
+    lev[nlev - 1] = psi;
+    int rc = OFDFT_OK;
+    for (int L = 0; L < nlev - 1 && rc == OFDFT_OK; L++) {
+        cudaError_t e = cudaMalloc(&lev[L], (size_t)grids[L]->N * sizeof(T));
+        if (e != cudaSuccess) rc = fail(fine, OFDFT_ERR_OOM, "cudaMalloc multi-step level", e);
+    }
+    // the initial psi goes straight to the coarsest grid; each converged psi goes one level up
+    if (rc == OFDFT_OK) rc = interpolate_impl<T>(fine, psi, grids[0], lev[0]);
+    ofdft_opt_report r;
+    for (int L = 0; L < nlev && rc == OFDFT_OK; L++) {
+        if (L > 0) {
+            if ((rc = interpolate_impl<T>(grids[L - 1], lev[L - 1], grids[L], lev[L]))) break;
+            CK(cudaStreamSynchronize(grids[L - 1]->stream), "stream synchronize");
+        }
+        rc = optimize_impl<T>(grids[L], lev[L], f, Ne, tol, max_iter, L == nlev - 1 ? rep : &r);
+        if (rc == OFDFT_ERR_NOT_CONVERGED && L < nlev - 1) rc = OFDFT_OK;   // a coarse level only seeds the next
+        if (rc && L < nlev - 1 && grids[L] != fine) fine->err = grids[L]->err;
+    }
+    cudaStreamSynchronize(fine->stream);
+    for (int L = 0; L < nlev - 1; L++) cudaFree(lev[L]);
+    return rc;
+}
+
 // ---------------------------------------------------------------- optimiser
 template <typename T> struct Dev {
     ofdft_grid *g;
@@ -1544,6 +1606,40 @@ int ofdft_ewald(ofdft_grid *g, double *E_out, double *F_out) {
     if (!E_out && !F_out) return fail(g, OFDFT_ERR_INVALID_ARG, "E_out and F_out are both NULL");
     if (!g->have_ions) return fail(g, OFDFT_ERR_NO_IONS, "the Ewald sum needs ions");
     return ewald_impl(g, E_out, F_out);
+}
+
+int ofdft_interpolate(ofdft_grid *from, const void *src_dev, ofdft_grid *to, void *dst_dev, int precision) {
+    if (!from || !to) return OFDFT_ERR_INVALID_ARG;
+    if (!src_dev || !dst_dev) return fail(to, OFDFT_ERR_INVALID_ARG, "src or dst is NULL");
+    if (!same_cell(from, to)) return fail(to, OFDFT_ERR_INVALID_ARG, "the two grids must share one cell");
+    int rc;
+    if (precision == OFDFT_FP64) rc = interpolate_impl<double>(from, (const double *)src_dev, to, (double *)dst_dev);
+    else if (precision == OFDFT_FP32_MIXED) rc = interpolate_impl<float>(from, (const float *)src_dev, to, (float *)dst_dev);
+    else return fail(to, OFDFT_ERR_INVALID_ARG, "unknown precision");
+    if (rc) return rc;
+    ofdft_grid *g = to;
+    CK(cudaStreamSynchronize(to->stream), "stream synchronize");
+    return OFDFT_OK;
+}
+
+int ofdft_optimize_density_multistep(int n_levels, ofdft_grid *const *grids, void *psi_dev, const ofdft_functional *f,
+                                     double N_e, double tol_E_per_atom, int max_iter, ofdft_opt_report *rep) {
+    if (n_levels < 1 || !grids) return OFDFT_ERR_INVALID_ARG;
+    ofdft_grid *fine = grids[n_levels - 1];
+    for (int L = 0; L < n_levels; L++)
+        if (!grids[L]) return OFDFT_ERR_INVALID_ARG;
+    if (!psi_dev || !(N_e > 0.0) || max_iter < 1 || !f) return fail(fine, OFDFT_ERR_INVALID_ARG, "psi, f, N_e or max_iter");
+    for (int L = 0; L < n_levels; L++) {
+        if (!same_cell(grids[L], fine)) return fail(fine, OFDFT_ERR_INVALID_ARG, "all levels must share one cell");
+        int rc = check_functional(grids[L], f);
+        if (rc) {
+            fine->err = grids[L]->err;
+            return rc;
+        }
+    }
+    if (f->precision == OFDFT_FP64)
+        return multistep_impl<double>(n_levels, grids, (double *)psi_dev, f, N_e, tol_E_per_atom, max_iter, rep);
+    return multistep_impl<float>(n_levels, grids, (float *)psi_dev, f, N_e, tol_E_per_atom, max_iter, rep);
 }
 
 int ofdft_optimize_density(ofdft_grid *g, void *psi_dev, const ofdft_functional *f, double N_e,

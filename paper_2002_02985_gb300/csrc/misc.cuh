@@ -63,6 +63,12 @@ template <typename T>
 cudaError_t launch_square(T *rho, T *psi, double scale, long long N, cudaStream_t s);
 // d = -g + beta d ; dot partial <d, g> computed by launch_dot afterwards
 template <typename T> cudaError_t launch_copy(T *dst, const T *src, long long N, cudaStream_t s);
+// Fourier interpolation between two grids of one cell on normalised half spectra (layouts
+// [k0][k1][k2], k2 <= n2/2): frequencies present on both grids are copied; a Nyquist term
+// of the smaller grid is shared between +-n/2 of the larger (up) or made of both (down).
+template <typename C>
+cudaError_t launch_spectral_map(const C *src, int f0, int f1, int f2, C *dst, int t0, int t1, int t2,
+                                cudaStream_t s);
 // x += c[0] (c a device scalar)
 template <typename T> cudaError_t launch_add_scalar(T *x, const double *c, long long N, cudaStream_t s);
 // optimiser preconditioner on a normalised half spectrum: h(G) *= a G^2 / (G^4 + a G^2 + b), h(0) kept

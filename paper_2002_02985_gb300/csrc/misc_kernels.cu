@@ -445,6 +445,92 @@ template <typename T> cudaError_t launch_copy(T *dst, const T *src, long long N,
     return cudaGetLastError();
 }
 
+// sources of to-index j along one full axis: up to two (index, weight)
+__device__ __forceinline__ int axis_sources(int j, int nf, int nt, int *src, double *w) {
+    const int m = (j <= nt / 2) ? j : j - nt;                // signed frequency on the target grid
+    const int small = nf < nt ? nf : nt;
+    const int am = m < 0 ? -m : m;
+    if (2 * am < small) {
+        src[0] = ((m % nf) + nf) % nf;
+        w[0] = 1.0;
+        return 1;
+    }
+    if (small % 2 == 0 && 2 * am == small) {
+        if (nt > nf) {                                         // +-nf/2 on the target: half the Nyquist each
+            src[0] = nf / 2;
+            w[0] = 0.5;
+            return 1;
+        }
+        if (nt < nf) {                                         // target Nyquist (m = +nt/2): both signs
+            if (m < 0) return 0;
+            src[0] = nt / 2;
+            src[1] = nf - nt / 2;
+            w[0] = w[1] = 1.0;
+            return 2;
+        }
+        src[0] = j;
+        w[0] = 1.0;
+        return 1;
+    }
+    return 0;
+}
+
+template <typename C>
+__global__ void spectral_map_kernel(const C *src, int f0, int f1, int f2, C *dst, int t0, int t1, int t2) {
+    const int fh = f2 / 2 + 1, th = t2 / 2 + 1;
+    const long long NT = (long long)t0 * t1 * th, stride = (long long)gridDim.x * blockDim.x;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < NT; e += stride) {
+        const int j2 = (int)(e % th);
+        const long long r = e / th;
+        const int j1 = (int)(r % t1), j0 = (int)(r / t1);
+        int s0[2], s1[2];
+        double w0[2], w1[2];
+        const int n0 = axis_sources(j0, f0, t0, s0, w0), n1 = axis_sources(j1, f1, t1, s1, w1);
+        // last axis (half spectrum, m2 = j2 >= 0): sources (index, weight, conjugate-partner?)
+        const int small2 = f2 < t2 ? f2 : t2;
+        int n2 = 0, i2[2] = {0, 0}, cj[2] = {0, 0};
+        double w2[2] = {0.0, 0.0};
+        if (2 * j2 < small2) {
+            i2[0] = j2; w2[0] = 1.0; n2 = 1;
+        } else if (small2 % 2 == 0 && 2 * j2 == small2) {
+            if (t2 > f2) { i2[0] = j2; w2[0] = 0.5; n2 = 1; }
+            else if (t2 < f2) { i2[0] = j2; w2[0] = 1.0; i2[1] = j2; w2[1] = 1.0; cj[1] = 1; n2 = 2; }
+            else { i2[0] = j2; w2[0] = 1.0; n2 = 1; }
+        }
+        double ax = 0.0, ay = 0.0;
+        for (int a = 0; a < n0; a++)
+            for (int b = 0; b < n1; b++)
+                for (int c = 0; c < n2; c++) {
+                    const double w = w0[a] * w1[b] * w2[c];
+                    if (!cj[c]) {
+                        const C v = src[((long long)s0[a] * f1 + s1[b]) * fh + i2[c]];
+                        ax += w * v.x;
+                        ay += w * v.y;
+                    } else {                                   // coefficient at -m2: conj of (-m0, -m1, +m2)
+                        const int q0 = (f0 - s0[a]) % f0, q1 = (f1 - s1[b]) % f1;
+                        const C v = src[((long long)q0 * f1 + q1) * fh + i2[c]];
+                        ax += w * v.x;
+                        ay -= w * v.y;
+                    }
+                }
+        C out;
+        out.x = (decltype(out.x))(e == 0 ? 0.0 : ax);          // the mean is added back after the inverse
+        out.y = (decltype(out.y))(e == 0 ? 0.0 : ay);
+        dst[e] = out;
+    }
+}
+
+template <typename C>
+cudaError_t launch_spectral_map(const C *src, int f0, int f1, int f2, C *dst, int t0, int t1, int t2,
+                                cudaStream_t s) {
+    spectral_map_kernel<C><<<1216, 256, 0, s>>>(src, f0, f1, f2, dst, t0, t1, t2);
+    return cudaGetLastError();
+}
+template cudaError_t launch_spectral_map<float2>(const float2 *, int, int, int, float2 *, int, int, int,
+                                                 cudaStream_t);
+template cudaError_t launch_spectral_map<double2>(const double2 *, int, int, int, double2 *, int, int, int,
+                                                  cudaStream_t);
+
 template <typename T> __global__ void add_scalar_kernel(T *x, const double *c, long long N) {
     const T v = (T)c[0];
     const long long stride = (long long)gridDim.x * blockDim.x;
