@@ -565,10 +565,18 @@ def algorithmic_bytes(kernel, wl, esize):
     return int(table.get(kernel, 0))
 
 
+# the files the E+V evaluation kernels (stats, rows, pencils, reciprocal space,
+# finalize) and their launches are compiled from
+EVAL_KERNEL_SOURCES = ("common.cuh", "fft.cuh", "eval.cuh", "kernels.cuh", "inst.cuh",
+                       "inst_a.cu", "inst_b.cu", "inst_c.cu", "inst_d.cu", "eval_kernels.cu")
+
+
 def kernel_source_sha():
+    """Hash of the evaluation kernels' sources: an ncu summary stamped with another
+    hash describes different code."""
     import hashlib
     d = os.path.join(ROOT, "paper_2002_02985_gb300", "csrc")
-    names = sorted(f for f in os.listdir(d) if f.endswith(".cu")) + sorted(f for f in os.listdir(d) if f.endswith(".cuh"))
+    names = EVAL_KERNEL_SOURCES
     h = hashlib.sha256()
     for f in names:
         h.update(open(os.path.join(d, f), "rb").read())
