@@ -5,12 +5,26 @@ Sec. 2.4: minimise E[psi^2] subject to int psi^2 = N_e (Eq. euler2), repeating
 psi_{k+1} = psi_k cos(lambda_k) + p_k sin(lambda_k) with p_k orthogonal to
 psi_k and normalised to N_e, which conserves the charge exactly.
 
-Readings (the paper leaves them to SciPy): Polak-Ribiere+ conjugate
-gradient, restarted on loss of descent; a strong-Wolfe line search on lambda
-(c1 = 1e-4, c2 = 0.2, at most 10 evaluations per search, cubic
-interpolation); the spline knots are recomputed at the start of every
-iteration and frozen inside its line search; convergence when
-|E_k - E_{k-1}| < tol * n_atoms for 3 consecutive iterations.
+Step (1) offers the three direction methods the paper names (Sec. 2.4):
+nonlinear conjugate gradient, truncated Newton (TN) and limited-memory BFGS.
+
+Readings (the paper leaves them to SciPy and to its references):
+- CG: Polak-Ribiere+, restarted on loss of descent and every 50 iterations.
+- TN: the Newton equation H x = -g is solved approximately by an inner CG
+  (Newton-CG with a forcing term min(0.5, sqrt|g|) |g|, stopped at the first
+  direction of non-positive curvature), in the tangent space of the sphere
+  int psi^2 = N_e; H is the Hessian of the Lagrangian E - mu (int psi^2 - N_e),
+  applied by central finite differences of the gradient 2 psi V[psi^2] dV.
+- L-BFGS: two-loop recursion over the last m pairs (s, y) of steps in psi and
+  changes of the projected gradient, initial inverse Hessian (s.y / y.y) I;
+  a pair with s.y <= 0 is not stored; the memory is cleared on a failed search.
+- Step (2): a strong-Wolfe line search on lambda (c1 = 1e-4, c2 = 0.2, at most
+  10 evaluations per search, cubic interpolation).  CG starts from the last
+  accepted lambda; TN and L-BFGS from the length of their step,
+  lambda = atan(|x_perp| / |psi|), which the rotation maps psi + x_perp onto.
+- The spline knots are recomputed at the start of every iteration and frozen
+  inside its line search; convergence when |E_k - E_{k-1}| < tol * n_atoms for
+  3 consecutive iterations.
 Parity unpinned for the trajectory: only the converged energy is compared.
 """
 from __future__ import annotations
@@ -38,10 +52,32 @@ def _cubic_min(a, fa, da, b, fb, db):
     return b - (b - a) * (db + d2 - d1) / den
 
 
+def hessian_vector(g: Grid, psi, x, func: Functional, Vext_G, mu: float, h: float = 1e-4):
+    """Hessian of the Lagrangian E[psi^2] - mu (int psi^2 - N_e) applied to x, by
+    central differences of the gradient dE/dpsi = 2 psi V[psi^2] dV:
+
+        H x = (grad(psi + e x) - grad(psi - e x)) / (2 e) - 2 mu dV x,
+        e = h |psi| / |x|.
+
+    Returns (H x, number of evaluations used)."""
+    e = h * math.sqrt(np.sum(psi * psi) / np.sum(x * x))
+    gp = 2.0 * (psi + e * x) * evaluate(g, (psi + e * x) ** 2, func, Vext_G)[1] * g.dV
+    gm = 2.0 * (psi - e * x) * evaluate(g, (psi - e * x) ** 2, func, Vext_G)[1] * g.dV
+    return (gp - gm) / (2.0 * e) - 2.0 * mu * g.dV * x, 2
+
+
+def _tangent(v, psi):
+    """Component of v orthogonal to psi."""
+    return v - (np.sum(v * psi) / np.sum(psi * psi)) * psi
+
+
 def optimize_density(g: Grid, psi0, func: Functional, Vext_G, n_electrons: float, n_atoms: int,
                      tol: float = 1e-6, max_iter: int = 200, c1: float = 1e-4, c2: float = 0.2,
-                     max_ls: int = 10, fixed_iter: int | None = None):
-    """Returns dict(psi, E, energies, iterations, evals, history)."""
+                     max_ls: int = 10, fixed_iter: int | None = None, method: str = "cg",
+                     max_inner: int = 20, lbfgs_m: int = 5):
+    """method: 'cg' | 'tn' | 'lbfgs'.  Returns dict(psi, E, energies, iterations, evals, history)."""
+    if method not in ("cg", "tn", "lbfgs"):
+        raise ValueError("unknown method %r" % method)
     psi = np.asarray(psi0, dtype=np.float64).copy()
     psi *= math.sqrt(n_electrons / (np.sum(psi * psi) * g.dV))
     evals = 0
@@ -62,6 +98,8 @@ def optimize_density(g: Grid, psi0, func: Functional, Vext_G, n_electrons: float
     history = [E["total"]]
     d_prev = None
     g_prev = None
+    pairs = []                    # L-BFGS memory: (s, y, 1 / s.y)
+    psi_prev = None
     lam_prev = 0.05
     small = 0
     it = 0
@@ -70,20 +108,69 @@ def optimize_density(g: Grid, psi0, func: Functional, Vext_G, n_electrons: float
         dEdpsi = 2.0 * psi * V * g.dV
         mu = np.sum(psi * dEdpsi) / (2.0 * n_electrons)
         grad = dEdpsi - 2.0 * mu * psi * g.dV
-        if d_prev is None or it % 50 == 1:
-            d = -grad
-        else:
-            beta = max(0.0, float(np.sum(grad * (grad - g_prev)) / np.sum(g_prev * g_prev)))
-            d = -grad + beta * d_prev
-            if np.sum(d * grad) >= 0.0:
+        if method == "cg":
+            if d_prev is None or it % 50 == 1:
                 d = -grad
-        g_prev, d_prev = grad, d
+            else:
+                beta = max(0.0, float(np.sum(grad * (grad - g_prev)) / np.sum(g_prev * g_prev)))
+                d = -grad + beta * d_prev
+                if np.sum(d * grad) >= 0.0:
+                    d = -grad
+        elif method == "tn":
+            # inner CG on H x = -grad (tangent space), forcing term eta |grad|
+            gn = math.sqrt(np.sum(grad * grad))
+            stop = min(0.5, math.sqrt(gn)) * gn
+            x = np.zeros_like(psi)
+            r = grad.copy()
+            q = -r
+            for j in range(max_inner):
+                Hq, ne = hessian_vector(g, psi, q, f_it, Vext_G, mu)
+                evals += ne
+                Hq = _tangent(Hq, psi)
+                curv = float(np.sum(q * Hq))
+                if curv <= 0.0:
+                    if j == 0:
+                        x = -grad
+                    break
+                a = float(np.sum(r * r)) / curv
+                x = x + a * q
+                r_new = r + a * Hq
+                if math.sqrt(np.sum(r_new * r_new)) < stop:
+                    break
+                q = -r_new + (np.sum(r_new * r_new) / np.sum(r * r)) * q
+                r = r_new
+            d = x if np.sum(x * grad) < 0.0 else -grad
+        else:
+            # L-BFGS two-loop recursion
+            if psi_prev is not None:
+                s_k, y_k = psi - psi_prev, grad - g_prev
+                sy = float(np.sum(s_k * y_k))
+                if sy > 0.0:
+                    pairs.append((s_k, y_k, 1.0 / sy))
+                    if len(pairs) > lbfgs_m:
+                        pairs.pop(0)
+            q = grad.copy()
+            alphas = []
+            for s_k, y_k, rh in reversed(pairs):
+                a = rh * float(np.sum(s_k * q))
+                alphas.append(a)
+                q = q - a * y_k
+            if pairs:
+                s_k, y_k, _ = pairs[-1]
+                q = q * (float(np.sum(s_k * y_k)) / float(np.sum(y_k * y_k)))
+            for (s_k, y_k, rh), a in zip(pairs, reversed(alphas)):
+                b = rh * float(np.sum(y_k * q))
+                q = q + (a - b) * s_k
+            d = -q if np.sum(q * grad) > 0.0 else -grad
+        g_prev, d_prev, psi_prev = grad, d, psi
         p = d - (np.sum(d * psi) / np.sum(psi * psi)) * psi
+        p_len = math.sqrt(np.sum(p * p) * g.dV / n_electrons)     # |p_perp| / |psi|
         p *= math.sqrt(n_electrons / (np.sum(p * p) * g.dV))
         phi0 = E["total"]
         dphi0 = float(np.sum(dEdpsi * p))
         if dphi0 >= 0.0:
             d_prev = None
+            pairs = []
             continue
 
         def phi(lam):
@@ -94,7 +181,7 @@ def optimize_density(g: Grid, psi0, func: Functional, Vext_G, n_electrons: float
 
         # strong-Wolfe search (bracketing + zoom with cubic interpolation)
         lam_lo, f_lo, d_lo = 0.0, phi0, dphi0
-        lam = min(max(lam_prev, 1e-4), 0.5)
+        lam = min(max(lam_prev if method == "cg" else math.atan(p_len), 1e-4), 0.5)
         best = None
         n_ls = 0
         lam_hi = None
@@ -124,6 +211,8 @@ def optimize_density(g: Grid, psi0, func: Functional, Vext_G, n_electrons: float
         fl, lam, E_new, V_new, psi_new = best
         if fl >= phi0:
             d_prev = None            # no decrease: restart with steepest descent
+            pairs = []
+            psi_prev = None
             if fixed_iter is None and small >= 3:
                 break
             small += 1

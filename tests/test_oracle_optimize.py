@@ -68,3 +68,126 @@ def test_multistep_reaches_the_single_level_minimum():
                                tol=1e-10, max_iter=400)
     assert abs(multi["E"] - direct["E"]) / wl["n_atoms"] < 1e-8
     assert multi["levels"][1] < direct["iterations"]
+
+
+# --------------------------------------------------------------------------- TN / L-BFGS
+def _schroedinger_case(n=10):
+    """vW + local PP only: E[psi^2] = dV psi^T (K/2 + diag v) psi with K the spectral
+    -Laplacian, a quadratic form.  Under int psi^2 = N_e its minimum is N_e times the
+    lowest eigenvalue of H = K/2 + diag v (the one-orbital Schroedinger ground state,
+    Sec. 2.4's psi = sqrt(rho) picture), found here by dense diagonalisation."""
+    cell, pos = W.fcc_positions(1)
+    g = Grid(cell, (n, n, n))
+    Vg = fn.external_potential_G(g, pos, np.zeros(4, int), [3.0], [0.9])
+    v = g.ifft(Vg).reshape(-1)
+    N = g.N
+    K = np.empty((N, N))
+    e = np.zeros(N)
+    for j in range(N):               # columns of the spectral -Laplacian (cubic cell: symmetric)
+        e[j] = 1.0
+        K[:, j] = g.ifft(g.G2 * g.fft(e.reshape(g.shape))).reshape(-1)
+        e[j] = 0.0
+    H = 0.5 * K + np.diag(v)
+    return g, Vg, H
+
+
+def test_dense_hamiltonian_is_symmetric_with_a_nodeless_ground_state():
+    g, _, H = _schroedinger_case(8)
+    assert np.max(np.abs(H - H.T)) < 1e-10 * np.max(np.abs(H))
+    w, U = np.linalg.eigh(H)
+    u0 = U[:, 0] * np.sign(U[0, 0])
+    assert np.all(u0 > 0.0)          # ground state of a local Hamiltonian has no node
+    assert w[1] - w[0] > 1e-3        # and is non-degenerate here
+
+
+def test_hessian_vector_equals_dense_lagrangian_hessian():
+    """For the quadratic vW + PP functional the Lagrangian Hessian is exactly
+    2 dV (H - mu); the finite-difference product must reproduce it."""
+    from oracle.optimize import hessian_vector
+    g, Vg, H = _schroedinger_case(8)
+    rng = np.random.default_rng(3)
+    psi = 1.0 + 0.2 * rng.random(g.shape)
+    x = rng.standard_normal(g.shape)
+    f = Functional(terms=("VW", "PP"))
+    mu = 0.37
+    Hx, _ = hessian_vector(g, psi, x, f, Vg, mu)
+    ref = 2.0 * g.dV * (H @ x.reshape(-1) - mu * x.reshape(-1))
+    assert np.max(np.abs(Hx.reshape(-1) - ref)) < 1e-7 * np.max(np.abs(ref))
+
+
+def test_hessian_vector_matches_second_differences_of_the_energy():
+    """TF + vW + Hartree + PP (nonlinear in psi): x.Hx from differences of the gradient
+    equals d^2/dt^2 of the Lagrangian E[(psi + t x)^2] - mu int (psi + t x)^2 from
+    differences of the ENERGY alone, and the product is symmetric (y.Hx = x.Hy).
+    (The LWT term is left out: its linear spline in k_F has kinks wherever k_F crosses
+    a knot, so its second derivative along a line is not a smooth function of t.)"""
+    from oracle.optimize import hessian_vector
+    g, rho, Vg = _small_al()
+    f = Functional(terms=("TF", "VW", "HARTREE", "PP"))
+    psi = np.sqrt(rho)
+    rng = np.random.default_rng(11)
+    x = psi * rng.standard_normal(g.shape) * 0.3
+    y = psi * rng.standard_normal(g.shape) * 0.3
+    mu = 0.21
+    Hx, _ = hessian_vector(g, psi, x, f, Vg, mu)
+    Hy, _ = hessian_vector(g, psi, y, f, Vg, mu)
+    h = 1e-3
+
+    def L(t):
+        q = psi + t * x
+        return evaluate(g, q * q, f, Vg)[0]["total"] - mu * np.sum(q * q) * g.dV
+
+    d2 = (-L(2 * h) + 16 * L(h) - 30 * L(0.0) + 16 * L(-h) - L(-2 * h)) / (12 * h * h)
+    xHx = float(np.sum(x * Hx))
+    assert abs(xHx - d2) < 1e-7 * abs(d2)
+    assert abs(float(np.sum(y * Hx)) - float(np.sum(x * Hy))) < 1e-6 * abs(xHx)
+
+
+def test_every_method_reaches_the_schroedinger_ground_state():
+    g, Vg, H = _schroedinger_case(10)
+    E0 = 4.0 * np.linalg.eigvalsh(H)[0]
+    rng = np.random.default_rng(2)
+    psi0 = 1.0 + 0.3 * rng.random(g.shape)
+    f = Functional(terms=("VW", "PP"))
+    for method in ("cg", "tn", "lbfgs"):
+        res = optimize_density(g, psi0, f, Vg, 4.0, 4, tol=1e-13, max_iter=500, method=method)
+        assert abs(res["E"] - E0) < 1e-9 * abs(E0), (method, res["E"], E0, res["iterations"])
+
+
+def _residual(g, psi, f, Vg, ne):
+    E, V = evaluate(g, psi * psi, f, Vg)
+    mu = np.sum(psi * psi * V) * g.dV / ne
+    return math.sqrt(np.sum(((V - mu) * psi) ** 2) * g.dV)
+
+
+def test_tn_and_lbfgs_reach_the_cg_minimum_in_fewer_iterations():
+    """TF + vW + Hartree + PP: a convex problem in rho, one minimum for all three
+    methods; Newton-CG's curvature information shows as far fewer outer iterations."""
+    g, rho, Vg = _small_al()
+    f = Functional(terms=("TF", "VW", "HARTREE", "PP"))
+    out = {m: optimize_density(g, np.sqrt(rho), f, Vg, 12.0, 4, tol=1e-11, max_iter=400, method=m)
+           for m in ("cg", "tn", "lbfgs")}
+    for m in ("tn", "lbfgs"):
+        assert abs(out[m]["E"] - out["cg"]["E"]) / 4 < 1e-10, (m, out[m]["E"], out["cg"]["E"])
+        assert _residual(g, out[m]["psi"], f, Vg, 12.0) < 1e-4
+    assert out["tn"]["iterations"] < out["cg"]["iterations"] / 2
+    assert out["lbfgs"]["iterations"] <= out["cg"]["iterations"]
+
+
+def test_methods_end_at_stationary_points_of_the_lwt_functional():
+    """With the LWT term (knots frozen) the functional is not convex: its linear spline
+    in k_F has kinks, and on this small noisy cell CG and TN settle in two different
+    local minima 3e-5 Ha apart, each stable when the other method is restarted from
+    it.  What holds for every method: a stationary point (small Euler-Lagrange
+    residual), at an energy far below the start and within 1e-5 Ha/atom of the others."""
+    g, rho, Vg = _small_al()
+    f = Functional(n_knots=6, knots=fn.make_knots(rho, 6))
+    E0 = evaluate(g, rho, f, Vg)[0]["total"]
+    Es = []
+    for m in ("cg", "tn", "lbfgs"):
+        r = optimize_density(g, np.sqrt(rho), f, Vg, 12.0, 4, tol=1e-11, max_iter=400, method=m)
+        assert _residual(g, r["psi"], f, Vg, 12.0) < 3e-5, m
+        assert abs(np.sum(r["psi"] ** 2) * g.dV - 12.0) < 1e-10
+        Es.append(r["E"])
+    assert max(Es) < E0 - 1e-2
+    assert (max(Es) - min(Es)) / 4 < 1e-5
