@@ -11,7 +11,8 @@ nonlinear conjugate gradient, truncated Newton (TN) and limited-memory BFGS.
 Readings (the paper leaves them to SciPy and to its references):
 - CG: Polak-Ribiere+, restarted on loss of descent and every 50 iterations.
 - TN: the Newton equation H x = -g is solved approximately by an inner CG
-  (Newton-CG with a forcing term min(0.5, sqrt|g|) |g|, stopped at the first
+  (Newton-CG, stopped when |r| < min(0.5, sqrt(res)) |g| with res the RMS
+  Euler-Lagrange residual per electron, |g| / (2 sqrt(dV N_e)), or at the first
   direction of non-positive curvature), in the tangent space of the sphere
   int psi^2 = N_e; H is the Hessian of the Lagrangian E - mu (int psi^2 - N_e),
   applied by central finite differences of the gradient 2 psi V[psi^2] dV.
@@ -19,9 +20,10 @@ Readings (the paper leaves them to SciPy and to its references):
   changes of the projected gradient, initial inverse Hessian (s.y / y.y) I;
   a pair with s.y <= 0 is not stored; the memory is cleared on a failed search.
 - Step (2): a strong-Wolfe line search on lambda (c1 = 1e-4, c2 = 0.2, at most
-  10 evaluations per search, cubic interpolation).  CG starts from the last
-  accepted lambda; TN and L-BFGS from the length of their step,
-  lambda = atan(|x_perp| / |psi|), which the rotation maps psi + x_perp onto.
+  10 evaluations per search, cubic interpolation).  A TN or L-BFGS direction
+  built from curvature starts from the length of its step,
+  lambda = atan(|x_perp| / |psi|), which the rotation maps psi + x_perp onto;
+  CG and steepest-descent fallbacks from the last accepted lambda.
 - The spline knots are recomputed at the start of every iteration and frozen
   inside its line search; convergence when |E_k - E_{k-1}| < tol * n_atoms for
   3 consecutive iterations.
@@ -108,6 +110,7 @@ def optimize_density(g: Grid, psi0, func: Functional, Vext_G, n_electrons: float
         dEdpsi = 2.0 * psi * V * g.dV
         mu = np.sum(psi * dEdpsi) / (2.0 * n_electrons)
         grad = dEdpsi - 2.0 * mu * psi * g.dV
+        newton = False                # direction built from curvature information
         if method == "cg":
             if d_prev is None or it % 50 == 1:
                 d = -grad
@@ -119,7 +122,7 @@ def optimize_density(g: Grid, psi0, func: Functional, Vext_G, n_electrons: float
         elif method == "tn":
             # inner CG on H x = -grad (tangent space), forcing term eta |grad|
             gn = math.sqrt(np.sum(grad * grad))
-            stop = min(0.5, math.sqrt(gn)) * gn
+            stop = min(0.5, math.sqrt(gn / (2.0 * math.sqrt(g.dV * n_electrons)))) * gn
             x = np.zeros_like(psi)
             r = grad.copy()
             q = -r
@@ -132,6 +135,7 @@ def optimize_density(g: Grid, psi0, func: Functional, Vext_G, n_electrons: float
                     if j == 0:
                         x = -grad
                     break
+                newton = True
                 a = float(np.sum(r * r)) / curv
                 x = x + a * q
                 r_new = r + a * Hq
@@ -139,7 +143,10 @@ def optimize_density(g: Grid, psi0, func: Functional, Vext_G, n_electrons: float
                     break
                 q = -r_new + (np.sum(r_new * r_new) / np.sum(r * r)) * q
                 r = r_new
-            d = x if np.sum(x * grad) < 0.0 else -grad
+            if np.sum(x * grad) < 0.0:
+                d = x
+            else:
+                d, newton = -grad, False
         else:
             # L-BFGS two-loop recursion
             if psi_prev is not None:
@@ -161,7 +168,8 @@ def optimize_density(g: Grid, psi0, func: Functional, Vext_G, n_electrons: float
             for (s_k, y_k, rh), a in zip(pairs, reversed(alphas)):
                 b = rh * float(np.sum(y_k * q))
                 q = q + (a - b) * s_k
-            d = -q if np.sum(q * grad) > 0.0 else -grad
+            newton = bool(pairs) and np.sum(q * grad) > 0.0
+            d = -q if newton else -grad
         g_prev, d_prev, psi_prev = grad, d, psi
         p = d - (np.sum(d * psi) / np.sum(psi * psi)) * psi
         p_len = math.sqrt(np.sum(p * p) * g.dV / n_electrons)     # |p_perp| / |psi|
@@ -181,7 +189,7 @@ def optimize_density(g: Grid, psi0, func: Functional, Vext_G, n_electrons: float
 
         # strong-Wolfe search (bracketing + zoom with cubic interpolation)
         lam_lo, f_lo, d_lo = 0.0, phi0, dphi0
-        lam = min(max(lam_prev if method == "cg" else math.atan(p_len), 1e-4), 0.5)
+        lam = min(max(math.atan(p_len) if newton else lam_prev, 1e-4), 0.5)
         best = None
         n_ls = 0
         lam_hi = None
