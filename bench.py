@@ -305,14 +305,29 @@ def run_scale(args):
             "kernels": {k: {"launches": n, "avg_ms": round(v / max(1, n), 3)} for k, (n, v) in prof.items() if n},
             "checks": out}
     if args.optimize:
-        psi = rho.sqrt()
-        t0 = time.perf_counter()
-        rep = g.optimize_density(psi, f32, wl["n_electrons"], tol_per_atom=1e-6, max_iter=args.max_iter)
-        line["optimize"] = {"seconds": round(time.perf_counter() - t0, 1), "converged": rep["converged"],
-                            "iterations": rep["iterations"], "evaluations": rep["evaluations"],
-                            "E_per_atom": rep["energy"] / wl["n_atoms"], "last_dE_per_atom": rep["last_dE"] / wl["n_atoms"],
-                            "residual": rep["residual"]}
+        line["optimize"] = optimize_runs(g, rho, f32, wl, args)
     print(json.dumps(line), flush=True)
+
+
+def optimize_runs(g, rho, f32, wl, args):
+    """The density optimiser of Sec. 2.4 from sqrt(rho) to 1e-6 Ha/atom with the chosen
+    direction method(s) (not part of the timed step)."""
+    import torch
+    out = {}
+    methods = ("cg", "tn", "lbfgs") if args.opt_method == "all" else (args.opt_method,)
+    for m in methods:
+        psi = rho.sqrt().contiguous()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rep = g.optimize_density(psi, f32, wl["n_electrons"], tol_per_atom=1e-6, max_iter=args.max_iter, method=m,
+                                 max_inner=args.max_inner)
+        torch.cuda.synchronize()
+        out[m] = {"seconds": round(time.perf_counter() - t0, 2), "converged": rep["converged"],
+                  "iterations": rep["iterations"], "evaluations": rep["evaluations"],
+                  "E_per_atom": rep["energy"] / wl["n_atoms"], "last_dE_per_atom": rep["last_dE"] / wl["n_atoms"],
+                  "residual": rep["residual"]}
+        del psi
+    return out[methods[0]] if len(methods) == 1 else out
 
 
 def run_gpu(args):
@@ -528,16 +543,7 @@ def run_gpu(args):
         res["coarse_grid"] = list(coarse.shape)
         line["multistep"] = res
     if args.optimize and rank == 0:
-        # the density optimiser of Sec. 2.4 from sqrt(rho) to 1e-6 Ha/atom (not part of the timed step)
-        psi = rho.sqrt().contiguous()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        rep = g.optimize_density(psi, f32, wl["n_electrons"], tol_per_atom=1e-6, max_iter=args.max_iter)
-        torch.cuda.synchronize()
-        line["optimize"] = {"seconds": round(time.perf_counter() - t0, 2), "converged": rep["converged"],
-                            "iterations": rep["iterations"], "evaluations": rep["evaluations"],
-                            "E_per_atom": rep["energy"] / wl["n_atoms"],
-                            "last_dE_per_atom": rep["last_dE"] / wl["n_atoms"], "residual": rep["residual"]}
+        line["optimize"] = optimize_runs(g, rho, f32, wl, args)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
@@ -665,6 +671,9 @@ def main():
     ap.add_argument("--optimize", action="store_true")
     ap.add_argument("--multistep", action="store_true", help="also time the multi-step optimisation (half-grid first)")
     ap.add_argument("--max-iter", type=int, default=200)
+    ap.add_argument("--opt-method", default="cg", choices=["cg", "tn", "lbfgs", "all"],
+                    help="direction method of --optimize (all: each in turn)")
+    ap.add_argument("--max-inner", type=int, default=0, help="TN inner steps per outer iteration (0: library default)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

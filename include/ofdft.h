@@ -170,7 +170,8 @@ int ofdft_forces(ofdft_grid *g, const void *rho_dev, int precision, double *F_ou
  * Errors: OFDFT_ERR_NO_IONS, OFDFT_ERR_INVALID_ARG, OFDFT_ERR_OOM, OFDFT_ERR_CUDA. */
 int ofdft_ewald(ofdft_grid *g, double *E_out, double *F_out);
 
-/* psi = sqrt(rho) CG density optimisation (Sec. 2.4, Eq. euler2):
+/* psi = sqrt(rho) density optimisation (Sec. 2.4, Eq. euler2) by preconditioned CG
+ * (ofdft_optimize_density_ex below offers TN and L-BFGS):
  * psi_dev (device [N], precision of f) holds the initial psi and receives the
  * result; int psi^2 = N_e is imposed first and then conserved by the
  * psi cos(l) + p sin(l) update.  Stops when |E_k - E_{k-1}| < tol_E_per_atom *
@@ -180,6 +181,37 @@ int ofdft_ewald(ofdft_grid *g, double *E_out, double *F_out);
 int ofdft_optimize_density(ofdft_grid *g, void *psi_dev, const ofdft_functional *f,
                            double N_e, double tol_E_per_atom, int max_iter,
                            ofdft_opt_report *rep);
+
+/* Search-direction methods of the density optimiser (Sec. 2.4, step 1: the paper names
+ * nonlinear CG, L-BFGS and truncated Newton). */
+#define OFDFT_OPT_CG 0      /* Polak-Ribiere+ conjugate gradient (the default) */
+#define OFDFT_OPT_TN 1      /* truncated Newton: inner CG on the Newton equation */
+#define OFDFT_OPT_LBFGS 2   /* limited-memory BFGS */
+
+typedef struct {
+    int method;         /* OFDFT_OPT_CG | OFDFT_OPT_TN | OFDFT_OPT_LBFGS */
+    int precondition;   /* nonzero: the model-Hessian preconditioner a G^2/(G^4 + a G^2 + b)
+                           (a from the local terms, b from Hartree at the mean density)
+                           on the gradient (CG, TN's inner CG, L-BFGS's initial inverse Hessian) */
+    int max_inner;      /* TN: at most this many inner CG steps (each one evaluation) per
+                           outer iteration; 0 = 10; at most 100 */
+    int lbfgs_m;        /* L-BFGS: correction pairs kept (2 fields each); 0 = 5; at most 32 */
+} ofdft_opt_options;
+
+/* ofdft_optimize_density with a choice of direction method (opt NULL = CG, preconditioned).
+ * TN: the Newton equation H x = -g of the Lagrangian E - mu (int psi^2 - N_e) is solved in
+ * the tangent space of the constraint by preconditioned CG, stopped when the residual
+ * falls below min(0.5, sqrt(res)) |g| (res = RMS Euler-Lagrange residual per electron) or
+ * curvature turns non-positive; H q is a forward difference of the gradient 2 psi V dV
+ * (one E+V evaluation at psi + e q, |e q| = 1e-3 |psi| in FP32-mixed, 1e-6 in FP64).
+ * L-BFGS: two-loop recursion over the last lbfgs_m pairs (step of psi, change of the
+ * projected gradient), initial inverse Hessian gamma P.  Both start the line search at the
+ * length of their step.  Allocates 4 (TN) or 2 lbfgs_m (L-BFGS) more device fields of N
+ * elements, kept with the grid.  Errors: as ofdft_optimize_density, OFDFT_ERR_INVALID_ARG
+ * for options out of range. */
+int ofdft_optimize_density_ex(ofdft_grid *g, void *psi_dev, const ofdft_functional *f,
+                              double N_e, double tol_E_per_atom, int max_iter,
+                              const ofdft_opt_options *opt, ofdft_opt_report *rep);
 
 /* Fourier (band-limited) interpolation of a real periodic field between two grids of
  * one cell, the step that carries a converged density to a finer grid in the paper's

@@ -200,11 +200,17 @@ class Grid:
         return F
 
     def optimize_density(self, psi, func: Functional, n_electrons: float, tol_per_atom: float = 1e-6,
-                         max_iter: int = 200, raise_on_not_converged: bool = False):
+                         max_iter: int = 200, raise_on_not_converged: bool = False, method: str = "cg",
+                         precondition: bool = True, max_inner: int = 0, lbfgs_m: int = 0):
+        """Sec. 2.4's psi = sqrt(rho) optimisation in place on psi; method 'cg' | 'tn' | 'lbfgs'."""
+        methods = {"cg": L.OPT_CG, "tn": L.OPT_TN, "lbfgs": L.OPT_LBFGS}
+        if method not in methods:
+            raise ValueError("method must be one of %s" % sorted(methods))
         rep = L.COptReport()
         c, keep = func.to_c()
-        st = self.lib.ofdft_optimize_density(self.h, _ptr(self._field(psi, func)), ct.byref(c), n_electrons,
-                                             tol_per_atom, max_iter, ct.byref(rep))
+        opt = L.COptOptions(methods[method], int(bool(precondition)), max_inner, lbfgs_m)
+        st = self.lib.ofdft_optimize_density_ex(self.h, _ptr(self._field(psi, func)), ct.byref(c), n_electrons,
+                                                tol_per_atom, max_iter, ct.byref(opt), ct.byref(rep))
         if st != L.OFDFT_OK and not (st == -6 and not raise_on_not_converged):
             _check(self.lib, st, self.h)
         del keep

@@ -25,6 +25,7 @@ KNOTS_LOG, KNOTS_ARITH = 0, 1
 NLPOT_EXACT, NLPOT_INTERP = 0, 1
 KERNEL_LWT, KERNEL_WT_GLOBAL = 0, 1
 FP64, FP32_MIXED = 0, 1
+OPT_CG, OPT_TN, OPT_LBFGS = 0, 1, 2
 
 # symbols declared in include/ofdft.h (checked by the CPU test suite)
 EXPORTS = (
@@ -33,7 +34,7 @@ EXPORTS = (
     "ofdft_energy_potential_batched", "ofdft_status_string", "ofdft_last_error", "ofdft_version",
     "ofdft_profile_enable", "ofdft_profile_reset", "ofdft_profile_read",
     "ofdft_tf_energy_potential_noalloc", "ofdft_set_ions_pme", "ofdft_ewald", "ofdft_interpolate",
-    "ofdft_optimize_density_multistep",
+    "ofdft_optimize_density_multistep", "ofdft_optimize_density_ex",
 )
 NOALLOC_MAX_POINTS = 8388608
 
@@ -57,6 +58,10 @@ class COptReport(ct.Structure):
     _fields_ = [("iterations", ct.c_int), ("evaluations", ct.c_int), ("energy", ct.c_double),
                 ("energies", ct.c_double * N_ENERGIES), ("mu", ct.c_double), ("residual", ct.c_double),
                 ("last_dE", ct.c_double)]
+
+
+class COptOptions(ct.Structure):
+    _fields_ = [("method", ct.c_int), ("precondition", ct.c_int), ("max_inner", ct.c_int), ("lbfgs_m", ct.c_int)]
 
 
 _lib = None
@@ -83,6 +88,8 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.ofdft_optimize_density_multistep.argtypes = [I, ct.POINTER(P), V, ct.POINTER(CFunctional), D, D, I,
                                                      ct.POINTER(COptReport)]
     lib.ofdft_optimize_density.argtypes = [P, V, ct.POINTER(CFunctional), D, D, I, ct.POINTER(COptReport)]
+    lib.ofdft_optimize_density_ex.argtypes = [P, V, ct.POINTER(CFunctional), D, D, I, ct.POINTER(COptOptions),
+                                              ct.POINTER(COptReport)]
     lib.ofdft_energy_potential_batched.argtypes = [I, ct.POINTER(P), ct.POINTER(V), ct.POINTER(CFunctional),
                                                    ct.POINTER(D), ct.POINTER(V), ct.POINTER(ct.POINTER(D))]
     lib.ofdft_profile_enable.argtypes = [P, I]

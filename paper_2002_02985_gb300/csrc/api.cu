@@ -72,6 +72,8 @@ template <typename T> struct Workspace {
     double *part_stats = nullptr, *part_ax0 = nullptr, *part_row = nullptr, *part_misc = nullptr;
     unsigned *ticket = nullptr;       // stats completion counter
     T *opt = nullptr;                 // optimiser fields (8 * N), allocated on demand
+    T *opt_ext = nullptr;             // TN / L-BFGS fields (opt_ext_fields * N), on demand
+    int opt_ext_fields = 0;
     LaunchSet ks;                     // FFT-carrying kernels (size-specialised where compiled)
     int Brow = 0, thr_rowf = 0, thr_rowi = 0, TW1 = 0, thr_p1 = 0, TW0 = 0, thr_ax0 = 0, nb_row = 0, nb_ax0 = 0;
     int grid_p1 = 0;
@@ -300,6 +302,7 @@ template <typename T> void free_ws(Workspace<T> &w) {
     cudaFree(w.part_misc);
     cudaFree(w.ticket);
     cudaFree(w.opt);
+    cudaFree(w.opt_ext);
     w = Workspace<T>();
 }
 
@@ -895,7 +898,8 @@ int ewald_impl(ofdft_grid *g, double *E_out, double *F_out) {
 
 template <typename T>
 int optimize_impl(ofdft_grid *g, T *psi, const ofdft_functional *f0, double Ne, double tol, int max_iter,
-                  ofdft_opt_report *rep);
+                  const ofdft_opt_options &o, ofdft_opt_report *rep);
+const ofdft_opt_options kOptDefaults = {OFDFT_OPT_CG, 1, 0, 0};
 
 // ---------------------------------------------------------------- Fourier interpolation between grids
 bool same_cell(const ofdft_grid *a, const ofdft_grid *b) {
@@ -946,7 +950,7 @@ int multistep_impl(int nlev, ofdft_grid *const *grids, T *psi, const ofdft_funct
             if ((rc = interpolate_impl<T>(grids[L - 1], lev[L - 1], grids[L], lev[L]))) break;
             CK(cudaStreamSynchronize(grids[L - 1]->stream), "stream synchronize");
         }
-        rc = optimize_impl<T>(grids[L], lev[L], f, Ne, tol, max_iter, L == nlev - 1 ? rep : &r);
+        rc = optimize_impl<T>(grids[L], lev[L], f, Ne, tol, max_iter, kOptDefaults, L == nlev - 1 ? rep : &r);
         if (rc == OFDFT_ERR_NOT_CONVERGED && L < nlev - 1) rc = OFDFT_OK;   // a coarse level only seeds the next
         if (rc && L < nlev - 1 && grids[L] != fine) fine->err = grids[L]->err;
     }
@@ -983,7 +987,7 @@ double cubic_min(double a, double fa, double da, double b, double fb, double db,
 
 template <typename T>
 int optimize_impl(ofdft_grid *g, T *psi, const ofdft_functional *f0, double Ne, double tol, int max_iter,
-                  ofdft_opt_report *rep) {
+                  const ofdft_opt_options &o, ofdft_opt_report *rep) {
     const long long N = g->N;
     int rc = ensure_ws<T>(g, 3);
     if (rc) return rc;
@@ -991,6 +995,19 @@ int optimize_impl(ofdft_grid *g, T *psi, const ofdft_functional *f0, double Ne, 
     if (!w.opt) CK(cudaMalloc(&w.opt, 8 * (size_t)N * sizeof(T)), "cudaMalloc optimiser fields");
     T *rho = w.opt, *V = rho + N, *grad = V + N, *gprev = grad + N, *d = gprev + N, *p = d + N, *psil = p + N;
     T *tmp = psil + N;
+    const int method = o.method;
+    const int max_inner = o.max_inner > 0 ? o.max_inner : 10;
+    const int lm = o.lbfgs_m > 0 ? o.lbfgs_m : 5;
+    // more fields: TN's q, Hq, Vq, r; L-BFGS's m pairs (s, y)
+    const int n_ext = method == OFDFT_OPT_TN ? 4 : (method == OFDFT_OPT_LBFGS ? 2 * lm : 0);
+    if (n_ext > w.opt_ext_fields) {
+        cudaFree(w.opt_ext);
+        w.opt_ext = nullptr;
+        w.opt_ext_fields = 0;
+        CK(cudaMalloc(&w.opt_ext, (size_t)n_ext * (size_t)N * sizeof(T)), "cudaMalloc optimiser history");
+        w.opt_ext_fields = n_ext;
+    }
+    T *ext = w.opt_ext;
     Dev<T> dv{g, &w};
     cudaStream_t s = g->stream;
     // Preconditioner of the gradient, P(G) = a G^2 / (G^4 + a G^2 + b), the inverse of a model
@@ -998,10 +1015,10 @@ int optimize_impl(ofdft_grid *g, T *psi, const ofdft_functional *f0, double Ne, 
     // grows with the grid's cut-off, so plain CG needs ever more iterations on finer grids),
     // a = (70/9) C_TF rho_m^(2/3) from the local terms, b/G^2 = 16 pi rho_m / G^2 from Hartree
     // (stiff long-wavelength charge moves; a kinetic-only preconditioner amplifies exactly
-    // those and stalls).  OFDFT_OPT_PRECOND=0 turns it off.
+    // those and stalls).  OFDFT_OPT_PRECOND=0 in the environment turns it off as well.
     typedef typename Vec2<T>::type C;
     const char *env_pc = std::getenv("OFDFT_OPT_PRECOND");
-    const bool precond = !(env_pc && env_pc[0] == '0');
+    const bool precond = o.precondition && !(env_pc && env_pc[0] == '0');
     const double rho_m = Ne / g->omega;
     const double pa = 70.0 / 9.0 * kCTF * std::pow(rho_m, 2.0 / 3.0), pb = 16.0 * kPi * rho_m;
     double bv[9];
@@ -1015,6 +1032,22 @@ int optimize_impl(ofdft_grid *g, T *psi, const ofdft_functional *f0, double Ne, 
         CK(launch_precond<C>((C *)w.chan, g->n[0], g->n[1], g->n[2], bv, pa, pb, s), "preconditioner");
         if ((r = inverse_plain<T>(g, w, 0, out, x))) return r;
         CK(launch_add_scalar<T>(out, w.scal + S_RHO_MEAN, N, s), "preconditioner mean");
+        return OFDFT_OK;
+    };
+    double pp = 0.0;                   // <psi, psi> of the current iterate
+    auto project = [&](T *v) -> int {  // v -= (<v, psi> / <psi, psi>) psi: the tangent space
+        CK(launch_axpby<T>(v, psi, -dv.dot(v, psi) / pp, 1.0, N, s), "projection");
+        return OFDFT_OK;
+    };
+    // preconditioned steepest descent -P g (projected), or -g, into out
+    auto steepest = [&](T *out) -> int {
+        if (precond) {
+            int r = apply_precond(grad, z);
+            if (r) return r;
+            CK(launch_axpby<T>(out, z, -1.0, 0.0, N, s), "axpby");
+        } else {
+            CK(launch_axpby<T>(out, grad, -1.0, 0.0, N, s), "axpby");
+        }
         return OFDFT_OK;
     };
     const bool lwt_auto = (f0->terms & OFDFT_TERM_NL) && f0->kernel == OFDFT_KERNEL_LWT && !f0->knots;
@@ -1041,42 +1074,159 @@ int optimize_impl(ofdft_grid *g, T *psi, const ofdft_functional *f0, double Ne, 
         if ((rc = eval_sync<T>(g, rho, &f, V, E))) return rc;
         evals++;
     }
+
+    // ---- truncated Newton: inner preconditioned CG on H x = -g in the tangent space,
+    // H q by a forward difference of the gradient (one evaluation per inner step)
+    const double h_fd = sizeof(T) == 4 ? 1e-3 : 1e-6;   // |e q| / |psi| of the difference
+    double mu = 0.0;
+    auto tn_direction = [&](bool &newton) -> int {
+        T *q = ext, *Hq = ext + N, *Vq = ext + 2 * N, *r = ext + 3 * N, *x = d;
+        double Eq[E_NUM];
+        const double gn = std::sqrt(dv.dot(grad, grad));
+        // forcing term on the RMS Euler-Lagrange residual per electron, |g| / (2 sqrt(dV N_e))
+        const double stop = std::min(0.5, std::sqrt(gn / (2.0 * std::sqrt(g->dV * Ne)))) * gn;
+        CK(cudaMemsetAsync(x, 0, (size_t)N * sizeof(T), s), "memset");
+        CK(launch_copy<T>(r, grad, N, s), "copy");
+        const T *zr = r;
+        int e2;
+        if (precond) {
+            if ((e2 = apply_precond(r, z)) || (e2 = project(z))) return e2;
+            zr = z;
+        }
+        double rz = dv.dot(r, zr);
+        CK(launch_axpby<T>(q, zr, -1.0, 0.0, N, s), "axpby");
+        newton = false;
+        for (int j = 0; j < max_inner; j++) {
+            const double e = h_fd * std::sqrt(pp / dv.dot(q, q));
+            CK(launch_rotate<T>(psil, rho, psi, q, 1.0, e, N, s), "perturb");
+            if ((e2 = eval_sync<T>(g, rho, &f, Vq, Eq))) return e2;
+            evals++;
+            CK(launch_hvp<T>(Hq, psi, q, V, Vq, e, mu, g->dV, N, s), "Hessian product");
+            if ((e2 = project(Hq))) return e2;
+            const double curv = dv.dot(q, Hq);
+            if (!(curv > 0.0)) break;             // non-positive curvature: keep x so far
+            newton = true;
+            const double a = rz / curv;
+            CK(launch_axpby<T>(x, q, a, 1.0, N, s), "axpby");
+            CK(launch_axpby<T>(r, Hq, a, 1.0, N, s), "axpby");
+            if (j == max_inner - 1 || std::sqrt(dv.dot(r, r)) < stop) break;
+            if (precond) {
+                if ((e2 = apply_precond(r, z)) || (e2 = project(z))) return e2;
+            }
+            const double rz_new = dv.dot(r, zr);
+            CK(launch_axpby<T>(q, zr, -1.0, rz_new / rz, N, s), "axpby");
+            rz = rz_new;
+        }
+        if (!newton || !(dv.dot(x, grad) < 0.0)) {
+            newton = false;
+            return steepest(x);
+        }
+        return OFDFT_OK;
+    };
+
+    // ---- L-BFGS: two-loop recursion over a ring of m pairs (s = step of psi, y = change
+    // of the projected gradient); initial inverse Hessian gamma P (or gamma I)
+    std::vector<double> l_rho(lm, 0.0), l_alpha(lm, 0.0);
+    int l_count = 0, l_head = 0;        // pairs stored; slot of the next pair
+    bool l_pending = false;             // S(l_head) holds the last step, waiting for its y
+    auto Sk = [&](int k) { return ext + (size_t)(2 * k) * (size_t)N; };
+    auto Yk = [&](int k) { return ext + (size_t)(2 * k + 1) * (size_t)N; };
+    auto lbfgs_direction = [&](bool &newton) -> int {
+        int e2;
+        if (l_pending) {
+            T *y = Yk(l_head);
+            CK(launch_copy<T>(y, grad, N, s), "copy");
+            CK(launch_axpby<T>(y, gprev, -1.0, 1.0, N, s), "axpby");
+            const double sy = dv.dot(Sk(l_head), y);
+            if (sy > 0.0) {
+                l_rho[l_head] = 1.0 / sy;
+                l_head = (l_head + 1) % lm;
+                l_count = std::min(l_count + 1, lm);
+            } else {
+                l_count = std::min(l_count, lm - 1);   // the slot (the oldest pair's) was overwritten
+            }
+            l_pending = false;
+        }
+        CK(launch_copy<T>(gprev, grad, N, s), "copy");
+        newton = false;
+        if (l_count == 0) return steepest(d);
+        CK(launch_copy<T>(d, grad, N, s), "copy");
+        for (int i = 0; i < l_count; i++) {             // newest to oldest
+            const int k = (l_head - 1 - i + 2 * lm) % lm;
+            l_alpha[k] = l_rho[k] * dv.dot(Sk(k), d);
+            CK(launch_axpby<T>(d, Yk(k), -l_alpha[k], 1.0, N, s), "axpby");
+        }
+        const int kn = (l_head - 1 + lm) % lm;         // newest pair
+        if (precond) {
+            if ((e2 = apply_precond(Yk(kn), z)) || (e2 = project(z))) return e2;
+            const double gamma = (1.0 / l_rho[kn]) / dv.dot(Yk(kn), z);
+            if ((e2 = apply_precond(d, z)) || (e2 = project(z))) return e2;
+            CK(launch_axpby<T>(d, z, gamma, 0.0, N, s), "axpby");
+        } else {
+            const double gamma = (1.0 / l_rho[kn]) / dv.dot(Yk(kn), Yk(kn));
+            CK(launch_axpby<T>(d, d, 0.0, gamma, N, s), "axpby");
+        }
+        for (int i = l_count - 1; i >= 0; i--) {        // oldest to newest
+            const int k = (l_head - 1 - i + 2 * lm) % lm;
+            const double b = l_rho[k] * dv.dot(Yk(k), d);
+            CK(launch_axpby<T>(d, Sk(k), l_alpha[k] - b, 1.0, N, s), "axpby");
+        }
+        CK(launch_axpby<T>(d, d, 0.0, -1.0, N, s), "axpby");
+        if (dv.dot(d, grad) < 0.0) {
+            newton = true;
+            return OFDFT_OK;
+        }
+        return steepest(d);
+    };
+    auto forget = [&]() {               // after a failed search: no conjugacy, no history
+        l_count = 0;
+        l_pending = false;
+    };
+
     double lam_prev = 0.05;
     int small = 0, it = 0, restarts = 0;
     bool have_dir = false;
-    double last_dE = 0.0, mu = 0.0;
+    double last_dE = 0.0;
     const double c1 = 1e-4, c2 = 0.2;
     while (it < max_iter) {
         it++;
         // g = 2 psi (V - mu) dV, mu = int rho V / N_e
+        pp = dv.dot(psi, psi);
         mu = dv.dot(psi, psi, V) * g->dV / Ne;
         CK(launch_grad<T>(grad, psi, V, mu, g->dV, N, s), "grad");
-        double beta = 0.0, zg = 0.0;
-        const T *src = grad;           // the (preconditioned) steepest-descent direction
-        if (precond) {
-            if ((rc = apply_precond(grad, z))) return rc;
-            src = z;
-            zg = dv.dot(z, grad);
-        }
-        if (have_dir && (it % 50) != 1) {
+        bool newton = false;           // a TN / L-BFGS direction built from curvature
+        if (method == OFDFT_OPT_TN) {
+            if ((rc = tn_direction(newton))) return rc;
+        } else if (method == OFDFT_OPT_LBFGS) {
+            if ((rc = lbfgs_direction(newton))) return rc;
+        } else {
+            double beta = 0.0, zg = 0.0;
+            const T *src = grad;       // the (preconditioned) steepest-descent direction
             if (precond) {
-                // preconditioned PR+: beta = <z, g - g_prev> / <z_prev, g_prev>
-                beta = zg_prev > 0.0 ? std::max(0.0, (zg - dv.dot(z, gprev)) / zg_prev) : 0.0;
-            } else {
-                const double gg = dv.dot(grad, grad), ggp = dv.dot(grad, gprev), gpgp = dv.dot(gprev, gprev);
-                beta = std::max(0.0, (gg - ggp) / gpgp);
+                if ((rc = apply_precond(grad, z))) return rc;
+                src = z;
+                zg = dv.dot(z, grad);
             }
+            if (have_dir && (it % 50) != 1) {
+                if (precond) {
+                    // preconditioned PR+: beta = <z, g - g_prev> / <z_prev, g_prev>
+                    beta = zg_prev > 0.0 ? std::max(0.0, (zg - dv.dot(z, gprev)) / zg_prev) : 0.0;
+                } else {
+                    const double gg = dv.dot(grad, grad), ggp = dv.dot(grad, gprev), gpgp = dv.dot(gprev, gprev);
+                    beta = std::max(0.0, (gg - ggp) / gpgp);
+                }
+            }
+            // d = -src + beta d
+            if (have_dir && beta > 0.0) CK(launch_axpby<T>(d, src, -1.0, beta, N, s), "axpby");
+            else CK(launch_axpby<T>(d, src, -1.0, 0.0, N, s), "axpby");
+            if (dv.dot(d, grad) >= 0.0) CK(launch_axpby<T>(d, src, -1.0, 0.0, N, s), "axpby");
+            CK(launch_copy<T>(gprev, grad, N, s), "copy");
+            zg_prev = zg;
+            have_dir = true;
         }
-        // d = -src + beta d
-        if (have_dir && beta > 0.0) CK(launch_axpby<T>(d, src, -1.0, beta, N, s), "axpby");
-        else CK(launch_axpby<T>(d, src, -1.0, 0.0, N, s), "axpby");
-        if (dv.dot(d, grad) >= 0.0) CK(launch_axpby<T>(d, src, -1.0, 0.0, N, s), "axpby");
-        CK(launch_copy<T>(gprev, grad, N, s), "copy");
-        zg_prev = zg;
-        have_dir = true;
         // p = d - (<d,psi>/<psi,psi>) psi, normalised to N_e
         CK(launch_copy<T>(p, d, N, s), "copy");
-        const double dpsi = dv.dot(d, psi), pp = dv.dot(psi, psi);
+        const double dpsi = dv.dot(d, psi);
         CK(launch_axpby<T>(p, psi, -dpsi / pp, 1.0, N, s), "axpby");
         const double pn = dv.dot(p, p) * g->dV;
         if (!(pn > 0.0)) break;
@@ -1086,6 +1236,7 @@ int optimize_impl(ofdft_grid *g, T *psi, const ofdft_functional *f0, double Ne, 
         const double dphi0 = 2.0 * g->dV * dv.dot(psi, V, p);
         if (dphi0 >= 0.0) {
             have_dir = false;
+            forget();
             if (++restarts > 3) break;
             continue;
         }
@@ -1100,7 +1251,8 @@ int optimize_impl(ofdft_grid *g, T *psi, const ofdft_functional *f0, double Ne, 
             return OFDFT_OK;
         };
         double lam_lo = 0.0, f_lo = phi0, d_lo = dphi0, lam_hi = -1.0, f_hi = 0.0, d_hi = 0.0;
-        double lam = std::min(std::max(lam_prev, 1e-4), 0.5);
+        // a curvature-built step has a length: psi + x_perp lies on the rotation at atan(|x_perp|/|psi|)
+        double lam = std::min(std::max(newton ? std::atan(std::sqrt(pn / Ne)) : lam_prev, 1e-4), 0.5);
         double best_f = 1e300, best_lam = 0.0;
         for (int ls = 0; ls < 10; ls++) {
             double El[E_NUM], dl;
@@ -1126,6 +1278,7 @@ int optimize_impl(ofdft_grid *g, T *psi, const ofdft_functional *f0, double Ne, 
         }
         if (!(best_f < phi0)) {
             have_dir = false;
+            forget();
             if (++restarts > 3) break;
             // restore V at psi for the next gradient
             CK(launch_square<T>(rho, psi, 1.0, N, s), "square");
@@ -1137,6 +1290,11 @@ int optimize_impl(ofdft_grid *g, T *psi, const ofdft_functional *f0, double Ne, 
         lam_prev = best_lam;
         // accept: psi <- psi cos + p sin, and V at the accepted point
         CK(launch_rotate<T>(psil, rho, psi, p, std::cos(best_lam), std::sin(best_lam), N, s), "rotate");
+        if (method == OFDFT_OPT_LBFGS) {            // s = psi_new - psi
+            CK(launch_copy<T>(Sk(l_head), psil, N, s), "copy");
+            CK(launch_axpby<T>(Sk(l_head), psi, -1.0, 1.0, N, s), "axpby");
+            l_pending = true;
+        }
         CK(launch_copy<T>(psi, psil, N, s), "copy");
         // The rotation conserves int psi^2 exactly only in exact arithmetic; in FP32
         // the rounding drift accumulates over iterations (and lowers E with the
@@ -1642,15 +1800,25 @@ int ofdft_optimize_density_multistep(int n_levels, ofdft_grid *const *grids, voi
     return multistep_impl<float>(n_levels, grids, (float *)psi_dev, f, N_e, tol_E_per_atom, max_iter, rep);
 }
 
-int ofdft_optimize_density(ofdft_grid *g, void *psi_dev, const ofdft_functional *f, double N_e,
-                           double tol_E_per_atom, int max_iter, ofdft_opt_report *rep) {
+int ofdft_optimize_density_ex(ofdft_grid *g, void *psi_dev, const ofdft_functional *f, double N_e,
+                              double tol_E_per_atom, int max_iter, const ofdft_opt_options *opt,
+                              ofdft_opt_report *rep) {
     if (!g) return OFDFT_ERR_INVALID_ARG;
     if (!psi_dev || !(N_e > 0.0) || max_iter < 1) return fail(g, OFDFT_ERR_INVALID_ARG, "psi, N_e or max_iter");
+    const ofdft_opt_options o = opt ? *opt : kOptDefaults;
+    if (o.method < OFDFT_OPT_CG || o.method > OFDFT_OPT_LBFGS || o.max_inner < 0 || o.max_inner > 100 ||
+        o.lbfgs_m < 0 || o.lbfgs_m > 32)
+        return fail(g, OFDFT_ERR_INVALID_ARG, "optimiser options");
     int rc = check_functional(g, f);
     if (rc) return rc;
     if (f->precision == OFDFT_FP64)
-        return optimize_impl<double>(g, (double *)psi_dev, f, N_e, tol_E_per_atom, max_iter, rep);
-    return optimize_impl<float>(g, (float *)psi_dev, f, N_e, tol_E_per_atom, max_iter, rep);
+        return optimize_impl<double>(g, (double *)psi_dev, f, N_e, tol_E_per_atom, max_iter, o, rep);
+    return optimize_impl<float>(g, (float *)psi_dev, f, N_e, tol_E_per_atom, max_iter, o, rep);
+}
+
+int ofdft_optimize_density(ofdft_grid *g, void *psi_dev, const ofdft_functional *f, double N_e,
+                           double tol_E_per_atom, int max_iter, ofdft_opt_report *rep) {
+    return ofdft_optimize_density_ex(g, psi_dev, f, N_e, tol_E_per_atom, max_iter, nullptr, rep);
 }
 
 int ofdft_energy_potential_batched(int n, ofdft_grid *const *grids, const void *const *rho_dev,

@@ -69,6 +69,11 @@ template <typename T> cudaError_t launch_copy(T *dst, const T *src, long long N,
 template <typename C>
 cudaError_t launch_spectral_map(const C *src, int f0, int f1, int f2, C *dst, int t0, int t1, int t2,
                                 cudaStream_t s);
+// Hq = 2 dV (q (Vq - mu) + psi (Vq - V) / e): the Hessian of E[psi^2] - mu int psi^2 applied
+// to q by a forward difference, Vq = V[(psi + e q)^2]
+template <typename T>
+cudaError_t launch_hvp(T *Hq, const T *psi, const T *q, const T *V, const T *Vq, double e, double mu, double dV,
+                       long long N, cudaStream_t s);
 // x += c[0] (c a device scalar)
 template <typename T> cudaError_t launch_add_scalar(T *x, const double *c, long long N, cudaStream_t s);
 // optimiser preconditioner on a normalised half spectrum: h(G) *= a G^2 / (G^4 + a G^2 + b), h(0) kept

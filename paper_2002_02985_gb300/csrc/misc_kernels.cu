@@ -387,6 +387,10 @@ cudaError_t launch_dot(const T *a, const T *b, const T *c, long long N, double *
 
 template <typename T> __global__ void axpby_kernel(T *y, const T *x, T al, T be, long long N) {
     const long long stride = (long long)gridDim.x * blockDim.x;
+    if (be == (T)0) {                  // y is not read: it may hold anything, NaN included
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += stride) y[i] = al * x[i];
+        return;
+    }
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += stride)
         y[i] = al * x[i] + be * y[i];
 }
@@ -569,7 +573,27 @@ cudaError_t launch_precond(C *h, int n0, int n1, int n2, const double *bv, doubl
 template cudaError_t launch_precond<float2>(float2 *, int, int, int, const double *, double, double, cudaStream_t);
 template cudaError_t launch_precond<double2>(double2 *, int, int, int, const double *, double, double, cudaStream_t);
 
+// Lagrangian Hessian times q by a forward difference of the gradient 2 psi V[psi^2] dV:
+// Hq = 2 dV (q Vq + psi (Vq - V) / e - mu q), Vq the potential at psi + e q.
+template <typename T>
+__global__ void hvp_kernel(T *Hq, const T *psi, const T *q, const T *V, const T *Vq, T inv_e, T mu, T dV2,
+                           long long N) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += stride) {
+        const T vq = Vq[i], qi = q[i];
+        Hq[i] = dV2 * (qi * (vq - mu) + psi[i] * (vq - V[i]) * inv_e);
+    }
+}
+template <typename T>
+cudaError_t launch_hvp(T *Hq, const T *psi, const T *q, const T *V, const T *Vq, double e, double mu, double dV,
+                       long long N, cudaStream_t s) {
+    hvp_kernel<T><<<1216, 256, 0, s>>>(Hq, psi, q, V, Vq, (T)(1.0 / e), (T)mu, (T)(2.0 * dV), N);
+    return cudaGetLastError();
+}
+
 #define INST(T)                                                                                              \
+    template cudaError_t launch_hvp<T>(T *, const T *, const T *, const T *, const T *, double, double,      \
+                                       double, long long, cudaStream_t);                                     \
     template cudaError_t launch_add_scalar<T>(T *, const double *, long long, cudaStream_t);                  \
     template cudaError_t launch_dot<T>(const T *, const T *, const T *, long long, double *, int, double *,    \
                                        cudaStream_t);                                                        \
