@@ -19,6 +19,9 @@ Readings (the paper leaves them to SciPy and to its references):
 - L-BFGS: two-loop recursion over the last m pairs (s, y) of steps in psi and
   changes of the projected gradient, initial inverse Hessian (s.y / y.y) I;
   a pair with s.y <= 0 is not stored; the memory is cleared on a failed search.
+- Step (3), the update: the orthogonal psi cos(lambda) + p sin(lambda) (default), or
+  the scaling scheme psi + t p renormalised to N_e with p not orthogonalised (with p
+  orthogonal to psi the two are one curve, t = tan(lambda)).
 - Step (2): a strong-Wolfe line search on lambda (c1 = 1e-4, c2 = 0.2, at most
   10 evaluations per search, cubic interpolation).  A TN or L-BFGS direction
   built from curvature starts from the length of its step,
@@ -68,6 +71,20 @@ def hessian_vector(g: Grid, psi, x, func: Functional, Vext_G, mu: float, h: floa
     return (gp - gm) / (2.0 * e) - 2.0 * mu * g.dV * x, 2
 
 
+def update_curve(psi, p, t: float, dV: float, n_electrons: float, update: str = "rotate"):
+    """Step (3) of Sec. 2.4: the trial psi at step t along p and its derivative in t.
+    rotate: psi cos t + p sin t (p orthogonal to psi, int p^2 = N_e);
+    scale:  psi_t = c (psi + t p), c = sqrt(N_e / n), n = int (psi + t p)^2, so that
+            d psi_t / dt = c p - (n' / 2n) psi_t with n' = 2 int (psi + t p) p."""
+    if update == "rotate":
+        return psi * math.cos(t) + p * math.sin(t), -psi * math.sin(t) + p * math.cos(t)
+    q = psi + t * p
+    n = np.sum(q * q) * dV
+    c = math.sqrt(n_electrons / n)
+    psi_t = c * q
+    return psi_t, c * p - (np.sum(q * p) * dV / n) * psi_t
+
+
 def _tangent(v, psi):
     """Component of v orthogonal to psi."""
     return v - (np.sum(v * psi) / np.sum(psi * psi)) * psi
@@ -76,10 +93,14 @@ def _tangent(v, psi):
 def optimize_density(g: Grid, psi0, func: Functional, Vext_G, n_electrons: float, n_atoms: int,
                      tol: float = 1e-6, max_iter: int = 200, c1: float = 1e-4, c2: float = 0.2,
                      max_ls: int = 10, fixed_iter: int | None = None, method: str = "cg",
-                     max_inner: int = 20, lbfgs_m: int = 5):
-    """method: 'cg' | 'tn' | 'lbfgs'.  Returns dict(psi, E, energies, iterations, evals, history)."""
+                     max_inner: int = 20, lbfgs_m: int = 5, update: str = "rotate"):
+    """method: 'cg' | 'tn' | 'lbfgs'; update: 'rotate' (psi cos + p sin, p orthogonal to psi)
+    or 'scale' (psi + t p renormalised, p not orthogonalised).
+    Returns dict(psi, E, energies, iterations, evals, history)."""
     if method not in ("cg", "tn", "lbfgs"):
         raise ValueError("unknown method %r" % method)
+    if update not in ("rotate", "scale"):
+        raise ValueError("unknown update %r" % update)
     psi = np.asarray(psi0, dtype=np.float64).copy()
     psi *= math.sqrt(n_electrons / (np.sum(psi * psi) * g.dV))
     evals = 0
@@ -171,25 +192,30 @@ def optimize_density(g: Grid, psi0, func: Functional, Vext_G, n_electrons: float
             newton = bool(pairs) and np.sum(q * grad) > 0.0
             d = -q if newton else -grad
         g_prev, d_prev, psi_prev = grad, d, psi
-        p = d - (np.sum(d * psi) / np.sum(psi * psi)) * psi
-        p_len = math.sqrt(np.sum(p * p) * g.dV / n_electrons)     # |p_perp| / |psi|
+        if update == "rotate":
+            p = d - (np.sum(d * psi) / np.sum(psi * psi)) * psi
+            p_len = math.sqrt(np.sum(p * p) * g.dV / n_electrons)     # |p_perp| / |psi|
+            step0 = math.atan(p_len)                                 # psi + p_perp on the rotation
+        else:
+            p = d.copy()
+            p_len = math.sqrt(np.sum(p * p) * g.dV / n_electrons)     # |d| / |psi|
+            step0 = p_len                                            # psi + d at t = |d| / |psi|
         p *= math.sqrt(n_electrons / (np.sum(p * p) * g.dV))
         phi0 = E["total"]
-        dphi0 = float(np.sum(dEdpsi * p))
+        dphi0 = float(np.sum(grad * p))
         if dphi0 >= 0.0:
             d_prev = None
             pairs = []
             continue
 
         def phi(lam):
-            psi_l = psi * math.cos(lam) + p * math.sin(lam)
+            psi_l, dpsi = update_curve(psi, p, lam, g.dV, n_electrons, update)
             E_l, V_l = energy(psi_l, f_it)
-            dpsi = -psi * math.sin(lam) + p * math.cos(lam)
             return E_l, V_l, psi_l, float(np.sum(2.0 * psi_l * V_l * g.dV * dpsi))
 
         # strong-Wolfe search (bracketing + zoom with cubic interpolation)
         lam_lo, f_lo, d_lo = 0.0, phi0, dphi0
-        lam = min(max(math.atan(p_len) if newton else lam_prev, 1e-4), 0.5)
+        lam = min(max(step0 if newton else lam_prev, 1e-4), 0.5)
         best = None
         n_ls = 0
         lam_hi = None

@@ -191,3 +191,50 @@ def test_methods_end_at_stationary_points_of_the_lwt_functional():
         Es.append(r["E"])
     assert max(Es) < E0 - 1e-2
     assert (max(Es) - min(Es)) / 4 < 1e-5
+
+
+# --------------------------------------------------------------------------- scaling update
+def test_scaling_update_stays_normalised_and_its_derivative_is_exact():
+    from oracle.optimize import update_curve
+    g, rho, _ = _small_al()
+    psi = np.sqrt(rho)
+    d = np.random.default_rng(4).standard_normal(g.shape) * psi      # not orthogonal to psi
+    p = d * math.sqrt(12.0 / (np.sum(d * d) * g.dV))
+    for t in (0.0, 0.2, 0.9):
+        q, dq = update_curve(psi, p, t, g.dV, 12.0, "scale")
+        assert abs(np.sum(q * q) * g.dV - 12.0) < 1e-11
+        h = 1e-5
+        fd = (update_curve(psi, p, t + h, g.dV, 12.0, "scale")[0]
+              - update_curve(psi, p, t - h, g.dV, 12.0, "scale")[0]) / (2 * h)
+        assert np.max(np.abs(fd - dq)) < 1e-7 * np.max(np.abs(dq))
+        # the renormalised point is psi + t p scaled: parallel to it
+        r = psi + t * p
+        assert np.max(np.abs(q * (np.sum(r * r) / np.sum(q * r)) - r)) < 1e-12 * np.max(np.abs(r))
+
+
+def test_scaling_with_orthogonal_p_is_the_rotation_at_atan_t():
+    from oracle.optimize import update_curve
+    g, rho, _ = _small_al()
+    psi = np.sqrt(rho)
+    d = np.random.default_rng(9).standard_normal(g.shape) * psi
+    p = d - np.sum(d * psi) / np.sum(psi * psi) * psi
+    p *= math.sqrt(12.0 / (np.sum(p * p) * g.dV))
+    for t in (0.1, 0.7, 2.0):
+        a = update_curve(psi, p, t, g.dV, 12.0, "scale")[0]
+        b = update_curve(psi, p, math.atan(t), g.dV, 12.0, "rotate")[0]
+        assert np.max(np.abs(a - b)) < 1e-12 * np.max(np.abs(b))
+
+
+def test_scaling_update_reaches_the_same_minima():
+    g, Vg, H = _schroedinger_case(10)
+    E0 = 4.0 * np.linalg.eigvalsh(H)[0]
+    psi0 = 1.0 + 0.3 * np.random.default_rng(2).random(g.shape)
+    for method in ("cg", "tn"):
+        r = optimize_density(g, psi0, Functional(terms=("VW", "PP")), Vg, 4.0, 4, tol=1e-13, max_iter=500,
+                             method=method, update="scale")
+        assert abs(r["E"] - E0) < 1e-9 * abs(E0), (method, r["E"], E0)
+    g, rho, Vg = _small_al()
+    f = Functional(terms=("TF", "VW", "HARTREE", "PP"))
+    a = optimize_density(g, np.sqrt(rho), f, Vg, 12.0, 4, tol=1e-11, max_iter=400)
+    b = optimize_density(g, np.sqrt(rho), f, Vg, 12.0, 4, tol=1e-11, max_iter=400, update="scale")
+    assert abs(a["E"] - b["E"]) / 4 < 1e-10
