@@ -196,7 +196,13 @@ typedef struct {
     int max_inner;      /* TN: at most this many inner CG steps (each one evaluation) per
                            outer iteration; 0 = 10; at most 100 */
     int lbfgs_m;        /* L-BFGS: correction pairs kept (2 fields each); 0 = 5; at most 32 */
+    int update;         /* step (3): OFDFT_UPDATE_ROTATE psi cos(l) + p sin(l), p orthogonal to psi
+                           (default), or OFDFT_UPDATE_SCALE psi + t p renormalised to N_e, p not
+                           orthogonalised (the paper's scaling scheme, "not always stable") */
 } ofdft_opt_options;
+
+#define OFDFT_UPDATE_ROTATE 0
+#define OFDFT_UPDATE_SCALE 1
 
 /* ofdft_optimize_density with a choice of direction method (opt NULL = CG, preconditioned).
  * TN: the Newton equation H x = -g of the Lagrangian E - mu (int psi^2 - N_e) is solved in
@@ -234,6 +240,54 @@ int ofdft_interpolate(ofdft_grid *from, const void *src_dev, ofdft_grid *to, voi
 int ofdft_optimize_density_multistep(int n_levels, ofdft_grid *const *grids, void *psi_dev,
                                      const ofdft_functional *f, double N_e, double tol_E_per_atom,
                                      int max_iter, ofdft_opt_report *rep);
+
+/* ---- Real-time TD-OFDFT (Sec. "Time-Dependent OFDFT", Eq. cn).  A complex collective
+ * orbital psi = sqrt(rho) e^{iS}, held as two real device fields (re, im; precision of f),
+ * obeys i dpsi/dt = H psi, H psi = -lap psi / 2 + v_eff[rho] psi with v_eff = d(E - T_vW)/drho
+ * for the functional f (its von Weizsaecker term becomes the Laplacian; adiabatic: v_eff at
+ * the instantaneous density).  Positions r are cell-centred, r = A^T (f - 1/2) for the
+ * fractional grid coordinates f. */
+typedef struct {
+    double dt;              /* time step (a.u. of time); negative propagates backwards */
+    int n_steps;            /* steps to take (>= 0) */
+    int n_corrector;        /* corrector passes per step (0..16): each solves the step again
+                               from psi(t) with (v_eff(t) + v_eff(t+dt)) / 2 of the last pass */
+    double solver_tol;      /* relative residual of each Crank-Nicolson solve; 0 = 1e-11 (FP64)
+                               or 1e-5 (FP32-mixed) */
+    int max_solver_iter;    /* CG iterations per solve; 0 = 200 */
+} ofdft_td_options;
+
+typedef struct {
+    int steps;              /* steps taken */
+    int evaluations;        /* v_eff evaluations */
+    int solver_iterations;  /* CG iterations over all solves */
+    double max_residual;    /* largest final relative residual of a solve */
+} ofdft_td_report;
+
+/* psi <- psi exp(i k.r) (the laser kick; k HOST double[3], 1/bohr).  precision: of psi.
+ * Enqueued on the handle's stream. */
+int ofdft_td_kick(ofdft_grid *g, void *psi_re, void *psi_im, const double k[3], int precision);
+
+/* Propagate psi (DEVICE re/im, in place) by n_steps Crank-Nicolson steps
+ * (1 + i dt/2 H) psi(t+dt) = (1 - i dt/2 H) psi(t) — the form that integrates i dpsi/dt = H psi;
+ * the paper prints the two signs exchanged, which with its kick exp(-ikx) is the complex
+ * conjugate of this scheme under exp(+ikx): the same density, dipole and spectrum.
+ * Each step is a predictor (v_eff at rho(t)) and n_corrector passes.  Each linear system is
+ * solved through its normal equations (1 + dt^2/4 H^2) x = (1 - i dt/2 H)^2 psi(t), real and
+ * imaginary parts by preconditioned CG (M = 1/(1 + dt^2/4 (G^2/2 + vbar)^2)).
+ * rho0: DEVICE [N] reference density for the dipole, or NULL (0).  dipole: HOST
+ * double[n_steps + 1][3] receiving delta mu(t_n) = sum_r r (|psi|^2 - rho0) dV, or NULL.
+ * Allocates 20 device fields of N elements (kept with the grid).  Returns
+ * OFDFT_ERR_NOT_CONVERGED (after all steps, report filled) if a solve reached max_solver_iter;
+ * otherwise as ofdft_energy_potential (the functional's PP term needs ions). */
+int ofdft_td_propagate(ofdft_grid *g, void *psi_re, void *psi_im, const void *rho0, const ofdft_functional *f,
+                       const ofdft_td_options *opt, double *dipole, ofdft_td_report *rep);
+
+/* Oscillator strength sigma(w) = w Im[delta mu~(w)] with delta mu~(w) = sum_n dmu_n
+ * e^{(i w - gamma) t_n} dt, t_n = n dt (HOST arrays: dmu[n], omega[n_omega] -> sigma[n_omega];
+ * dmu is the dipole component along the kick; gamma >= 0 damps the finite record). */
+int ofdft_td_spectrum(const double *dmu, int n, double dt, double gamma, int n_omega, const double *omega,
+                      double *sigma);
 
 /* Batched evaluation of n independent grids (snapshots), possibly of different
  * shapes: E_out HOST [n][OFDFT_N_ENERGIES]; V_dev[i] and F_out[i] may be NULL (F_out needs ions).

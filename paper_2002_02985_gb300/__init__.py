@@ -199,16 +199,50 @@ class Grid:
         _check(self.lib, st, self.h)
         return F
 
+    def td_kick(self, psi_re, psi_im, k):
+        """psi <- psi exp(i k.r) with cell-centred r (the kick of the TD-OFDFT section)."""
+        import torch
+        if psi_re.dtype not in (torch.float32, torch.float64) or psi_im.dtype != psi_re.dtype:
+            raise ValueError("psi_re and psi_im must both be float32 or both float64")
+        prec = L.FP64 if psi_re.dtype == torch.float64 else L.FP32_MIXED
+        f = Functional(precision=prec)
+        psi_re, psi_im = self._field(psi_re, f), self._field(psi_im, f)
+        kk = np.ascontiguousarray(np.asarray(k, dtype=np.float64))
+        _check(self.lib, self.lib.ofdft_td_kick(self.h, _ptr(psi_re), _ptr(psi_im),
+                                                kk.ctypes.data_as(ct.POINTER(ct.c_double)), prec), self.h)
+
+    def td_propagate(self, psi_re, psi_im, rho0, func: Functional, dt: float, n_steps: int, n_corrector: int = 1,
+                     solver_tol: float = 0.0, max_solver_iter: int = 0, want_dipole: bool = True,
+                     raise_on_not_converged: bool = True):
+        """Real-time TD-OFDFT (Eq. cn): psi_re/psi_im propagated in place.  Returns
+        (dipoles [n_steps + 1][3] or None, report dict)."""
+        opt = L.CTdOptions(dt, n_steps, n_corrector, solver_tol, max_solver_iter)
+        rep = L.CTdReport()
+        dip = np.zeros((n_steps + 1, 3)) if want_dipole else None
+        c, keep = func.to_c()
+        dp = dip.ctypes.data_as(ct.POINTER(ct.c_double)) if want_dipole else None
+        st = self.lib.ofdft_td_propagate(self.h, _ptr(self._field(psi_re, func)), _ptr(self._field(psi_im, func)),
+                                         _ptr(self._field(rho0, func)) if rho0 is not None else None, ct.byref(c),
+                                         ct.byref(opt), dp,
+                                         ct.byref(rep))
+        if st != L.OFDFT_OK and not (st == -6 and not raise_on_not_converged):
+            _check(self.lib, st, self.h)
+        del keep
+        return dip, dict(steps=rep.steps, evaluations=rep.evaluations, solver_iterations=rep.solver_iterations,
+                         max_residual=rep.max_residual, converged=(st == 0))
+
     def optimize_density(self, psi, func: Functional, n_electrons: float, tol_per_atom: float = 1e-6,
                          max_iter: int = 200, raise_on_not_converged: bool = False, method: str = "cg",
-                         precondition: bool = True, max_inner: int = 0, lbfgs_m: int = 0):
-        """Sec. 2.4's psi = sqrt(rho) optimisation in place on psi; method 'cg' | 'tn' | 'lbfgs'."""
+                         precondition: bool = True, max_inner: int = 0, lbfgs_m: int = 0, update: str = "rotate"):
+        """Sec. 2.4's psi = sqrt(rho) optimisation in place on psi; method 'cg' | 'tn' | 'lbfgs',
+        update 'rotate' | 'scale'."""
         methods = {"cg": L.OPT_CG, "tn": L.OPT_TN, "lbfgs": L.OPT_LBFGS}
-        if method not in methods:
-            raise ValueError("method must be one of %s" % sorted(methods))
+        updates = {"rotate": L.UPDATE_ROTATE, "scale": L.UPDATE_SCALE}
+        if method not in methods or update not in updates:
+            raise ValueError("method must be one of %s, update one of %s" % (sorted(methods), sorted(updates)))
         rep = L.COptReport()
         c, keep = func.to_c()
-        opt = L.COptOptions(methods[method], int(bool(precondition)), max_inner, lbfgs_m)
+        opt = L.COptOptions(methods[method], int(bool(precondition)), max_inner, lbfgs_m, updates[update])
         st = self.lib.ofdft_optimize_density_ex(self.h, _ptr(self._field(psi, func)), ct.byref(c), n_electrons,
                                                 tol_per_atom, max_iter, ct.byref(opt), ct.byref(rep))
         if st != L.OFDFT_OK and not (st == -6 and not raise_on_not_converged):
@@ -217,6 +251,19 @@ class Grid:
         return dict(converged=(st == 0), iterations=rep.iterations, evaluations=rep.evaluations,
                     energy=rep.energy, energies=dict(zip(ENERGY_KEYS, list(rep.energies))), mu=rep.mu,
                     residual=rep.residual, last_dE=rep.last_dE)
+
+
+def td_spectrum(dmu, dt: float, omega, gamma: float = 0.0):
+    """Oscillator strength sigma(w) = w Im sum_n dmu_n e^{(i w - gamma) n dt} dt (host C)."""
+    dmu = np.ascontiguousarray(np.asarray(dmu, dtype=np.float64))
+    omega = np.ascontiguousarray(np.asarray(omega, dtype=np.float64))
+    out = np.zeros_like(omega)
+    P = ct.POINTER(ct.c_double)
+    st = library().ofdft_td_spectrum(dmu.ctypes.data_as(P), len(dmu), dt, gamma, len(omega), omega.ctypes.data_as(P),
+                                     out.ctypes.data_as(P))
+    if st != L.OFDFT_OK:
+        raise ValueError("ofdft_td_spectrum: %s" % L.STATUS.get(st, st))
+    return out
 
 
 def optimize_density_multistep(grids, psi, func: Functional, n_electrons: float, tol_per_atom: float = 1e-6,

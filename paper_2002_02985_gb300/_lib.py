@@ -26,6 +26,7 @@ NLPOT_EXACT, NLPOT_INTERP = 0, 1
 KERNEL_LWT, KERNEL_WT_GLOBAL = 0, 1
 FP64, FP32_MIXED = 0, 1
 OPT_CG, OPT_TN, OPT_LBFGS = 0, 1, 2
+UPDATE_ROTATE, UPDATE_SCALE = 0, 1
 
 # symbols declared in include/ofdft.h (checked by the CPU test suite)
 EXPORTS = (
@@ -34,7 +35,8 @@ EXPORTS = (
     "ofdft_energy_potential_batched", "ofdft_status_string", "ofdft_last_error", "ofdft_version",
     "ofdft_profile_enable", "ofdft_profile_reset", "ofdft_profile_read",
     "ofdft_tf_energy_potential_noalloc", "ofdft_set_ions_pme", "ofdft_ewald", "ofdft_interpolate",
-    "ofdft_optimize_density_multistep", "ofdft_optimize_density_ex",
+    "ofdft_optimize_density_multistep", "ofdft_optimize_density_ex", "ofdft_td_kick", "ofdft_td_propagate",
+    "ofdft_td_spectrum",
 )
 NOALLOC_MAX_POINTS = 8388608
 
@@ -61,7 +63,18 @@ class COptReport(ct.Structure):
 
 
 class COptOptions(ct.Structure):
-    _fields_ = [("method", ct.c_int), ("precondition", ct.c_int), ("max_inner", ct.c_int), ("lbfgs_m", ct.c_int)]
+    _fields_ = [("method", ct.c_int), ("precondition", ct.c_int), ("max_inner", ct.c_int), ("lbfgs_m", ct.c_int),
+                ("update", ct.c_int)]
+
+
+class CTdOptions(ct.Structure):
+    _fields_ = [("dt", ct.c_double), ("n_steps", ct.c_int), ("n_corrector", ct.c_int), ("solver_tol", ct.c_double),
+                ("max_solver_iter", ct.c_int)]
+
+
+class CTdReport(ct.Structure):
+    _fields_ = [("steps", ct.c_int), ("evaluations", ct.c_int), ("solver_iterations", ct.c_int),
+                ("max_residual", ct.c_double)]
 
 
 _lib = None
@@ -90,6 +103,10 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.ofdft_optimize_density.argtypes = [P, V, ct.POINTER(CFunctional), D, D, I, ct.POINTER(COptReport)]
     lib.ofdft_optimize_density_ex.argtypes = [P, V, ct.POINTER(CFunctional), D, D, I, ct.POINTER(COptOptions),
                                               ct.POINTER(COptReport)]
+    lib.ofdft_td_kick.argtypes = [P, V, V, ct.POINTER(D), I]
+    lib.ofdft_td_propagate.argtypes = [P, V, V, V, ct.POINTER(CFunctional), ct.POINTER(CTdOptions), ct.POINTER(D),
+                                       ct.POINTER(CTdReport)]
+    lib.ofdft_td_spectrum.argtypes = [ct.POINTER(D), I, D, D, I, ct.POINTER(D), ct.POINTER(D)]
     lib.ofdft_energy_potential_batched.argtypes = [I, ct.POINTER(P), ct.POINTER(V), ct.POINTER(CFunctional),
                                                    ct.POINTER(D), ct.POINTER(V), ct.POINTER(ct.POINTER(D))]
     lib.ofdft_profile_enable.argtypes = [P, I]

@@ -73,6 +73,7 @@ template <typename T> struct Workspace {
     unsigned *ticket = nullptr;       // stats completion counter
     T *opt = nullptr;                 // optimiser fields (8 * N), allocated on demand
     T *opt_ext = nullptr;             // TN / L-BFGS fields (opt_ext_fields * N), on demand
+    T *td = nullptr;                  // TD-OFDFT fields (20 * N), on demand
     int opt_ext_fields = 0;
     LaunchSet ks;                     // FFT-carrying kernels (size-specialised where compiled)
     int Brow = 0, thr_rowf = 0, thr_rowi = 0, TW1 = 0, thr_p1 = 0, TW0 = 0, thr_ax0 = 0, nb_row = 0, nb_ax0 = 0;
@@ -303,6 +304,7 @@ template <typename T> void free_ws(Workspace<T> &w) {
     cudaFree(w.ticket);
     cudaFree(w.opt);
     cudaFree(w.opt_ext);
+    cudaFree(w.td);
     w = Workspace<T>();
 }
 
@@ -899,7 +901,7 @@ int ewald_impl(ofdft_grid *g, double *E_out, double *F_out) {
 template <typename T>
 int optimize_impl(ofdft_grid *g, T *psi, const ofdft_functional *f0, double Ne, double tol, int max_iter,
                   const ofdft_opt_options &o, ofdft_opt_report *rep);
-const ofdft_opt_options kOptDefaults = {OFDFT_OPT_CG, 1, 0, 0};
+const ofdft_opt_options kOptDefaults = {OFDFT_OPT_CG, 1, 0, 0, OFDFT_UPDATE_ROTATE};
 
 // ---------------------------------------------------------------- Fourier interpolation between grids
 bool same_cell(const ofdft_grid *a, const ofdft_grid *b) {
@@ -1019,6 +1021,7 @@ int optimize_impl(ofdft_grid *g, T *psi, const ofdft_functional *f0, double Ne, 
     typedef typename Vec2<T>::type C;
     const char *env_pc = std::getenv("OFDFT_OPT_PRECOND");
     const bool precond = o.precondition && !(env_pc && env_pc[0] == '0');
+    const bool scale_upd = o.update == OFDFT_UPDATE_SCALE;
     const double rho_m = Ne / g->omega;
     const double pa = 70.0 / 9.0 * kCTF * std::pow(rho_m, 2.0 / 3.0), pb = 16.0 * kPi * rho_m;
     double bv[9];
@@ -1224,27 +1227,47 @@ int optimize_impl(ofdft_grid *g, T *psi, const ofdft_functional *f0, double Ne, 
             zg_prev = zg;
             have_dir = true;
         }
-        // p = d - (<d,psi>/<psi,psi>) psi, normalised to N_e
+        // rotation: p = d - (<d,psi>/<psi,psi>) psi; scaling: p = d; then normalised to N_e
         CK(launch_copy<T>(p, d, N, s), "copy");
-        const double dpsi = dv.dot(d, psi);
-        CK(launch_axpby<T>(p, psi, -dpsi / pp, 1.0, N, s), "axpby");
+        if (!scale_upd) CK(launch_axpby<T>(p, psi, -dv.dot(d, psi) / pp, 1.0, N, s), "axpby");
         const double pn = dv.dot(p, p) * g->dV;
         if (!(pn > 0.0)) break;
         CK(launch_axpby<T>(p, psi, 0.0, std::sqrt(Ne / pn), N, s), "axpby");
         const double phi0 = E[0];
-        // dE/dlambda at 0 = sum dE/dpsi p = sum 2 psi V dV p
-        const double dphi0 = 2.0 * g->dV * dv.dot(psi, V, p);
+        // dE/dlambda at 0 = <g, p> with the projected gradient g (either update)
+        const double dphi0 = dv.dot(grad, p);
         if (dphi0 >= 0.0) {
             have_dir = false;
             forget();
             if (++restarts > 3) break;
             continue;
         }
+        // the trial point psi_l (and rho = psi_l^2) at step lam; c, n: the scaling's factor
+        auto trial = [&](double lam, double &c, double &n) -> int {
+            if (!scale_upd) {
+                CK(launch_rotate<T>(psil, rho, psi, p, std::cos(lam), std::sin(lam), N, s), "rotate");
+                return OFDFT_OK;
+            }
+            // psi_t = c (psi + t p), c = sqrt(N_e / n), n = int (psi + t p)^2
+            CK(launch_rotate<T>(psil, rho, psi, p, 1.0, lam, N, s), "step");
+            n = dv.dot(psil, psil) * g->dV;
+            c = std::sqrt(Ne / n);
+            CK(launch_square<T>(rho, psil, c, N, s), "renormalise");
+            return OFDFT_OK;
+        };
         auto phi = [&](double lam, double *El, double &dl) -> int {
-            CK(launch_rotate<T>(psil, rho, psi, p, std::cos(lam), std::sin(lam), N, s), "rotate");
-            int r = eval_sync<T>(g, rho, &f, V, El);
+            double c = 1.0, n = Ne;
+            int r = trial(lam, c, n);
+            if (r) return r;
+            r = eval_sync<T>(g, rho, &f, V, El);
             evals++;
             if (r) return r;
+            if (scale_upd) {
+                // d psi_t/dt = c p - (int (psi + t p) p / n) psi_t, int (psi + t p) p = <psi_t, p> dV / c
+                const double qp = dv.dot(psil, p) * g->dV / c;
+                dl = 2.0 * g->dV * (c * dv.dot(psil, V, p) - (qp / n) * dv.dot(psil, psil, V));
+                return OFDFT_OK;
+            }
             // dpsi/dlambda = -psi sin + p cos into tmp (grad is free scratch here)
             CK(launch_rotate<T>(tmp, grad, psi, p, -std::sin(lam), std::cos(lam), N, s), "rotate");
             dl = 2.0 * g->dV * dv.dot(psil, V, tmp);
@@ -1252,7 +1275,9 @@ int optimize_impl(ofdft_grid *g, T *psi, const ofdft_functional *f0, double Ne, 
         };
         double lam_lo = 0.0, f_lo = phi0, d_lo = dphi0, lam_hi = -1.0, f_hi = 0.0, d_hi = 0.0;
         // a curvature-built step has a length: psi + x_perp lies on the rotation at atan(|x_perp|/|psi|)
-        double lam = std::min(std::max(newton ? std::atan(std::sqrt(pn / Ne)) : lam_prev, 1e-4), 0.5);
+        // (scaling: psi + d is reached at t = |d| / |psi|)
+        const double step0 = scale_upd ? std::sqrt(pn / Ne) : std::atan(std::sqrt(pn / Ne));
+        double lam = std::min(std::max(newton ? step0 : lam_prev, 1e-4), 0.5);
         double best_f = 1e300, best_lam = 0.0;
         for (int ls = 0; ls < 10; ls++) {
             double El[E_NUM], dl;
@@ -1288,8 +1313,11 @@ int optimize_impl(ofdft_grid *g, T *psi, const ofdft_functional *f0, double Ne, 
         }
         restarts = 0;
         lam_prev = best_lam;
-        // accept: psi <- psi cos + p sin, and V at the accepted point
-        CK(launch_rotate<T>(psil, rho, psi, p, std::cos(best_lam), std::sin(best_lam), N, s), "rotate");
+        // accept: psi <- the trial point at best_lam, and V at the accepted point
+        {
+            double c, n;
+            if ((rc = trial(best_lam, c, n))) return rc;
+        }
         if (method == OFDFT_OPT_LBFGS) {            // s = psi_new - psi
             CK(launch_copy<T>(Sk(l_head), psil, N, s), "copy");
             CK(launch_axpby<T>(Sk(l_head), psi, -1.0, 1.0, N, s), "axpby");
@@ -1325,6 +1353,192 @@ int optimize_impl(ofdft_grid *g, T *psi, const ofdft_functional *f0, double Ne, 
         rep->last_dE = last_dE;
     }
     return small >= 3 ? OFDFT_OK : OFDFT_ERR_NOT_CONVERGED;
+}
+
+// ---------------------------------------------------------------- real-time TD-OFDFT
+// H psi = -lap psi / 2 + v_eff psi with v_eff = d(E - T_vW)/drho; each Crank-Nicolson step
+// (1 + i tau H) psi(t+dt) = (1 - i tau H) psi(t), tau = dt/2, is solved through its normal
+// equations (1 + tau^2 H^2) x = (1 - i tau H)^2 psi(t): H is real, so the real and imaginary
+// parts are two real symmetric positive definite systems, solved together by preconditioned
+// CG with M = 1 / (1 + tau^2 (G^2/2 + vbar)^2) diagonal in G.
+constexpr int kTdFields = 20;
+
+template <typename T>
+int td_impl(ofdft_grid *g, T *pre, T *pim, const T *rho0, const ofdft_functional *f0, const ofdft_td_options &o,
+            double *dip, ofdft_td_report *rep) {
+    typedef typename Vec2<T>::type C;
+    const long long N = g->N;
+    int rc = ensure_ws<T>(g, 3);
+    if (rc) return rc;
+    Workspace<T> &w = ws<T>(g);
+    if (!w.td) CK(cudaMalloc(&w.td, (size_t)kTdFields * (size_t)N * sizeof(T)), "cudaMalloc TD fields");
+    T *F[kTdFields];
+    for (int k = 0; k < kTdFields; k++) F[k] = w.td + (size_t)k * (size_t)N;
+    T *p0[2] = {F[0], F[1]};           // psi(t)
+    T *c[2] = {F[2], F[3]};            // right-hand sides
+    T *r[2] = {F[4], F[5]}, *z[2] = {F[6], F[7]}, *q[2] = {F[8], F[9]}, *Aq[2] = {F[10], F[11]};
+    T *h1 = F[12], *hp[2] = {F[13], F[14]};
+    T *vt = F[15], *vn = F[16], *vm = F[17], *rho = F[18];
+    T *x[2] = {pre, pim};
+    Dev<T> dv{g, &w};
+    cudaStream_t s = g->stream;
+    double bv[9];
+    for (int i = 0; i < 9; i++) bv[i] = 2.0 * kPi * g->recip[i];
+    TdCell cell;
+    for (int i = 0; i < 9; i++) cell.a[i] = g->cell[i];
+    ofdft_functional f = *f0;
+    f.terms &= ~(unsigned)OFDFT_TERM_VW;
+    const bool have_v = f.terms != 0;
+    const double tol = o.solver_tol > 0.0 ? o.solver_tol : (sizeof(T) == 8 ? 1e-11 : 1e-5);
+    const int max_it = o.max_solver_iter > 0 ? o.max_solver_iter : 200;
+    const double tau = 0.5 * o.dt;
+    int evals = 0, cg_total = 0;
+    double max_res = 0.0;
+    bool all_conv = true;
+    double Ed[E_NUM];
+    const int n0 = g->n[0], n1 = g->n[1], n2 = g->n[2];
+
+    auto veff = [&](T *v) -> int {      // v_eff at rho = |x|^2 (rho kept for vbar)
+        CK(launch_abs2<T>(rho, x[0], x[1], N, s), "density");
+        if (!have_v) {
+            CK(cudaMemsetAsync(v, 0, (size_t)N * sizeof(T), s), "memset");
+            return OFDFT_OK;
+        }
+        int e = eval_sync<T>(g, rho, &f, v, Ed);
+        evals++;
+        return e;
+    };
+    auto apply_h = [&](const T *u, const T *v, T *out) -> int {   // out = K u + v u
+        int e = forward_plain<T>(g, w, u);
+        if (e) return e;
+        CK(launch_spectral_factor<C>((C *)w.chan, n0, n1, n2, bv, 0, 0.0, 0.0, s), "kinetic");
+        if ((e = inverse_plain<T>(g, w, 0, out, u))) return e;
+        CK(launch_add_vu<T>(out, v, u, 1.0, 1.0, N, s), "potential");
+        return OFDFT_OK;
+    };
+    auto apply_a = [&](const T *u, const T *v, T *out) -> int {   // out = (1 + tau^2 H^2) u
+        int e = apply_h(u, v, h1);
+        if (e || (e = apply_h(h1, v, out))) return e;
+        CK(launch_axpby<T>(out, u, 1.0, tau * tau, N, s), "axpby");
+        return OFDFT_OK;
+    };
+    double vbar = 0.0;
+    auto apply_m = [&](const T *u, T *out) -> int {              // out = M u
+        int e = forward_plain<T>(g, w, u);
+        if (e) return e;
+        CK(launch_spectral_factor<C>((C *)w.chan, n0, n1, n2, bv, 1, tau, vbar, s), "preconditioner");
+        if ((e = inverse_plain<T>(g, w, 0, out, u))) return e;
+        const double a0 = tau * vbar;
+        CK(launch_add_scaled_scalar<T>(out, w.scal + S_RHO_MEAN, 1.0 / (1.0 + a0 * a0), N, s), "mean");
+        return OFDFT_OK;
+    };
+    // x <- psi(t + dt) for the Hamiltonian with potential v, x holding the initial guess
+    auto cn_solve = [&](const T *v) -> int {
+        int e;
+        vbar = 0.0;
+        if (have_v) {   // v weighted by the density held in rho (any vbar gives the same solution)
+            const double sr = dv.dot(rho, rho) > 0.0 ? dv.dot(x[0], x[0]) + dv.dot(x[1], x[1]) : 0.0;
+            if (sr > 0.0) vbar = dv.dot(rho, v) / sr;
+        }
+        // c = (1 - i tau H)^2 psi(t):  c_re = p_re + 2 tau H p_im - tau^2 H^2 p_re,
+        //                               c_im = p_im - 2 tau H p_re - tau^2 H^2 p_im
+        for (int j = 0; j < 2; j++)
+            if ((e = apply_h(p0[j], v, hp[j]))) return e;
+        for (int j = 0; j < 2; j++) {
+            if ((e = apply_h(hp[j], v, c[j]))) return e;
+            CK(launch_axpby<T>(c[j], p0[j], 1.0, -tau * tau, N, s), "axpby");
+            CK(launch_axpby<T>(c[j], hp[1 - j], j == 0 ? 2.0 * tau : -2.0 * tau, 1.0, N, s), "axpby");
+        }
+        double nc[2], rz[2];
+        bool done[2];
+        int its = 0;
+        for (int j = 0; j < 2; j++) {
+            nc[j] = std::sqrt(dv.dot(c[j], c[j]));
+            done[j] = !(nc[j] > 0.0);
+            if (done[j]) {
+                CK(cudaMemsetAsync(x[j], 0, (size_t)N * sizeof(T), s), "memset");
+                continue;
+            }
+            if ((e = apply_a(x[j], v, r[j]))) return e;
+            CK(launch_axpby<T>(r[j], c[j], 1.0, -1.0, N, s), "axpby");      // r = c - A x
+            if (std::sqrt(dv.dot(r[j], r[j])) <= tol * nc[j]) {
+                done[j] = true;
+                continue;
+            }
+            if ((e = apply_m(r[j], z[j]))) return e;
+            CK(launch_copy<T>(q[j], z[j], N, s), "copy");
+            rz[j] = dv.dot(r[j], z[j]);
+        }
+        double res = 0.0;
+        while (!(done[0] && done[1]) && its < max_it) {
+            its++;
+            for (int j = 0; j < 2; j++) {
+                if (done[j]) continue;
+                if ((e = apply_a(q[j], v, Aq[j]))) return e;
+                const double qAq = dv.dot(q[j], Aq[j]);
+                if (!(qAq > 0.0)) {
+                    done[j] = true;
+                    continue;
+                }
+                const double a = rz[j] / qAq;
+                CK(launch_axpby<T>(x[j], q[j], a, 1.0, N, s), "axpby");
+                CK(launch_axpby<T>(r[j], Aq[j], -a, 1.0, N, s), "axpby");
+                const double rn = std::sqrt(dv.dot(r[j], r[j])) / nc[j];
+                if (rn <= tol) {
+                    done[j] = true;
+                    res = std::max(res, rn);
+                    continue;
+                }
+                if ((e = apply_m(r[j], z[j]))) return e;
+                const double rz_new = dv.dot(r[j], z[j]);
+                CK(launch_axpby<T>(q[j], z[j], 1.0, rz_new / rz[j], N, s), "axpby");
+                rz[j] = rz_new;
+            }
+        }
+        if (!(done[0] && done[1])) {
+            all_conv = false;
+            for (int j = 0; j < 2; j++)
+                if (!done[j]) res = std::max(res, std::sqrt(dv.dot(r[j], r[j])) / nc[j]);
+        }
+        cg_total += its;
+        max_res = std::max(max_res, res);
+        return OFDFT_OK;
+    };
+    auto dipole = [&](double *out) -> int {
+        if (!out) return OFDFT_OK;
+        CK(launch_dipole<T>(x[0], x[1], rho0, n0, n1, n2, cell, g->dV, w.part_misc + 2560, 384, w.part_misc + 3840, s),
+           "dipole");
+        CK(cudaMemcpyAsync(g->h_pinned + 44, w.part_misc + 3840, 3 * sizeof(double), cudaMemcpyDeviceToHost, s),
+           "copy dipole");
+        CK(cudaStreamSynchronize(s), "stream synchronize");
+        for (int k = 0; k < 3; k++) out[k] = g->h_pinned[44 + k];
+        return OFDFT_OK;
+    };
+
+    if ((rc = veff(vt))) return rc;
+    if ((rc = dipole(dip))) return rc;
+    int step = 0;
+    for (; step < o.n_steps; step++) {
+        for (int j = 0; j < 2; j++) CK(launch_copy<T>(p0[j], x[j], N, s), "copy");
+        if ((rc = cn_solve(vt))) return rc;                 // predictor
+        if ((rc = veff(vn))) return rc;
+        for (int k = 0; k < o.n_corrector; k++) {           // correctors: mean of the two potentials
+            CK(launch_copy<T>(vm, vt, N, s), "copy");
+            CK(launch_axpby<T>(vm, vn, 0.5, 0.5, N, s), "axpby");
+            if ((rc = cn_solve(vm))) return rc;
+            if ((rc = veff(vn))) return rc;
+        }
+        std::swap(vt, vn);
+        if ((rc = dipole(dip ? dip + 3 * (size_t)(step + 1) : nullptr))) return rc;
+    }
+    CK(cudaStreamSynchronize(s), "stream synchronize");
+    if (rep) {
+        rep->steps = step;
+        rep->evaluations = evals;
+        rep->solver_iterations = cg_total;
+        rep->max_residual = max_res;
+    }
+    return all_conv ? OFDFT_OK : fail(g, OFDFT_ERR_NOT_CONVERGED, "a Crank-Nicolson solve reached max_solver_iter");
 }
 
 // ---------------------------------------------------------------- batched evaluation
@@ -1780,6 +1994,50 @@ int ofdft_interpolate(ofdft_grid *from, const void *src_dev, ofdft_grid *to, voi
     return OFDFT_OK;
 }
 
+int ofdft_td_kick(ofdft_grid *g, void *psi_re, void *psi_im, const double k[3], int precision) {
+    if (!g) return OFDFT_ERR_INVALID_ARG;
+    if (!psi_re || !psi_im || !k) return fail(g, OFDFT_ERR_INVALID_ARG, "psi or k is NULL");
+    TdCell cell;
+    for (int i = 0; i < 9; i++) cell.a[i] = g->cell[i];
+    if (precision == OFDFT_FP64)
+        CK(launch_kick<double>((double *)psi_re, (double *)psi_im, g->n[0], g->n[1], g->n[2], cell, k, g->stream), "kick");
+    else if (precision == OFDFT_FP32_MIXED)
+        CK(launch_kick<float>((float *)psi_re, (float *)psi_im, g->n[0], g->n[1], g->n[2], cell, k, g->stream), "kick");
+    else
+        return fail(g, OFDFT_ERR_INVALID_ARG, "unknown precision");
+    return OFDFT_OK;
+}
+
+int ofdft_td_propagate(ofdft_grid *g, void *psi_re, void *psi_im, const void *rho0, const ofdft_functional *f,
+                       const ofdft_td_options *opt, double *dipole, ofdft_td_report *rep) {
+    if (!g) return OFDFT_ERR_INVALID_ARG;
+    if (!psi_re || !psi_im || !opt) return fail(g, OFDFT_ERR_INVALID_ARG, "psi or options NULL");
+    if (!(std::isfinite(opt->dt) && opt->dt != 0.0) || opt->n_steps < 0 || opt->n_corrector < 0 ||
+        opt->n_corrector > 16 || opt->max_solver_iter < 0 || !(opt->solver_tol >= 0.0))
+        return fail(g, OFDFT_ERR_INVALID_ARG, "TD options");
+    int rc = check_functional(g, f);
+    if (rc) return rc;
+    if (f->precision == OFDFT_FP64)
+        return td_impl<double>(g, (double *)psi_re, (double *)psi_im, (const double *)rho0, f, *opt, dipole, rep);
+    return td_impl<float>(g, (float *)psi_re, (float *)psi_im, (const float *)rho0, f, *opt, dipole, rep);
+}
+
+int ofdft_td_spectrum(const double *dmu, int n, double dt, double gamma, int n_omega, const double *omega,
+                      double *sigma) {
+    if (!dmu || !omega || !sigma || n < 1 || n_omega < 0 || !(dt != 0.0) || !(gamma >= 0.0))
+        return OFDFT_ERR_INVALID_ARG;
+    for (int m = 0; m < n_omega; m++) {
+        // Im sum_n dmu_n e^{(i w - gamma) t_n} dt, the phase kept in [0, 2 pi) for accuracy
+        double im = 0.0;
+        for (int k = 0; k < n; k++) {
+            const double t = k * dt;
+            im += dmu[k] * std::exp(-gamma * t) * std::sin(std::fmod(omega[m] * t, 2.0 * kPi));
+        }
+        sigma[m] = omega[m] * im * dt;
+    }
+    return OFDFT_OK;
+}
+
 int ofdft_optimize_density_multistep(int n_levels, ofdft_grid *const *grids, void *psi_dev, const ofdft_functional *f,
                                      double N_e, double tol_E_per_atom, int max_iter, ofdft_opt_report *rep) {
     if (n_levels < 1 || !grids) return OFDFT_ERR_INVALID_ARG;
@@ -1807,7 +2065,7 @@ int ofdft_optimize_density_ex(ofdft_grid *g, void *psi_dev, const ofdft_function
     if (!psi_dev || !(N_e > 0.0) || max_iter < 1) return fail(g, OFDFT_ERR_INVALID_ARG, "psi, N_e or max_iter");
     const ofdft_opt_options o = opt ? *opt : kOptDefaults;
     if (o.method < OFDFT_OPT_CG || o.method > OFDFT_OPT_LBFGS || o.max_inner < 0 || o.max_inner > 100 ||
-        o.lbfgs_m < 0 || o.lbfgs_m > 32)
+        o.lbfgs_m < 0 || o.lbfgs_m > 32 || o.update < OFDFT_UPDATE_ROTATE || o.update > OFDFT_UPDATE_SCALE)
         return fail(g, OFDFT_ERR_INVALID_ARG, "optimiser options");
     int rc = check_functional(g, f);
     if (rc) return rc;

@@ -74,6 +74,29 @@ cudaError_t launch_spectral_map(const C *src, int f0, int f1, int f2, C *dst, in
 template <typename T>
 cudaError_t launch_hvp(T *Hq, const T *psi, const T *q, const T *V, const T *Vq, double e, double mu, double dV,
                        long long N, cudaStream_t s);
+// ---- real-time TD-OFDFT
+struct TdCell {
+    double a[9];      // lattice vectors (rows), bohr
+};
+// h(G) *= G^2/2 (mode 0) or 1 / (1 + tau^2 (G^2/2 + vbar)^2) (mode 1), normalised half spectrum
+template <typename C>
+cudaError_t launch_spectral_factor(C *h, int n0, int n1, int n2, const double *bvec, int mode, double tau, double vbar,
+                                   cudaStream_t s);
+// out = a out + b v u
+template <typename T>
+cudaError_t launch_add_vu(T *out, const T *v, const T *u, double a, double b, long long N, cudaStream_t s);
+// rho = re^2 + im^2
+template <typename T> cudaError_t launch_abs2(T *rho, const T *re, const T *im, long long N, cudaStream_t s);
+// x += f c[0]
+template <typename T>
+cudaError_t launch_add_scaled_scalar(T *x, const double *c, double f, long long N, cudaStream_t s);
+// psi <- psi exp(i k . r), r = A^T (f - 1/2) the cell-centred position
+template <typename T>
+cudaError_t launch_kick(T *re, T *im, int n0, int n1, int n2, const TdCell &c, const double *k, cudaStream_t s);
+// out[0..2] = sum_r r (|psi|^2 - rho0) dV (rho0 may be NULL); part holds 3 nblk partials
+template <typename T>
+cudaError_t launch_dipole(const T *re, const T *im, const T *rho0, int n0, int n1, int n2, const TdCell &c, double dV,
+                          double *part, int nblk, double *out, cudaStream_t s);
 // x += c[0] (c a device scalar)
 template <typename T> cudaError_t launch_add_scalar(T *x, const double *c, long long N, cudaStream_t s);
 // optimiser preconditioner on a normalised half spectrum: h(G) *= a G^2 / (G^4 + a G^2 + b), h(0) kept

@@ -591,7 +591,163 @@ cudaError_t launch_hvp(T *Hq, const T *psi, const T *q, const T *V, const T *Vq,
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- real-time TD-OFDFT
+// h(G) *= f(G) on a normalised half spectrum: MODE 0 the kinetic K = G^2/2 (K(0) = 0),
+// MODE 1 the Crank-Nicolson normal-equation preconditioner 1 / (1 + tau^2 (G^2/2 + vbar)^2)
+template <typename C, int MODE>
+__global__ void spectral_factor_kernel(C *h, int n0, int n1, int n2, double b0, double b1, double b2, double b3,
+                                       double b4, double b5, double b6, double b7, double b8, double tau,
+                                       double vbar) {
+    const int n2h = n2 / 2 + 1;
+    const long long NH = (long long)n0 * n1 * n2h, stride = (long long)gridDim.x * blockDim.x;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < NH; e += stride) {
+        const int k2 = (int)(e % n2h);
+        const long long r = e / n2h;
+        const int k1 = (int)(r % n1), k0 = (int)(r / n1);
+        const double m0 = (k0 <= n0 / 2) ? k0 : k0 - n0, m1 = (k1 <= n1 / 2) ? k1 : k1 - n1, m2 = k2;
+        const double gx = m0 * b0 + m1 * b3 + m2 * b6, gy = m0 * b1 + m1 * b4 + m2 * b7, gz = m0 * b2 + m1 * b5 + m2 * b8;
+        const double kin = 0.5 * (gx * gx + gy * gy + gz * gz);
+        double f;
+        if (MODE == 0) {
+            f = kin;
+        } else {
+            const double a = tau * (kin + vbar);
+            f = 1.0 / (1.0 + a * a);
+        }
+        C v = h[e];
+        v.x = (decltype(v.x))(v.x * f);
+        v.y = (decltype(v.y))(v.y * f);
+        h[e] = v;
+    }
+}
+template <typename C>
+cudaError_t launch_spectral_factor(C *h, int n0, int n1, int n2, const double *bv, int mode, double tau, double vbar,
+                                   cudaStream_t s) {
+    if (mode == 0)
+        spectral_factor_kernel<C, 0><<<1216, 256, 0, s>>>(h, n0, n1, n2, bv[0], bv[1], bv[2], bv[3], bv[4], bv[5],
+                                                         bv[6], bv[7], bv[8], tau, vbar);
+    else
+        spectral_factor_kernel<C, 1><<<1216, 256, 0, s>>>(h, n0, n1, n2, bv[0], bv[1], bv[2], bv[3], bv[4], bv[5],
+                                                         bv[6], bv[7], bv[8], tau, vbar);
+    return cudaGetLastError();
+}
+template cudaError_t launch_spectral_factor<float2>(float2 *, int, int, int, const double *, int, double, double,
+                                                    cudaStream_t);
+template cudaError_t launch_spectral_factor<double2>(double2 *, int, int, int, const double *, int, double, double,
+                                                     cudaStream_t);
+
+// out = a out + b v u
+template <typename T> __global__ void add_vu_kernel(T *out, const T *v, const T *u, T a, T b, long long N) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += stride)
+        out[i] = a * out[i] + b * v[i] * u[i];
+}
+template <typename T>
+cudaError_t launch_add_vu(T *out, const T *v, const T *u, double a, double b, long long N, cudaStream_t s) {
+    add_vu_kernel<T><<<1216, 256, 0, s>>>(out, v, u, (T)a, (T)b, N);
+    return cudaGetLastError();
+}
+
+// rho = re^2 + im^2
+template <typename T> __global__ void abs2_kernel(T *rho, const T *re, const T *im, long long N) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += stride)
+        rho[i] = re[i] * re[i] + im[i] * im[i];
+}
+template <typename T> cudaError_t launch_abs2(T *rho, const T *re, const T *im, long long N, cudaStream_t s) {
+    abs2_kernel<T><<<1216, 256, 0, s>>>(rho, re, im, N);
+    return cudaGetLastError();
+}
+
+// x += f c[0]
+template <typename T> __global__ void add_scaled_scalar_kernel(T *x, const double *c, double f, long long N) {
+    const T v = (T)(f * c[0]);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += stride) x[i] += v;
+}
+template <typename T>
+cudaError_t launch_add_scaled_scalar(T *x, const double *c, double f, long long N, cudaStream_t s) {
+    add_scaled_scalar_kernel<T><<<1216, 256, 0, s>>>(x, c, f, N);
+    return cudaGetLastError();
+}
+
+// cell-centred Cartesian position of grid point i: r = A^T (f - 1/2), f = (i0/n0, i1/n1, i2/n2)
+__device__ __forceinline__ void centred_position(long long i, int n0, int n1, int n2, const TdCell &c, double &x,
+                                                 double &y, double &z) {
+    const int i2 = (int)(i % n2);
+    const long long r = i / n2;
+    const int i1 = (int)(r % n1), i0 = (int)(r / n1);
+    const double f0 = (double)i0 / n0 - 0.5, f1 = (double)i1 / n1 - 0.5, f2 = (double)i2 / n2 - 0.5;
+    x = f0 * c.a[0] + f1 * c.a[3] + f2 * c.a[6];
+    y = f0 * c.a[1] + f1 * c.a[4] + f2 * c.a[7];
+    z = f0 * c.a[2] + f1 * c.a[5] + f2 * c.a[8];
+}
+
+// psi <- psi exp(i k . r)
+template <typename T>
+__global__ void kick_kernel(T *re, T *im, int n0, int n1, int n2, TdCell c, double kx, double ky, double kz,
+                            long long N) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += stride) {
+        double x, y, z;
+        centred_position(i, n0, n1, n2, c, x, y, z);
+        double sn, cs;
+        sincos(kx * x + ky * y + kz * z, &sn, &cs);
+        const double a = (double)re[i], b = (double)im[i];
+        re[i] = (T)(a * cs - b * sn);
+        im[i] = (T)(a * sn + b * cs);
+    }
+}
+template <typename T>
+cudaError_t launch_kick(T *re, T *im, int n0, int n1, int n2, const TdCell &c, const double *k, cudaStream_t s) {
+    kick_kernel<T><<<1216, 256, 0, s>>>(re, im, n0, n1, n2, c, k[0], k[1], k[2], (long long)n0 * n1 * n2);
+    return cudaGetLastError();
+}
+
+// partials of sum_r r (|psi|^2 - rho0) dV: part[3 b + k], then the three sums into out[0..2]
+template <typename T>
+__global__ void __launch_bounds__(256) dipole_kernel(const T *re, const T *im, const T *rho0, int n0, int n1, int n2,
+                                                     TdCell c, double dV, long long N, double *part) {
+    __shared__ double sd[3 * 32];
+    double acc[3] = {0.0, 0.0, 0.0};
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += stride) {
+        double x, y, z;
+        centred_position(i, n0, n1, n2, c, x, y, z);
+        const double a = (double)re[i], b = (double)im[i];
+        const double d = a * a + b * b - (rho0 ? (double)rho0[i] : 0.0);
+        acc[0] += x * d;
+        acc[1] += y * d;
+        acc[2] += z * d;
+    }
+    block_sum_n<3>(acc, sd);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 3; k++) part[3 * blockIdx.x + k] = acc[k] * dV;
+}
+__global__ void __launch_bounds__(256) sum3_partials_kernel(const double *part, int n, double *out) {
+    __shared__ double sd[3 * 32];
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        for (int k = 0; k < 3; k++) acc[k] += part[3 * i + k];
+    block_sum_n<3>(acc, sd);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 3; k++) out[k] = acc[k];
+}
+template <typename T>
+cudaError_t launch_dipole(const T *re, const T *im, const T *rho0, int n0, int n1, int n2, const TdCell &c, double dV,
+                          double *part, int nblk, double *out, cudaStream_t s) {
+    dipole_kernel<T><<<nblk, 256, 0, s>>>(re, im, rho0, n0, n1, n2, c, dV, (long long)n0 * n1 * n2, part);
+    sum3_partials_kernel<<<1, 256, 0, s>>>(part, nblk, out);
+    return cudaGetLastError();
+}
+
 #define INST(T)                                                                                              \
+    template cudaError_t launch_add_vu<T>(T *, const T *, const T *, double, double, long long, cudaStream_t); \
+    template cudaError_t launch_abs2<T>(T *, const T *, const T *, long long, cudaStream_t);                 \
+    template cudaError_t launch_add_scaled_scalar<T>(T *, const double *, double, long long, cudaStream_t);  \
+    template cudaError_t launch_kick<T>(T *, T *, int, int, int, const TdCell &, const double *, cudaStream_t); \
+    template cudaError_t launch_dipole<T>(const T *, const T *, const T *, int, int, int, const TdCell &,     \
+                                          double, double *, int, double *, cudaStream_t);                    \
     template cudaError_t launch_hvp<T>(T *, const T *, const T *, const T *, const T *, double, double,      \
                                        double, long long, cudaStream_t);                                     \
     template cudaError_t launch_add_scalar<T>(T *, const double *, long long, cudaStream_t);                  \
