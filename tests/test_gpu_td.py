@@ -106,34 +106,46 @@ def _cluster():
     return og, cell, pos, rho0
 
 
+# (oracle terms, library terms, PP, density floor).  The LWT case starts from the blob
+# floored at 1e-8 (as the Mg147 workload's density): on the raw blob (rho down to 1e-27,
+# knots recomputed from min/max rho at every evaluation) the trajectory amplifies the
+# linear solves' residuals about 1e4 times (GPU vs oracle: 9e-8 at solver_tol 1e-11,
+# 8e-10 at 1e-13, 4e-11 at 1e-14), which says nothing about either implementation.
 CASES = {
-    "tf_vw_h": (("TF", "VW", "HARTREE"), T_ALL, False),
-    "tf_vw_h_pp_xc": (("TF", "VW", "HARTREE", "PP", "XC"), T_ALL | L.TERM_PP | L.TERM_XC, True),
-    "lwt": (("TF", "VW", "NL", "HARTREE", "PP"), T_ALL | L.TERM_NL | L.TERM_PP, True),
+    "tf_vw_h": (("TF", "VW", "HARTREE"), T_ALL, False, 0.0),
+    "tf_vw_h_pp_xc": (("TF", "VW", "HARTREE", "PP", "XC"), T_ALL | L.TERM_PP | L.TERM_XC, True, 0.0),
+    "lwt": (("TF", "VW", "NL", "HARTREE", "PP"), T_ALL | L.TERM_NL | L.TERM_PP, True, 1e-8),
 }
+
+
+def _start(og, rho0, floor):
+    if floor > 0.0:
+        rho0 = np.maximum(rho0, floor)
+        rho0 = rho0 * 4.0 / (rho0.sum() * og.dV)
+    return rho0, otd.kick(og, np.sqrt(rho0), [0.05, 0.02, 0.0])
 
 
 @pytest.fixture(scope="module")
 def oracle_runs():
     out = {}
-    og, cell, pos, rho0 = _cluster()
-    psi0 = otd.kick(og, np.sqrt(rho0), [0.05, 0.02, 0.0])
-    for name, (oterms, _, pp) in CASES.items():
+    og, cell, pos, rho_blob = _cluster()
+    for name, (oterms, _, pp, floor) in CASES.items():
+        rho0, psi0 = _start(og, rho_blob, floor)
         Vg = ofn.external_potential_G(og, pos, [0, 0], [2.0], [1.0]) if pp else None
         psi, dip = otd.propagate(og, psi0, rho0, OFunc(terms=oterms, n_knots=8), Vg, 0.05, 8, n_corrector=1)
-        out[name] = (psi, dip)
-    return og, cell, pos, rho0, psi0, out
+        out[name] = (rho0, psi0, psi, dip)
+    return og, cell, pos, out
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
 @pytest.mark.parametrize("precision", [L.FP64, L.FP32_MIXED])
 def test_propagation_matches_the_oracle(oracle_runs, name, precision):
-    og, cell, pos, rho0, psi0, out = oracle_runs
-    _, terms, pp = CASES[name]
+    og, cell, pos, out = oracle_runs
+    _, terms, pp, _ = CASES[name]
+    rho0, psi0, opsi, odip = out[name]
     f = ofd.Functional(terms=terms, n_knots=8, precision=precision)
     ions = (pos, [0, 0], [2.0], [1.0]) if pp else None
     psi, dip, rep, g = _run_gpu(cell, og.shape, psi0, rho0, f, 0.05, 8, ions=ions)
-    opsi, odip = out[name]
     scale = np.max(np.abs(opsi))
     if precision == L.FP64:
         assert np.max(np.abs(psi - opsi)) < 1e-9 * scale, name
