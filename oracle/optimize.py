@@ -22,6 +22,9 @@ Readings (the paper leaves them to SciPy and to its references):
 - Step (3), the update: the orthogonal psi cos(lambda) + p sin(lambda) (default), or
   the scaling scheme psi + t p renormalised to N_e with p not orthogonalised (with p
   orthogonal to psi the two are one curve, t = tan(lambda)).
+- The paper's two ways to optimise: the step minimises the energy (default) or the norm of
+  the residual of Eq. euler2, |2 psi (V - mu) dV| (backtracking from the first trial by
+  halves until the norm falls by the factor 1 - c1; the directions are the same).
 - Step (2): a strong-Wolfe line search on lambda (c1 = 1e-4, c2 = 0.2, at most
   10 evaluations per search, cubic interpolation).  A TN or L-BFGS direction
   built from curvature starts from the length of its step,
@@ -93,14 +96,17 @@ def _tangent(v, psi):
 def optimize_density(g: Grid, psi0, func: Functional, Vext_G, n_electrons: float, n_atoms: int,
                      tol: float = 1e-6, max_iter: int = 200, c1: float = 1e-4, c2: float = 0.2,
                      max_ls: int = 10, fixed_iter: int | None = None, method: str = "cg",
-                     max_inner: int = 20, lbfgs_m: int = 5, update: str = "rotate"):
+                     max_inner: int = 20, lbfgs_m: int = 5, update: str = "rotate", objective: str = "energy"):
     """method: 'cg' | 'tn' | 'lbfgs'; update: 'rotate' (psi cos + p sin, p orthogonal to psi)
-    or 'scale' (psi + t p renormalised, p not orthogonalised).
+    or 'scale' (psi + t p renormalised, p not orthogonalised); objective of the line search:
+    'energy' (direct minimisation) or 'residual' (the norm of Eq. euler2's residual).
     Returns dict(psi, E, energies, iterations, evals, history)."""
     if method not in ("cg", "tn", "lbfgs"):
         raise ValueError("unknown method %r" % method)
     if update not in ("rotate", "scale"):
         raise ValueError("unknown update %r" % update)
+    if objective not in ("energy", "residual"):
+        raise ValueError("unknown objective %r" % objective)
     psi = np.asarray(psi0, dtype=np.float64).copy()
     psi *= math.sqrt(n_electrons / (np.sum(psi * psi) * g.dV))
     evals = 0
@@ -213,37 +219,27 @@ def optimize_density(g: Grid, psi0, func: Functional, Vext_G, n_electrons: float
             E_l, V_l = energy(psi_l, f_it)
             return E_l, V_l, psi_l, float(np.sum(2.0 * psi_l * V_l * g.dV * dpsi))
 
-        # strong-Wolfe search (bracketing + zoom with cubic interpolation)
-        lam_lo, f_lo, d_lo = 0.0, phi0, dphi0
         lam = min(max(step0 if newton else lam_prev, 1e-4), 0.5)
-        best = None
-        n_ls = 0
-        lam_hi = None
-        while n_ls < max_ls:
-            n_ls += 1
-            E_l, V_l, psi_l, dl = phi(lam)
-            fl = E_l["total"]
-            if best is None or fl < best[0]:
-                best = (fl, lam, E_l, V_l, psi_l)
-            if fl > phi0 + c1 * lam * dphi0 or (lam_hi is None and fl >= f_lo and lam_lo > 0.0):
-                lam_hi, f_hi, d_hi = lam, fl, dl
-            elif abs(dl) <= -c2 * dphi0:
-                break
-            elif dl >= 0.0:
-                lam_hi, f_hi, d_hi = lam_lo, f_lo, d_lo
-                lam_lo, f_lo, d_lo = lam, fl, dl
-            else:
-                lam_lo, f_lo, d_lo = lam, fl, dl
-                if lam_hi is None:
-                    lam = min(2.0 * lam, math.pi / 2.0)
-                    continue
-            c = _cubic_min(lam_lo, f_lo, d_lo, lam_hi, f_hi, d_hi)
-            lo, hi = min(lam_lo, lam_hi), max(lam_lo, lam_hi)
-            if c is None or not (lo + 0.1 * (hi - lo) <= c <= hi - 0.1 * (hi - lo)):
-                c = 0.5 * (lam_lo + lam_hi)
-            lam = c
-        fl, lam, E_new, V_new, psi_new = best
-        if fl >= phi0:
+        if objective == "residual":
+            # the step lowers the norm of the residual of Eq. euler2, |2 psi (V - mu) dV|:
+            # backtracking from the first trial until it falls by the factor (1 - c1)
+            r0 = math.sqrt(float(np.sum(grad * grad)))
+            best = None
+            for _ in range(max_ls):
+                psi_l, _ = update_curve(psi, p, lam, g.dV, n_electrons, update)
+                E_l, V_l = energy(psi_l, f_it)
+                mu_l = np.sum(psi_l * psi_l * V_l) * g.dV / n_electrons
+                r_l = math.sqrt(float(np.sum((2.0 * psi_l * (V_l - mu_l) * g.dV) ** 2)))
+                if best is None or r_l < best[0]:
+                    best = (r_l, lam, E_l, V_l, psi_l)
+                if r_l <= (1.0 - c1) * r0:
+                    break
+                lam *= 0.5
+            improved = best[0] < r0
+            _, lam, E_new, V_new, psi_new = best
+        else:
+            improved, lam, E_new, V_new, psi_new = _wolfe_search(phi, phi0, dphi0, lam, c1, c2, max_ls)
+        if not improved:
             d_prev = None            # no decrease: restart with steepest descent
             pairs = []
             psi_prev = None
@@ -267,6 +263,40 @@ def optimize_density(g: Grid, psi0, func: Functional, Vext_G, n_electrons: float
         if small >= 3:
             break
     return dict(psi=psi, E=E["total"], energies=E, iterations=it, evals=evals, history=history)
+
+
+def _wolfe_search(phi, phi0, dphi0, lam, c1, c2, max_ls):
+    """Strong-Wolfe search on phi(lam) = (E, V, psi, dE/dlam) (bracketing + zoom with cubic
+    interpolation).  Returns (decreased, lam, E, V, psi) of the lowest trial."""
+    lam_lo, f_lo, d_lo = 0.0, phi0, dphi0
+    best = None
+    n_ls = 0
+    lam_hi = None
+    while n_ls < max_ls:
+        n_ls += 1
+        E_l, V_l, psi_l, dl = phi(lam)
+        fl = E_l["total"]
+        if best is None or fl < best[0]:
+            best = (fl, lam, E_l, V_l, psi_l)
+        if fl > phi0 + c1 * lam * dphi0 or (lam_hi is None and fl >= f_lo and lam_lo > 0.0):
+            lam_hi, f_hi, d_hi = lam, fl, dl
+        elif abs(dl) <= -c2 * dphi0:
+            break
+        elif dl >= 0.0:
+            lam_hi, f_hi, d_hi = lam_lo, f_lo, d_lo
+            lam_lo, f_lo, d_lo = lam, fl, dl
+        else:
+            lam_lo, f_lo, d_lo = lam, fl, dl
+            if lam_hi is None:
+                lam = min(2.0 * lam, math.pi / 2.0)
+                continue
+        c = _cubic_min(lam_lo, f_lo, d_lo, lam_hi, f_hi, d_hi)
+        lo, hi = min(lam_lo, lam_hi), max(lam_lo, lam_hi)
+        if c is None or not (lo + 0.1 * (hi - lo) <= c <= hi - 0.1 * (hi - lo)):
+            c = 0.5 * (lam_lo + lam_hi)
+        lam = c
+    fl, lam, E_new, V_new, psi_new = best
+    return fl < phi0, lam, E_new, V_new, psi_new
 
 
 def optimize_multistep(grids, psi0, func: Functional, Vext_list, n_electrons: float, n_atoms: int,

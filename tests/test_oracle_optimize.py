@@ -238,3 +238,36 @@ def test_scaling_update_reaches_the_same_minima():
     a = optimize_density(g, np.sqrt(rho), f, Vg, 12.0, 4, tol=1e-11, max_iter=400)
     b = optimize_density(g, np.sqrt(rho), f, Vg, 12.0, 4, tol=1e-11, max_iter=400, update="scale")
     assert abs(a["E"] - b["E"]) / 4 < 1e-10
+
+
+# --------------------------------------------------------------------------- residual minimisation
+def test_residual_minimisation_reaches_the_same_minima():
+    """Sec. 2.4's second way (the step lowers the norm of Eq. euler2's residual): the
+    Schroedinger ground state and the convex minimum, with CG and TN directions."""
+    g, Vg, H = _schroedinger_case(10)
+    E0 = 4.0 * np.linalg.eigvalsh(H)[0]
+    psi0 = 1.0 + 0.3 * np.random.default_rng(2).random(g.shape)
+    for method in ("cg", "tn"):
+        r = optimize_density(g, psi0, Functional(terms=("VW", "PP")), Vg, 4.0, 4, tol=1e-13, max_iter=800,
+                             method=method, objective="residual")
+        assert abs(r["E"] - E0) < 1e-9 * abs(E0), (method, r["E"], E0, r["iterations"])
+    g, rho, Vg = _small_al()
+    f = Functional(terms=("TF", "VW", "HARTREE", "PP"))
+    a = optimize_density(g, np.sqrt(rho), f, Vg, 12.0, 4, tol=1e-11, max_iter=400)
+    b = optimize_density(g, np.sqrt(rho), f, Vg, 12.0, 4, tol=1e-11, max_iter=400, method="tn",
+                         objective="residual")
+    assert abs(a["E"] - b["E"]) / 4 < 1e-10
+    assert _residual(g, b["psi"], f, Vg, 12.0) < 1e-5
+
+
+def test_residual_minimisation_lowers_the_residual_every_step():
+    g, rho, Vg = _small_al()
+    f = Functional(terms=("TF", "VW", "HARTREE", "PP"))
+    psi = np.sqrt(rho)
+    res = [_residual(g, psi, f, Vg, 12.0)]
+    for _ in range(6):
+        r = optimize_density(g, psi, f, Vg, 12.0, 4, max_iter=1, fixed_iter=1, method="tn", objective="residual")
+        psi = r["psi"]
+        res.append(_residual(g, psi, f, Vg, 12.0))
+    assert all(b < a for a, b in zip(res, res[1:])), res
+    assert res[-1] < 1e-2 * res[0]
