@@ -199,7 +199,14 @@ typedef struct {
     int update;         /* step (3): OFDFT_UPDATE_ROTATE psi cos(l) + p sin(l), p orthogonal to psi
                            (default), or OFDFT_UPDATE_SCALE psi + t p renormalised to N_e, p not
                            orthogonalised (the paper's scaling scheme, "not always stable") */
+    int objective;      /* OFDFT_OBJECTIVE_ENERGY: the line search minimises E (strong Wolfe, default);
+                           OFDFT_OBJECTIVE_RESIDUAL: the step lowers the norm of the residual of
+                           Eq. euler2, |2 psi (V - mu) dV| (backtracking by halves from the first
+                           trial until it falls by 1e-4 relative) - the paper's second way */
 } ofdft_opt_options;
+
+#define OFDFT_OBJECTIVE_ENERGY 0
+#define OFDFT_OBJECTIVE_RESIDUAL 1
 
 #define OFDFT_UPDATE_ROTATE 0
 #define OFDFT_UPDATE_SCALE 1

@@ -233,16 +233,20 @@ class Grid:
 
     def optimize_density(self, psi, func: Functional, n_electrons: float, tol_per_atom: float = 1e-6,
                          max_iter: int = 200, raise_on_not_converged: bool = False, method: str = "cg",
-                         precondition: bool = True, max_inner: int = 0, lbfgs_m: int = 0, update: str = "rotate"):
+                         precondition: bool = True, max_inner: int = 0, lbfgs_m: int = 0, update: str = "rotate",
+                         objective: str = "energy"):
         """Sec. 2.4's psi = sqrt(rho) optimisation in place on psi; method 'cg' | 'tn' | 'lbfgs',
-        update 'rotate' | 'scale'."""
+        update 'rotate' | 'scale', objective of the step 'energy' | 'residual'."""
         methods = {"cg": L.OPT_CG, "tn": L.OPT_TN, "lbfgs": L.OPT_LBFGS}
         updates = {"rotate": L.UPDATE_ROTATE, "scale": L.UPDATE_SCALE}
-        if method not in methods or update not in updates:
-            raise ValueError("method must be one of %s, update one of %s" % (sorted(methods), sorted(updates)))
+        objectives = {"energy": L.OBJECTIVE_ENERGY, "residual": L.OBJECTIVE_RESIDUAL}
+        if method not in methods or update not in updates or objective not in objectives:
+            raise ValueError("method must be one of %s, update one of %s, objective one of %s"
+                             % (sorted(methods), sorted(updates), sorted(objectives)))
         rep = L.COptReport()
         c, keep = func.to_c()
-        opt = L.COptOptions(methods[method], int(bool(precondition)), max_inner, lbfgs_m, updates[update])
+        opt = L.COptOptions(methods[method], int(bool(precondition)), max_inner, lbfgs_m, updates[update],
+                            objectives[objective])
         st = self.lib.ofdft_optimize_density_ex(self.h, _ptr(self._field(psi, func)), ct.byref(c), n_electrons,
                                                 tol_per_atom, max_iter, ct.byref(opt), ct.byref(rep))
         if st != L.OFDFT_OK and not (st == -6 and not raise_on_not_converged):

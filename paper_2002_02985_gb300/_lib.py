@@ -27,6 +27,7 @@ KERNEL_LWT, KERNEL_WT_GLOBAL = 0, 1
 FP64, FP32_MIXED = 0, 1
 OPT_CG, OPT_TN, OPT_LBFGS = 0, 1, 2
 UPDATE_ROTATE, UPDATE_SCALE = 0, 1
+OBJECTIVE_ENERGY, OBJECTIVE_RESIDUAL = 0, 1
 
 # symbols declared in include/ofdft.h (checked by the CPU test suite)
 EXPORTS = (
@@ -64,7 +65,7 @@ class COptReport(ct.Structure):
 
 class COptOptions(ct.Structure):
     _fields_ = [("method", ct.c_int), ("precondition", ct.c_int), ("max_inner", ct.c_int), ("lbfgs_m", ct.c_int),
-                ("update", ct.c_int)]
+                ("update", ct.c_int), ("objective", ct.c_int)]
 
 
 class CTdOptions(ct.Structure):

@@ -901,7 +901,7 @@ int ewald_impl(ofdft_grid *g, double *E_out, double *F_out) {
 template <typename T>
 int optimize_impl(ofdft_grid *g, T *psi, const ofdft_functional *f0, double Ne, double tol, int max_iter,
                   const ofdft_opt_options &o, ofdft_opt_report *rep);
-const ofdft_opt_options kOptDefaults = {OFDFT_OPT_CG, 1, 0, 0, OFDFT_UPDATE_ROTATE};
+const ofdft_opt_options kOptDefaults = {OFDFT_OPT_CG, 1, 0, 0, OFDFT_UPDATE_ROTATE, OFDFT_OBJECTIVE_ENERGY};
 
 // ---------------------------------------------------------------- Fourier interpolation between grids
 bool same_cell(const ofdft_grid *a, const ofdft_grid *b) {
@@ -1022,6 +1022,7 @@ int optimize_impl(ofdft_grid *g, T *psi, const ofdft_functional *f0, double Ne, 
     const char *env_pc = std::getenv("OFDFT_OPT_PRECOND");
     const bool precond = o.precondition && !(env_pc && env_pc[0] == '0');
     const bool scale_upd = o.update == OFDFT_UPDATE_SCALE;
+    const bool resid_obj = o.objective == OFDFT_OBJECTIVE_RESIDUAL;
     const double rho_m = Ne / g->omega;
     const double pa = 70.0 / 9.0 * kCTF * std::pow(rho_m, 2.0 / 3.0), pb = 16.0 * kPi * rho_m;
     double bv[9];
@@ -1279,7 +1280,27 @@ int optimize_impl(ofdft_grid *g, T *psi, const ofdft_functional *f0, double Ne, 
         const double step0 = scale_upd ? std::sqrt(pn / Ne) : std::atan(std::sqrt(pn / Ne));
         double lam = std::min(std::max(newton ? step0 : lam_prev, 1e-4), 0.5);
         double best_f = 1e300, best_lam = 0.0;
-        for (int ls = 0; ls < 10; ls++) {
+        bool improved = false;
+        if (resid_obj) {
+            // the step lowers the norm of the residual of Eq. euler2, |2 psi (V - mu) dV|:
+            // backtracking from the first trial by halves until it falls by the factor 1 - c1
+            const double r0 = std::sqrt(dv.dot(grad, grad));
+            double best_r = r0;
+            for (int ls = 0; ls < 10; ls++) {
+                double cc = 1.0, nn = Ne, El[E_NUM];
+                if ((rc = trial(lam, cc, nn))) return rc;
+                if ((rc = eval_sync<T>(g, rho, &f, V, El))) return rc;
+                evals++;
+                const double mul = dv.dot(psil, psil, V) * g->dV / Ne;
+                CK(launch_grad<T>(tmp, psil, V, mul, g->dV, N, s), "residual");
+                const double rl = std::sqrt(dv.dot(tmp, tmp));
+                if (rl < best_r) { best_r = rl; best_lam = lam; std::memcpy(Enew, El, sizeof(El)); }
+                if (rl <= (1.0 - c1) * r0) break;
+                lam *= 0.5;
+            }
+            improved = best_r < r0;
+        }
+        for (int ls = 0; ls < 10 && !resid_obj; ls++) {
             double El[E_NUM], dl;
             if ((rc = phi(lam, El, dl))) return rc;
             const double fl = El[0];
@@ -1301,7 +1322,8 @@ int optimize_impl(ofdft_grid *g, T *psi, const ofdft_functional *f0, double Ne, 
             if (!ok || !(c >= lo + 0.1 * (hi - lo) && c <= hi - 0.1 * (hi - lo))) c = 0.5 * (lam_lo + lam_hi);
             lam = c;
         }
-        if (!(best_f < phi0)) {
+        if (!resid_obj) improved = best_f < phi0;
+        if (!improved) {
             have_dir = false;
             forget();
             if (++restarts > 3) break;
@@ -1433,7 +1455,8 @@ int td_impl(ofdft_grid *g, T *pre, T *pim, const T *rho0, const ofdft_functional
         return OFDFT_OK;
     };
     // x <- psi(t + dt) for the Hamiltonian with potential v, x holding the initial guess
-    auto cn_solve = [&](const T *v) -> int {
+    // (x_is_psi: the guess is psi(t) itself, whose residual follows from the right-hand side)
+    auto cn_solve = [&](const T *v, bool x_is_psi) -> int {
         int e;
         vbar = 0.0;
         if (have_v) {   // v weighted by the density held in rho (any vbar gives the same solution)
@@ -1446,6 +1469,11 @@ int td_impl(ofdft_grid *g, T *pre, T *pim, const T *rho0, const ofdft_functional
             if ((e = apply_h(p0[j], v, hp[j]))) return e;
         for (int j = 0; j < 2; j++) {
             if ((e = apply_h(hp[j], v, c[j]))) return e;
+            if (x_is_psi) {
+                // r = c - (1 + tau^2 H^2) psi = -2 tau^2 H^2 p_j +- 2 tau H p_(other)
+                CK(launch_copy<T>(r[j], c[j], N, s), "copy");
+                CK(launch_axpby<T>(r[j], hp[1 - j], j == 0 ? 2.0 * tau : -2.0 * tau, -2.0 * tau * tau, N, s), "axpby");
+            }
             CK(launch_axpby<T>(c[j], p0[j], 1.0, -tau * tau, N, s), "axpby");
             CK(launch_axpby<T>(c[j], hp[1 - j], j == 0 ? 2.0 * tau : -2.0 * tau, 1.0, N, s), "axpby");
         }
@@ -1459,8 +1487,10 @@ int td_impl(ofdft_grid *g, T *pre, T *pim, const T *rho0, const ofdft_functional
                 CK(cudaMemsetAsync(x[j], 0, (size_t)N * sizeof(T), s), "memset");
                 continue;
             }
-            if ((e = apply_a(x[j], v, r[j]))) return e;
-            CK(launch_axpby<T>(r[j], c[j], 1.0, -1.0, N, s), "axpby");      // r = c - A x
+            if (!x_is_psi) {
+                if ((e = apply_a(x[j], v, r[j]))) return e;
+                CK(launch_axpby<T>(r[j], c[j], 1.0, -1.0, N, s), "axpby");  // r = c - A x
+            }
             if (std::sqrt(dv.dot(r[j], r[j])) <= tol * nc[j]) {
                 done[j] = true;
                 continue;
@@ -1520,12 +1550,12 @@ int td_impl(ofdft_grid *g, T *pre, T *pim, const T *rho0, const ofdft_functional
     int step = 0;
     for (; step < o.n_steps; step++) {
         for (int j = 0; j < 2; j++) CK(launch_copy<T>(p0[j], x[j], N, s), "copy");
-        if ((rc = cn_solve(vt))) return rc;                 // predictor
+        if ((rc = cn_solve(vt, true))) return rc;           // predictor (from psi(t))
         if ((rc = veff(vn))) return rc;
         for (int k = 0; k < o.n_corrector; k++) {           // correctors: mean of the two potentials
             CK(launch_copy<T>(vm, vt, N, s), "copy");
             CK(launch_axpby<T>(vm, vn, 0.5, 0.5, N, s), "axpby");
-            if ((rc = cn_solve(vm))) return rc;
+            if ((rc = cn_solve(vm, false))) return rc;     // from the last solution
             if ((rc = veff(vn))) return rc;
         }
         std::swap(vt, vn);
@@ -2065,7 +2095,8 @@ int ofdft_optimize_density_ex(ofdft_grid *g, void *psi_dev, const ofdft_function
     if (!psi_dev || !(N_e > 0.0) || max_iter < 1) return fail(g, OFDFT_ERR_INVALID_ARG, "psi, N_e or max_iter");
     const ofdft_opt_options o = opt ? *opt : kOptDefaults;
     if (o.method < OFDFT_OPT_CG || o.method > OFDFT_OPT_LBFGS || o.max_inner < 0 || o.max_inner > 100 ||
-        o.lbfgs_m < 0 || o.lbfgs_m > 32 || o.update < OFDFT_UPDATE_ROTATE || o.update > OFDFT_UPDATE_SCALE)
+        o.lbfgs_m < 0 || o.lbfgs_m > 32 || o.update < OFDFT_UPDATE_ROTATE || o.update > OFDFT_UPDATE_SCALE ||
+        o.objective < OFDFT_OBJECTIVE_ENERGY || o.objective > OFDFT_OBJECTIVE_RESIDUAL)
         return fail(g, OFDFT_ERR_INVALID_ARG, "optimiser options");
     int rc = check_functional(g, f);
     if (rc) return rc;

@@ -45,12 +45,12 @@ def _grid(wl):
     return g
 
 
-def _run(wl, rho, func, method, tol, max_iter=400, update="rotate"):
+def _run(wl, rho, func, method, tol, max_iter=400, update="rotate", objective="energy"):
     g = _grid(wl)
     dt = torch.float64 if func.precision == L.FP64 else torch.float32
     psi = torch.from_numpy(np.sqrt(rho)).to("cuda", dt).contiguous()
     rep = g.optimize_density(psi, func, wl["n_electrons"], tol_per_atom=tol, max_iter=max_iter, method=method,
-                             update=update)
+                             update=update, objective=objective)
     charge = float((psi.double() ** 2).sum()) * g.dV
     assert abs(charge - wl["n_electrons"]) <= (1e-10 if func.precision == L.FP64 else 1e-6) * wl["n_electrons"]
     return rep
@@ -133,6 +133,18 @@ def test_scaling_update_reaches_the_same_minima(case, ground_state, convex_minim
     assert abs(rep["energy"] - convex_minimum) / wl["n_atoms"] <= 1e-6, (method, rep, convex_minimum)
 
 
+@pytest.mark.parametrize("method", ("cg", "tn"))
+def test_residual_minimisation_reaches_the_same_minima(case, ground_state, convex_minimum, method):
+    """Sec. 2.4's second way: each step lowers the norm of the residual of Eq. euler2."""
+    wl, rho, _, _ = case
+    f = ofd.Functional(terms=L.TERM_VW | L.TERM_PP, precision=L.FP64)
+    rep = _run(wl, rho, f, method, 1e-13, max_iter=800, objective="residual")
+    assert abs(rep["energy"] - ground_state) <= 1e-9 * abs(ground_state), (method, rep)
+    f = ofd.Functional(terms=L.TERM_TF | L.TERM_VW | L.TERM_HARTREE | L.TERM_PP, precision=L.FP32_MIXED)
+    rep = _run(wl, rho, f, method, 1e-8, max_iter=800, objective="residual")
+    assert abs(rep["energy"] - convex_minimum) / wl["n_atoms"] <= 1e-6, (method, rep, convex_minimum)
+
+
 def test_tn_needs_fewer_outer_iterations_than_cg(case):
     wl, rho, _, _ = case
     f = ofd.Functional(terms=L.TERM_TF | L.TERM_VW | L.TERM_HARTREE | L.TERM_PP, precision=L.FP64)
@@ -148,7 +160,8 @@ def test_optimiser_options_out_of_range_are_rejected(case):
     c, keep = ofd.Functional().to_c()
     rep = L.COptReport()
     for bad in (L.COptOptions(7, 1, 0, 0, 0), L.COptOptions(L.OPT_TN, 1, 101, 0, 0), L.COptOptions(L.OPT_LBFGS, 1, 0, 33, 0),
-                L.COptOptions(L.OPT_TN, 1, -1, 0, 0), L.COptOptions(L.OPT_CG, 1, 0, 0, 2)):
+                L.COptOptions(L.OPT_TN, 1, -1, 0, 0), L.COptOptions(L.OPT_CG, 1, 0, 0, 2),
+                L.COptOptions(L.OPT_CG, 1, 0, 0, 0, 2)):
         st = g.lib.ofdft_optimize_density_ex(g.h, ct.c_void_p(psi.data_ptr()), ct.byref(c), wl["n_electrons"], 1e-6,
                                              10, ct.byref(bad), ct.byref(rep))
         assert st == L.OFDFT_ERR_INVALID_ARG
@@ -156,4 +169,6 @@ def test_optimiser_options_out_of_range_are_rejected(case):
         g.optimize_density(psi, ofd.Functional(), wl["n_electrons"], method="newton")
     with pytest.raises(ValueError):
         g.optimize_density(psi, ofd.Functional(), wl["n_electrons"], update="shift")
+    with pytest.raises(ValueError):
+        g.optimize_density(psi, ofd.Functional(), wl["n_electrons"], objective="force")
     del keep
