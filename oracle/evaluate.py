@@ -28,6 +28,8 @@ class Functional:
     knots: np.ndarray | None = None   # frozen knots (e.g. for finite differences)
     potential: str = "exact"          # 'exact' | 'interpolated'
     kernel: str = "lwt"               # 'lwt' | 'wt_global'
+    mgp_x: float = 0.0                # Eq. MGP's (x, y): x = 0 is Wang-Teter; (1, 5/6) MGP,
+    mgp_y: float = 5.0 / 6.0          # (1/2, 5/6) MGPA, (1, 5/3) MGPG
     extra: dict = field(default_factory=dict)
 
 
@@ -46,11 +48,11 @@ def evaluate(g: Grid, rho, func: Functional, Vext_G=None):
         V += v
     if "NL" in func.terms:
         if func.kernel == "wt_global":
-            e, v = fn.nonlocal_wt_global(g, rho, func.alpha, func.beta)
+            e, v = fn.nonlocal_wt_global(g, rho, func.alpha, func.beta, mgp=(func.mgp_x, func.mgp_y))
         else:
             knots = func.knots if func.knots is not None else fn.make_knots(rho, func.n_knots, func.spacing)
             e, v = fn.nonlocal_lwt(g, rho, np.asarray(knots, dtype=np.float64), func.alpha, func.beta,
-                                   func.potential)
+                                   func.potential, mgp=(func.mgp_x, func.mgp_y))
         E["NL"] = e
         V += v
     if "HARTREE" in func.terms:

@@ -12,6 +12,7 @@ import numpy as np
 
 from .grid import Grid
 from .lindhard import C_WT, G_NL
+from .mgp import kernel as mgp_kernel
 
 C_TF = 0.3 * (3.0 * np.pi ** 2) ** (2.0 / 3.0)
 RHO_FLOOR = 1e-20     # reading: guard for rho^(alpha-1), 1/psi and kF (paper silent)
@@ -124,7 +125,7 @@ def spline_weights(kF, knots):
     return j, t, inv_dk, inside
 
 
-def nonlocal_lwt(g: Grid, rho, knots, alpha=5.0 / 6.0, beta=5.0 / 6.0, potential="exact"):
+def nonlocal_lwt(g: Grid, rho, knots, alpha=5.0 / 6.0, beta=5.0 / 6.0, potential="exact", mgp=(0.0, 5.0 / 6.0)):
     """Density-dependent-kernel KEDF (LWT) through steps s1-s4 (Sec. 2.3).
 
     Energy (reading of Eq. nl2 with the kernel at the local kF(r)):
@@ -135,7 +136,8 @@ def nonlocal_lwt(g: Grid, rho, knots, alpha=5.0 / 6.0, beta=5.0 / 6.0, potential
             + rho^alpha Psi kF/(3 rho),   Psi = sum_j h'_j(kF) y_j.
     Potential 'interpolated' = the paper's s3->s4 blend of per-knot WT
     potentials, 2 alpha rho^(alpha-1) Phi (alpha = beta only): same energy,
-    not the exact derivative."""
+    not the exact derivative.
+    mgp = (x, y): the knots' kernels are those of Eq. MGP (x = 0: Eq. WT), giving LMGP/A/G."""
     rf = np.maximum(rho, RHO_FLOOR)
     kF = fermi_wavevector(rho)
     j, t, inv_dk, inside = spline_weights(kF, knots)
@@ -146,7 +148,7 @@ def nonlocal_lwt(g: Grid, rho, knots, alpha=5.0 / 6.0, beta=5.0 / 6.0, potential
     Psi = np.zeros_like(rf)
     T2 = np.zeros_like(rf)
     for m in range(M):                      # one knot at a time: memory O(N)
-        K = C_WT * G_NL(g.Gnorm / (2.0 * knots[m]))         # step s2
+        K = mgp_kernel(g.Gnorm / (2.0 * knots[m]), *mgp)    # step s2
         y = g.ifft(K * rb_hat)                               # step s3
         h = np.where(j == m, 1.0 - t, 0.0) + np.where(j == m - 1, t, 0.0)
         hp = np.where(j == m, -inv_dk, 0.0) + np.where(j == m - 1, inv_dk, 0.0)
@@ -164,14 +166,15 @@ def nonlocal_lwt(g: Grid, rho, knots, alpha=5.0 / 6.0, beta=5.0 / 6.0, potential
     return E, V
 
 
-def nonlocal_wt_global(g: Grid, rho, alpha=5.0 / 6.0, beta=5.0 / 6.0, rho0=None):
-    """Wang-Teter with one kernel at kF(rho0), rho0 = N_e/Omega (Eq. nl2 with Eq. WT):
+def nonlocal_wt_global(g: Grid, rho, alpha=5.0 / 6.0, beta=5.0 / 6.0, rho0=None, mgp=(0.0, 5.0 / 6.0)):
+    """Wang-Teter with one kernel at kF(rho0), rho0 = N_e/Omega (Eq. nl2 with Eq. WT; with
+    mgp = (x, y), x != 0, the kernel of Eq. MGP: the MGP/A/G functionals):
         E = int rho^alpha (K * rho^beta),
         V = alpha rho^(alpha-1) (K * rho^beta) + beta rho^(beta-1) (K * rho^alpha)."""
     rf = np.maximum(rho, RHO_FLOOR)
     if rho0 is None:
         rho0 = np.sum(rho) * g.dV / g.omega
-    K = C_WT * G_NL(g.Gnorm / (2.0 * float(fermi_wavevector(rho0))))
+    K = mgp_kernel(g.Gnorm / (2.0 * float(fermi_wavevector(rho0))), *mgp)
     cb = g.ifft(K * g.fft(rf ** beta))
     ca = g.ifft(K * g.fft(rf ** alpha))
     E = np.sum(rf ** alpha * cb) * g.dV
