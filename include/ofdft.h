@@ -89,6 +89,13 @@ typedef struct {
     int kernel;            /* OFDFT_KERNEL_LWT | OFDFT_KERNEL_WT_GLOBAL */
     int precision;         /* OFDFT_FP64 | OFDFT_FP32_MIXED */
     double rho_floor;      /* guard for rho^(alpha-1), 1/psi, kF (<= 0 means 1e-20) */
+    double mgp_x;          /* Eq. MGP's x: 0 = the Wang-Teter kernel of Eq. WT (LWT / global WT);
+                              MGP and MGPG 1, MGPA 1/2 (with LWT: LMGP/A/G).  |x| <= 10 */
+    double mgp_y;          /* Eq. MGP's y, used when mgp_x != 0: MGP/MGPA 5/6, MGPG 5/3; (0, 10].
+                              Reading: eta(q,t) = q/(2 k_F t^(1/3)), k_F of the scaled density
+                              t rho.  The correction is tabulated once per grid and y (2^20 + 1
+                              points in eta/(1+eta), FP64 quadrature on the GPU) and interpolated
+                              linearly per G and knot */
 } ofdft_functional;
 
 /* Analytic local pseudopotential per species: v(q) = -4 pi Z exp(-(q rc)^2/4) / q^2,

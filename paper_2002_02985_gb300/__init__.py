@@ -48,6 +48,8 @@ class Functional:
     kernel: int = L.KERNEL_LWT
     precision: int = L.FP32_MIXED
     rho_floor: float = 1e-20
+    mgp_x: float = 0.0              # Eq. MGP: 0 Wang-Teter; (1, 5/6) MGP, (1/2, 5/6) MGPA, (1, 5/3) MGPG
+    mgp_y: float = 5.0 / 6.0
 
     def to_c(self):
         c = L.CFunctional()
@@ -65,6 +67,8 @@ class Functional:
         c.kernel = self.kernel
         c.precision = self.precision
         c.rho_floor = self.rho_floor
+        c.mgp_x = self.mgp_x
+        c.mgp_y = self.mgp_y
         return c, keep
 
     @property

@@ -46,7 +46,7 @@ class CFunctional(ct.Structure):
     _fields_ = [("terms", ct.c_uint), ("alpha", ct.c_double), ("beta", ct.c_double),
                 ("n_knots", ct.c_int), ("knot_spacing", ct.c_int), ("knots", ct.POINTER(ct.c_double)),
                 ("nl_potential", ct.c_int), ("kernel", ct.c_int), ("precision", ct.c_int),
-                ("rho_floor", ct.c_double)]
+                ("rho_floor", ct.c_double), ("mgp_x", ct.c_double), ("mgp_y", ct.c_double)]
 
 
 class CSpecies(ct.Structure):

@@ -74,6 +74,8 @@ template <typename T> struct Workspace {
     T *opt = nullptr;                 // optimiser fields (8 * N), allocated on demand
     T *opt_ext = nullptr;             // TN / L-BFGS fields (opt_ext_fields * N), on demand
     T *td = nullptr;                  // TD-OFDFT fields (20 * N), on demand
+    T *mgp_tab = nullptr;             // MGP correction table (kMgpTable points), on demand
+    double mgp_y = 0.0;               // the y it was built for (0: not built)
     int opt_ext_fields = 0;
     LaunchSet ks;                     // FFT-carrying kernels (size-specialised where compiled)
     int Brow = 0, thr_rowf = 0, thr_rowi = 0, TW1 = 0, thr_p1 = 0, TW0 = 0, thr_ax0 = 0, nb_row = 0, nb_ax0 = 0;
@@ -305,6 +307,7 @@ template <typename T> void free_ws(Workspace<T> &w) {
     cudaFree(w.opt);
     cudaFree(w.opt_ext);
     cudaFree(w.td);
+    cudaFree(w.mgp_tab);
     w = Workspace<T>();
 }
 
@@ -365,6 +368,9 @@ int check_functional(ofdft_grid *g, const ofdft_functional *f) {
             return fail(g, OFDFT_ERR_INVALID_ARG, "interpolated potential needs alpha == beta");
         if (f->kernel != OFDFT_KERNEL_LWT && f->kernel != OFDFT_KERNEL_WT_GLOBAL)
             return fail(g, OFDFT_ERR_INVALID_ARG, "unknown kernel");
+        if (!std::isfinite(f->mgp_x) || std::fabs(f->mgp_x) > 10.0 ||
+            (f->mgp_x != 0.0 && !(f->mgp_y > 0.0 && f->mgp_y <= 10.0)))
+            return fail(g, OFDFT_ERR_INVALID_ARG, "mgp_x must be in [-10, 10], mgp_y in (0, 10]");
         if (f->knots && f->kernel == OFDFT_KERNEL_LWT)
             for (int m = 0; m + 1 < f->n_knots; m++)
                 if (!(f->knots[m + 1] >= f->knots[m]) || !(f->knots[0] > 0.0))
@@ -410,6 +416,50 @@ void prof_collect(ofdft_grid *g) {
 const char *kKernelNames[K_NKERNEL] = {"stats", "knots", "row_fwd", "pencil_fwd", "axis0_recip",
                                        "pencil_inv", "row_inv", "finalize"};
 
+// ---------------------------------------------------------------- MGP kernel table
+constexpr int kMgpTable = (1 << 20) + 1;
+
+// 8-point Gauss-Legendre rule on [-1, 1]: nodes (Newton on the Legendre recurrence) then weights
+void gauss_legendre8(double *out) {
+    const int n = 8;
+    for (int i = 0; i < n; i++) {
+        double x = std::cos(kPi * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; it++) {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= n; k++) {
+                const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (x * p1 - p0) / (x * x - 1.0);
+            const double dx = p1 / dp;
+            x -= dx;
+            if (std::fabs(dx) < 1e-16) break;
+        }
+        out[i] = x;
+        out[n + i] = 2.0 / ((1.0 - x * x) * dp * dp);
+    }
+}
+
+bool uses_mgp(const ofdft_functional *f) { return (f->terms & OFDFT_TERM_NL) && f->mgp_x != 0.0; }
+
+// the correction table of the functional's y on g's stream (built once per y)
+template <typename T> int ensure_mgp_table(ofdft_grid *g, const ofdft_functional *f) {
+    if (!uses_mgp(f)) return OFDFT_OK;
+    Workspace<T> &w = ws<T>(g);
+    if (!w.mgp_tab) {
+        CK(cudaMalloc(&w.mgp_tab, (size_t)kMgpTable * sizeof(T)), "cudaMalloc MGP table");
+        w.mgp_y = 0.0;
+    }
+    if (w.mgp_y != f->mgp_y) {
+        double gl[16];
+        gauss_legendre8(gl);
+        CK(launch_mgp_table<T>(w.mgp_tab, kMgpTable, f->mgp_y, gl, g->stream), "MGP table");
+        w.mgp_y = f->mgp_y;
+    }
+    return OFDFT_OK;
+}
+
 // Fill the evaluation arguments and enqueue one evaluation.
 template <typename T>
 int enqueue_eval(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, double *E_dev_out) {
@@ -424,6 +474,7 @@ int enqueue_eval(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, d
         rc = ensure_vext<T>(g);
         if (rc) return rc;
     }
+    if ((rc = ensure_mgp_table<T>(g, f))) return rc;
     EvalArgs<T> a;
     std::memset(&a, 0, sizeof(a));
     a.n0 = g->n[0];
@@ -441,6 +492,12 @@ int enqueue_eval(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, d
     a.vext = w.vext;
     a.terms = f->terms;
     a.kernel = f->kernel;
+    if (uses_mgp(f)) {
+        a.mgp_tab = w.mgp_tab;
+        a.mgp_n = kMgpTable;
+        a.mgp_1mx = (T)(1.0 - f->mgp_x);
+        a.mgp_3xy = (T)(3.0 * f->mgp_x * f->mgp_y);
+    }
     a.nlpot = f->nl_potential;
     a.M = M;
     a.alpha = (T)f->alpha;
@@ -1610,6 +1667,7 @@ template <typename T> int prepare_batch_grid(ofdft_grid *g, const ofdft_function
     if (rc) return rc;
     if ((f->terms & OFDFT_TERM_PP) && (rc = ensure_vext<T>(g))) return rc;
     if (forces && (rc = ensure_force_buffers<T>(g))) return rc;
+    if ((rc = ensure_mgp_table<T>(g, f))) return rc;     // before any graph capture
     return OFDFT_OK;
 }
 

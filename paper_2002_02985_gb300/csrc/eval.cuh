@@ -52,6 +52,9 @@ template <typename T> struct EvalArgs {
     const C *vext;           // V_ext(G) half spectrum, null if no PP
     unsigned terms;
     int kernel, nlpot, M;    // kernel: 0 LWT, 1 WT global
+    const T *mgp_tab;        // MGP correction J_y on eta/(1+eta) (null: Wang-Teter kernel)
+    int mgp_n;               // table points
+    T mgp_1mx, mgp_3xy;      // K = C_WT ((1 - x) G_NL + 3 x y J_y)
     T alpha, beta, floor_;
     double *scal;            // S_* slots
     double *knots_d;         // [M] FP64 knots
@@ -164,5 +167,8 @@ template <typename T> cudaError_t launch_eval(const EvalArgs<T> &a, const Launch
 template <typename T> cudaError_t launch_inverse_cols_rows(const EvalArgs<T> &a, const LaunchSet &ks, cudaStream_t s);
 // stats + knots + row_fwd + forward pencil along n1 only (the channels of a.fwd_ch / a.col_ch)
 template <typename T> cudaError_t launch_forward_rows_cols(const EvalArgs<T> &a, const LaunchSet &ks, cudaStream_t s);
+// Table of the MGP correction J_y(eta) = 2 int_0^1 r^(6y-1) G_NL(eta/r^2) dr at eta = u/(1-u),
+// u = i/(n-1), i = 0..n-1 (FP64 Gauss-Legendre quadrature; gl = 8 nodes and 8 weights on [-1, 1])
+template <typename T> cudaError_t launch_mgp_table(T *tab, int n, double y, const double *gl, cudaStream_t s);
 
 }  // namespace ofdft

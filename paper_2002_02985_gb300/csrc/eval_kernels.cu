@@ -116,7 +116,68 @@ cudaError_t launch_inverse_cols_rows(const EvalArgs<T> &a, const LaunchSet &ks, 
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- MGP correction table
+// J_y(eta) = 2 int_0^1 r^p G_NL(eta / r^2) dr, p = 6y - 1 (the t-integral of Eq. MGP after
+// t = r^6 and an integration by parts).  G_NL has a logarithmic kink at r = sqrt(eta); each
+// piece between 0, the kink and 1 is split at its middle and each half is cut into panels
+// shrinking geometrically (by halves) toward its outer end, 8-point Gauss-Legendre on each.
+struct Gl8 {
+    double x[8], w[8];
+};
+constexpr int kMgpGrade = 24;
+
+__device__ __forceinline__ double mgp_panel(double a, double b, double eta, double p, const Gl8 &q) {
+    const double c = 0.5 * (a + b), h = 0.5 * (b - a);
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const double r = c + h * q.x[k];
+        s += q.w[k] * pow(r, p) * gnl<double>(eta / (r * r));
+    }
+    return 2.0 * h * s;
+}
+__device__ double mgp_graded(double a, double b, double eta, double p, const Gl8 &q) {
+    const double m = 0.5 * (a + b);
+    double s = mgp_panel(a, a + (m - a) * ldexp(1.0, -kMgpGrade), eta, p, q) +
+               mgp_panel(b - (b - m) * ldexp(1.0, -kMgpGrade), b, eta, p, q);
+    for (int j = 0; j < kMgpGrade; j++) {
+        s += mgp_panel(a + (m - a) * ldexp(1.0, -(j + 1)), a + (m - a) * ldexp(1.0, -j), eta, p, q);
+        s += mgp_panel(b - (b - m) * ldexp(1.0, -j), b - (b - m) * ldexp(1.0, -(j + 1)), eta, p, q);
+    }
+    return s;
+}
+template <typename T> __global__ void mgp_table_kernel(T *tab, int n, double y, Gl8 q) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double p = 6.0 * y - 1.0;
+    double J;
+    if (i == 0) {
+        J = 0.0;                                   // eta = 0: G_NL(0) = 0
+    } else if (i == n - 1) {
+        J = -8.0 / (15.0 * y);                     // eta -> infinity: G_NL -> -8/5
+    } else {
+        const double u = (double)i / (double)(n - 1), eta = u / (1.0 - u);
+        if (eta < 1.0) {
+            const double rk = sqrt(eta);
+            J = mgp_graded(0.0, rk, eta, p, q) + mgp_graded(rk, 1.0, eta, p, q);
+        } else {
+            J = mgp_graded(0.0, 1.0, eta, p, q);
+        }
+    }
+    tab[i] = (T)J;
+}
+template <typename T> cudaError_t launch_mgp_table(T *tab, int n, double y, const double *gl, cudaStream_t s) {
+    Gl8 q;
+    for (int k = 0; k < 8; k++) {
+        q.x[k] = gl[k];
+        q.w[k] = gl[8 + k];
+    }
+    mgp_table_kernel<T><<<(n + 127) / 128, 128, 0, s>>>(tab, n, y, q);
+    return cudaGetLastError();
+}
+
 #define INST(T)                                                                                              \
+    template cudaError_t launch_mgp_table<T>(T *, int, double, const double *, cudaStream_t);               \
     template bool find_specialised<T>(int, int, const void **, const void **, int *, int *);                 \
     template LaunchSet generic_kernels<T>();                                                                 \
     template cudaError_t launch_eval<T>(const EvalArgs<T> &, const LaunchSet &, cudaStream_t, const ProfHook *); \

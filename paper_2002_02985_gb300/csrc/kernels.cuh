@@ -118,6 +118,16 @@ template <typename T> __device__ __forceinline__ T gnl(T eta) {
     return gdiv((T)1, F) - (T)3 * eta * eta - (T)1;
 }
 
+// MGP correction J_y(eta) by linear interpolation in u = eta / (1 + eta) of the table a.mgp_tab
+// (n points, u = i/(n-1)); the kernel value of Eq. MGP is C_WT ((1 - x) G_NL + 3 x y J_y).
+template <typename T> __device__ __forceinline__ T mgp_j(const T *tab, int n, T eta) {
+    const T pos = gdiv(eta, (T)1 + eta) * (T)(n - 1);
+    int i = (int)pos;
+    i = i > n - 2 ? n - 2 : i;
+    const T f = pos - (T)i, t0 = tab[i];
+    return t0 + f * (tab[i + 1] - t0);
+}
+
 // ======================================================================= LDA exchange-correlation
 // Dirac exchange and the Perdew-Zunger (1981) fit of the Ceperley-Alder correlation,
 // spin unpolarised (the xc of the paper's benchmarks, Sec. 3.1), with
@@ -585,6 +595,11 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
     }
     const T invN = (T)(1.0 / (double)a.N);
     double eH = 0.0, eV = 0.0, eP = 0.0, eN = 0.0;
+    // kernel of Eq. WT, or of Eq. MGP when the correction table is given
+    auto kval = [&](T eta) -> T {
+        const T gv = gnl(eta);
+        return a.mgp_tab ? a.mgp_1mx * gv + a.mgp_3xy * mgp_j(a.mgp_tab, a.mgp_n, eta) : gv;
+    };
 
     // ---- Hartree + local pseudopotential
     if (a.terms & (8u | 16u)) {
@@ -661,7 +676,7 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
             T fN = 0;
             for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
                 const int w = idx % TW;
-                const T K = (T)kCWT * gnl(gn[idx] * hk);
+                const T K = (T)kCWT * kval(gn[idx] * hk);
                 const C Sa = cscale(S[idx], invN);
                 const C Rb = Rr[idx];
                 fN += cw[w] * K * (Sa.x * Rb.x + Sa.y * Rb.y);
@@ -693,7 +708,7 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
                 }
                 T fN = 0;
                 for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
-                    const T K = (T)kCWT * gnl(gn[idx] * hk);
+                    const T K = (T)kCWT * kval(gn[idx] * hk);
                     if (exact) {
                         // E_NL += Omega sum_G w Re(conj(FFT[h_m rho^alpha]) K_m FFT[rho^beta])
                         const C Sm = cscale(S[idx], invN);

@@ -58,7 +58,7 @@ def run_both(cell, shape, pos, rho64, func_kw, precision, species=None, Z=(2.0,)
                spacing="log" if f.knot_spacing == L.KNOTS_LOG else "arith",
                knots=None if f.knots is None else np.asarray(f.knots),
                potential="exact" if f.nl_potential == L.NLPOT_EXACT else "interpolated",
-               kernel="lwt" if f.kernel == L.KERNEL_LWT else "wt_global")
+               kernel="lwt" if f.kernel == L.KERNEL_LWT else "wt_global", mgp_x=f.mgp_x, mgp_y=f.mgp_y)
     Eo, Vo = evaluate(og, rho_in.astype(np.float64), of, Vg)
     return E, V.double().cpu().numpy(), Eo, Vo, og, g
 
@@ -77,6 +77,12 @@ FP64_CASES = [
     ((20, 20, 20), dict(n_knots=4, kernel=L.KERNEL_WT_GLOBAL)),
     ((25, 32, 18), dict(n_knots=7)),
     ((18, 16, 20), dict(n_knots=6, terms=L.TERMS_VALID)),            # with LDA xc
+    # Eq. MGP kernels (tabulated correction on the GPU, quadrature in the oracle)
+    ((12, 10, 15), dict(n_knots=5, mgp_x=1.0)),                       # LMGP
+    ((16, 18, 20), dict(n_knots=6, mgp_x=0.5)),                       # LMGPA
+    ((14, 12, 16), dict(n_knots=5, mgp_x=1.0, mgp_y=5.0 / 3.0)),      # LMGPG
+    ((20, 20, 20), dict(n_knots=4, kernel=L.KERNEL_WT_GLOBAL, mgp_x=1.0)),   # MGP (global k_F)
+    ((16, 14, 18), dict(n_knots=6, mgp_x=1.0, nl_potential=L.NLPOT_INTERP)),
 ]
 
 
@@ -103,6 +109,7 @@ FP32_CASES = [
     ("fcc-al-4/32", dict()),
     ("fcc-al-4/32", dict(nl_potential=L.NLPOT_INTERP)),
     ("fcc-al-4/32", dict(terms=L.TERMS_VALID)),                        # with LDA xc
+    ("fcc-al-4/32", dict(mgp_x=1.0)),                                  # LMGP
 ]
 
 
@@ -151,6 +158,16 @@ def test_frozen_knots_fp64():
     E, V, Eo, Vo, og, _ = run_both(cell, shape, pos, rho, dict(n_knots=6, knots=knots), L.FP64)
     assert abs(E["NL"] - Eo["NL"]) <= 1e-10 * abs(Eo["NL"])
     assert np.max(np.abs(V - Vo)) <= 1e-9
+
+
+def test_mgp_parameters_out_of_range_are_errors():
+    cell, pos, rho = small_case((12, 10, 15))
+    g = ofd.Grid(cell, (12, 10, 15))
+    g.set_ions(pos, np.zeros(len(pos), np.int32), (2.0,), (0.9,))
+    r = torch.from_numpy(rho).cuda()
+    for kw in (dict(mgp_x=1.0, mgp_y=0.0), dict(mgp_x=11.0), dict(mgp_x=float("nan")), dict(mgp_x=1.0, mgp_y=12.0)):
+        with pytest.raises(ofd.OFDFTError):
+            g.energy_potential(r, ofd.Functional(precision=L.FP64, n_knots=5, **kw))
 
 
 def test_bad_density_and_unsupported_size_are_errors():
