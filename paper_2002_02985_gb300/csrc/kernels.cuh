@@ -707,17 +707,28 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
                     S = slot(sl);
                 }
                 T fN = 0;
-                for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
-                    const T K = (T)kCWT * kval(gn[idx] * hk);
-                    if (exact) {
-                        // E_NL += Omega sum_G w Re(conj(FFT[h_m rho^alpha]) K_m FFT[rho^beta])
-                        const C Sm = cscale(S[idx], invN);
-                        const C Rb = Rr[idx];
-                        fN += cw[idx % TW] * K * (Sm.x * Rb.x + Sm.y * Rb.y);
-                        A[idx] = cadd(A[idx], cscale(Sm, K));
+                // the kernel's form is fixed for the launch: one loop per form, no per-G test
+                auto knot_loop = [&](auto mgp) {
+                    for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
+                        T K;
+                        if constexpr (decltype(mgp)::value) {
+                            const T eta = gn[idx] * hk;
+                            K = (T)kCWT * (a.mgp_1mx * gnl(eta) + a.mgp_3xy * mgp_j(a.mgp_tab, a.mgp_n, eta));
+                        } else {
+                            K = (T)kCWT * gnl(gn[idx] * hk);
+                        }
+                        if (exact) {
+                            // E_NL += Omega sum_G w Re(conj(FFT[h_m rho^alpha]) K_m FFT[rho^beta])
+                            const C Sm = cscale(S[idx], invN);
+                            const C Rb = Rr[idx];
+                            fN += cw[idx % TW] * K * (Sm.x * Rb.x + Sm.y * Rb.y);
+                            A[idx] = cadd(A[idx], cscale(Sm, K));
+                        }
+                        S[idx] = cscale(Rr[idx], K);
                     }
-                    S[idx] = cscale(Rr[idx], K);
-                }
+                };
+                if (a.mgp_tab) knot_loop(std::true_type{});
+                else knot_loop(std::false_type{});
                 eN += (double)fN;
                 __syncthreads();
                 S = inv(S);

@@ -80,9 +80,9 @@ FP64_CASES = [
     # Eq. MGP kernels (tabulated correction on the GPU, quadrature in the oracle)
     ((12, 10, 15), dict(n_knots=5, mgp_x=1.0)),                       # LMGP
     ((16, 18, 20), dict(n_knots=6, mgp_x=0.5)),                       # LMGPA
-    ((14, 12, 16), dict(n_knots=5, mgp_x=1.0, mgp_y=5.0 / 3.0)),      # LMGPG
+    ((15, 12, 16), dict(n_knots=5, mgp_x=1.0, mgp_y=5.0 / 3.0)),      # LMGPG
     ((20, 20, 20), dict(n_knots=4, kernel=L.KERNEL_WT_GLOBAL, mgp_x=1.0)),   # MGP (global k_F)
-    ((16, 14, 18), dict(n_knots=6, mgp_x=1.0, nl_potential=L.NLPOT_INTERP)),
+    ((16, 18, 12), dict(n_knots=6, mgp_x=1.0, nl_potential=L.NLPOT_INTERP)),
 ]
 
 
