@@ -219,6 +219,7 @@ template <typename T> int choose_launch(ofdft_grid *g, Workspace<T> &w) {
     // axis 0 with the reciprocal-space products
     if (!generic_only && find_specialised<T>(ROLE_AXIS0, g->n[0], &k1, &k2, &Bv, &ntv)) {
         w.ks.axis0 = k1;
+        w.ks.axis0_mgp = k2;
         w.TW0 = Bv;
         w.thr_ax0 = ntv;
         w.ax0_scr = axis0_oop<T>(g->n[0]) ? 1 : 0;

@@ -148,6 +148,7 @@ struct LaunchSet {
     const void *row_fwd = nullptr, *row_inv = nullptr;   // depend on n2
     const void *pen_fwd = nullptr, *pen_inv = nullptr;   // depend on n1
     const void *axis0 = nullptr;                         // depends on n0
+    const void *axis0_mgp = nullptr;                     // the same with Eq. MGP kernels
 };
 
 // role of a kernel family for the size registry

@@ -20,13 +20,14 @@ template <typename T> LaunchSet generic_kernels() {
     ks.row_inv = (const void *)row_inv_kernel<T, RtPolicy<T, 2>>;
     ks.pen_fwd = (const void *)pencil1_kernel<T, -1, RtPolicy<T, 1>>;
     ks.pen_inv = (const void *)pencil1_kernel<T, +1, RtPolicy<T, 1>>;
-    ks.axis0 = (const void *)axis0_kernel<T, RtPolicy<T, 0>>;
+    ks.axis0 = (const void *)axis0_kernel<T, RtPolicy<T, 0>, false>;
+    ks.axis0_mgp = (const void *)axis0_kernel<T, RtPolicy<T, 0>, true>;
     return ks;
 }
 
 cudaError_t prepare_kernels(const LaunchSet &ks) {
-    const void *k[5] = {ks.row_fwd, ks.row_inv, ks.pen_fwd, ks.pen_inv, ks.axis0};
-    for (int i = 0; i < 5; i++) {
+    const void *k[6] = {ks.row_fwd, ks.row_inv, ks.pen_fwd, ks.pen_inv, ks.axis0, ks.axis0_mgp};
+    for (int i = 0; i < 6; i++) {
         if (!k[i]) continue;
         cudaError_t e = allow_max_dynamic_smem(k[i]);
         if (e != cudaSuccess) return e;
@@ -71,7 +72,8 @@ cudaError_t launch_eval(const EvalArgs<T> &a, const LaunchSet &ks, cudaStream_t 
         mark(K_PENCIL_FWD, 1);
     }
     mark(K_AXIS0, 0);
-    e = launch(ks.axis0, dim3(a.nb_ax0), a.thr_ax0, axis0_smem_bytes<T>(a.n0, a.TW0, a.ax0_scr), a, s);
+    e = launch(a.mgp_tab ? ks.axis0_mgp : ks.axis0, dim3(a.nb_ax0), a.thr_ax0,
+               axis0_smem_bytes<T>(a.n0, a.TW0, a.ax0_scr), a, s);
     if (e) return e;
     mark(K_AXIS0, 1);
     if (a.ncol_inv > 0) {

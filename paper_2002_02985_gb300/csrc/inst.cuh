@@ -30,8 +30,8 @@
             *B = PTW;                                                                         \
             *nt = PNT;                                                                        \
         } else {                                                                              \
-            *k1 = (const void *)axis0_kernel<T, PA>;                                          \
-            *k2 = nullptr;                                                                    \
+            *k1 = (const void *)axis0_kernel<T, PA, false>;                                   \
+            *k2 = (const void *)axis0_kernel<T, PA, true>;                                    \
             *B = ATW;                                                                         \
             *nt = ANT;                                                                        \
         }                                                                                     \
@@ -65,12 +65,13 @@
 
 
 // OFDFT_SPECIALISE_AXIS0(T, N, TW, NT, MAXR, MINB): only the reciprocal-space kernel for n0 = N
-// (out of place or in place as axis0_oop<T>(N) says, which the host also uses for its scratch).
+// (out of place or in place as axis0_oop<T>(N) says, which the host also uses for its scratch);
+// k1 is the Wang-Teter form, k2 the Eq. MGP form.
 #define OFDFT_SPECIALISE_AXIS0(T, N, TW, NT, MAXR, MINB)                                      \
     if (role == ROLE_AXIS0 && n == N) {                                                       \
         typedef ::ofdft::CtPolicy<T, N, TW, TW, NT, MAXR, MINB, ::ofdft::axis0_oop<T>(N)> PA;  \
-        *k1 = (const void *)axis0_kernel<T, PA>;                                              \
-        *k2 = nullptr;                                                                        \
+        *k1 = (const void *)axis0_kernel<T, PA, false>;                                       \
+        *k2 = (const void *)axis0_kernel<T, PA, true>;                                        \
         *B = TW;                                                                              \
         *nt = NT;                                                                             \
         return true;                                                                          \

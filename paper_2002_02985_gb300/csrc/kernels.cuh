@@ -491,7 +491,7 @@ __device__ __forceinline__ void pencil1_body(const EvalArgs<T> &a) {
 // of two rotating buffers while the current one is transformed.
 // Partials per block: [0] sum_G w |rho_hat|^2/G^2, [1] sum_G w G^2 |psi_hat|^2,
 // [2] sum_G w Re(conj(rho_hat) V_ext), [3] nonlocal energy in G space.
-template <typename T, class P>
+template <typename T, class P, bool MGP>
 __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
     typedef typename Vec2<T>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -595,10 +595,10 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
     }
     const T invN = (T)(1.0 / (double)a.N);
     double eH = 0.0, eV = 0.0, eP = 0.0, eN = 0.0;
-    // kernel of Eq. WT, or of Eq. MGP when the correction table is given
+    // kernel of Eq. WT, or of Eq. MGP (the instantiation with the correction table)
     auto kval = [&](T eta) -> T {
-        const T gv = gnl(eta);
-        return a.mgp_tab ? a.mgp_1mx * gv + a.mgp_3xy * mgp_j(a.mgp_tab, a.mgp_n, eta) : gv;
+        if constexpr (MGP) return a.mgp_1mx * gnl(eta) + a.mgp_3xy * mgp_j(a.mgp_tab, a.mgp_n, eta);
+        else return gnl(eta);
     };
 
     // ---- Hartree + local pseudopotential
@@ -707,28 +707,17 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
                     S = slot(sl);
                 }
                 T fN = 0;
-                // the kernel's form is fixed for the launch: one loop per form, no per-G test
-                auto knot_loop = [&](auto mgp) {
-                    for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
-                        T K;
-                        if constexpr (decltype(mgp)::value) {
-                            const T eta = gn[idx] * hk;
-                            K = (T)kCWT * (a.mgp_1mx * gnl(eta) + a.mgp_3xy * mgp_j(a.mgp_tab, a.mgp_n, eta));
-                        } else {
-                            K = (T)kCWT * gnl(gn[idx] * hk);
-                        }
-                        if (exact) {
-                            // E_NL += Omega sum_G w Re(conj(FFT[h_m rho^alpha]) K_m FFT[rho^beta])
-                            const C Sm = cscale(S[idx], invN);
-                            const C Rb = Rr[idx];
-                            fN += cw[idx % TW] * K * (Sm.x * Rb.x + Sm.y * Rb.y);
-                            A[idx] = cadd(A[idx], cscale(Sm, K));
-                        }
-                        S[idx] = cscale(Rr[idx], K);
+                for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
+                    const T K = (T)kCWT * kval(gn[idx] * hk);
+                    if (exact) {
+                        // E_NL += Omega sum_G w Re(conj(FFT[h_m rho^alpha]) K_m FFT[rho^beta])
+                        const C Sm = cscale(S[idx], invN);
+                        const C Rb = Rr[idx];
+                        fN += cw[idx % TW] * K * (Sm.x * Rb.x + Sm.y * Rb.y);
+                        A[idx] = cadd(A[idx], cscale(Sm, K));
                     }
-                };
-                if (a.mgp_tab) knot_loop(std::true_type{});
-                else knot_loop(std::false_type{});
+                    S[idx] = cscale(Rr[idx], K);
+                }
                 eN += (double)fN;
                 __syncthreads();
                 S = inv(S);
@@ -1332,9 +1321,11 @@ template <typename T, int DIR, class P>
 __global__ void __launch_bounds__(P::max_threads, P::min_blocks) pencil1_kernel(EvalArgs<T> a) {
     pencil1_body<T, DIR, P>(a);
 }
-template <typename T, class P>
+// MGP: the knots' kernels of Eq. MGP from the correction table (a separate instantiation,
+// so that the Wang-Teter form carries no trace of it)
+template <typename T, class P, bool MGP = false>
 __global__ void __launch_bounds__(P::max_threads, P::min_blocks_ax0) axis0_kernel(EvalArgs<T> a) {
-    axis0_body<T, P>(a);
+    axis0_body<T, P, MGP>(a);
 }
 template <typename T, class P>
 __global__ void __launch_bounds__(P::max_threads, P::min_blocks) row_inv_kernel(EvalArgs<T> a) {
