@@ -216,6 +216,8 @@ def workload(name: str, index: int = 0) -> dict:
     fcc-al-108-snap  snapshot `index` (0..63) of jittered 108-atom FCC Al,
                      grid drawn from {64,80,96,120}^3, 16 knots
     fcc-al-1m/1024   64^3 FCC Al cells (1,048,576 atoms), 1024^3, 12 knots
+    mg55/128         Mackay icosahedron Mg55 in a 40 bohr box, 128^3 (>= 9 bohr of vacuum
+                     around the outer shell: an isolated cluster for dipoles and spectra)
     """
     if name == "fcc-al-4/32":
         return _al_workload(1, (32, 32, 32), 0.05, 1, 10)
@@ -237,4 +239,12 @@ def workload(name: str, index: int = 0) -> dict:
                     species=np.zeros(n, dtype=np.int32), Z=np.array([2.0]), rc=np.array([1.0]),
                     charges=np.full(n, 2.0), n_electrons=2.0 * n, sigma=1.4, noise=0.0, seed=3,
                     density_floor=1e-8, n_knots=30, n_atoms=n)
+    if name == "mg55/128":
+        L = 40.0
+        pos = mackay_icosahedron(2, 5.5) + L / 2.0
+        n = len(pos)
+        return dict(cell=np.diag([L, L, L]), shape=(128, 128, 128), positions=pos,
+                    species=np.zeros(n, dtype=np.int32), Z=np.array([2.0]), rc=np.array([1.0]),
+                    charges=np.full(n, 2.0), n_electrons=2.0 * n, sigma=1.4, noise=0.0, seed=3,
+                    density_floor=1e-8, n_knots=16, n_atoms=n)
     raise KeyError(name)
