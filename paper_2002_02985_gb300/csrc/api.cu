@@ -82,6 +82,10 @@ template <typename T> struct Workspace {
     int grid_p1 = 0;
     int row2_G = 0;                   // channel-batched row kernels in use: channels per group
     int ax0_scr = 0;                  // the reciprocal-space kernel transforms out of place
+    // plain one-channel transforms (preconditioner, interpolation, TD-OFDFT): the per-channel row
+    // kernels where compiled (the channel-batched ones would leave most of each block idle)
+    LaunchSet ks_plain;
+    int Brow_p = 0, thr_rowf_p = 0, thr_rowi_p = 0, row2_G_p = 0;
 };
 
 }  // namespace
@@ -231,7 +235,20 @@ template <typename T> int choose_launch(ofdft_grid *g, Workspace<T> &w) {
         w.TW0 = TW;
         w.thr_ax0 = std::min(std::max(threads_for(g->plan[0], TW, cap), 128), tmax);
     }
+    w.ks_plain = w.ks;
+    w.Brow_p = w.Brow;
+    w.thr_rowf_p = w.thr_rowf;
+    w.thr_rowi_p = w.thr_rowi;
+    w.row2_G_p = w.row2_G;
+    if (w.row2_G && find_specialised<T>(ROLE_ROW, g->n[2], &k1, &k2, &Bv, &ntv)) {
+        w.ks_plain.row_fwd = k1;
+        w.ks_plain.row_inv = k2;
+        w.Brow_p = Bv;
+        w.thr_rowf_p = w.thr_rowi_p = ntv;
+        w.row2_G_p = 0;
+    }
     cudaError_t e = prepare_kernels(w.ks);
+    if (e == cudaSuccess) e = prepare_kernels(w.ks_plain);
     if (e != cudaSuccess) return fail(g, OFDFT_ERR_CUDA, "kernel attributes", e);
     // persistent pencil grid: every resident block slot of the device, once
     int per_sm = 0;
@@ -614,9 +631,9 @@ template <typename T> EvalArgs<T> plain_args(ofdft_grid *g, Workspace<T> &w, con
     a.nb_stats = 2 * g->nsm; a.nb_ax0 = w.nb_ax0; a.nb_row = w.nb_row;
     a.p0 = g->plan[0]; a.p1 = g->plan[1]; a.p2 = g->plan[2];
     a.tw0 = w.tw[0]; a.tw1 = w.tw[1]; a.tw2 = w.tw[2];
-    a.Brow = w.Brow; a.thr_rowf = w.thr_rowf; a.thr_rowi = w.thr_rowi;
+    a.Brow = w.Brow_p; a.thr_rowf = w.thr_rowf_p; a.thr_rowi = w.thr_rowi_p;
     a.TW1 = w.TW1; a.thr_p1 = w.thr_p1; a.TW0 = w.TW0; a.thr_ax0 = w.thr_ax0; a.grid_p1 = w.grid_p1;
-    a.row2_G = w.row2_G; a.ax0_scr = w.ax0_scr;
+    a.row2_G = w.row2_G_p; a.ax0_scr = w.ax0_scr;
     a.nfwd = 1; a.fwd_ch[0] = CH_HPP; a.ncol = 1; a.col_ch[0] = CH_HPP;
     return a;
 }
@@ -624,7 +641,7 @@ template <typename T> EvalArgs<T> plain_args(ofdft_grid *g, Workspace<T> &w, con
 // normalised half spectrum (1/N) of a real field into slot CH_HPP (G = 0 is not kept)
 template <typename T> int forward_plain(ofdft_grid *g, Workspace<T> &w, const T *field) {
     EvalArgs<T> a = plain_args<T>(g, w, field);
-    CK(launch_forward_rows_cols<T>(a, w.ks, g->stream), "forward transform");
+    CK(launch_forward_rows_cols<T>(a, w.ks_plain, g->stream), "forward transform");
     CK(launch_axis0_fft<T>(w.chan, g->n[0], (long long)g->n[1] * g->n2h, g->plan[0], w.tw[0], w.TW0, w.thr_ax0,
                            1.0 / (double)g->N, g->stream, -1),
        "forward transform along n0");
@@ -645,7 +662,7 @@ template <typename T> int inverse_plain(ofdft_grid *g, Workspace<T> &w, int slot
     CK(launch_axis0_fft<T>((C *)w.chan + (size_t)slot * g->NH, g->n[0], (long long)g->n[1] * g->n2h, g->plan[0],
                            w.tw[0], w.TW0, w.thr_ax0, 1.0, g->stream, +1),
        "inverse transform along n0");
-    CK(launch_inverse_cols_rows<T>(a, w.ks, g->stream), "inverse transform");
+    CK(launch_inverse_cols_rows<T>(a, w.ks_plain, g->stream), "inverse transform");
     return OFDFT_OK;
 }
 

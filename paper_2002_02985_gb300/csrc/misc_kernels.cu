@@ -343,6 +343,14 @@ cudaError_t launch_axis0_fft(typename Vec2<T>::type *data, int n0, long long P, 
         if (e != cudaSuccess) return e;
         attr = true;
     }
+    // a plain transform has one channel: wide column tiles (coalesced rows of up to 32 complex)
+    // and 256 threads, independent of the reciprocal-space kernel's tile
+    (void)TW;
+    (void)thr;
+    int tw_cols = 32;
+    while (tw_cols > 1 && (size_t)n0 * sizeof(C) * (1 + tw_cols) > 96 * 1024) tw_cols /= 2;
+    TW = tw_cols;
+    thr = 256;
     const size_t sm = (size_t)n0 * sizeof(C) * (1 + TW);
     const unsigned nb = (unsigned)((P + TW - 1) / TW);
     if (dir < 0) axis0_fft_kernel<T, CAP, -1><<<nb, thr, sm, s>>>(data, n0, P, p, tw, TW, (T)scale);
@@ -360,10 +368,23 @@ __global__ void __launch_bounds__(256) dot_kernel(const T *a, const T *b, const 
     __shared__ double sd[32];
     double acc = 0.0;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += stride) {
-        double v = (double)a[i] * (double)b[i];
-        if (c) v *= (double)c[i];
-        acc += v;
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (sizeof(T) == 4) {
+        // FP32 products in groups of 8 grid strides, each group added in FP64 (the FP64 pipe
+        // of GB300 would otherwise bound this pass)
+        while (i < N) {
+            T g = 0;
+#pragma unroll
+            for (int u = 0; u < 8; u++, i += stride)
+                if (i < N) g += c ? a[i] * b[i] * c[i] : a[i] * b[i];
+            acc += (double)g;
+        }
+    } else {
+        for (; i < N; i += stride) {
+            double v = (double)a[i] * (double)b[i];
+            if (c) v *= (double)c[i];
+            acc += v;
+        }
     }
     acc = block_sum(acc, sd);
     if (threadIdx.x == 0) part[blockIdx.x] = acc;
@@ -545,29 +566,45 @@ template <typename T> cudaError_t launch_add_scalar(T *x, const double *c, long 
     return cudaGetLastError();
 }
 
+// G^2 of half-spectrum element e in the spectrum's own precision R (float for the FP32-mixed
+// path: GB300's FP64 rate would make these elementwise passes FP64-bound)
+template <typename R>
+__device__ __forceinline__ R half_spectrum_g2(long long e, int n0, int n1, int n2h, const R *b) {
+    const int k2 = (int)(e % n2h);
+    const long long r = e / n2h;
+    const int k1 = (int)(r % n1), k0 = (int)(r / n1);
+    const R m0 = (R)((k0 <= n0 / 2) ? k0 : k0 - n0), m1 = (R)((k1 <= n1 / 2) ? k1 : k1 - n1), m2 = (R)k2;
+    const R gx = m0 * b[0] + m1 * b[3] + m2 * b[6], gy = m0 * b[1] + m1 * b[4] + m2 * b[7],
+            gz = m0 * b[2] + m1 * b[5] + m2 * b[8];
+    return gx * gx + gy * gy + gz * gz;
+}
+struct Bvec9 {
+    double v[9];
+};
+
 template <typename C>
-__global__ void precond_kernel(C *h, int n0, int n1, int n2, double b0, double b1, double b2, double b3,
-                               double b4, double b5, double b6, double b7, double b8, double pa, double pb) {
+__global__ void precond_kernel(C *h, int n0, int n1, int n2, Bvec9 bv, double pa_, double pb_) {
+    typedef decltype(h[0].x) R;
+    R b[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++) b[i] = (R)bv.v[i];
+    const R pa = (R)pa_, pb = (R)pb_;
     const int n2h = n2 / 2 + 1;
     const long long NH = (long long)n0 * n1 * n2h, stride = (long long)gridDim.x * blockDim.x;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < NH; e += stride) {
-        const int k2 = (int)(e % n2h);
-        const long long r = e / n2h;
-        const int k1 = (int)(r % n1), k0 = (int)(r / n1);
-        const double m0 = (k0 <= n0 / 2) ? k0 : k0 - n0, m1 = (k1 <= n1 / 2) ? k1 : k1 - n1, m2 = k2;
-        const double gx = m0 * b0 + m1 * b3 + m2 * b6, gy = m0 * b1 + m1 * b4 + m2 * b7, gz = m0 * b2 + m1 * b5 + m2 * b8;
-        const double q2 = gx * gx + gy * gy + gz * gz;
-        const double f = (q2 > 0.0) ? pa * q2 / (q2 * q2 + pa * q2 + pb) : 1.0;
+        const R q2 = half_spectrum_g2<R>(e, n0, n1, n2h, b);
+        const R f = (q2 > (R)0) ? pa * q2 / (q2 * q2 + pa * q2 + pb) : (R)1;
         C v = h[e];
-        v.x = (decltype(v.x))(v.x * f);
-        v.y = (decltype(v.y))(v.y * f);
+        v.x *= f;
+        v.y *= f;
         h[e] = v;
     }
 }
 template <typename C>
 cudaError_t launch_precond(C *h, int n0, int n1, int n2, const double *bv, double a, double b, cudaStream_t s) {
-    precond_kernel<C><<<1216, 256, 0, s>>>(h, n0, n1, n2, bv[0], bv[1], bv[2], bv[3], bv[4], bv[5], bv[6], bv[7],
-                                           bv[8], a, b);
+    Bvec9 b9;
+    for (int i = 0; i < 9; i++) b9.v[i] = bv[i];
+    precond_kernel<C><<<1216, 256, 0, s>>>(h, n0, n1, n2, b9, a, b);
     return cudaGetLastError();
 }
 template cudaError_t launch_precond<float2>(float2 *, int, int, int, const double *, double, double, cudaStream_t);
@@ -595,40 +632,38 @@ cudaError_t launch_hvp(T *Hq, const T *psi, const T *q, const T *V, const T *Vq,
 // h(G) *= f(G) on a normalised half spectrum: MODE 0 the kinetic K = G^2/2 (K(0) = 0),
 // MODE 1 the Crank-Nicolson normal-equation preconditioner 1 / (1 + tau^2 (G^2/2 + vbar)^2)
 template <typename C, int MODE>
-__global__ void spectral_factor_kernel(C *h, int n0, int n1, int n2, double b0, double b1, double b2, double b3,
-                                       double b4, double b5, double b6, double b7, double b8, double tau,
-                                       double vbar) {
+__global__ void spectral_factor_kernel(C *h, int n0, int n1, int n2, Bvec9 bv, double tau_, double vbar_) {
+    typedef decltype(h[0].x) R;
+    R b[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++) b[i] = (R)bv.v[i];
+    const R tau = (R)tau_, vbar = (R)vbar_;
     const int n2h = n2 / 2 + 1;
     const long long NH = (long long)n0 * n1 * n2h, stride = (long long)gridDim.x * blockDim.x;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < NH; e += stride) {
-        const int k2 = (int)(e % n2h);
-        const long long r = e / n2h;
-        const int k1 = (int)(r % n1), k0 = (int)(r / n1);
-        const double m0 = (k0 <= n0 / 2) ? k0 : k0 - n0, m1 = (k1 <= n1 / 2) ? k1 : k1 - n1, m2 = k2;
-        const double gx = m0 * b0 + m1 * b3 + m2 * b6, gy = m0 * b1 + m1 * b4 + m2 * b7, gz = m0 * b2 + m1 * b5 + m2 * b8;
-        const double kin = 0.5 * (gx * gx + gy * gy + gz * gz);
-        double f;
+        const R kin = (R)0.5 * half_spectrum_g2<R>(e, n0, n1, n2h, b);
+        R f;
         if (MODE == 0) {
             f = kin;
         } else {
-            const double a = tau * (kin + vbar);
-            f = 1.0 / (1.0 + a * a);
+            const R x = tau * (kin + vbar);
+            f = (R)1 / ((R)1 + x * x);
         }
         C v = h[e];
-        v.x = (decltype(v.x))(v.x * f);
-        v.y = (decltype(v.y))(v.y * f);
+        v.x *= f;
+        v.y *= f;
         h[e] = v;
     }
 }
 template <typename C>
 cudaError_t launch_spectral_factor(C *h, int n0, int n1, int n2, const double *bv, int mode, double tau, double vbar,
                                    cudaStream_t s) {
+    Bvec9 b9;
+    for (int i = 0; i < 9; i++) b9.v[i] = bv[i];
     if (mode == 0)
-        spectral_factor_kernel<C, 0><<<1216, 256, 0, s>>>(h, n0, n1, n2, bv[0], bv[1], bv[2], bv[3], bv[4], bv[5],
-                                                         bv[6], bv[7], bv[8], tau, vbar);
+        spectral_factor_kernel<C, 0><<<1216, 256, 0, s>>>(h, n0, n1, n2, b9, tau, vbar);
     else
-        spectral_factor_kernel<C, 1><<<1216, 256, 0, s>>>(h, n0, n1, n2, bv[0], bv[1], bv[2], bv[3], bv[4], bv[5],
-                                                         bv[6], bv[7], bv[8], tau, vbar);
+        spectral_factor_kernel<C, 1><<<1216, 256, 0, s>>>(h, n0, n1, n2, b9, tau, vbar);
     return cudaGetLastError();
 }
 template cudaError_t launch_spectral_factor<float2>(float2 *, int, int, int, const double *, int, double, double,
@@ -704,21 +739,28 @@ cudaError_t launch_kick(T *re, T *im, int n0, int n1, int n2, const TdCell &c, c
     return cudaGetLastError();
 }
 
-// partials of sum_r r (|psi|^2 - rho0) dV: part[3 b + k], then the three sums into out[0..2]
+// partials of sum_r r (|psi|^2 - rho0) dV: part[3 b + k], then the three sums into out[0..2].
+// Positions and products in T (FP32 in the FP32-mixed path), sums in FP64.
 template <typename T>
 __global__ void __launch_bounds__(256) dipole_kernel(const T *re, const T *im, const T *rho0, int n0, int n1, int n2,
                                                      TdCell c, double dV, long long N, double *part) {
     __shared__ double sd[3 * 32];
     double acc[3] = {0.0, 0.0, 0.0};
+    T a9[9];
+#pragma unroll
+    for (int k = 0; k < 9; k++) a9[k] = (T)c.a[k];
+    const T r0 = (T)1 / (T)n0, r1 = (T)1 / (T)n1, r2 = (T)1 / (T)n2;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += stride) {
-        double x, y, z;
-        centred_position(i, n0, n1, n2, c, x, y, z);
-        const double a = (double)re[i], b = (double)im[i];
-        const double d = a * a + b * b - (rho0 ? (double)rho0[i] : 0.0);
-        acc[0] += x * d;
-        acc[1] += y * d;
-        acc[2] += z * d;
+        const int i2 = (int)(i % n2);
+        const long long q = i / n2;
+        const int i1 = (int)(q % n1), i0 = (int)(q / n1);
+        const T f0 = (T)i0 * r0 - (T)0.5, f1 = (T)i1 * r1 - (T)0.5, f2 = (T)i2 * r2 - (T)0.5;
+        const T a = re[i], b = im[i];
+        const T d = a * a + b * b - (rho0 ? rho0[i] : (T)0);
+        acc[0] += (double)((f0 * a9[0] + f1 * a9[3] + f2 * a9[6]) * d);
+        acc[1] += (double)((f0 * a9[1] + f1 * a9[4] + f2 * a9[7]) * d);
+        acc[2] += (double)((f0 * a9[2] + f1 * a9[5] + f2 * a9[8]) * d);
     }
     block_sum_n<3>(acc, sd);
     if (threadIdx.x == 0)
