@@ -331,11 +331,58 @@ __global__ void __launch_bounds__(512) axis0_fft_kernel(typename Vec2<T>::type *
     }
 }
 
+// the same with the length, the tile (TWC columns) and the radix plan fixed at compile time
+template <typename T, int N, int TWC, int DIR>
+__global__ void __launch_bounds__(256) axis0_fft_ct_kernel(typename Vec2<T>::type *data, long long P,
+                                                           const typename Vec2<T>::type *twg, T scale) {
+    typedef typename Vec2<T>::type C;
+    constexpr int MAXR = sizeof(T) == 4 ? 16 : 8;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tw = (C *)smem_raw;
+    C *buf = tw + N;
+    for (int i = threadIdx.x; i < N; i += 256) tw[i] = twg[i];
+    const long long c0 = (long long)blockIdx.x * TWC;
+    for (int idx = threadIdx.x; idx < N * TWC; idx += 256) {
+        const int w = idx % TWC, i = idx / TWC;
+        buf[idx] = (c0 + w < P) ? data[(size_t)i * P + c0 + w] : cmake<C>((T)0, (T)0);
+    }
+    __syncthreads();
+    ct::fft<DIR, N, TWC, TWC, 256, MAXR>(buf, tw);
+    for (int idx = threadIdx.x; idx < N * TWC; idx += 256) {
+        const int w = idx % TWC, i = idx / TWC;
+        if (c0 + w < P) data[(size_t)i * P + c0 + w] = cscale(buf[idx], scale);
+    }
+}
+
+template <typename T, int N, int TWC>
+cudaError_t launch_axis0_fft_ct(typename Vec2<T>::type *data, long long P, const typename Vec2<T>::type *tw,
+                                double scale, cudaStream_t s, int dir) {
+    typedef typename Vec2<T>::type C;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = allow_max_dynamic_smem(axis0_fft_ct_kernel<T, N, TWC, -1>);
+        if (e == cudaSuccess) e = allow_max_dynamic_smem(axis0_fft_ct_kernel<T, N, TWC, 1>);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const size_t sm = (size_t)N * sizeof(C) * (1 + TWC);
+    const unsigned nb = (unsigned)((P + TWC - 1) / TWC);
+    if (dir < 0) axis0_fft_ct_kernel<T, N, TWC, -1><<<nb, 256, sm, s>>>(data, P, tw, (T)scale);
+    else axis0_fft_ct_kernel<T, N, TWC, 1><<<nb, 256, sm, s>>>(data, P, tw, (T)scale);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_axis0_fft(typename Vec2<T>::type *data, int n0, long long P, const FFTPlan &p,
                              const typename Vec2<T>::type *tw, int TW, int thr, double scale, cudaStream_t s, int dir) {
     typedef typename Vec2<T>::type C;
     constexpr int CAP = sizeof(T) == 4 ? 16 : 8;
+    // compile-time forms for the common lengths
+    if (n0 == 64) return launch_axis0_fft_ct<T, 64, 32>(data, P, tw, scale, s, dir);
+    if (n0 == 96) return launch_axis0_fft_ct<T, 96, 32>(data, P, tw, scale, s, dir);
+    if (n0 == 128) return launch_axis0_fft_ct<T, 128, 32>(data, P, tw, scale, s, dir);
+    if (n0 == 192) return launch_axis0_fft_ct<T, 192, 16>(data, P, tw, scale, s, dir);
+    if (n0 == 256) return launch_axis0_fft_ct<T, 256, 16>(data, P, tw, scale, s, dir);
     static bool attr = false;
     if (!attr) {
         cudaError_t e = allow_max_dynamic_smem(axis0_fft_kernel<T, CAP, -1>);

@@ -50,9 +50,10 @@ def _run_gpu(cell, shape, psi0, rho0, func, dt, n, n_corr=1, ions=None, tol=0.0)
     return re.double().cpu().numpy() + 1j * im.double().cpu().numpy(), dip, rep, g
 
 
+@pytest.mark.parametrize("n", [16, 64, 96, 128, 192, 256])     # generic and compile-time n0 transforms
 @pytest.mark.parametrize("precision,tol", [(L.FP64, 1e-11), (L.FP32_MIXED, 2e-5)])
-def test_plane_wave_takes_the_cn_phase(precision, tol):
-    og, cell = _box(16, 10.0)
+def test_plane_wave_takes_the_cn_phase(precision, tol, n):
+    og, cell = _box(n, 10.0)
     G = 2 * np.pi * np.array([2.0, -1.0, 3.0]) / 10.0
     psi0 = np.exp(1j * (otd.positions(og) @ G))
     dt, n = 0.3, 7
