@@ -77,6 +77,13 @@ class Functional:
         return torch.float64 if self.precision == L.FP64 else torch.float32
 
 
+# Eq. MGP's (x, y) of the named functionals (Sec. 2.3): Functional(**MGP) etc.; with the
+# default local kernel they are LMGP / LMGPA / LMGPG
+MGP = dict(mgp_x=1.0, mgp_y=5.0 / 6.0)
+MGPA = dict(mgp_x=0.5, mgp_y=5.0 / 6.0)
+MGPG = dict(mgp_x=1.0, mgp_y=5.0 / 3.0)
+
+
 def _check(lib, status, handle=None):
     if status != L.OFDFT_OK:
         msg = lib.ofdft_last_error(handle).decode() if handle else lib.ofdft_status_string(status).decode()
