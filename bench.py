@@ -71,7 +71,11 @@ class Clocks:
 
     def __init__(self, gpu_index):
         self.p = None
-        self.out = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # the raw samples go to $OFDFT_CLOCKS_DIR (default: the temporary directory); the JSON
+        # line carries their summary
+        import tempfile
+        d = os.environ.get("OFDFT_CLOCKS_DIR") or tempfile.gettempdir()
+        self.out = os.path.join(d, f"clocks_{os.getpid()}.csv")
         try:
             os.makedirs(os.path.dirname(self.out), exist_ok=True)
             self.f = open(self.out, "w")
