@@ -291,7 +291,7 @@ int ofdft_td_kick(ofdft_grid *g, void *psi_re, void *psi_im, const double k[3], 
  * imaginary parts by preconditioned CG (M = 1/(1 + dt^2/4 (G^2/2 + vbar)^2)).
  * rho0: DEVICE [N] reference density for the dipole, or NULL (0).  dipole: HOST
  * double[n_steps + 1][3] receiving delta mu(t_n) = sum_r r (|psi|^2 - rho0) dV, or NULL.
- * Allocates 20 device fields of N elements (kept with the grid).  Returns
+ * Allocates 19 device fields of N elements (kept with the grid).  Returns
  * OFDFT_ERR_NOT_CONVERGED (after all steps, report filled) if a solve reached max_solver_iter;
  * otherwise as ofdft_energy_potential (the functional's PP term needs ions). */
 int ofdft_td_propagate(ofdft_grid *g, void *psi_re, void *psi_im, const void *rho0, const ofdft_functional *f,

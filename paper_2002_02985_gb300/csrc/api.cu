@@ -73,7 +73,7 @@ template <typename T> struct Workspace {
     unsigned *ticket = nullptr;       // stats completion counter
     T *opt = nullptr;                 // optimiser fields (8 * N), allocated on demand
     T *opt_ext = nullptr;             // TN / L-BFGS fields (opt_ext_fields * N), on demand
-    T *td = nullptr;                  // TD-OFDFT fields (20 * N), on demand
+    T *td = nullptr;                  // TD-OFDFT fields (19 * N), on demand
     T *mgp_tab = nullptr;             // MGP correction table (kMgpTable points), on demand
     double mgp_y = 0.0;               // the y it was built for (0: not built)
     int opt_ext_fields = 0;
@@ -1458,7 +1458,7 @@ int optimize_impl(ofdft_grid *g, T *psi, const ofdft_functional *f0, double Ne, 
 // equations (1 + tau^2 H^2) x = (1 - i tau H)^2 psi(t): H is real, so the real and imaginary
 // parts are two real symmetric positive definite systems, solved together by preconditioned
 // CG with M = 1 / (1 + tau^2 (G^2/2 + vbar)^2) diagonal in G.
-constexpr int kTdFields = 20;
+constexpr int kTdFields = 19;
 
 template <typename T>
 int td_impl(ofdft_grid *g, T *pre, T *pim, const T *rho0, const ofdft_functional *f0, const ofdft_td_options &o,
@@ -1535,7 +1535,7 @@ int td_impl(ofdft_grid *g, T *pre, T *pim, const T *rho0, const ofdft_functional
         int e;
         vbar = 0.0;
         if (have_v) {   // v weighted by the density held in rho (any vbar gives the same solution)
-            const double sr = dv.dot(rho, rho) > 0.0 ? dv.dot(x[0], x[0]) + dv.dot(x[1], x[1]) : 0.0;
+            const double sr = dv.dot(x[0], x[0]) + dv.dot(x[1], x[1]);
             if (sr > 0.0) vbar = dv.dot(rho, v) / sr;
         }
         // c = (1 - i tau H)^2 psi(t):  c_re = p_re + 2 tau H p_im - tau^2 H^2 p_re,
