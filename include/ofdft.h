@@ -278,8 +278,10 @@ typedef struct {
     double max_residual;    /* largest final relative residual of a solve */
 } ofdft_td_report;
 
-/* psi <- psi exp(i k.r) (the laser kick; k HOST double[3], 1/bohr).  precision: of psi.
- * Enqueued on the handle's stream. */
+/* psi <- psi exp(i k.r) (the laser kick of the TD-OFDFT section, with this library's sign,
+ * see ofdft_td_propagate; k HOST double[3], 1/bohr).  psi_re, psi_im: DEVICE [N] of the
+ * precision given (OFDFT_FP32_MIXED: float, OFDFT_FP64: double).  Enqueued on the handle's
+ * stream.  Errors: OFDFT_ERR_INVALID_ARG (NULL pointer, unknown precision), OFDFT_ERR_CUDA. */
 int ofdft_td_kick(ofdft_grid *g, void *psi_re, void *psi_im, const double k[3], int precision);
 
 /* Propagate psi (DEVICE re/im, in place) by n_steps Crank-Nicolson steps
@@ -299,7 +301,9 @@ int ofdft_td_propagate(ofdft_grid *g, void *psi_re, void *psi_im, const void *rh
 
 /* Oscillator strength sigma(w) = w Im[delta mu~(w)] with delta mu~(w) = sum_n dmu_n
  * e^{(i w - gamma) t_n} dt, t_n = n dt (HOST arrays: dmu[n], omega[n_omega] -> sigma[n_omega];
- * dmu is the dipole component along the kick; gamma >= 0 damps the finite record). */
+ * dmu is the dipole component along the kick; gamma >= 0 damps the finite record).  Host
+ * arithmetic only (no device, no handle).  Errors: OFDFT_ERR_INVALID_ARG (NULL pointer,
+ * n < 1, n_omega < 0, dt = 0, gamma < 0). */
 int ofdft_td_spectrum(const double *dmu, int n, double dt, double gamma, int n_omega, const double *omega,
                       double *sigma);
 
