@@ -325,10 +325,40 @@ int ofdft_profile_enable(ofdft_grid *g, int enable);
 int ofdft_profile_reset(ofdft_grid *g);
 int ofdft_profile_read(ofdft_grid *g, int idx, const char **name, int *launches, double *total_ms);
 
+/* Options of a grid for tests, diagnostics and callers with special needs.  None
+ * changes what is computed (kernel choices agree to floating-point rounding).
+ *   OFDFT_OPTION_KERNELS      OFDFT_KERNELS_AUTO (default): size-specialised kernels where
+ *                             compiled, their launch shapes picked by the autotuner at the first
+ *                             evaluation; OFDFT_KERNELS_GENERIC: the runtime-size kernels only;
+ *                             OFDFT_KERNELS_PER_CHANNEL_ROWS: specialised kernels with the rows
+ *                             transformed one channel at a time; OFDFT_KERNELS_TILE_RECIP:
+ *                             specialised kernels with the column-tile reciprocal-space kernel in
+ *                             place of the persistent register-resident one.  A change drops the grid's
+ *                             workspaces (synchronising its stream); they are rebuilt on next use.
+ *   OFDFT_OPTION_BATCH_GRAPH  1 (default): a batched call whose first grid is g is captured once
+ *                             into a CUDA graph and replayed; 0: enqueued directly on every call.
+ *   OFDFT_OPTION_WAIT_POLLS   polls of the bounded device-side wait for bulk (TMA) copies before
+ *                             it gives up (default 4194304; 0 makes it give up at once, so that
+ *                             the evaluation returns OFDFT_ERR_TIMEOUT: a test of that path; the
+ *                             kernel still lets its copies land before it exits).
+ *   OFDFT_OPTION_ALLOC_CAP    bytes of device memory the grid may allocate from now on (0: no cap);
+ *                             an allocation past the cap fails with OFDFT_ERR_OOM.
+ * Errors: OFDFT_ERR_INVALID_ARG (NULL, unknown option or value). */
+#define OFDFT_OPTION_KERNELS      1
+#define OFDFT_OPTION_BATCH_GRAPH  2
+#define OFDFT_OPTION_WAIT_POLLS   3
+#define OFDFT_OPTION_ALLOC_CAP    4
+#define OFDFT_KERNELS_AUTO              0
+#define OFDFT_KERNELS_GENERIC           1
+#define OFDFT_KERNELS_PER_CHANNEL_ROWS  2
+#define OFDFT_KERNELS_TILE_RECIP        3
+int ofdft_set_option(ofdft_grid *g, int option, long long value);
+
 /* Thomas-Fermi energy and potential that allocates no device memory.
  * The paper has no counterpart: this exists for callers that cannot let a
  * library call cudaMalloc -- a host application whose own allocator owns all
- * device memory, or code running while a stream is captured into a CUDA graph.
+ * device memory (a pool sized up front, or memory shared with another runtime),
+ * or code that must not pay for cudaMalloc's device-wide synchronisation.
  * Computes E_TF = C_TF sum_r rho^(5/3) dV into E_dev (DEVICE double[1]) and,
  * when V_dev is not NULL, V_TF = (5/3) C_TF rho^(2/3) into V_dev (DEVICE [n],
  * same precision as rho), asynchronously on cuda_stream.  The reduction
@@ -338,7 +368,10 @@ int ofdft_profile_read(ofdft_grid *g, int idx, const char **name, int *launches,
  * The first call on each device looks up the array's device address (make it
  * before any stream capture).  All calls share the array, so calls that
  * overlap on the GPU race; order them on one stream.  Matches
- * ofdft_energy_potential with terms = OFDFT_TERM_TF. */
+ * ofdft_energy_potential with terms = OFDFT_TERM_TF, except on a bad density:
+ * NaN, Inf or negative values give E = NaN (the regular call returns
+ * OFDFT_ERR_BAD_DENSITY, which needs a synchronisation this call does not make);
+ * V is then (5/3) C_TF max(rho, 0)^(2/3) as in the regular call. */
 #define OFDFT_NOALLOC_MAX_POINTS 8388608LL   /* 4096 blocks x 2048 points */
 int ofdft_tf_energy_potential_noalloc(const void *rho_dev, long long n, double dV, int precision,
                                       double *E_dev, void *V_dev, void *cuda_stream);

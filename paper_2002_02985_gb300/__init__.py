@@ -117,6 +117,10 @@ class Grid:
         self.h = h
         self.n_ions = 0
 
+    def set_option(self, option: int, value: int):
+        """ofdft_set_option: kernel choice, batch graph, bounded-wait polls, allocation cap."""
+        _check(self.lib, self.lib.ofdft_set_option(self.h, option, int(value)), self.h)
+
     def close(self):
         if getattr(self, "h", None):
             self.lib.ofdft_grid_destroy(self.h)

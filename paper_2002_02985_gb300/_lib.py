@@ -28,6 +28,11 @@ FP64, FP32_MIXED = 0, 1
 OPT_CG, OPT_TN, OPT_LBFGS = 0, 1, 2
 UPDATE_ROTATE, UPDATE_SCALE = 0, 1
 OBJECTIVE_ENERGY, OBJECTIVE_RESIDUAL = 0, 1
+OPTION_KERNELS, OPTION_BATCH_GRAPH, OPTION_WAIT_POLLS, OPTION_ALLOC_CAP = 1, 2, 3, 4
+KERNELS_AUTO, KERNELS_GENERIC, KERNELS_PER_CHANNEL_ROWS, KERNELS_TILE_RECIP = 0, 1, 2, 3
+OFDFT_ERR_OOM = -4
+OFDFT_ERR_NOT_CONVERGED = -6
+OFDFT_ERR_TIMEOUT = -8
 
 # symbols declared in include/ofdft.h (checked by the CPU test suite)
 EXPORTS = (
@@ -37,7 +42,7 @@ EXPORTS = (
     "ofdft_profile_enable", "ofdft_profile_reset", "ofdft_profile_read",
     "ofdft_tf_energy_potential_noalloc", "ofdft_set_ions_pme", "ofdft_ewald", "ofdft_interpolate",
     "ofdft_optimize_density_multistep", "ofdft_optimize_density_ex", "ofdft_td_kick", "ofdft_td_propagate",
-    "ofdft_td_spectrum",
+    "ofdft_td_spectrum", "ofdft_set_option",
 )
 NOALLOC_MAX_POINTS = 8388608
 
@@ -114,6 +119,7 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.ofdft_profile_reset.argtypes = [P]
     lib.ofdft_profile_read.argtypes = [P, I, ct.POINTER(ct.c_char_p), ct.POINTER(I), ct.POINTER(D)]
     lib.ofdft_tf_energy_potential_noalloc.argtypes = [V, ct.c_longlong, D, I, V, V, P]
+    lib.ofdft_set_option.argtypes = [P, I, ct.c_longlong]
     lib.ofdft_status_string.argtypes = [I]
     lib.ofdft_status_string.restype = ct.c_char_p
     lib.ofdft_last_error.argtypes = [P]

@@ -8,8 +8,11 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "../../include/ofdft.h"
 #include "eval.cuh"
+#include "recip.cuh"
 #include "ewald.cuh"
 #include "misc.cuh"
 #include "pme.cuh"
@@ -86,6 +89,12 @@ template <typename T> struct Workspace {
     // kernels where compiled (the channel-batched ones would leave most of each block idle)
     LaunchSet ks_plain;
     int Brow_p = 0, thr_rowf_p = 0, thr_rowi_p = 0, row2_G_p = 0;
+    // persistent reciprocal-space kernel: its grid, and its tensor maps with the buffers
+    // and channel count they were encoded for
+    int recip_grid = 0;
+    RecipMaps maps;
+    const void *maps_chan = nullptr, *maps_vext = nullptr;
+    int maps_nslots = 0;
 };
 
 }  // namespace
@@ -134,6 +143,11 @@ struct ofdft_grid {
     double *d_Z = nullptr, *d_rc = nullptr;
     double *h_pinned = nullptr;  // 64 doubles of pinned host memory
     std::string err;
+    // ofdft_set_option
+    int kernel_choice = OFDFT_KERNELS_AUTO;
+    int batch_graph = 1;
+    unsigned wait_polls = 1u << 22;
+    size_t alloc_cap = 0, alloc_bytes = 0;
     // per-kernel CUDA-event timing (ofdft_profile_*)
     bool prof_on = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -168,23 +182,61 @@ int fail(ofdft_grid *g, int code, const char *what, cudaError_t e = cudaSuccess)
 
 static_assert(E_NUM == OFDFT_N_ENERGIES, "energy slots");
 
+// every device allocation of a grid goes through here: the optional cap of
+// ofdft_set_option(OFDFT_OPTION_ALLOC_CAP) is checked first (out of memory past it)
+template <typename P> cudaError_t gmalloc(ofdft_grid *g, P **p, size_t bytes) {
+    if (g->alloc_cap && g->alloc_bytes + bytes > g->alloc_cap) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMalloc((void **)p, bytes);
+    if (e == cudaSuccess) g->alloc_bytes += bytes;
+    return e;
+}
+
 template <typename T> Workspace<T> &ws(ofdft_grid *g);
 template <> Workspace<float> &ws<float>(ofdft_grid *g) { return g->w32; }
 template <> Workspace<double> &ws<double>(ofdft_grid *g) { return g->w64; }
+
+// cuTensorMapEncodeTiled from the driver (through the runtime's entry-point query, so the
+// library does not link libcuda); null if the driver does not provide it
+PFN_cuTensorMapEncodeTiled_v12000 tensor_encoder() {
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }();
+    return fn;
+}
+
+// 3-D tensor map over nch half spectra of T words: [channel][k0][c], c < PL complex values,
+// boxes of 32 complex x box_rows rows x 1 channel
+template <typename T>
+bool encode_spectra_map(CUtensorMap *m, const void *base, long long PL, int n0, int nch, int box_rows) {
+    const int wpc = 2;                                   // T words per complex value
+    const cuuint64_t dims[3] = {(cuuint64_t)(PL * wpc), (cuuint64_t)n0, (cuuint64_t)nch};
+    const cuuint64_t strides[2] = {(cuuint64_t)(PL * wpc * sizeof(T)), (cuuint64_t)(PL * n0 * wpc * sizeof(T))};
+    const cuuint32_t box[3] = {(cuuint32_t)(32 * wpc), (cuuint32_t)box_rows, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = tensor_encoder()(m, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                                        3, const_cast<void *>(base), dims, strides, box, estr,
+                                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
 
 template <typename T> int choose_launch(ofdft_grid *g, Workspace<T> &w) {
     typedef typename Vec2<T>::type C;
     const size_t row_budget = 110 * 1024;
     const int cap = Cap<T>::value, tmax = kMaxThreads;
-    const char *env = std::getenv("OFDFT_FORCE_GENERIC");
-    const bool generic_only = env && env[0] == '1';
+    const bool generic_only = g->kernel_choice == OFDFT_KERNELS_GENERIC;
     w.ks = generic_kernels<T>();
     const void *k1 = nullptr, *k2 = nullptr;
     int Bv = 0, ntv = 0;
-    // rows (n2): the channel-batched form where compiled (OFDFT_ROW_PER_CHANNEL=1 keeps the
-    // per-channel form, for comparison), else the per-channel form
-    const char *env_rows = std::getenv("OFDFT_ROW_PER_CHANNEL");
-    const bool per_channel = env_rows && env_rows[0] == '1';
+    // rows (n2): the channel-batched form where compiled (OFDFT_KERNELS_PER_CHANNEL_ROWS keeps
+    // the per-channel form, for comparison), else the per-channel form
+    const bool per_channel = g->kernel_choice == OFDFT_KERNELS_PER_CHANNEL_ROWS;
     w.row2_G = 0;
     if (!generic_only && !per_channel && find_specialised<T>(ROLE_ROW2, g->n[2], &k1, &k2, &Bv, &ntv)) {
         w.ks.row_fwd = k1;
@@ -235,6 +287,14 @@ template <typename T> int choose_launch(ofdft_grid *g, Workspace<T> &w) {
         w.TW0 = TW;
         w.thr_ax0 = std::min(std::max(threads_for(g->plan[0], TW, cap), 128), tmax);
     }
+    // the persistent reciprocal-space kernel where compiled for n0 (its tensor maps need rows of
+    // an even number of complex values: 16-byte strides)
+    w.ks.recip = RecipLaunch();
+    const long long PLc = (long long)g->n[1] * g->n2h;
+    RecipLaunch rl;
+    if (!generic_only && g->kernel_choice != OFDFT_KERNELS_TILE_RECIP && PLc % 2 == 0 && tensor_encoder() &&
+        find_recip<T>(g->n[0], &rl))
+        w.ks.recip = rl;
     w.ks_plain = w.ks;
     w.Brow_p = w.Brow;
     w.thr_rowf_p = w.thr_rowf;
@@ -260,6 +320,11 @@ template <typename T> int choose_launch(ofdft_grid *g, Workspace<T> &w) {
     w.nb_row = (int)(((R + 1) / 2 + w.Brow - 1) / w.Brow);
     const long long P = (long long)g->n[1] * g->n2h;
     w.nb_ax0 = (int)((P + w.TW0 - 1) / w.TW0);
+    if (w.ks.recip.k) {
+        const int ntile = (int)((P + 31) / 32);
+        w.recip_grid = std::min(ntile, w.ks.recip.per_sm * g->nsm);
+        w.nb_ax0 = std::max(w.nb_ax0, w.recip_grid);      // partials sized for either kernel
+    }
     return OFDFT_OK;
 }
 
@@ -277,22 +342,22 @@ template <typename T> int ensure_ws(ofdft_grid *g, int nslots) {
                 h[k].x = (T)std::cos(ang);
                 h[k].y = (T)std::sin(ang);
             }
-            CK(cudaMalloc(&w.tw[a], n * sizeof(C)), "cudaMalloc twiddles");
+            CK(gmalloc(g, &w.tw[a], n * sizeof(C)), "cudaMalloc twiddles");
             CK(cudaMemcpy(w.tw[a], h.data(), n * sizeof(C), cudaMemcpyHostToDevice), "upload twiddles");
         }
-        CK(cudaMalloc(&w.scal, 64 * sizeof(double)), "cudaMalloc scalars");
+        CK(gmalloc(g, &w.scal, 64 * sizeof(double)), "cudaMalloc scalars");
         CK(cudaMemset(w.scal, 0, 64 * sizeof(double)), "memset");
-        CK(cudaMalloc(&w.energies, 8 * sizeof(double)), "cudaMalloc energies");
-        CK(cudaMalloc(&w.knots_d, OFDFT_MAX_KNOTS * sizeof(double)), "cudaMalloc knots");
-        CK(cudaMalloc(&w.knots_t, OFDFT_MAX_KNOTS * sizeof(T)), "cudaMalloc knots");
-        CK(cudaMalloc(&w.invdk_t, OFDFT_MAX_KNOTS * sizeof(T)), "cudaMalloc knots");
+        CK(gmalloc(g, &w.energies, 8 * sizeof(double)), "cudaMalloc energies");
+        CK(gmalloc(g, &w.knots_d, OFDFT_MAX_KNOTS * sizeof(double)), "cudaMalloc knots");
+        CK(gmalloc(g, &w.knots_t, OFDFT_MAX_KNOTS * sizeof(T)), "cudaMalloc knots");
+        CK(gmalloc(g, &w.invdk_t, OFDFT_MAX_KNOTS * sizeof(T)), "cudaMalloc knots");
         const int nbs = 2 * g->nsm;
-        CK(cudaMalloc(&w.part_stats, 3 * nbs * sizeof(double)), "cudaMalloc partials");
-        CK(cudaMalloc(&w.part_minmax, 2 * nbs * sizeof(T)), "cudaMalloc partials");
-        CK(cudaMalloc(&w.part_ax0, 4 * (size_t)w.nb_ax0 * sizeof(double)), "cudaMalloc partials");
-        CK(cudaMalloc(&w.part_row, (size_t)w.nb_row * sizeof(double)), "cudaMalloc partials");
-        CK(cudaMalloc(&w.part_misc, 4096 * sizeof(double)), "cudaMalloc partials");
-        CK(cudaMalloc(&w.ticket, sizeof(unsigned)), "cudaMalloc ticket");
+        CK(gmalloc(g, &w.part_stats, 3 * nbs * sizeof(double)), "cudaMalloc partials");
+        CK(gmalloc(g, &w.part_minmax, 2 * nbs * sizeof(T)), "cudaMalloc partials");
+        CK(gmalloc(g, &w.part_ax0, 4 * (size_t)w.nb_ax0 * sizeof(double)), "cudaMalloc partials");
+        CK(gmalloc(g, &w.part_row, (size_t)w.nb_row * sizeof(double)), "cudaMalloc partials");
+        CK(gmalloc(g, &w.part_misc, 4096 * sizeof(double)), "cudaMalloc partials");
+        CK(gmalloc(g, &w.ticket, sizeof(unsigned)), "cudaMalloc ticket");
         CK(cudaMemset(w.ticket, 0, sizeof(unsigned)), "memset ticket");
         w.ready = true;
     }
@@ -300,7 +365,7 @@ template <typename T> int ensure_ws(ofdft_grid *g, int nslots) {
         if (w.chan) cudaFree(w.chan);
         w.chan = nullptr;
         w.nslots = 0;
-        CK(cudaMalloc(&w.chan, (size_t)nslots * g->NH * sizeof(C)), "cudaMalloc channel workspace");
+        CK(gmalloc(g, &w.chan, (size_t)nslots * g->NH * sizeof(C)), "cudaMalloc channel workspace");
         w.nslots = nslots;
         g->generation++;
     }
@@ -356,7 +421,7 @@ template <typename T> int ensure_vext(ofdft_grid *g) {
     bool &fresh = sizeof(T) == 4 ? g->vext_fresh32 : g->vext_fresh64;
     if (fresh) return OFDFT_OK;
     if (!w.vext) {
-        CK(cudaMalloc(&w.vext, g->NH * sizeof(C)), "cudaMalloc V_ext(G)");
+        CK(gmalloc(g, &w.vext, g->NH * sizeof(C)), "cudaMalloc V_ext(G)");
         g->generation++;
     }
     if (g->pme_order > 0) {
@@ -466,7 +531,7 @@ template <typename T> int ensure_mgp_table(ofdft_grid *g, const ofdft_functional
     if (!uses_mgp(f)) return OFDFT_OK;
     Workspace<T> &w = ws<T>(g);
     if (!w.mgp_tab) {
-        CK(cudaMalloc(&w.mgp_tab, (size_t)kMgpTable * sizeof(T)), "cudaMalloc MGP table");
+        CK(gmalloc(g, &w.mgp_tab, (size_t)kMgpTable * sizeof(T)), "cudaMalloc MGP table");
         w.mgp_y = 0.0;
     }
     if (w.mgp_y != f->mgp_y) {
@@ -535,7 +600,7 @@ int enqueue_eval(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, d
     a.energies = E_dev_out ? E_dev_out : w.energies;
     a.ticket = w.ticket;
     a.nb_stats = 2 * g->nsm;
-    a.nb_ax0 = w.nb_ax0;
+    a.nb_ax0 = w.ks.recip.k ? w.recip_grid : w.nb_ax0;
     a.nb_row = w.nb_row;
     a.p0 = g->plan[0];
     a.p1 = g->plan[1];
@@ -553,6 +618,7 @@ int enqueue_eval(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, d
     a.grid_p1 = w.grid_p1;
     a.row2_G = w.row2_G;
     a.ax0_scr = w.ax0_scr;
+    a.wait_polls = g->wait_polls;
     // channel lists
     const bool hpp = f->terms & (OFDFT_TERM_HARTREE | OFDFT_TERM_PP);
     const bool vw = f->terms & OFDFT_TERM_VW;
@@ -591,13 +657,36 @@ int enqueue_eval(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, d
             }
         }
     }
-    // clears the bad-density flag, the WT kF (recomputed) and the device-wait timeout flag
-    static_assert(S_TIMEOUT == S_BAD + 2, "flag slots");
-    CK(cudaMemsetAsync(w.scal + S_BAD, 0, 3 * sizeof(double), g->stream), "memset flags");
+    // clears the bad-density flag, the WT kF (recomputed) and the device-wait counters
+    static_assert(S_TIMEOUT == S_BAD + 2 && S_FATAL == S_BAD + 3, "flag slots");
+    CK(cudaMemsetAsync(w.scal + S_BAD, 0, 4 * sizeof(double), g->stream), "memset flags");
     if (a.frozen) CK(cudaMemcpyAsync(w.knots_d, f->knots, M * sizeof(double), cudaMemcpyHostToDevice, g->stream),
                      "upload knots");
+    if (w.ks.recip.k && (w.maps_chan != w.chan || w.maps_vext != w.vext || w.maps_nslots != w.nslots)) {
+        const long long PL = (long long)g->n[1] * g->n2h;
+        const int box_rows = g->n[0] > 256 ? 256 : g->n[0];
+        if (!encode_spectra_map<T>(&w.maps.chan, w.chan, PL, g->n[0], w.nslots, box_rows) ||
+            !encode_spectra_map<T>(&w.maps.vext, w.vext ? (const void *)w.vext : (const void *)w.chan, PL, g->n[0],
+                                   1, box_rows))
+            return fail(g, OFDFT_ERR_CUDA, "tensor map encoding");
+        w.maps_chan = w.chan;
+        w.maps_vext = w.vext;
+        w.maps_nslots = w.nslots;
+    }
     ProfHook hook{prof_record, g};
-    CK(launch_eval<T>(a, w.ks, g->stream, g->prof_on ? &hook : nullptr), "evaluation kernels");
+    CK(launch_eval<T>(a, w.ks, g->stream, g->prof_on ? &hook : nullptr, w.ks.recip.k ? &w.maps : nullptr),
+       "evaluation kernels");
+    return OFDFT_OK;
+}
+
+// status of the device-wait counters of an evaluation (host copies of the S_TIMEOUT and
+// S_FATAL slots): bounded waits for bulk copies that expired, and those whose copies did not
+// land within the second, longer bound either
+int wait_status(ofdft_grid *g, const double *scal) {
+    if (scal[S_FATAL] != 0.0)
+        return fail(g, OFDFT_ERR_TIMEOUT, "a bounded device wait expired and bulk copies may still have been in "
+                                          "flight: every result of this call is invalid");
+    if (scal[S_TIMEOUT] != 0.0) return fail(g, OFDFT_ERR_TIMEOUT, "a bounded device wait expired");
     return OFDFT_OK;
 }
 
@@ -610,7 +699,7 @@ int eval_sync(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, doub
     CK(cudaMemcpyAsync(g->h_pinned + 8, w.scal, S_NSCAL * sizeof(double), cudaMemcpyDeviceToHost, g->stream),
        "copy scalars");
     CK(cudaStreamSynchronize(g->stream), "stream synchronize");
-    if (g->h_pinned[8 + S_TIMEOUT] != 0.0) return fail(g, OFDFT_ERR_TIMEOUT, "a bounded device wait expired");
+    if ((rc = wait_status(g, g->h_pinned + 8))) return rc;
     if (g->h_pinned[8 + S_BAD] != 0.0) return fail(g, OFDFT_ERR_BAD_DENSITY, "density has NaN/Inf or negative values");
     if (E_out) std::memcpy(E_out, g->h_pinned, E_NUM * sizeof(double));
     return OFDFT_OK;
@@ -668,14 +757,14 @@ template <typename T> int inverse_plain(ofdft_grid *g, Workspace<T> &w, int slot
 
 template <typename T> int ensure_pme_buffers(ofdft_grid *g) {
     if (!g->Qfix) {
-        CK(cudaMalloc(&g->Qfix, (size_t)g->N * sizeof(unsigned long long)), "cudaMalloc PME grid");
+        CK(gmalloc(g, &g->Qfix, (size_t)g->N * sizeof(unsigned long long)), "cudaMalloc PME grid");
         g->generation++;
     }
     if (g->pme_real_bytes < (size_t)g->N * sizeof(T)) {
         cudaFree(g->pme_real);
         g->pme_real = nullptr;
         g->pme_real_bytes = 0;
-        CK(cudaMalloc(&g->pme_real, (size_t)g->N * sizeof(T)), "cudaMalloc PME field");
+        CK(gmalloc(g, &g->pme_real, (size_t)g->N * sizeof(T)), "cudaMalloc PME field");
         g->pme_real_bytes = (size_t)g->N * sizeof(T);
         g->generation++;
     }
@@ -748,7 +837,7 @@ template <typename T> int ensure_force_buffers(ofdft_grid *g) {
         cudaFree(g->fpart);
         g->fpart = nullptr;
         g->fpart_len = 0;
-        CK(cudaMalloc(&g->fpart, plen * sizeof(double)), "cudaMalloc force partials");
+        CK(gmalloc(g, &g->fpart, plen * sizeof(double)), "cudaMalloc force partials");
         g->fpart_len = plen;
         g->generation++;
     }
@@ -757,7 +846,7 @@ template <typename T> int ensure_force_buffers(ofdft_grid *g) {
         cudaFree(g->gc);
         g->gc = nullptr;
         g->gc_len = 0;
-        CK(cudaMalloc(&g->gc, 2 * (size_t)g->NH * sizeof(float4)), "cudaMalloc force scratch");
+        CK(gmalloc(g, &g->gc, 2 * (size_t)g->NH * sizeof(float4)), "cudaMalloc force scratch");
         g->gc_len = g->NH;
         g->generation++;
     }
@@ -766,7 +855,7 @@ template <typename T> int ensure_force_buffers(ofdft_grid *g) {
         cudaFreeHost(g->F_pinned);
         g->F_dev = g->F_pinned = nullptr;
         g->F_len = 0;
-        CK(cudaMalloc(&g->F_dev, (size_t)3 * g->n_ions * sizeof(double)), "cudaMalloc forces");
+        CK(gmalloc(g, &g->F_dev, (size_t)3 * g->n_ions * sizeof(double)), "cudaMalloc forces");
         CK(cudaMallocHost(&g->F_pinned, (size_t)3 * g->n_ions * sizeof(double)), "cudaMallocHost forces");
         g->F_len = g->n_ions;
         g->generation++;
@@ -876,16 +965,16 @@ int ewald_impl(ofdft_grid *g, double *E_out, double *F_out) {
         g->ew_cell = g->ew_orig = g->ew_cstart = nullptr;
         g->ew_F = g->ew_e = nullptr;
         g->ew_n = g->ew_ncell = 0;
-        CK(cudaMalloc(&g->ew_p, (size_t)n * sizeof(double4)), "cudaMalloc Ewald ions");
-        CK(cudaMalloc(&g->ew_cell, (size_t)n * sizeof(int)), "cudaMalloc Ewald ions");
-        CK(cudaMalloc(&g->ew_orig, (size_t)n * sizeof(int)), "cudaMalloc Ewald ions");
-        CK(cudaMalloc(&g->ew_F, (size_t)6 * n * sizeof(double)), "cudaMalloc Ewald forces");
-        CK(cudaMalloc(&g->ew_e, (size_t)n * sizeof(double)), "cudaMalloc Ewald energies");
-        CK(cudaMalloc(&g->ew_cstart, (size_t)(ncell + 1) * sizeof(int)), "cudaMalloc Ewald cells");
+        CK(gmalloc(g, &g->ew_p, (size_t)n * sizeof(double4)), "cudaMalloc Ewald ions");
+        CK(gmalloc(g, &g->ew_cell, (size_t)n * sizeof(int)), "cudaMalloc Ewald ions");
+        CK(gmalloc(g, &g->ew_orig, (size_t)n * sizeof(int)), "cudaMalloc Ewald ions");
+        CK(gmalloc(g, &g->ew_F, (size_t)6 * n * sizeof(double)), "cudaMalloc Ewald forces");
+        CK(gmalloc(g, &g->ew_e, (size_t)n * sizeof(double)), "cudaMalloc Ewald energies");
+        CK(gmalloc(g, &g->ew_cstart, (size_t)(ncell + 1) * sizeof(int)), "cudaMalloc Ewald cells");
         g->ew_n = n;
         g->ew_ncell = (int)ncell;
     }
-    if (!g->ew_part) CK(cudaMalloc(&g->ew_part, (kEwaldBlocks + 8) * sizeof(double)), "cudaMalloc Ewald partials");
+    if (!g->ew_part) CK(gmalloc(g, &g->ew_part, (kEwaldBlocks + 8) * sizeof(double)), "cudaMalloc Ewald partials");
     cudaStream_t st = g->stream;
     CK(cudaMemcpyAsync(g->ew_p, sp.data(), (size_t)n * sizeof(double4), cudaMemcpyHostToDevice, st), "upload");
     CK(cudaMemcpyAsync(g->ew_cell, scell.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice, st), "upload");
@@ -1016,7 +1105,7 @@ int multistep_impl(int nlev, ofdft_grid *const *grids, T *psi, const ofdft_funct
     lev[nlev - 1] = psi;
     int rc = OFDFT_OK;
     for (int L = 0; L < nlev - 1 && rc == OFDFT_OK; L++) {
-        cudaError_t e = cudaMalloc(&lev[L], (size_t)grids[L]->N * sizeof(T));
+        cudaError_t e = gmalloc(grids[L], &lev[L], (size_t)grids[L]->N * sizeof(T));
         if (e != cudaSuccess) rc = fail(fine, OFDFT_ERR_OOM, "cudaMalloc multi-step level", e);
     }
     // the initial psi goes straight to the coarsest grid; each converged psi goes one level up
@@ -1037,16 +1126,28 @@ int multistep_impl(int nlev, ofdft_grid *const *grids, T *psi, const ofdft_funct
 }
 
 // ---------------------------------------------------------------- optimiser
+// FP64 dot products of device fields read back to the host.  The first CUDA error is kept
+// in err (later products return NaN); the loops that use them check it every iteration.
 template <typename T> struct Dev {
     ofdft_grid *g;
     Workspace<T> *w;
+    cudaError_t err = cudaSuccess;
     double dot(const T *a, const T *b, const T *c = nullptr) {
-        launch_dot<T>(a, b, c, g->N, w->part_misc, 1024, w->part_misc + 2048, g->stream);
-        double r = 0.0;
-        cudaMemcpyAsync(g->h_pinned + 40, w->part_misc + 2048, sizeof(double), cudaMemcpyDeviceToHost, g->stream);
-        cudaStreamSynchronize(g->stream);
-        r = g->h_pinned[40];
-        return r;
+        if (err != cudaSuccess) return std::nan("");
+        cudaError_t e = launch_dot<T>(a, b, c, g->N, w->part_misc, 1024, w->part_misc + 2048, g->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(g->h_pinned + 40, w->part_misc + 2048, sizeof(double), cudaMemcpyDeviceToHost,
+                                g->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+        if (e != cudaSuccess) {
+            err = e;
+            return std::nan("");
+        }
+        return g->h_pinned[40];
+    }
+    // OFDFT_OK, or the status of the first failed product (message kept in the handle)
+    int status() const {
+        return err == cudaSuccess ? OFDFT_OK : fail(g, OFDFT_ERR_CUDA, "dot product", err);
     }
 };
 
@@ -1069,7 +1170,7 @@ int optimize_impl(ofdft_grid *g, T *psi, const ofdft_functional *f0, double Ne, 
     int rc = ensure_ws<T>(g, 3);
     if (rc) return rc;
     Workspace<T> &w = ws<T>(g);
-    if (!w.opt) CK(cudaMalloc(&w.opt, 8 * (size_t)N * sizeof(T)), "cudaMalloc optimiser fields");
+    if (!w.opt) CK(gmalloc(g, &w.opt, 8 * (size_t)N * sizeof(T)), "cudaMalloc optimiser fields");
     T *rho = w.opt, *V = rho + N, *grad = V + N, *gprev = grad + N, *d = gprev + N, *p = d + N, *psil = p + N;
     T *tmp = psil + N;
     const int method = o.method;
@@ -1081,7 +1182,7 @@ int optimize_impl(ofdft_grid *g, T *psi, const ofdft_functional *f0, double Ne, 
         cudaFree(w.opt_ext);
         w.opt_ext = nullptr;
         w.opt_ext_fields = 0;
-        CK(cudaMalloc(&w.opt_ext, (size_t)n_ext * (size_t)N * sizeof(T)), "cudaMalloc optimiser history");
+        CK(gmalloc(g, &w.opt_ext, (size_t)n_ext * (size_t)N * sizeof(T)), "cudaMalloc optimiser history");
         w.opt_ext_fields = n_ext;
     }
     T *ext = w.opt_ext;
@@ -1092,10 +1193,9 @@ int optimize_impl(ofdft_grid *g, T *psi, const ofdft_functional *f0, double Ne, 
     // grows with the grid's cut-off, so plain CG needs ever more iterations on finer grids),
     // a = (70/9) C_TF rho_m^(2/3) from the local terms, b/G^2 = 16 pi rho_m / G^2 from Hartree
     // (stiff long-wavelength charge moves; a kinetic-only preconditioner amplifies exactly
-    // those and stalls).  OFDFT_OPT_PRECOND=0 in the environment turns it off as well.
+    // those and stalls).
     typedef typename Vec2<T>::type C;
-    const char *env_pc = std::getenv("OFDFT_OPT_PRECOND");
-    const bool precond = o.precondition && !(env_pc && env_pc[0] == '0');
+    const bool precond = o.precondition != 0;
     const bool scale_upd = o.update == OFDFT_UPDATE_SCALE;
     const bool resid_obj = o.objective == OFDFT_OBJECTIVE_RESIDUAL;
     const double rho_m = Ne / g->omega;
@@ -1268,6 +1368,7 @@ int optimize_impl(ofdft_grid *g, T *psi, const ofdft_functional *f0, double Ne, 
     double last_dE = 0.0;
     const double c1 = 1e-4, c2 = 0.2;
     while (it < max_iter) {
+        if ((rc = dv.status())) return rc;
         it++;
         // g = 2 psi (V - mu) dV, mu = int rho V / N_e
         pp = dv.dot(psi, psi);
@@ -1449,7 +1550,8 @@ int optimize_impl(ofdft_grid *g, T *psi, const ofdft_functional *f0, double Ne, 
         rep->residual = std::sqrt(dv.dot(grad, grad) * g->dV);
         rep->last_dE = last_dE;
     }
-    return small >= 3 ? OFDFT_OK : OFDFT_ERR_NOT_CONVERGED;
+    if ((rc = dv.status())) return rc;
+    return small >= 3 ? OFDFT_OK : fail(g, OFDFT_ERR_NOT_CONVERGED, "the optimiser reached max_iter");
 }
 
 // ---------------------------------------------------------------- real-time TD-OFDFT
@@ -1468,7 +1570,7 @@ int td_impl(ofdft_grid *g, T *pre, T *pim, const T *rho0, const ofdft_functional
     int rc = ensure_ws<T>(g, 3);
     if (rc) return rc;
     Workspace<T> &w = ws<T>(g);
-    if (!w.td) CK(cudaMalloc(&w.td, (size_t)kTdFields * (size_t)N * sizeof(T)), "cudaMalloc TD fields");
+    if (!w.td) CK(gmalloc(g, &w.td, (size_t)kTdFields * (size_t)N * sizeof(T)), "cudaMalloc TD fields");
     T *F[kTdFields];
     for (int k = 0; k < kTdFields; k++) F[k] = w.td + (size_t)k * (size_t)N;
     T *p0[2] = {F[0], F[1]};           // psi(t)
@@ -1624,6 +1726,7 @@ int td_impl(ofdft_grid *g, T *pre, T *pim, const T *rho0, const ofdft_functional
     if ((rc = dipole(dip))) return rc;
     int step = 0;
     for (; step < o.n_steps; step++) {
+        if ((rc = dv.status())) return rc;
         for (int j = 0; j < 2; j++) CK(launch_copy<T>(p0[j], x[j], N, s), "copy");
         if ((rc = cn_solve(vt, true))) return rc;           // predictor (from psi(t))
         if ((rc = veff(vn))) return rc;
@@ -1637,6 +1740,7 @@ int td_impl(ofdft_grid *g, T *pre, T *pim, const T *rho0, const ofdft_functional
         if ((rc = dipole(dip ? dip + 3 * (size_t)(step + 1) : nullptr))) return rc;
     }
     CK(cudaStreamSynchronize(s), "stream synchronize");
+    if ((rc = dv.status())) return rc;
     if (rep) {
         rep->steps = step;
         rep->evaluations = evals;
@@ -1736,8 +1840,7 @@ int batched_impl(int n, ofdft_grid *const *grids, const void *const *rho_dev, co
         int rc = prepare_batch_grid<T>(grids[i], f, F_out && F_out[i]);
         if (rc) return rc;
     }
-    const char *env = std::getenv("OFDFT_BATCH_GRAPH");
-    bool use_graph = !(env && env[0] == '0') && !f->knots;
+    bool use_graph = g0->batch_graph && !f->knots;
     for (int i = 0; i < n; i++) use_graph = use_graph && !grids[i]->prof_on;
     cudaError_t e;
     if (use_graph) {
@@ -1787,7 +1890,7 @@ int batched_impl(int n, ofdft_grid *const *grids, const void *const *rho_dev, co
     if (e != cudaSuccess) return fail(g0, OFDFT_ERR_CUDA, "stream synchronize", e);
     for (int i = 0; i < n; i++) {
         ofdft_grid *g = grids[i];
-        if (g->h_pinned[8 + S_TIMEOUT] != 0.0) return fail(g, OFDFT_ERR_TIMEOUT, "a bounded device wait expired");
+        if (int rc = wait_status(g, g->h_pinned + 8)) return rc;
         if (g->h_pinned[8 + S_BAD] != 0.0) return fail(g, OFDFT_ERR_BAD_DENSITY, "bad density in batch");
         std::memcpy(E_out + E_NUM * i, g->h_pinned, E_NUM * sizeof(double));
         if (F_out && F_out[i]) std::memcpy(F_out[i], g->F_pinned, (size_t)3 * g->n_ions * sizeof(double));
@@ -1885,6 +1988,40 @@ int ofdft_profile_read(ofdft_grid *g, int idx, const char **name, int *launches,
     return OFDFT_OK;
 }
 
+int ofdft_set_option(ofdft_grid *g, int option, long long value) {
+    if (!g) return OFDFT_ERR_INVALID_ARG;
+    switch (option) {
+        case OFDFT_OPTION_KERNELS:
+            if (value != OFDFT_KERNELS_AUTO && value != OFDFT_KERNELS_GENERIC &&
+                value != OFDFT_KERNELS_PER_CHANNEL_ROWS && value != OFDFT_KERNELS_TILE_RECIP)
+                return fail(g, OFDFT_ERR_INVALID_ARG, "unknown kernel choice");
+            if (value != g->kernel_choice) {
+                // the launch plan is made with the workspaces: drop them (rebuilt on next use)
+                cudaStreamSynchronize(g->stream);
+                free_ws(g->w32);
+                free_ws(g->w64);
+                g->vext_fresh32 = g->vext_fresh64 = false;
+                g->generation++;
+                g->kernel_choice = (int)value;
+            }
+            return OFDFT_OK;
+        case OFDFT_OPTION_BATCH_GRAPH:
+            g->batch_graph = value != 0;
+            return OFDFT_OK;
+        case OFDFT_OPTION_WAIT_POLLS:
+            if (value < 0 || value > (1LL << 30)) return fail(g, OFDFT_ERR_INVALID_ARG, "wait polls out of range");
+            g->wait_polls = (unsigned)value;
+            return OFDFT_OK;
+        case OFDFT_OPTION_ALLOC_CAP:
+            if (value < 0) return fail(g, OFDFT_ERR_INVALID_ARG, "negative allocation cap");
+            g->alloc_cap = (size_t)value;
+            g->alloc_bytes = 0;
+            return OFDFT_OK;
+        default:
+            return fail(g, OFDFT_ERR_INVALID_ARG, "unknown option");
+    }
+}
+
 int ofdft_grid_destroy(ofdft_grid *g) {
     if (!g) return OFDFT_ERR_INVALID_ARG;
     cudaStreamSynchronize(g->stream);
@@ -1942,9 +2079,9 @@ int store_ions(ofdft_grid *g, const ofdft_ions *ions, const ofdft_species *sp) {
         g->d_pos = nullptr;
         g->d_species = nullptr;
         g->d_Z = g->d_rc = nullptr;
-        CK(cudaMalloc(&g->d_species, n * sizeof(int)), "cudaMalloc species");
-        CK(cudaMalloc(&g->d_Z, sp->n_species * sizeof(double)), "cudaMalloc Z");
-        CK(cudaMalloc(&g->d_rc, sp->n_species * sizeof(double)), "cudaMalloc rc");
+        CK(gmalloc(g, &g->d_species, n * sizeof(int)), "cudaMalloc species");
+        CK(gmalloc(g, &g->d_Z, sp->n_species * sizeof(double)), "cudaMalloc Z");
+        CK(gmalloc(g, &g->d_rc, sp->n_species * sizeof(double)), "cudaMalloc rc");
     }
     g->n_ions = n;
     g->n_species = sp->n_species;
@@ -1973,8 +2110,8 @@ int ofdft_set_ions(ofdft_grid *g, const ofdft_ions *ions, const ofdft_species *s
     g->pme_order = 0;
     const int n = g->n_ions;
     if (!g->ph) {
-        CK(cudaMalloc(&g->ph, (size_t)n * (g->n[0] + g->n[1] + g->n2h) * sizeof(double2)), "cudaMalloc phases");
-        CK(cudaMalloc(&g->ph32, (size_t)n * (g->n[0] + g->n[1] + g->n2h) * sizeof(float2)), "cudaMalloc phases");
+        CK(gmalloc(g, &g->ph, (size_t)n * (g->n[0] + g->n[1] + g->n2h) * sizeof(double2)), "cudaMalloc phases");
+        CK(gmalloc(g, &g->ph32, (size_t)n * (g->n[0] + g->n[1] + g->n2h) * sizeof(float2)), "cudaMalloc phases");
     }
     // per-axis phase tables e^{-2 pi i m_a f_a}, f = R . inv(cell) (fractional)
     const int na[3] = {g->n[0], g->n[1], g->n2h};
@@ -2009,7 +2146,7 @@ int ofdft_set_ions_pme(ofdft_grid *g, const ofdft_ions *ions, const ofdft_specie
     int rc = store_ions(g, ions, sp);
     if (rc) return rc;
     g->pme_order = order;
-    if (!g->d_pos) CK(cudaMalloc(&g->d_pos, (size_t)3 * g->n_ions * sizeof(double)), "cudaMalloc positions");
+    if (!g->d_pos) CK(gmalloc(g, &g->d_pos, (size_t)3 * g->n_ions * sizeof(double)), "cudaMalloc positions");
     CK(cudaMemcpy(g->d_pos, g->pos.data(), (size_t)3 * g->n_ions * sizeof(double), cudaMemcpyHostToDevice),
        "upload positions");
     // conj b_a(k) = conj( e^{2 pi i (p-1) k/n} / sum_{j=0}^{p-2} M_p(j+1) e^{2 pi i k j/n} )
@@ -2045,7 +2182,7 @@ int ofdft_set_ions_pme(ofdft_grid *g, const ofdft_ions *ions, const ofdft_specie
         }
         off += na[ax];
     }
-    if (!g->pmeB) CK(cudaMalloc(&g->pmeB, B.size() * sizeof(double2)), "cudaMalloc PME factors");
+    if (!g->pmeB) CK(gmalloc(g, &g->pmeB, B.size() * sizeof(double2)), "cudaMalloc PME factors");
     CK(cudaMemcpy(g->pmeB, B.data(), B.size() * sizeof(double2), cudaMemcpyHostToDevice), "upload PME factors");
     return OFDFT_OK;
 }

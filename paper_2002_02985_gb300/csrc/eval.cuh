@@ -28,7 +28,9 @@ enum { CONS_ADD = 0, CONS_VW = 1, CONS_T2 = 2, CONS_KNOT = 3, CONS_WT_A = 4, CON
 // scalar slots (double) in the workspace
 enum {
     S_SUM_RHO = 0, S_SUM_TF = 1, S_RHO_MIN = 2, S_RHO_MAX = 3, S_RHO_MEAN = 4, S_BAD = 5,
-    S_KF_WT = 6, S_TIMEOUT = 7, S_NSCAL = 8,
+    S_KF_WT = 6, S_TIMEOUT = 7,   // S_TIMEOUT: bounded waits that expired (the copies then landed)
+    S_FATAL = 8,                  // waits whose copies did not land within the second bound either
+    S_NSCAL = 9,
     S_FIN = 16                 // [16, 21): the finalize blocks' five sums
 };
 // energy slots: total, TF, vW, NL, H, PP, XC
@@ -75,6 +77,7 @@ template <typename T> struct EvalArgs {
     int grid_p1;                         // persistent grid of the n1 pencil kernels
     int row2_G;                          // channel-batched row kernels: channels per group (0: per-channel form)
     int ax0_scr;                         // the reciprocal-space kernel has a scratch tile (out-of-place transforms)
+    unsigned wait_polls;                 // polls of a bounded wait for bulk copies before it gives up
     int nfwd, fwd_ch[kMaxChan];          // channels formed by row_fwd (slot ids)
     int ncol, col_ch[kMaxChan];          // channels transformed forward along n1
     int ncol_inv, col_inv_ch[kMaxChan];  // channels transformed back along n1
@@ -143,13 +146,28 @@ template <typename T> __host__ __device__ inline size_t rowi_smem(const EvalArgs
     return a.row2_G ? row2_smem_bytes<T>(a.n2, a.row2_G) : row_inv_smem_bytes<T>(a.n2, a.Brow);
 }
 
+// The persistent reciprocal-space kernel (register-resident n0 transforms, tensor-map tile
+// loads; recip.cuh) compiled for an n0: Wang-Teter and Eq. MGP forms, block size, dynamic
+// shared memory, blocks per SM.
+struct RecipLaunch {
+    const void *k = nullptr, *k_mgp = nullptr;
+    int nt = 0, per_sm = 1;
+    size_t smem = 0;
+};
+
 // The five FFT-carrying kernels of one evaluation (generic or size-specialised).
 struct LaunchSet {
     const void *row_fwd = nullptr, *row_inv = nullptr;   // depend on n2
     const void *pen_fwd = nullptr, *pen_inv = nullptr;   // depend on n1
     const void *axis0 = nullptr;                         // depends on n0
     const void *axis0_mgp = nullptr;                     // the same with Eq. MGP kernels
+    RecipLaunch recip;                                   // replaces axis0 when its k is set
 };
+
+// tensor maps of the persistent reciprocal-space kernel (defined in recip.cuh)
+struct RecipMaps;
+// the persistent reciprocal-space kernel compiled for n0 = n in precision T, if any
+template <typename T> bool find_recip(int n, RecipLaunch *out);
 
 // role of a kernel family for the size registry
 enum { ROLE_ROW = 0, ROLE_PENCIL = 1, ROLE_AXIS0 = 2, ROLE_ROW2 = 3 };
@@ -162,8 +180,10 @@ template <typename T> LaunchSet generic_kernels();
 // Let every kernel of the set use the device's full opt-in shared memory.
 cudaError_t prepare_kernels(const LaunchSet &ks);
 
+// maps: the tensor maps of the persistent reciprocal-space kernel (needed when ks.recip.k is set;
+// a.nb_ax0 is then its grid)
 template <typename T> cudaError_t launch_eval(const EvalArgs<T> &a, const LaunchSet &ks, cudaStream_t s,
-                                              const ProfHook *prof = nullptr);
+                                              const ProfHook *prof = nullptr, const RecipMaps *maps = nullptr);
 // inverse pencil along n1 + C2R rows of the channels in a.col_inv_ch / a.inv_ch (CONS_ADD), V = result
 template <typename T> cudaError_t launch_inverse_cols_rows(const EvalArgs<T> &a, const LaunchSet &ks, cudaStream_t s);
 // stats + knots + row_fwd + forward pencil along n1 only (the channels of a.fwd_ch / a.col_ch)

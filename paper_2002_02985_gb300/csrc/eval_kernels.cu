@@ -26,8 +26,9 @@ template <typename T> LaunchSet generic_kernels() {
 }
 
 cudaError_t prepare_kernels(const LaunchSet &ks) {
-    const void *k[6] = {ks.row_fwd, ks.row_inv, ks.pen_fwd, ks.pen_inv, ks.axis0, ks.axis0_mgp};
-    for (int i = 0; i < 6; i++) {
+    const void *k[8] = {ks.row_fwd, ks.row_inv, ks.pen_fwd, ks.pen_inv, ks.axis0, ks.axis0_mgp, ks.recip.k,
+                        ks.recip.k_mgp};
+    for (int i = 0; i < 8; i++) {
         if (!k[i]) continue;
         cudaError_t e = allow_max_dynamic_smem(k[i]);
         if (e != cudaSuccess) return e;
@@ -48,7 +49,8 @@ static cudaError_t launch(const void *k, dim3 g, int nt, size_t smem, const Eval
 }
 
 template <typename T>
-cudaError_t launch_eval(const EvalArgs<T> &a, const LaunchSet &ks, cudaStream_t s, const ProfHook *ph) {
+cudaError_t launch_eval(const EvalArgs<T> &a, const LaunchSet &ks, cudaStream_t s, const ProfHook *ph,
+                        const RecipMaps *maps) {
     const long long R = (long long)a.n0 * a.n1;
     const long long pairs = (R + 1) / 2;
     const int nrt = (int)((pairs + a.Brow - 1) / a.Brow);
@@ -72,8 +74,14 @@ cudaError_t launch_eval(const EvalArgs<T> &a, const LaunchSet &ks, cudaStream_t 
         mark(K_PENCIL_FWD, 1);
     }
     mark(K_AXIS0, 0);
-    e = launch(a.mgp_tab ? ks.axis0_mgp : ks.axis0, dim3(a.nb_ax0), a.thr_ax0,
-               axis0_smem_bytes<T>(a.n0, a.TW0, a.ax0_scr), a, s);
+    if (ks.recip.k && maps) {
+        void *args[] = {(void *)&a, (void *)maps};
+        e = cudaLaunchKernel(a.mgp_tab ? ks.recip.k_mgp : ks.recip.k, dim3(a.nb_ax0), dim3(ks.recip.nt), args,
+                             ks.recip.smem, s);
+    } else {
+        e = launch(a.mgp_tab ? ks.axis0_mgp : ks.axis0, dim3(a.nb_ax0), a.thr_ax0,
+                   axis0_smem_bytes<T>(a.n0, a.TW0, a.ax0_scr), a, s);
+    }
     if (e) return e;
     mark(K_AXIS0, 1);
     if (a.ncol_inv > 0) {
@@ -182,7 +190,8 @@ template <typename T> cudaError_t launch_mgp_table(T *tab, int n, double y, cons
     template cudaError_t launch_mgp_table<T>(T *, int, double, const double *, cudaStream_t);               \
     template bool find_specialised<T>(int, int, const void **, const void **, int *, int *);                 \
     template LaunchSet generic_kernels<T>();                                                                 \
-    template cudaError_t launch_eval<T>(const EvalArgs<T> &, const LaunchSet &, cudaStream_t, const ProfHook *); \
+    template cudaError_t launch_eval<T>(const EvalArgs<T> &, const LaunchSet &, cudaStream_t, const ProfHook *,   \
+                                        const RecipMaps *);                                                  \
     template cudaError_t launch_forward_rows_cols<T>(const EvalArgs<T> &, const LaunchSet &, cudaStream_t); \
     template cudaError_t launch_inverse_cols_rows<T>(const EvalArgs<T> &, const LaunchSet &, cudaStream_t);
 INST(float)

@@ -172,6 +172,17 @@ template <typename T> __device__ __forceinline__ int knot_interval(T kc, const T
     return lo;
 }
 
+// Whether kF(x) lies in the knot range [k_1, k_M] (the exact potential's slope term is
+// applied only there).  With knots made from the density (s1) the end knots are kF of the
+// floored min and max density, and kF is monotone, so the test is taken on the density
+// itself: points at the minimum or maximum density (every point of a floored vacuum) are
+// then inside in any precision, as they are in exact arithmetic.  Caller-given knots are
+// compared in kF.
+template <typename T>
+__device__ __forceinline__ bool in_knot_range(const EvalArgs<T> &a, T xf, T kf, T klo, T khi, T rlo, T rhi) {
+    return a.frozen ? (kf >= klo && kf <= khi) : (xf >= rlo && xf <= rhi);
+}
+
 // ======================================================================= knots (s1)
 // FP64 reduction of the stats partials (read through L2: they were written by
 // other blocks of the same launch), the mean density, E_TF, and the M knots
@@ -778,6 +789,8 @@ __device__ __forceinline__ void row_inv_body(const EvalArgs<T> &a) {
     }
     __syncthreads();
     const T psi_floor = dsqrt(a.floor_);
+    const T rlo = (T)a.scal[S_RHO_MIN] > a.floor_ ? (T)a.scal[S_RHO_MIN] : a.floor_;
+    const T rhi = (T)a.scal[S_RHO_MAX] > a.floor_ ? (T)a.scal[S_RHO_MAX] : a.floor_;
     for (int o = threadIdx.x; o < PP; o += NT) {
         const int rr = o % (2 * B), i2 = o / (2 * B);
         const T x = stg[rr * pitch + i2];
@@ -803,7 +816,7 @@ __device__ __forceinline__ void row_inv_body(const EvalArgs<T> &a) {
             sb1[o] = rb / xf;
             if (lwt) {
                 const T kf = dcbrt((T)kThreePi2 * xf);
-                const bool inside = kf >= sk[0] && kf <= sk[M - 1];
+                const bool inside = in_knot_range(a, xf, kf, sk[0], sk[M - 1], rlo, rhi);
                 const T kc = kf < sk[0] ? sk[0] : (kf > sk[M - 1] ? sk[M - 1] : kf);
                 const int j = knot_interval(kc, sk, M);
                 sj[o] = (unsigned char)j;
@@ -1101,6 +1114,8 @@ __device__ __forceinline__ void row_inv2_body(const EvalArgs<T> &a) {
     unsigned phase = 0;
     const T psi_floor = dsqrt(a.floor_);
     const T alpha_eff = interp ? (T)2 * a.alpha : a.alpha;
+    const T rlo = (T)a.scal[S_RHO_MIN] > a.floor_ ? (T)a.scal[S_RHO_MIN] : a.floor_;
+    const T rhi = (T)a.scal[S_RHO_MAX] > a.floor_ ? (T)a.scal[S_RHO_MAX] : a.floor_;
     // per point: V accumulator (starts at V_TF), factors of the semilocal channels,
     // and the knot interval with the weights of its two knots in V (wa, wb) and,
     // interpolated mode, in the real-space E_NL (ea, eb)
@@ -1137,7 +1152,7 @@ __device__ __forceinline__ void row_inv2_body(const EvalArgs<T> &a) {
                     fb1[q][s] = a.beta * (rb / xf);
                     if (lwt) {
                         const T kf = dcbrt((T)kThreePi2 * xf);
-                        const bool inside = kf >= sk[0] && kf <= sk[M - 1];
+                        const bool inside = in_knot_range(a, xf, kf, sk[0], sk[M - 1], rlo, rhi);
                         const T kc = kf < sk[0] ? sk[0] : (kf > sk[M - 1] ? sk[M - 1] : kf);
                         const int j = knot_interval(kc, sk, M);
                         const T t = (kc - sk[j]) * sdk[j], idk = sdk[j];
@@ -1174,15 +1189,17 @@ __device__ __forceinline__ void row_inv2_body(const EvalArgs<T> &a) {
                 mbar_arrive_expect_tx(&mbar, bytes * (unsigned)gact);
                 for (int s = 0; s < gact; s++)
                     bulk_g2s(scr + 2 * s * n2h, a.chan + (size_t)sch[g0 + s] * a.NH + row0 * n2h, bytes, &mbar);
-                s_ok = mbar_wait_bounded(&mbar, phase, 1u << 22) ? 1 : 0;
+                s_ok = mbar_wait_bounded(&mbar, phase, a.wait_polls) ? 1 : 0;
             }
             __syncthreads();
             if (!s_ok) {
-                // the copies did not arrive in time: flag it, give them one more bounded
-                // wait (they target this block's shared memory) and stop working
+                // the copies did not arrive in time: flag it and stop working, but first let
+                // them land (they target this block's shared memory, which the next block on
+                // this SM may own) with a longer bounded wait; if even that expires the flag
+                // says so (2: copies may still be in flight, the whole call is invalid)
                 if (threadIdx.x == 0) {
-                    a.scal[S_TIMEOUT] = 1.0;
-                    mbar_wait_bounded(&mbar, phase, 1u << 22);
+                    const bool drained = mbar_wait_bounded(&mbar, phase, 1u << 26);
+                    atomicAdd(a.scal + (drained ? S_TIMEOUT : S_FATAL), 1.0);
                 }
                 alive = false;
                 break;

@@ -390,14 +390,26 @@ cudaError_t launch_axis0_fft(typename Vec2<T>::type *data, int n0, long long P, 
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    // a plain transform has one channel: wide column tiles (coalesced rows of up to 32 complex)
-    // and 256 threads, independent of the reciprocal-space kernel's tile
+    // a plain transform has one channel: wide column tiles (coalesced rows of up to 32 complex),
+    // independent of the reciprocal-space kernel's tile.  Each thread stages at most CAP values
+    // per pass, so a pass of radix R over TW columns needs (n0/R) TW / (CAP/R) threads: the tile
+    // is narrowed until every pass fits in 512 threads and 96 KB
     (void)TW;
     (void)thr;
+    auto need = [&](int cols) {
+        long long nt = 32;
+        for (int i = 0; i < p.npass; i++) {
+            const int R = p.radix[i], mb = CAP / R;
+            const long long t = ((long long)(n0 / R) * cols + mb - 1) / mb;
+            nt = t > nt ? t : nt;
+        }
+        return (int)((nt + 31) / 32 * 32);
+    };
     int tw_cols = 32;
-    while (tw_cols > 1 && (size_t)n0 * sizeof(C) * (1 + tw_cols) > 96 * 1024) tw_cols /= 2;
+    while (tw_cols > 1 && ((size_t)n0 * sizeof(C) * (1 + tw_cols) > 96 * 1024 || need(tw_cols) > 512)) tw_cols /= 2;
     TW = tw_cols;
-    thr = 256;
+    thr = need(TW) > 256 ? need(TW) : 256;
+    if (thr > 512) return cudaErrorInvalidConfiguration;
     const size_t sm = (size_t)n0 * sizeof(C) * (1 + TW);
     const unsigned nb = (unsigned)((P + TW - 1) / TW);
     if (dir < 0) axis0_fft_kernel<T, CAP, -1><<<nb, thr, sm, s>>>(data, n0, P, p, tw, TW, (T)scale);

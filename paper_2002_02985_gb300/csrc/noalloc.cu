@@ -3,18 +3,27 @@
 // The regular entry points keep their reduction partials in a workspace that
 // the library allocates with cudaMalloc on first use.  Some callers cannot let
 // a library allocate: a host program whose own allocator owns all device
-// memory, or code that runs while a CUDA stream is being captured into a graph
-// (cudaMalloc is not allowed inside a capture and would otherwise synchronise
-// the device).  For them this variant of the density reduction keeps its
-// partials in a fixed file-scope device array.
+// memory (a pool it sized up front, or memory shared with another runtime),
+// where an allocation behind its back can fail or fragment that pool, or code
+// that must not pay for cudaMalloc's device-wide synchronisation.  For them this
+// variant of the density reduction keeps its partials in a fixed file-scope
+// device array.
 //
 // The array is a static __device__ symbol: every GPU that loads the library
 // holds it until the process exits.  Host code must not pass the symbol itself
 // to a kernel (on the host it is only a stand-in, not a device address): its
 // device address is looked up once per device with cudaGetSymbolAddress and
-// that pointer is passed instead.  All calls share the array and it keeps the
-// last call's contents, so two calls that overlap on the GPU (different
+// that pointer is passed instead.  The first call on a device does that
+// look-up; make that first call before any stream capture.  All calls share
+// the array and it keeps the last call's contents (the completion ticket is
+// cleared on every call), so two calls that overlap on the GPU (different
 // streams, no ordering between them) race on it.
+//
+// A density with NaN, Inf or negative values gives E = NaN: the regular entry
+// point returns OFDFT_ERR_BAD_DENSITY instead, which this one cannot do without
+// synchronising its stream.
+#include <atomic>
+
 #include "../../include/ofdft.h"
 #include "common.cuh"
 
@@ -29,8 +38,10 @@ constexpr int kMaxBlocks = OFDFT_NOALLOC_MAX_POINTS / kPerBlock; // 4096
 // completion ticket (an unsigned int in the first 4 bytes of that double).
 static __device__ __align__(256) double noalloc_scratch[kMaxBlocks + 2];
 
+// per-device address of the array (host threads may race on a first call: each one
+// stores the same value, atomically)
 constexpr int kMaxDevices = 64;
-double *g_scratch_ptr[kMaxDevices] = {nullptr};
+std::atomic<double *> g_scratch_ptr[kMaxDevices];
 
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
@@ -39,16 +50,20 @@ tf_noalloc_kernel(const T *rho, long long n, double c_dV, T *V, double *E, doubl
     __shared__ int last;
     const long long base = (long long)blockIdx.x * kPerBlock;
     double acc = 0.0;
+    int bad = 0;
 #pragma unroll
     for (int k = 0; k < kPerThread; k++) {
         const long long i = base + (long long)k * kBlock + threadIdx.x;
         if (i < n) {
             const T x = rho[i];
+            if (!(x >= (T)0) || x - x != (T)0) bad = 1;                // NaN, negative or Inf
             const T c = ofdft::dcbrt(x > (T)0 ? x : (T)0);
             acc += (double)(x * c * c);                               // rho^(5/3)
             if (V) V[i] = (T)(5.0 / 3.0 * ofdft::kCTF) * c * c;       // (5/3) C_TF rho^(2/3)
         }
     }
+    // a bad value anywhere in the block makes its partial, hence E, NaN
+    if (__syncthreads_or(bad)) acc = __longlong_as_double(0x7ff8000000000000LL);
     acc = ofdft::block_sum(acc, sd);
     unsigned int *ticket = (unsigned int *)(scratch + kMaxBlocks);
     if (threadIdx.x == 0) {
@@ -77,13 +92,14 @@ extern "C" int ofdft_tf_energy_potential_noalloc(const void *rho_dev, long long 
     if (precision != OFDFT_FP64 && precision != OFDFT_FP32_MIXED) return OFDFT_ERR_INVALID_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return OFDFT_ERR_CUDA;
-    if (!g_scratch_ptr[dev]) {
+    double *scratch = g_scratch_ptr[dev].load(std::memory_order_acquire);
+    if (!scratch) {
         // once per device, with that device current: the device address of the array
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, noalloc_scratch) != cudaSuccess || !p) return OFDFT_ERR_CUDA;
-        g_scratch_ptr[dev] = (double *)p;
+        scratch = (double *)p;
+        g_scratch_ptr[dev].store(scratch, std::memory_order_release);
     }
-    double *scratch = g_scratch_ptr[dev];
     cudaStream_t s = (cudaStream_t)cuda_stream;
     // the completion ticket must start at zero
     if (cudaMemsetAsync(scratch + kMaxBlocks, 0, sizeof(double), s) != cudaSuccess) return OFDFT_ERR_CUDA;

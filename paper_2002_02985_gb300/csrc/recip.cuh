@@ -1,0 +1,432 @@
+// Reciprocal-space kernel with register-resident transforms along n0 and
+// tensor-map (TMA) tile loads: the persistent form of the axis-0 pass of one
+// evaluation (Sec. 2.3 s2 and the reciprocal half of s3, with the Hartree, local
+// pseudopotential and von Weizsaecker products of Eq. efunc).
+//
+// Work unit: a tile of 32 consecutive columns c = (k1, k2) of the half spectrum
+// and all N values of k0.  One block per SM loops over the tiles t = blockIdx.x,
+// blockIdx.x + gridDim.x, ...; a single thread keeps NSTAGE channel tiles in
+// flight with cp.async.bulk.tensor copies (3-D tensor map over [channel][k0][c],
+// one mbarrier per stage, bounded waits), across tile boundaries.
+//
+// Thread (w, t) = (lane, warp) owns column w of the tile and, through every pass
+// of the Stockham transform, the E = N / TC elements t + q TC + r N/R of that
+// column (TC = number of warps).  Each pass runs in registers; between passes
+// the values go through a shared exchange tile (one barrier per exchange, two
+// exchange tiles used alternately).  The forward transform ends with frequency
+// k0 = t + q TC + r N/R_last in register q R_last + r, which is exactly the input
+// order of the inverse transform with the radices reversed, so the reciprocal
+// products are applied in registers and the inverse starts without an exchange.
+// A warp always touches one row of 32 consecutive columns: every shared-memory
+// access is a conflict-free 256-byte row, and every global store a coalesced
+// 256-byte segment.  rho^beta hat, the term-2 accumulator and |G| stay in
+// registers for the whole tile.
+#pragma once
+
+#include <cuda.h>
+
+#include "kernels.cuh"
+
+namespace ofdft {
+namespace rs {
+
+// radices: greedily the largest of 16, 8, 4, 2, 5, 3 dividing both what is left of
+// N and E (the per-thread element count), so that every pass gives each thread
+// whole butterflies
+constexpr int pick(int m, int E) {
+    return (m % 16 == 0 && E % 16 == 0) ? 16
+         : (m % 8 == 0 && E % 8 == 0)   ? 8
+         : (m % 4 == 0 && E % 4 == 0)   ? 4
+         : (m % 2 == 0 && E % 2 == 0)   ? 2
+         : (m % 5 == 0 && E % 5 == 0)   ? 5
+         : (m % 3 == 0 && E % 3 == 0)   ? 3
+                                        : 0;
+}
+constexpr int npass(int N, int E) {
+    int m = N, c = 0;
+    while (m > 1) {
+        const int r = pick(m, E);
+        if (!r) return -1;
+        m /= r;
+        c++;
+    }
+    return c;
+}
+// radix of forward pass p
+constexpr int radix(int N, int E, int p) {
+    int m = N;
+    for (int q = 0; q < p; q++) m /= pick(m, E);
+    return pick(m, E);
+}
+// inverse pass p uses the forward radices in reverse order
+constexpr int iradix(int N, int E, int p) { return radix(N, E, npass(N, E) - 1 - p); }
+constexpr int fns(int N, int E, int p) {
+    int s = 1;
+    for (int q = 0; q < p; q++) s *= radix(N, E, q);
+    return s;
+}
+constexpr int ins(int N, int E, int p) {
+    int s = 1;
+    for (int q = 0; q < p; q++) s *= iradix(N, E, q);
+    return s;
+}
+
+// twiddles and butterflies of one pass on the thread's registers: butterfly q (of E/R) is
+// j = t + q TC, its inputs in v[q R .. q R + R - 1]
+template <int DIR, int N, int E, int TC, int R, int NS, typename C>
+__device__ __forceinline__ void pass(C (&v)[E], int t, const C *tw) {
+#pragma unroll
+    for (int q = 0; q < E / R; q++) {
+        if constexpr (NS > 1) {
+            const int k = (t + q * TC) % NS;
+#pragma unroll
+            for (int r = 1; r < R; r++) {
+                C w = tw[r * k * (N / (NS * R))];
+                if (DIR > 0) w.y = -w.y;
+                v[q * R + r] = cmul(v[q * R + r], w);
+            }
+        }
+        dft<DIR, R>(&v[q * R]);
+    }
+}
+
+// the outputs of a pass (radix R, NS) into the exchange tile X[e][32]
+template <int N, int E, int TC, int R, int NS, typename C>
+__device__ __forceinline__ void put(const C (&v)[E], int t, int w, C *X) {
+#pragma unroll
+    for (int q = 0; q < E / R; q++) {
+        const int j = t + q * TC, k = j % NS, base = (j / NS) * NS * R + k;
+#pragma unroll
+        for (int r = 0; r < R; r++) X[(base + r * NS) * 32 + w] = v[q * R + r];
+    }
+}
+
+// the inputs of a pass of radix R from a tile X[e][32]: element j + r N/R of butterfly j
+template <int N, int E, int TC, int R, typename C>
+__device__ __forceinline__ void get(C (&v)[E], int t, int w, const C *X) {
+#pragma unroll
+    for (int q = 0; q < E / R; q++)
+#pragma unroll
+        for (int r = 0; r < R; r++) v[q * R + r] = X[(t + q * TC + r * (N / R)) * 32 + w];
+}
+
+// passes p .. P-1 of a transform on the registers, with an exchange (put, block barrier,
+// get) between consecutive passes; the exchange tiles alternate.  bar() returns true when
+// a bounded wait failed, which ends the transform early (true is returned).
+template <int DIR, int N, int E, int TC, int p, typename C, typename Bar>
+__device__ __forceinline__ bool passes(C (&v)[E], int t, int w, const C *tw, C *Xa, C *Xb, bool &xsel, Bar &bar) {
+    constexpr int P = npass(N, E);
+    if constexpr (p < P) {
+        constexpr int R = DIR < 0 ? radix(N, E, p) : iradix(N, E, p);
+        constexpr int NS = DIR < 0 ? fns(N, E, p) : ins(N, E, p);
+        pass<DIR, N, E, TC, R, NS>(v, t, tw);
+        if constexpr (p + 1 < P) {
+            C *X = xsel ? Xb : Xa;
+            xsel = !xsel;
+            put<N, E, TC, R, NS>(v, t, w, X);
+            if (bar()) return true;
+            get<N, E, TC, (DIR < 0 ? radix(N, E, p + 1) : iradix(N, E, p + 1))>(v, t, w, X);
+        }
+        return passes<DIR, N, E, TC, p + 1>(v, t, w, tw, Xa, Xb, xsel, bar);
+    } else {
+        return false;
+    }
+}
+
+}  // namespace rs
+
+// ---------------------------------------------------------------- tensor copies
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Kernel parameters beside EvalArgs: the tensor maps of the channel workspace
+// ([channel][k0][c] of T words) and of V_ext(G) (a one-channel map of the same shape).
+struct RecipMaps {
+    CUtensorMap chan;
+    CUtensorMap vext;
+};
+
+template <typename T, int N, int E, int NSTAGE> struct RecipShape {
+    typedef typename Vec2<T>::type C;
+    static constexpr int TC = N / E, NT = 32 * TC, TILE = N * 32;
+    static constexpr int BOXR = N > 256 ? 256 : N;    // rows per tensor copy (box limit 256)
+    static constexpr size_t smem = (size_t)(NSTAGE + 2) * TILE * sizeof(C) + (size_t)N * sizeof(C) + 1024;
+    static_assert(rs::npass(N, E) >= 2, "at least two passes");
+    static_assert(N % BOXR == 0, "row boxes");
+};
+
+template <typename T, int N, int E, int NSTAGE, bool MGP>
+__global__ void __launch_bounds__(32 * (N / E), 1)
+    recip_kernel(const EvalArgs<T> a, const __grid_constant__ RecipMaps maps) {
+    typedef typename Vec2<T>::type C;
+    typedef RecipShape<T, N, E, NSTAGE> S;
+    constexpr int TC = S::TC, NT = S::NT, TILE = S::TILE, P = rs::npass(N, E);
+    constexpr int RL = rs::radix(N, E, P - 1);           // last forward radix
+    constexpr int WPC = (int)(sizeof(C) / sizeof(T));    // T words per complex (2)
+    // dynamic shared memory, rounded up to a 1 KB boundary (tensor-copy destinations are
+    // 128-byte aligned; the launch adds 1 KB)
+    extern __shared__ __align__(16) unsigned char recip_smem[];
+    C *const stage = (C *)(recip_smem + ((1024u - (smem_u32(recip_smem) & 1023u)) & 1023u));
+    C *const Xa = stage + NSTAGE * TILE;
+    C *const Xb = Xa + TILE;
+    C *const tw = Xb + TILE;
+    __shared__ __align__(8) uint64_t full[NSTAGE];
+    __shared__ int s_nload;
+    __shared__ double sd[4 * 32];
+    __shared__ T sk[OFDFT_MAX_KNOTS];
+    __shared__ int order[kMaxChan + 1];         // HPP, V_ext, vW, rho^beta, M knots: at most 4 + 64
+    const int w = threadIdx.x & 31, t = threadIdx.x >> 5;
+    const int n2h = a.n2h;
+    const long long PL = (long long)a.n1 * n2h;
+    const int ntile = (int)((PL + 31) / 32);
+    const bool lwt = a.kernel == 0, exact = a.nlpot == 0;
+    const bool hp = a.terms & (8u | 16u), pp = a.terms & 16u;
+
+    // loads of one tile in consumption order: channel slots, -1 for V_ext(G)
+    int nload = 0;
+    if (threadIdx.x == 0) {
+        if (hp) order[nload++] = CH_HPP;
+        if (pp) order[nload++] = -1;
+        if (a.terms & 2u) order[nload++] = CH_VW;
+        if (a.terms & 4u) {
+            order[nload++] = CH_NL;
+            if (!lwt) order[nload++] = CH_KNOT0;
+            else if (exact)
+                for (int m = 0; m < a.M; m++) order[nload++] = CH_KNOT0 + m;
+        }
+        s_nload = nload;
+        for (int s = 0; s < NSTAGE; s++) mbar_init(&full[s], 1);
+        fence_proxy_async_smem();
+    }
+    for (int i = threadIdx.x; i < N; i += NT) tw[i] = a.tw0[i];
+    if ((a.terms & 4u) && lwt)
+        for (int i = threadIdx.x; i < a.M; i += NT) sk[i] = a.knots_t[i];
+    __syncthreads();
+    nload = s_nload;
+    const int my_tiles = (int)blockIdx.x < ntile ? (ntile - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const long long total = (long long)my_tiles * nload;
+    long long issued = 0, cons = 0, pend = 0, L = 0;   // loads issued, released, read since the last barrier, next
+    // thread 0: start loads while their stages are free
+    auto refill = [&]() {
+        if (threadIdx.x != 0) return;
+        bool fenced = false;
+        while (issued < total && issued < cons + NSTAGE) {
+            const int ti = (int)(issued / nload), i = (int)(issued - (long long)ti * nload);
+            const int c0 = (blockIdx.x + ti * gridDim.x) * 32;
+            const int st = (int)(issued % NSTAGE);
+            if (!fenced) {
+                fence_proxy_async_smem();           // the stage was last read through the generic proxy
+                fenced = true;
+            }
+            mbar_arrive_expect_tx(&full[st], (unsigned)(TILE * sizeof(C)));
+            const int ch = order[i];
+#pragma unroll
+            for (int rb = 0; rb < N / S::BOXR; rb++) {
+                C *dst = stage + st * TILE + rb * S::BOXR * 32;
+                if (ch >= 0) tma_load_3d(dst, &maps.chan, c0 * WPC, rb * S::BOXR, ch, &full[st]);
+                else tma_load_3d(dst, &maps.vext, c0 * WPC, rb * S::BOXR, 0, &full[st]);
+            }
+            issued++;
+        }
+    };
+    // block barrier: true (in every thread alike) if a bounded wait of any thread failed
+    // before it; otherwise what was read before it is released and its stages refilled.
+    // After a failure nothing more is issued, and the loads from cons to issued are the
+    // ones that may still be in flight.
+    int wfail = 0;
+    auto bar = [&]() -> bool {
+        if (__syncthreads_or(wfail)) return true;
+        cons += pend;
+        pend = 0;
+        refill();
+        return false;
+    };
+    // the tile of load L (waits for it with a bounded number of polls)
+    auto wait_load = [&]() -> const C * {
+        const int st = (int)(L % NSTAGE);
+        if (!mbar_wait_bounded(&full[st], (unsigned)((L / NSTAGE) & 1), a.wait_polls)) wfail = 1;
+        L++;
+        pend++;
+        return stage + st * TILE;
+    };
+    refill();
+
+    C v[E];
+    bool xsel = false;                         // exchange tile of the next exchange
+    // forward transform of the next load into v (frequency order of the last pass)
+    auto forward = [&]() -> bool {
+        rs::get<N, E, TC, rs::radix(N, E, 0)>(v, t, w, wait_load());
+        return rs::passes<-1, N, E, TC, 0>(v, t, w, tw, Xa, Xb, xsel, bar);
+    };
+    // inverse transform of v and store of the column into channel ch
+    auto inverse_store = [&](int ch, long long col) -> bool {
+        if (rs::passes<+1, N, E, TC, 0>(v, t, w, tw, Xa, Xb, xsel, bar)) return true;
+        if (col < PL) {
+            constexpr int R1 = rs::radix(N, E, 0);
+            C *dst = a.chan + (size_t)ch * a.NH + col;
+#pragma unroll
+            for (int q = 0; q < E / R1; q++)
+#pragma unroll
+                for (int r = 0; r < R1; r++) dst[(size_t)(t + q * TC + r * (N / R1)) * PL] = v[q * R1 + r];
+        }
+        return false;
+    };
+    auto kval = [&](T eta) -> T {
+        if constexpr (MGP) return a.mgp_1mx * gnl(eta) + a.mgp_3xy * mgp_j(a.mgp_tab, a.mgp_n, eta);
+        else return gnl(eta);
+    };
+
+    const T invN = (T)(1.0 / (double)a.N);
+    double eH = 0.0, eV = 0.0, eP = 0.0, eN = 0.0;
+    bool failed = false;
+    for (int ti = 0; ti < my_tiles && !failed; ti++) {
+        const long long col = (long long)(blockIdx.x + ti * gridDim.x) * 32 + w;
+        // this thread's column: its G components, half-spectrum weight, and |G| at its frequencies
+        T cw, gn[E];
+        {
+            const int k1 = (int)(col / n2h), k2 = (int)(col % n2h);
+            const double m1 = (k1 <= a.n1 / 2) ? k1 : k1 - a.n1, m2 = k2;
+            T cv[3];
+            for (int d = 0; d < 3; d++) cv[d] = (T)(m1 * a.bvec[3 + d] + m2 * a.bvec[6 + d]);
+            cw = (col < PL) ? ((k2 == 0 || (a.n2 % 2 == 0 && k2 == a.n2 / 2)) ? (T)1 : (T)2) : (T)0;
+#pragma unroll
+            for (int q = 0; q < E / RL; q++)
+#pragma unroll
+                for (int r = 0; r < RL; r++) {
+                    const int k0 = t + q * TC + r * (N / RL);
+                    const T m0 = (T)(k0 <= N / 2 ? k0 : k0 - N);
+                    const T gx = cv[0] + m0 * (T)a.bvec[0], gy = cv[1] + m0 * (T)a.bvec[1],
+                            gz = cv[2] + m0 * (T)a.bvec[2];
+                    gn[q * RL + r] = dsqrt(gx * gx + gy * gy + gz * gz);
+                }
+        }
+        // ---- Hartree + local pseudopotential
+        if (hp) {
+            if ((failed = forward())) break;
+            C vx[E];
+            if (pp) {
+                const C *X = wait_load();
+#pragma unroll
+                for (int q = 0; q < E / RL; q++)
+#pragma unroll
+                    for (int r = 0; r < RL; r++) vx[q * RL + r] = X[(t + q * TC + r * (N / RL)) * 32 + w];
+            }
+            T fH = 0, fP = 0;
+#pragma unroll
+            for (int i = 0; i < E; i++) {
+                const C X0 = cscale(v[i], invN);
+                const T g2 = gn[i] * gn[i];
+                C out = cmake<C>((T)0, (T)0);
+                if (g2 > (T)0) {
+                    if (a.terms & 8u) {
+                        const T f = (T)1 / g2;
+                        fH += cw * (X0.x * X0.x + X0.y * X0.y) * f;
+                        out = cscale(X0, (T)(4.0 * kPi) * f);
+                    }
+                    if (pp) {
+                        fP += cw * (X0.x * vx[i].x + X0.y * vx[i].y);
+                        out = cadd(out, vx[i]);
+                    }
+                } else if (pp) {
+                    out = vx[i];                      // G = 0: V_ext(0) only
+                }
+                v[i] = out;
+            }
+            eH += (double)fH;
+            eP += (double)fP;
+            if ((failed = inverse_store(CH_HPP, col))) break;
+        }
+        // ---- von Weizsaecker (psi form)
+        if (a.terms & 2u) {
+            if ((failed = forward())) break;
+            T fV = 0;
+#pragma unroll
+            for (int i = 0; i < E; i++) {
+                const C X0 = cscale(v[i], invN);
+                const T g2 = gn[i] * gn[i];
+                fV += cw * g2 * (X0.x * X0.x + X0.y * X0.y);
+                v[i] = cscale(X0, g2);
+            }
+            eV += (double)fV;
+            if ((failed = inverse_store(CH_VW, col))) break;
+        }
+        // ---- nonlocal: kernels at the knots (s2) and the reciprocal half of s3
+        if (a.terms & 4u) {
+            if ((failed = forward())) break;
+            C Rr[E];
+#pragma unroll
+            for (int i = 0; i < E; i++) Rr[i] = cscale(v[i], invN);
+            if (!lwt) {
+                const T hk = (T)(0.5 / a.scal[S_KF_WT]);
+                if ((failed = forward())) break;
+                T fN = 0;
+#pragma unroll
+                for (int i = 0; i < E; i++) {
+                    const T K = (T)kCWT * kval(gn[i] * hk);
+                    const C Sa = cscale(v[i], invN);
+                    fN += cw * K * (Sa.x * Rr[i].x + Sa.y * Rr[i].y);
+                    Rr[i] = cscale(Rr[i], K);
+                    v[i] = cscale(Sa, K);
+                }
+                eN += (double)fN;
+                if ((failed = inverse_store(CH_KNOT0, col))) break;
+#pragma unroll
+                for (int i = 0; i < E; i++) v[i] = Rr[i];
+                if ((failed = inverse_store(CH_NL, col))) break;
+            } else {
+                C A[E];
+#pragma unroll
+                for (int i = 0; i < E; i++) A[i] = cmake<C>((T)0, (T)0);
+                for (int m = 0; m < a.M && !failed; m++) {
+                    const T hk = (T)0.5 / sk[m];
+                    T fN = 0;
+                    if (exact) {
+                        if ((failed = forward())) break;
+#pragma unroll
+                        for (int i = 0; i < E; i++) {
+                            const T K = (T)kCWT * kval(gn[i] * hk);
+                            // E_NL += Omega sum_G w Re(conj(FFT[h_m rho^alpha]) K_m FFT[rho^beta])
+                            const C Sm = cscale(v[i], invN);
+                            fN += cw * K * (Sm.x * Rr[i].x + Sm.y * Rr[i].y);
+                            A[i] = cadd(A[i], cscale(Sm, K));
+                            v[i] = cscale(Rr[i], K);
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < E; i++) v[i] = cscale(Rr[i], (T)kCWT * kval(gn[i] * hk));
+                    }
+                    eN += (double)fN;
+                    failed = inverse_store(CH_KNOT0 + m, col);
+                }
+                if (failed) break;
+                if (exact) {
+#pragma unroll
+                    for (int i = 0; i < E; i++) v[i] = A[i];
+                    if ((failed = inverse_store(CH_NL, col))) break;
+                }
+            }
+        }
+    }
+    if (failed) {
+        // a bounded wait expired: let every copy issued so far land (they target this
+        // block's shared memory) with a longer bounded wait, flag it and leave
+        if (threadIdx.x == 0) {
+            bool drained = true;
+            for (long long l = cons; l < issued; l++)
+                drained = mbar_wait_bounded(&full[l % NSTAGE], (unsigned)((l / NSTAGE) & 1), 1u << 26) && drained;
+            atomicAdd(a.scal + (drained ? S_TIMEOUT : S_FATAL), 1.0);
+        }
+        return;
+    }
+    double r4[4] = {eH, eV, eP, eN};
+    block_sum_n<4>(r4, sd);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 4; k++) a.part_ax0[4 * blockIdx.x + k] = r4[k];
+}
+
+}  // namespace ofdft

@@ -110,11 +110,10 @@ def test_autograd_matches_finite_differences():
         assert abs(fdF - float(pos.grad[I, a])) <= 1e-7 + 1e-6 * abs(fdF)
 
 
-@pytest.mark.parametrize("graph", ["1", "0"])
-def test_batched_equals_single_evaluations(graph, monkeypatch):
+@pytest.mark.parametrize("graph", [1, 0])
+def test_batched_equals_single_evaluations(graph):
     """Batched snapshots (fork/join over internal streams; captured into a CUDA graph
     and replayed when graph = 1) give bit-identical results to single calls."""
-    monkeypatch.setenv("OFDFT_BATCH_GRAPH", graph)
     grids, rhos, singles = [], [], []
     f = ofd.Functional(n_knots=16)
     for s in range(4):
@@ -125,6 +124,7 @@ def test_batched_equals_single_evaluations(graph, monkeypatch):
         rho = W.renormalise(W.apply_noise(W.gaussian_density(cell, (n, n, n), pos, 3.0, 1.0), 0.02, s), cell,
                             wl["n_electrons"])
         g = ofd.Grid(cell, (n, n, n))
+        g.set_option(L.OPTION_BATCH_GRAPH, graph)
         g.set_ions(pos, wl["species"], wl["Z"], wl["rc"])
         r = torch.from_numpy(rho.astype(np.float32)).cuda()
         grids.append(g)

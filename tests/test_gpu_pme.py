@@ -77,3 +77,32 @@ def test_pme_charge_grid_is_bit_reproducible():
         g.set_ions(pos, species, Z, rc, pme_order=8)
         out.append(g.energy_potential(r, ofd.Functional(n_knots=6))[0])
     assert out[0] == out[1]
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+@pytest.mark.parametrize("precision", [L.FP64, L.FP32_MIXED])
+def test_pme_long_axis_supercell_matches_the_cell(axis, precision):
+    """A 4-atom FCC cell repeated 64 times along one axis (1024 points there, 16 on the others):
+    the PME structure factor runs one-channel transforms of length 1024 along that axis, and
+    the perfect supercell's energy per atom equals that of the cell (oracle, direct S(G))."""
+    wl1 = W.workload("fcc-al-4/16")
+    reps = [1, 1, 1]
+    reps[axis] = 64
+    cell = np.diag([wl1["cell"][a][a] * reps[a] for a in range(3)])
+    shape = tuple(16 * r for r in reps)
+    ijk = np.stack(np.meshgrid(*[np.arange(r) for r in reps], indexing="ij"), -1).reshape(-1, 3)
+    pos = (ijk[:, None, :] * np.diag(wl1["cell"])[None, None, :] + wl1["positions"][None]).reshape(-1, 3)
+    r1 = W.model_density(wl1)
+    rho = np.tile(r1, reps)
+    dt = torch.float64 if precision == L.FP64 else torch.float32
+    if precision == L.FP32_MIXED:
+        r1 = r1.astype(np.float32).astype(np.float64)
+    g = ofd.Grid(cell, shape)
+    g.set_ions(pos, np.zeros(len(pos), np.int32), wl1["Z"], wl1["rc"], pme_order=10)
+    E, V = g.energy_potential(torch.from_numpy(rho).to("cuda", dt).contiguous(),
+                              ofd.Functional(n_knots=12, precision=precision))
+    og = OGrid(wl1["cell"], wl1["shape"])
+    Vg = ofn.external_potential_G(og, wl1["positions"], wl1["species"], wl1["Z"], wl1["rc"])
+    E1, _ = evaluate(og, r1, OFunc(n_knots=12), Vg)
+    for k in ("TF", "vW", "NL", "H", "PP", "total"):
+        assert abs(E[k] / len(pos) - E1[k] / 4) <= 1e-6, (k, E[k] / len(pos), E1[k] / 4)
