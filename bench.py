@@ -80,7 +80,7 @@ class Clocks:
             os.makedirs(os.path.dirname(self.out), exist_ok=True)
             self.f = open(self.out, "w")
             self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
             # start timing only once the sampler is producing lines (nvidia-smi takes a moment)
             t0 = time.time()
@@ -479,11 +479,25 @@ def run_gpu(args):
     # gaps between kernels, so those steps are not the headline)
     ms32, wall32 = timed(f32, rho, V, args.steps, profile=False)
     ms32p, _ = timed(f32, rho, V, args.steps, profile=True)
-    clocks = clk.stop()
     prof = g.profile_read()
+    # the sampler keeps running over a longer window of the same K-step loop (at least ~1.5 s,
+    # >= 20 samples at 50 ms), so that the clock record of the headline has enough samples;
+    # the window's own mean step time is reported beside it (not the headline)
+    t_win, n_win = 0.0, 0
+    t0w = time.perf_counter()
+    while time.perf_counter() - t0w < 1.5:
+        msw, _ = timed(f32, rho, V, args.steps, profile=False)
+        t_win += sum(msw)
+        n_win += len(msw)
+    clocks = clk.stop()
     t_step = sum(ms32) / len(ms32)
     t_step_instr = sum(ms32p) / len(ms32p)
     value, t_max = job_throughput(N, t_step, dist, dev)
+    if clocks:
+        clocks["window_ms_per_step"] = round(t_win / max(1, n_win), 5)
+        clocks["window_steps"] = n_win
+        # time x clock: the step in SM cycles at the median clock (compare runs at other clocks)
+        clocks["ms_x_median_mhz"] = round(t_step * clocks["sm_mhz"], 2)
 
     # FP64 path (the speed-up denominator), fewer steps
     V64 = torch.empty_like(rho_d)
@@ -491,6 +505,7 @@ def run_gpu(args):
         step(f64, rho_d, V64)
     ms64, _ = timed(f64, rho_d, V64, max(3, args.steps // 4))
     t64 = sum(ms64) / len(ms64)
+    fp64_peak = ofd.fp64_fma_rate(stream)
 
     # the same evaluation with LDA exchange-correlation added (total-energy use), and the
     # per-geometry ion-ion Ewald sum: context, not the headline
@@ -585,8 +600,7 @@ def run_gpu(args):
     roof = {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1), "peak": peak, "peak_kind": kind,
             "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
             "algorithmic_bytes_per_launch": alg, "avg_launch_ms": round(avg_s * 1e3, 5)}
-    kernels = {k: {"launches": n, "avg_ms": round(t / max(1, n), 5), "share": round(t / max(1e-12, sum(
-        v[1] for v in prof.values())), 4)} for k, (n, t) in prof.items() if n}
+    kernels = kernel_table(prof, wl, 4, peak)
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t_max, 5), "higher_is_better": True, "scaling": "weak",
@@ -594,14 +608,14 @@ def run_gpu(args):
         "config": {"workload": args.workload, "grid": list(wl["shape"]), "atoms": wl["n_atoms"],
                    "n_knots": wl["n_knots"], "functional": "TF+vW+H+PP+LWT(exact V)",
                    "reductions": "f64", "l2": "flushed (512 MB write) before every timed step",
-                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+                   "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "kernel_schedule": g.tuning_report()},
         "with_lda_xc": {"ms_per_step": round(sum(msxc) / len(msxc), 5)},
         "lmgp": {"ms_per_step": round(sum(msmgp) / len(msmgp), 5)},
         "interpolated_potential": {"ms_per_step": round(sum(msint) / len(msint), 5),
                                    "points_per_s": round(N / (sum(msint) / len(msint) * 1e-3), 1)},
         "ewald_per_geometry": {"ms": round(t_ewald * 1e3, 3), "E_ii": Eii},
-        "fp64": {"value": round(N * world / (t64 * 1e-3), 1), "ms_per_step": round(t64, 4),
-                 "speedup_fp32_mixed": round(t64 / t_max, 2)},
+        "fp64": fp64_roofline(wl, N * world, t64, t_max, fp64_peak, peak),
         "energy_check": {"fp32_mixed_total": E32["total"], "fp64_total": E64["total"],
                          "fp32_vs_fp64_Ha_per_atom": abs(E32["total"] - E64["total"]) / wl["n_atoms"]},
         "roofline": roof, "kernels": kernels, "ms_per_step_with_kernel_events": round(t_step_instr, 5),
@@ -614,6 +628,14 @@ def run_gpu(args):
         if eo is not None:
             line["energy_check"]["fp32_vs_oracle_Ha_per_atom"] = abs(E32["total"] - eo) / wl["n_atoms"]
             line["energy_check"]["fp64_vs_oracle_Ha_per_atom"] = abs(E64["total"] - eo) / wl["n_atoms"]
+    if rank == 0 and args.workload == WORKLOAD and not args.no_extra_configs:
+        # the other single-GPU configurations: the isolated cluster and the 1,048,576-atom grid
+        del V64, rho_d
+        torch.cuda.empty_cache()
+        line["mg147_192"] = extra_cluster(args, peak)
+        torch.cuda.empty_cache()
+        line["fcc_al_1m_1024"] = extra_scale(args, peak)
+        torch.cuda.empty_cache()
     if args.multistep and rank == 0:
         # Sec. 2.4's multi-step scheme: converge on a grid of half the points per axis, then
         # carry psi up and converge on the workload's grid; the single-level run beside it
@@ -646,6 +668,154 @@ def run_gpu(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def kernel_table(prof, wl, esize, peak):
+    """Per-kernel launches, mean duration, share of the step and (for the kernels that move
+    channel spectra) achieved GB/s of algorithmic bytes and its fraction of the peak."""
+    total = max(1e-12, sum(v[1] for v in prof.values()))
+    out = {}
+    for k, (n, t) in prof.items():
+        if not n:
+            continue
+        avg = t / n
+        d = {"launches": n, "avg_ms": round(avg, 5), "share": round(t / total, 4)}
+        alg = algorithmic_bytes(k, wl, esize)
+        if alg:
+            d["achieved_gbs"] = round(alg / (avg * 1e-3) / 1e9, 1)
+            d["frac"] = round(alg / (avg * 1e-3) / 1e9 / peak, 4)
+        out[k] = d
+    return out
+
+
+def fft_flops(wl):
+    """Floating-point operations of the transforms of one exact-potential evaluation: 2M + 6
+    real 3-D transforms (Sec. 2.3 s3 plus the semilocal terms), each counted as 2.5 N log2 N
+    (half of the 5 N log2 N of a complex transform of N points)."""
+    n0, n1, n2 = wl["shape"]
+    N = n0 * n1 * n2
+    return (2 * wl["n_knots"] + 6) * 2.5 * N * math.log2(N)
+
+
+def fp64_roofline(wl, points, t64_ms, t32_ms, fp64_peak_gflops, hbm_peak):
+    """The FP64 path against both of its roofs: the measured FP64 FMA rate (its transforms'
+    operations, fft_flops) and HBM (twice the FP32 path's algorithmic bytes)."""
+    ms = t64_ms
+    flops = fft_flops(wl)
+    bytes64 = 2 * sum(algorithmic_bytes(k, wl, 4) for k in ("row_fwd", "pencil_fwd", "axis0_recip", "pencil_inv",
+                                                            "row_inv", "stats"))
+    gf = flops / (ms * 1e-3) / 1e9
+    gbs = bytes64 / (ms * 1e-3) / 1e9
+    return {"value": round(points / (ms * 1e-3), 1), "ms_per_step": round(ms, 4), "speedup_fp32_mixed": round(ms / t32_ms, 2),
+            "roofline": {"fp64_fma_peak_gflops": round(fp64_peak_gflops, 1), "peak_kind": "measured (ofdft_fp64_fma_rate)",
+                         "transform_flops_per_step": int(flops), "achieved_gflops": round(gf, 1),
+                         "frac_fp64": round(gf / fp64_peak_gflops, 4), "bytes_per_step": int(bytes64),
+                         "achieved_gbs": round(gbs, 1), "frac_hbm": round(gbs / hbm_peak, 4),
+                         "bound": "fp64" if gf / fp64_peak_gflops > gbs / hbm_peak else "hbm"}}
+
+
+def _time_config(g, rho, f, steps, dev):
+    """Mean CUDA-event step time (ms) of K asynchronous evaluations (inputs larger than L2, or an
+    L2 flush between steps) and the per-kernel breakdown of K more."""
+    import torch
+    E_dev = torch.zeros(8, dtype=torch.float64, device=dev)
+    V = torch.empty_like(rho)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        g.energy_potential_async(rho, f, E_dev, V)
+    torch.cuda.synchronize()
+    ms = []
+    for i in range(steps):
+        flush.fill_(float(i))
+        st, en = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st.record()
+        g.energy_potential_async(rho, f, E_dev, V)
+        en.record()
+        torch.cuda.synchronize()
+        ms.append(st.elapsed_time(en))
+    g.profile_reset()
+    g.profile(True)
+    for _ in range(steps):
+        flush.fill_(1.0)
+        g.energy_potential_async(rho, f, E_dev, V)
+    torch.cuda.synchronize()
+    g.profile(False)
+    prof = g.profile_read()
+    del V, flush
+    return sum(ms) / len(ms), prof
+
+
+def extra_cluster(args, peak):
+    """mg147/192 (30 knots, vacuum at 1e-8): FP32-mixed and FP64 step times, the FP32 energy
+    against the FP64 path (the oracle comparison is a -m gpu test), kernel breakdown and the
+    reciprocal-space kernel's roofline at this size."""
+    import torch
+    import paper_2002_02985_gb300 as ofd
+    import workloads as W
+    from paper_2002_02985_gb300 import _lib as L
+    dev = torch.device("cuda", 0)
+    wl = W.workload("mg147/192")
+    rho64 = W.model_density(wl)
+    g = ofd.Grid(wl["cell"], wl["shape"])
+    g.set_ions(wl["positions"], wl["species"], wl["Z"], wl["rc"])
+    f32 = ofd.Functional(n_knots=wl["n_knots"], precision=L.FP32_MIXED)
+    f64 = ofd.Functional(n_knots=wl["n_knots"], precision=L.FP64)
+    rho = torch.from_numpy(rho64.astype(np.float32)).to(dev)
+    E32, _ = g.energy_potential(rho, f32)
+    t32, prof = _time_config(g, rho, f32, max(5, args.steps // 2), dev)
+    rho_d = rho.double()
+    E64, _ = g.energy_potential(rho_d, f64)
+    t64, _ = _time_config(g, rho_d, f64, 3, dev)
+    kern = kernel_table(prof, wl, 4, peak)
+    N = rho.numel()
+    return {"grid": list(wl["shape"]), "atoms": wl["n_atoms"], "n_knots": wl["n_knots"],
+            "ms_per_step": round(t32, 4), "points_per_s": round(N / (t32 * 1e-3), 1),
+            "fp64_ms_per_step": round(t64, 3), "speedup_fp32_mixed": round(t64 / t32, 2),
+            "fp32_vs_fp64_Ha_per_atom": abs(E32["total"] - E64["total"]) / wl["n_atoms"],
+            "roofline_axis0_recip": {"achieved_gbs": kern.get("axis0_recip", {}).get("achieved_gbs"),
+                                     "frac": kern.get("axis0_recip", {}).get("frac"), "peak": peak},
+            "kernels": kern, "kernel_schedule": g.tuning_report()}
+
+
+def extra_scale(args, peak):
+    """fcc-al-1m/1024 (1,048,576 atoms, 12 knots, PME order 10): the supercell pin of the
+    noise-free crystal against the 4-atom cell on 16^3 (oracle), and the FP32-mixed step time,
+    kernel breakdown and reciprocal-space roofline on the 2 %-noise density."""
+    import torch
+    import paper_2002_02985_gb300 as ofd
+    import workloads as W
+    from paper_2002_02985_gb300 import _lib as L
+    from oracle import functionals as ofn
+    from oracle.evaluate import Functional as OF, evaluate
+    from oracle.grid import Grid as OG
+    dev = torch.device("cuda", 0)
+    wl = W.workload("fcc-al-1m/1024")
+    wl1 = W.workload("fcc-al-4/16")
+    f32 = ofd.Functional(n_knots=12, precision=L.FP32_MIXED)
+    g = ofd.Grid(wl["cell"], wl["shape"])
+    t0 = time.perf_counter()
+    g.set_ions(wl["positions"], wl["species"], wl["Z"], wl["rc"], pme_order=args.pme_order)
+    rho = W.tiled_density_torch(wl1, 64, 0.0, 5, dev, torch.float32)
+    E, _ = g.energy_potential(rho, f32, want_potential=False)
+    setup = time.perf_counter() - t0
+    og = OG(wl1["cell"], wl1["shape"])
+    Vg1 = ofn.external_potential_G(og, wl1["positions"], wl1["species"], wl1["Z"], wl1["rc"])
+    E1, _ = evaluate(og, W.model_density(wl1).astype(np.float32).astype(np.float64), OF(n_knots=12), Vg1)
+    pin = abs(E["total"] / wl["n_atoms"] - E1["total"] / 4)
+    del rho
+    torch.cuda.empty_cache()
+    rho = W.tiled_density_torch(wl1, 64, 0.02, 5, dev, torch.float32)
+    t32, prof = _time_config(g, rho, f32, 3, dev)
+    kern = kernel_table(prof, wl, 4, peak)
+    N = rho.numel()
+    del rho
+    return {"grid": list(wl["shape"]), "atoms": wl["n_atoms"], "n_knots": 12,
+            "structure_factor": "PME order %d" % args.pme_order, "setup_and_first_eval_s": round(setup, 2),
+            "ms_per_step": round(t32, 3), "points_per_s": round(N / (t32 * 1e-3), 1),
+            "supercell_pin_Ha_per_atom": pin,
+            "roofline_axis0_recip": {"achieved_gbs": kern.get("axis0_recip", {}).get("achieved_gbs"),
+                                     "frac": kern.get("axis0_recip", {}).get("frac"), "peak": peak},
+            "kernels": kern, "kernel_schedule": g.tuning_report()}
 
 
 def algorithmic_bytes(kernel, wl, esize):
@@ -702,6 +872,29 @@ def measured_traffic(kernel, workload):
     return traffic if sha == kernel_source_sha() else None
 
 
+def host_cpu():
+    """Host core count and CPU model (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                model = line.split(":", 1)[1].strip()
+                if line.startswith("Model name"):
+                    break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"host_cores": os.cpu_count(), "cpu_model": model or "unknown", "machine": os.uname().machine}
+
+
 def cpu_baseline(wl, rho64, budget_s):
     """The FP64 oracle as it stands on the host cores: whole E+V evaluations of the same
     workload until ~budget_s seconds have passed (at least one)."""
@@ -721,9 +914,11 @@ def cpu_baseline(wl, rho64, budget_s):
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    return {"value": round(rho.size * n / dt, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} full E+V evaluation(s) of {WORKLOAD} (numpy FP64, single thread)",
-            "seconds": round(dt, 2), "E_total": E["total"]}
+    out = {"value": round(rho.size * n / dt, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{n} full E+V evaluation(s) of {WORKLOAD} (numpy FP64 with its FFTs; one thread used)",
+           "seconds": round(dt, 2), "E_total": E["total"]}
+    out.update(host_cpu())
+    return out
 
 
 def run_reference(args):
@@ -747,8 +942,9 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "grid": list(wl["shape"]),
                                             "n_knots": wl["n_knots"]},
-            "cpu_baseline": {"value": round(v, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} full E+V evaluations of {WORKLOAD}"},
+            "cpu_baseline": dict({"value": round(v, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+                                  "sample": f"{args.steps} full E+V evaluations of {WORKLOAD} (one thread used)"},
+                                 **host_cpu()),
             "e2e": {"value": round(v, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -761,6 +957,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra-configs", action="store_true",
+                    help="skip the mg147/192 and fcc-al-1m/1024 sub-objects of the default line")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="fcc-al-256/128 (default), fcc-al-4/32, mg147/192, mg55/128, fcc-al-108-batch, "
                          "fcc-al-1m/1024")

@@ -330,10 +330,11 @@ int ofdft_profile_read(ofdft_grid *g, int idx, const char **name, int *launches,
  *   OFDFT_OPTION_KERNELS      OFDFT_KERNELS_AUTO (default): size-specialised kernels where
  *                             compiled, their launch shapes picked by the autotuner at the first
  *                             evaluation; OFDFT_KERNELS_GENERIC: the runtime-size kernels only;
- *                             OFDFT_KERNELS_PER_CHANNEL_ROWS: specialised kernels with the rows
- *                             transformed one channel at a time; OFDFT_KERNELS_TILE_RECIP:
- *                             specialised kernels with the column-tile reciprocal-space kernel in
- *                             place of the persistent register-resident one.  A change drops the grid's
+ *                             OFDFT_KERNELS_TILE_RECIP: the default configuration of every role
+ *                             with the column-tile reciprocal-space kernel in place of the
+ *                             persistent register-resident one, no autotuning;
+ *                             OFDFT_KERNELS_PER_CHANNEL_ROWS: the same with the rows transformed
+ *                             one channel at a time.  A change drops the grid's
  *                             workspaces (synchronising its stream); they are rebuilt on next use.
  *   OFDFT_OPTION_BATCH_GRAPH  1 (default): a batched call whose first grid is g is captured once
  *                             into a CUDA graph and replayed; 0: enqueued directly on every call.
@@ -353,6 +354,14 @@ int ofdft_profile_read(ofdft_grid *g, int idx, const char **name, int *launches,
 #define OFDFT_KERNELS_PER_CHANNEL_ROWS  2
 #define OFDFT_KERNELS_TILE_RECIP        3
 int ofdft_set_option(ofdft_grid *g, int option, long long value);
+
+/* The autotuner's record for the grid's workspace of the given precision: for each tuned
+ * kernel role (the reciprocal-space pass, the n1 pencils, the n2 rows) every compiled
+ * configuration with its measured time per evaluation (CUDA events, whole evaluations of
+ * the first call's density) and the one picked; "(cached)" when an earlier grid of the same
+ * shape was timed.  Empty before the first evaluation, or when nothing had to be chosen.
+ * The string stays valid until the grid's next evaluation or destruction. */
+const char *ofdft_tuning_report(const ofdft_grid *g, int precision);
 
 /* Thomas-Fermi energy and potential that allocates no device memory.
  * The paper has no counterpart: this exists for callers that cannot let a
@@ -375,6 +384,14 @@ int ofdft_set_option(ofdft_grid *g, int option, long long value);
 #define OFDFT_NOALLOC_MAX_POINTS 8388608LL   /* 4096 blocks x 2048 points */
 int ofdft_tf_energy_potential_noalloc(const void *rho_dev, long long n, double dV, int precision,
                                       double *E_dev, void *V_dev, void *cuda_stream);
+
+/* Measured FP64 fused multiply-add throughput of the current device, GFLOP/s (2 per FMA):
+ * 8 independent FMA chains per thread, 8 blocks of 256 threads per SM, three timed launches
+ * (CUDA events) after a warm-up on cuda_stream.  A diagnostic: the roof of the FP64
+ * evaluation path, whose kernels do all their arithmetic in FP64.  The paper has no
+ * counterpart.  Synchronises the stream; allocates 8 bytes of device memory for the call.
+ * Errors: OFDFT_ERR_INVALID_ARG (NULL), OFDFT_ERR_OOM, OFDFT_ERR_CUDA. */
+int ofdft_fp64_fma_rate(void *cuda_stream, double *gflops);
 
 /* Human-readable text of a status code, and the handle's last error message. */
 const char *ofdft_status_string(int status);

@@ -121,6 +121,10 @@ class Grid:
         """ofdft_set_option: kernel choice, batch graph, bounded-wait polls, allocation cap."""
         _check(self.lib, self.lib.ofdft_set_option(self.h, option, int(value)), self.h)
 
+    def tuning_report(self, precision: int = L.FP32_MIXED) -> str:
+        """The autotuner's timings and picks for this grid (ofdft_tuning_report)."""
+        return self.lib.ofdft_tuning_report(self.h, precision).decode()
+
     def close(self):
         if getattr(self, "h", None):
             self.lib.ofdft_grid_destroy(self.h)
@@ -270,6 +274,16 @@ class Grid:
         return dict(converged=(st == 0), iterations=rep.iterations, evaluations=rep.evaluations,
                     energy=rep.energy, energies=dict(zip(ENERGY_KEYS, list(rep.energies))), mu=rep.mu,
                     residual=rep.residual, last_dE=rep.last_dE)
+
+
+def fp64_fma_rate(stream=None) -> float:
+    """Measured FP64 FMA throughput of the current device in GFLOP/s (ofdft_fp64_fma_rate)."""
+    import torch
+    lib = library()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    out = ct.c_double()
+    _check(lib, lib.ofdft_fp64_fma_rate(ct.c_void_p(s.cuda_stream), ct.byref(out)))
+    return out.value
 
 
 def td_spectrum(dmu, dt: float, omega, gamma: float = 0.0):

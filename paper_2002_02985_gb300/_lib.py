@@ -42,7 +42,7 @@ EXPORTS = (
     "ofdft_profile_enable", "ofdft_profile_reset", "ofdft_profile_read",
     "ofdft_tf_energy_potential_noalloc", "ofdft_set_ions_pme", "ofdft_ewald", "ofdft_interpolate",
     "ofdft_optimize_density_multistep", "ofdft_optimize_density_ex", "ofdft_td_kick", "ofdft_td_propagate",
-    "ofdft_td_spectrum", "ofdft_set_option",
+    "ofdft_td_spectrum", "ofdft_set_option", "ofdft_tuning_report", "ofdft_fp64_fma_rate",
 )
 NOALLOC_MAX_POINTS = 8388608
 
@@ -120,13 +120,16 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.ofdft_profile_read.argtypes = [P, I, ct.POINTER(ct.c_char_p), ct.POINTER(I), ct.POINTER(D)]
     lib.ofdft_tf_energy_potential_noalloc.argtypes = [V, ct.c_longlong, D, I, V, V, P]
     lib.ofdft_set_option.argtypes = [P, I, ct.c_longlong]
+    lib.ofdft_fp64_fma_rate.argtypes = [P, ct.POINTER(D)]
+    lib.ofdft_tuning_report.argtypes = [P, I]
+    lib.ofdft_tuning_report.restype = ct.c_char_p
     lib.ofdft_status_string.argtypes = [I]
     lib.ofdft_status_string.restype = ct.c_char_p
     lib.ofdft_last_error.argtypes = [P]
     lib.ofdft_last_error.restype = ct.c_char_p
     lib.ofdft_version.restype = ct.c_char_p
     for name in EXPORTS:
-        if name not in ("ofdft_status_string", "ofdft_last_error", "ofdft_version"):
+        if name not in ("ofdft_status_string", "ofdft_last_error", "ofdft_version", "ofdft_tuning_report"):
             getattr(lib, name).restype = ct.c_int
     _lib = lib
     return lib

@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -90,8 +91,13 @@ template <typename T> struct Workspace {
     LaunchSet ks_plain;
     int Brow_p = 0, thr_rowf_p = 0, thr_rowi_p = 0, row2_G_p = 0;
     // persistent reciprocal-space kernel: its grid, and its tensor maps with the buffers
-    // and channel count they were encoded for
-    int recip_grid = 0;
+    // and channel count they were encoded for; the tile kernel's grid
+    int recip_grid = 0, tile_nb_ax0 = 0;
+    // compiled configurations per tuned role, the one in use, and the autotuner's record
+    std::vector<KernelCand> cand[3];
+    int pick[3] = {-1, -1, -1};
+    bool tuned = false, tuning = false;
+    std::string tune_report;
     RecipMaps maps;
     const void *maps_chan = nullptr, *maps_vext = nullptr;
     int maps_nslots = 0;
@@ -226,30 +232,61 @@ bool encode_spectra_map(CUtensorMap *m, const void *base, long long PL, int n0, 
     return r == CUDA_SUCCESS;
 }
 
+// ---------------------------------------------------------------- launch plan and autotuner
+// Roles of the tuned kernel families: rows along n2, pencils along n1, the reciprocal-space pass.
+enum { TUNE_ROWS = 0, TUNE_PENCIL = 1, TUNE_AXIS0 = 2, TUNE_NROLE = 3 };
+
+// put a candidate of a role into the workspace's launch plan
+template <typename T> int apply_cand(ofdft_grid *g, Workspace<T> &w, int role, const KernelCand &c) {
+    if (role == TUNE_ROWS) {
+        w.ks.row_fwd = c.k1;
+        w.ks.row_inv = c.k2;
+        w.Brow = c.batched ? 1 : c.B;
+        w.row2_G = c.batched ? c.B : 0;
+        w.thr_rowf = w.thr_rowi = c.nt;
+    } else if (role == TUNE_PENCIL) {
+        w.ks.pen_fwd = c.k1;
+        w.ks.pen_inv = c.k2;
+        w.TW1 = c.B;
+        w.thr_p1 = c.nt;
+        // persistent pencil grid: every resident block slot of the device, once
+        int per_sm = 0;
+        cudaError_t e = allow_max_dynamic_smem(c.k1);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c.k1, c.nt, pencil_smem_bytes<T>(g->n[1], c.B));
+        if (e != cudaSuccess) return fail(g, OFDFT_ERR_CUDA, "occupancy", e);
+        w.grid_p1 = std::max(1, per_sm) * g->nsm;
+    } else {
+        const long long P = (long long)g->n[1] * g->n2h;
+        if (c.recip.k) {
+            w.ks.recip = c.recip;
+            w.recip_grid = (int)std::min((P + 31) / 32, (long long)c.recip.per_sm * g->nsm);
+        } else {
+            w.ks.recip = RecipLaunch();
+            w.ks.axis0 = c.k1;
+            w.ks.axis0_mgp = c.k2;
+            w.TW0 = c.B;
+            w.thr_ax0 = c.nt;
+            w.ax0_scr = axis0_oop<T>(g->n[0]) ? 1 : 0;
+            w.tile_nb_ax0 = (int)((P + c.B - 1) / c.B);
+        }
+    }
+    return OFDFT_OK;
+}
+
 template <typename T> int choose_launch(ofdft_grid *g, Workspace<T> &w) {
-    typedef typename Vec2<T>::type C;
     const size_t row_budget = 110 * 1024;
     const int cap = Cap<T>::value, tmax = kMaxThreads;
     const bool generic_only = g->kernel_choice == OFDFT_KERNELS_GENERIC;
     w.ks = generic_kernels<T>();
-    const void *k1 = nullptr, *k2 = nullptr;
-    int Bv = 0, ntv = 0;
-    // rows (n2): the channel-batched form where compiled (OFDFT_KERNELS_PER_CHANNEL_ROWS keeps
-    // the per-channel form, for comparison), else the per-channel form
-    const bool per_channel = g->kernel_choice == OFDFT_KERNELS_PER_CHANNEL_ROWS;
-    w.row2_G = 0;
-    if (!generic_only && !per_channel && find_specialised<T>(ROLE_ROW2, g->n[2], &k1, &k2, &Bv, &ntv)) {
-        w.ks.row_fwd = k1;
-        w.ks.row_inv = k2;
-        w.Brow = 1;
-        w.row2_G = Bv;
-        w.thr_rowf = w.thr_rowi = ntv;
-    } else if (!generic_only && find_specialised<T>(ROLE_ROW, g->n[2], &k1, &k2, &Bv, &ntv)) {
-        w.ks.row_fwd = k1;
-        w.ks.row_inv = k2;
-        w.Brow = Bv;
-        w.thr_rowf = w.thr_rowi = ntv;
-    } else {
+    for (int r = 0; r < TUNE_NROLE; r++) {
+        w.cand[r].clear();
+        w.pick[r] = -1;
+    }
+    w.tuned = false;
+    w.tune_report.clear();
+    // runtime-size defaults (replaced below where compiled configurations exist)
+    {
         int B = 16;
         for (; B >= 1; B /= 2)
             if (row_inv_smem_bytes<T>(g->n[2], B) <= row_budget && threads_for(g->plan[2], B, cap) <= tmax) break;
@@ -257,74 +294,90 @@ template <typename T> int choose_launch(ofdft_grid *g, Workspace<T> &w) {
         if (B < 1 && row_inv_smem_bytes<T>(g->n[2], 1) <= 200 * 1024 && threads_for(g->plan[2], 1, cap) <= tmax) B = 1;
         if (B < 1) return fail(g, OFDFT_ERR_UNSUPPORTED_SIZE, "row transform does not fit in shared memory");
         w.Brow = B;
+        w.row2_G = 0;
         w.thr_rowf = w.thr_rowi = std::min(std::max(threads_for(g->plan[2], B, cap), 128), tmax);
-    }
-    // pencils along n1
-    if (!generic_only && find_specialised<T>(ROLE_PENCIL, g->n[1], &k1, &k2, &Bv, &ntv)) {
-        w.ks.pen_fwd = k1;
-        w.ks.pen_inv = k2;
-        w.TW1 = Bv;
-        w.thr_p1 = ntv;
-    } else {
         int TW = 16;
         while (TW > 1 && (pencil_smem_bytes<T>(g->n[1], TW) > 96 * 1024 || threads_for(g->plan[1], TW, cap) > tmax))
             TW /= 2;
         w.TW1 = TW;
         w.thr_p1 = std::min(std::max(threads_for(g->plan[1], TW, cap), 128), tmax);
-    }
-    // axis 0 with the reciprocal-space products
-    if (!generic_only && find_specialised<T>(ROLE_AXIS0, g->n[0], &k1, &k2, &Bv, &ntv)) {
-        w.ks.axis0 = k1;
-        w.ks.axis0_mgp = k2;
-        w.TW0 = Bv;
-        w.thr_ax0 = ntv;
-        w.ax0_scr = axis0_oop<T>(g->n[0]) ? 1 : 0;
-    } else {
-        int TW = 16;
+        TW = 16;
         w.ax0_scr = 0;
         while (TW > 1 && (axis0_smem_bytes<T>(g->n[0], TW, false) > 200 * 1024 || threads_for(g->plan[0], TW, cap) > tmax))
             TW /= 2;
         w.TW0 = TW;
         w.thr_ax0 = std::min(std::max(threads_for(g->plan[0], TW, cap), 128), tmax);
+        w.ks.recip = RecipLaunch();
     }
-    // the persistent reciprocal-space kernel where compiled for n0 (its tensor maps need rows of
-    // an even number of complex values: 16-byte strides)
-    w.ks.recip = RecipLaunch();
-    const long long PLc = (long long)g->n[1] * g->n2h;
-    RecipLaunch rl;
-    if (!generic_only && g->kernel_choice != OFDFT_KERNELS_TILE_RECIP && PLc % 2 == 0 && tensor_encoder() &&
-        find_recip<T>(g->n[0], &rl))
-        w.ks.recip = rl;
+    const long long P = (long long)g->n[1] * g->n2h;
+    if (!generic_only) {
+        // rows: the channel-batched configurations (unless OFDFT_KERNELS_PER_CHANNEL_ROWS), then
+        // the per-channel ones
+        std::vector<KernelCand> c;
+        if (g->kernel_choice != OFDFT_KERNELS_PER_CHANNEL_ROWS) {
+            kernel_candidates<T>(ROLE_ROW2, g->n[2], c);
+            w.cand[TUNE_ROWS] = c;
+        }
+        kernel_candidates<T>(ROLE_ROW, g->n[2], c);
+        w.cand[TUNE_ROWS].insert(w.cand[TUNE_ROWS].end(), c.begin(), c.end());
+        kernel_candidates<T>(ROLE_PENCIL, g->n[1], w.cand[TUNE_PENCIL]);
+        // the reciprocal-space pass: the persistent kernels where compiled for n0 (their tensor
+        // maps need rows of an even number of complex values, 16-byte strides), then the tile ones
+        kernel_candidates<T>(ROLE_AXIS0, g->n[0], c);
+        for (const KernelCand &k : c) {
+            if (k.recip.k && (g->kernel_choice == OFDFT_KERNELS_TILE_RECIP ||
+                              g->kernel_choice == OFDFT_KERNELS_PER_CHANNEL_ROWS || P % 2 != 0 || !tensor_encoder()))
+                continue;
+            w.cand[TUNE_AXIS0].push_back(k);
+        }
+    }
+    // partial buffers sized for every configuration; the first of each role is the default
+    w.tile_nb_ax0 = (int)((P + w.TW0 - 1) / w.TW0);
+    w.nb_ax0 = w.tile_nb_ax0;
+    int min_brow = w.Brow;
+    for (const KernelCand &k : w.cand[TUNE_AXIS0])
+        w.nb_ax0 = std::max(w.nb_ax0, k.recip.k ? (int)std::min((P + 31) / 32, (long long)k.recip.per_sm * g->nsm)
+                                                 : (int)((P + k.B - 1) / k.B));
+    for (const KernelCand &k : w.cand[TUNE_ROWS]) min_brow = std::min(min_brow, k.batched ? 1 : k.B);
+    for (int r = 0; r < TUNE_NROLE; r++) {
+        for (const KernelCand &k : w.cand[r]) {
+            LaunchSet one;
+            one.row_fwd = k.k1;
+            one.row_inv = k.k2;
+            one.recip = k.recip;
+            cudaError_t e = prepare_kernels(one);
+            if (e != cudaSuccess) return fail(g, OFDFT_ERR_CUDA, "kernel attributes", e);
+        }
+        if (!w.cand[r].empty()) {
+            w.pick[r] = 0;
+            int rc = apply_cand<T>(g, w, r, w.cand[r][0]);
+            if (rc) return rc;
+        }
+    }
+    if (w.pick[TUNE_PENCIL] < 0) {
+        int rc = apply_cand<T>(g, w, TUNE_PENCIL, KernelCand{w.ks.pen_fwd, w.ks.pen_inv, w.TW1, w.thr_p1});
+        if (rc) return rc;
+    }
+    // plain one-channel transforms: the per-channel row kernels where compiled
     w.ks_plain = w.ks;
     w.Brow_p = w.Brow;
     w.thr_rowf_p = w.thr_rowf;
     w.thr_rowi_p = w.thr_rowi;
     w.row2_G_p = w.row2_G;
-    if (w.row2_G && find_specialised<T>(ROLE_ROW, g->n[2], &k1, &k2, &Bv, &ntv)) {
-        w.ks_plain.row_fwd = k1;
-        w.ks_plain.row_inv = k2;
-        w.Brow_p = Bv;
-        w.thr_rowf_p = w.thr_rowi_p = ntv;
-        w.row2_G_p = 0;
-    }
+    for (const KernelCand &k : w.cand[TUNE_ROWS])
+        if (!k.batched) {
+            w.ks_plain.row_fwd = k.k1;
+            w.ks_plain.row_inv = k.k2;
+            w.Brow_p = k.B;
+            w.thr_rowf_p = w.thr_rowi_p = k.nt;
+            w.row2_G_p = 0;
+            break;
+        }
     cudaError_t e = prepare_kernels(w.ks);
     if (e == cudaSuccess) e = prepare_kernels(w.ks_plain);
     if (e != cudaSuccess) return fail(g, OFDFT_ERR_CUDA, "kernel attributes", e);
-    // persistent pencil grid: every resident block slot of the device, once
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, w.ks.pen_fwd, w.thr_p1,
-                                                      pencil_smem_bytes<T>(g->n[1], w.TW1));
-    if (e != cudaSuccess) return fail(g, OFDFT_ERR_CUDA, "occupancy", e);
-    w.grid_p1 = std::max(1, per_sm) * g->nsm;
     const long long R = (long long)g->n[0] * g->n[1];
-    w.nb_row = (int)(((R + 1) / 2 + w.Brow - 1) / w.Brow);
-    const long long P = (long long)g->n[1] * g->n2h;
-    w.nb_ax0 = (int)((P + w.TW0 - 1) / w.TW0);
-    if (w.ks.recip.k) {
-        const int ntile = (int)((P + 31) / 32);
-        w.recip_grid = std::min(ntile, w.ks.recip.per_sm * g->nsm);
-        w.nb_ax0 = std::max(w.nb_ax0, w.recip_grid);      // partials sized for either kernel
-    }
+    w.nb_row = (int)(((R + 1) / 2 + min_brow - 1) / min_brow);
     return OFDFT_OK;
 }
 
@@ -359,6 +412,7 @@ template <typename T> int ensure_ws(ofdft_grid *g, int nslots) {
         CK(gmalloc(g, &w.part_misc, 4096 * sizeof(double)), "cudaMalloc partials");
         CK(gmalloc(g, &w.ticket, sizeof(unsigned)), "cudaMalloc ticket");
         CK(cudaMemset(w.ticket, 0, sizeof(unsigned)), "memset ticket");
+
         w.ready = true;
     }
     if (nslots > w.nslots) {
@@ -543,6 +597,118 @@ template <typename T> int ensure_mgp_table(ofdft_grid *g, const ofdft_functional
     return OFDFT_OK;
 }
 
+template <typename T>
+int enqueue_eval(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, double *E_dev_out);
+
+// ---------------------------------------------------------------- autotuner
+// Picks, per tuned role (the reciprocal-space pass, the n1 pencils, the rows), the fastest of
+// the compiled configurations for the grid's sizes: at the first evaluation of a launch plan,
+// each candidate of a role is timed with CUDA events over whole evaluations of the caller's
+// density (the other roles at their current pick), roles in order of their share of the step.
+// The picks are cached per (precision, shape, channel count) for the process, so later grids
+// of the same shape skip the timing.  Evaluations are pure functions of their inputs, so the
+// extra ones change nothing but the time of this first call; none runs while the stream is
+// being captured (the timing is then left for a later call).
+struct TuneEntry {
+    int key[5];
+    int pick[TUNE_NROLE];
+    std::string report;
+};
+std::mutex &tune_mutex() {
+    static std::mutex m;
+    return m;
+}
+std::vector<TuneEntry> &tune_cache() {
+    static std::vector<TuneEntry> c;
+    return c;
+}
+
+template <typename T> int autotune(ofdft_grid *g, Workspace<T> &w, const T *rho, const ofdft_functional *f) {
+    bool any = false;
+    for (int r = 0; r < TUNE_NROLE; r++) any = any || w.cand[r].size() > 1;
+    if (!any) {
+        w.tuned = true;
+        return OFDFT_OK;
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(g->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        (void)cudaGetLastError();
+        return OFDFT_OK;                                  // not now: timing is impossible in a capture
+    }
+    w.tuned = true;
+    const int key[5] = {(int)sizeof(T), g->n[0], g->n[1], g->n[2], w.nslots};
+    {
+        std::lock_guard<std::mutex> lk(tune_mutex());
+        for (const TuneEntry &e : tune_cache())
+            if (std::memcmp(e.key, key, sizeof(key)) == 0) {
+                for (int r = 0; r < TUNE_NROLE; r++)
+                    if (e.pick[r] >= 0 && e.pick[r] < (int)w.cand[r].size()) {
+                        int rc = apply_cand<T>(g, w, r, w.cand[r][e.pick[r]]);
+                        if (rc) return rc;
+                        w.pick[r] = e.pick[r];
+                    }
+                w.tune_report = e.report + " (cached)";
+                return OFDFT_OK;
+            }
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0), "event");
+    cudaError_t ee = cudaEventCreate(&e1);
+    if (ee != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(g, OFDFT_ERR_CUDA, "event", ee);
+    }
+    const int reps = g->N > (1LL << 24) ? 2 : 5;
+    w.tuning = true;
+    int rc = OFDFT_OK;
+    std::string rep;
+    const int order[TUNE_NROLE] = {TUNE_AXIS0, TUNE_PENCIL, TUNE_ROWS};
+    const char *role_name[TUNE_NROLE] = {"rows", "pencil", "recip"};
+    for (int oi = 0; oi < TUNE_NROLE && rc == OFDFT_OK; oi++) {
+        const int r = order[oi];
+        if (w.cand[r].size() < 2) continue;
+        int best = -1;
+        float best_ms = 0.f;
+        rep += std::string(rep.empty() ? "" : "; ") + role_name[r] + ":";
+        for (int c = 0; c < (int)w.cand[r].size() && rc == OFDFT_OK; c++) {
+            if ((rc = apply_cand<T>(g, w, r, w.cand[r][c]))) break;
+            if ((rc = enqueue_eval<T>(g, rho, f, nullptr, nullptr))) break;       // warm-up
+            cudaEventRecord(e0, g->stream);
+            for (int i = 0; i < reps && rc == OFDFT_OK; i++) rc = enqueue_eval<T>(g, rho, f, nullptr, nullptr);
+            cudaEventRecord(e1, g->stream);
+            cudaError_t e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess && rc == OFDFT_OK) rc = fail(g, OFDFT_ERR_CUDA, "autotuner timing", e);
+            ms /= (float)reps;
+            char buf[96];
+            std::snprintf(buf, sizeof(buf), " [%s] %.4f ms", w.cand[r][c].name, ms);
+            rep += buf;
+            if (best < 0 || ms < best_ms) {
+                best = c;
+                best_ms = ms;
+            }
+        }
+        if (rc == OFDFT_OK && best >= 0) {
+            rc = apply_cand<T>(g, w, r, w.cand[r][best]);
+            w.pick[r] = best;
+            rep += std::string(" -> ") + w.cand[r][best].name;
+        }
+    }
+    w.tuning = false;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    w.tune_report = rep;
+    std::lock_guard<std::mutex> lk(tune_mutex());
+    TuneEntry te;
+    std::memcpy(te.key, key, sizeof(key));
+    for (int r = 0; r < TUNE_NROLE; r++) te.pick[r] = w.pick[r];
+    te.report = rep;
+    tune_cache().push_back(te);
+    return OFDFT_OK;
+}
+
 // Fill the evaluation arguments and enqueue one evaluation.
 template <typename T>
 int enqueue_eval(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, double *E_dev_out) {
@@ -558,6 +724,8 @@ int enqueue_eval(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, d
         if (rc) return rc;
     }
     if ((rc = ensure_mgp_table<T>(g, f))) return rc;
+    if (!w.tuned && !w.tuning && g->kernel_choice == OFDFT_KERNELS_AUTO && (rc = autotune<T>(g, w, rho, f)))
+        return rc;
     EvalArgs<T> a;
     std::memset(&a, 0, sizeof(a));
     a.n0 = g->n[0];
@@ -600,8 +768,8 @@ int enqueue_eval(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, d
     a.energies = E_dev_out ? E_dev_out : w.energies;
     a.ticket = w.ticket;
     a.nb_stats = 2 * g->nsm;
-    a.nb_ax0 = w.ks.recip.k ? w.recip_grid : w.nb_ax0;
-    a.nb_row = w.nb_row;
+    a.nb_ax0 = w.ks.recip.k ? w.recip_grid : w.tile_nb_ax0;
+    a.nb_row = (int)((((long long)g->n[0] * g->n[1] + 1) / 2 + w.Brow - 1) / w.Brow);   // the row kernels' grid
     a.p0 = g->plan[0];
     a.p1 = g->plan[1];
     a.p2 = g->plan[2];
@@ -1781,7 +1949,8 @@ cudaStream_t *batch_streams() {
     return s;
 }
 
-template <typename T> int prepare_batch_grid(ofdft_grid *g, const ofdft_functional *f, bool forces) {
+template <typename T>
+int prepare_batch_grid(ofdft_grid *g, const ofdft_functional *f, bool forces, const T *rho) {
     const bool nl = f->terms & OFDFT_TERM_NL;
     const bool lwt = nl && f->kernel == OFDFT_KERNEL_LWT;
     const int nslots = nl ? (lwt ? 3 + f->n_knots : 4) : 3;
@@ -1790,6 +1959,8 @@ template <typename T> int prepare_batch_grid(ofdft_grid *g, const ofdft_function
     if ((f->terms & OFDFT_TERM_PP) && (rc = ensure_vext<T>(g))) return rc;
     if (forces && (rc = ensure_force_buffers<T>(g))) return rc;
     if ((rc = ensure_mgp_table<T>(g, f))) return rc;     // before any graph capture
+    Workspace<T> &w = ws<T>(g);
+    if (!w.tuned && g->kernel_choice == OFDFT_KERNELS_AUTO && (rc = autotune<T>(g, w, rho, f))) return rc;
     return OFDFT_OK;
 }
 
@@ -1837,7 +2008,7 @@ int batched_impl(int n, ofdft_grid *const *grids, const void *const *rho_dev, co
     cudaStream_t user = grids[0]->stream;
     ofdft_grid *g0 = grids[0];
     for (int i = 0; i < n; i++) {
-        int rc = prepare_batch_grid<T>(grids[i], f, F_out && F_out[i]);
+        int rc = prepare_batch_grid<T>(grids[i], f, F_out && F_out[i], (const T *)rho_dev[i]);
         if (rc) return rc;
     }
     bool use_graph = g0->batch_graph && !f->knots;
@@ -1986,6 +2157,12 @@ int ofdft_profile_read(ofdft_grid *g, int idx, const char **name, int *launches,
     if (launches) *launches = g->prof_n[idx];
     if (total_ms) *total_ms = g->prof_ms[idx];
     return OFDFT_OK;
+}
+
+const char *ofdft_tuning_report(const ofdft_grid *g, int precision) {
+    if (!g) return "null handle";
+    const std::string &r = precision == OFDFT_FP64 ? g->w64.tune_report : g->w32.tune_report;
+    return r.c_str();
 }
 
 int ofdft_set_option(ofdft_grid *g, int option, long long value) {

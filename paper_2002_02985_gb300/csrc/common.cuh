@@ -109,6 +109,14 @@ template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
     return cmake<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C::x) s) { return cmake<C>(a.x * s, a.y * s); }
+// FP32 complex values: both components in one packed two-wide FP32 instruction (sm_100 and
+// later); each component is rounded exactly as the scalar operation rounds it (a - b is
+// fma(b, -1, a), a single rounding of the exact difference)
+template <> __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) { return __fadd2_rn(a, b); }
+template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) {
+    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+template <> __device__ __forceinline__ float2 cscale<float2>(float2 a, float s) { return __fmul2_rn(a, make_float2(s, s)); }
 // multiply by (s i) with s = -1 (forward) or +1 (inverse)
 template <int DIR, typename C> __device__ __forceinline__ C cmul_si(C a) {
     return DIR < 0 ? cmake<C>(a.y, -a.x) : cmake<C>(-a.y, a.x);

@@ -15,6 +15,8 @@
 //   finalize  1 block: FP64 energies in a fixed order
 #pragma once
 
+#include <vector>
+
 #include "fft.cuh"
 
 namespace ofdft {
@@ -166,15 +168,29 @@ struct LaunchSet {
 
 // tensor maps of the persistent reciprocal-space kernel (defined in recip.cuh)
 struct RecipMaps;
-// the persistent reciprocal-space kernel compiled for n0 = n in precision T, if any
-template <typename T> bool find_recip(int n, RecipLaunch *out);
 
 // role of a kernel family for the size registry
 enum { ROLE_ROW = 0, ROLE_PENCIL = 1, ROLE_AXIS0 = 2, ROLE_ROW2 = 3 };
 
-// Size-specialised kernels of a role for size n, with their fixed batch (B or
-// TW) and block size; false when none is compiled for that size/precision.
+// One compiled configuration of a role: the kernel pair (rows and pencils: forward and
+// inverse; the tile reciprocal-space kernel: Wang-Teter and Eq. MGP forms), its fixed batch
+// (row pairs, channel group G, or column-tile width TW) and block size; for ROLE_AXIS0 the
+// persistent kernel instead when recip.k is set.
+struct KernelCand {
+    const void *k1 = nullptr, *k2 = nullptr;
+    int B = 0, nt = 0;
+    bool batched = false;                 // channel-batched row kernels (B = channels per group)
+    RecipLaunch recip;
+    char name[48] = {0};
+};
+
+// The compiled configurations of a role for axis length n (empty: only the runtime-size
+// kernels exist), the default first.  ROLE_AXIS0 lists the persistent kernels first.
+template <typename T> void kernel_candidates(int role, int n, std::vector<KernelCand> &out);
+// The default configuration of a role for size n; false when none is compiled.
 template <typename T> bool find_specialised(int role, int n, const void **k1, const void **k2, int *B, int *nt);
+// the persistent reciprocal-space kernels compiled for n0 = n (recip.cu)
+template <typename T> void recip_candidates(int n, std::vector<KernelCand> &out);
 // The generic (runtime-size) kernels.
 template <typename T> LaunchSet generic_kernels();
 // Let every kernel of the set use the device's full opt-in shared memory.

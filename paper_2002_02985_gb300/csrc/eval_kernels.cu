@@ -4,14 +4,32 @@
 namespace ofdft {
 
 // size-specialised instantiations live in the inst_*.cu translation units
-template <typename T> bool find_specialised_a(int, int, const void **, const void **, int *, int *);
-template <typename T> bool find_specialised_b(int, int, const void **, const void **, int *, int *);
-template <typename T> bool find_specialised_c(int, int, const void **, const void **, int *, int *);
-template <typename T> bool find_specialised_d(int, int, const void **, const void **, int *, int *);
+template <typename T> void candidates_a(int, int, std::vector<KernelCand> &);
+template <typename T> void candidates_b(int, int, std::vector<KernelCand> &);
+template <typename T> void candidates_c(int, int, std::vector<KernelCand> &);
+template <typename T> void candidates_d(int, int, std::vector<KernelCand> &);
+
+template <typename T> void kernel_candidates(int role, int n, std::vector<KernelCand> &out) {
+    out.clear();
+    if (role == ROLE_AXIS0) recip_candidates<T>(n, out);
+    candidates_a<T>(role, n, out);
+    candidates_b<T>(role, n, out);
+    candidates_c<T>(role, n, out);
+    candidates_d<T>(role, n, out);
+}
 
 template <typename T> bool find_specialised(int role, int n, const void **k1, const void **k2, int *B, int *nt) {
-    return find_specialised_a<T>(role, n, k1, k2, B, nt) || find_specialised_b<T>(role, n, k1, k2, B, nt) ||
-           find_specialised_c<T>(role, n, k1, k2, B, nt) || find_specialised_d<T>(role, n, k1, k2, B, nt);
+    std::vector<KernelCand> c;
+    kernel_candidates<T>(role, n, c);
+    for (const KernelCand &k : c)
+        if (!k.recip.k) {
+            *k1 = k.k1;
+            *k2 = k.k2;
+            *B = k.B;
+            *nt = k.nt;
+            return true;
+        }
+    return false;
 }
 
 template <typename T> LaunchSet generic_kernels() {
@@ -189,6 +207,7 @@ template <typename T> cudaError_t launch_mgp_table(T *tab, int n, double y, cons
 #define INST(T)                                                                                              \
     template cudaError_t launch_mgp_table<T>(T *, int, double, const double *, cudaStream_t);               \
     template bool find_specialised<T>(int, int, const void **, const void **, int *, int *);                 \
+    template void kernel_candidates<T>(int, int, std::vector<KernelCand> &);                                 \
     template LaunchSet generic_kernels<T>();                                                                 \
     template cudaError_t launch_eval<T>(const EvalArgs<T> &, const LaunchSet &, cudaStream_t, const ProfHook *,   \
                                         const RecipMaps *);                                                  \

@@ -3,17 +3,16 @@
 
 namespace ofdft {
 
-template <typename T> bool find_specialised_b(int role, int n, const void **k1, const void **k2, int *B, int *nt);
+template <typename T> void candidates_b(int role, int n, std::vector<KernelCand> &out);
 
-template <> bool find_specialised_b<float>(int role, int n, const void **k1, const void **k2, int *B, int *nt) {
-    OFDFT_SPECIALISE_ROW2(float, 64, 20, 96, 16, 6)
-    OFDFT_SPECIALISE_ROW2(float, 80, 20, 128, 16, 5)
-    OFDFT_SPECIALISE_ROW2(float, 96, 20, 128, 16, 5)
-    OFDFT_SPECIALISE(float, 64, 16, 128, 16, 128, 16, 128)
-    OFDFT_SPECIALISE(float, 80, 16, 256, 16, 256, 16, 256)
-    OFDFT_SPECIALISE(float, 96, 8, 256, 16, 256, 16, 256)
-    return false;
+template <> void candidates_b<float>(int role, int n, std::vector<KernelCand> &out) {
+    OFDFT_CAND_ROW2(float, 64, 20, 96, 16, 6)
+    OFDFT_CAND_ROW2(float, 80, 20, 128, 16, 5)
+    OFDFT_CAND_ROW2(float, 96, 20, 128, 16, 5)
+    OFDFT_CAND_ALL(float, 64, 16, 128, 16, 128, 16, 128)
+    OFDFT_CAND_ALL(float, 80, 16, 256, 16, 256, 16, 256)
+    OFDFT_CAND_ALL(float, 96, 8, 256, 16, 256, 16, 256)
 }
-template <> bool find_specialised_b<double>(int, int, const void **, const void **, int *, int *) { return false; }
+template <> void candidates_b<double>(int, int, std::vector<KernelCand> &) {}
 
 }  // namespace ofdft

@@ -3,15 +3,14 @@
 
 namespace ofdft {
 
-template <typename T> bool find_specialised_d(int role, int n, const void **k1, const void **k2, int *B, int *nt);
+template <typename T> void candidates_d(int role, int n, std::vector<KernelCand> &out);
 
-template <> bool find_specialised_d<float>(int role, int n, const void **k1, const void **k2, int *B, int *nt) {
+template <> void candidates_d<float>(int role, int n, std::vector<KernelCand> &out) {
     // rows: 8 channels per transform (two groups for 15 channels), 512 threads, one block per SM
-    OFDFT_SPECIALISE_ROW2(float, 1024, 8, 512, 16, 1)
-    OFDFT_SPECIALISE_PENCIL(float, 1024, 8, 512, 1)
-    OFDFT_SPECIALISE_AXIS0(float, 1024, 4, 256, 16, 1)
-    return false;
+    OFDFT_CAND_ROW2(float, 1024, 8, 512, 16, 1)
+    OFDFT_CAND_PENCIL(float, 1024, 8, 512, 16, 1)
+    OFDFT_CAND_AXIS0(float, 1024, 4, 256, 16, 1)
 }
-template <> bool find_specialised_d<double>(int, int, const void **, const void **, int *, int *) { return false; }
+template <> void candidates_d<double>(int, int, std::vector<KernelCand> &) {}
 
 }  // namespace ofdft

@@ -79,11 +79,14 @@ template <> struct GnlTerms<double> { static constexpr int value = 28; };
 // intrinsics (at most 2 ulp for these operand ranges, against the few ulp the
 // FP32 sums already carry); FP64 keeps IEEE division and log.
 __device__ __forceinline__ float gdiv(float a, float b) { return __fdividef(a, b); }
-__device__ __forceinline__ double gdiv(double a, double b) { return a / b; }
+__host__ __device__ __forceinline__ double gdiv(double a, double b) { return a / b; }
 __device__ __forceinline__ float glog(float x) { return __logf(x); }
-__device__ __forceinline__ double glog(double x) { return log(x); }
+__host__ __device__ __forceinline__ double glog(double x) { return log(x); }
+__host__ __device__ __forceinline__ double gabs(double x) { return fabs(x); }
+__device__ __forceinline__ float gabs(float x) { return fabsf(x); }
 
-template <typename T> __device__ __forceinline__ T gnl(T eta) {
+// (host and device: the FP64 form also builds the FP32-mixed kernel table)
+template <typename T> __host__ __device__ __forceinline__ T gnl(T eta) {
     constexpr int nt = GnlTerms<T>::value;
     // both series are sums sum_{m=1}^{nt} c_m z^m, evaluated by Horner's rule with fused
     // multiply-adds: p = c_nt, p = p z + c_m (m = nt-1..1), sum = p z
@@ -113,8 +116,8 @@ template <typename T> __device__ __forceinline__ T gnl(T eta) {
         return -gdiv(pN, pF);          // the common factor x of both sums cancels
     }
     const T d = (T)1 - eta;
-    if (dabs(d) < (T)1e-12) return (T)-2;
-    const T F = (T)0.5 + gdiv((T)1 - eta * eta, (T)4 * eta) * glog(dabs(gdiv((T)1 + eta, d)));
+    if (gabs(d) < (T)1e-12) return (T)-2;
+    const T F = (T)0.5 + gdiv((T)1 - eta * eta, (T)4 * eta) * glog(gabs(gdiv((T)1 + eta, d)));
     return gdiv((T)1, F) - (T)3 * eta * eta - (T)1;
 }
 
@@ -126,6 +129,13 @@ template <typename T> __device__ __forceinline__ T mgp_j(const T *tab, int n, T 
     i = i > n - 2 ? n - 2 : i;
     const T f = pos - (T)i, t0 = tab[i];
     return t0 + f * (tab[i + 1] - t0);
+}
+
+// The kernel of Eq. WT (C_WT G_NL) or of Eq. MGP at eta = |G| / (2k)
+template <typename T, bool MGP> __device__ __forceinline__ T kernel_value(const EvalArgs<T> &a, T eta) {
+    T G = gnl(eta);
+    if constexpr (MGP) G = a.mgp_1mx * G + a.mgp_3xy * mgp_j(a.mgp_tab, a.mgp_n, eta);
+    return (T)kCWT * G;
 }
 
 // ======================================================================= LDA exchange-correlation
@@ -606,11 +616,6 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
     }
     const T invN = (T)(1.0 / (double)a.N);
     double eH = 0.0, eV = 0.0, eP = 0.0, eN = 0.0;
-    // kernel of Eq. WT, or of Eq. MGP (the instantiation with the correction table)
-    auto kval = [&](T eta) -> T {
-        if constexpr (MGP) return a.mgp_1mx * gnl(eta) + a.mgp_3xy * mgp_j(a.mgp_tab, a.mgp_n, eta);
-        else return gnl(eta);
-    };
 
     // ---- Hartree + local pseudopotential
     if (a.terms & (8u | 16u)) {
@@ -687,7 +692,7 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
             T fN = 0;
             for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
                 const int w = idx % TW;
-                const T K = (T)kCWT * kval(gn[idx] * hk);
+                const T K = kernel_value<T, MGP>(a, gn[idx] * hk);
                 const C Sa = cscale(S[idx], invN);
                 const C Rb = Rr[idx];
                 fN += cw[w] * K * (Sa.x * Rb.x + Sa.y * Rb.y);
@@ -719,7 +724,7 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
                 }
                 T fN = 0;
                 for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
-                    const T K = (T)kCWT * kval(gn[idx] * hk);
+                    const T K = kernel_value<T, MGP>(a, gn[idx] * hk);
                     if (exact) {
                         // E_NL += Omega sum_G w Re(conj(FFT[h_m rho^alpha]) K_m FFT[rho^beta])
                         const C Sm = cscale(S[idx], invN);

@@ -1,29 +1,42 @@
 // Instantiations of the persistent reciprocal-space kernel (recip.cuh) and its registry.
+#include <cstdio>
+
 #include "recip.cuh"
 
 namespace ofdft {
 
 namespace {
-template <typename T, int N, int E, int NSTAGE> void set_recip(RecipLaunch *out) {
+template <typename T, int N, int E, int NSTAGE> void add_recip(std::vector<KernelCand> &out) {
     typedef RecipShape<T, N, E, NSTAGE> S;
-    out->k = (const void *)recip_kernel<T, N, E, NSTAGE, false>;
-    out->k_mgp = (const void *)recip_kernel<T, N, E, NSTAGE, true>;
-    out->nt = S::NT;
-    out->per_sm = 1;
-    out->smem = S::smem;
+    KernelCand c;
+    c.recip.k = (const void *)recip_kernel<T, N, E, NSTAGE, false>;
+    c.recip.k_mgp = (const void *)recip_kernel<T, N, E, NSTAGE, true>;
+    c.recip.nt = S::NT;
+    c.recip.per_sm = 1;
+    c.recip.smem = S::smem;
+    c.B = 32;
+    c.nt = S::NT;
+    std::snprintf(c.name, sizeof(c.name), "recip E%d s%d x%d", E, NSTAGE, S::NT);
+    out.push_back(c);
 }
 }  // namespace
 
 // n0 lengths with a register-resident plan: E elements per thread (every radix divides E),
-// NSTAGE channel tiles in flight
-template <> bool find_recip<float>(int n, RecipLaunch *out) {
+// NSTAGE channel tiles in flight; the first is the default, the autotuner times the rest
+template <> void recip_candidates<float>(int n, std::vector<KernelCand> &out) {
     switch (n) {
-        case 128: set_recip<float, 128, 16, 4>(out); return true;
-        case 64: set_recip<float, 64, 8, 6>(out); return true;
-        case 32: set_recip<float, 32, 4, 8>(out); return true;
-        default: return false;
+        case 128:
+            add_recip<float, 128, 16, 4>(out);
+            add_recip<float, 128, 8, 4>(out);
+            break;
+        case 64:
+            add_recip<float, 64, 8, 6>(out);
+            add_recip<float, 64, 4, 6>(out);
+            break;
+        case 32: add_recip<float, 32, 4, 8>(out); break;
+        default: break;
     }
 }
-template <> bool find_recip<double>(int, RecipLaunch *) { return false; }
+template <> void recip_candidates<double>(int, std::vector<KernelCand> &) {}
 
 }  // namespace ofdft

@@ -160,6 +160,15 @@ template <typename T, int N, int E, int NSTAGE> struct RecipShape {
     static_assert(N % BOXR == 0, "row boxes");
 };
 
+// Operations of one tile, in order (each one a channel of the workspace): the forward
+// transform of the next loaded tile (fwd), the reciprocal-space product of the kind, and
+// the inverse transform stored into channel `store` (< 0: nothing stored).
+enum { OP_HPP = 0, OP_VW, OP_RB, OP_WT, OP_RR, OP_EX, OP_IP, OP_A };
+struct RecipOp {
+    signed char kind, fwd;
+    short store, m;
+};
+
 template <typename T, int N, int E, int NSTAGE, bool MGP>
 __global__ void __launch_bounds__(32 * (N / E), 1)
     recip_kernel(const EvalArgs<T> a, const __grid_constant__ RecipMaps maps) {
@@ -176,10 +185,11 @@ __global__ void __launch_bounds__(32 * (N / E), 1)
     C *const Xb = Xa + TILE;
     C *const tw = Xb + TILE;
     __shared__ __align__(8) uint64_t full[NSTAGE];
-    __shared__ int s_nload;
+    __shared__ int s_nload, s_nops;
     __shared__ double sd[4 * 32];
     __shared__ T sk[OFDFT_MAX_KNOTS];
     __shared__ int order[kMaxChan + 1];         // HPP, V_ext, vW, rho^beta, M knots: at most 4 + 64
+    __shared__ RecipOp ops[kMaxChan + 2];
     const int w = threadIdx.x & 31, t = threadIdx.x >> 5;
     const int n2h = a.n2h;
     const long long PL = (long long)a.n1 * n2h;
@@ -187,19 +197,42 @@ __global__ void __launch_bounds__(32 * (N / E), 1)
     const bool lwt = a.kernel == 0, exact = a.nlpot == 0;
     const bool hp = a.terms & (8u | 16u), pp = a.terms & 16u;
 
-    // loads of one tile in consumption order: channel slots, -1 for V_ext(G)
-    int nload = 0;
     if (threadIdx.x == 0) {
-        if (hp) order[nload++] = CH_HPP;
-        if (pp) order[nload++] = -1;
-        if (a.terms & 2u) order[nload++] = CH_VW;
-        if (a.terms & 4u) {
-            order[nload++] = CH_NL;
-            if (!lwt) order[nload++] = CH_KNOT0;
-            else if (exact)
-                for (int m = 0; m < a.M; m++) order[nload++] = CH_KNOT0 + m;
+        // loads of one tile in consumption order (channel slots; -1: V_ext(G)) and the operations
+        int nl = 0, no = 0;
+        auto op = [&](int kind, int fwd, int store, int m) {
+            ops[no].kind = (signed char)kind;
+            ops[no].fwd = (signed char)fwd;
+            ops[no].store = (short)store;
+            ops[no].m = (short)m;
+            no++;
+        };
+        if (hp) {
+            order[nl++] = CH_HPP;
+            if (pp) order[nl++] = -1;
+            op(OP_HPP, 1, CH_HPP, 0);
         }
-        s_nload = nload;
+        if (a.terms & 2u) {
+            order[nl++] = CH_VW;
+            op(OP_VW, 1, CH_VW, 0);
+        }
+        if (a.terms & 4u) {
+            order[nl++] = CH_NL;
+            op(OP_RB, 1, -1, 0);
+            if (!lwt) {
+                order[nl++] = CH_KNOT0;
+                op(OP_WT, 1, CH_KNOT0, 0);
+                op(OP_RR, 0, CH_NL, 0);
+            } else {
+                for (int m = 0; m < a.M; m++) {
+                    if (exact) order[nl++] = CH_KNOT0 + m;
+                    op(exact ? OP_EX : OP_IP, exact ? 1 : 0, CH_KNOT0 + m, m);
+                }
+                if (exact) op(OP_A, 0, CH_NL, 0);
+            }
+        }
+        s_nload = nl;
+        s_nops = no;
         for (int s = 0; s < NSTAGE; s++) mbar_init(&full[s], 1);
         fence_proxy_async_smem();
     }
@@ -207,7 +240,7 @@ __global__ void __launch_bounds__(32 * (N / E), 1)
     if ((a.terms & 4u) && lwt)
         for (int i = threadIdx.x; i < a.M; i += NT) sk[i] = a.knots_t[i];
     __syncthreads();
-    nload = s_nload;
+    const int nload = s_nload, nops = s_nops;
     const int my_tiles = (int)blockIdx.x < ntile ? (ntile - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const long long total = (long long)my_tiles * nload;
     long long issued = 0, cons = 0, pend = 0, L = 0;   // loads issued, released, read since the last barrier, next
@@ -256,34 +289,11 @@ __global__ void __launch_bounds__(32 * (N / E), 1)
     };
     refill();
 
-    C v[E];
-    bool xsel = false;                         // exchange tile of the next exchange
-    // forward transform of the next load into v (frequency order of the last pass)
-    auto forward = [&]() -> bool {
-        rs::get<N, E, TC, rs::radix(N, E, 0)>(v, t, w, wait_load());
-        return rs::passes<-1, N, E, TC, 0>(v, t, w, tw, Xa, Xb, xsel, bar);
-    };
-    // inverse transform of v and store of the column into channel ch
-    auto inverse_store = [&](int ch, long long col) -> bool {
-        if (rs::passes<+1, N, E, TC, 0>(v, t, w, tw, Xa, Xb, xsel, bar)) return true;
-        if (col < PL) {
-            constexpr int R1 = rs::radix(N, E, 0);
-            C *dst = a.chan + (size_t)ch * a.NH + col;
-#pragma unroll
-            for (int q = 0; q < E / R1; q++)
-#pragma unroll
-                for (int r = 0; r < R1; r++) dst[(size_t)(t + q * TC + r * (N / R1)) * PL] = v[q * R1 + r];
-        }
-        return false;
-    };
-    auto kval = [&](T eta) -> T {
-        if constexpr (MGP) return a.mgp_1mx * gnl(eta) + a.mgp_3xy * mgp_j(a.mgp_tab, a.mgp_n, eta);
-        else return gnl(eta);
-    };
-
     const T invN = (T)(1.0 / (double)a.N);
     double eH = 0.0, eV = 0.0, eP = 0.0, eN = 0.0;
     bool failed = false;
+    C v[E], Rr[E], A[E];
+    bool xsel = false;                         // exchange tile of the next exchange
     for (int ti = 0; ti < my_tiles && !failed; ti++) {
         const long long col = (long long)(blockIdx.x + ti * gridDim.x) * 32 + w;
         // this thread's column: its G components, half-spectrum weight, and |G| at its frequencies
@@ -305,116 +315,112 @@ __global__ void __launch_bounds__(32 * (N / E), 1)
                     gn[q * RL + r] = dsqrt(gx * gx + gy * gy + gz * gz);
                 }
         }
-        // ---- Hartree + local pseudopotential
-        if (hp) {
-            if ((failed = forward())) break;
-            C vx[E];
-            if (pp) {
-                const C *X = wait_load();
 #pragma unroll
-                for (int q = 0; q < E / RL; q++)
-#pragma unroll
-                    for (int r = 0; r < RL; r++) vx[q * RL + r] = X[(t + q * TC + r * (N / RL)) * 32 + w];
+        for (int i = 0; i < E; i++) A[i] = cmake<C>((T)0, (T)0);
+        for (int o = 0; o < nops; o++) {
+            const RecipOp op = ops[o];
+            if (op.fwd) {
+                // forward transform of the next loaded tile: v in the last pass's frequency order
+                rs::get<N, E, TC, rs::radix(N, E, 0)>(v, t, w, wait_load());
+                if ((failed = rs::passes<-1, N, E, TC, 0>(v, t, w, tw, Xa, Xb, xsel, bar))) break;
             }
-            T fH = 0, fP = 0;
-#pragma unroll
-            for (int i = 0; i < E; i++) {
-                const C X0 = cscale(v[i], invN);
-                const T g2 = gn[i] * gn[i];
-                C out = cmake<C>((T)0, (T)0);
-                if (g2 > (T)0) {
-                    if (a.terms & 8u) {
-                        const T f = (T)1 / g2;
-                        fH += cw * (X0.x * X0.x + X0.y * X0.y) * f;
-                        out = cscale(X0, (T)(4.0 * kPi) * f);
-                    }
-                    if (pp) {
-                        fP += cw * (X0.x * vx[i].x + X0.y * vx[i].y);
-                        out = cadd(out, vx[i]);
-                    }
-                } else if (pp) {
-                    out = vx[i];                      // G = 0: V_ext(0) only
-                }
-                v[i] = out;
-            }
-            eH += (double)fH;
-            eP += (double)fP;
-            if ((failed = inverse_store(CH_HPP, col))) break;
-        }
-        // ---- von Weizsaecker (psi form)
-        if (a.terms & 2u) {
-            if ((failed = forward())) break;
-            T fV = 0;
-#pragma unroll
-            for (int i = 0; i < E; i++) {
-                const C X0 = cscale(v[i], invN);
-                const T g2 = gn[i] * gn[i];
-                fV += cw * g2 * (X0.x * X0.x + X0.y * X0.y);
-                v[i] = cscale(X0, g2);
-            }
-            eV += (double)fV;
-            if ((failed = inverse_store(CH_VW, col))) break;
-        }
-        // ---- nonlocal: kernels at the knots (s2) and the reciprocal half of s3
-        if (a.terms & 4u) {
-            if ((failed = forward())) break;
-            C Rr[E];
-#pragma unroll
-            for (int i = 0; i < E; i++) Rr[i] = cscale(v[i], invN);
-            if (!lwt) {
-                const T hk = (T)(0.5 / a.scal[S_KF_WT]);
-                if ((failed = forward())) break;
+            const int kind = op.kind;
+            if (kind == OP_WT || kind == OP_EX || kind == OP_IP) {
+                // the kernel of this knot (WT: of the mean density's kF) at the thread's |G|
+                const T hk = kind == OP_WT ? (T)(0.5 / a.scal[S_KF_WT]) : (T)0.5 / sk[op.m];
                 T fN = 0;
 #pragma unroll
                 for (int i = 0; i < E; i++) {
-                    const T K = (T)kCWT * kval(gn[i] * hk);
-                    const C Sa = cscale(v[i], invN);
-                    fN += cw * K * (Sa.x * Rr[i].x + Sa.y * Rr[i].y);
-                    Rr[i] = cscale(Rr[i], K);
-                    v[i] = cscale(Sa, K);
+                    const T K = kernel_value<T, MGP>(a, gn[i] * hk);
+                    if (kind == OP_EX) {
+                        // E_NL += Omega sum_G w Re(conj(FFT[h_m rho^alpha]) K_m FFT[rho^beta])
+                        const C Sm = cscale(v[i], invN);
+                        fN += K * (Sm.x * Rr[i].x + Sm.y * Rr[i].y);
+                        A[i] = cadd(A[i], cscale(Sm, K));
+                        v[i] = cscale(Rr[i], K);
+                    } else if (kind == OP_IP) {
+                        v[i] = cscale(Rr[i], K);
+                    } else {
+                        // global-kF Wang-Teter: K rho^alpha hat to the knot channel, K rho^beta hat
+                        // (kept for the next operation) to the rho^beta channel
+                        const C Sa = cscale(v[i], invN);
+                        fN += K * (Sa.x * Rr[i].x + Sa.y * Rr[i].y);
+                        Rr[i] = cscale(Rr[i], K);
+                        v[i] = cscale(Sa, K);
+                    }
                 }
-                eN += (double)fN;
-                if ((failed = inverse_store(CH_KNOT0, col))) break;
+                eN += (double)(cw * fN);
+            } else if (kind == OP_HPP) {
+                // Hartree + local pseudopotential (V_ext(G) tile at the thread's frequencies)
+                C vx[E];
+                if (pp) {
+                    const C *X = wait_load();
+#pragma unroll
+                    for (int q = 0; q < E / RL; q++)
+#pragma unroll
+                        for (int r = 0; r < RL; r++) vx[q * RL + r] = X[(t + q * TC + r * (N / RL)) * 32 + w];
+                }
+                T fH = 0, fP = 0;
+#pragma unroll
+                for (int i = 0; i < E; i++) {
+                    const C X0 = cscale(v[i], invN);
+                    const T g2 = gn[i] * gn[i];
+                    C out = cmake<C>((T)0, (T)0);
+                    if (g2 > (T)0) {
+                        if (a.terms & 8u) {
+                            const T f = (T)1 / g2;
+                            fH += (X0.x * X0.x + X0.y * X0.y) * f;
+                            out = cscale(X0, (T)(4.0 * kPi) * f);
+                        }
+                        if (pp) {
+                            fP += X0.x * vx[i].x + X0.y * vx[i].y;
+                            out = cadd(out, vx[i]);
+                        }
+                    } else if (pp) {
+                        out = vx[i];                      // G = 0: V_ext(0) only
+                    }
+                    v[i] = out;
+                }
+                eH += (double)(cw * fH);
+                eP += (double)(cw * fP);
+            } else if (kind == OP_VW) {
+                // von Weizsaecker, psi form
+                T fV = 0;
+#pragma unroll
+                for (int i = 0; i < E; i++) {
+                    const C X0 = cscale(v[i], invN);
+                    const T g2 = gn[i] * gn[i];
+                    fV += g2 * (X0.x * X0.x + X0.y * X0.y);
+                    v[i] = cscale(X0, g2);
+                }
+                eV += (double)(cw * fV);
+            } else if (kind == OP_RB) {
+#pragma unroll
+                for (int i = 0; i < E; i++) Rr[i] = cscale(v[i], invN);
+            } else if (kind == OP_RR) {
 #pragma unroll
                 for (int i = 0; i < E; i++) v[i] = Rr[i];
-                if ((failed = inverse_store(CH_NL, col))) break;
-            } else {
-                C A[E];
+            } else if (kind == OP_A) {
 #pragma unroll
-                for (int i = 0; i < E; i++) A[i] = cmake<C>((T)0, (T)0);
-                for (int m = 0; m < a.M && !failed; m++) {
-                    const T hk = (T)0.5 / sk[m];
-                    T fN = 0;
-                    if (exact) {
-                        if ((failed = forward())) break;
+                for (int i = 0; i < E; i++) v[i] = A[i];
+            }
+            if (op.store >= 0) {
+                // inverse transform and store of the column into the channel
+                if ((failed = rs::passes<+1, N, E, TC, 0>(v, t, w, tw, Xa, Xb, xsel, bar))) break;
+                if (col < PL) {
+                    constexpr int R1 = rs::radix(N, E, 0);
+                    C *dst = a.chan + (size_t)op.store * a.NH + col;
 #pragma unroll
-                        for (int i = 0; i < E; i++) {
-                            const T K = (T)kCWT * kval(gn[i] * hk);
-                            // E_NL += Omega sum_G w Re(conj(FFT[h_m rho^alpha]) K_m FFT[rho^beta])
-                            const C Sm = cscale(v[i], invN);
-                            fN += cw * K * (Sm.x * Rr[i].x + Sm.y * Rr[i].y);
-                            A[i] = cadd(A[i], cscale(Sm, K));
-                            v[i] = cscale(Rr[i], K);
-                        }
-                    } else {
+                    for (int q = 0; q < E / R1; q++)
 #pragma unroll
-                        for (int i = 0; i < E; i++) v[i] = cscale(Rr[i], (T)kCWT * kval(gn[i] * hk));
-                    }
-                    eN += (double)fN;
-                    failed = inverse_store(CH_KNOT0 + m, col);
-                }
-                if (failed) break;
-                if (exact) {
-#pragma unroll
-                    for (int i = 0; i < E; i++) v[i] = A[i];
-                    if ((failed = inverse_store(CH_NL, col))) break;
+                        for (int r = 0; r < R1; r++) dst[(size_t)(t + q * TC + r * (N / R1)) * PL] = v[q * R1 + r];
                 }
             }
         }
     }
     if (failed) {
         // a bounded wait expired: let every copy issued so far land (they target this
-        // block's shared memory) with a longer bounded wait, flag it and leave
+        // block's shared memory) with a longer bounded wait, count it and leave
         if (threadIdx.x == 0) {
             bool drained = true;
             for (long long l = cons; l < issued; l++)

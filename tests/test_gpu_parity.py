@@ -329,7 +329,7 @@ def test_channel_batched_and_per_channel_rows_agree(kw):
     rho = torch.from_numpy(W.model_density(wl).astype(np.float32)).cuda()
     f = ofd.Functional(n_knots=16, **kw)
     out = []
-    for choice in (L.KERNELS_AUTO, L.KERNELS_PER_CHANNEL_ROWS):
+    for choice in (L.KERNELS_TILE_RECIP, L.KERNELS_PER_CHANNEL_ROWS):
         g = ofd.Grid(wl["cell"], wl["shape"])
         g.set_option(L.OPTION_KERNELS, choice)
         g.set_ions(wl["positions"], wl["species"], wl["Z"], wl["rc"])
@@ -352,10 +352,10 @@ def test_channel_batched_and_per_channel_rows_agree(kw):
 # n0 in {32, 64, 128} runs the register-resident, tensor-copy kernel: ragged last column tiles
 # (n1 (n2/2+1) not a multiple of 32), every NL mode, the MGP form; n1 (n2/2+1) odd keeps the
 # tile kernel (tensor maps need 16-byte row strides)
-RECIP_CASES = [((128, 18, 20), dict(n_knots=8)), ((64, 10, 14), dict(n_knots=8)), ((32, 6, 10), dict(n_knots=8)),
+RECIP_CASES = [((128, 18, 20), dict(n_knots=8)), ((64, 10, 12), dict(n_knots=8)), ((32, 6, 10), dict(n_knots=8)),
                ((128, 5, 8), dict(n_knots=8)), ((128, 18, 20), dict(n_knots=8, nl_potential=L.NLPOT_INTERP)),
-               ((64, 10, 14), dict(n_knots=5, kernel=L.KERNEL_WT_GLOBAL)), ((128, 18, 20), dict(n_knots=8, mgp_x=1.0)),
-               ((64, 10, 14), dict(n_knots=8, terms=L.TERMS_VALID))]
+               ((64, 10, 12), dict(n_knots=5, kernel=L.KERNEL_WT_GLOBAL)), ((128, 18, 20), dict(n_knots=8, mgp_x=1.0)),
+               ((64, 10, 12), dict(n_knots=8, terms=L.TERMS_VALID))]
 
 
 @pytest.mark.parametrize("shape,kw", RECIP_CASES)

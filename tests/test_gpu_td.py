@@ -126,44 +126,6 @@ def _start(og, rho0, floor):
     return rho0, otd.kick(og, np.sqrt(rho0), [0.05, 0.02, 0.0])
 
 
-def _evaluated_densities(og, psi0, func, Vg, dt, n):
-    """The densities at which a predictor-corrector run (one corrector pass) evaluates
-    v_eff: rho(0), then per step the predictor's and the corrector's |psi|^2."""
-    dens = [np.abs(psi0) ** 2]
-    psi, v = psi0, otd.effective_potential(og, dens[0], func, Vg)
-    for _ in range(n):
-        x, _ = otd.cn_solve(og, psi, v, dt)
-        dens.append(np.abs(x) ** 2)
-        vn = otd.effective_potential(og, dens[-1], func, Vg)
-        x, _ = otd.cn_solve(og, psi, 0.5 * (v + vn), dt)
-        dens.append(np.abs(x) ** 2)
-        v = otd.effective_potential(og, dens[-1], func, Vg)
-        psi = x
-    return dens
-
-
-def _near_knot_region(dens, n_knots, rtol=1e-5, reach=2):
-    """Points within `reach` grid steps (periodic) of a point whose kF lies within rtol of
-    an interior knot of any evaluated density: there the LWT potential's spline interval
-    (and with it the exact potential's slope term) is a floating-point decision that FP32
-    and FP64 may take differently, and the Crank-Nicolson steps carry the difference to
-    the neighbouring points.  (The end knots are kF of the minimum and maximum density;
-    whether a point is in the knot range is decided on the density, identically in both
-    precisions, so the floored vacuum, all at the first knot, needs no mask.)"""
-    near = np.zeros(dens[0].shape, bool)
-    for d in dens:
-        k = ofn.make_knots(d, n_knots)[1:-1]
-        kF = ofn.fermi_wavevector(d)
-        near |= np.min(np.abs(kF[..., None] / k - 1.0), axis=-1) <= rtol
-    out = near.copy()
-    for a in range(3):
-        grown = out.copy()
-        for s in range(1, reach + 1):
-            grown |= np.roll(out, s, axis=a) | np.roll(out, -s, axis=a)
-        out = grown
-    return out
-
-
 @pytest.fixture(scope="module")
 def oracle_runs():
     out = {}
@@ -172,11 +134,7 @@ def oracle_runs():
         rho0, psi0 = _start(og, rho_blob, floor)
         Vg = ofn.external_potential_G(og, pos, [0, 0], [2.0], [1.0]) if pp else None
         psi, dip = otd.propagate(og, psi0, rho0, OFunc(terms=oterms, n_knots=8), Vg, 0.05, 8, n_corrector=1)
-        region = None
-        if name == "lwt":
-            func = OFunc(terms=oterms, n_knots=8)
-            region = _near_knot_region(_evaluated_densities(og, psi0, func, Vg, 0.05, 8), 8)
-        out[name] = (rho0, psi0, psi, dip, region)
+        out[name] = (rho0, psi0, psi, dip)
     return og, cell, pos, out
 
 
@@ -185,24 +143,22 @@ def oracle_runs():
 def test_propagation_matches_the_oracle(oracle_runs, name, precision):
     og, cell, pos, out = oracle_runs
     _, terms, pp, _ = CASES[name]
-    rho0, psi0, opsi, odip, region = out[name]
+    rho0, psi0, opsi, odip = out[name]
     f = ofd.Functional(terms=terms, n_knots=8, precision=precision)
     ions = (pos, [0, 0], [2.0], [1.0]) if pp else None
-    psi, dip, rep, g = _run_gpu(cell, og.shape, psi0, rho0, f, 0.05, 8, ions=ions)
+    # FP32-mixed solves to a 1e-7 relative residual: the LWT trajectory amplifies the solves'
+    # residuals (at the default 1e-5 its psi moves 5e-4 of max|psi| from the oracle's; at 1e-7,
+    # 1e-6), so the bound below tests the evaluations and the propagator, not the stop rule
+    tol = 1e-7 if precision == L.FP32_MIXED else 0.0
+    psi, dip, rep, g = _run_gpu(cell, og.shape, psi0, rho0, f, 0.05, 8, ions=ions, tol=tol)
     scale = np.max(np.abs(opsi))
     if precision == L.FP64:
         assert np.max(np.abs(psi - opsi)) < 1e-9 * scale, name
         assert np.max(np.abs(dip - odip)) < 1e-10, name
         assert abs(np.sum(np.abs(psi) ** 2) * og.dV - 4.0) < 1e-10
     else:
-        # FP32-mixed: v_eff to ~1e-6 relative, solves to 1e-5.  The LWT potential is compared
-        # away from the near-knot region (points near a knot of any evaluated density, grown
-        # by two grid steps), as the evaluation tests mask near-knot points; the dipole, an
-        # integral over the whole cell, keeps the same bound
-        keep = np.ones(og.shape, bool) if region is None else ~region
-        assert keep.mean() > 0.75, keep.mean()
-        err = np.max(np.abs(psi - opsi)[keep])
-        assert err < 2e-4 * scale, (name, err / scale, np.max(np.abs(psi - opsi)) / scale, keep.mean())
+        # FP32-mixed: v_eff to ~1e-6 relative, solves to 1e-7
+        assert np.max(np.abs(psi - opsi)) < 2e-4 * scale, name
         assert np.max(np.abs(dip - odip)) < 2e-4 * np.max(np.abs(odip)), name
     assert dip[-1][0] > 0.0 and rep["steps"] == 8 and rep["evaluations"] == 1 + 8 * 2
 
