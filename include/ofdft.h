@@ -344,11 +344,19 @@ int ofdft_profile_read(ofdft_grid *g, int idx, const char **name, int *launches,
  *                             kernel still lets its copies land before it exits).
  *   OFDFT_OPTION_ALLOC_CAP    bytes of device memory the grid may allocate from now on (0: no cap);
  *                             an allocation past the cap fails with OFDFT_ERR_OOM.
+ *   OFDFT_OPTION_PICK_ROWS, _PICK_PENCIL, _PICK_RECIP
+ *                             index of the compiled configuration of that kernel role to use
+ *                             (the order of ofdft_tuning_report; -1, the default: the autotuner
+ *                             picks; an index past the list keeps the role's default).  A change
+ *                             drops the grid's workspaces like OFDFT_OPTION_KERNELS.
  * Errors: OFDFT_ERR_INVALID_ARG (NULL, unknown option or value). */
 #define OFDFT_OPTION_KERNELS      1
 #define OFDFT_OPTION_BATCH_GRAPH  2
 #define OFDFT_OPTION_WAIT_POLLS   3
 #define OFDFT_OPTION_ALLOC_CAP    4
+#define OFDFT_OPTION_PICK_ROWS    5
+#define OFDFT_OPTION_PICK_PENCIL  6
+#define OFDFT_OPTION_PICK_RECIP   7
 #define OFDFT_KERNELS_AUTO              0
 #define OFDFT_KERNELS_GENERIC           1
 #define OFDFT_KERNELS_PER_CHANNEL_ROWS  2

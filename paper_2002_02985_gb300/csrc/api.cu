@@ -151,6 +151,7 @@ struct ofdft_grid {
     std::string err;
     // ofdft_set_option
     int kernel_choice = OFDFT_KERNELS_AUTO;
+    int force_pick[3] = {-1, -1, -1};    // per tuned role: a fixed candidate (-1: the autotuner's pick)
     int batch_graph = 1;
     unsigned wait_polls = 1u << 22;
     size_t alloc_cap = 0, alloc_bytes = 0;
@@ -349,8 +350,9 @@ template <typename T> int choose_launch(ofdft_grid *g, Workspace<T> &w) {
             if (e != cudaSuccess) return fail(g, OFDFT_ERR_CUDA, "kernel attributes", e);
         }
         if (!w.cand[r].empty()) {
-            w.pick[r] = 0;
-            int rc = apply_cand<T>(g, w, r, w.cand[r][0]);
+            const int fp = g->force_pick[r];
+            w.pick[r] = (fp >= 0 && fp < (int)w.cand[r].size()) ? fp : 0;
+            int rc = apply_cand<T>(g, w, r, w.cand[r][w.pick[r]]);
             if (rc) return rc;
         }
     }
@@ -610,7 +612,7 @@ int enqueue_eval(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, d
 // extra ones change nothing but the time of this first call; none runs while the stream is
 // being captured (the timing is then left for a later call).
 struct TuneEntry {
-    int key[5];
+    int key[8];
     int pick[TUNE_NROLE];
     std::string report;
 };
@@ -623,11 +625,25 @@ std::vector<TuneEntry> &tune_cache() {
     return c;
 }
 
+// the configurations of every role with the one in use (marked *), for roles nothing timed
+template <typename T> std::string plan_report(const Workspace<T> &w) {
+    const char *role_name[TUNE_NROLE] = {"rows", "pencil", "recip"};
+    std::string rep;
+    for (int r = TUNE_NROLE - 1; r >= 0; r--) {
+        if (w.cand[r].empty()) continue;
+        rep += std::string(rep.empty() ? "" : "; ") + role_name[r] + ":";
+        for (int c = 0; c < (int)w.cand[r].size(); c++)
+            rep += std::string(" [") + w.cand[r][c].name + "]" + (c == w.pick[r] ? "*" : "");
+    }
+    return rep;
+}
+
 template <typename T> int autotune(ofdft_grid *g, Workspace<T> &w, const T *rho, const ofdft_functional *f) {
     bool any = false;
-    for (int r = 0; r < TUNE_NROLE; r++) any = any || w.cand[r].size() > 1;
+    for (int r = 0; r < TUNE_NROLE; r++) any = any || (w.cand[r].size() > 1 && g->force_pick[r] < 0);
     if (!any) {
         w.tuned = true;
+        w.tune_report = plan_report(w) + " (nothing timed)";
         return OFDFT_OK;
     }
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -636,7 +652,8 @@ template <typename T> int autotune(ofdft_grid *g, Workspace<T> &w, const T *rho,
         return OFDFT_OK;                                  // not now: timing is impossible in a capture
     }
     w.tuned = true;
-    const int key[5] = {(int)sizeof(T), g->n[0], g->n[1], g->n[2], w.nslots};
+    const int key[8] = {(int)sizeof(T), g->n[0], g->n[1], g->n[2], w.nslots, g->force_pick[0], g->force_pick[1],
+                        g->force_pick[2]};
     {
         std::lock_guard<std::mutex> lk(tune_mutex());
         for (const TuneEntry &e : tune_cache())
@@ -666,7 +683,7 @@ template <typename T> int autotune(ofdft_grid *g, Workspace<T> &w, const T *rho,
     const char *role_name[TUNE_NROLE] = {"rows", "pencil", "recip"};
     for (int oi = 0; oi < TUNE_NROLE && rc == OFDFT_OK; oi++) {
         const int r = order[oi];
-        if (w.cand[r].size() < 2) continue;
+        if (w.cand[r].size() < 2 || g->force_pick[r] >= 0) continue;
         int best = -1;
         float best_ms = 0.f;
         rep += std::string(rep.empty() ? "" : "; ") + role_name[r] + ":";
@@ -2189,6 +2206,22 @@ int ofdft_set_option(ofdft_grid *g, int option, long long value) {
             if (value < 0 || value > (1LL << 30)) return fail(g, OFDFT_ERR_INVALID_ARG, "wait polls out of range");
             g->wait_polls = (unsigned)value;
             return OFDFT_OK;
+        case OFDFT_OPTION_PICK_ROWS:
+        case OFDFT_OPTION_PICK_PENCIL:
+        case OFDFT_OPTION_PICK_RECIP: {
+            if (value < -1 || value > 255) return fail(g, OFDFT_ERR_INVALID_ARG, "candidate index out of range");
+            const int r = option == OFDFT_OPTION_PICK_ROWS ? TUNE_ROWS
+                        : option == OFDFT_OPTION_PICK_PENCIL ? TUNE_PENCIL : TUNE_AXIS0;
+            if (g->force_pick[r] != (int)value) {
+                cudaStreamSynchronize(g->stream);
+                free_ws(g->w32);
+                free_ws(g->w64);
+                g->vext_fresh32 = g->vext_fresh64 = false;
+                g->generation++;
+                g->force_pick[r] = (int)value;
+            }
+            return OFDFT_OK;
+        }
         case OFDFT_OPTION_ALLOC_CAP:
             if (value < 0) return fail(g, OFDFT_ERR_INVALID_ARG, "negative allocation cap");
             g->alloc_cap = (size_t)value;

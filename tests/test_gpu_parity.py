@@ -43,11 +43,13 @@ def small_case(shape, cell=None, natoms=3, seed=0, noise=0.1):
     return cell, pos, rho
 
 
-def run_both(cell, shape, pos, rho64, func_kw, precision, species=None, Z=(2.0,), rc=(0.9,)):
+def run_both(cell, shape, pos, rho64, func_kw, precision, species=None, Z=(2.0,), rc=(0.9,), options=()):
     species = np.zeros(len(pos), np.int32) if species is None else species
     dt = torch.float64 if precision == L.FP64 else torch.float32
     rho_in = rho64 if precision == L.FP64 else rho64.astype(np.float32)
     g = ofd.Grid(cell, shape)
+    for opt, val in options:
+        g.set_option(opt, val)
     g.set_ions(pos, species, Z, rc)
     f = ofd.Functional(precision=precision, **func_kw)
     E, V = g.energy_potential(torch.from_numpy(np.ascontiguousarray(rho_in)).to("cuda", dt), f)
@@ -356,6 +358,38 @@ RECIP_CASES = [((128, 18, 20), dict(n_knots=8)), ((64, 10, 12), dict(n_knots=8))
                ((128, 5, 8), dict(n_knots=8)), ((128, 18, 20), dict(n_knots=8, nl_potential=L.NLPOT_INTERP)),
                ((64, 10, 12), dict(n_knots=5, kernel=L.KERNEL_WT_GLOBAL)), ((128, 18, 20), dict(n_knots=8, mgp_x=1.0)),
                ((64, 10, 12), dict(n_knots=8, terms=L.TERMS_VALID))]
+
+
+def _bulk_case(shape):
+    cell = np.array([[0.25 * shape[0], 0.0, 0.0], [0.3, 0.45 * shape[1], 0.0], [-0.2, 0.1, 0.4 * shape[2]]])
+    vol = abs(np.linalg.det(cell))
+    a = vol / max(2, round(vol / 110.0))
+    counts = [max(1, round(np.linalg.norm(cell[i]) / a ** (1.0 / 3.0))) for i in range(3)]
+    pos = lattice_positions(cell, counts, sum(shape))
+    rho = W.renormalise(W.apply_noise(W.gaussian_density(cell, shape, pos, 3.0, 1.0), 0.05, 3), cell, 3.0 * len(pos))
+    return cell, pos, rho
+
+
+@pytest.mark.parametrize("pick", range(8))
+@pytest.mark.parametrize("shape", [(128, 18, 20), (64, 10, 12), (32, 6, 10)])
+def test_every_reciprocal_kernel_configuration_matches_oracle(shape, pick):
+    """Each compiled configuration of the reciprocal-space pass for the shape's n0 (the
+    autotuner's candidates, forced one at a time; indices past the list are skipped)."""
+    cell, pos, rho = _bulk_case(shape)
+    g = ofd.Grid(cell, shape)
+    g.set_ions(pos, np.zeros(len(pos), np.int32), (3.0,), (0.8,))
+    g.energy_potential(torch.from_numpy(rho.astype(np.float32)).cuda(), ofd.Functional(n_knots=8))
+    n_cand = g.tuning_report().split(";")[0].count("[")
+    if not g.tuning_report().startswith("recip") or pick >= n_cand:
+        pytest.skip("no such configuration")
+    for kw in (dict(n_knots=8), dict(n_knots=5, kernel=L.KERNEL_WT_GLOBAL), dict(n_knots=8, nl_potential=L.NLPOT_INTERP)):
+        E, V, Eo, Vo, og, g2 = run_both(cell, shape, pos, rho, kw, L.FP32_MIXED, Z=(3.0,), rc=(0.8,),
+                                        options=((L.OPTION_PICK_RECIP, pick),))
+        nat = len(pos)
+        for k in ("TF", "vW", "NL", "H", "PP", "total"):
+            assert abs(E[k] - Eo[k]) / nat <= 1e-6, (pick, kw, k, E[k], Eo[k])
+        m = knot_mask(rho.astype(np.float32).astype(np.float64), kw["n_knots"])
+        assert np.linalg.norm((V - Vo)[m]) / np.linalg.norm(Vo[m]) <= 1e-4, (pick, kw)
 
 
 @pytest.mark.parametrize("shape,kw", RECIP_CASES)
