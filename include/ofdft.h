@@ -344,6 +344,16 @@ int ofdft_profile_read(ofdft_grid *g, int idx, const char **name, int *launches,
  *                             kernel still lets its copies land before it exits).
  *   OFDFT_OPTION_ALLOC_CAP    bytes of device memory the grid may allocate from now on (0: no cap);
  *                             an allocation past the cap fails with OFDFT_ERR_OOM.
+ *   OFDFT_OPTION_EXACT_SUMS   1: in FP32-mixed evaluations and optimiser dot products every term of
+ *                             every energy sum (and every FP32 product of a dot product) is added
+ *                             in FP64; 0 (default): terms are summed in FP32 over short runs (at
+ *                             most 16 terms: a thread's grid points or tile elements of one
+ *                             channel, 8 products of a dot product), the runs in FP64, except the
+ *                             density sums of the first kernel, whose per-thread partials are
+ *                             added across each warp in FP32.  For tests that bound the error of
+ *                             that grouping: evaluations then run the runtime-size kernels (the
+ *                             same as OFDFT_KERNELS_GENERIC apart from the sums); slower.  A change
+ *                             drops the grid's workspaces like OFDFT_OPTION_KERNELS.
  *   OFDFT_OPTION_PICK_ROWS, _PICK_PENCIL, _PICK_RECIP
  *                             index of the compiled configuration of that kernel role to use
  *                             (the order of ofdft_tuning_report; -1, the default: the autotuner
@@ -357,6 +367,7 @@ int ofdft_profile_read(ofdft_grid *g, int idx, const char **name, int *launches,
 #define OFDFT_OPTION_PICK_ROWS    5
 #define OFDFT_OPTION_PICK_PENCIL  6
 #define OFDFT_OPTION_PICK_RECIP   7
+#define OFDFT_OPTION_EXACT_SUMS   8
 #define OFDFT_KERNELS_AUTO              0
 #define OFDFT_KERNELS_GENERIC           1
 #define OFDFT_KERNELS_PER_CHANNEL_ROWS  2

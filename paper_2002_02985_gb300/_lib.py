@@ -29,7 +29,7 @@ OPT_CG, OPT_TN, OPT_LBFGS = 0, 1, 2
 UPDATE_ROTATE, UPDATE_SCALE = 0, 1
 OBJECTIVE_ENERGY, OBJECTIVE_RESIDUAL = 0, 1
 OPTION_KERNELS, OPTION_BATCH_GRAPH, OPTION_WAIT_POLLS, OPTION_ALLOC_CAP = 1, 2, 3, 4
-OPTION_PICK_ROWS, OPTION_PICK_PENCIL, OPTION_PICK_RECIP = 5, 6, 7
+OPTION_PICK_ROWS, OPTION_PICK_PENCIL, OPTION_PICK_RECIP, OPTION_EXACT_SUMS = 5, 6, 7, 8
 KERNELS_AUTO, KERNELS_GENERIC, KERNELS_PER_CHANNEL_ROWS, KERNELS_TILE_RECIP = 0, 1, 2, 3
 OFDFT_ERR_OOM = -4
 OFDFT_ERR_NOT_CONVERGED = -6

@@ -152,6 +152,7 @@ struct ofdft_grid {
     // ofdft_set_option
     int kernel_choice = OFDFT_KERNELS_AUTO;
     int force_pick[3] = {-1, -1, -1};    // per tuned role: a fixed candidate (-1: the autotuner's pick)
+    int exact_sums = 0;                  // FP32-mixed: every energy term and dot product term in FP64
     int batch_graph = 1;
     unsigned wait_polls = 1u << 22;
     size_t alloc_cap = 0, alloc_bytes = 0;
@@ -278,8 +279,10 @@ template <typename T> int apply_cand(ofdft_grid *g, Workspace<T> &w, int role, c
 template <typename T> int choose_launch(ofdft_grid *g, Workspace<T> &w) {
     const size_t row_budget = 110 * 1024;
     const int cap = Cap<T>::value, tmax = kMaxThreads;
-    const bool generic_only = g->kernel_choice == OFDFT_KERNELS_GENERIC;
-    w.ks = generic_kernels<T>();
+    // exact sums run the runtime-size kernels in their FP64-summing forms (the specialised ones
+    // keep only the default grouping)
+    const bool generic_only = g->kernel_choice == OFDFT_KERNELS_GENERIC || g->exact_sums;
+    w.ks = generic_kernels<T>(g->exact_sums != 0);
     for (int r = 0; r < TUNE_NROLE; r++) {
         w.cand[r].clear();
         w.pick[r] = -1;
@@ -804,6 +807,7 @@ int enqueue_eval(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, d
     a.row2_G = w.row2_G;
     a.ax0_scr = w.ax0_scr;
     a.wait_polls = g->wait_polls;
+    a.exact_sums = g->exact_sums;
     // channel lists
     const bool hpp = f->terms & (OFDFT_TERM_HARTREE | OFDFT_TERM_PP);
     const bool vw = f->terms & OFDFT_TERM_VW;
@@ -1319,7 +1323,8 @@ template <typename T> struct Dev {
     cudaError_t err = cudaSuccess;
     double dot(const T *a, const T *b, const T *c = nullptr) {
         if (err != cudaSuccess) return std::nan("");
-        cudaError_t e = launch_dot<T>(a, b, c, g->N, w->part_misc, 1024, w->part_misc + 2048, g->stream);
+        cudaError_t e = launch_dot<T>(a, b, c, g->N, w->part_misc, 1024, w->part_misc + 2048, g->stream,
+                                      g->exact_sums != 0);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(g->h_pinned + 40, w->part_misc + 2048, sizeof(double), cudaMemcpyDeviceToHost,
                                 g->stream);
@@ -2222,6 +2227,16 @@ int ofdft_set_option(ofdft_grid *g, int option, long long value) {
             }
             return OFDFT_OK;
         }
+        case OFDFT_OPTION_EXACT_SUMS:
+            if ((value != 0) != (g->exact_sums != 0)) {
+                cudaStreamSynchronize(g->stream);
+                free_ws(g->w32);
+                free_ws(g->w64);
+                g->vext_fresh32 = g->vext_fresh64 = false;
+                g->generation++;
+                g->exact_sums = value != 0;
+            }
+            return OFDFT_OK;
         case OFDFT_OPTION_ALLOC_CAP:
             if (value < 0) return fail(g, OFDFT_ERR_INVALID_ARG, "negative allocation cap");
             g->alloc_cap = (size_t)value;

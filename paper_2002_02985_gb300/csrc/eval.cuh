@@ -80,6 +80,7 @@ template <typename T> struct EvalArgs {
     int row2_G;                          // channel-batched row kernels: channels per group (0: per-channel form)
     int ax0_scr;                         // the reciprocal-space kernel has a scratch tile (out-of-place transforms)
     unsigned wait_polls;                 // polls of a bounded wait for bulk copies before it gives up
+    int exact_sums;                      // FP32-mixed test option: every energy term added in FP64
     int nfwd, fwd_ch[kMaxChan];          // channels formed by row_fwd (slot ids)
     int ncol, col_ch[kMaxChan];          // channels transformed forward along n1
     int ncol_inv, col_inv_ch[kMaxChan];  // channels transformed back along n1
@@ -191,8 +192,8 @@ template <typename T> void kernel_candidates(int role, int n, std::vector<Kernel
 template <typename T> bool find_specialised(int role, int n, const void **k1, const void **k2, int *B, int *nt);
 // the persistent reciprocal-space kernels compiled for n0 = n (recip.cu)
 template <typename T> void recip_candidates(int n, std::vector<KernelCand> &out);
-// The generic (runtime-size) kernels.
-template <typename T> LaunchSet generic_kernels();
+// The generic (runtime-size) kernels (exact_sums: the forms that add every energy term in FP64).
+template <typename T> LaunchSet generic_kernels(bool exact_sums = false);
 // Let every kernel of the set use the device's full opt-in shared memory.
 cudaError_t prepare_kernels(const LaunchSet &ks);
 

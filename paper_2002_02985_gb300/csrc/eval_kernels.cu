@@ -32,14 +32,20 @@ template <typename T> bool find_specialised(int role, int n, const void **k1, co
     return false;
 }
 
-template <typename T> LaunchSet generic_kernels() {
+template <typename T> LaunchSet generic_kernels(bool exact_sums) {
     LaunchSet ks;
     ks.row_fwd = (const void *)row_fwd_kernel<T, RtPolicy<T, 2>>;
-    ks.row_inv = (const void *)row_inv_kernel<T, RtPolicy<T, 2>>;
     ks.pen_fwd = (const void *)pencil1_kernel<T, -1, RtPolicy<T, 1>>;
     ks.pen_inv = (const void *)pencil1_kernel<T, +1, RtPolicy<T, 1>>;
-    ks.axis0 = (const void *)axis0_kernel<T, RtPolicy<T, 0>, false>;
-    ks.axis0_mgp = (const void *)axis0_kernel<T, RtPolicy<T, 0>, true>;
+    if (exact_sums) {
+        ks.row_inv = (const void *)row_inv_kernel<T, RtPolicy<T, 2>, true>;
+        ks.axis0 = (const void *)axis0_kernel<T, RtPolicy<T, 0>, false, true>;
+        ks.axis0_mgp = (const void *)axis0_kernel<T, RtPolicy<T, 0>, true, true>;
+    } else {
+        ks.row_inv = (const void *)row_inv_kernel<T, RtPolicy<T, 2>>;
+        ks.axis0 = (const void *)axis0_kernel<T, RtPolicy<T, 0>, false>;
+        ks.axis0_mgp = (const void *)axis0_kernel<T, RtPolicy<T, 0>, true>;
+    }
     return ks;
 }
 
@@ -77,7 +83,8 @@ cudaError_t launch_eval(const EvalArgs<T> &a, const LaunchSet &ks, cudaStream_t 
         if (ph) ph->record(ph->ctx, id, phase, s);
     };
     mark(K_STATS, 0);
-    stats_kernel<T><<<a.nb_stats, 256, 0, s>>>(a);        // (its last block makes the knots)
+    if (a.exact_sums) stats_kernel<T, true><<<a.nb_stats, 256, 0, s>>>(a);   // (its last block makes the knots)
+    else stats_kernel<T><<<a.nb_stats, 256, 0, s>>>(a);
     mark(K_STATS, 1);
     if (a.nfwd > 0) {
         mark(K_ROW_FWD, 0);
@@ -208,7 +215,7 @@ template <typename T> cudaError_t launch_mgp_table(T *tab, int n, double y, cons
     template cudaError_t launch_mgp_table<T>(T *, int, double, const double *, cudaStream_t);               \
     template bool find_specialised<T>(int, int, const void **, const void **, int *, int *);                 \
     template void kernel_candidates<T>(int, int, std::vector<KernelCand> &);                                 \
-    template LaunchSet generic_kernels<T>();                                                                 \
+    template LaunchSet generic_kernels<T>(bool);                                                             \
     template cudaError_t launch_eval<T>(const EvalArgs<T> &, const LaunchSet &, cudaStream_t, const ProfHook *,   \
                                         const RecipMaps *);                                                  \
     template cudaError_t launch_forward_rows_cols<T>(const EvalArgs<T> &, const LaunchSet &, cudaStream_t); \

@@ -170,6 +170,21 @@ template <typename T> __device__ __forceinline__ T lda_xc(T rho, T &v) {
     return rho * (ex + ec);
 }
 
+// ======================================================================= energy partials
+// An FP32-mixed per-thread energy partial: terms summed in T over a short run (a tile's
+// elements of one thread, a few grid points) and folded into FP64 once (the default), or,
+// with the exact-sums test option, every term converted and added in FP64.  FP64 builds
+// add every term in FP64 either way.
+template <typename T, bool XS> struct Part {
+    T f = (T)0;
+    double d = 0.0;
+    __device__ __forceinline__ void add(T v) {
+        if constexpr (XS) d += (double)v;
+        else f += v;
+    }
+    __device__ __forceinline__ double value() const { return XS ? d : (double)f; }
+};
+
 // ======================================================================= helpers
 template <typename T> __device__ __forceinline__ int knot_interval(T kc, const T *knots, int M) {
     // largest j in [0, M-2] with knots[j] <= kc (binary search; kc already clamped)
@@ -260,7 +275,7 @@ __device__ __forceinline__ void knots_from_partials(const EvalArgs<T> &a, double
 }
 
 // ======================================================================= stats (s1 input)
-template <typename T>
+template <typename T, bool XS = false>
 __global__ void __launch_bounds__(256) stats_kernel(EvalArgs<T> a) {
     __shared__ double sd[3 * 32];
     __shared__ T st[32];
@@ -285,7 +300,8 @@ __global__ void __launch_bounds__(256) stats_kernel(EvalArgs<T> a) {
                 for (int q = 0; q < 4; q++) x[u][q] = (4 * gi + q < a.N) ? a.rho[4 * gi + q] : (T)0;
             }
         }
-        // FP32-mixed: the U groups are summed in FP32 too (one FP64 add per sum per iteration)
+        // FP32-mixed: the U groups are summed in FP32 too (one FP64 add per sum per iteration);
+        // with exact sums every point is added in FP64
         T r16 = 0, t16 = 0, x16 = 0;
 #pragma unroll
         for (int u = 0; u < U; u++) {
@@ -297,11 +313,19 @@ __global__ void __launch_bounds__(256) stats_kernel(EvalArgs<T> a) {
                     const T xv = x[u][q];
                     if (!(xv >= (T)0) || !(xv < (T)3.0e38)) bad = 1;      // NaN, Inf or negative
                     const T c = dcbrt(xv);
-                    r4 += xv;
-                    t4 += xv * c * c;                                      // rho^(5/3)
+                    T xe = 0;
                     if (xc) {
                         T vxc;
-                        x4 += lda_xc(xv > a.floor_ ? xv : a.floor_, vxc);  // rho eps_xc
+                        xe = lda_xc(xv > a.floor_ ? xv : a.floor_, vxc);   // rho eps_xc
+                    }
+                    if constexpr (sizeof(T) == 4 && XS) {
+                        s_rho += (double)xv;
+                        s_tf += (double)(xv * c * c);
+                        s_xc += (double)xe;
+                    } else {
+                        r4 += xv;
+                        t4 += xv * c * c;                                  // rho^(5/3)
+                        x4 += xe;
                     }
                     mn = xv < mn ? xv : mn;
                     mx = xv > mx ? xv : mx;
@@ -324,7 +348,7 @@ __global__ void __launch_bounds__(256) stats_kernel(EvalArgs<T> a) {
         }
     }
     double r[3] = {s_rho, s_tf, s_xc};
-    if constexpr (sizeof(T) == 4) block_sum_n_f32warp<3>(r, sd);
+    if constexpr (sizeof(T) == 4 && !XS) block_sum_n_f32warp<3>(r, sd);
     else block_sum_n<3>(r, sd);
     if (threadIdx.x == 0)
         for (int k = 0; k < 3; k++) a.part_stats[3 * blockIdx.x + k] = r[k];
@@ -512,7 +536,7 @@ __device__ __forceinline__ void pencil1_body(const EvalArgs<T> &a) {
 // of two rotating buffers while the current one is transformed.
 // Partials per block: [0] sum_G w |rho_hat|^2/G^2, [1] sum_G w G^2 |psi_hat|^2,
 // [2] sum_G w Re(conj(rho_hat) V_ext), [3] nonlocal energy in G space.
-template <typename T, class P, bool MGP>
+template <typename T, class P, bool MGP, bool XS = false>
 __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
     typedef typename Vec2<T>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -622,7 +646,7 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
         const int sl = next();
         C *S = fwd(slot(sl));
         set_slot(sl, S);
-        T fH = 0, fP = 0;          // per-thread partials in T, folded into FP64 once
+        Part<T, XS> fH, fP;     // per-thread partials, folded into FP64 once
         for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
             const int w = idx % TW, i = idx / TW;
             const long long col = c0 + w;
@@ -634,12 +658,12 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
                 const T wgt = cw[w];
                 if (a.terms & 8u) {
                     const T f = (T)1 / g2;
-                    fH += wgt * (X0.x * X0.x + X0.y * X0.y) * f;
+                    fH.add(wgt * (X0.x * X0.x + X0.y * X0.y) * f);
                     out = cscale(X0, (T)(4.0 * kPi) * f);
                 }
                 if (a.terms & 16u) {
                     const C v = a.vext[(size_t)i * PL + col];
-                    fP += wgt * (X0.x * v.x + X0.y * v.y);
+                    fP.add(wgt * (X0.x * v.x + X0.y * v.y));
                     out = cadd(out, v);
                 }
             } else if (col < PL && (a.terms & 16u)) {
@@ -647,8 +671,8 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
             }
             S[idx] = out;
         }
-        eH += (double)fH;
-        eP += (double)fP;
+        eH += fH.value();
+        eP += fP.value();
         __syncthreads();
         S = inv(S);
         set_slot(sl, S);
@@ -659,16 +683,16 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
         const int sl = next();
         C *S = fwd(slot(sl));
         set_slot(sl, S);
-        T fV = 0;
+        Part<T, XS> fV;
         for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
             const int w = idx % TW;
             const C X0 = cscale(S[idx], invN);
             const T g = gn[idx];
             const T g2 = g * g;
-            fV += cw[w] * g2 * (X0.x * X0.x + X0.y * X0.y);
+            fV.add(cw[w] * g2 * (X0.x * X0.x + X0.y * X0.y));
             S[idx] = cscale(X0, g2);
         }
-        eV += (double)fV;
+        eV += fV.value();
         __syncthreads();
         S = inv(S);
         set_slot(sl, S);
@@ -689,17 +713,17 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
             const int sl = next();
             C *S = fwd(slot(sl));
             set_slot(sl, S);
-            T fN = 0;
+            Part<T, XS> fN;
             for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
                 const int w = idx % TW;
                 const T K = kernel_value<T, MGP>(a, gn[idx] * hk);
                 const C Sa = cscale(S[idx], invN);
                 const C Rb = Rr[idx];
-                fN += cw[w] * K * (Sa.x * Rb.x + Sa.y * Rb.y);
+                fN.add(cw[w] * K * (Sa.x * Rb.x + Sa.y * Rb.y));
                 Rr[idx] = cscale(Rb, K);
                 S[idx] = cscale(Sa, K);
             }
-            eN += (double)fN;
+            eN += fN.value();
             __syncthreads();
             Rr = inv(Rr);
             S = inv(S);
@@ -722,19 +746,19 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
                     sl = m & 1;
                     S = slot(sl);
                 }
-                T fN = 0;
+                Part<T, XS> fN;
                 for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
                     const T K = kernel_value<T, MGP>(a, gn[idx] * hk);
                     if (exact) {
                         // E_NL += Omega sum_G w Re(conj(FFT[h_m rho^alpha]) K_m FFT[rho^beta])
                         const C Sm = cscale(S[idx], invN);
                         const C Rb = Rr[idx];
-                        fN += cw[idx % TW] * K * (Sm.x * Rb.x + Sm.y * Rb.y);
+                        fN.add(cw[idx % TW] * K * (Sm.x * Rb.x + Sm.y * Rb.y));
                         A[idx] = cadd(A[idx], cscale(Sm, K));
                     }
                     S[idx] = cscale(Rr[idx], K);
                 }
-                eN += (double)fN;
+                eN += fN.value();
                 __syncthreads();
                 S = inv(S);
                 set_slot(sl, S);
@@ -755,7 +779,7 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
 }
 
 // ======================================================================= row inverse (C2R along n2) + s4 + V
-template <typename T, class P>
+template <typename T, class P, bool XS = false>
 __device__ __forceinline__ void row_inv_body(const EvalArgs<T> &a) {
     typedef typename Vec2<T>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -831,7 +855,7 @@ __device__ __forceinline__ void row_inv_body(const EvalArgs<T> &a) {
         }
     }
     __syncthreads();
-    T fNL = 0;
+    Part<T, XS> fNL;
     const T alpha_eff = interp ? (T)2 * a.alpha : a.alpha;
     // the pair of half-spectrum rows of every (pair, k) this thread packs; with a
     // compile-time policy the next channel's values are loaded into registers
@@ -907,7 +931,7 @@ __device__ __forceinline__ void row_inv_body(const EvalArgs<T> &a) {
                         const T h = (j == m) ? (T)1 - t : t;
                         if (interp) {
                             acc += y * alpha_eff * sa1[o + s] * h;
-                            if (row0 + 2 * b + s < R) fNL += sk3[o + s] * h * y;
+                            if (row0 + 2 * b + s < R) fNL.add(sk3[o + s] * h * y);
                         } else {
                             const T hp = (j == m) ? -idk : idk;
                             acc += y * sa1[o + s] * (alpha_eff * h + sk3[o + s] * hp);
@@ -931,7 +955,7 @@ __device__ __forceinline__ void row_inv_body(const EvalArgs<T> &a) {
             if (row < R) a.V[row * n + i2] = stg[rr * pitch + i2];
         }
     }
-    const double eNL = block_sum((double)fNL, sd);
+    const double eNL = block_sum(fNL.value(), sd);
     if (threadIdx.x == 0) a.part_row[blockIdx.x] = eNL;
 }
 
@@ -1179,7 +1203,7 @@ __device__ __forceinline__ void row_inv2_body(const EvalArgs<T> &a) {
             }
         }
     }
-    T fNL = 0;
+    Part<T, false> fNL;
     bool alive = true;
     for (int g0 = 0; g0 < ni; g0 += G) {
         const int gact = ni - g0 < G ? ni - g0 : G;
@@ -1260,12 +1284,12 @@ __device__ __forceinline__ void row_inv2_body(const EvalArgs<T> &a) {
                         if (ca >= 0 && ca < gact) {
                             const T y = ((const T *)(row + ca))[s];
                             acc[q][s] += y * wa[q][s];
-                            fNL += ea[q][s] * y;
+                            fNL.add(ea[q][s] * y);
                         }
                         if (ca + 1 >= 0 && ca + 1 < gact) {
                             const T y = ((const T *)(row + ca + 1))[s];
                             acc[q][s] += y * wb[q][s];
-                            fNL += eb[q][s] * y;
+                            fNL.add(eb[q][s] * y);
                         }
                     }
                 }
@@ -1284,7 +1308,7 @@ __device__ __forceinline__ void row_inv2_body(const EvalArgs<T> &a) {
         }
     }
     if (lwt && interp) {                     // the only mode with a real-space E_NL
-        const double eNL = block_sum((double)fNL, sd);
+        const double eNL = block_sum(fNL.value(), sd);
         if (threadIdx.x == 0) a.part_row[blockIdx.x] = eNL;
     }
 }
@@ -1345,13 +1369,14 @@ __global__ void __launch_bounds__(P::max_threads, P::min_blocks) pencil1_kernel(
 }
 // MGP: the knots' kernels of Eq. MGP from the correction table (a separate instantiation,
 // so that the Wang-Teter form carries no trace of it)
-template <typename T, class P, bool MGP = false>
+// XS: every energy term added in FP64 (the exact-sums test option; runtime-size kernels only)
+template <typename T, class P, bool MGP = false, bool XS = false>
 __global__ void __launch_bounds__(P::max_threads, P::min_blocks_ax0) axis0_kernel(EvalArgs<T> a) {
-    axis0_body<T, P, MGP>(a);
+    axis0_body<T, P, MGP, XS>(a);
 }
-template <typename T, class P>
+template <typename T, class P, bool XS = false>
 __global__ void __launch_bounds__(P::max_threads, P::min_blocks) row_inv_kernel(EvalArgs<T> a) {
-    row_inv_body<T, P>(a);
+    row_inv_body<T, P, XS>(a);
 }
 template <typename T, class Q>
 __global__ void __launch_bounds__(Q::NT_, Q::min_blocks) row_fwd2_kernel(EvalArgs<T> a) {

@@ -45,9 +45,10 @@ cudaError_t launch_axis0_fft(typename Vec2<T>::type *data, int n0, long long P, 
 
 // ---- optimiser vector kernels (all reductions FP64, fixed order) ----------
 // out[slot] = sum_i a_i b_i (c_i if c != null)
+// (exact: every FP32 product converted and summed in FP64, for tests of the default grouping)
 template <typename T>
 cudaError_t launch_dot(const T *a, const T *b, const T *c, long long N, double *partials, int nblk,
-                       double *out, cudaStream_t s);
+                       double *out, cudaStream_t s, bool exact = false);
 // y = alpha * x + beta * y (scalars read from device double pointers when given)
 template <typename T>
 cudaError_t launch_axpby(T *y, const T *x, double alpha, double beta, long long N, cudaStream_t s);

@@ -423,12 +423,15 @@ template cudaError_t launch_axis0_fft<double>(double2 *, int, long long, const F
 
 // ---------------------------------------------------------------- optimiser vectors
 template <typename T>
-__global__ void __launch_bounds__(256) dot_kernel(const T *a, const T *b, const T *c, long long N, double *part) {
+__global__ void __launch_bounds__(256) dot_kernel(const T *a, const T *b, const T *c, long long N, double *part,
+                                                  bool exact) {
     __shared__ double sd[32];
     double acc = 0.0;
     const long long stride = (long long)gridDim.x * blockDim.x;
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (sizeof(T) == 4) {
+    if (sizeof(T) == 4 && exact) {
+        for (; i < N; i += stride) acc += (double)(c ? a[i] * b[i] * c[i] : a[i] * b[i]);
+    } else if (sizeof(T) == 4) {
         // FP32 products in groups of 8 grid strides, each group added in FP64 (the FP64 pipe
         // of GB300 would otherwise bound this pass)
         while (i < N) {
@@ -459,8 +462,8 @@ __global__ void __launch_bounds__(256) sum_partials_kernel(const double *part, i
 
 template <typename T>
 cudaError_t launch_dot(const T *a, const T *b, const T *c, long long N, double *partials, int nblk, double *out,
-                       cudaStream_t s) {
-    dot_kernel<T><<<nblk, 256, 0, s>>>(a, b, c, N, partials);
+                       cudaStream_t s, bool exact) {
+    dot_kernel<T><<<nblk, 256, 0, s>>>(a, b, c, N, partials, exact);
     sum_partials_kernel<<<1, 256, 0, s>>>(partials, nblk, out);
     return cudaGetLastError();
 }
@@ -853,7 +856,7 @@ cudaError_t launch_dipole(const T *re, const T *im, const T *rho0, int n0, int n
                                        double, long long, cudaStream_t);                                     \
     template cudaError_t launch_add_scalar<T>(T *, const double *, long long, cudaStream_t);                  \
     template cudaError_t launch_dot<T>(const T *, const T *, const T *, long long, double *, int, double *,    \
-                                       cudaStream_t);                                                        \
+                                       cudaStream_t, bool);                                                  \
     template cudaError_t launch_axpby<T>(T *, const T *, double, double, long long, cudaStream_t);           \
     template cudaError_t launch_rotate<T>(T *, T *, const T *, const T *, double, double, long long,         \
                                           cudaStream_t);                                                     \

@@ -328,14 +328,14 @@ __global__ void __launch_bounds__(32 * (N / E), 1)
             if (kind == OP_WT || kind == OP_EX || kind == OP_IP) {
                 // the kernel of this knot (WT: of the mean density's kF) at the thread's |G|
                 const T hk = kind == OP_WT ? (T)(0.5 / a.scal[S_KF_WT]) : (T)0.5 / sk[op.m];
-                T fN = 0;
+                Part<T, false> fN;
 #pragma unroll
                 for (int i = 0; i < E; i++) {
                     const T K = kernel_value<T, MGP>(a, gn[i] * hk);
                     if (kind == OP_EX) {
                         // E_NL += Omega sum_G w Re(conj(FFT[h_m rho^alpha]) K_m FFT[rho^beta])
                         const C Sm = cscale(v[i], invN);
-                        fN += K * (Sm.x * Rr[i].x + Sm.y * Rr[i].y);
+                        fN.add(cw * K * (Sm.x * Rr[i].x + Sm.y * Rr[i].y));
                         A[i] = cadd(A[i], cscale(Sm, K));
                         v[i] = cscale(Rr[i], K);
                     } else if (kind == OP_IP) {
@@ -344,12 +344,12 @@ __global__ void __launch_bounds__(32 * (N / E), 1)
                         // global-kF Wang-Teter: K rho^alpha hat to the knot channel, K rho^beta hat
                         // (kept for the next operation) to the rho^beta channel
                         const C Sa = cscale(v[i], invN);
-                        fN += K * (Sa.x * Rr[i].x + Sa.y * Rr[i].y);
+                        fN.add(cw * K * (Sa.x * Rr[i].x + Sa.y * Rr[i].y));
                         Rr[i] = cscale(Rr[i], K);
                         v[i] = cscale(Sa, K);
                     }
                 }
-                eN += (double)(cw * fN);
+                eN += fN.value();
             } else if (kind == OP_HPP) {
                 // Hartree + local pseudopotential (V_ext(G) tile at the thread's frequencies)
                 C vx[E];
@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(32 * (N / E), 1)
 #pragma unroll
                         for (int r = 0; r < RL; r++) vx[q * RL + r] = X[(t + q * TC + r * (N / RL)) * 32 + w];
                 }
-                T fH = 0, fP = 0;
+                Part<T, false> fH, fP;
 #pragma unroll
                 for (int i = 0; i < E; i++) {
                     const C X0 = cscale(v[i], invN);
@@ -369,11 +369,11 @@ __global__ void __launch_bounds__(32 * (N / E), 1)
                     if (g2 > (T)0) {
                         if (a.terms & 8u) {
                             const T f = (T)1 / g2;
-                            fH += (X0.x * X0.x + X0.y * X0.y) * f;
+                            fH.add(cw * (X0.x * X0.x + X0.y * X0.y) * f);
                             out = cscale(X0, (T)(4.0 * kPi) * f);
                         }
                         if (pp) {
-                            fP += X0.x * vx[i].x + X0.y * vx[i].y;
+                            fP.add(cw * (X0.x * vx[i].x + X0.y * vx[i].y));
                             out = cadd(out, vx[i]);
                         }
                     } else if (pp) {
@@ -381,19 +381,19 @@ __global__ void __launch_bounds__(32 * (N / E), 1)
                     }
                     v[i] = out;
                 }
-                eH += (double)(cw * fH);
-                eP += (double)(cw * fP);
+                eH += fH.value();
+                eP += fP.value();
             } else if (kind == OP_VW) {
                 // von Weizsaecker, psi form
-                T fV = 0;
+                Part<T, false> fV;
 #pragma unroll
                 for (int i = 0; i < E; i++) {
                     const C X0 = cscale(v[i], invN);
                     const T g2 = gn[i] * gn[i];
-                    fV += g2 * (X0.x * X0.x + X0.y * X0.y);
+                    fV.add(cw * g2 * (X0.x * X0.x + X0.y * X0.y));
                     v[i] = cscale(X0, g2);
                 }
-                eV += (double)(cw * fV);
+                eV += fV.value();
             } else if (kind == OP_RB) {
 #pragma unroll
                 for (int i = 0; i < E; i++) Rr[i] = cscale(v[i], invN);
