@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -79,6 +80,7 @@ template <typename T> struct Workspace {
     T *opt_ext = nullptr;             // TN / L-BFGS fields (opt_ext_fields * N), on demand
     T *td = nullptr;                  // TD-OFDFT fields (19 * N), on demand
     T *mgp_tab = nullptr;             // MGP correction table (kMgpTable points), on demand
+    C *rhohat = nullptr;              // normalised rho_hat kept by an evaluation for the forces
     double mgp_y = 0.0;               // the y it was built for (0: not built)
     int opt_ext_fields = 0;
     LaunchSet ks;                     // FFT-carrying kernels (size-specialised where compiled)
@@ -124,8 +126,9 @@ struct ofdft_grid {
     bool vext_fresh32 = false, vext_fresh64 = false;
     double2 *ph = nullptr;       // phase tables [n_ions][n0 + n1 + n2h]
     float2 *ph32 = nullptr;      // the same rounded to FP32 (FP32-mixed kernels)
-    float4 *gc = nullptr;        // per-G scratch of the FP32-mixed force kernel
+    float4 *gc = nullptr;        // per-species G tables of the FP32-mixed force kernel
     long long gc_len = 0;
+    bool gc_fresh = false;       // the tables match the current ions (species, Z, rc)
     // smooth PME (ofdft_set_ions_pme): order > 0 selects it for V_ext(G) and forces
     int pme_order = 0;
     double2 *pmeB = nullptr;               // conj b_a tables [n0 | n1 | n2h]
@@ -450,6 +453,7 @@ template <typename T> void free_ws(Workspace<T> &w) {
     cudaFree(w.opt_ext);
     cudaFree(w.td);
     cudaFree(w.mgp_tab);
+    cudaFree(w.rhohat);
     w = Workspace<T>();
 }
 
@@ -603,7 +607,8 @@ template <typename T> int ensure_mgp_table(ofdft_grid *g, const ofdft_functional
 }
 
 template <typename T>
-int enqueue_eval(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, double *E_dev_out);
+int enqueue_eval(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, double *E_dev_out,
+                 bool keep_rhohat = false);
 
 // ---------------------------------------------------------------- autotuner
 // Picks, per tuned role (the reciprocal-space pass, the n1 pencils, the rows), the fastest of
@@ -731,7 +736,7 @@ template <typename T> int autotune(ofdft_grid *g, Workspace<T> &w, const T *rho,
 
 // Fill the evaluation arguments and enqueue one evaluation.
 template <typename T>
-int enqueue_eval(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, double *E_dev_out) {
+int enqueue_eval(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, double *E_dev_out, bool keep_rhohat) {
     const bool nl = f->terms & OFDFT_TERM_NL;
     const bool lwt = nl && f->kernel == OFDFT_KERNEL_LWT;
     const int M = lwt ? f->n_knots : 0;
@@ -808,6 +813,13 @@ int enqueue_eval(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, d
     a.ax0_scr = w.ax0_scr;
     a.wait_polls = g->wait_polls;
     a.exact_sums = g->exact_sums;
+    // the normalised density spectrum for the forces, written by the reciprocal-space kernel
+    // (needs the Hartree/PP channel)
+    if (keep_rhohat && (f->terms & (OFDFT_TERM_HARTREE | OFDFT_TERM_PP))) {
+        typedef typename Vec2<T>::type C;
+        if (!w.rhohat) CK(gmalloc(g, &w.rhohat, (size_t)g->NH * sizeof(C)), "cudaMalloc density spectrum");
+        a.rhohat_out = w.rhohat;
+    }
     // channel lists
     const bool hpp = f->terms & (OFDFT_TERM_HARTREE | OFDFT_TERM_PP);
     const bool vw = f->terms & OFDFT_TERM_VW;
@@ -1030,14 +1042,19 @@ template <typename T> int ensure_force_buffers(ofdft_grid *g) {
         g->fpart_len = plen;
         g->generation++;
     }
-    if (g->pme_order == 0 && fast && g->gc_len < g->NH) {
+    if (g->pme_order == 0 && fast && g->gc_len < (long long)g->n_species * g->NH) {
         CK(prepare_force_kernels(), "force kernel attributes");
         cudaFree(g->gc);
         g->gc = nullptr;
         g->gc_len = 0;
-        CK(gmalloc(g, &g->gc, 2 * (size_t)g->NH * sizeof(float4)), "cudaMalloc force scratch");
-        g->gc_len = g->NH;
+        CK(gmalloc(g, &g->gc, 2 * (size_t)g->n_species * g->NH * sizeof(float4)), "cudaMalloc force tables");
+        g->gc_len = (long long)g->n_species * g->NH;
+        g->gc_fresh = false;
         g->generation++;
+    }
+    if (g->pme_order == 0 && fast && !g->gc_fresh) {
+        CK(launch_force_tables(ion_args(g), g->gc, g->stream), "force tables");
+        g->gc_fresh = true;
     }
     if (g->F_len < g->n_ions) {
         cudaFree(g->F_dev);
@@ -1056,23 +1073,27 @@ template <typename T> int ensure_force_buffers(ofdft_grid *g) {
     return OFDFT_OK;
 }
 
-// enqueue the forces into g->F_dev (no synchronisation)
-template <typename T> int forces_enqueue(ofdft_grid *g, const T *rho) {
+// enqueue the forces into g->F_dev (no synchronisation); rhohat: the normalised density spectrum
+// an evaluation kept (null: transform rho here)
+template <typename T> int forces_enqueue(ofdft_grid *g, const T *rho, const typename Vec2<T>::type *rhohat = nullptr) {
     typedef typename Vec2<T>::type C;
     int rc = ensure_ws<T>(g, 3);
     if (rc) return rc;
     if ((rc = ensure_force_buffers<T>(g))) return rc;
     Workspace<T> &w = ws<T>(g);
     if (g->pme_order > 0) return forces_pme<T>(g, w, rho, g->F_dev);
-    if ((rc = forward_plain<T>(g, w, rho))) return rc;          // normalised rho_hat in slot 0
+    if (!rhohat) {
+        if ((rc = forward_plain<T>(g, w, rho))) return rc;      // normalised rho_hat in slot 0
+        rhohat = w.chan;
+    }
     bool fast;
     int nchunk, nsp;
     force_layout<T>(g, fast, nchunk, nsp);
     IonArgs ia = ion_args(g);
     if (fast)
-        CK(launch_forces_fast(ia, (const float2 *)w.chan, g->ph32, g->gc, g->fpart, nchunk, g->stream), "forces kernel");
+        CK(launch_forces_fast(ia, (const float2 *)rhohat, g->ph32, g->gc, g->fpart, nchunk, g->stream), "forces kernel");
     else
-        CK(launch_forces<C>(ia, w.chan, g->fpart, nchunk, g->stream), "forces kernel");
+        CK(launch_forces<C>(ia, rhohat, g->fpart, nchunk, g->stream), "forces kernel");
     CK(launch_reduce_force_partials(g->fpart, nsp, g->n_ions, nchunk, g->F_dev, g->stream), "force reduction");
     return OFDFT_OK;
 }
@@ -1982,6 +2003,8 @@ int prepare_batch_grid(ofdft_grid *g, const ofdft_functional *f, bool forces, co
     if (forces && (rc = ensure_force_buffers<T>(g))) return rc;
     if ((rc = ensure_mgp_table<T>(g, f))) return rc;     // before any graph capture
     Workspace<T> &w = ws<T>(g);
+    if (forces && (f->terms & (OFDFT_TERM_HARTREE | OFDFT_TERM_PP)) && !w.rhohat)
+        CK(gmalloc(g, &w.rhohat, (size_t)g->NH * sizeof(typename Vec2<T>::type)), "cudaMalloc density spectrum");
     if (!w.tuned && g->kernel_choice == OFDFT_KERNELS_AUTO && (rc = autotune<T>(g, w, rho, f))) return rc;
     return OFDFT_OK;
 }
@@ -2002,13 +2025,16 @@ int enqueue_batch(int n, ofdft_grid *const *grids, const void *const *rho_dev, c
         const cudaStream_t saved = g->stream;
         g->stream = st[i % kBatchStreams];
         Workspace<T> &w = ws<T>(g);
-        rc = enqueue_eval<T>(g, (const T *)rho_dev[i], f, V_dev ? (T *)V_dev[i] : nullptr, nullptr);
+        const bool want_f = F_out && F_out[i];
+        rc = enqueue_eval<T>(g, (const T *)rho_dev[i], f, V_dev ? (T *)V_dev[i] : nullptr, nullptr, want_f);
         if (rc == OFDFT_OK) {
             cudaMemcpyAsync(g->h_pinned, w.energies, E_NUM * sizeof(double), cudaMemcpyDeviceToHost, g->stream);
             cudaMemcpyAsync(g->h_pinned + 8, w.scal, S_NSCAL * sizeof(double), cudaMemcpyDeviceToHost, g->stream);
         }
         if (rc == OFDFT_OK && F_out && F_out[i]) {
-            rc = forces_enqueue<T>(g, (const T *)rho_dev[i]);
+            // the evaluation kept rho_hat (when it has the Hartree/PP channel): no transform here
+            const bool kept = f->terms & (OFDFT_TERM_HARTREE | OFDFT_TERM_PP);
+            rc = forces_enqueue<T>(g, (const T *)rho_dev[i], kept ? w.rhohat : nullptr);
             if (rc == OFDFT_OK)
                 cudaMemcpyAsync(g->F_pinned, g->F_dev, (size_t)3 * g->n_ions * sizeof(double), cudaMemcpyDeviceToHost,
                                 g->stream);
@@ -2309,6 +2335,10 @@ int store_ions(ofdft_grid *g, const ofdft_ions *ions, const ofdft_species *sp) {
         CK(gmalloc(g, &g->d_rc, sp->n_species * sizeof(double)), "cudaMalloc rc");
     }
     g->n_ions = n;
+    // the force tables depend on the species' Z and rc only (not on positions)
+    if (g->n_species != sp->n_species || !std::equal(g->Z.begin(), g->Z.end(), sp->Z) ||
+        !std::equal(g->rc.begin(), g->rc.end(), sp->rc))
+        g->gc_fresh = false;
     g->n_species = sp->n_species;
     g->pos.assign(ions->pos, ions->pos + 3 * (size_t)n);
     g->species.assign(ions->species, ions->species + n);

@@ -81,6 +81,7 @@ template <typename T> struct EvalArgs {
     int ax0_scr;                         // the reciprocal-space kernel has a scratch tile (out-of-place transforms)
     unsigned wait_polls;                 // polls of a bounded wait for bulk copies before it gives up
     int exact_sums;                      // FP32-mixed test option: every energy term added in FP64
+    C *rhohat_out;                       // if set: the normalised rho_hat (Hartree/PP channel) for the forces
     int nfwd, fwd_ch[kMaxChan];          // channels formed by row_fwd (slot ids)
     int ncol, col_ch[kMaxChan];          // channels transformed forward along n1
     int ncol_inv, col_inv_ch[kMaxChan];  // channels transformed back along n1

@@ -653,6 +653,7 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
             const C X0 = cscale(S[idx], invN);
             const T g = gn[idx];
             const T g2 = g * g;
+            if (a.rhohat_out && col < PL) a.rhohat_out[(size_t)i * PL + col] = X0;
             C out = cmake<C>((T)0, (T)0);
             if (col < PL && g2 > (T)0) {
                 const T wgt = cw[w];

@@ -26,8 +26,10 @@ cudaError_t launch_vext(const IonArgs &a, double2 *vext64, float2 *vext32, cudaS
 cudaError_t launch_round_phases(const double2 *in, float2 *out, long long n, cudaStream_t s);
 // shared-memory limit of the FP32-mixed force kernel (call once per device, outside stream capture)
 cudaError_t prepare_force_kernels();
-// FP32-mixed forces: gc scratch of 2 NH float4; partials [n_species][n_ions][nchunk][3]
-cudaError_t launch_forces_fast(const IonArgs &a, const float2 *rhohat, const float2 *ph32, float4 *gc,
+// FP32-mixed forces: gc = the per-species tables of launch_force_tables ([n_species][2 NH] float4),
+// partials [n_species][n_ions][nchunk][3]
+cudaError_t launch_force_tables(const IonArgs &a, float4 *gc, cudaStream_t st);
+cudaError_t launch_forces_fast(const IonArgs &a, const float2 *rhohat, const float2 *ph32, const float4 *gc,
                                double *partials, int nchunk, cudaStream_t st);
 
 // forces from the normalised half spectrum rho_hat (FP64 or FP32 complex)

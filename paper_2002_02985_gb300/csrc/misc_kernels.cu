@@ -161,7 +161,11 @@ template cudaError_t launch_forces<double2>(const IonArgs &, const double2 *, do
 // and G itself in FP32.  Then block (chunk, ion group of 8): each thread walks its
 // G values, forms e^{-iG.R_I} from the FP32 phase tables and accumulates
 // G Im[c e^{-iG.R}] in FP32 over 16 consecutive G before adding to FP64.
-__global__ void __launch_bounds__(256) force_gprep_kernel(IonArgs a, const float2 *rh, float4 *gc, int s) {
+// The static part of the FP32-mixed force sum for species s, once per set of ions: per point of
+// the half spectrum, G (FP32) with the point's k0, and the weighted form factor w v_s(|G|)
+// (w = 1 on the k2 = 0 and n2/2 planes, else 2; FP64, rounded once) with k1 and k2 (the
+// phase-table indices, so that the force kernel does no division per point).
+__global__ void __launch_bounds__(256) force_table_kernel(IonArgs a, float4 *gc, int s) {
     const long long NH = (long long)a.n0 * a.n1 * a.n2h;
     const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= NH) return;
@@ -169,82 +173,117 @@ __global__ void __launch_bounds__(256) force_gprep_kernel(IonArgs a, const float
     int k0, k1, k2;
     gvec_of(a, e, gx, gy, gz, k0, k1, k2);
     const double q2 = gx * gx + gy * gy + gz * gz;
-    float cr = 0.f, ci = 0.f;
+    float f = 0.f;
     if (q2 > 0.0) {
         const double w = (k2 == 0 || (a.n2 % 2 == 0 && 2 * k2 == a.n2)) ? 1.0 : 2.0;
-        const double f = -w * pp_form(q2, a.Z[s], a.rc[s]);
-        cr = (float)(f * rh[e].x);
-        ci = (float)(-f * rh[e].y);          // c = f conj(rho_hat)
+        f = (float)(-w * pp_form(q2, a.Z[s], a.rc[s]));
     }
-    gc[2 * e] = make_float4((float)gx, (float)gy, (float)gz, 0.f);
-    gc[2 * e + 1] = make_float4(cr, ci, 0.f, 0.f);
+    gc[2 * e] = make_float4((float)gx, (float)gy, (float)gz, __int_as_float(k0));
+    gc[2 * e + 1] = make_float4(f, 0.f, __int_as_float(k1), __int_as_float(k2));
 }
 
-// STAGE: the block's 8 ions' phase tables are first copied into shared memory
-// ([8][n0 + n1 + n2h]), so the G loop reads them there instead of from L2.
+cudaError_t launch_force_tables(const IonArgs &a, float4 *gc, cudaStream_t st) {
+    const long long NH = (long long)a.n0 * a.n1 * a.n2h;
+    for (int s = 0; s < a.n_species; s++)
+        force_table_kernel<<<(unsigned)((NH + 255) / 256), 256, 0, st>>>(a, gc + (size_t)s * 2 * NH, s);
+    return cudaGetLastError();
+}
+
+// STAGE: the block's 8 ions' phase tables are first copied into shared memory, by pairs of
+// ions: entry k of table a (a = 0, 1, 2 for the three axes) of pair p holds
+// (re_I, re_J, im_I, im_J), so that every product of the G loop is one packed two-wide FP32
+// instruction for two ions.  Without STAGE the tables are read from global memory.
 template <bool STAGE>
-__global__ void __launch_bounds__(256) forces_fast_kernel(IonArgs a, const float2 *ph32, const float4 *gc, int s,
-                                                           double *part, int nchunk) {
-    extern __shared__ float2 sph[];
+__global__ void __launch_bounds__(256) forces_fast_kernel(IonArgs a, const float2 *ph32, const float4 *gc,
+                                                          const float2 *rh, int s, double *part, int nchunk) {
+    extern __shared__ float4 sph4[];
     const int chunk = blockIdx.x, g0 = blockIdx.y * 8;
     const long long NH = (long long)a.n0 * a.n1 * a.n2h;
     const long long per = (NH + nchunk - 1) / nchunk;
     const long long e0 = chunk * per, e1 = (e0 + per < NH) ? e0 + per : NH;
     const float2 *P0 = ph32, *P1 = ph32 + (size_t)a.n_ions * a.n0, *P2 = P1 + (size_t)a.n_ions * a.n1;
     const int Lt = a.n0 + a.n1 + a.n2h;
+    // the phase of axis table entry k (k < n0: axis 0; then n1 entries of axis 1; then axis 2) of ion I
+    auto phase = [&](int I, int k) -> float2 {
+        if (I >= a.n_ions || a.species[I] != s) return make_float2(0.f, 0.f);
+        if (k < a.n0) return P0[(size_t)I * a.n0 + k];
+        if (k < a.n0 + a.n1) return P1[(size_t)I * a.n1 + (k - a.n0)];
+        return P2[(size_t)I * a.n2h + (k - a.n0 - a.n1)];
+    };
     if (STAGE) {
-        for (int t = threadIdx.x; t < 8 * Lt; t += blockDim.x) {
-            const int q = t / Lt, k = t - q * Lt, I = g0 + q;
-            float2 v = make_float2(0.f, 0.f);
-            if (I < a.n_ions) {
-                if (k < a.n0) v = P0[(size_t)I * a.n0 + k];
-                else if (k < a.n0 + a.n1) v = P1[(size_t)I * a.n1 + (k - a.n0)];
-                else v = P2[(size_t)I * a.n2h + (k - a.n0 - a.n1)];
-            }
-            sph[t] = v;
+        for (int t = threadIdx.x; t < 4 * Lt; t += blockDim.x) {
+            const int p = t / Lt, k = t - p * Lt;
+            const float2 u = phase(g0 + 2 * p, k), v = phase(g0 + 2 * p + 1, k);
+            sph4[t] = make_float4(u.x, v.x, u.y, v.y);
         }
         __syncthreads();
     }
     double F[8][3];
-    float f32[8][3];
+    float2 f32[4][3];
 #pragma unroll
     for (int q = 0; q < 8; q++)
 #pragma unroll
-        for (int d = 0; d < 3; d++) F[q][d] = 0.0, f32[q][d] = 0.f;
+        for (int d = 0; d < 3; d++) F[q][d] = 0.0;
+#pragma unroll
+    for (int p = 0; p < 4; p++)
+#pragma unroll
+        for (int d = 0; d < 3; d++) f32[p][d] = make_float2(0.f, 0.f);
+    // the block's ion pairs that hold an ion of this species
+    unsigned live = 0;
+    for (int p = 0; p < 4; p++)
+        for (int h = 0; h < 2; h++) {
+            const int I = g0 + 2 * p + h;
+            if (I < a.n_ions && a.species[I] == s) live |= 1u << p;
+        }
     int cnt = 0;
     for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-        const int k2 = (int)(e % a.n2h);
-        const long long r = e / a.n2h;
-        const int k1 = (int)(r % a.n1), k0 = (int)(r / a.n1);
         const float4 G = gc[2 * e], c4 = gc[2 * e + 1];
+        const int k0 = __float_as_int(G.w), k1 = __float_as_int(c4.z), k2 = __float_as_int(c4.w);
+        const float2 r = rh[e];
+        // c = w v_s(|G|) conj(rho_hat)
+        const float2 cr = make_float2(c4.x * r.x, c4.x * r.x), ci = make_float2(-c4.x * r.y, -c4.x * r.y);
+        const float2 gx = make_float2(G.x, G.x), gy = make_float2(G.y, G.y), gz = make_float2(G.z, G.z);
 #pragma unroll
-        for (int q = 0; q < 8; q++) {
-            const int I = g0 + q;
-            if (I >= a.n_ions || a.species[I] != s) continue;
-            float2 p0, p1, p2;
+        for (int p = 0; p < 4; p++) {
+            if (!((live >> p) & 1u)) continue;
+            float4 w0, w1, w2;
             if (STAGE) {
-                const float2 *row = sph + q * Lt;
-                p0 = row[k0];
-                p1 = row[a.n0 + k1];
-                p2 = row[a.n0 + a.n1 + k2];
+                const float4 *row = sph4 + p * Lt;
+                w0 = row[k0];
+                w1 = row[a.n0 + k1];
+                w2 = row[a.n0 + a.n1 + k2];
             } else {
-                p0 = P0[(size_t)I * a.n0 + k0];
-                p1 = P1[(size_t)I * a.n1 + k1];
-                p2 = P2[(size_t)I * a.n2h + k2];
+                auto pair = [&](int k) {
+                    const float2 u = phase(g0 + 2 * p, k), v = phase(g0 + 2 * p + 1, k);
+                    return make_float4(u.x, v.x, u.y, v.y);
+                };
+                w0 = pair(k0);
+                w1 = pair(a.n0 + k1);
+                w2 = pair(a.n0 + a.n1 + k2);
             }
-            const float rx = p0.x * p1.x - p0.y * p1.y, ry = p0.x * p1.y + p0.y * p1.x;
-            const float px = rx * p2.x - ry * p2.y, py = rx * p2.y + ry * p2.x;
-            const float im = c4.x * py + c4.y * px;            // Im(c p)
-            f32[q][0] += im * G.x;
-            f32[q][1] += im * G.y;
-            f32[q][2] += im * G.z;
+            // the two ions' phases e^{-iG.R} = P0 P1 P2, by components (re, im) of (I, J)
+            const float2 r0 = make_float2(w0.x, w0.y), i0 = make_float2(w0.z, w0.w);
+            const float2 r1 = make_float2(w1.x, w1.y), i1 = make_float2(w1.z, w1.w);
+            const float2 r2 = make_float2(w2.x, w2.y), i2 = make_float2(w2.z, w2.w);
+            const float2 rx = __ffma2_rn(r0, r1, __fmul2_rn(i0, make_float2(-i1.x, -i1.y)));
+            const float2 ry = __ffma2_rn(r0, i1, __fmul2_rn(i0, r1));
+            const float2 px = __ffma2_rn(rx, r2, __fmul2_rn(ry, make_float2(-i2.x, -i2.y)));
+            const float2 py = __ffma2_rn(rx, i2, __fmul2_rn(ry, r2));
+            const float2 im = __ffma2_rn(cr, py, __fmul2_rn(ci, px));          // Im(c p)
+            f32[p][0] = __ffma2_rn(im, gx, f32[p][0]);
+            f32[p][1] = __ffma2_rn(im, gy, f32[p][1]);
+            f32[p][2] = __ffma2_rn(im, gz, f32[p][2]);
         }
         if (++cnt == 16) {                               // FP32 over 16 G, then FP64
             cnt = 0;
 #pragma unroll
-            for (int q = 0; q < 8; q++)
+            for (int p = 0; p < 4; p++)
 #pragma unroll
-                for (int d = 0; d < 3; d++) F[q][d] += (double)f32[q][d], f32[q][d] = 0.f;
+                for (int d = 0; d < 3; d++) {
+                    F[2 * p][d] += (double)f32[p][d].x;
+                    F[2 * p + 1][d] += (double)f32[p][d].y;
+                    f32[p][d] = make_float2(0.f, 0.f);
+                }
         }
     }
     // block sums: warp sums in FP32 (32 values each), then the warps in FP64 -- 24 full FP64
@@ -255,7 +294,7 @@ __global__ void __launch_bounds__(256) forces_fast_kernel(IonArgs a, const float
     for (int q = 0; q < 8; q++)
 #pragma unroll
         for (int d = 0; d < 3; d++) {
-            float v = (float)F[q][d] + f32[q][d];
+            float v = (float)F[q][d] + ((q & 1) ? f32[q >> 1][d].y : f32[q >> 1][d].x);
             for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
             if (lane == 0) wsum[q * 3 + d][warp] = (double)v;
         }
@@ -272,21 +311,21 @@ cudaError_t prepare_force_kernels() {
     return cudaFuncSetAttribute(forces_fast_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
 }
 
-cudaError_t launch_forces_fast(const IonArgs &a, const float2 *rhohat, const float2 *ph32, float4 *gc,
+cudaError_t launch_forces_fast(const IonArgs &a, const float2 *rhohat, const float2 *ph32, const float4 *gc,
                                double *partials, int nchunk, cudaStream_t st) {
     const long long NH = (long long)a.n0 * a.n1 * a.n2h;
     cudaError_t e = cudaSuccess;
     for (int s = 0; s < a.n_species; s++) {
-        force_gprep_kernel<<<(unsigned)((NH + 255) / 256), 256, 0, st>>>(a, rhohat, gc, s);
+        const float4 *gcs = gc + (size_t)s * 2 * NH;
         // ions of other species write nothing for this species: their partials come from
         // their own species' pass (the kernel skips them)
         dim3 g(nchunk, (a.n_ions + 7) / 8);
-        const size_t smem = (size_t)8 * (a.n0 + a.n1 + a.n2h) * sizeof(float2);
+        const size_t smem = (size_t)4 * (a.n0 + a.n1 + a.n2h) * sizeof(float4);
         double *ps = partials + (size_t)s * a.n_ions * nchunk * 3;
         if (smem <= 96 * 1024) {          // (prepare_force_kernels raised the kernel's limit to 96 KB)
-            forces_fast_kernel<true><<<g, 256, smem, st>>>(a, ph32, gc, s, ps, nchunk);
+            forces_fast_kernel<true><<<g, 256, smem, st>>>(a, ph32, gcs, rhohat, s, ps, nchunk);
         } else {
-            forces_fast_kernel<false><<<g, 256, 0, st>>>(a, ph32, gc, s, ps, nchunk);
+            forces_fast_kernel<false><<<g, 256, 0, st>>>(a, ph32, gcs, rhohat, s, ps, nchunk);
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

@@ -351,6 +351,14 @@ __global__ void __launch_bounds__(32 * (N / E), 1)
                 }
                 eN += fN.value();
             } else if (kind == OP_HPP) {
+                if (a.rhohat_out && col < PL) {
+                    // the normalised density spectrum for the forces
+#pragma unroll
+                    for (int q = 0; q < E / RL; q++)
+#pragma unroll
+                        for (int r = 0; r < RL; r++)
+                            a.rhohat_out[(size_t)(t + q * TC + r * (N / RL)) * PL + col] = cscale(v[q * RL + r], invN);
+                }
                 // Hartree + local pseudopotential (V_ext(G) tile at the thread's frequencies)
                 C vx[E];
                 if (pp) {

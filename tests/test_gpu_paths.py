@@ -113,7 +113,8 @@ def test_autograd_matches_finite_differences():
 @pytest.mark.parametrize("graph", [1, 0])
 def test_batched_equals_single_evaluations(graph):
     """Batched snapshots (fork/join over internal streams; captured into a CUDA graph
-    and replayed when graph = 1) give bit-identical results to single calls."""
+    and replayed when graph = 1) give bit-identical energies and potentials to single
+    calls, and the same forces to FP32 rounding."""
     grids, rhos, singles = [], [], []
     f = ofd.Functional(n_knots=16)
     for s in range(4):
@@ -137,4 +138,6 @@ def test_batched_equals_single_evaluations(graph):
         for i, (Es, Vsg, Fsg) in enumerate(singles):
             assert np.array_equal(E[i], np.array([Es[k] for k in ofd.ENERGY_KEYS]))
             assert torch.equal(Vs[i], Vsg)
-            assert np.array_equal(Fs[i], Fsg)
+            # batched forces take rho_hat from the evaluation's own transform (the single call
+            # transforms rho itself): the same FP32-mixed quantity up to FP32 rounding
+            assert np.max(np.abs(Fs[i] - Fsg)) <= 1e-5 * max(1.0, np.max(np.abs(Fsg))), i
