@@ -102,7 +102,7 @@ template <typename T> struct Workspace {
     std::string tune_report;
     RecipMaps maps;
     const void *maps_chan = nullptr, *maps_vext = nullptr;
-    int maps_nslots = 0;
+    int maps_nslots = 0, maps_tw = 0;
 };
 
 }  // namespace
@@ -222,13 +222,13 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_encoder() {
 }
 
 // 3-D tensor map over nch half spectra of T words: [channel][k0][c], c < PL complex values,
-// boxes of 32 complex x box_rows rows x 1 channel
+// boxes of box_cols complex x box_rows rows x 1 channel
 template <typename T>
-bool encode_spectra_map(CUtensorMap *m, const void *base, long long PL, int n0, int nch, int box_rows) {
+bool encode_spectra_map(CUtensorMap *m, const void *base, long long PL, int n0, int nch, int box_rows, int box_cols) {
     const int wpc = 2;                                   // T words per complex value
     const cuuint64_t dims[3] = {(cuuint64_t)(PL * wpc), (cuuint64_t)n0, (cuuint64_t)nch};
     const cuuint64_t strides[2] = {(cuuint64_t)(PL * wpc * sizeof(T)), (cuuint64_t)(PL * n0 * wpc * sizeof(T))};
-    const cuuint32_t box[3] = {(cuuint32_t)(32 * wpc), (cuuint32_t)box_rows, 1};
+    const cuuint32_t box[3] = {(cuuint32_t)(box_cols * wpc), (cuuint32_t)box_rows, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     const CUresult r = tensor_encoder()(m, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
                                         3, const_cast<void *>(base), dims, strides, box, estr,
@@ -265,7 +265,7 @@ template <typename T> int apply_cand(ofdft_grid *g, Workspace<T> &w, int role, c
         const long long P = (long long)g->n[1] * g->n2h;
         if (c.recip.k) {
             w.ks.recip = c.recip;
-            w.recip_grid = (int)std::min((P + 31) / 32, (long long)c.recip.per_sm * g->nsm);
+            w.recip_grid = (int)std::min((P + c.recip.tw - 1) / c.recip.tw, (long long)c.recip.per_sm * g->nsm);
         } else {
             w.ks.recip = RecipLaunch();
             w.ks.axis0 = c.k1;
@@ -343,7 +343,8 @@ template <typename T> int choose_launch(ofdft_grid *g, Workspace<T> &w) {
     w.nb_ax0 = w.tile_nb_ax0;
     int min_brow = w.Brow;
     for (const KernelCand &k : w.cand[TUNE_AXIS0])
-        w.nb_ax0 = std::max(w.nb_ax0, k.recip.k ? (int)std::min((P + 31) / 32, (long long)k.recip.per_sm * g->nsm)
+        w.nb_ax0 = std::max(w.nb_ax0, k.recip.k ? (int)std::min((P + k.recip.tw - 1) / k.recip.tw,
+                                                                (long long)k.recip.per_sm * g->nsm)
                                                  : (int)((P + k.B - 1) / k.B));
     for (const KernelCand &k : w.cand[TUNE_ROWS]) min_brow = std::min(min_brow, k.batched ? 1 : k.B);
     for (int r = 0; r < TUNE_NROLE; r++) {
@@ -863,16 +864,18 @@ int enqueue_eval(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, d
     CK(cudaMemsetAsync(w.scal + S_BAD, 0, 4 * sizeof(double), g->stream), "memset flags");
     if (a.frozen) CK(cudaMemcpyAsync(w.knots_d, f->knots, M * sizeof(double), cudaMemcpyHostToDevice, g->stream),
                      "upload knots");
-    if (w.ks.recip.k && (w.maps_chan != w.chan || w.maps_vext != w.vext || w.maps_nslots != w.nslots)) {
+    if (w.ks.recip.k && (w.maps_chan != w.chan || w.maps_vext != w.vext || w.maps_nslots != w.nslots ||
+                         w.maps_tw != w.ks.recip.tw)) {
         const long long PL = (long long)g->n[1] * g->n2h;
-        const int box_rows = g->n[0] > 256 ? 256 : g->n[0];
-        if (!encode_spectra_map<T>(&w.maps.chan, w.chan, PL, g->n[0], w.nslots, box_rows) ||
+        const int box_rows = g->n[0] > 256 ? 256 : g->n[0], tw = w.ks.recip.tw;
+        if (!encode_spectra_map<T>(&w.maps.chan, w.chan, PL, g->n[0], w.nslots, box_rows, tw) ||
             !encode_spectra_map<T>(&w.maps.vext, w.vext ? (const void *)w.vext : (const void *)w.chan, PL, g->n[0],
-                                   1, box_rows))
+                                   1, box_rows, tw))
             return fail(g, OFDFT_ERR_CUDA, "tensor map encoding");
         w.maps_chan = w.chan;
         w.maps_vext = w.vext;
         w.maps_nslots = w.nslots;
+        w.maps_tw = tw;
     }
     ProfHook hook{prof_record, g};
     CK(launch_eval<T>(a, w.ks, g->stream, g->prof_on ? &hook : nullptr, w.ks.recip.k ? &w.maps : nullptr),

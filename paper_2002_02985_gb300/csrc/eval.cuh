@@ -156,6 +156,7 @@ template <typename T> __host__ __device__ inline size_t rowi_smem(const EvalArgs
 struct RecipLaunch {
     const void *k = nullptr, *k_mgp = nullptr;
     int nt = 0, per_sm = 1;
+    int tw = 32;                 // columns per tile (the tensor copies' box width)
     size_t smem = 0;
 };
 

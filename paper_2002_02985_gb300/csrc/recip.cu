@@ -6,17 +6,19 @@
 namespace ofdft {
 
 namespace {
-template <typename T, int N, int E, int NSTAGE> void add_recip(std::vector<KernelCand> &out) {
-    typedef RecipShape<T, N, E, NSTAGE> S;
+// TW columns per tile, MINB blocks per SM
+template <typename T, int N, int E, int NSTAGE, int TW = 32, int MINB = 1> void add_recip(std::vector<KernelCand> &out) {
+    typedef RecipShape<T, N, E, NSTAGE, TW> S;
     KernelCand c;
-    c.recip.k = (const void *)recip_kernel<T, N, E, NSTAGE, false>;
-    c.recip.k_mgp = (const void *)recip_kernel<T, N, E, NSTAGE, true>;
+    c.recip.k = (const void *)recip_kernel<T, N, E, NSTAGE, false, TW, MINB>;
+    c.recip.k_mgp = (const void *)recip_kernel<T, N, E, NSTAGE, true, TW, MINB>;
     c.recip.nt = S::NT;
-    c.recip.per_sm = 1;
+    c.recip.per_sm = MINB;
+    c.recip.tw = TW;
     c.recip.smem = S::smem;
-    c.B = 32;
+    c.B = TW;
     c.nt = S::NT;
-    std::snprintf(c.name, sizeof(c.name), "recip E%d s%d x%d", E, NSTAGE, S::NT);
+    std::snprintf(c.name, sizeof(c.name), "recip E%d s%d w%d x%d b%d", E, NSTAGE, TW, S::NT, MINB);
     out.push_back(c);
 }
 }  // namespace
@@ -26,12 +28,14 @@ template <typename T, int N, int E, int NSTAGE> void add_recip(std::vector<Kerne
 template <> void recip_candidates<float>(int n, std::vector<KernelCand> &out) {
     switch (n) {
         case 128:
+            add_recip<float, 128, 8, 4, 16, 2>(out);
+            add_recip<float, 128, 16, 4, 16, 2>(out);
             add_recip<float, 128, 16, 4>(out);
             add_recip<float, 128, 8, 4>(out);
             break;
         case 64:
             add_recip<float, 64, 8, 6>(out);
-            add_recip<float, 64, 4, 6>(out);
+            add_recip<float, 64, 4, 4, 16, 2>(out);
             break;
         case 32: add_recip<float, 32, 4, 8>(out); break;
         default: break;

@@ -3,23 +3,23 @@
 // evaluation (Sec. 2.3 s2 and the reciprocal half of s3, with the Hartree, local
 // pseudopotential and von Weizsaecker products of Eq. efunc).
 //
-// Work unit: a tile of 32 consecutive columns c = (k1, k2) of the half spectrum
-// and all N values of k0.  One block per SM loops over the tiles t = blockIdx.x,
+// Work unit: a tile of TW (32 or 16) consecutive columns c = (k1, k2) of the half
+// spectrum and all N values of k0.  MINB blocks per SM loop over the tiles t = blockIdx.x,
 // blockIdx.x + gridDim.x, ...; a single thread keeps NSTAGE channel tiles in
 // flight with cp.async.bulk.tensor copies (3-D tensor map over [channel][k0][c],
 // one mbarrier per stage, bounded waits), across tile boundaries.
 //
-// Thread (w, t) = (lane, warp) owns column w of the tile and, through every pass
-// of the Stockham transform, the E = N / TC elements t + q TC + r N/R of that
-// column (TC = number of warps).  Each pass runs in registers; between passes
+// Thread (w, t) = (threadIdx.x mod TW, threadIdx.x / TW) owns column w of the tile
+// and, through every pass of the Stockham transform, the E = N / TC elements
+// t + q TC + r N/R of that column (TC = number of column groups).  Each pass runs in registers; between passes
 // the values go through a shared exchange tile (one barrier per exchange, two
 // exchange tiles used alternately).  The forward transform ends with frequency
 // k0 = t + q TC + r N/R_last in register q R_last + r, which is exactly the input
 // order of the inverse transform with the radices reversed, so the reciprocal
 // products are applied in registers and the inverse starts without an exchange.
-// A warp always touches one row of 32 consecutive columns: every shared-memory
-// access is a conflict-free 256-byte row, and every global store a coalesced
-// 256-byte segment.  rho^beta hat, the term-2 accumulator and |G| stay in
+// A warp always touches one row of 32 consecutive columns (TW = 32) or two rows of
+// 16 (TW = 16): every shared-memory access is conflict-free, and every global
+// store whole 128- or 256-byte segments.  rho^beta hat, the term-2 accumulator and |G| stay in
 // registers for the whole tile.
 #pragma once
 
@@ -90,30 +90,30 @@ __device__ __forceinline__ void pass(C (&v)[E], int t, const C *tw) {
     }
 }
 
-// the outputs of a pass (radix R, NS) into the exchange tile X[e][32]
-template <int N, int E, int TC, int R, int NS, typename C>
+// the outputs of a pass (radix R, NS) into the exchange tile X[e][TW]
+template <int N, int E, int TC, int TW, int R, int NS, typename C>
 __device__ __forceinline__ void put(const C (&v)[E], int t, int w, C *X) {
 #pragma unroll
     for (int q = 0; q < E / R; q++) {
         const int j = t + q * TC, k = j % NS, base = (j / NS) * NS * R + k;
 #pragma unroll
-        for (int r = 0; r < R; r++) X[(base + r * NS) * 32 + w] = v[q * R + r];
+        for (int r = 0; r < R; r++) X[(base + r * NS) * TW + w] = v[q * R + r];
     }
 }
 
-// the inputs of a pass of radix R from a tile X[e][32]: element j + r N/R of butterfly j
-template <int N, int E, int TC, int R, typename C>
+// the inputs of a pass of radix R from a tile X[e][TW]: element j + r N/R of butterfly j
+template <int N, int E, int TC, int TW, int R, typename C>
 __device__ __forceinline__ void get(C (&v)[E], int t, int w, const C *X) {
 #pragma unroll
     for (int q = 0; q < E / R; q++)
 #pragma unroll
-        for (int r = 0; r < R; r++) v[q * R + r] = X[(t + q * TC + r * (N / R)) * 32 + w];
+        for (int r = 0; r < R; r++) v[q * R + r] = X[(t + q * TC + r * (N / R)) * TW + w];
 }
 
 // passes p .. P-1 of a transform on the registers, with an exchange (put, block barrier,
 // get) between consecutive passes; the exchange tiles alternate.  bar() returns true when
 // a bounded wait failed, which ends the transform early (true is returned).
-template <int DIR, int N, int E, int TC, int p, typename C, typename Bar>
+template <int DIR, int N, int E, int TC, int TW, int p, typename C, typename Bar>
 __device__ __forceinline__ bool passes(C (&v)[E], int t, int w, const C *tw, C *Xa, C *Xb, bool &xsel, Bar &bar) {
     constexpr int P = npass(N, E);
     if constexpr (p < P) {
@@ -123,11 +123,11 @@ __device__ __forceinline__ bool passes(C (&v)[E], int t, int w, const C *tw, C *
         if constexpr (p + 1 < P) {
             C *X = xsel ? Xb : Xa;
             xsel = !xsel;
-            put<N, E, TC, R, NS>(v, t, w, X);
+            put<N, E, TC, TW, R, NS>(v, t, w, X);
             if (bar()) return true;
-            get<N, E, TC, (DIR < 0 ? radix(N, E, p + 1) : iradix(N, E, p + 1))>(v, t, w, X);
+            get<N, E, TC, TW, (DIR < 0 ? radix(N, E, p + 1) : iradix(N, E, p + 1))>(v, t, w, X);
         }
-        return passes<DIR, N, E, TC, p + 1>(v, t, w, tw, Xa, Xb, xsel, bar);
+        return passes<DIR, N, E, TC, TW, p + 1>(v, t, w, tw, Xa, Xb, xsel, bar);
     } else {
         return false;
     }
@@ -151,9 +151,9 @@ struct RecipMaps {
     CUtensorMap vext;
 };
 
-template <typename T, int N, int E, int NSTAGE> struct RecipShape {
+template <typename T, int N, int E, int NSTAGE, int TW = 32> struct RecipShape {
     typedef typename Vec2<T>::type C;
-    static constexpr int TC = N / E, NT = 32 * TC, TILE = N * 32;
+    static constexpr int TC = N / E, NT = TW * TC, TILE = N * TW;
     static constexpr int BOXR = N > 256 ? 256 : N;    // rows per tensor copy (box limit 256)
     static constexpr size_t smem = (size_t)(NSTAGE + 2) * TILE * sizeof(C) + (size_t)N * sizeof(C) + 1024;
     static_assert(rs::npass(N, E) >= 2, "at least two passes");
@@ -169,11 +169,11 @@ struct RecipOp {
     short store, m;
 };
 
-template <typename T, int N, int E, int NSTAGE, bool MGP>
-__global__ void __launch_bounds__(32 * (N / E), 1)
+template <typename T, int N, int E, int NSTAGE, bool MGP, int TW = 32, int MINB = 1>
+__global__ void __launch_bounds__(TW * (N / E), MINB)
     recip_kernel(const EvalArgs<T> a, const __grid_constant__ RecipMaps maps) {
     typedef typename Vec2<T>::type C;
-    typedef RecipShape<T, N, E, NSTAGE> S;
+    typedef RecipShape<T, N, E, NSTAGE, TW> S;
     constexpr int TC = S::TC, NT = S::NT, TILE = S::TILE, P = rs::npass(N, E);
     constexpr int RL = rs::radix(N, E, P - 1);           // last forward radix
     constexpr int WPC = (int)(sizeof(C) / sizeof(T));    // T words per complex (2)
@@ -190,10 +190,12 @@ __global__ void __launch_bounds__(32 * (N / E), 1)
     __shared__ T sk[OFDFT_MAX_KNOTS];
     __shared__ int order[kMaxChan + 1];         // HPP, V_ext, vW, rho^beta, M knots: at most 4 + 64
     __shared__ RecipOp ops[kMaxChan + 2];
-    const int w = threadIdx.x & 31, t = threadIdx.x >> 5;
+    // thread (w, t): column w of the tile, element set t (TW = 32: a warp is one t; TW = 16:
+    // two t per warp, each half-warp one 128-byte row of every shared tile)
+    const int w = threadIdx.x % TW, t = threadIdx.x / TW;
     const int n2h = a.n2h;
     const long long PL = (long long)a.n1 * n2h;
-    const int ntile = (int)((PL + 31) / 32);
+    const int ntile = (int)((PL + TW - 1) / TW);
     const bool lwt = a.kernel == 0, exact = a.nlpot == 0;
     const bool hp = a.terms & (8u | 16u), pp = a.terms & 16u;
 
@@ -250,7 +252,7 @@ __global__ void __launch_bounds__(32 * (N / E), 1)
         bool fenced = false;
         while (issued < total && issued < cons + NSTAGE) {
             const int ti = (int)(issued / nload), i = (int)(issued - (long long)ti * nload);
-            const int c0 = (blockIdx.x + ti * gridDim.x) * 32;
+            const int c0 = (blockIdx.x + ti * gridDim.x) * TW;
             const int st = (int)(issued % NSTAGE);
             if (!fenced) {
                 fence_proxy_async_smem();           // the stage was last read through the generic proxy
@@ -260,7 +262,7 @@ __global__ void __launch_bounds__(32 * (N / E), 1)
             const int ch = order[i];
 #pragma unroll
             for (int rb = 0; rb < N / S::BOXR; rb++) {
-                C *dst = stage + st * TILE + rb * S::BOXR * 32;
+                C *dst = stage + st * TILE + rb * S::BOXR * TW;
                 if (ch >= 0) tma_load_3d(dst, &maps.chan, c0 * WPC, rb * S::BOXR, ch, &full[st]);
                 else tma_load_3d(dst, &maps.vext, c0 * WPC, rb * S::BOXR, 0, &full[st]);
             }
@@ -295,7 +297,7 @@ __global__ void __launch_bounds__(32 * (N / E), 1)
     C v[E], Rr[E], A[E];
     bool xsel = false;                         // exchange tile of the next exchange
     for (int ti = 0; ti < my_tiles && !failed; ti++) {
-        const long long col = (long long)(blockIdx.x + ti * gridDim.x) * 32 + w;
+        const long long col = (long long)(blockIdx.x + ti * gridDim.x) * TW + w;
         // this thread's column: its G components, half-spectrum weight, and |G| at its frequencies
         T cw, gn[E];
         {
@@ -321,8 +323,8 @@ __global__ void __launch_bounds__(32 * (N / E), 1)
             const RecipOp op = ops[o];
             if (op.fwd) {
                 // forward transform of the next loaded tile: v in the last pass's frequency order
-                rs::get<N, E, TC, rs::radix(N, E, 0)>(v, t, w, wait_load());
-                if ((failed = rs::passes<-1, N, E, TC, 0>(v, t, w, tw, Xa, Xb, xsel, bar))) break;
+                rs::get<N, E, TC, TW, rs::radix(N, E, 0)>(v, t, w, wait_load());
+                if ((failed = rs::passes<-1, N, E, TC, TW, 0>(v, t, w, tw, Xa, Xb, xsel, bar))) break;
             }
             const int kind = op.kind;
             if (kind == OP_WT || kind == OP_EX || kind == OP_IP) {
@@ -366,7 +368,7 @@ __global__ void __launch_bounds__(32 * (N / E), 1)
 #pragma unroll
                     for (int q = 0; q < E / RL; q++)
 #pragma unroll
-                        for (int r = 0; r < RL; r++) vx[q * RL + r] = X[(t + q * TC + r * (N / RL)) * 32 + w];
+                        for (int r = 0; r < RL; r++) vx[q * RL + r] = X[(t + q * TC + r * (N / RL)) * TW + w];
                 }
                 Part<T, false> fH, fP;
 #pragma unroll
@@ -414,7 +416,7 @@ __global__ void __launch_bounds__(32 * (N / E), 1)
             }
             if (op.store >= 0) {
                 // inverse transform and store of the column into the channel
-                if ((failed = rs::passes<+1, N, E, TC, 0>(v, t, w, tw, Xa, Xb, xsel, bar))) break;
+                if ((failed = rs::passes<+1, N, E, TC, TW, 0>(v, t, w, tw, Xa, Xb, xsel, bar))) break;
                 if (col < PL) {
                     constexpr int R1 = rs::radix(N, E, 0);
                     C *dst = a.chan + (size_t)op.store * a.NH + col;
