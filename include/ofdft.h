@@ -308,12 +308,25 @@ int ofdft_td_spectrum(const double *dmu, int n, double dt, double gamma, int n_o
                       double *sigma);
 
 /* Batched evaluation of n independent grids (snapshots), possibly of different
- * shapes: E_out HOST [n][OFDFT_N_ENERGIES]; V_dev[i] and F_out[i] may be NULL (F_out needs ions).
- * All grids must share one stream; the batch is enqueued back to back and
- * synchronised once. */
+ * shapes (Sec. 3.2: many independent OFDFT problems farmed out at once): E_out HOST
+ * [n][OFDFT_N_ENERGIES]; V_dev[i] and F_out[i] may be NULL (F_out needs ions).  All grids
+ * must share one stream, and one grid may appear only once.  Snapshots whose evaluations
+ * share a launch geometry (same shape, same compiled kernels) are grouped: each pass of the
+ * evaluation is ONE launch over up to 32 of them, every snapshot keeping the blocks and
+ * reduction order of its single evaluation (results bit-identical to single calls); groups
+ * run concurrently on internal streams forked from and joined into the grids' stream, and
+ * the whole batch is captured once into a CUDA graph and replayed while the arguments are
+ * unchanged (OFDFT_OPTION_BATCH_GRAPH, OFDFT_OPTION_BATCH_GROUPED of the first grid).
+ * Synchronises once.  Allocates, per distinct batch, the device copy of the evaluations'
+ * arguments (a few KB per snapshot, kept with the cached plan; at most 16 plans). */
 int ofdft_energy_potential_batched(int n, ofdft_grid *const *grids, const void *const *rho_dev,
                                    const ofdft_functional *f, double *E_out,
                                    void *const *V_dev, double *const *F_out);
+
+/* The plan of the last batched call whose first grid was g: its launch groups (shape and
+ * snapshot count each) and the kernel launches of the batch's evaluations; "" before any.
+ * The string stays valid until the next batched call with g first (or g's destruction). */
+const char *ofdft_batch_report(const ofdft_grid *g);
 
 /* Per-kernel device timing of the evaluation pipeline (tracing aid, results
  * unchanged).  While enabled, every kernel launch of an evaluation is bracketed
@@ -338,6 +351,9 @@ int ofdft_profile_read(ofdft_grid *g, int idx, const char **name, int *launches,
  *                             workspaces (synchronising its stream); they are rebuilt on next use.
  *   OFDFT_OPTION_BATCH_GRAPH  1 (default): a batched call whose first grid is g is captured once
  *                             into a CUDA graph and replayed; 0: enqueued directly on every call.
+ *   OFDFT_OPTION_BATCH_GROUPED 1 (default): a batched call whose first grid is g launches each
+ *                             pass once per group of snapshots with one launch geometry; 0: one
+ *                             launch per snapshot and pass (the same results).
  *   OFDFT_OPTION_WAIT_POLLS   polls of the bounded device-side wait for bulk (TMA) copies before
  *                             it gives up (default 4194304; 0 makes it give up at once, so that
  *                             the evaluation returns OFDFT_ERR_TIMEOUT: a test of that path; the
@@ -368,6 +384,7 @@ int ofdft_profile_read(ofdft_grid *g, int idx, const char **name, int *launches,
 #define OFDFT_OPTION_PICK_PENCIL  6
 #define OFDFT_OPTION_PICK_RECIP   7
 #define OFDFT_OPTION_EXACT_SUMS   8
+#define OFDFT_OPTION_BATCH_GROUPED 9
 #define OFDFT_KERNELS_AUTO              0
 #define OFDFT_KERNELS_GENERIC           1
 #define OFDFT_KERNELS_PER_CHANNEL_ROWS  2

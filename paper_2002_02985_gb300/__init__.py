@@ -125,6 +125,10 @@ class Grid:
         """The autotuner's timings and picks for this grid (ofdft_tuning_report)."""
         return self.lib.ofdft_tuning_report(self.h, precision).decode()
 
+    def batch_report(self) -> str:
+        """The plan of the last batched call with this grid first (ofdft_batch_report)."""
+        return self.lib.ofdft_batch_report(self.h).decode()
+
     def close(self):
         if getattr(self, "h", None):
             self.lib.ofdft_grid_destroy(self.h)

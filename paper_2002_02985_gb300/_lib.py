@@ -30,6 +30,7 @@ UPDATE_ROTATE, UPDATE_SCALE = 0, 1
 OBJECTIVE_ENERGY, OBJECTIVE_RESIDUAL = 0, 1
 OPTION_KERNELS, OPTION_BATCH_GRAPH, OPTION_WAIT_POLLS, OPTION_ALLOC_CAP = 1, 2, 3, 4
 OPTION_PICK_ROWS, OPTION_PICK_PENCIL, OPTION_PICK_RECIP, OPTION_EXACT_SUMS = 5, 6, 7, 8
+OPTION_BATCH_GROUPED = 9
 KERNELS_AUTO, KERNELS_GENERIC, KERNELS_PER_CHANNEL_ROWS, KERNELS_TILE_RECIP = 0, 1, 2, 3
 OFDFT_ERR_OOM = -4
 OFDFT_ERR_NOT_CONVERGED = -6
@@ -43,7 +44,7 @@ EXPORTS = (
     "ofdft_profile_enable", "ofdft_profile_reset", "ofdft_profile_read",
     "ofdft_tf_energy_potential_noalloc", "ofdft_set_ions_pme", "ofdft_ewald", "ofdft_interpolate",
     "ofdft_optimize_density_multistep", "ofdft_optimize_density_ex", "ofdft_td_kick", "ofdft_td_propagate",
-    "ofdft_td_spectrum", "ofdft_set_option", "ofdft_tuning_report", "ofdft_fp64_fma_rate",
+    "ofdft_td_spectrum", "ofdft_set_option", "ofdft_tuning_report", "ofdft_fp64_fma_rate", "ofdft_batch_report",
 )
 NOALLOC_MAX_POINTS = 8388608
 
@@ -124,13 +125,16 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.ofdft_fp64_fma_rate.argtypes = [P, ct.POINTER(D)]
     lib.ofdft_tuning_report.argtypes = [P, I]
     lib.ofdft_tuning_report.restype = ct.c_char_p
+    lib.ofdft_batch_report.argtypes = [P]
+    lib.ofdft_batch_report.restype = ct.c_char_p
     lib.ofdft_status_string.argtypes = [I]
     lib.ofdft_status_string.restype = ct.c_char_p
     lib.ofdft_last_error.argtypes = [P]
     lib.ofdft_last_error.restype = ct.c_char_p
     lib.ofdft_version.restype = ct.c_char_p
     for name in EXPORTS:
-        if name not in ("ofdft_status_string", "ofdft_last_error", "ofdft_version", "ofdft_tuning_report"):
+        if name not in ("ofdft_status_string", "ofdft_last_error", "ofdft_version", "ofdft_tuning_report",
+                        "ofdft_batch_report"):
             getattr(lib, name).restype = ct.c_int
     _lib = lib
     return lib

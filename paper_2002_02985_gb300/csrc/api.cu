@@ -157,6 +157,8 @@ struct ofdft_grid {
     int force_pick[3] = {-1, -1, -1};    // per tuned role: a fixed candidate (-1: the autotuner's pick)
     int exact_sums = 0;                  // FP32-mixed: every energy term and dot product term in FP64
     int batch_graph = 1;
+    int batch_grouped = 1;
+    std::string batch_report;            // the plan of the last batch whose first grid this was
     unsigned wait_polls = 1u << 22;
     size_t alloc_cap = 0, alloc_bytes = 0;
     // per-kernel CUDA-event timing (ofdft_profile_*)
@@ -246,12 +248,16 @@ template <typename T> int apply_cand(ofdft_grid *g, Workspace<T> &w, int role, c
     if (role == TUNE_ROWS) {
         w.ks.row_fwd = c.k1;
         w.ks.row_inv = c.k2;
+        w.ks.row_fwd_g = c.g1;
+        w.ks.row_inv_g = c.g2;
         w.Brow = c.batched ? 1 : c.B;
         w.row2_G = c.batched ? c.B : 0;
         w.thr_rowf = w.thr_rowi = c.nt;
     } else if (role == TUNE_PENCIL) {
         w.ks.pen_fwd = c.k1;
         w.ks.pen_inv = c.k2;
+        w.ks.pen_fwd_g = c.g1;
+        w.ks.pen_inv_g = c.g2;
         w.TW1 = c.B;
         w.thr_p1 = c.nt;
         // persistent pencil grid: every resident block slot of the device, once
@@ -270,6 +276,8 @@ template <typename T> int apply_cand(ofdft_grid *g, Workspace<T> &w, int role, c
             w.ks.recip = RecipLaunch();
             w.ks.axis0 = c.k1;
             w.ks.axis0_mgp = c.k2;
+            w.ks.axis0_g = c.g1;
+            w.ks.axis0_mgp_g = c.g2;
             w.TW0 = c.B;
             w.thr_ax0 = c.nt;
             w.ax0_scr = axis0_oop<T>(g->n[0]) ? 1 : 0;
@@ -352,6 +360,8 @@ template <typename T> int choose_launch(ofdft_grid *g, Workspace<T> &w) {
             LaunchSet one;
             one.row_fwd = k.k1;
             one.row_inv = k.k2;
+            one.row_fwd_g = k.g1;
+            one.row_inv_g = k.g2;
             one.recip = k.recip;
             cudaError_t e = prepare_kernels(one);
             if (e != cudaSuccess) return fail(g, OFDFT_ERR_CUDA, "kernel attributes", e);
@@ -364,7 +374,7 @@ template <typename T> int choose_launch(ofdft_grid *g, Workspace<T> &w) {
         }
     }
     if (w.pick[TUNE_PENCIL] < 0) {
-        int rc = apply_cand<T>(g, w, TUNE_PENCIL, KernelCand{w.ks.pen_fwd, w.ks.pen_inv, w.TW1, w.thr_p1});
+        int rc = apply_cand<T>(g, w, TUNE_PENCIL, KernelCand{w.ks.pen_fwd, w.ks.pen_inv, w.ks.pen_fwd_g, w.ks.pen_inv_g, w.TW1, w.thr_p1});
         if (rc) return rc;
     }
     // plain one-channel transforms: the per-channel row kernels where compiled
@@ -735,9 +745,11 @@ template <typename T> int autotune(ofdft_grid *g, Workspace<T> &w, const T *rho,
     return OFDFT_OK;
 }
 
-// Fill the evaluation arguments and enqueue one evaluation.
+// Fill the arguments of one evaluation (host work: the workspace, V_ext(G), the tuner's picks
+// and the tensor maps are made ready first; nothing is launched).
 template <typename T>
-int enqueue_eval(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, double *E_dev_out, bool keep_rhohat) {
+int eval_args(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, double *E_dev_out, bool keep_rhohat,
+              EvalArgs<T> &a) {
     const bool nl = f->terms & OFDFT_TERM_NL;
     const bool lwt = nl && f->kernel == OFDFT_KERNEL_LWT;
     const int M = lwt ? f->n_knots : 0;
@@ -752,7 +764,6 @@ int enqueue_eval(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, d
     if ((rc = ensure_mgp_table<T>(g, f))) return rc;
     if (!w.tuned && !w.tuning && g->kernel_choice == OFDFT_KERNELS_AUTO && (rc = autotune<T>(g, w, rho, f)))
         return rc;
-    EvalArgs<T> a;
     std::memset(&a, 0, sizeof(a));
     a.n0 = g->n[0];
     a.n1 = g->n[1];
@@ -859,11 +870,6 @@ int enqueue_eval(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, d
             }
         }
     }
-    // clears the bad-density flag, the WT kF (recomputed) and the device-wait counters
-    static_assert(S_TIMEOUT == S_BAD + 2 && S_FATAL == S_BAD + 3, "flag slots");
-    CK(cudaMemsetAsync(w.scal + S_BAD, 0, 4 * sizeof(double), g->stream), "memset flags");
-    if (a.frozen) CK(cudaMemcpyAsync(w.knots_d, f->knots, M * sizeof(double), cudaMemcpyHostToDevice, g->stream),
-                     "upload knots");
     if (w.ks.recip.k && (w.maps_chan != w.chan || w.maps_vext != w.vext || w.maps_nslots != w.nslots ||
                          w.maps_tw != w.ks.recip.tw)) {
         const long long PL = (long long)g->n[1] * g->n2h;
@@ -877,10 +883,36 @@ int enqueue_eval(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, d
         w.maps_nslots = w.nslots;
         w.maps_tw = tw;
     }
+    return OFDFT_OK;
+}
+
+// the knots a functional supplies (frozen knots) to the evaluation's FP64 knot buffer
+template <typename T> int upload_knots(ofdft_grid *g, const EvalArgs<T> &a, const ofdft_functional *f) {
+    if (a.frozen)
+        CK(cudaMemcpyAsync(a.knots_d, f->knots, a.M * sizeof(double), cudaMemcpyHostToDevice, g->stream),
+           "upload knots");
+    return OFDFT_OK;
+}
+
+// Enqueue one evaluation with filled arguments on g->stream.
+template <typename T> int eval_launch(ofdft_grid *g, const EvalArgs<T> &a, const ofdft_functional *f) {
+    Workspace<T> &w = ws<T>(g);
+    // clears the bad-density flag, the WT kF (recomputed) and the device-wait counters
+    static_assert(S_TIMEOUT == S_BAD + 2 && S_FATAL == S_BAD + 3, "flag slots");
+    CK(cudaMemsetAsync(a.scal + S_BAD, 0, 4 * sizeof(double), g->stream), "memset flags");
+    if (int rc = upload_knots<T>(g, a, f)) return rc;
     ProfHook hook{prof_record, g};
     CK(launch_eval<T>(a, w.ks, g->stream, g->prof_on ? &hook : nullptr, w.ks.recip.k ? &w.maps : nullptr),
        "evaluation kernels");
     return OFDFT_OK;
+}
+
+// Fill the evaluation arguments and enqueue one evaluation.
+template <typename T>
+int enqueue_eval(ofdft_grid *g, const T *rho, const ofdft_functional *f, T *V, double *E_dev_out, bool keep_rhohat) {
+    EvalArgs<T> a;
+    if (int rc = eval_args<T>(g, rho, f, V, E_dev_out, keep_rhohat, a)) return rc;
+    return eval_launch<T>(g, a, f);
 }
 
 // status of the device-wait counters of an evaluation (host copies of the S_TIMEOUT and
@@ -1965,20 +1997,41 @@ int td_impl(ofdft_grid *g, T *pre, T *pim, const T *rho0, const ofdft_functional
 }
 
 // ---------------------------------------------------------------- batched evaluation
-// Snapshots are spread over a few internal streams forked from (and joined back
-// into) the caller's stream, so that small grids overlap on the GPU; the whole
-// batch is captured once into a CUDA graph and replayed while the arguments and
-// the grids' device buffers are unchanged.
+// A batch is planned once per distinct set of arguments: the snapshots are partitioned into
+// groups that share one launch geometry (grid shape, compiled kernels, tiles, channel
+// lists); each group of up to kGroupMax snapshots runs every pass of its evaluations as one
+// grouped launch (the arguments in device memory, uploaded with the plan), single snapshots
+// run the single-evaluation launches.  Groups are spread over a few internal streams forked
+// from (and joined back into) the caller's stream, the heaviest first onto the least loaded
+// stream; the energies and status slots of every snapshot are gathered by one kernel and
+// copied to the host once.  The whole batch is captured once into a CUDA graph and replayed
+// while the plan's key (the functional, the stream, every snapshot's arguments and kernels)
+// is unchanged.
 constexpr int kBatchStreams = 4;
+constexpr int kBatchPlans = 16;
 
-struct BatchGraph {
-    std::vector<uintptr_t> key;
+struct BatchPlan {
+    std::vector<unsigned char> key;
     cudaGraphExec_t exec = nullptr;
+    void *dargs = nullptr;                 // the evaluations' arguments in plan order (device)
+    double *dcol = nullptr, *hcol = nullptr;   // gathered energies and slots (device, pinned host)
+    std::vector<int> order;                // plan position -> snapshot
+    std::vector<int> gbeg, gstream;        // group g: positions [gbeg[g], gbeg[g + 1]), its stream
+    int launches = 0;                      // kernel launches of the batch's evaluations
+    std::string report;
 };
 
-std::vector<BatchGraph> &graph_cache() {
-    static std::vector<BatchGraph> c;
+std::vector<BatchPlan> &batch_plans() {
+    static std::vector<BatchPlan> c;
     return c;
+}
+
+void free_plan(BatchPlan &p) {
+    if (p.exec) cudaGraphExecDestroy(p.exec);
+    cudaFree(p.dargs);
+    cudaFree(p.dcol);
+    cudaFreeHost(p.hcol);
+    p = BatchPlan();
 }
 
 // kBatchStreams worker streams, then the stream a batch graph is captured on (the
@@ -2012,10 +2065,117 @@ int prepare_batch_grid(ofdft_grid *g, const ofdft_functional *f, bool forces, co
     return OFDFT_OK;
 }
 
-// enqueue the whole batch on the caller's stream (fork/join over internal streams)
+template <typename T> void append_bytes(std::vector<unsigned char> &key, const T &v) {
+    const unsigned char *b = (const unsigned char *)&v;
+    key.insert(key.end(), b, b + sizeof(T));
+}
+
+// the kernels of a launch set, field by field (no padding bytes)
+void append_kernels(std::vector<unsigned char> &key, const LaunchSet &ks) {
+    const void *p[] = {ks.row_fwd,   ks.row_inv,   ks.pen_fwd,     ks.pen_inv,    ks.axis0,     ks.axis0_mgp,
+                       ks.recip.k,   ks.recip.k_mgp, ks.recip.g,   ks.recip.g_mgp, ks.row_fwd_g, ks.row_inv_g,
+                       ks.pen_fwd_g, ks.pen_inv_g, ks.axis0_g,     ks.axis0_mgp_g};
+    const long long v[] = {ks.recip.nt, ks.recip.per_sm, ks.recip.tw, (long long)ks.recip.smem};
+    append_bytes(key, p);
+    append_bytes(key, v);
+}
+
+// the launch geometry of an evaluation: what a grouped launch shares between its evaluations
+// (the reciprocal-space pass: the persistent kernel's, or else the tile kernel's)
+template <typename T> std::vector<unsigned char> launch_signature(const LaunchSet &ks_in, const EvalArgs<T> &a) {
+    LaunchSet ks = ks_in;
+    int tile[3] = {a.TW0, a.thr_ax0, a.ax0_scr};
+    if (ks.recip.k) {
+        ks.axis0 = ks.axis0_mgp = ks.axis0_g = ks.axis0_mgp_g = nullptr;
+        tile[0] = tile[1] = tile[2] = 0;
+    } else {
+        ks.recip = RecipLaunch();
+    }
+    std::vector<unsigned char> k;
+    append_kernels(k, ks);
+    const int v[] = {a.n0,       a.n1,       a.n2,    a.nb_stats, a.nb_ax0, a.nb_row, a.Brow,     a.thr_rowf,
+                     a.thr_rowi, a.TW1,      a.thr_p1, tile[0],   tile[1],  tile[2],  a.grid_p1,  a.row2_G,
+                     a.nfwd,     a.ncol,     a.ncol_inv, a.exact_sums, a.mgp_tab != nullptr};
+    append_bytes(k, v);
+    return k;
+}
+
+// Plan a batch: groups, their streams, and the device copy of the arguments.
 template <typename T>
-int enqueue_batch(int n, ofdft_grid *const *grids, const void *const *rho_dev, const ofdft_functional *f,
-                  void *const *V_dev, double *const *F_out, cudaStream_t user) {
+int make_plan(ofdft_grid *g0, int n, ofdft_grid *const *grids, const std::vector<EvalArgs<T>> &args, bool grouped,
+              BatchPlan &p) {
+    std::vector<std::vector<unsigned char>> sig(n);
+    std::vector<char> ok(n);
+    for (int i = 0; i < n; i++) {
+        sig[i] = launch_signature<T>(ws<T>(grids[i]).ks, args[i]);
+        ok[i] = grouped && grouped_ok<T>(ws<T>(grids[i]).ks, args[i]);
+    }
+    // groups: snapshots of equal signature in first-seen order, cut at kGroupMax
+    std::vector<char> used(n, 0);
+    std::vector<long long> work;
+    for (int i = 0; i < n; i++) {
+        if (used[i]) continue;
+        std::vector<int> mem{i};
+        used[i] = 1;
+        if (ok[i])
+            for (int j = i + 1; j < n; j++)
+                if (!used[j] && ok[j] && sig[j] == sig[i]) {
+                    mem.push_back(j);
+                    used[j] = 1;
+                }
+        for (size_t c = 0; c < mem.size(); c += kGroupMax) {
+            p.gbeg.push_back((int)p.order.size());
+            for (size_t m = c; m < std::min(mem.size(), c + kGroupMax); m++) p.order.push_back(mem[m]);
+            work.push_back(grids[i]->N * (long long)std::min((size_t)kGroupMax, mem.size() - c));
+        }
+    }
+    const int ng = (int)p.gbeg.size();
+    p.gbeg.push_back(n);
+    // what the plan launches per batch (evaluation kernels and the gather; forces excluded)
+    char buf[160];
+    std::snprintf(buf, sizeof(buf), "%d snapshots in %d launch groups:", n, ng);
+    p.report = buf;
+    p.launches = 1;
+    for (int gi = 0; gi < ng; gi++) {
+        const EvalArgs<T> &a = args[p.order[p.gbeg[gi]]];
+        const int K = p.gbeg[gi + 1] - p.gbeg[gi];
+        p.launches += (K > 1 ? 1 : 0) + 4 + (a.nfwd > 0) + (a.ncol > 0) + (a.ncol_inv > 0);
+        const bool recip = ws<T>(grids[p.order[p.gbeg[gi]]]).ks.recip.k != nullptr;
+        std::snprintf(buf, sizeof(buf), "%s %dx%dx%d x%d%s", gi ? "," : "", a.n0, a.n1, a.n2, K,
+                      K > 1 ? (recip ? " (grouped, persistent recip)" : " (grouped)") : "");
+        p.report += buf;
+    }
+    std::snprintf(buf, sizeof(buf), "; %d kernel launches per batch (forces excluded)", p.launches);
+    p.report += buf;
+    // streams: the heaviest group first onto the least loaded stream
+    std::vector<int> idx(ng);
+    for (int gi = 0; gi < ng; gi++) idx[gi] = gi;
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return work[x] > work[y]; });
+    long long load[kBatchStreams] = {0};
+    p.gstream.assign(ng, 0);
+    for (int gi : idx) {
+        const int s = (int)(std::min_element(load, load + kBatchStreams) - load);
+        p.gstream[gi] = s;
+        load[s] += work[gi];
+    }
+    // the arguments in plan order, the gather buffers
+    std::vector<EvalArgs<T>> ordered(n);
+    for (int j = 0; j < n; j++) ordered[j] = args[p.order[j]];
+    ofdft_grid *g = g0;
+    const size_t W = E_NUM + S_NSCAL;
+    CK(cudaMalloc(&p.dargs, (size_t)n * sizeof(EvalArgs<T>)), "cudaMalloc batch arguments");
+    CK(cudaMalloc((void **)&p.dcol, (size_t)n * W * sizeof(double)), "cudaMalloc batch results");
+    CK(cudaMallocHost((void **)&p.hcol, (size_t)n * W * sizeof(double)), "cudaMallocHost batch results");
+    CK(cudaMemcpy(p.dargs, ordered.data(), (size_t)n * sizeof(EvalArgs<T>), cudaMemcpyHostToDevice),
+       "upload batch arguments");
+    return OFDFT_OK;
+}
+
+// Enqueue a planned batch on the caller's stream (fork/join over the internal streams).
+template <typename T>
+int enqueue_batch(const BatchPlan &p, int n, ofdft_grid *const *grids, const void *const *rho_dev,
+                  const ofdft_functional *f, const std::vector<EvalArgs<T>> &args, double *const *F_out,
+                  cudaStream_t user) {
     cudaStream_t *st = batch_streams();
     cudaEvent_t fork, join[kBatchStreams];
     cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
@@ -2023,26 +2183,51 @@ int enqueue_batch(int n, ofdft_grid *const *grids, const void *const *rho_dev, c
     int rc = OFDFT_OK;
     cudaEventRecord(fork, user);
     for (int k = 0; k < kBatchStreams; k++) cudaStreamWaitEvent(st[k], fork, 0);
-    for (int i = 0; i < n && rc == OFDFT_OK; i++) {
-        ofdft_grid *g = grids[i];
-        const cudaStream_t saved = g->stream;
-        g->stream = st[i % kBatchStreams];
-        Workspace<T> &w = ws<T>(g);
-        const bool want_f = F_out && F_out[i];
-        rc = enqueue_eval<T>(g, (const T *)rho_dev[i], f, V_dev ? (T *)V_dev[i] : nullptr, nullptr, want_f);
-        if (rc == OFDFT_OK) {
-            cudaMemcpyAsync(g->h_pinned, w.energies, E_NUM * sizeof(double), cudaMemcpyDeviceToHost, g->stream);
-            cudaMemcpyAsync(g->h_pinned + 8, w.scal, S_NSCAL * sizeof(double), cudaMemcpyDeviceToHost, g->stream);
+    const EvalArgs<T> *dargs = (const EvalArgs<T> *)p.dargs;
+    const int ng = (int)p.gstream.size();
+    for (int gi = 0; gi < ng && rc == OFDFT_OK; gi++) {
+        const int b = p.gbeg[gi], K = p.gbeg[gi + 1] - b;
+        const cudaStream_t s = st[p.gstream[gi]];
+        ofdft_grid *g = grids[p.order[b]];
+        if (K == 1) {
+            const cudaStream_t saved = g->stream;
+            g->stream = s;
+            rc = eval_launch<T>(g, args[p.order[b]], f);
+            g->stream = saved;
+        } else {
+            RecipMaps maps[kGroupMax];
+            for (int m = 0; m < K && rc == OFDFT_OK; m++) {
+                ofdft_grid *gm = grids[p.order[b + m]];
+                maps[m] = ws<T>(gm).maps;
+                const cudaStream_t saved = gm->stream;
+                gm->stream = s;
+                rc = upload_knots<T>(gm, args[p.order[b + m]], f);
+                gm->stream = saved;
+            }
+            if (rc) break;
+            const Workspace<T> &w = ws<T>(g);
+            cudaError_t e = launch_group<T>(args[p.order[b]], dargs + b, K, w.ks, s, w.ks.recip.k ? maps : nullptr);
+            if (e != cudaSuccess) {
+                rc = fail(g, OFDFT_ERR_CUDA, "grouped evaluation kernels", e);
+                break;
+            }
         }
-        if (rc == OFDFT_OK && F_out && F_out[i]) {
-            // the evaluation kept rho_hat (when it has the Hartree/PP channel): no transform here
+        // forces of the group's snapshots on the group's stream (rho_hat from the evaluation)
+        for (int m = 0; m < K && rc == OFDFT_OK; m++) {
+            const int i = p.order[b + m];
+            if (!(F_out && F_out[i])) continue;
+            ofdft_grid *gm = grids[i];
+            const cudaStream_t saved = gm->stream;
+            gm->stream = s;
             const bool kept = f->terms & (OFDFT_TERM_HARTREE | OFDFT_TERM_PP);
-            rc = forces_enqueue<T>(g, (const T *)rho_dev[i], kept ? w.rhohat : nullptr);
-            if (rc == OFDFT_OK)
-                cudaMemcpyAsync(g->F_pinned, g->F_dev, (size_t)3 * g->n_ions * sizeof(double), cudaMemcpyDeviceToHost,
-                                g->stream);
+            rc = forces_enqueue<T>(gm, (const T *)rho_dev[i], kept ? ws<T>(gm).rhohat : nullptr);
+            if (rc == OFDFT_OK) {
+                cudaError_t e = cudaMemcpyAsync(gm->F_pinned, gm->F_dev, (size_t)3 * gm->n_ions * sizeof(double),
+                                                cudaMemcpyDeviceToHost, s);
+                if (e != cudaSuccess) rc = fail(gm, OFDFT_ERR_CUDA, "forces copy", e);
+            }
+            gm->stream = saved;
         }
-        g->stream = saved;
     }
     for (int k = 0; k < kBatchStreams; k++) {
         cudaEventRecord(join[k], st[k]);
@@ -2050,71 +2235,106 @@ int enqueue_batch(int n, ofdft_grid *const *grids, const void *const *rho_dev, c
     }
     cudaEventDestroy(fork);
     for (int k = 0; k < kBatchStreams; k++) cudaEventDestroy(join[k]);
-    return rc;
+    if (rc) return rc;
+    ofdft_grid *g = grids[0];
+    CK(launch_collect<T>(dargs, n, p.dcol, user), "gather batch results");
+    CK(cudaMemcpyAsync(p.hcol, p.dcol, (size_t)n * (E_NUM + S_NSCAL) * sizeof(double), cudaMemcpyDeviceToHost,
+                       user),
+       "batch results copy");
+    return OFDFT_OK;
 }
 
 template <typename T>
 int batched_impl(int n, ofdft_grid *const *grids, const void *const *rho_dev, const ofdft_functional *f,
                  double *E_out, void *const *V_dev, double *const *F_out) {
-    cudaStream_t user = grids[0]->stream;
     ofdft_grid *g0 = grids[0];
+    cudaStream_t user = g0->stream;
+    for (int i = 0; i < n; i++)
+        for (int j = i + 1; j < n; j++)
+            if (grids[j] == grids[i]) return fail(g0, OFDFT_ERR_INVALID_ARG, "a grid appears twice in the batch");
+    std::vector<EvalArgs<T>> args(n);
     for (int i = 0; i < n; i++) {
-        int rc = prepare_batch_grid<T>(grids[i], f, F_out && F_out[i], (const T *)rho_dev[i]);
+        const bool want_f = F_out && F_out[i];
+        int rc = prepare_batch_grid<T>(grids[i], f, want_f, (const T *)rho_dev[i]);
+        if (!rc) rc = eval_args<T>(grids[i], (const T *)rho_dev[i], f, V_dev ? (T *)V_dev[i] : nullptr, nullptr, want_f,
+                                   args[i]);
         if (rc) return rc;
     }
     bool use_graph = g0->batch_graph && !f->knots;
     for (int i = 0; i < n; i++) use_graph = use_graph && !grids[i]->prof_on;
+    // key: the functional, the stream, the modes; per snapshot the grid, its buffer generation,
+    // whether forces are wanted, its kernels and its arguments (every pointer and size)
+    std::vector<unsigned char> key;
+    append_bytes(key, *f);
+    append_bytes(key, user);
+    append_bytes(key, (int)use_graph);
+    append_bytes(key, g0->batch_grouped);
+    append_bytes(key, (int)sizeof(T));
+    for (int i = 0; i < n; i++) {
+        append_bytes(key, grids[i]);
+        append_bytes(key, grids[i]->generation);
+        append_bytes(key, (int)(F_out && F_out[i]));
+        append_kernels(key, ws<T>(grids[i]).ks);
+        append_bytes(key, args[i]);
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    append_bytes(key, dev);
+    BatchPlan *plan = nullptr;
+    for (auto &bp : batch_plans())
+        if (bp.key == key) plan = &bp;
     cudaError_t e;
-    if (use_graph) {
-        // key: functional, then per snapshot the grid, its buffer generation and the pointers
-        std::vector<uintptr_t> key;
-        const unsigned char *fb = (const unsigned char *)f;
-        for (size_t b = 0; b < sizeof(ofdft_functional); b++) key.push_back(fb[b]);
-        key.push_back((uintptr_t)user);
-        for (int i = 0; i < n; i++) {
-            key.push_back((uintptr_t)grids[i]);
-            key.push_back((uintptr_t)grids[i]->generation);
-            key.push_back((uintptr_t)rho_dev[i]);
-            key.push_back(V_dev ? (uintptr_t)V_dev[i] : 0);
-            key.push_back((F_out && F_out[i]) ? 1 : 0);
+    if (!plan) {
+        if ((int)batch_plans().size() >= kBatchPlans) {
+            e = cudaStreamSynchronize(user);                 // (no call leaves a batch in flight)
+            if (e != cudaSuccess) return fail(g0, OFDFT_ERR_CUDA, "stream synchronize", e);
+            free_plan(batch_plans().front());
+            batch_plans().erase(batch_plans().begin());
         }
-        cudaGraphExec_t exec = nullptr;
-        for (auto &bg : graph_cache())
-            if (bg.key == key) exec = bg.exec;
-        if (!exec) {
+        BatchPlan np;
+        int rc = make_plan<T>(g0, n, grids, args, g0->batch_grouped != 0, np);
+        if (!rc && use_graph) {
             cudaGraph_t graph = nullptr;
             cudaStream_t origin = batch_streams()[kBatchStreams];
             e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
-            if (e != cudaSuccess) return fail(g0, OFDFT_ERR_CUDA, "begin capture", e);
-            int rc = enqueue_batch<T>(n, grids, rho_dev, f, V_dev, F_out, origin);
-            e = cudaStreamEndCapture(origin, &graph);
-            if (rc) {
+            if (e != cudaSuccess) rc = fail(g0, OFDFT_ERR_CUDA, "begin capture", e);
+            if (!rc) {
+                rc = enqueue_batch<T>(np, n, grids, rho_dev, f, args, F_out, origin);
+                e = cudaStreamEndCapture(origin, &graph);
+                if (!rc && e != cudaSuccess) rc = fail(g0, OFDFT_ERR_CUDA, "end capture", e);
+                if (!rc) {
+                    e = cudaGraphInstantiate(&np.exec, graph, 0);
+                    if (e != cudaSuccess) rc = fail(g0, OFDFT_ERR_CUDA, "graph instantiate", e);
+                }
                 if (graph) cudaGraphDestroy(graph);
-                return rc;
             }
-            if (e != cudaSuccess) return fail(g0, OFDFT_ERR_CUDA, "end capture", e);
-            e = cudaGraphInstantiate(&exec, graph, 0);
-            cudaGraphDestroy(graph);
-            if (e != cudaSuccess) return fail(g0, OFDFT_ERR_CUDA, "graph instantiate", e);
-            if (graph_cache().size() >= 16) {
-                cudaGraphExecDestroy(graph_cache().front().exec);
-                graph_cache().erase(graph_cache().begin());
-            }
-            graph_cache().push_back({key, exec});
         }
-        e = cudaGraphLaunch(exec, user);
+        if (rc) {
+            free_plan(np);
+            return rc;
+        }
+        np.key = std::move(key);
+        batch_plans().push_back(std::move(np));
+        plan = &batch_plans().back();
+    }
+    g0->batch_report = plan->report + (plan->exec ? ", replayed as one CUDA graph" : "");
+    if (plan->exec) {
+        e = cudaGraphLaunch(plan->exec, user);
         if (e != cudaSuccess) return fail(g0, OFDFT_ERR_CUDA, "graph launch", e);
     } else {
-        int rc = enqueue_batch<T>(n, grids, rho_dev, f, V_dev, F_out, user);
+        int rc = enqueue_batch<T>(*plan, n, grids, rho_dev, f, args, F_out, user);
         if (rc) return rc;
     }
     e = cudaStreamSynchronize(user);
     if (e != cudaSuccess) return fail(g0, OFDFT_ERR_CUDA, "stream synchronize", e);
-    for (int i = 0; i < n; i++) {
+    const int W = E_NUM + S_NSCAL;
+    for (int j = 0; j < n; j++) {
+        const int i = plan->order[j];
         ofdft_grid *g = grids[i];
-        if (int rc = wait_status(g, g->h_pinned + 8)) return rc;
-        if (g->h_pinned[8 + S_BAD] != 0.0) return fail(g, OFDFT_ERR_BAD_DENSITY, "bad density in batch");
-        std::memcpy(E_out + E_NUM * i, g->h_pinned, E_NUM * sizeof(double));
+        const double *r = plan->hcol + (size_t)j * W;
+        if (int rc = wait_status(g, r + E_NUM)) return rc;
+        if (r[E_NUM + S_BAD] != 0.0) return fail(g, OFDFT_ERR_BAD_DENSITY, "bad density in batch");
+        std::memcpy(E_out + E_NUM * i, r, E_NUM * sizeof(double));
         if (F_out && F_out[i]) std::memcpy(F_out[i], g->F_pinned, (size_t)3 * g->n_ions * sizeof(double));
     }
     return OFDFT_OK;
@@ -2216,6 +2436,11 @@ const char *ofdft_tuning_report(const ofdft_grid *g, int precision) {
     return r.c_str();
 }
 
+const char *ofdft_batch_report(const ofdft_grid *g) {
+    if (!g) return "null handle";
+    return g->batch_report.c_str();
+}
+
 int ofdft_set_option(ofdft_grid *g, int option, long long value) {
     if (!g) return OFDFT_ERR_INVALID_ARG;
     switch (option) {
@@ -2235,6 +2460,9 @@ int ofdft_set_option(ofdft_grid *g, int option, long long value) {
             return OFDFT_OK;
         case OFDFT_OPTION_BATCH_GRAPH:
             g->batch_graph = value != 0;
+            return OFDFT_OK;
+        case OFDFT_OPTION_BATCH_GROUPED:
+            g->batch_grouped = value != 0;
             return OFDFT_OK;
         case OFDFT_OPTION_WAIT_POLLS:
             if (value < 0 || value > (1LL << 30)) return fail(g, OFDFT_ERR_INVALID_ARG, "wait polls out of range");

@@ -39,6 +39,7 @@ enum {
 enum { E_TOT = 0, E_TF = 1, E_VW = 2, E_NL = 3, E_H = 4, E_PP = 5, E_XC = 6, E_NUM = 7 };
 
 constexpr int kMaxChan = 3 + OFDFT_MAX_KNOTS;
+constexpr int kGroupMax = 32;        // evaluations per grouped launch (tensor maps in the parameters)
 constexpr int kMaxThreads = 512;     // block size bound of the FFT kernels
 
 // complex values a thread stages per FFT pass (register budget per precision)
@@ -150,11 +151,18 @@ template <typename T> __host__ __device__ inline size_t rowi_smem(const EvalArgs
     return a.row2_G ? row2_smem_bytes<T>(a.n2, a.row2_G) : row_inv_smem_bytes<T>(a.n2, a.Brow);
 }
 
+// persistent pencil grid: at most grid_p1 blocks (resident capacity), never more than tiles
+template <typename T> inline unsigned pencil_tiles(const EvalArgs<T> &a, int nch) {
+    const long long t = (((long long)a.n0 * a.n2h + a.TW1 - 1) / a.TW1) * nch;
+    return (unsigned)(t < a.grid_p1 ? t : a.grid_p1);
+}
+
 // The persistent reciprocal-space kernel (register-resident n0 transforms, tensor-map tile
 // loads; recip.cuh) compiled for an n0: Wang-Teter and Eq. MGP forms, block size, dynamic
 // shared memory, blocks per SM.
 struct RecipLaunch {
     const void *k = nullptr, *k_mgp = nullptr;
+    const void *g = nullptr, *g_mgp = nullptr;   // grouped forms (null: none compiled)
     int nt = 0, per_sm = 1;
     int tw = 32;                 // columns per tile (the tensor copies' box width)
     size_t smem = 0;
@@ -167,6 +175,10 @@ struct LaunchSet {
     const void *axis0 = nullptr;                         // depends on n0
     const void *axis0_mgp = nullptr;                     // the same with Eq. MGP kernels
     RecipLaunch recip;                                   // replaces axis0 when its k is set
+    // grouped forms of the five (one launch over the evaluations of a batch that share a
+    // launch geometry); null where none is compiled
+    const void *row_fwd_g = nullptr, *row_inv_g = nullptr, *pen_fwd_g = nullptr, *pen_inv_g = nullptr;
+    const void *axis0_g = nullptr, *axis0_mgp_g = nullptr;
 };
 
 // tensor maps of the persistent reciprocal-space kernel (defined in recip.cuh)
@@ -181,6 +193,7 @@ enum { ROLE_ROW = 0, ROLE_PENCIL = 1, ROLE_AXIS0 = 2, ROLE_ROW2 = 3 };
 // persistent kernel instead when recip.k is set.
 struct KernelCand {
     const void *k1 = nullptr, *k2 = nullptr;
+    const void *g1 = nullptr, *g2 = nullptr;   // their grouped forms
     int B = 0, nt = 0;
     bool batched = false;                 // channel-batched row kernels (B = channels per group)
     RecipLaunch recip;
@@ -196,6 +209,8 @@ template <typename T> bool find_specialised(int role, int n, const void **k1, co
 template <typename T> void recip_candidates(int n, std::vector<KernelCand> &out);
 // The generic (runtime-size) kernels (exact_sums: the forms that add every energy term in FP64).
 template <typename T> LaunchSet generic_kernels(bool exact_sums = false);
+// the grouped forms of the generic kernels (without exact sums) into ks (group_kernels.cu)
+template <typename T> void generic_group_kernels(LaunchSet &ks);
 // Let every kernel of the set use the device's full opt-in shared memory.
 cudaError_t prepare_kernels(const LaunchSet &ks);
 
@@ -203,6 +218,15 @@ cudaError_t prepare_kernels(const LaunchSet &ks);
 // a.nb_ax0 is then its grid)
 template <typename T> cudaError_t launch_eval(const EvalArgs<T> &a, const LaunchSet &ks, cudaStream_t s,
                                               const ProfHook *prof = nullptr, const RecipMaps *maps = nullptr);
+// Grouped launch of K <= kGroupMax evaluations sharing a's launch geometry (a: the host copy
+// of any one of them; ga: all K in device memory; maps: their K tensor-map pairs when
+// ks.recip.k is set).  Only when grouped_ok(ks, a): every kernel of the evaluation has a
+// grouped form (FP32 kernels, without the exact-sums option).
+template <typename T> bool grouped_ok(const LaunchSet &ks, const EvalArgs<T> &a);
+template <typename T> cudaError_t launch_group(const EvalArgs<T> &a, const EvalArgs<T> *ga, int K, const LaunchSet &ks,
+                                               cudaStream_t s, const RecipMaps *maps = nullptr);
+// copies the energies and scalar slots of ga[0..n) to out (E_NUM + S_NSCAL doubles each)
+template <typename T> cudaError_t launch_collect(const EvalArgs<T> *ga, int n, double *out, cudaStream_t s);
 // inverse pencil along n1 + C2R rows of the channels in a.col_inv_ch / a.inv_ch (CONS_ADD), V = result
 template <typename T> cudaError_t launch_inverse_cols_rows(const EvalArgs<T> &a, const LaunchSet &ks, cudaStream_t s);
 // stats + knots + row_fwd + forward pencil along n1 only (the channels of a.fwd_ch / a.col_ch)

@@ -37,6 +37,7 @@ template <typename T> LaunchSet generic_kernels(bool exact_sums) {
     ks.row_fwd = (const void *)row_fwd_kernel<T, RtPolicy<T, 2>>;
     ks.pen_fwd = (const void *)pencil1_kernel<T, -1, RtPolicy<T, 1>>;
     ks.pen_inv = (const void *)pencil1_kernel<T, +1, RtPolicy<T, 1>>;
+    if (!exact_sums) generic_group_kernels<T>(ks);
     if (exact_sums) {
         ks.row_inv = (const void *)row_inv_kernel<T, RtPolicy<T, 2>, true>;
         ks.axis0 = (const void *)axis0_kernel<T, RtPolicy<T, 0>, false, true>;
@@ -50,9 +51,10 @@ template <typename T> LaunchSet generic_kernels(bool exact_sums) {
 }
 
 cudaError_t prepare_kernels(const LaunchSet &ks) {
-    const void *k[8] = {ks.row_fwd, ks.row_inv, ks.pen_fwd, ks.pen_inv, ks.axis0, ks.axis0_mgp, ks.recip.k,
-                        ks.recip.k_mgp};
-    for (int i = 0; i < 8; i++) {
+    const void *k[16] = {ks.row_fwd,   ks.row_inv,   ks.pen_fwd,   ks.pen_inv,   ks.axis0,     ks.axis0_mgp,
+                         ks.recip.k,   ks.recip.k_mgp, ks.recip.g, ks.recip.g_mgp, ks.row_fwd_g, ks.row_inv_g,
+                         ks.pen_fwd_g, ks.pen_inv_g, ks.axis0_g,   ks.axis0_mgp_g};
+    for (int i = 0; i < 16; i++) {
         if (!k[i]) continue;
         cudaError_t e = allow_max_dynamic_smem(k[i]);
         if (e != cudaSuccess) return e;
@@ -60,11 +62,6 @@ cudaError_t prepare_kernels(const LaunchSet &ks) {
     return cudaSuccess;
 }
 
-// persistent pencil grid: at most grid_p1 blocks (resident capacity), never more than tiles
-template <typename T> static unsigned pencil_tiles(const EvalArgs<T> &a, int nch) {
-    const long long t = (((long long)a.n0 * a.n2h + a.TW1 - 1) / a.TW1) * nch;
-    return (unsigned)(t < a.grid_p1 ? t : a.grid_p1);
-}
 
 template <typename T>
 static cudaError_t launch(const void *k, dim3 g, int nt, size_t smem, const EvalArgs<T> &a, cudaStream_t s) {

@@ -1,7 +1,8 @@
 // Size-specialised instantiations of the FFT-carrying kernels: candidate lists.
 //
-// Each macro appends one compile-time configuration for axis length N to the
-// candidate list `out` of the requested role (see kernel_candidates in eval.cuh);
+// Each macro appends one compile-time configuration for axis length N (the kernels and
+// their grouped forms) to the candidate list `out` of the requested role (see
+// kernel_candidates in eval.cuh);
 // the first candidate of a role is its default, and the autotuner times the others
 // at a grid's first evaluation.
 //   OFDFT_CAND_ROW(T, N, RB, NT, MAXR, MINB)    per-channel row kernels: RB row pairs per
@@ -20,11 +21,14 @@
 #include "kernels.cuh"
 
 namespace ofdft {
-inline KernelCand make_cand(const void *k1, const void *k2, int B, int nt, const char *kind, int maxr, int minb) {
+inline KernelCand make_cand(const void *k1, const void *k2, const void *g1, const void *g2, int B, int nt,
+                            const char *kind, int maxr, int minb) {
     KernelCand c;
     c.batched = kind[4] == '2';
     c.k1 = k1;
     c.k2 = k2;
+    c.g1 = g1;
+    c.g2 = g2;
     c.B = B;
     c.nt = nt;
     std::snprintf(c.name, sizeof(c.name), "%s %dx%d r%d b%d", kind, B, nt, maxr, minb);
@@ -36,6 +40,7 @@ inline KernelCand make_cand(const void *k1, const void *k2, int B, int nt, const
     if (role == ROLE_ROW && n == N) {                                                                   \
         typedef ::ofdft::CtPolicy<T, N, RB, RB + 1, NT, MAXR, MINB> PR;                                 \
         out.push_back(make_cand((const void *)row_fwd_kernel<T, PR>, (const void *)row_inv_kernel<T, PR>, \
+                                (const void *)row_fwd_group<T, PR>, (const void *)row_inv_group<T, PR>,   \
                                 RB, NT, "rows", MAXR, MINB));                                           \
     }
 
@@ -43,6 +48,7 @@ inline KernelCand make_cand(const void *k1, const void *k2, int B, int nt, const
     if (role == ROLE_ROW2 && n == N) {                                                                  \
         typedef ::ofdft::RowPolicy2<T, N, G, NT, MAXR, MINB> PQ;                                        \
         out.push_back(make_cand((const void *)row_fwd2_kernel<T, PQ>, (const void *)row_inv2_kernel<T, PQ>, \
+                                (const void *)row_fwd2_group<T, PQ>, (const void *)row_inv2_group<T, PQ>, \
                                 G, NT, "rows2", MAXR, MINB));                                           \
     }
 
@@ -50,6 +56,7 @@ inline KernelCand make_cand(const void *k1, const void *k2, int B, int nt, const
     if (role == ROLE_PENCIL && n == N) {                                                                \
         typedef ::ofdft::CtPolicy<T, N, TW, TW, NT, MAXR, MINB> PP;                                     \
         out.push_back(make_cand((const void *)pencil1_kernel<T, -1, PP>, (const void *)pencil1_kernel<T, +1, PP>, \
+                                (const void *)pencil1_group<T, -1, PP>, (const void *)pencil1_group<T, +1, PP>, \
                                 TW, NT, "pencil", MAXR, MINB));                                         \
     }
 
@@ -59,6 +66,7 @@ inline KernelCand make_cand(const void *k1, const void *k2, int B, int nt, const
     if (role == ROLE_AXIS0 && n == N) {                                                                 \
         typedef ::ofdft::CtPolicy<T, N, TW, TW, NT, MAXR, MINB, ::ofdft::axis0_oop<T>(N)> PA;           \
         out.push_back(make_cand((const void *)axis0_kernel<T, PA, false>, (const void *)axis0_kernel<T, PA, true>, \
+                                (const void *)axis0_group<T, PA, false>, (const void *)axis0_group<T, PA, true>, \
                                 TW, NT, "tile", MAXR, MINB));                                           \
     }
 

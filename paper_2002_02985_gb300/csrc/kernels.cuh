@@ -275,8 +275,8 @@ __device__ __forceinline__ void knots_from_partials(const EvalArgs<T> &a, double
 }
 
 // ======================================================================= stats (s1 input)
-template <typename T, bool XS = false>
-__global__ void __launch_bounds__(256) stats_kernel(EvalArgs<T> a) {
+template <typename T, bool XS>
+__device__ __forceinline__ void stats_body(const EvalArgs<T> &a, const int bid, const int nblk) {
     __shared__ double sd[3 * 32];
     __shared__ T st[32];
     double s_rho = 0.0, s_tf = 0.0, s_xc = 0.0;
@@ -286,9 +286,9 @@ __global__ void __launch_bounds__(256) stats_kernel(EvalArgs<T> a) {
     // groups of 4 consecutive points: summed in T, then added in FP64 (keeps the FP64 pipe
     // idle); U groups a grid stride apart per iteration, all loaded before any is used
     constexpr int U = 4;
-    const long long ng = (a.N + 3) / 4, stride = (long long)gridDim.x * blockDim.x;
+    const long long ng = (a.N + 3) / 4, stride = (long long)nblk * blockDim.x;
     const bool vec = (reinterpret_cast<uintptr_t>(a.rho) % (4 * sizeof(T)) == 0) && (a.N % 4 == 0);
-    for (long long g0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; g0 < ng; g0 += U * stride) {
+    for (long long g0 = bid * (long long)blockDim.x + threadIdx.x; g0 < ng; g0 += U * stride) {
         T x[U][4];
 #pragma unroll
         for (int u = 0; u < U; u++) {
@@ -351,11 +351,11 @@ __global__ void __launch_bounds__(256) stats_kernel(EvalArgs<T> a) {
     if constexpr (sizeof(T) == 4 && !XS) block_sum_n_f32warp<3>(r, sd);
     else block_sum_n<3>(r, sd);
     if (threadIdx.x == 0)
-        for (int k = 0; k < 3; k++) a.part_stats[3 * blockIdx.x + k] = r[k];
+        for (int k = 0; k < 3; k++) a.part_stats[3 * bid + k] = r[k];
     mn = block_min(mn, st);
-    if (threadIdx.x == 0) a.part_minmax[2 * blockIdx.x] = mn;
+    if (threadIdx.x == 0) a.part_minmax[2 * bid] = mn;
     mx = block_max(mx, st);
-    if (threadIdx.x == 0) a.part_minmax[2 * blockIdx.x + 1] = mx;
+    if (threadIdx.x == 0) a.part_minmax[2 * bid + 1] = mx;
     bad = __syncthreads_or(bad);
     if (threadIdx.x == 0 && bad) a.scal[S_BAD] = 1.0;
     // the last block to finish reduces every block's partials and makes the knots (thread 0
@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(256) stats_kernel(EvalArgs<T> a) {
     __shared__ bool last;
     if (threadIdx.x == 0) {
         __threadfence();
-        last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
+        last = atomicAdd(a.ticket, 1u) == nblk - 1;
     }
     __syncthreads();
     if (!last) return;
@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(256) stats_kernel(EvalArgs<T> a) {
 // The density is staged through shared memory ([rr][pitch], pitch odd) so that
 // both the global loads and the shared-memory transposition are conflict free.
 template <typename T, class P>
-__device__ __forceinline__ void row_fwd_body(const EvalArgs<T> &a) {
+__device__ __forceinline__ void row_fwd_body(const EvalArgs<T> &a, const int bid, const int nblk) {
     typedef typename Vec2<T>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = P::n(a), B = P::B(a), ld = P::ld(a), NT = P::nt();
@@ -397,7 +397,7 @@ __device__ __forceinline__ void row_fwd_body(const EvalArgs<T> &a) {
     __shared__ T sk[OFDFT_MAX_KNOTS];
 
     const long long R = (long long)a.n0 * a.n1;
-    const long long row0 = 2LL * B * blockIdx.x;
+    const long long row0 = 2LL * B * bid;
     for (int i = threadIdx.x; i < n; i += NT) tw[i] = a.tw2[i];
     const bool lwt = (a.terms & 4u) && a.kernel == 0;
     const int M = a.M;
@@ -477,7 +477,7 @@ __device__ __forceinline__ void row_fwd_body(const EvalArgs<T> &a) {
 // all n1 rows.  The next tile is prefetched with cp.async into the second of two
 // buffers while the current one is transformed and stored.
 template <typename T, int DIR, class P>
-__device__ __forceinline__ void pencil1_body(const EvalArgs<T> &a) {
+__device__ __forceinline__ void pencil1_body(const EvalArgs<T> &a, const int bid, const int nblk) {
     typedef typename Vec2<T>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = P::n(a), TW = P::B(a), n2h = a.n2h, NT = P::nt();
@@ -510,12 +510,12 @@ __device__ __forceinline__ void pencil1_body(const EvalArgs<T> &a) {
         cp_async_commit();
     };
     int it = 0;
-    if ((int)blockIdx.x < total) prefetch(blockIdx.x, b0);
-    for (int t = blockIdx.x; t < total; t += gridDim.x, it++) {
+    if (bid < total) prefetch(bid, b0);
+    for (int t = bid; t < total; t += nblk, it++) {
         C *cur = (it & 1) ? b1 : b0;
         cp_async_wait<0>();
         __syncthreads();
-        if (t + (int)gridDim.x < total) prefetch(t + gridDim.x, (it & 1) ? b0 : b1);
+        if (t + (int)nblk < total) prefetch(t + nblk, (it & 1) ? b0 : b1);
         const C *res = P::template fft2<DIR>(cur, scr, a, tw);
         long long c0;
         C *base = tile_base(t, c0);
@@ -537,7 +537,7 @@ __device__ __forceinline__ void pencil1_body(const EvalArgs<T> &a) {
 // Partials per block: [0] sum_G w |rho_hat|^2/G^2, [1] sum_G w G^2 |psi_hat|^2,
 // [2] sum_G w Re(conj(rho_hat) V_ext), [3] nonlocal energy in G space.
 template <typename T, class P, bool MGP, bool XS = false>
-__device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
+__device__ __forceinline__ void axis0_body(const EvalArgs<T> &a, const int bid, const int nblk) {
     typedef typename Vec2<T>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double sd[4 * 32];
@@ -572,7 +572,7 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
                 for (int m = 0; m < a.M; m++) order[q++] = CH_KNOT0 + m;
         }
     }
-    const long long c0 = (long long)blockIdx.x * TW;
+    const long long c0 = (long long)bid * TW;
     auto prefetch = [&](C *dst, int ch) {
         const C *src = a.chan + (size_t)ch * a.NH;
         for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
@@ -776,12 +776,12 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a) {
     double r[4] = {eH, eV, eP, eN};
     block_sum_n<4>(r, sd);
     if (threadIdx.x == 0)
-        for (int k = 0; k < 4; k++) a.part_ax0[4 * blockIdx.x + k] = r[k];
+        for (int k = 0; k < 4; k++) a.part_ax0[4 * bid + k] = r[k];
 }
 
 // ======================================================================= row inverse (C2R along n2) + s4 + V
 template <typename T, class P, bool XS = false>
-__device__ __forceinline__ void row_inv_body(const EvalArgs<T> &a) {
+__device__ __forceinline__ void row_inv_body(const EvalArgs<T> &a, const int bid, const int nblk) {
     typedef typename Vec2<T>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double sd[32];
@@ -802,7 +802,7 @@ __device__ __forceinline__ void row_inv_body(const EvalArgs<T> &a) {
     unsigned char *sj = (unsigned char *)(st + PP);
 
     const long long R = (long long)a.n0 * a.n1;
-    const long long row0 = 2LL * B * blockIdx.x;
+    const long long row0 = 2LL * B * bid;
     const bool lwt = (a.terms & 4u) && a.kernel == 0;
     const bool interp = a.nlpot == 1;
     const int M = a.M;
@@ -957,7 +957,7 @@ __device__ __forceinline__ void row_inv_body(const EvalArgs<T> &a) {
         }
     }
     const double eNL = block_sum(fNL.value(), sd);
-    if (threadIdx.x == 0) a.part_row[blockIdx.x] = eNL;
+    if (threadIdx.x == 0) a.part_row[bid] = eNL;
 }
 
 // ======================================================================= rows, channel-batched form
@@ -985,7 +985,7 @@ struct RowPolicy2 {
 };
 
 template <typename T, class Q>
-__device__ __forceinline__ void row_fwd2_body(const EvalArgs<T> &a) {
+__device__ __forceinline__ void row_fwd2_body(const EvalArgs<T> &a, const int bid, const int nblk) {
     typedef typename Vec2<T>::type C;
     constexpr int n = Q::N_, G = Q::G_, LD = Q::LD, NT = Q::NT_, E = Q::E, n2h = n / 2 + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -995,7 +995,7 @@ __device__ __forceinline__ void row_fwd2_body(const EvalArgs<T> &a) {
     __shared__ T sk[OFDFT_MAX_KNOTS], sdk[OFDFT_MAX_KNOTS];
     __shared__ int sch[kMaxChan], skpos;
     const long long R = (long long)a.n0 * a.n1;
-    const long long row0 = 2LL * blockIdx.x;
+    const long long row0 = 2LL * bid;
     const bool has1 = row0 + 1 < R;
     const bool nl = a.terms & 4u, lwt = nl && a.kernel == 0;
     const int M = a.M, nf = a.nfwd;
@@ -1099,7 +1099,7 @@ __device__ __forceinline__ void row_fwd2_body(const EvalArgs<T> &a) {
 }
 
 template <typename T, class Q>
-__device__ __forceinline__ void row_inv2_body(const EvalArgs<T> &a) {
+__device__ __forceinline__ void row_inv2_body(const EvalArgs<T> &a, const int bid, const int nblk) {
     typedef typename Vec2<T>::type C;
     constexpr int n = Q::N_, G = Q::G_, LD = Q::LD, NT = Q::NT_, E = Q::E, n2h = n / 2 + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1112,7 +1112,7 @@ __device__ __forceinline__ void row_inv2_body(const EvalArgs<T> &a) {
     __shared__ T sk[OFDFT_MAX_KNOTS], sdk[OFDFT_MAX_KNOTS];
     __shared__ int sch[kMaxChan], skind[kMaxChan], skpos;
     const long long R = (long long)a.n0 * a.n1;
-    const long long row0 = 2LL * blockIdx.x;
+    const long long row0 = 2LL * bid;
     const bool has1 = row0 + 1 < R;
     const bool nl = a.terms & 4u, lwt = nl && a.kernel == 0, interp = a.nlpot == 1;
     const int M = a.M, ni = a.ninv;
@@ -1310,7 +1310,7 @@ __device__ __forceinline__ void row_inv2_body(const EvalArgs<T> &a) {
     }
     if (lwt && interp) {                     // the only mode with a real-space E_NL
         const double eNL = block_sum(fNL.value(), sd);
-        if (threadIdx.x == 0) a.part_row[blockIdx.x] = eNL;
+        if (threadIdx.x == 0) a.part_row[bid] = eNL;
     }
 }
 
@@ -1318,13 +1318,13 @@ __device__ __forceinline__ void row_inv2_body(const EvalArgs<T> &a) {
 // FP64 energies from the per-block partials of the reciprocal-space kernel (and, for
 // the interpolated LWT mode, of the row kernel), summed in a fixed order.
 template <typename T>
-__global__ void __launch_bounds__(256) finalize_kernel(EvalArgs<T> a) {
+__device__ __forceinline__ void finalize_body(const EvalArgs<T> &a, const int bid, const int nblk) {
     // block k sums one kind of partial (0..3: the reciprocal-space kernel's E_H, E_vW,
     // E_PP and G-space E_NL sums; 4: the rows' real-space E_NL), so the FP64 work is
     // spread over five SMs; the last block to finish assembles the energies
     __shared__ double sd[32];
     __shared__ bool last;
-    const int k = blockIdx.x;
+    const int k = bid;
     const bool real_space = a.kernel == 0 && a.nlpot == 1;
     double acc = 0.0;
     if (k < 4) {
@@ -1337,7 +1337,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(EvalArgs<T> a) {
     if (threadIdx.x == 0) {
         sums[k] = acc;
         __threadfence();
-        last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
+        last = atomicAdd(a.ticket, 1u) == nblk - 1;
     }
     __syncthreads();
     if (!last || threadIdx.x != 0) return;
@@ -1360,32 +1360,92 @@ __global__ void __launch_bounds__(256) finalize_kernel(EvalArgs<T> a) {
 }
 
 // ======================================================================= kernel wrappers
+// Single evaluation: the arguments in the kernel's parameter space, block b = blockIdx.x.
+template <typename T, bool XS = false>
+__global__ void __launch_bounds__(256) stats_kernel(EvalArgs<T> a) {
+    stats_body<T, XS>(a, blockIdx.x, gridDim.x);
+}
+template <typename T>
+__global__ void __launch_bounds__(256) finalize_kernel(EvalArgs<T> a) {
+    finalize_body<T>(a, blockIdx.x, gridDim.x);
+}
 template <typename T, class P>
 __global__ void __launch_bounds__(P::max_threads, P::min_blocks) row_fwd_kernel(EvalArgs<T> a) {
-    row_fwd_body<T, P>(a);
+    row_fwd_body<T, P>(a, blockIdx.x, gridDim.x);
 }
 template <typename T, int DIR, class P>
 __global__ void __launch_bounds__(P::max_threads, P::min_blocks) pencil1_kernel(EvalArgs<T> a) {
-    pencil1_body<T, DIR, P>(a);
+    pencil1_body<T, DIR, P>(a, blockIdx.x, gridDim.x);
 }
 // MGP: the knots' kernels of Eq. MGP from the correction table (a separate instantiation,
 // so that the Wang-Teter form carries no trace of it)
 // XS: every energy term added in FP64 (the exact-sums test option; runtime-size kernels only)
 template <typename T, class P, bool MGP = false, bool XS = false>
 __global__ void __launch_bounds__(P::max_threads, P::min_blocks_ax0) axis0_kernel(EvalArgs<T> a) {
-    axis0_body<T, P, MGP, XS>(a);
+    axis0_body<T, P, MGP, XS>(a, blockIdx.x, gridDim.x);
 }
 template <typename T, class P, bool XS = false>
 __global__ void __launch_bounds__(P::max_threads, P::min_blocks) row_inv_kernel(EvalArgs<T> a) {
-    row_inv_body<T, P, XS>(a);
+    row_inv_body<T, P, XS>(a, blockIdx.x, gridDim.x);
 }
 template <typename T, class Q>
 __global__ void __launch_bounds__(Q::NT_, Q::min_blocks) row_fwd2_kernel(EvalArgs<T> a) {
-    row_fwd2_body<T, Q>(a);
+    row_fwd2_body<T, Q>(a, blockIdx.x, gridDim.x);
 }
 template <typename T, class Q>
 __global__ void __launch_bounds__(Q::NT_, Q::min_blocks) row_inv2_kernel(EvalArgs<T> a) {
-    row_inv2_body<T, Q>(a);
+    row_inv2_body<T, Q>(a, blockIdx.x, gridDim.x);
+}
+
+// Grouped: one launch runs a pass of K evaluations that share one launch geometry (the
+// snapshots of one grid shape in a batch).  The arguments of evaluation k sit at ga[k] in
+// global memory; block b works on evaluation b / bps as that evaluation's block b mod bps,
+// so every evaluation sees exactly the blocks, partial sums and reduction order of its
+// single launch (bit-identical results).
+#define OFDFT_GROUP_INDEX const int gk = blockIdx.x / bps, gb = blockIdx.x - gk * bps
+template <typename T, bool XS = false>
+__global__ void __launch_bounds__(256) stats_group(const EvalArgs<T> *__restrict__ ga, int bps) {
+    OFDFT_GROUP_INDEX;
+    stats_body<T, XS>(ga[gk], gb, bps);
+}
+template <typename T>
+__global__ void __launch_bounds__(256) finalize_group(const EvalArgs<T> *__restrict__ ga, int bps) {
+    OFDFT_GROUP_INDEX;
+    finalize_body<T>(ga[gk], gb, bps);
+}
+template <typename T, class P>
+__global__ void __launch_bounds__(P::max_threads, P::min_blocks) row_fwd_group(const EvalArgs<T> *__restrict__ ga,
+                                                                                int bps) {
+    OFDFT_GROUP_INDEX;
+    row_fwd_body<T, P>(ga[gk], gb, bps);
+}
+template <typename T, int DIR, class P>
+__global__ void __launch_bounds__(P::max_threads, P::min_blocks) pencil1_group(const EvalArgs<T> *__restrict__ ga,
+                                                                                int bps) {
+    OFDFT_GROUP_INDEX;
+    pencil1_body<T, DIR, P>(ga[gk], gb, bps);
+}
+template <typename T, class P, bool MGP = false>
+__global__ void __launch_bounds__(P::max_threads, P::min_blocks_ax0) axis0_group(const EvalArgs<T> *__restrict__ ga,
+                                                                                  int bps) {
+    OFDFT_GROUP_INDEX;
+    axis0_body<T, P, MGP, false>(ga[gk], gb, bps);
+}
+template <typename T, class P>
+__global__ void __launch_bounds__(P::max_threads, P::min_blocks) row_inv_group(const EvalArgs<T> *__restrict__ ga,
+                                                                                int bps) {
+    OFDFT_GROUP_INDEX;
+    row_inv_body<T, P, false>(ga[gk], gb, bps);
+}
+template <typename T, class Q>
+__global__ void __launch_bounds__(Q::NT_, Q::min_blocks) row_fwd2_group(const EvalArgs<T> *__restrict__ ga, int bps) {
+    OFDFT_GROUP_INDEX;
+    row_fwd2_body<T, Q>(ga[gk], gb, bps);
+}
+template <typename T, class Q>
+__global__ void __launch_bounds__(Q::NT_, Q::min_blocks) row_inv2_group(const EvalArgs<T> *__restrict__ ga, int bps) {
+    OFDFT_GROUP_INDEX;
+    row_inv2_body<T, Q>(ga[gk], gb, bps);
 }
 
 }  // namespace ofdft

@@ -12,6 +12,8 @@ template <typename T, int N, int E, int NSTAGE, int TW = 32, int MINB = 1> void 
     KernelCand c;
     c.recip.k = (const void *)recip_kernel<T, N, E, NSTAGE, false, TW, MINB>;
     c.recip.k_mgp = (const void *)recip_kernel<T, N, E, NSTAGE, true, TW, MINB>;
+    c.recip.g = (const void *)recip_group<T, N, E, NSTAGE, false, TW, MINB>;
+    c.recip.g_mgp = (const void *)recip_group<T, N, E, NSTAGE, true, TW, MINB>;
     c.recip.nt = S::NT;
     c.recip.per_sm = MINB;
     c.recip.tw = TW;

@@ -4,8 +4,8 @@
 // pseudopotential and von Weizsaecker products of Eq. efunc).
 //
 // Work unit: a tile of TW (32 or 16) consecutive columns c = (k1, k2) of the half
-// spectrum and all N values of k0.  MINB blocks per SM loop over the tiles t = blockIdx.x,
-// blockIdx.x + gridDim.x, ...; a single thread keeps NSTAGE channel tiles in
+// spectrum and all N values of k0.  MINB blocks per SM loop over the tiles t = b,
+// b + (blocks), ...; a single thread keeps NSTAGE channel tiles in
 // flight with cp.async.bulk.tensor copies (3-D tensor map over [channel][k0][c],
 // one mbarrier per stage, bounded waits), across tile boundaries.
 //
@@ -169,9 +169,9 @@ struct RecipOp {
     short store, m;
 };
 
-template <typename T, int N, int E, int NSTAGE, bool MGP, int TW = 32, int MINB = 1>
-__global__ void __launch_bounds__(TW * (N / E), MINB)
-    recip_kernel(const EvalArgs<T> a, const __grid_constant__ RecipMaps maps) {
+template <typename T, int N, int E, int NSTAGE, bool MGP, int TW>
+__device__ __forceinline__ void recip_body(const EvalArgs<T> &a, const RecipMaps &maps, const int bid,
+                                           const int nblk) {
     typedef typename Vec2<T>::type C;
     typedef RecipShape<T, N, E, NSTAGE, TW> S;
     constexpr int TC = S::TC, NT = S::NT, TILE = S::TILE, P = rs::npass(N, E);
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(TW * (N / E), MINB)
         for (int i = threadIdx.x; i < a.M; i += NT) sk[i] = a.knots_t[i];
     __syncthreads();
     const int nload = s_nload, nops = s_nops;
-    const int my_tiles = (int)blockIdx.x < ntile ? (ntile - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int my_tiles = bid < ntile ? (ntile - 1 - bid) / nblk + 1 : 0;
     const long long total = (long long)my_tiles * nload;
     long long issued = 0, cons = 0, pend = 0, L = 0;   // loads issued, released, read since the last barrier, next
     // thread 0: start loads while their stages are free
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(TW * (N / E), MINB)
         bool fenced = false;
         while (issued < total && issued < cons + NSTAGE) {
             const int ti = (int)(issued / nload), i = (int)(issued - (long long)ti * nload);
-            const int c0 = (blockIdx.x + ti * gridDim.x) * TW;
+            const int c0 = (bid + ti * nblk) * TW;
             const int st = (int)(issued % NSTAGE);
             if (!fenced) {
                 fence_proxy_async_smem();           // the stage was last read through the generic proxy
@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(TW * (N / E), MINB)
     C v[E], Rr[E], A[E];
     bool xsel = false;                         // exchange tile of the next exchange
     for (int ti = 0; ti < my_tiles && !failed; ti++) {
-        const long long col = (long long)(blockIdx.x + ti * gridDim.x) * TW + w;
+        const long long col = (long long)(bid + ti * nblk) * TW + w;
         // this thread's column: its G components, half-spectrum weight, and |G| at its frequencies
         T cw, gn[E];
         {
@@ -442,7 +442,26 @@ __global__ void __launch_bounds__(TW * (N / E), MINB)
     double r4[4] = {eH, eV, eP, eN};
     block_sum_n<4>(r4, sd);
     if (threadIdx.x == 0)
-        for (int k = 0; k < 4; k++) a.part_ax0[4 * blockIdx.x + k] = r4[k];
+        for (int k = 0; k < 4; k++) a.part_ax0[4 * bid + k] = r4[k];
+}
+
+// single evaluation (tensor maps in the parameter space)
+template <typename T, int N, int E, int NSTAGE, bool MGP, int TW = 32, int MINB = 1>
+__global__ void __launch_bounds__(TW * (N / E), MINB)
+    recip_kernel(const EvalArgs<T> a, const __grid_constant__ RecipMaps maps) {
+    recip_body<T, N, E, NSTAGE, MGP, TW>(a, maps, blockIdx.x, gridDim.x);
+}
+
+// grouped (see the grouped wrappers of kernels.cuh): evaluation k's arguments at ga[k], its
+// tensor maps at maps.m[k] (parameter space, at most kGroupMax evaluations per launch)
+struct RecipMapsGroup {
+    RecipMaps m[kGroupMax];
+};
+template <typename T, int N, int E, int NSTAGE, bool MGP, int TW = 32, int MINB = 1>
+__global__ void __launch_bounds__(TW * (N / E), MINB)
+    recip_group(const EvalArgs<T> *__restrict__ ga, int bps, const __grid_constant__ RecipMapsGroup maps) {
+    OFDFT_GROUP_INDEX;
+    recip_body<T, N, E, NSTAGE, MGP, TW>(ga[gk], maps.m[gk], gb, bps);
 }
 
 }  // namespace ofdft

@@ -141,3 +141,77 @@ def test_batched_equals_single_evaluations(graph):
             # batched forces take rho_hat from the evaluation's own transform (the single call
             # transforms rho itself): the same FP32-mixed quantity up to FP32 rounding
             assert np.max(np.abs(Fs[i] - Fsg)) <= 1e-5 * max(1.0, np.max(np.abs(Fsg))), i
+
+
+def _snapshot(s, n):
+    wl = W.workload("fcc-al-108-snap", s)
+    cell, pos = wl["cell"], wl["positions"]
+    rho = W.renormalise(W.apply_noise(W.gaussian_density(cell, (n, n, n), pos, 3.0, 1.0), 0.02, s), cell,
+                        wl["n_electrons"])
+    g = ofd.Grid(cell, (n, n, n))
+    g.set_ions(pos, wl["species"], wl["Z"], wl["rc"])
+    return g, torch.from_numpy(rho.astype(np.float32)).cuda()
+
+
+@pytest.mark.parametrize("graph", [1, 0])
+@pytest.mark.parametrize("grouped", [1, 0])
+def test_grouped_batch_equals_single_evaluations(graph, grouped):
+    """Snapshots of repeated and uneven sizes: grouped launches (one launch per pass over the
+    snapshots of one launch geometry) give bit-identical energies and potentials to single
+    calls.  64^3 runs the persistent reciprocal-space kernel (tensor maps of every snapshot in
+    one launch), 80^3 the size-specialised tile kernels, 48^3 the runtime-size kernels; 36^3
+    stays a single snapshot."""
+    sizes = [64, 48, 80, 64, 36, 48, 80, 64, 48]
+    f = ofd.Functional(n_knots=16)
+    grids, rhos, singles = [], [], []
+    for s, n in enumerate(sizes):
+        g, r = _snapshot(s, n)
+        if n == 64:
+            g.set_option(L.OPTION_PICK_RECIP, 1)        # a persistent-kernel configuration
+        grids.append(g)
+        rhos.append(r)
+        E, V = g.energy_potential(r, f)
+        singles.append((E, V, g.forces(r)))
+    grids[0].set_option(L.OPTION_BATCH_GRAPH, graph)
+    grids[0].set_option(L.OPTION_BATCH_GROUPED, grouped)
+    Vbuf = [torch.empty_like(r) for r in rhos]
+    for rep in range(3):
+        E, Vs, Fs = ofd.energy_potential_batched(grids, rhos, f, want_potential=True, want_forces=True, V_out=Vbuf)
+        for i, (Es, Vsg, Fsg) in enumerate(singles):
+            assert np.array_equal(E[i], np.array([Es[k] for k in ofd.ENERGY_KEYS])), (rep, i)
+            assert torch.equal(Vs[i], Vsg), (rep, i)
+            assert np.max(np.abs(Fs[i] - Fsg)) <= 1e-5 * max(1.0, np.max(np.abs(Fsg))), (rep, i)
+    rep_s = grids[0].batch_report()
+    # (the 64^3 grids were tuned at different times; their plans still match)
+    if grouped:
+        assert "4 launch groups" in rep_s and "64x64x64 x3 (grouped, persistent recip)" in rep_s, rep_s
+        assert "48x48x48 x3 (grouped)" in rep_s and "36x36x36 x1;" in rep_s, rep_s
+    else:
+        assert "9 launch groups" in rep_s, rep_s
+    assert ("CUDA graph" in rep_s) == bool(graph), rep_s
+
+
+def test_grouped_batch_splits_past_the_group_limit():
+    """34 snapshots of one shape: two grouped launches per pass (32 + 2), every snapshot
+    bit-identical to its single evaluation; a second call with new potential buffers makes a
+    new plan."""
+    f = ofd.Functional(n_knots=8)
+    grids, rhos, singles = [], [], []
+    for s in range(34):
+        g, r = _snapshot(s % 64, 24)
+        grids.append(g)
+        rhos.append(r)
+        singles.append(g.energy_potential(r, f))
+    for call in range(2):
+        E, Vs, _ = ofd.energy_potential_batched(grids, rhos, f, want_potential=True)
+        for i, (Es, Vsg) in enumerate(singles):
+            assert np.array_equal(E[i], np.array([Es[k] for k in ofd.ENERGY_KEYS])), (call, i)
+            assert torch.equal(Vs[i], Vsg), (call, i)
+    assert "2 launch groups: 24x24x24 x32 (grouped), 24x24x24 x2 (grouped)" in grids[0].batch_report()
+
+
+def test_batch_with_a_repeated_grid_is_rejected():
+    g, r = _snapshot(0, 32)
+    with pytest.raises(ofd.OFDFTError) as e:
+        ofd.energy_potential_batched([g, g], [r, r], ofd.Functional(n_knots=8))
+    assert e.value.status == L.OFDFT_ERR_INVALID_ARG
