@@ -126,9 +126,11 @@ struct ofdft_grid {
     bool vext_fresh32 = false, vext_fresh64 = false;
     double2 *ph = nullptr;       // phase tables [n_ions][n0 + n1 + n2h]
     float2 *ph32 = nullptr;      // the same rounded to FP32 (FP32-mixed kernels)
-    float4 *gc = nullptr;        // per-species G tables of the FP32-mixed force kernel
-    long long gc_len = 0;
-    bool gc_fresh = false;       // the tables match the current ions (species, Z, rc)
+    float *gf = nullptr;         // per-species form-factor tables of the FP32-mixed force kernel
+    long long gf_len = 0;
+    bool gf_fresh = false;       // the tables match the current ions (species, Z, rc)
+    int *d_sp_ions = nullptr;    // the ions grouped by species (device), the groups' offsets (host)
+    std::vector<int> sp_off;
     // smooth PME (ofdft_set_ions_pme): order > 0 selects it for V_ext(G) and forces
     int pme_order = 0;
     double2 *pmeB = nullptr;               // conj b_a tables [n0 | n1 | n2h]
@@ -1057,18 +1059,19 @@ template <typename T> int forces_pme(ofdft_grid *g, Workspace<T> &w, const T *rh
 
 // ---------------------------------------------------------------- forces
 // Force kernels in use for this grid/precision and the size of their partials.
-template <typename T> void force_layout(ofdft_grid *g, bool &fast, int &nchunk, int &nsp) {
+// FP32-mixed direct forces: the separable kernel, partials [n_ions][row-tile blocks][3]; FP64 (and
+// FP32 past 64 Mi half-spectrum points): one block per (ion, chunk), partials [n_ions][16][3]
+template <typename T> void force_layout(ofdft_grid *g, bool &fast, int &nchunk) {
     fast = sizeof(T) == 4 && g->NH <= (64LL << 20);
-    nchunk = fast ? std::max(16, 1024 / ((g->n_ions + 7) / 8)) : 16;
-    nsp = fast ? g->n_species : 1;
+    nchunk = fast ? forces_sep_blocks(ion_args(g), g->nsm) : 16;
 }
 
 // device buffers of the force computation (outside any stream capture)
 template <typename T> int ensure_force_buffers(ofdft_grid *g) {
     bool fast;
-    int nchunk, nsp;
-    force_layout<T>(g, fast, nchunk, nsp);
-    const size_t plen = (size_t)nsp * g->n_ions * nchunk * 3;
+    int nchunk;
+    force_layout<T>(g, fast, nchunk);
+    const size_t plen = (size_t)g->n_ions * nchunk * 3;
     if (g->pme_order == 0 && plen > g->fpart_len) {
         cudaFree(g->fpart);
         g->fpart = nullptr;
@@ -1077,19 +1080,18 @@ template <typename T> int ensure_force_buffers(ofdft_grid *g) {
         g->fpart_len = plen;
         g->generation++;
     }
-    if (g->pme_order == 0 && fast && g->gc_len < (long long)g->n_species * g->NH) {
-        CK(prepare_force_kernels(), "force kernel attributes");
-        cudaFree(g->gc);
-        g->gc = nullptr;
-        g->gc_len = 0;
-        CK(gmalloc(g, &g->gc, 2 * (size_t)g->n_species * g->NH * sizeof(float4)), "cudaMalloc force tables");
-        g->gc_len = (long long)g->n_species * g->NH;
-        g->gc_fresh = false;
+    if (g->pme_order == 0 && fast && g->gf_len < (long long)g->n_species * g->NH) {
+        cudaFree(g->gf);
+        g->gf = nullptr;
+        g->gf_len = 0;
+        CK(gmalloc(g, &g->gf, (size_t)g->n_species * g->NH * sizeof(float)), "cudaMalloc force tables");
+        g->gf_len = (long long)g->n_species * g->NH;
+        g->gf_fresh = false;
         g->generation++;
     }
-    if (g->pme_order == 0 && fast && !g->gc_fresh) {
-        CK(launch_force_tables(ion_args(g), g->gc, g->stream), "force tables");
-        g->gc_fresh = true;
+    if (g->pme_order == 0 && fast && !g->gf_fresh) {
+        CK(launch_force_tables(ion_args(g), g->gf, g->stream), "force tables");
+        g->gf_fresh = true;
     }
     if (g->F_len < g->n_ions) {
         cudaFree(g->F_dev);
@@ -1122,14 +1124,18 @@ template <typename T> int forces_enqueue(ofdft_grid *g, const T *rho, const type
         rhohat = w.chan;
     }
     bool fast;
-    int nchunk, nsp;
-    force_layout<T>(g, fast, nchunk, nsp);
+    int nchunk;
+    force_layout<T>(g, fast, nchunk);
     IonArgs ia = ion_args(g);
-    if (fast)
-        CK(launch_forces_fast(ia, (const float2 *)rhohat, g->ph32, g->gc, g->fpart, nchunk, g->stream), "forces kernel");
-    else
+    if (fast) {
+        CK(launch_forces_sep(ia, (const float2 *)rhohat, g->ph32, g->gf, g->d_sp_ions, g->sp_off.data(), nchunk,
+                             g->fpart, g->stream),
+           "forces kernel");
+        CK(launch_reduce_force_sep(ia, g->fpart, nchunk, g->F_dev, g->stream), "force reduction");
+    } else {
         CK(launch_forces<C>(ia, rhohat, g->fpart, nchunk, g->stream), "forces kernel");
-    CK(launch_reduce_force_partials(g->fpart, nsp, g->n_ions, nchunk, g->F_dev, g->stream), "force reduction");
+        CK(launch_reduce_force_partials(g->fpart, g->n_ions, nchunk, g->F_dev, g->stream), "force reduction");
+    }
     return OFDFT_OK;
 }
 
@@ -1279,12 +1285,12 @@ int ewald_impl(ofdft_grid *g, double *E_out, double *F_out) {
             }
         } else {
             bool fast;
-            int nchunk, nsp;
-            force_layout<double>(g, fast, nchunk, nsp);
+            int nchunk;
+            force_layout<double>(g, fast, nchunk);
             IonArgs ia = ion_args(g);
             ia.charge_ff = 1;
             CK(launch_forces<C>(ia, sz, g->fpart, nchunk, st), "Ewald forces");
-            CK(launch_reduce_force_partials(g->fpart, nsp, n, nchunk, Frec, st), "force reduction");
+            CK(launch_reduce_force_partials(g->fpart, n, nchunk, Frec, st), "force reduction");
         }
     }
     std::vector<double> F2(F_out ? 6 * (size_t)n : 0);
@@ -2513,7 +2519,8 @@ int ofdft_grid_destroy(ofdft_grid *g) {
     free_ws(g->w64);
     cudaFree(g->ph);
     cudaFree(g->ph32);
-    cudaFree(g->gc);
+    cudaFree(g->gf);
+    cudaFree(g->d_sp_ions);
     cudaFree(g->fpart);
     cudaFree(g->F_dev);
     cudaFreeHost(g->F_pinned);
@@ -2554,14 +2561,17 @@ int store_ions(ofdft_grid *g, const ofdft_ions *ions, const ofdft_species *sp) {
         cudaFree(g->ph32);
         cudaFree(g->d_pos);
         cudaFree(g->d_species);
+        cudaFree(g->d_sp_ions);
         cudaFree(g->d_Z);
         cudaFree(g->d_rc);
         g->ph = nullptr;
         g->ph32 = nullptr;
         g->d_pos = nullptr;
         g->d_species = nullptr;
+        g->d_sp_ions = nullptr;
         g->d_Z = g->d_rc = nullptr;
         CK(gmalloc(g, &g->d_species, n * sizeof(int)), "cudaMalloc species");
+        CK(gmalloc(g, &g->d_sp_ions, n * sizeof(int)), "cudaMalloc species lists");
         CK(gmalloc(g, &g->d_Z, sp->n_species * sizeof(double)), "cudaMalloc Z");
         CK(gmalloc(g, &g->d_rc, sp->n_species * sizeof(double)), "cudaMalloc rc");
     }
@@ -2569,7 +2579,7 @@ int store_ions(ofdft_grid *g, const ofdft_ions *ions, const ofdft_species *sp) {
     // the force tables depend on the species' Z and rc only (not on positions)
     if (g->n_species != sp->n_species || !std::equal(g->Z.begin(), g->Z.end(), sp->Z) ||
         !std::equal(g->rc.begin(), g->rc.end(), sp->rc))
-        g->gc_fresh = false;
+        g->gf_fresh = false;
     g->n_species = sp->n_species;
     g->pos.assign(ions->pos, ions->pos + 3 * (size_t)n);
     g->species.assign(ions->species, ions->species + n);
@@ -2577,7 +2587,12 @@ int store_ions(ofdft_grid *g, const ofdft_ions *ions, const ofdft_species *sp) {
     g->rc.assign(sp->rc, sp->rc + sp->n_species);
     g->species_count.assign(sp->n_species, 0);
     for (int i = 0; i < n; i++) g->species_count[g->species[i]]++;
+    g->sp_off.assign(sp->n_species + 1, 0);
+    for (int s = 0; s < sp->n_species; s++) g->sp_off[s + 1] = g->sp_off[s] + g->species_count[s];
+    std::vector<int> lists(n), fill(g->sp_off.begin(), g->sp_off.end() - 1);
+    for (int i = 0; i < n; i++) lists[fill[g->species[i]]++] = i;
     CK(cudaMemcpy(g->d_species, g->species.data(), n * sizeof(int), cudaMemcpyHostToDevice), "upload species");
+    CK(cudaMemcpy(g->d_sp_ions, lists.data(), n * sizeof(int), cudaMemcpyHostToDevice), "upload species lists");
     CK(cudaMemcpy(g->d_Z, g->Z.data(), g->n_species * sizeof(double), cudaMemcpyHostToDevice), "upload Z");
     CK(cudaMemcpy(g->d_rc, g->rc.data(), g->n_species * sizeof(double), cudaMemcpyHostToDevice), "upload rc");
     g->have_ions = true;

@@ -24,20 +24,22 @@ struct IonArgs {
 cudaError_t launch_vext(const IonArgs &a, double2 *vext64, float2 *vext32, cudaStream_t s,
                         const float2 *ph32 = nullptr);
 cudaError_t launch_round_phases(const double2 *in, float2 *out, long long n, cudaStream_t s);
-// shared-memory limit of the FP32-mixed force kernel (call once per device, outside stream capture)
-cudaError_t prepare_force_kernels();
-// FP32-mixed forces: gc = the per-species tables of launch_force_tables ([n_species][2 NH] float4),
-// partials [n_species][n_ions][nchunk][3]
-cudaError_t launch_force_tables(const IonArgs &a, float4 *gc, cudaStream_t st);
-cudaError_t launch_forces_fast(const IonArgs &a, const float2 *rhohat, const float2 *ph32, const float4 *gc,
-                               double *partials, int nchunk, cudaStream_t st);
+// FP32-mixed forces (separable form): gf = the per-species tables of launch_force_tables
+// ([n_species][NH] floats: -w v_s(|G|)); sp_ions = the ions grouped by species, sp_off (HOST)
+// the groups' offsets; partials [n_ions][nrb][3] (the S_a sums per row-tile block), then
+// launch_reduce_force_sep assembles F_I = sum_a b_a S_a(I)
+cudaError_t launch_force_tables(const IonArgs &a, float *gf, cudaStream_t st);
+int forces_sep_blocks(const IonArgs &a, int nsm);
+cudaError_t launch_forces_sep(const IonArgs &a, const float2 *rhohat, const float2 *ph32, const float *gf,
+                              const int *sp_ions, const int *sp_off, int nrb, double *partials, cudaStream_t st);
+cudaError_t launch_reduce_force_sep(const IonArgs &a, const double *part, int nrb, double *F, cudaStream_t s);
 
 // forces from the normalised half spectrum rho_hat (FP64 or FP32 complex)
 template <typename C>
 cudaError_t launch_forces(const IonArgs &a, const C *rhohat, double *partials, int nchunk, cudaStream_t s);
 
-cudaError_t launch_reduce_force_partials(const double *part, int nsp, int n_ions, int nchunk, double *F,
-                                         cudaStream_t s);
+// F = the partials [n_ions][nchunk][3] summed over the chunks in order
+cudaError_t launch_reduce_force_partials(const double *part, int n_ions, int nchunk, double *F, cudaStream_t s);
 
 // plain forward FFT along n0 of a half spectrum (in place), used by forces
 template <typename T>

@@ -157,15 +157,20 @@ cudaError_t launch_forces(const IonArgs &a, const C *rhohat, double *partials, i
 template cudaError_t launch_forces<float2>(const IonArgs &, const float2 *, double *, int, cudaStream_t);
 template cudaError_t launch_forces<double2>(const IonArgs &, const double2 *, double *, int, cudaStream_t);
 
-// Forces, FP32-mixed path.  Per G (once, not per ion): c(G) = -w v_s(|G|) conj(rho_hat)
-// and G itself in FP32.  Then block (chunk, ion group of 8): each thread walks its
-// G values, forms e^{-iG.R_I} from the FP32 phase tables and accumulates
-// G Im[c e^{-iG.R}] in FP32 over 16 consecutive G before adding to FP64.
-// The static part of the FP32-mixed force sum for species s, once per set of ions: per point of
-// the half spectrum, G (FP32) with the point's k0, and the weighted form factor w v_s(|G|)
-// (w = 1 on the k2 = 0 and n2/2 planes, else 2; FP64, rounded once) with k1 and k2 (the
-// phase-table indices, so that the force kernel does no division per point).
-__global__ void __launch_bounds__(256) force_table_kernel(IonArgs a, float4 *gc, int s) {
+// Forces, FP32-mixed path.  With G = sum_a m_a b_a (b_a: the rows of bvec, 2 pi times the
+// reciprocal vectors), the force on ion I of species s is
+//   F_I = sum_a b_a S_a(I),   S_a(I) = sum_G m_a Im[c(G) e^{-iG.R_I}],
+//   c(G) = -w v_s(|G|) conj(rho_hat(G))   (w = 1 on the k2 = 0 and n2/2 planes, else 2).
+// The phase factorises over the axes, e^{-iG.R} = P0(k0) P1(k1) P2(k2), so with the rows
+// r = (k0, k1) of the half spectrum
+//   U_I(r) = sum_k2 c(r, k2) P2_I(k2),   V_I(r) = sum_k2 k2 c(r, k2) P2_I(k2)
+// (two complex products [rows x k2] x [k2 x ions]) and
+//   S_0 += m0 Im[P01 U],  S_1 += m1 Im[P01 U],  S_2 += Im[P01 V],   P01 = P0(k0) P1(k1).
+// The first step carries all the work: 16 FP32 operations per (row, k2, ion), as packed
+// two-ion FP32x2 FMAs from register tiles; the second is once per (row, ion).
+
+// the static part of c for species s, once per set of ions: gf[e] = -w v_s(|G|) (FP64, rounded once)
+__global__ void __launch_bounds__(256) force_table_kernel(IonArgs a, float *gf, int s) {
     const long long NH = (long long)a.n0 * a.n1 * a.n2h;
     const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= NH) return;
@@ -178,173 +183,191 @@ __global__ void __launch_bounds__(256) force_table_kernel(IonArgs a, float4 *gc,
         const double w = (k2 == 0 || (a.n2 % 2 == 0 && 2 * k2 == a.n2)) ? 1.0 : 2.0;
         f = (float)(-w * pp_form(q2, a.Z[s], a.rc[s]));
     }
-    gc[2 * e] = make_float4((float)gx, (float)gy, (float)gz, __int_as_float(k0));
-    gc[2 * e + 1] = make_float4(f, 0.f, __int_as_float(k1), __int_as_float(k2));
+    gf[e] = f;
 }
 
-cudaError_t launch_force_tables(const IonArgs &a, float4 *gc, cudaStream_t st) {
+cudaError_t launch_force_tables(const IonArgs &a, float *gf, cudaStream_t st) {
     const long long NH = (long long)a.n0 * a.n1 * a.n2h;
     for (int s = 0; s < a.n_species; s++)
-        force_table_kernel<<<(unsigned)((NH + 255) / 256), 256, 0, st>>>(a, gc + (size_t)s * 2 * NH, s);
+        force_table_kernel<<<(unsigned)((NH + 255) / 256), 256, 0, st>>>(a, gf + (size_t)s * NH, s);
     return cudaGetLastError();
 }
 
-// STAGE: the block's 8 ions' phase tables are first copied into shared memory, by pairs of
-// ions: entry k of table a (a = 0, 1, 2 for the three axes) of pair p holds
-// (re_I, re_J, im_I, im_J), so that every product of the G loop is one packed two-wide FP32
-// instruction for two ions.  Without STAGE the tables are read from global memory.
-template <bool STAGE>
-__global__ void __launch_bounds__(256) forces_fast_kernel(IonArgs a, const float2 *ph32, const float4 *gc,
-                                                          const float2 *rh, int s, double *part, int nchunk) {
-    extern __shared__ float4 sph4[];
-    const int chunk = blockIdx.x, g0 = blockIdx.y * 8;
-    const long long NH = (long long)a.n0 * a.n1 * a.n2h;
-    const long long per = (NH + nchunk - 1) / nchunk;
-    const long long e0 = chunk * per, e1 = (e0 + per < NH) ? e0 + per : NH;
+// Block: kFR rows x kFI ions of one species (its ions listed in ions[0, nion)), looping over
+// the row tiles blockIdx.x, blockIdx.x + gridDim.x, ...; k2 is staged kFK at a time.  Thread
+// (tr, ti) = (threadIdx.x / 16, threadIdx.x % 16) owns rows 4 tr .. 4 tr + 3 and ions 4 ti ..
+// 4 ti + 3 of the tile (two pairs, each pair packed (I, J) in FP32x2).  U and V are summed in
+// FP32 over k2; the second step in FP32 over the thread's 4 rows, then FP64.
+constexpr int kFR = 64, kFI = 64, kFK = 32;
+__global__ void __launch_bounds__(256) forces_sep_kernel(IonArgs a, const float2 *ph32, const float *gf,
+                                                         const float2 *rh, const int *ions, int nion, double *part) {
+    __shared__ __align__(16) float2 cs[kFK][kFR + 2];          // c(r, k2), [k2][row] (padded rows)
+    __shared__ __align__(16) float4 ps[kFK][kFI / 2 + 1];      // P2 of ion pairs: (re_I, re_J, im_I, im_J)
+    __shared__ double red[8][kFI][3];
+    const int ti = threadIdx.x & 15, tr = threadIdx.x >> 4;
+    const int rows = a.n0 * a.n1, n2h = a.n2h;
+    const int ion0 = blockIdx.y * kFI;
     const float2 *P0 = ph32, *P1 = ph32 + (size_t)a.n_ions * a.n0, *P2 = P1 + (size_t)a.n_ions * a.n1;
-    const int Lt = a.n0 + a.n1 + a.n2h;
-    // the phase of axis table entry k (k < n0: axis 0; then n1 entries of axis 1; then axis 2) of ion I
-    auto phase = [&](int I, int k) -> float2 {
-        if (I >= a.n_ions || a.species[I] != s) return make_float2(0.f, 0.f);
-        if (k < a.n0) return P0[(size_t)I * a.n0 + k];
-        if (k < a.n0 + a.n1) return P1[(size_t)I * a.n1 + (k - a.n0)];
-        return P2[(size_t)I * a.n2h + (k - a.n0 - a.n1)];
-    };
-    if (STAGE) {
-        for (int t = threadIdx.x; t < 4 * Lt; t += blockDim.x) {
-            const int p = t / Lt, k = t - p * Lt;
-            const float2 u = phase(g0 + 2 * p, k), v = phase(g0 + 2 * p + 1, k);
-            sph4[t] = make_float4(u.x, v.x, u.y, v.y);
-        }
-        __syncthreads();
-    }
-    double F[8][3];
-    float2 f32[4][3];
+    // this thread's four ions (global indices; -1 past the species' list)
+    int myI[4];
 #pragma unroll
-    for (int q = 0; q < 8; q++)
+    for (int q = 0; q < 4; q++) myI[q] = (ion0 + 4 * ti + q < nion) ? ions[ion0 + 4 * ti + q] : -1;
+    double S[4][3];
 #pragma unroll
-        for (int d = 0; d < 3; d++) F[q][d] = 0.0;
+    for (int q = 0; q < 4; q++) S[q][0] = S[q][1] = S[q][2] = 0.0;
+    const int ntile = (rows + kFR - 1) / kFR;
+    for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+        const int r0 = tile * kFR;
+        float2 U[4][2][2], V[4][2][2];                         // [row][pair][re, im] (FP32x2 over the pair)
 #pragma unroll
-    for (int p = 0; p < 4; p++)
+        for (int j = 0; j < 4; j++)
 #pragma unroll
-        for (int d = 0; d < 3; d++) f32[p][d] = make_float2(0.f, 0.f);
-    // the block's ion pairs that hold an ion of this species
-    unsigned live = 0;
-    for (int p = 0; p < 4; p++)
-        for (int h = 0; h < 2; h++) {
-            const int I = g0 + 2 * p + h;
-            if (I < a.n_ions && a.species[I] == s) live |= 1u << p;
-        }
-    int cnt = 0;
-    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-        const float4 G = gc[2 * e], c4 = gc[2 * e + 1];
-        const int k0 = __float_as_int(G.w), k1 = __float_as_int(c4.z), k2 = __float_as_int(c4.w);
-        const float2 r = rh[e];
-        // c = w v_s(|G|) conj(rho_hat)
-        const float2 cr = make_float2(c4.x * r.x, c4.x * r.x), ci = make_float2(-c4.x * r.y, -c4.x * r.y);
-        const float2 gx = make_float2(G.x, G.x), gy = make_float2(G.y, G.y), gz = make_float2(G.z, G.z);
-#pragma unroll
-        for (int p = 0; p < 4; p++) {
-            if (!((live >> p) & 1u)) continue;
-            float4 w0, w1, w2;
-            if (STAGE) {
-                const float4 *row = sph4 + p * Lt;
-                w0 = row[k0];
-                w1 = row[a.n0 + k1];
-                w2 = row[a.n0 + a.n1 + k2];
-            } else {
-                auto pair = [&](int k) {
-                    const float2 u = phase(g0 + 2 * p, k), v = phase(g0 + 2 * p + 1, k);
-                    return make_float4(u.x, v.x, u.y, v.y);
-                };
-                w0 = pair(k0);
-                w1 = pair(a.n0 + k1);
-                w2 = pair(a.n0 + a.n1 + k2);
-            }
-            // the two ions' phases e^{-iG.R} = P0 P1 P2, by components (re, im) of (I, J)
-            const float2 r0 = make_float2(w0.x, w0.y), i0 = make_float2(w0.z, w0.w);
-            const float2 r1 = make_float2(w1.x, w1.y), i1 = make_float2(w1.z, w1.w);
-            const float2 r2 = make_float2(w2.x, w2.y), i2 = make_float2(w2.z, w2.w);
-            const float2 rx = __ffma2_rn(r0, r1, __fmul2_rn(i0, make_float2(-i1.x, -i1.y)));
-            const float2 ry = __ffma2_rn(r0, i1, __fmul2_rn(i0, r1));
-            const float2 px = __ffma2_rn(rx, r2, __fmul2_rn(ry, make_float2(-i2.x, -i2.y)));
-            const float2 py = __ffma2_rn(rx, i2, __fmul2_rn(ry, r2));
-            const float2 im = __ffma2_rn(cr, py, __fmul2_rn(ci, px));          // Im(c p)
-            f32[p][0] = __ffma2_rn(im, gx, f32[p][0]);
-            f32[p][1] = __ffma2_rn(im, gy, f32[p][1]);
-            f32[p][2] = __ffma2_rn(im, gz, f32[p][2]);
-        }
-        if (++cnt == 16) {                               // FP32 over 16 G, then FP64
-            cnt = 0;
-#pragma unroll
-            for (int p = 0; p < 4; p++)
-#pragma unroll
-                for (int d = 0; d < 3; d++) {
-                    F[2 * p][d] += (double)f32[p][d].x;
-                    F[2 * p + 1][d] += (double)f32[p][d].y;
-                    f32[p][d] = make_float2(0.f, 0.f);
+            for (int p = 0; p < 2; p++) U[j][p][0] = U[j][p][1] = V[j][p][0] = V[j][p][1] = make_float2(0.f, 0.f);
+        for (int kc = 0; kc < n2h; kc += kFK) {
+            __syncthreads();                                   // the previous chunk is consumed
+            for (int idx = threadIdx.x; idx < kFR * kFK; idx += 256) {
+                const int i = idx / kFK, k = idx - i * kFK;
+                float2 c = make_float2(0.f, 0.f);
+                if (r0 + i < rows && kc + k < n2h) {
+                    const long long e = (long long)(r0 + i) * n2h + kc + k;
+                    const float f = gf[e];
+                    const float2 r = rh[e];
+                    c = make_float2(f * r.x, -f * r.y);
                 }
-        }
-    }
-    // block sums: warp sums in FP32 (32 values each), then the warps in FP64 -- 24 full FP64
-    // block reductions per block had kept the FP64 pipe half busy
-    __shared__ double wsum[24][8];                     // (blocks of 256 threads: 8 warps)
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+                cs[k][i] = c;
+            }
+            for (int idx = threadIdx.x; idx < (kFI / 2) * kFK; idx += 256) {
+                const int pp = idx / kFK, k = idx - pp * kFK;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (kc + k < n2h) {
+                    const int t0 = ion0 + 2 * pp, t1 = t0 + 1;
+                    const float2 u = t0 < nion ? P2[(size_t)ions[t0] * n2h + kc + k] : make_float2(0.f, 0.f);
+                    const float2 w = t1 < nion ? P2[(size_t)ions[t1] * n2h + kc + k] : make_float2(0.f, 0.f);
+                    v = make_float4(u.x, w.x, u.y, w.y);
+                }
+                ps[k][pp] = v;
+            }
+            __syncthreads();
+            const int kn = min(kFK, n2h - kc);
+#pragma unroll 2
+            for (int k = 0; k < kn; k++) {
+                const float4 c01 = *reinterpret_cast<const float4 *>(&cs[k][4 * tr]);
+                const float4 c23 = *reinterpret_cast<const float4 *>(&cs[k][4 * tr + 2]);
+                const float4 pa = ps[k][2 * ti], pb = ps[k][2 * ti + 1];
+                const float kf = (float)(kc + k);
+                const float cr[4] = {c01.x, c01.z, c23.x, c23.z}, ci[4] = {c01.y, c01.w, c23.y, c23.w};
+                const float2 Pr[2] = {make_float2(pa.x, pa.y), make_float2(pb.x, pb.y)};
+                const float2 Pi[2] = {make_float2(pa.z, pa.w), make_float2(pb.z, pb.w)};
 #pragma unroll
-    for (int q = 0; q < 8; q++)
+                for (int j = 0; j < 4; j++) {
+                    const float2 a_r = make_float2(cr[j], cr[j]), a_i = make_float2(ci[j], ci[j]);
+                    const float2 n_i = make_float2(-ci[j], -ci[j]);
+                    const float br = kf * cr[j], bi = kf * ci[j];
+                    const float2 b_r = make_float2(br, br), b_i = make_float2(bi, bi), m_i = make_float2(-bi, -bi);
+#pragma unroll
+                    for (int p = 0; p < 2; p++) {
+                        // (c P2): re = cr Pr - ci Pi, im = cr Pi + ci Pr (two ions at once)
+                        U[j][p][0] = __ffma2_rn(n_i, Pi[p], __ffma2_rn(a_r, Pr[p], U[j][p][0]));
+                        U[j][p][1] = __ffma2_rn(a_i, Pr[p], __ffma2_rn(a_r, Pi[p], U[j][p][1]));
+                        V[j][p][0] = __ffma2_rn(m_i, Pi[p], __ffma2_rn(b_r, Pr[p], V[j][p][0]));
+                        V[j][p][1] = __ffma2_rn(b_i, Pr[p], __ffma2_rn(b_r, Pi[p], V[j][p][1]));
+                    }
+                }
+            }
+        }
+        // second step: the rows' P01 and the three sums of each of the thread's ions
+        float s32[4][3];
+#pragma unroll
+        for (int q = 0; q < 4; q++) s32[q][0] = s32[q][1] = s32[q][2] = 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int r = r0 + 4 * tr + j;
+            if (r >= rows) continue;
+            const int k0 = r / a.n1, k1 = r - k0 * a.n1;
+            const float m0 = (float)(k0 <= a.n0 / 2 ? k0 : k0 - a.n0), m1 = (float)(k1 <= a.n1 / 2 ? k1 : k1 - a.n1);
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                if (myI[q] < 0) continue;
+                const float2 p0 = P0[(size_t)myI[q] * a.n0 + k0], p1 = P1[(size_t)myI[q] * a.n1 + k1];
+                const float pr = p0.x * p1.x - p0.y * p1.y, pi = p0.x * p1.y + p0.y * p1.x;
+                const int p = q >> 1;
+                const float ur = (q & 1) ? U[j][p][0].y : U[j][p][0].x, ui = (q & 1) ? U[j][p][1].y : U[j][p][1].x;
+                const float vr = (q & 1) ? V[j][p][0].y : V[j][p][0].x, vi = (q & 1) ? V[j][p][1].y : V[j][p][1].x;
+                const float imU = pr * ui + pi * ur, imV = pr * vi + pi * vr;
+                s32[q][0] += m0 * imU;
+                s32[q][1] += m1 * imU;
+                s32[q][2] += imV;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+#pragma unroll
+            for (int d = 0; d < 3; d++) S[q][d] += (double)s32[q][d];
+    }
+    // block sums: the two row groups of a warp by a shuffle, then the 8 warps in shared memory
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int q = 0; q < 4; q++)
 #pragma unroll
         for (int d = 0; d < 3; d++) {
-            float v = (float)F[q][d] + ((q & 1) ? f32[q >> 1][d].y : f32[q >> 1][d].x);
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0) wsum[q * 3 + d][warp] = (double)v;
+            const double v = S[q][d] + __shfl_xor_sync(0xffffffffu, S[q][d], 16);
+            if (lane < 16) red[warp][4 * ti + q][d] = v;
         }
     __syncthreads();
-    if (threadIdx.x < 24) {
+    if (threadIdx.x < 3 * kFI) {
         const int q = threadIdx.x / 3, d = threadIdx.x - 3 * q;
         double t = 0.0;
-        for (int w = 0; w < nw; w++) t += wsum[threadIdx.x][w];
-        if (g0 + q < a.n_ions) part[(((size_t)(g0 + q)) * nchunk + chunk) * 3 + d] = t;
+        for (int w = 0; w < 8; w++) t += red[w][q][d];
+        if (ion0 + q < nion) part[((size_t)ions[ion0 + q] * gridDim.x + blockIdx.x) * 3 + d] = t;
     }
 }
 
-cudaError_t prepare_force_kernels() {
-    return cudaFuncSetAttribute(forces_fast_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+// row-tile blocks of the separable force kernel: about two waves (three blocks resident per SM)
+int forces_sep_blocks(const IonArgs &a, int nsm) {
+    const int ntile = (a.n0 * a.n1 + kFR - 1) / kFR, target = 6 * nsm;
+    return ntile < target ? ntile : target;
 }
 
-cudaError_t launch_forces_fast(const IonArgs &a, const float2 *rhohat, const float2 *ph32, const float4 *gc,
-                               double *partials, int nchunk, cudaStream_t st) {
+cudaError_t launch_forces_sep(const IonArgs &a, const float2 *rhohat, const float2 *ph32, const float *gf,
+                              const int *sp_ions, const int *sp_off, int nrb, double *partials, cudaStream_t st) {
     const long long NH = (long long)a.n0 * a.n1 * a.n2h;
-    cudaError_t e = cudaSuccess;
     for (int s = 0; s < a.n_species; s++) {
-        const float4 *gcs = gc + (size_t)s * 2 * NH;
-        // ions of other species write nothing for this species: their partials come from
-        // their own species' pass (the kernel skips them)
-        dim3 g(nchunk, (a.n_ions + 7) / 8);
-        const size_t smem = (size_t)4 * (a.n0 + a.n1 + a.n2h) * sizeof(float4);
-        double *ps = partials + (size_t)s * a.n_ions * nchunk * 3;
-        if (smem <= 96 * 1024) {          // (prepare_force_kernels raised the kernel's limit to 96 KB)
-            forces_fast_kernel<true><<<g, 256, smem, st>>>(a, ph32, gcs, rhohat, s, ps, nchunk);
-        } else {
-            forces_fast_kernel<false><<<g, 256, 0, st>>>(a, ph32, gcs, rhohat, s, ps, nchunk);
-        }
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        const int nion = sp_off[s + 1] - sp_off[s];
+        if (nion == 0) continue;
+        dim3 g(nrb, (nion + kFI - 1) / kFI);
+        forces_sep_kernel<<<g, 256, 0, st>>>(a, ph32, gf + (size_t)s * NH, rhohat, sp_ions + sp_off[s], nion,
+                                             partials);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
     }
-    return e;
+    return cudaSuccess;
 }
 
-// F[I][d] = sum over species and chunks of the partials [nsp][n_ions][nchunk][3] (fixed order)
-__global__ void reduce_force_partials_kernel(const double *part, int nsp, int n_ions, int nchunk, double *F) {
+// F_I = sum_a b_a S_a(I), S_a(I) = the partials [n_ions][nrb][3] summed over the row tiles in order
+__global__ void reduce_force_sep_kernel(IonArgs a, const double *part, int nrb, double *F) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= a.n_ions) return;
+    double S[3] = {0.0, 0.0, 0.0};
+    for (int c = 0; c < nrb; c++)
+        for (int k = 0; k < 3; k++) S[k] += part[((size_t)I * nrb + c) * 3 + k];
+    for (int d = 0; d < 3; d++) F[3 * I + d] = S[0] * a.bvec[d] + S[1] * a.bvec[3 + d] + S[2] * a.bvec[6 + d];
+}
+cudaError_t launch_reduce_force_sep(const IonArgs &a, const double *part, int nrb, double *F, cudaStream_t s) {
+    reduce_force_sep_kernel<<<(a.n_ions + 127) / 128, 128, 0, s>>>(a, part, nrb, F);
+    return cudaGetLastError();
+}
+
+// F[I][d] = sum over chunks of the partials [n_ions][nchunk][3] (fixed order)
+__global__ void reduce_force_partials_kernel(const double *part, int n_ions, int nchunk, double *F) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 3 * n_ions) return;
     const int I = t / 3, d = t - 3 * I;
     double s = 0.0;
-    for (int sp = 0; sp < nsp; sp++)
-        for (int c = 0; c < nchunk; c++) s += part[(((size_t)sp * n_ions + I) * nchunk + c) * 3 + d];
+    for (int c = 0; c < nchunk; c++) s += part[((size_t)I * nchunk + c) * 3 + d];
     F[t] = s;
 }
-cudaError_t launch_reduce_force_partials(const double *part, int nsp, int n_ions, int nchunk, double *F,
-                                         cudaStream_t s) {
-    reduce_force_partials_kernel<<<(3 * n_ions + 255) / 256, 256, 0, s>>>(part, nsp, n_ions, nchunk, F);
+cudaError_t launch_reduce_force_partials(const double *part, int n_ions, int nchunk, double *F, cudaStream_t s) {
+    reduce_force_partials_kernel<<<(3 * n_ions + 255) / 256, 256, 0, s>>>(part, n_ions, nchunk, F);
     return cudaGetLastError();
 }
 
