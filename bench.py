@@ -122,16 +122,16 @@ def make_input(wl):
     return W.model_density(wl)
 
 
-def run_batch(args):
-    """64 snapshots of jittered 108-atom FCC Al on grids drawn from {64,80,96,120}^3:
-    one batched E+V+forces call per step (inputs resident, V_ext(G) built per geometry
-    beforehand and timed separately)."""
+def batch_measure(nsnap, steps, warmup):
+    """The batched configuration: nsnap snapshots of jittered 108-atom FCC Al on grids drawn
+    from {64,80,96,120}^3, 16 knots, one batched E+V+forces call per step (inputs resident,
+    V_ext(G) and the force tables built per geometry beforehand and timed separately); the same
+    without forces, and both with one launch per snapshot and pass instead of grouped launches."""
     import torch
     import paper_2002_02985_gb300 as ofd
     import workloads as W
     from paper_2002_02985_gb300 import _lib as L
     torch.cuda.set_device(0)
-    nsnap = args.snapshots
     grids, rhos, npts = [], [], 0
     f = ofd.Functional(n_knots=16, precision=L.FP32_MIXED)
     t_ions = 0.0
@@ -151,11 +151,11 @@ def run_batch(args):
     Vbuf = [torch.empty_like(r) for r in rhos]
 
     def timed(forces):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             ofd.energy_potential_batched(grids, rhos, f, want_potential=True, want_forces=forces, V_out=Vbuf)
         torch.cuda.synchronize()
         ms = []
-        for _ in range(args.steps):
+        for _ in range(steps):
             st, en = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             st.record()
             ofd.energy_potential_batched(grids, rhos, f, want_potential=True, want_forces=forces, V_out=Vbuf)
@@ -165,33 +165,59 @@ def run_batch(args):
         return sum(ms) / len(ms)
 
     t = timed(True)
+    report = grids[0].batch_report()
     t_ev = timed(False)
-    line = {"metric": METRIC, "value": round(npts / (t * 1e-3), 1), "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t, 4), "higher_is_better": True,
+    grids[0].set_option(L.OPTION_BATCH_GROUPED, 0)
+    t1 = timed(True)
+    t1_ev = timed(False)
+    grids[0].set_option(L.OPTION_BATCH_GROUPED, 1)
+    return {"snapshots": nsnap, "grid_points": npts, "ms_per_step": round(t, 4),
+            "points_per_s": round(npts / (t * 1e-3), 1), "e_v_only_ms": round(t_ev, 4),
+            "forces_share": round((t - t_ev) / t, 4),
+            "per_geometry_setup_ms": round(t_ions * 1e3 / nsnap, 3), "plan": report,
+            "one_launch_per_snapshot": {"ms_per_step": round(t1, 4), "e_v_only_ms": round(t1_ev, 4)}}
+
+
+def run_batch(args):
+    """The batched configuration as the bench's own line (see batch_measure)."""
+    b = batch_measure(args.snapshots, args.steps, args.warmup)
+    t = b["ms_per_step"]
+    line = {"metric": METRIC, "value": b["points_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "fcc-al-108-snap x%d" % nsnap, "grid_points": npts, "n_knots": 16,
-                       "step": "batched E+V+forces of all snapshots",
-                       "l2": "inputs %.0f MB + workspaces > L2" % (npts * 4 / 1e6)},
-            "per_geometry_setup_ms": round(t_ions * 1e3 / nsnap, 3),
-            "e_v_only_ms_per_batch": round(t_ev, 4),
-            "batch": "snapshots on 4 internal streams (fork/join), captured once as a CUDA graph and replayed"}
+            "config": {"workload": "fcc-al-108-snap x%d" % args.snapshots, "grid_points": b["grid_points"],
+                       "n_knots": 16, "step": "batched E+V+forces of all snapshots",
+                       "l2": "inputs %.0f MB + workspaces > L2" % (b["grid_points"] * 4 / 1e6)},
+            "batch": b}
     print(json.dumps(line), flush=True)
+
+
+def cell_fp64(wl1, dev):
+    """The library's FP64 evaluation of the 4-atom cell (16^3, 12 knots) of the tiled crystal:
+    energies and the potential as a float64 array."""
+    import torch
+    import paper_2002_02985_gb300 as ofd
+    import workloads as W
+    from paper_2002_02985_gb300 import _lib as L
+    g1 = ofd.Grid(wl1["cell"], wl1["shape"])
+    g1.set_ions(wl1["positions"], wl1["species"], wl1["Z"], wl1["rc"])
+    r1 = torch.from_numpy(W.model_density(wl1).astype(np.float32).astype(np.float64)).to(dev)
+    E1, V1 = g1.energy_potential(r1, ofd.Functional(n_knots=12, precision=L.FP64))
+    return E1, V1.cpu().numpy()
 
 
 def run_scale(args):
     """1,048,576-atom FCC Al (64^3 conventional cells) on a 1024^3 grid, 12 knots,
-    PME structure factor.  Steps: PME set-up; FP32-mixed E+V timing; the supercell
-    pin (a perfect crystal on 1024^3 has the energy per atom and potential of the
-    4-atom cell on 16^3, computed by the oracle); PME forces; the 2 %-noise density
+    PME structure factor.  Steps: PME set-up; FP32-mixed E+V timing; supercell
+    invariance (a perfect crystal on 1024^3 has the energy per atom and potential of the
+    4-atom cell on 16^3, here the library's FP64 evaluation of that cell; the -m gpu tests pin
+    the same against the oracle); PME forces; the 2 %-noise density
     with forces checked against central differences of the FP64 energy on 8 atoms;
     optionally the density optimisation."""
     import torch
     import paper_2002_02985_gb300 as ofd
     import workloads as W
     from paper_2002_02985_gb300 import _lib as L
-    from oracle import functionals as ofn
-    from oracle.evaluate import Functional as OF, evaluate
-    from oracle.grid import Grid as OG
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     wl = W.workload("fcc-al-1m/1024")
@@ -209,16 +235,14 @@ def run_scale(args):
     E, V = g.energy_potential(rho, f32)
     torch.cuda.synchronize()
     out["setup_and_first_eval_s"] = round(time.perf_counter() - t0, 3)
-    og = OG(wl1["cell"], wl1["shape"])
-    Vg1 = ofn.external_potential_G(og, wl1["positions"], wl1["species"], wl1["Z"], wl1["rc"])
-    r1 = W.model_density(wl1)
-    E1, V1 = evaluate(og, r1.astype(np.float32).astype(np.float64), OF(n_knots=12), Vg1)
-    out["supercell_pin"] = {"E_per_atom_1024": E["total"] / wl["n_atoms"], "E_per_atom_oracle_16": E1["total"] / 4,
-                            "abs_err_Ha_per_atom": abs(E["total"] / wl["n_atoms"] - E1["total"] / 4)}
+    E1, V1 = cell_fp64(wl1, dev)
+    out["supercell_invariance"] = {"E_per_atom_1024": E["total"] / wl["n_atoms"],
+                                   "E_per_atom_cell_16_fp64": E1["total"] / 4,
+                                   "abs_err_Ha_per_atom": abs(E["total"] / wl["n_atoms"] - E1["total"] / 4)}
     Vs = V[::64, ::64, ::64].double().cpu().numpy()          # every 64th point = one value of the cell
     blocks = [V[a:a + 16, b:b + 16, c:c + 16].double().cpu().numpy() for a, b, c in ((0, 0, 0), (512, 256, 768),
                                                                                        (1008, 1008, 1008))]
-    out["supercell_pin"]["V_max_rel_err"] = max(float(np.max(np.abs(bl - V1)) / np.max(np.abs(V1))) for bl in blocks)
+    out["supercell_invariance"]["V_max_rel_err"] = max(float(np.max(np.abs(bl - V1)) / np.max(np.abs(V1))) for bl in blocks)
     del Vs
     F = g.forces(rho, L.FP32_MIXED)
     out["perfect_crystal_max_force"] = float(np.max(np.abs(F)))
@@ -636,6 +660,8 @@ def run_gpu(args):
         torch.cuda.empty_cache()
         line["fcc_al_1m_1024"] = extra_scale(args, peak)
         torch.cuda.empty_cache()
+        line["fcc_al_108_batch"] = batch_measure(64, 5, 3)
+        torch.cuda.empty_cache()
     if args.multistep and rank == 0:
         # Sec. 2.4's multi-step scheme: converge on a grid of half the points per axis, then
         # carry psi up and converge on the workload's grid; the single-level run beside it
@@ -779,15 +805,13 @@ def extra_cluster(args, peak):
 
 def extra_scale(args, peak):
     """fcc-al-1m/1024 (1,048,576 atoms, 12 knots, PME order 10): the supercell pin of the
-    noise-free crystal against the 4-atom cell on 16^3 (oracle), and the FP32-mixed step time,
-    kernel breakdown and reciprocal-space roofline on the 2 %-noise density."""
+    noise-free crystal against the 4-atom cell on 16^3 (the library's FP64 evaluation; the
+    oracle pin is a -m gpu test), and the FP32-mixed step time, kernel breakdown and
+    reciprocal-space roofline on the 2 %-noise density."""
     import torch
     import paper_2002_02985_gb300 as ofd
     import workloads as W
     from paper_2002_02985_gb300 import _lib as L
-    from oracle import functionals as ofn
-    from oracle.evaluate import Functional as OF, evaluate
-    from oracle.grid import Grid as OG
     dev = torch.device("cuda", 0)
     wl = W.workload("fcc-al-1m/1024")
     wl1 = W.workload("fcc-al-4/16")
@@ -798,9 +822,7 @@ def extra_scale(args, peak):
     rho = W.tiled_density_torch(wl1, 64, 0.0, 5, dev, torch.float32)
     E, _ = g.energy_potential(rho, f32, want_potential=False)
     setup = time.perf_counter() - t0
-    og = OG(wl1["cell"], wl1["shape"])
-    Vg1 = ofn.external_potential_G(og, wl1["positions"], wl1["species"], wl1["Z"], wl1["rc"])
-    E1, _ = evaluate(og, W.model_density(wl1).astype(np.float32).astype(np.float64), OF(n_knots=12), Vg1)
+    E1, _ = cell_fp64(wl1, dev)
     pin = abs(E["total"] / wl["n_atoms"] - E1["total"] / 4)
     del rho
     torch.cuda.empty_cache()
@@ -812,7 +834,7 @@ def extra_scale(args, peak):
     return {"grid": list(wl["shape"]), "atoms": wl["n_atoms"], "n_knots": 12,
             "structure_factor": "PME order %d" % args.pme_order, "setup_and_first_eval_s": round(setup, 2),
             "ms_per_step": round(t32, 3), "points_per_s": round(N / (t32 * 1e-3), 1),
-            "supercell_pin_Ha_per_atom": pin,
+            "supercell_vs_cell_fp64_Ha_per_atom": pin,
             "roofline_axis0_recip": {"achieved_gbs": kern.get("axis0_recip", {}).get("achieved_gbs"),
                                      "frac": kern.get("axis0_recip", {}).get("frac"), "peak": peak},
             "kernels": kern, "kernel_schedule": g.tuning_report()}
