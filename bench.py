@@ -455,6 +455,13 @@ def run_gpu(args):
     N = rho64.size
     stream = torch.cuda.current_stream()
     g = ofd.Grid(wl["cell"], wl["shape"], stream=stream)
+    if args.picks:
+        # fixed kernel configurations (rows, pencil, reciprocal-space indices of the tuning
+        # report) instead of the autotuner's timing: for profiler runs, whose serialised
+        # launches would time the candidates wrongly
+        for opt, v in zip((L.OPTION_PICK_ROWS, L.OPTION_PICK_PENCIL, L.OPTION_PICK_RECIP),
+                          (int(x) for x in args.picks.split(","))):
+            g.set_option(opt, v)
     g.set_ions(wl["positions"], wl["species"], wl["Z"], wl["rc"])
     f32 = ofd.Functional(n_knots=wl["n_knots"], precision=L.FP32_MIXED)
     f64 = ofd.Functional(n_knots=wl["n_knots"], precision=L.FP64)
@@ -986,6 +993,8 @@ def main():
                          "fcc-al-1m/1024")
     ap.add_argument("--snapshots", type=int, default=64)
     ap.add_argument("--pme-order", type=int, default=10)
+    ap.add_argument("--picks", default="",
+                    help="ROWS,PENCIL,RECIP: fixed kernel configurations (tuning-report indices) for the main grid")
     ap.add_argument("--optimize", action="store_true")
     ap.add_argument("--multistep", action="store_true", help="also time the multi-step optimisation (half-grid first)")
     ap.add_argument("--max-iter", type=int, default=200)
