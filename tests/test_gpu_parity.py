@@ -392,6 +392,31 @@ def test_every_reciprocal_kernel_configuration_matches_oracle(shape, pick):
         assert np.linalg.norm((V - Vo)[m]) / np.linalg.norm(Vo[m]) <= 1e-4, (pick, kw)
 
 
+@pytest.mark.parametrize("pick", range(10))
+def test_every_row_kernel_configuration_matches_oracle(pick):
+    """Each compiled configuration of the n2 rows for n2 = 128 (channel-batched with groups of
+    10 to 20 channels, per-channel; forced one at a time): 11 channels, 23 channels (two groups
+    for every channel-batched configuration), the Wang-Teter and interpolated modes."""
+    shape = (20, 18, 128)
+    cell, pos, rho = _bulk_case(shape)
+    g = ofd.Grid(cell, shape)
+    g.set_ions(pos, np.zeros(len(pos), np.int32), (3.0,), (0.8,))
+    g.energy_potential(torch.from_numpy(rho.astype(np.float32)).cuda(), ofd.Functional(n_knots=8))
+    rows = [seg for seg in g.tuning_report().split(";") if seg.strip().startswith("rows")]
+    n_cand = rows[0].count("[") if rows else 0
+    if pick >= n_cand:
+        pytest.skip("no such configuration")
+    for kw in (dict(n_knots=8), dict(n_knots=20), dict(n_knots=5, kernel=L.KERNEL_WT_GLOBAL),
+               dict(n_knots=8, nl_potential=L.NLPOT_INTERP)):
+        E, V, Eo, Vo, og, g2 = run_both(cell, shape, pos, rho, kw, L.FP32_MIXED, Z=(3.0,), rc=(0.8,),
+                                        options=((L.OPTION_PICK_ROWS, pick),))
+        nat = len(pos)
+        for k in ("TF", "vW", "NL", "H", "PP", "total"):
+            assert abs(E[k] - Eo[k]) / nat <= 1e-6, (pick, kw, k, E[k], Eo[k])
+        m = knot_mask(rho.astype(np.float32).astype(np.float64), kw["n_knots"])
+        assert np.linalg.norm((V - Vo)[m]) / np.linalg.norm(Vo[m]) <= 1e-4, (pick, kw)
+
+
 @pytest.mark.parametrize("shape,kw", RECIP_CASES)
 def test_fp32_reciprocal_kernel_shapes_match_oracle(shape, kw):
     cell = np.array([[0.25 * shape[0], 0.0, 0.0], [0.3, 0.45 * shape[1], 0.0], [-0.2, 0.1, 0.4 * shape[2]]])
