@@ -191,6 +191,33 @@ def test_grouped_batch_equals_single_evaluations(graph, grouped):
     assert ("CUDA graph" in rep_s) == bool(graph), rep_s
 
 
+def test_grouped_fp64_batch_equals_single_evaluations():
+    """FP64 snapshots (the FP64 kernels' grouped forms: 128-point specialised n2 rows, runtime-size
+    kernels elsewhere) grouped by shape, bit-identical to single calls."""
+    sizes = [(32, 32, 128), (24, 24, 24), (32, 32, 128), (24, 24, 24)]
+    f = ofd.Functional(n_knots=8, precision=L.FP64)
+    grids, rhos, singles = [], [], []
+    for s, shape in enumerate(sizes):
+        wl = W.workload("fcc-al-108-snap", s)
+        cell = wl["cell"] * (np.asarray(shape)[:, None] / 64.0)
+        pos = wl["positions"] * (np.asarray(shape) / 64.0)[None, :]
+        rho = W.renormalise(W.apply_noise(W.gaussian_density(cell, shape, pos, 3.0, 1.0), 0.02, s), cell,
+                            wl["n_electrons"])
+        g = ofd.Grid(cell, shape)
+        g.set_ions(pos, wl["species"], wl["Z"], wl["rc"])
+        r = torch.from_numpy(rho).cuda()
+        grids.append(g)
+        rhos.append(r)
+        singles.append(g.energy_potential(r, f))
+    for call in range(2):
+        E, Vs, _ = ofd.energy_potential_batched(grids, rhos, f, want_potential=True)
+        for i, (Es, Vsg) in enumerate(singles):
+            assert np.array_equal(E[i], np.array([Es[k] for k in ofd.ENERGY_KEYS])), (call, i)
+            assert torch.equal(Vs[i], Vsg), (call, i)
+    rep = grids[0].batch_report()
+    assert "32x32x128 x2 (grouped)" in rep and "24x24x24 x2 (grouped)" in rep, rep
+
+
 def test_grouped_batch_splits_past_the_group_limit():
     """34 snapshots of one shape: two grouped launches per pass (32 + 2), every snapshot
     bit-identical to its single evaluation; a second call with new potential buffers makes a
