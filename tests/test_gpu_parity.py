@@ -288,6 +288,33 @@ def test_length_1024_axes_match_oracle(shape):
     assert np.linalg.norm((V - Vo)[m]) / np.linalg.norm(Vo[m]) <= 1e-4
 
 
+@pytest.mark.parametrize("shape,option", [((20, 12, 1024), L.OPTION_PICK_ROWS), ((16, 1024, 18), L.OPTION_PICK_PENCIL),
+                                          ((1024, 12, 20), L.OPTION_PICK_RECIP)])
+@pytest.mark.parametrize("pick", range(3))
+def test_every_1024_configuration_matches_oracle(shape, option, pick):
+    """Each compiled configuration of the role whose axis has 1024 points (forced one at a
+    time; indices past the list are skipped), FP32-mixed, against the oracle."""
+    cell = np.diag([0.25 * n for n in shape])
+    vol = float(np.prod(np.diag(cell)))
+    counts = [max(1, round(vol / 110.0)) if n == 1024 else 1 for n in shape]
+    pos = lattice_positions(cell, counts, shape[0] + 11)
+    nat = len(pos)
+    rho = W.renormalise(W.apply_noise(W.gaussian_density(cell, shape, pos, 3.0, 1.0), 0.03, 6), cell, 3.0 * nat)
+    g = ofd.Grid(cell, shape)
+    g.set_ions(pos, np.zeros(nat, np.int32), (3.0,), (0.8,))
+    g.energy_potential(torch.from_numpy(rho.astype(np.float32)).cuda(), ofd.Functional(n_knots=6))
+    role = {L.OPTION_PICK_ROWS: "rows", L.OPTION_PICK_PENCIL: "pencil", L.OPTION_PICK_RECIP: "recip"}[option]
+    seg = [x for x in g.tuning_report().split(";") if x.strip().startswith(role)]
+    if not seg or pick >= seg[0].count("["):
+        pytest.skip("no such configuration")
+    E, V, Eo, Vo, og, _ = run_both(cell, shape, pos, rho, dict(n_knots=6), L.FP32_MIXED, Z=(3.0,), rc=(0.8,),
+                                   options=((option, pick),))
+    for k in ("TF", "vW", "NL", "H", "PP", "total"):
+        assert abs(E[k] - Eo[k]) / nat <= 1e-6, (pick, k, E[k], Eo[k])
+    m = knot_mask(rho.astype(np.float32).astype(np.float64), 6)
+    assert np.linalg.norm((V - Vo)[m]) / np.linalg.norm(Vo[m]) <= 1e-4, pick
+
+
 # ---------------------------------------------------------------- channel-batched row kernels (n2 = 128)
 ROW2_MODES = [dict(n_knots=16), dict(n_knots=24), dict(n_knots=16, nl_potential=L.NLPOT_INTERP),
               dict(n_knots=24, nl_potential=L.NLPOT_INTERP), dict(n_knots=5, kernel=L.KERNEL_WT_GLOBAL),
