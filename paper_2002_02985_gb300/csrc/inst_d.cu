@@ -10,11 +10,11 @@ template <> void candidates_d<float>(int role, int n, std::vector<KernelCand> &o
     OFDFT_CAND_ROW2(float, 1024, 8, 512, 16, 1)
     OFDFT_CAND_PENCIL(float, 1024, 8, 512, 16, 1)
     OFDFT_CAND_AXIS0(float, 1024, 4, 256, 16, 1)
-    // alternatives for the autotuner: smaller tiles at two blocks per SM, more threads per tile
+    // alternatives for the autotuner: 4-channel rows at two blocks per SM, 512 threads per
+    // column tile (measured picks at 1024^3; 4-column pencils at two blocks per SM and 2-column
+    // tiles were slower and are not compiled)
     OFDFT_CAND_ROW2(float, 1024, 4, 256, 16, 2)
-    OFDFT_CAND_PENCIL(float, 1024, 4, 256, 16, 2)
     OFDFT_CAND_AXIS0(float, 1024, 4, 512, 16, 1)
-    OFDFT_CAND_AXIS0(float, 1024, 2, 256, 16, 2)
 }
 template <> void candidates_d<double>(int, int, std::vector<KernelCand> &) {}
 
