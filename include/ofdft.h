@@ -316,7 +316,9 @@ int ofdft_td_spectrum(const double *dmu, int n, double dt, double gamma, int n_o
  * reduction order of its single evaluation (results bit-identical to single calls); groups
  * run concurrently on internal streams forked from and joined into the grids' stream, and
  * the whole batch is captured once into a CUDA graph and replayed while the arguments are
- * unchanged (OFDFT_OPTION_BATCH_GRAPH, OFDFT_OPTION_BATCH_GROUPED of the first grid).
+ * unchanged (OFDFT_OPTION_BATCH_GRAPH, OFDFT_OPTION_BATCH_GROUPED of the first grid; by
+ * default the first call times grouped and one-launch-per-snapshot enqueueing and keeps the
+ * faster).
  * Synchronises once.  Allocates, per distinct batch, the device copy of the evaluations'
  * arguments (a few KB per snapshot, kept with the cached plan; at most 16 plans). */
 int ofdft_energy_potential_batched(int n, ofdft_grid *const *grids, const void *const *rho_dev,
@@ -351,9 +353,11 @@ int ofdft_profile_read(ofdft_grid *g, int idx, const char **name, int *launches,
  *                             workspaces (synchronising its stream); they are rebuilt on next use.
  *   OFDFT_OPTION_BATCH_GRAPH  1 (default): a batched call whose first grid is g is captured once
  *                             into a CUDA graph and replayed; 0: enqueued directly on every call.
- *   OFDFT_OPTION_BATCH_GROUPED 1 (default): a batched call whose first grid is g launches each
- *                             pass once per group of snapshots with one launch geometry; 0: one
- *                             launch per snapshot and pass (the same results).
+ *   OFDFT_OPTION_BATCH_GROUPED -1 (default): the first batched call of a batch whose first grid
+ *                             is g runs it both ways (each once untimed, once timed with CUDA
+ *                             events) and later calls with the same arguments use the faster;
+ *                             1: each pass launched once per group of snapshots with one launch
+ *                             geometry; 0: one launch per snapshot and pass (the same results).
  *   OFDFT_OPTION_WAIT_POLLS   polls of the bounded device-side wait for bulk (TMA) copies before
  *                             it gives up (default 4194304; 0 makes it give up at once, so that
  *                             the evaluation returns OFDFT_ERR_TIMEOUT: a test of that path; the

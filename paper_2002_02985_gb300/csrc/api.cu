@@ -159,7 +159,7 @@ struct ofdft_grid {
     int force_pick[3] = {-1, -1, -1};    // per tuned role: a fixed candidate (-1: the autotuner's pick)
     int exact_sums = 0;                  // FP32-mixed: every energy term and dot product term in FP64
     int batch_graph = 1;
-    int batch_grouped = 1;
+    int batch_grouped = -1;              // -1: timed both ways at a batch's first call
     std::string batch_report;            // the plan of the last batch whose first grid this was
     unsigned wait_polls = 1u << 22;
     size_t alloc_cap = 0, alloc_bytes = 0;
@@ -260,6 +260,11 @@ template <typename T> int apply_cand(ofdft_grid *g, Workspace<T> &w, int role, c
         w.ks.pen_inv = c.k2;
         w.ks.pen_fwd_g = c.g1;
         w.ks.pen_inv_g = c.g2;
+        // the plain one-channel transforms use the same pencils (and the same TW1, threads and grid)
+        w.ks_plain.pen_fwd = c.k1;
+        w.ks_plain.pen_inv = c.k2;
+        w.ks_plain.pen_fwd_g = c.g1;
+        w.ks_plain.pen_inv_g = c.g2;
         w.TW1 = c.B;
         w.thr_p1 = c.nt;
         // persistent pencil grid: every resident block slot of the device, once
@@ -2032,6 +2037,18 @@ std::vector<BatchPlan> &batch_plans() {
     return c;
 }
 
+// the automatic grouping choice per batch (key without the grouping): 1 grouped, 0 not, and
+// the measured times
+struct BatchMode {
+    std::vector<unsigned char> key;
+    int grouped = 1;
+    std::string note;
+};
+std::vector<BatchMode> &batch_modes() {
+    static std::vector<BatchMode> c;
+    return c;
+}
+
 void free_plan(BatchPlan &p) {
     if (p.exec) cudaGraphExecDestroy(p.exec);
     cudaFree(p.dargs);
@@ -2177,6 +2194,25 @@ int make_plan(ofdft_grid *g0, int n, ofdft_grid *const *grids, const std::vector
     return OFDFT_OK;
 }
 
+// forces of snapshot i on stream s and their copy to the grid's pinned buffer (if wanted)
+template <typename T>
+int enqueue_forces(ofdft_grid *const *grids, const void *const *rho_dev, const ofdft_functional *f,
+                   double *const *F_out, int i, cudaStream_t s) {
+    if (!(F_out && F_out[i])) return OFDFT_OK;
+    ofdft_grid *g = grids[i];
+    const cudaStream_t saved = g->stream;
+    g->stream = s;
+    const bool kept = f->terms & (OFDFT_TERM_HARTREE | OFDFT_TERM_PP);
+    int rc = forces_enqueue<T>(g, (const T *)rho_dev[i], kept ? ws<T>(g).rhohat : nullptr);
+    if (rc == OFDFT_OK) {
+        cudaError_t e =
+            cudaMemcpyAsync(g->F_pinned, g->F_dev, (size_t)3 * g->n_ions * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) rc = fail(g, OFDFT_ERR_CUDA, "forces copy", e);
+    }
+    g->stream = saved;
+    return rc;
+}
+
 // Enqueue a planned batch on the caller's stream (fork/join over the internal streams).
 template <typename T>
 int enqueue_batch(const BatchPlan &p, int n, ofdft_grid *const *grids, const void *const *rho_dev,
@@ -2191,6 +2227,7 @@ int enqueue_batch(const BatchPlan &p, int n, ofdft_grid *const *grids, const voi
     for (int k = 0; k < kBatchStreams; k++) cudaStreamWaitEvent(st[k], fork, 0);
     const EvalArgs<T> *dargs = (const EvalArgs<T> *)p.dargs;
     const int ng = (int)p.gstream.size();
+    std::vector<cudaEvent_t> done(ng, nullptr);       // groups' evaluations complete (groups with forces)
     for (int gi = 0; gi < ng && rc == OFDFT_OK; gi++) {
         const int b = p.gbeg[gi], K = p.gbeg[gi + 1] - b;
         const cudaStream_t s = st[p.gstream[gi]];
@@ -2218,23 +2255,40 @@ int enqueue_batch(const BatchPlan &p, int n, ofdft_grid *const *grids, const voi
                 break;
             }
         }
-        // forces of the group's snapshots on the group's stream (rho_hat from the evaluation)
-        for (int m = 0; m < K && rc == OFDFT_OK; m++) {
-            const int i = p.order[b + m];
-            if (!(F_out && F_out[i])) continue;
-            ofdft_grid *gm = grids[i];
-            const cudaStream_t saved = gm->stream;
-            gm->stream = s;
-            const bool kept = f->terms & (OFDFT_TERM_HARTREE | OFDFT_TERM_PP);
-            rc = forces_enqueue<T>(gm, (const T *)rho_dev[i], kept ? ws<T>(gm).rhohat : nullptr);
-            if (rc == OFDFT_OK) {
-                cudaError_t e = cudaMemcpyAsync(gm->F_pinned, gm->F_dev, (size_t)3 * gm->n_ions * sizeof(double),
-                                                cudaMemcpyDeviceToHost, s);
-                if (e != cudaSuccess) rc = fail(gm, OFDFT_ERR_CUDA, "forces copy", e);
+        // forces (rho_hat from the evaluation): a single snapshot's right behind its evaluation;
+        // a group's once all groups' evaluations are enqueued (below)
+        if (K == 1) {
+            rc = enqueue_forces<T>(grids, rho_dev, f, F_out, p.order[b], s);
+        } else if (rc == OFDFT_OK) {
+            bool any_f = false;
+            for (int m = 0; m < K; m++) any_f = any_f || (F_out && F_out[p.order[b + m]]);
+            if (any_f) {
+                cudaError_t e = cudaEventCreateWithFlags(&done[gi], cudaEventDisableTiming);
+                if (e == cudaSuccess) e = cudaEventRecord(done[gi], s);
+                if (e != cudaSuccess) rc = fail(g, OFDFT_ERR_CUDA, "batch event", e);
             }
-            gm->stream = saved;
         }
     }
+    // a group's forces spread over all worker streams once its evaluations are done, so that
+    // they overlap one another and the other groups instead of queueing behind one stream;
+    // the lightest groups (the first to finish) first
+    std::vector<int> fo;
+    for (int gi = 0; gi < ng; gi++)
+        if (done[gi]) fo.push_back(gi);
+    std::stable_sort(fo.begin(), fo.end(), [&](int x, int y) {
+        return grids[p.order[p.gbeg[x]]]->N * (p.gbeg[x + 1] - p.gbeg[x]) <
+               grids[p.order[p.gbeg[y]]]->N * (p.gbeg[y + 1] - p.gbeg[y]);
+    });
+    for (int gi : fo) {
+        if (rc != OFDFT_OK) break;
+        const int b = p.gbeg[gi], K = p.gbeg[gi + 1] - b;
+        for (int k = 0; k < kBatchStreams; k++)
+            if (k != p.gstream[gi]) cudaStreamWaitEvent(st[k], done[gi], 0);
+        for (int m = 0; m < K && rc == OFDFT_OK; m++)
+            rc = enqueue_forces<T>(grids, rho_dev, f, F_out, p.order[b + m], st[(p.gstream[gi] + m) % kBatchStreams]);
+    }
+    for (cudaEvent_t e : done)
+        if (e) cudaEventDestroy(e);
     for (int k = 0; k < kBatchStreams; k++) {
         cudaEventRecord(join[k], st[k]);
         cudaStreamWaitEvent(user, join[k], 0);
@@ -2250,31 +2304,20 @@ int enqueue_batch(const BatchPlan &p, int n, ofdft_grid *const *grids, const voi
     return OFDFT_OK;
 }
 
+// the key of a batch plan: the functional, the stream, the modes; per snapshot the grid, its
+// buffer generation, whether forces are wanted, its kernels and its arguments (every pointer
+// and size); grouped = -1 leaves the grouping out (the automatic choice's key)
 template <typename T>
-int batched_impl(int n, ofdft_grid *const *grids, const void *const *rho_dev, const ofdft_functional *f,
-                 double *E_out, void *const *V_dev, double *const *F_out) {
+std::vector<unsigned char> batch_key(int n, ofdft_grid *const *grids, const ofdft_functional *f,
+                                     double *const *F_out, const std::vector<EvalArgs<T>> &args, int grouped) {
     ofdft_grid *g0 = grids[0];
-    cudaStream_t user = g0->stream;
-    for (int i = 0; i < n; i++)
-        for (int j = i + 1; j < n; j++)
-            if (grids[j] == grids[i]) return fail(g0, OFDFT_ERR_INVALID_ARG, "a grid appears twice in the batch");
-    std::vector<EvalArgs<T>> args(n);
-    for (int i = 0; i < n; i++) {
-        const bool want_f = F_out && F_out[i];
-        int rc = prepare_batch_grid<T>(grids[i], f, want_f, (const T *)rho_dev[i]);
-        if (!rc) rc = eval_args<T>(grids[i], (const T *)rho_dev[i], f, V_dev ? (T *)V_dev[i] : nullptr, nullptr, want_f,
-                                   args[i]);
-        if (rc) return rc;
-    }
     bool use_graph = g0->batch_graph && !f->knots;
     for (int i = 0; i < n; i++) use_graph = use_graph && !grids[i]->prof_on;
-    // key: the functional, the stream, the modes; per snapshot the grid, its buffer generation,
-    // whether forces are wanted, its kernels and its arguments (every pointer and size)
     std::vector<unsigned char> key;
     append_bytes(key, *f);
-    append_bytes(key, user);
+    append_bytes(key, g0->stream);
     append_bytes(key, (int)use_graph);
-    append_bytes(key, g0->batch_grouped);
+    append_bytes(key, grouped);
     append_bytes(key, (int)sizeof(T));
     for (int i = 0; i < n; i++) {
         append_bytes(key, grids[i]);
@@ -2286,6 +2329,20 @@ int batched_impl(int n, ofdft_grid *const *grids, const void *const *rho_dev, co
     int dev = 0;
     cudaGetDevice(&dev);
     append_bytes(key, dev);
+    return key;
+}
+
+// one batched call in the given mode (grouped 1 / 0); ms: if set, the device time of the
+// batch's enqueued work (CUDA events on the grids' stream)
+template <typename T>
+int batched_run(int n, ofdft_grid *const *grids, const void *const *rho_dev, const ofdft_functional *f, double *E_out,
+                void *const *V_dev, double *const *F_out, const std::vector<EvalArgs<T>> &args, int grouped,
+                float *ms) {
+    ofdft_grid *g0 = grids[0];
+    cudaStream_t user = g0->stream;
+    bool use_graph = g0->batch_graph && !f->knots;
+    for (int i = 0; i < n; i++) use_graph = use_graph && !grids[i]->prof_on;
+    std::vector<unsigned char> key = batch_key<T>(n, grids, f, F_out, args, grouped);
     BatchPlan *plan = nullptr;
     for (auto &bp : batch_plans())
         if (bp.key == key) plan = &bp;
@@ -2298,7 +2355,7 @@ int batched_impl(int n, ofdft_grid *const *grids, const void *const *rho_dev, co
             batch_plans().erase(batch_plans().begin());
         }
         BatchPlan np;
-        int rc = make_plan<T>(g0, n, grids, args, g0->batch_grouped != 0, np);
+        int rc = make_plan<T>(g0, n, grids, args, grouped != 0, np);
         if (!rc && use_graph) {
             cudaGraph_t graph = nullptr;
             cudaStream_t origin = batch_streams()[kBatchStreams];
@@ -2324,14 +2381,43 @@ int batched_impl(int n, ofdft_grid *const *grids, const void *const *rho_dev, co
         plan = &batch_plans().back();
     }
     g0->batch_report = plan->report + (plan->exec ? ", replayed as one CUDA graph" : "");
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (ms) {
+        e = cudaEventCreate(&t0);
+        if (e == cudaSuccess) e = cudaEventCreate(&t1);
+        if (e == cudaSuccess) e = cudaEventRecord(t0, user);
+        if (e != cudaSuccess) {
+            if (t0) cudaEventDestroy(t0);
+            if (t1) cudaEventDestroy(t1);
+            return fail(g0, OFDFT_ERR_CUDA, "event", e);
+        }
+    }
     if (plan->exec) {
         e = cudaGraphLaunch(plan->exec, user);
-        if (e != cudaSuccess) return fail(g0, OFDFT_ERR_CUDA, "graph launch", e);
+        if (e != cudaSuccess) {
+            if (ms) {
+                cudaEventDestroy(t0);
+                cudaEventDestroy(t1);
+            }
+            return fail(g0, OFDFT_ERR_CUDA, "graph launch", e);
+        }
     } else {
         int rc = enqueue_batch<T>(*plan, n, grids, rho_dev, f, args, F_out, user);
-        if (rc) return rc;
+        if (rc) {
+            if (ms) {
+                cudaEventDestroy(t0);
+                cudaEventDestroy(t1);
+            }
+            return rc;
+        }
     }
+    if (ms) cudaEventRecord(t1, user);
     e = cudaStreamSynchronize(user);
+    if (ms) {
+        if (e == cudaSuccess) e = cudaEventElapsedTime(ms, t0, t1);
+        cudaEventDestroy(t0);
+        cudaEventDestroy(t1);
+    }
     if (e != cudaSuccess) return fail(g0, OFDFT_ERR_CUDA, "stream synchronize", e);
     const int W = E_NUM + S_NSCAL;
     for (int j = 0; j < n; j++) {
@@ -2345,6 +2431,55 @@ int batched_impl(int n, ofdft_grid *const *grids, const void *const *rho_dev, co
     }
     return OFDFT_OK;
 }
+
+template <typename T>
+int batched_impl(int n, ofdft_grid *const *grids, const void *const *rho_dev, const ofdft_functional *f,
+                 double *E_out, void *const *V_dev, double *const *F_out) {
+    ofdft_grid *g0 = grids[0];
+    for (int i = 0; i < n; i++)
+        for (int j = i + 1; j < n; j++)
+            if (grids[j] == grids[i]) return fail(g0, OFDFT_ERR_INVALID_ARG, "a grid appears twice in the batch");
+    std::vector<EvalArgs<T>> args(n);
+    for (int i = 0; i < n; i++) {
+        const bool want_f = F_out && F_out[i];
+        int rc = prepare_batch_grid<T>(grids[i], f, want_f, (const T *)rho_dev[i]);
+        if (!rc) rc = eval_args<T>(grids[i], (const T *)rho_dev[i], f, V_dev ? (T *)V_dev[i] : nullptr, nullptr, want_f,
+                                   args[i]);
+        if (rc) return rc;
+    }
+    int grouped = g0->batch_grouped;
+    if (grouped >= 0) return batched_run<T>(n, grids, rho_dev, f, E_out, V_dev, F_out, args, grouped, nullptr);
+    // automatic: the first call of a batch runs it both ways (each once to build its plan, once
+    // timed with CUDA events) and keeps the faster for the later calls with the same key
+    const std::vector<unsigned char> key = batch_key<T>(n, grids, f, F_out, args, -1);
+    for (const BatchMode &d : batch_modes())
+        if (d.key == key) {
+            int rc = batched_run<T>(n, grids, rho_dev, f, E_out, V_dev, F_out, args, d.grouped, nullptr);
+            g0->batch_report += d.note;
+            return rc;
+        }
+    float ms[2] = {0.f, 0.f};
+    std::string rep[2];
+    for (int m = 1; m >= 0; m--) {
+        for (int r = 0; r < 2; r++)
+            if (int rc = batched_run<T>(n, grids, rho_dev, f, E_out, V_dev, F_out, args, m, r ? &ms[m] : nullptr))
+                return rc;
+        rep[m] = g0->batch_report;
+    }
+    BatchMode d;
+    d.key = key;
+    d.grouped = ms[1] <= ms[0] ? 1 : 0;
+    char buf[160];
+    std::snprintf(buf, sizeof(buf), " (automatic choice: grouped %.3f ms, one launch per snapshot %.3f ms)", ms[1],
+                  ms[0]);
+    d.note = buf;
+    g0->batch_report = rep[d.grouped] + d.note;
+    if (batch_modes().size() >= 64) batch_modes().erase(batch_modes().begin());
+    batch_modes().push_back(d);
+    // the outputs are those of the last run: the same as the chosen mode's (E and V bit-identical)
+    return OFDFT_OK;
+}
+
 
 }  // namespace
 
@@ -2468,7 +2603,8 @@ int ofdft_set_option(ofdft_grid *g, int option, long long value) {
             g->batch_graph = value != 0;
             return OFDFT_OK;
         case OFDFT_OPTION_BATCH_GROUPED:
-            g->batch_grouped = value != 0;
+            if (value < -1 || value > 1) return fail(g, OFDFT_ERR_INVALID_ARG, "batch grouping must be -1, 0 or 1");
+            g->batch_grouped = (int)value;
             return OFDFT_OK;
         case OFDFT_OPTION_WAIT_POLLS:
             if (value < 0 || value > (1LL << 30)) return fail(g, OFDFT_ERR_INVALID_ARG, "wait polls out of range");

@@ -73,7 +73,8 @@ def test_optimiser_reports_not_converged_with_a_filled_report():
 
 def test_unknown_options_are_rejected():
     wl, g, rho = _grid()
-    for opt, val in ((99, 0), (L.OPTION_KERNELS, 7), (L.OPTION_WAIT_POLLS, -1), (L.OPTION_ALLOC_CAP, -5)):
+    for opt, val in ((99, 0), (L.OPTION_KERNELS, 7), (L.OPTION_WAIT_POLLS, -1), (L.OPTION_ALLOC_CAP, -5),
+                     (L.OPTION_BATCH_GROUPED, 2)):
         with pytest.raises(ofd.OFDFTError) as e:
             g.set_option(opt, val)
         assert e.value.status == L.OFDFT_ERR_INVALID_ARG

@@ -9,6 +9,8 @@ Tolerances
               precision).
 Both sides read the same float32 density (the oracle upcasts it exactly).
 """
+import functools
+
 import numpy as np
 import pytest
 
@@ -164,6 +166,21 @@ def test_forces_match_oracle(precision, tol):
     assert np.max(np.abs(F - Fo)) <= tol * max(1.0, np.max(np.abs(Fo))), np.max(np.abs(F - Fo))
 
 
+@pytest.mark.parametrize("shape", [(16, 80, 20), (16, 96, 20), (24, 128, 20)])
+def test_forces_after_autotuning_match_oracle(shape):
+    """The plain one-channel transforms (single-call forces here) use the n1 pencils the
+    autotuner picked at the grid's first evaluation, with that pick's tile and block size."""
+    cell, pos, rho = _bulk_case(shape)
+    g = ofd.Grid(cell, shape)
+    g.set_ions(pos, np.zeros(len(pos), np.int32), (3.0,), (0.8,))
+    r = torch.from_numpy(rho.astype(np.float32)).cuda()
+    g.energy_potential(r, ofd.Functional(n_knots=8))          # tunes
+    F = g.forces(r)
+    og = OGrid(cell, shape)
+    Fo = oforces(og, rho.astype(np.float32).astype(np.float64), pos, np.zeros(len(pos), np.int32), [3.0], [0.8])
+    assert np.max(np.abs(F - Fo)) <= 1e-5 * max(1.0, np.max(np.abs(Fo))), (np.max(np.abs(F - Fo)), g.tuning_report())
+
+
 def test_frozen_knots_fp64():
     shape = (16, 16, 16)
     cell, pos, rho = small_case(shape, seed=9)
@@ -288,25 +305,45 @@ def test_length_1024_axes_match_oracle(shape):
     assert np.linalg.norm((V - Vo)[m]) / np.linalg.norm(Vo[m]) <= 1e-4
 
 
-@pytest.mark.parametrize("shape,option", [((20, 12, 1024), L.OPTION_PICK_ROWS), ((16, 1024, 18), L.OPTION_PICK_PENCIL),
-                                          ((1024, 12, 20), L.OPTION_PICK_RECIP)])
-@pytest.mark.parametrize("pick", range(3))
-def test_every_1024_configuration_matches_oracle(shape, option, pick):
-    """Each compiled configuration of the role whose axis has 1024 points (forced one at a
-    time; indices past the list are skipped), FP32-mixed, against the oracle."""
+@functools.lru_cache(maxsize=None)
+def _n_configurations(shape, role):
+    """How many configurations the autotuner times for a role at this shape (one evaluation of a
+    uniform density on a cubic-ish cell)."""
+    g = ofd.Grid(np.diag([0.25 * n for n in shape]), shape)
+    g.energy_potential(torch.full(shape, 0.01, dtype=torch.float32, device="cuda"),
+                       ofd.Functional(n_knots=6, terms=L.TERMS_ALL & ~L.TERM_PP))
+    seg = [x for x in g.tuning_report().split(";") if x.strip().startswith(role)]
+    return seg[0].count("[") if seg else 0
+
+
+@functools.lru_cache(maxsize=None)
+def _config_case(shape):
+    """A bulk-like density for the shape (built once per shape)."""
+    if max(shape) < 1024:
+        return _bulk_case(shape)
     cell = np.diag([0.25 * n for n in shape])
     vol = float(np.prod(np.diag(cell)))
     counts = [max(1, round(vol / 110.0)) if n == 1024 else 1 for n in shape]
     pos = lattice_positions(cell, counts, shape[0] + 11)
-    nat = len(pos)
-    rho = W.renormalise(W.apply_noise(W.gaussian_density(cell, shape, pos, 3.0, 1.0), 0.03, 6), cell, 3.0 * nat)
-    g = ofd.Grid(cell, shape)
-    g.set_ions(pos, np.zeros(nat, np.int32), (3.0,), (0.8,))
-    g.energy_potential(torch.from_numpy(rho.astype(np.float32)).cuda(), ofd.Functional(n_knots=6))
+    rho = W.renormalise(W.apply_noise(W.gaussian_density(cell, shape, pos, 3.0, 1.0), 0.03, 6), cell, 3.0 * len(pos))
+    return cell, pos, rho
+
+
+def _role_cases(n):
+    return [((20, 12, n), L.OPTION_PICK_ROWS), ((16, n, 18), L.OPTION_PICK_PENCIL), ((n, 12, 20), L.OPTION_PICK_RECIP)]
+
+
+@pytest.mark.parametrize("shape,option", [c for n in (64, 80, 96, 120, 192, 1024) for c in _role_cases(n)])
+@pytest.mark.parametrize("pick", range(5))
+def test_every_compiled_configuration_matches_oracle(shape, option, pick):
+    """Each compiled configuration of the role whose axis is long (the autotuner's candidates for
+    the rows, the n1 pencils or the reciprocal-space pass at 64 ... 1024 points, forced one at a
+    time; indices past the list are skipped), FP32-mixed, against the oracle."""
     role = {L.OPTION_PICK_ROWS: "rows", L.OPTION_PICK_PENCIL: "pencil", L.OPTION_PICK_RECIP: "recip"}[option]
-    seg = [x for x in g.tuning_report().split(";") if x.strip().startswith(role)]
-    if not seg or pick >= seg[0].count("["):
+    if pick >= _n_configurations(shape, role):
         pytest.skip("no such configuration")
+    cell, pos, rho = _config_case(shape)
+    nat = len(pos)
     E, V, Eo, Vo, og, _ = run_both(cell, shape, pos, rho, dict(n_knots=6), L.FP32_MIXED, Z=(3.0,), rc=(0.8,),
                                    options=((option, pick),))
     for k in ("TF", "vW", "NL", "H", "PP", "total"):

@@ -154,7 +154,7 @@ def _snapshot(s, n):
 
 
 @pytest.mark.parametrize("graph", [1, 0])
-@pytest.mark.parametrize("grouped", [1, 0])
+@pytest.mark.parametrize("grouped", [1, 0, -1])
 def test_grouped_batch_equals_single_evaluations(graph, grouped):
     """Snapshots of repeated and uneven sizes: grouped launches (one launch per pass over the
     snapshots of one launch geometry) give bit-identical energies and potentials to single
@@ -183,7 +183,9 @@ def test_grouped_batch_equals_single_evaluations(graph, grouped):
             assert np.max(np.abs(Fs[i] - Fsg)) <= 1e-5 * max(1.0, np.max(np.abs(Fsg))), (rep, i)
     rep_s = grids[0].batch_report()
     # (the 64^3 grids were tuned at different times; their plans still match)
-    if grouped:
+    if grouped < 0:
+        assert "automatic choice" in rep_s, rep_s
+    elif grouped:
         assert "4 launch groups" in rep_s and "64x64x64 x3 (grouped, persistent recip)" in rep_s, rep_s
         assert "48x48x48 x3 (grouped)" in rep_s and "36x36x36 x1;" in rep_s, rep_s
     else:
@@ -204,6 +206,7 @@ def test_grouped_fp64_batch_equals_single_evaluations():
         rho = W.renormalise(W.apply_noise(W.gaussian_density(cell, shape, pos, 3.0, 1.0), 0.02, s), cell,
                             wl["n_electrons"])
         g = ofd.Grid(cell, shape)
+        g.set_option(L.OPTION_BATCH_GROUPED, 1)
         g.set_ions(pos, wl["species"], wl["Z"], wl["rc"])
         r = torch.from_numpy(rho).cuda()
         grids.append(g)
@@ -226,6 +229,8 @@ def test_grouped_batch_splits_past_the_group_limit():
     grids, rhos, singles = [], [], []
     for s in range(34):
         g, r = _snapshot(s % 64, 24)
+        if s == 0:
+            g.set_option(L.OPTION_BATCH_GROUPED, 1)
         grids.append(g)
         rhos.append(r)
         singles.append(g.energy_potential(r, f))
