@@ -8,6 +8,7 @@
 #pragma once
 
 #include "eval.cuh"
+#include "gnl_fit.cuh"
 
 namespace ofdft {
 
@@ -71,7 +72,8 @@ struct CtPolicy {
 //   eta < 1/2:  F = 1 - sum_m a_m y^m,   num = -(8/3) y + sum_{m>=2} (a_m + 3 a_{m-1}) y^m
 //   eta > 2  :  F = sum_m a_m x^m,       num = -sum_{m>=1} (a_m + 3 a_{m+1}) x^m
 // and G_NL = num / F.  The loops are unrolled, so every coefficient folds to
-// a constant.
+// a constant.  (These series serve the FP64 kernels; the FP32-mixed kernels use the
+// polynomial forms of gnl_fit.cuh in the same two ranges.)
 template <typename T> struct GnlTerms { static constexpr int value = 10; };
 template <> struct GnlTerms<double> { static constexpr int value = 28; };
 
@@ -85,40 +87,61 @@ __host__ __device__ __forceinline__ double glog(double x) { return log(x); }
 __host__ __device__ __forceinline__ double gabs(double x) { return fabs(x); }
 __device__ __forceinline__ float gabs(float x) { return fabsf(x); }
 
-// (host and device: the FP64 form also builds the FP32-mixed kernel table)
-template <typename T> __host__ __device__ __forceinline__ T gnl(T eta) {
-    constexpr int nt = GnlTerms<T>::value;
-    // both series are sums sum_{m=1}^{nt} c_m z^m, evaluated by Horner's rule with fused
-    // multiply-adds: p = c_nt, p = p z + c_m (m = nt-1..1), sum = p z
-    if (eta < (T)0.5) {
-        const T y = eta * eta;
-        T pF = (T)(1.0 / (4.0 * nt * nt - 1.0));
-        T pN = (T)(1.0 / (4.0 * nt * nt - 1.0) + 3.0 / (4.0 * (nt - 1) * (nt - 1) - 1.0));
-#pragma unroll
-        for (int m = nt - 1; m >= 1; m--) {
-            const double am = 1.0 / (4.0 * m * m - 1.0);
-            const double lo = (m >= 2) ? am + 3.0 / (4.0 * (m - 1) * (m - 1) - 1.0) : -8.0 / 3.0;
-            pF = pF * y + (T)am;
-            pN = pN * y + (T)lo;
-        }
-        return gdiv(pN * y, (T)1 - pF * y);
-    } else if (eta > (T)2) {
-        const T x = gdiv((T)1, eta * eta);
-        T pF = (T)(1.0 / (4.0 * nt * nt - 1.0));
-        T pN = (T)(1.0 / (4.0 * nt * nt - 1.0) + 3.0 / (4.0 * (nt + 1) * (nt + 1) - 1.0));
-#pragma unroll
-        for (int m = nt - 1; m >= 1; m--) {
-            const double am = 1.0 / (4.0 * m * m - 1.0);
-            const double hi = am + 3.0 / (4.0 * (m + 1) * (m + 1) - 1.0);
-            pF = pF * x + (T)am;
-            pN = pN * x + (T)hi;
-        }
-        return -gdiv(pN, pF);          // the common factor x of both sums cancels
-    }
+// closed form between the series ranges (1/2 <= eta <= 2)
+template <typename T> __host__ __device__ __forceinline__ T gnl_mid(T eta) {
     const T d = (T)1 - eta;
     if (gabs(d) < (T)1e-12) return (T)-2;
     const T F = (T)0.5 + gdiv((T)1 - eta * eta, (T)4 * eta) * glog(gabs(gdiv((T)1 + eta, d)));
     return gdiv((T)1, F) - (T)3 * eta * eta - (T)1;
+}
+
+// (host and device: the FP64 form also builds the MGP correction table).  The FP32-mixed
+// kernels take G_NL below eta = 1/2 and above eta = 2 from the degree-6 polynomials of
+// gnl_fit.cuh (y S(y) and L(1/eta^2), within 2e-10 of the closed form: below FP32 rounding,
+// in 7 fused multiply-adds instead of two 10-term series and a division).
+template <typename T> __host__ __device__ __forceinline__ T gnl(T eta) {
+#ifdef __CUDA_ARCH__
+    if constexpr (sizeof(T) == 4) {
+        // both polynomials and the select carry no branch, so that the evaluations of a
+        // thread's several G vectors interleave; only 1/2 <= eta <= 2 branches
+        const float y = eta * eta;
+        const float gs = y * gnl_small_s(y), gl = gnl_large_l(gdiv(1.0f, y));
+        float g = eta < 0.5f ? gs : gl;
+        if (eta >= 0.5f && eta <= 2.0f) g = gnl_mid(eta);
+        return g;
+    } else
+#endif
+    {
+        constexpr int nt = GnlTerms<T>::value;
+        // both series are sums sum_{m=1}^{nt} c_m z^m, evaluated by Horner's rule with fused
+        // multiply-adds: p = c_nt, p = p z + c_m (m = nt-1..1), sum = p z
+        if (eta < (T)0.5) {
+            const T y = eta * eta;
+            T pF = (T)(1.0 / (4.0 * nt * nt - 1.0));
+            T pN = (T)(1.0 / (4.0 * nt * nt - 1.0) + 3.0 / (4.0 * (nt - 1) * (nt - 1) - 1.0));
+#pragma unroll
+            for (int m = nt - 1; m >= 1; m--) {
+                const double am = 1.0 / (4.0 * m * m - 1.0);
+                const double lo = (m >= 2) ? am + 3.0 / (4.0 * (m - 1) * (m - 1) - 1.0) : -8.0 / 3.0;
+                pF = pF * y + (T)am;
+                pN = pN * y + (T)lo;
+            }
+            return gdiv(pN * y, (T)1 - pF * y);
+        } else if (eta > (T)2) {
+            const T x = gdiv((T)1, eta * eta);
+            T pF = (T)(1.0 / (4.0 * nt * nt - 1.0));
+            T pN = (T)(1.0 / (4.0 * nt * nt - 1.0) + 3.0 / (4.0 * (nt + 1) * (nt + 1) - 1.0));
+#pragma unroll
+            for (int m = nt - 1; m >= 1; m--) {
+                const double am = 1.0 / (4.0 * m * m - 1.0);
+                const double hi = am + 3.0 / (4.0 * (m + 1) * (m + 1) - 1.0);
+                pF = pF * x + (T)am;
+                pN = pN * x + (T)hi;
+            }
+            return -gdiv(pN, pF);          // the common factor x of both sums cancels
+        }
+        return gnl_mid(eta);
+    }
 }
 
 // MGP correction J_y(eta) by linear interpolation in u = eta / (1 + eta) of the table a.mgp_tab
@@ -999,6 +1022,15 @@ __device__ __forceinline__ void row_fwd2_body(const EvalArgs<T> &a, const int bi
     const bool has1 = row0 + 1 < R;
     const bool nl = a.terms & 4u, lwt = nl && a.kernel == 0;
     const int M = a.M, nf = a.nfwd;
+    // the block's density values are requested first, so that their latency overlaps the
+    // table loads and the barrier below
+    T xr[E][2];
+#pragma unroll
+    for (int q = 0; q < E; q++) {
+        const int e = threadIdx.x + q * NT;
+#pragma unroll
+        for (int s = 0; s < 2; s++) xr[q][s] = (e < n && (s == 0 || has1)) ? a.rho[(row0 + s) * n + e] : (T)0;
+    }
     for (int i = threadIdx.x; i < n; i += NT) tw[i] = a.tw2[i];
     if (lwt)
         for (int i = threadIdx.x; i < M; i += NT) {
@@ -1029,7 +1061,7 @@ __device__ __forceinline__ void row_fwd2_body(const EvalArgs<T> &a, const int bi
             vh[q][s] = vv[q][s] = vb[q][s] = fa[q][s] = fb[q][s] = (T)0;
             jj[q][s] = 0;
             if (e < n && (s == 0 || has1)) {
-                const T x = a.rho[(row0 + s) * n + e];
+                const T x = xr[q][s];
                 vh[q][s] = x - mean;
                 vv[q][s] = dsqrt(x > (T)0 ? x : (T)0);
                 if (nl) {
@@ -1116,6 +1148,32 @@ __device__ __forceinline__ void row_inv2_body(const EvalArgs<T> &a, const int bi
     const bool has1 = row0 + 1 < R;
     const bool nl = a.terms & 4u, lwt = nl && a.kernel == 0, interp = a.nlpot == 1;
     const int M = a.M, ni = a.ninv;
+    // bulk (TMA) loads need 16-byte aligned rows: an even channel stride, both rows present.
+    // The two half-spectrum rows of each channel (contiguous in memory) are copied
+    // asynchronously into the scratch buffer, one bulk copy per channel, so that all of a
+    // group's loads are in flight at once; the first group's copies and the block's density
+    // values are requested before anything else, so that their latency overlaps the table
+    // loads, the barrier and the per-point factors below.
+    const bool bulk = has1 && (a.NH % 2 == 0) && (smem_u32(scr) % 16 == 0);
+    auto issue_rows = [&](int g0, int gact) {
+        const unsigned bytes = (unsigned)(2 * n2h * sizeof(C));
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&mbar, bytes * (unsigned)gact);
+        for (int s = 0; s < gact; s++)
+            bulk_g2s(scr + 2 * s * n2h, a.chan + (size_t)a.inv_ch[g0 + s] * a.NH + row0 * n2h, bytes, &mbar);
+    };
+    if (bulk && threadIdx.x == 0) {
+        mbar_init(&mbar, 1);
+        fence_proxy_async_smem();
+        issue_rows(0, ni < G ? ni : G);
+    }
+    T xr[E][2];
+#pragma unroll
+    for (int q = 0; q < E; q++) {
+        const int e = threadIdx.x + q * NT;
+#pragma unroll
+        for (int s = 0; s < 2; s++) xr[q][s] = (e < n && (s == 0 || has1)) ? a.rho[(row0 + s) * n + e] : (T)0;
+    }
     for (int i = threadIdx.x; i < n; i += NT) tw[i] = a.tw2[i];
     if (lwt)
         for (int i = threadIdx.x; i < M; i += NT) {
@@ -1132,12 +1190,6 @@ __device__ __forceinline__ void row_inv2_body(const EvalArgs<T> &a, const int bi
         for (int i = ni - 1; i >= 0; i--)
             if (a.inv_kind[i] == CONS_KNOT) k = i;
         skpos = k;
-    }
-    // bulk (TMA) loads need 16-byte aligned rows: an even channel stride, both rows present
-    const bool bulk = has1 && (a.NH % 2 == 0) && (smem_u32(scr) % 16 == 0);
-    if (bulk && threadIdx.x == 0) {
-        mbar_init(&mbar, 1);
-        fence_proxy_async_smem();
     }
     __syncthreads();
     const int kpos = skpos;
@@ -1160,7 +1212,7 @@ __device__ __forceinline__ void row_inv2_body(const EvalArgs<T> &a, const int bi
             jj[q][s] = 0;
             if (e < n) {
                 const bool valid = s == 0 || has1;
-                const T x = valid ? a.rho[(row0 + s) * n + e] : (T)0;
+                const T x = xr[q][s];
                 const T xp = x > (T)0 ? x : (T)0;
                 if (a.terms & 1u) {
                     const T c = dcbrt(xp);
@@ -1208,17 +1260,11 @@ __device__ __forceinline__ void row_inv2_body(const EvalArgs<T> &a, const int bi
     bool alive = true;
     for (int g0 = 0; g0 < ni; g0 += G) {
         const int gact = ni - g0 < G ? ni - g0 : G;
-        // the two half-spectrum rows of each channel (contiguous in memory) are copied
-        // asynchronously into the scratch buffer, so that all of a block's loads are in
-        // flight at once: one bulk copy per channel, else element copies (a missing
-        // second row reads as zeros)
+        // the group's rows by bulk copies (the first group's are already in flight), else
+        // element copies (a missing second row reads as zeros)
         if (bulk) {
             if (threadIdx.x == 0) {
-                const unsigned bytes = (unsigned)(2 * n2h * sizeof(C));
-                fence_proxy_async_smem();
-                mbar_arrive_expect_tx(&mbar, bytes * (unsigned)gact);
-                for (int s = 0; s < gact; s++)
-                    bulk_g2s(scr + 2 * s * n2h, a.chan + (size_t)sch[g0 + s] * a.NH + row0 * n2h, bytes, &mbar);
+                if (g0 > 0) issue_rows(g0, gact);
                 s_ok = mbar_wait_bounded(&mbar, phase, a.wait_polls) ? 1 : 0;
             }
             __syncthreads();

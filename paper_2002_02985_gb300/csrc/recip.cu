@@ -34,6 +34,11 @@ template <> void recip_candidates<float>(int n, std::vector<KernelCand> &out) {
             add_recip<float, 128, 16, 4, 16, 2>(out);
             add_recip<float, 128, 16, 4>(out);
             add_recip<float, 128, 8, 4>(out);
+            // 14 / 28 columns: the 128 x 65 columns of a 128^3 grid make 595 / 298 tiles, just under
+            // two per block (16 / 32 columns: 520 / 260 tiles, so a quarter of the blocks idle
+            // through the second round)
+            add_recip<float, 128, 8, 4, 14, 2>(out);
+            add_recip<float, 128, 8, 4, 28, 1>(out);
             break;
         case 64:
             add_recip<float, 64, 8, 6>(out);

@@ -3,7 +3,7 @@
 // evaluation (Sec. 2.3 s2 and the reciprocal half of s3, with the Hartree, local
 // pseudopotential and von Weizsaecker products of Eq. efunc).
 //
-// Work unit: a tile of TW (32 or 16) consecutive columns c = (k1, k2) of the half
+// Work unit: a tile of TW (even, at most 32) consecutive columns c = (k1, k2) of the half
 // spectrum and all N values of k0.  MINB blocks per SM loop over the tiles t = b,
 // b + (blocks), ...; a single thread keeps NSTAGE channel tiles in
 // flight with cp.async.bulk.tensor copies (3-D tensor map over [channel][k0][c],
@@ -17,9 +17,12 @@
 // k0 = t + q TC + r N/R_last in register q R_last + r, which is exactly the input
 // order of the inverse transform with the radices reversed, so the reciprocal
 // products are applied in registers and the inverse starts without an exchange.
-// A warp always touches one row of 32 consecutive columns (TW = 32) or two rows of
-// 16 (TW = 16): every shared-memory access is conflict-free, and every global
-// store whole 128- or 256-byte segments.  rho^beta hat, the term-2 accumulator and |G| stay in
+// With TW = 32 a warp touches one row of 32 consecutive columns and with TW = 16 two
+// rows of 16: every shared-memory access is conflict-free, and every global store
+// whole 128- or 256-byte segments.  TW = 14 or 28 (tiles that divide a 128 x 65 column
+// plane evenly over two rounds of the resident blocks) lets a warp's rows straddle
+// warps: a few exchange accesses take two wavefronts, and row segments start on
+// 16-byte boundaries (the tensor copies' x coordinate stays a multiple of 16 bytes).  rho^beta hat, the term-2 accumulator and |G| stay in
 // registers for the whole tile.
 #pragma once
 
@@ -244,16 +247,17 @@ __device__ __forceinline__ void recip_body(const EvalArgs<T> &a, const RecipMaps
     __syncthreads();
     const int nload = s_nload, nops = s_nops;
     const int my_tiles = bid < ntile ? (ntile - 1 - bid) / nblk + 1 : 0;
-    const long long total = (long long)my_tiles * nload;
-    long long issued = 0, cons = 0, pend = 0, L = 0;   // loads issued, released, read since the last barrier, next
+    // (32-bit counters: at most (n1 (n2/2+1) / TW + 1) tiles of at most kMaxChan + 1 loads)
+    const int total = my_tiles * nload;
+    int issued = 0, cons = 0, pend = 0, L = 0;          // loads issued, released, read since the last barrier, next
     // thread 0: start loads while their stages are free
     auto refill = [&]() {
         if (threadIdx.x != 0) return;
         bool fenced = false;
         while (issued < total && issued < cons + NSTAGE) {
-            const int ti = (int)(issued / nload), i = (int)(issued - (long long)ti * nload);
+            const int ti = issued / nload, i = issued - ti * nload;
             const int c0 = (bid + ti * nblk) * TW;
-            const int st = (int)(issued % NSTAGE);
+            const int st = issued % NSTAGE;
             if (!fenced) {
                 fence_proxy_async_smem();           // the stage was last read through the generic proxy
                 fenced = true;
@@ -283,7 +287,7 @@ __device__ __forceinline__ void recip_body(const EvalArgs<T> &a, const RecipMaps
     };
     // the tile of load L (waits for it with a bounded number of polls)
     auto wait_load = [&]() -> const C * {
-        const int st = (int)(L % NSTAGE);
+        const int st = L % NSTAGE;
         if (!mbar_wait_bounded(&full[st], (unsigned)((L / NSTAGE) & 1), a.wait_polls)) wfail = 1;
         L++;
         pend++;
@@ -297,11 +301,11 @@ __device__ __forceinline__ void recip_body(const EvalArgs<T> &a, const RecipMaps
     C v[E], Rr[E], A[E];
     bool xsel = false;                         // exchange tile of the next exchange
     for (int ti = 0; ti < my_tiles && !failed; ti++) {
-        const long long col = (long long)(bid + ti * nblk) * TW + w;
+        const int col = (bid + ti * nblk) * TW + w;          // (n1 (n2/2+1) < 2^31)
         // this thread's column: its G components, half-spectrum weight, and |G| at its frequencies
         T cw, gn[E];
         {
-            const int k1 = (int)(col / n2h), k2 = (int)(col % n2h);
+            const int k1 = col / n2h, k2 = col - k1 * n2h;
             const double m1 = (k1 <= a.n1 / 2) ? k1 : k1 - a.n1, m2 = k2;
             T cv[3];
             for (int d = 0; d < 3; d++) cv[d] = (T)(m1 * a.bvec[3 + d] + m2 * a.bvec[6 + d]);
@@ -433,7 +437,7 @@ __device__ __forceinline__ void recip_body(const EvalArgs<T> &a, const RecipMaps
         // block's shared memory) with a longer bounded wait, count it and leave
         if (threadIdx.x == 0) {
             bool drained = true;
-            for (long long l = cons; l < issued; l++)
+            for (int l = cons; l < issued; l++)
                 drained = mbar_wait_bounded(&full[l % NSTAGE], (unsigned)((l / NSTAGE) & 1), 1u << 26) && drained;
             atomicAdd(a.scal + (drained ? S_TIMEOUT : S_FATAL), 1.0);
         }
