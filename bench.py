@@ -869,8 +869,8 @@ def algorithmic_bytes(kernel, wl, esize):
 
 # the files the E+V evaluation kernels (stats, rows, pencils, reciprocal space,
 # finalize) and their launches are compiled from
-EVAL_KERNEL_SOURCES = ("common.cuh", "fft.cuh", "eval.cuh", "kernels.cuh", "inst.cuh", "recip.cuh", "recip.cu",
-                       "inst_a.cu", "inst_b.cu", "inst_c.cu", "inst_d.cu", "eval_kernels.cu")
+EVAL_KERNEL_SOURCES = ("common.cuh", "fft.cuh", "eval.cuh", "kernels.cuh", "gnl_fit.cuh", "inst.cuh", "recip.cuh",
+                       "recip.cu", "inst_a.cu", "inst_b.cu", "inst_c.cu", "inst_d.cu", "eval_kernels.cu")
 
 
 def kernel_source_sha():

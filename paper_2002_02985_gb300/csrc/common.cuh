@@ -25,6 +25,7 @@ template <typename K> inline cudaError_t allow_max_dynamic_smem(K kernel) {
 // C_TF = (3/10)(3 pi^2)^(2/3) and C_WT = (6/25)(3 pi^2)^(2/3) (Sec. 2.3, Eq. WT).
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kThreePi2 = 29.608813203268074;     // 3 pi^2
+constexpr double kCbrtThreePi2 = 3.0936677262801355;  // (3 pi^2)^(1/3)
 constexpr double kCTF = 2.871234000188191;           // 0.3 (3 pi^2)^(2/3)
 constexpr double kCWT = 2.2969872001505527;          // 0.24 (3 pi^2)^(2/3)
 

@@ -220,6 +220,43 @@ template <typename T> __device__ __forceinline__ int knot_interval(T kc, const T
     return lo;
 }
 
+// Knot interval of a clamped kF for geometric knots made from the density (s1, reading 4):
+// j from ln(kF / k_1) / ln(r) (ilr = 1 / ln r, r the knot ratio), then one step up and one
+// down with the binary search's rule, which gives its result exactly whenever the guess is
+// within one interval (ln r >= 1e-4 keeps the guess's rounding below a hundredth of an
+// interval).  ilr = 0 (caller-given or arithmetic knots, near-equal knots) uses the search.
+template <typename T> __device__ __forceinline__ T knot_log_scale(const EvalArgs<T> &a, const T *knots, int M) {
+    if (a.frozen || a.knot_spacing != 0 || M < 3) return (T)0;
+    const T lr = glog(gdiv(knots[M - 1], knots[0])) / (T)(M - 1);
+    return lr > (T)1e-4 ? (T)1 / lr : (T)0;
+}
+template <typename T> __device__ __forceinline__ int knot_interval_fast(T kc, const T *knots, int M, T ilr) {
+    if (ilr == (T)0) return knot_interval(kc, knots, M);
+    int j = (int)(glog(gdiv(kc, knots[0])) * ilr);
+    j = j < 0 ? 0 : (j > M - 2 ? M - 2 : j);
+    if (j < M - 2 && knots[j + 1] <= kc) j++;
+    if (j > 0 && knots[j] > kc) j--;
+    return j;
+}
+
+// rho^alpha, rho^beta and kF = (3 pi^2 rho)^(1/3) of a floored density xf.  For the
+// Lindhard-consistent exponents alpha = beta = 5/6 (the default functional) rho^(5/6) is
+// formed as sqrt(rho) cbrt(rho) and kF from the same cube root: two roots per point in
+// place of a general power and a second root.  Every kernel that places a point on the
+// knots calls this, so the forward and the inverse rows agree on the point's interval.
+template <typename T>
+__device__ __forceinline__ void point_powers(const EvalArgs<T> &a, T xf, T &ra, T &rb, T &kf) {
+    if (a.alpha == (T)(5.0 / 6.0) && a.beta == a.alpha) {
+        const T c = dcbrt(xf);
+        ra = rb = dsqrt(xf) * c;
+        kf = (T)kCbrtThreePi2 * c;
+    } else {
+        ra = dpow(xf, a.alpha);
+        rb = (a.beta == a.alpha) ? ra : dpow(xf, a.beta);
+        kf = dcbrt((T)kThreePi2 * xf);
+    }
+}
+
 // Whether kF(x) lies in the knot range [k_1, k_M] (the exact potential's slope term is
 // applied only there).  With knots made from the density (s1) the end knots are kF of the
 // floored min and max density, and kF is monotone, so the test is taken on the density
@@ -433,6 +470,7 @@ __device__ __forceinline__ void row_fwd_body(const EvalArgs<T> &a, const int bid
         stg[rr * pitch + i2] = (row < R) ? a.rho[row * n + i2] : (T)0;
     }
     __syncthreads();
+    const T ilr = lwt ? knot_log_scale(a, sk, M) : (T)0;
     // per-point quantities (o = idx = i2 * 2B + rr)
     for (int o = threadIdx.x; o < PP; o += NT) {
         const int rr = o % (2 * B), i2 = o / (2 * B);
@@ -440,13 +478,13 @@ __device__ __forceinline__ void row_fwd_body(const EvalArgs<T> &a, const int bid
         sx[o] = x;
         if (a.terms & 4u) {
             const T xf = x > a.floor_ ? x : a.floor_;
-            const T ra = dpow(xf, a.alpha);
+            T ra, rb, kf;
+            point_powers(a, xf, ra, rb, kf);
             sra[o] = ra;
-            srb[o] = (a.beta == a.alpha) ? ra : dpow(xf, a.beta);
+            srb[o] = rb;
             if (lwt) {
-                T kf = dcbrt((T)kThreePi2 * xf);
                 kf = kf < sk[0] ? sk[0] : (kf > sk[M - 1] ? sk[M - 1] : kf);
-                const int j = knot_interval(kf, sk, M);
+                const int j = knot_interval_fast(kf, sk, M, ilr);
                 sj[o] = (unsigned char)j;
                 st[o] = (kf - sk[j]) * a.invdk_t[j];
             }
@@ -841,6 +879,7 @@ __device__ __forceinline__ void row_inv_body(const EvalArgs<T> &a, const int bid
         stg[rr * pitch + i2] = (row < R) ? a.rho[row * n + i2] : (T)0;
     }
     __syncthreads();
+    const T ilr = lwt ? knot_log_scale(a, sk, M) : (T)0;
     const T psi_floor = dsqrt(a.floor_);
     const T rlo = (T)a.scal[S_RHO_MIN] > a.floor_ ? (T)a.scal[S_RHO_MIN] : a.floor_;
     const T rhi = (T)a.scal[S_RHO_MAX] > a.floor_ ? (T)a.scal[S_RHO_MAX] : a.floor_;
@@ -863,15 +902,14 @@ __device__ __forceinline__ void row_inv_body(const EvalArgs<T> &a, const int bid
         svw[o] = (T)1 / ((T)2 * (p > psi_floor ? p : psi_floor));
         if (a.terms & 4u) {
             const T xf = x > a.floor_ ? x : a.floor_;
-            const T ra = dpow(xf, a.alpha);
-            const T rb = (a.beta == a.alpha) ? ra : dpow(xf, a.beta);
+            T ra, rb, kf;
+            point_powers(a, xf, ra, rb, kf);
             sa1[o] = ra / xf;
             sb1[o] = rb / xf;
             if (lwt) {
-                const T kf = dcbrt((T)kThreePi2 * xf);
                 const bool inside = in_knot_range(a, xf, kf, sk[0], sk[M - 1], rlo, rhi);
                 const T kc = kf < sk[0] ? sk[0] : (kf > sk[M - 1] ? sk[M - 1] : kf);
-                const int j = knot_interval(kc, sk, M);
+                const int j = knot_interval_fast(kc, sk, M, ilr);
                 sj[o] = (unsigned char)j;
                 st[o] = (kc - sk[j]) * sidk[j];
                 sk3[o] = interp ? ra : (inside ? kf * (T)(1.0 / 3.0) : (T)0);
@@ -1049,6 +1087,7 @@ __device__ __forceinline__ void row_fwd2_body(const EvalArgs<T> &a, const int bi
     __syncthreads();
     const int kpos = skpos;
     const T mean = (T)a.scal[S_RHO_MEAN];
+    const T ilr = lwt ? knot_log_scale(a, sk, M) : (T)0;
     // per-point channel values: vh = rho - mean, vv = psi, vb = rho^beta,
     // fa/fb = (1 - t) rho^alpha / t rho^alpha for knots j/j+1 (WT: fa = rho^alpha)
     T vh[E][2], vv[E][2], vb[E][2], fa[E][2], fb[E][2];
@@ -1066,12 +1105,12 @@ __device__ __forceinline__ void row_fwd2_body(const EvalArgs<T> &a, const int bi
                 vv[q][s] = dsqrt(x > (T)0 ? x : (T)0);
                 if (nl) {
                     const T xf = x > a.floor_ ? x : a.floor_;
-                    const T ra = dpow(xf, a.alpha);
-                    vb[q][s] = (a.beta == a.alpha) ? ra : dpow(xf, a.beta);
+                    T ra, rb, kf;
+                    point_powers(a, xf, ra, rb, kf);
+                    vb[q][s] = rb;
                     if (lwt) {
-                        T kf = dcbrt((T)kThreePi2 * xf);
                         kf = kf < sk[0] ? sk[0] : (kf > sk[M - 1] ? sk[M - 1] : kf);
-                        const int j = knot_interval(kf, sk, M);
+                        const int j = knot_interval_fast(kf, sk, M, ilr);
                         const T t = (kf - sk[j]) * sdk[j];
                         jj[q][s] = j;
                         fa[q][s] = ((T)1 - t) * ra;
@@ -1194,6 +1233,7 @@ __device__ __forceinline__ void row_inv2_body(const EvalArgs<T> &a, const int bi
     __syncthreads();
     const int kpos = skpos;
     unsigned phase = 0;
+    const T ilr = lwt ? knot_log_scale(a, sk, M) : (T)0;
     const T psi_floor = dsqrt(a.floor_);
     const T alpha_eff = interp ? (T)2 * a.alpha : a.alpha;
     const T rlo = (T)a.scal[S_RHO_MIN] > a.floor_ ? (T)a.scal[S_RHO_MIN] : a.floor_;
@@ -1227,16 +1267,15 @@ __device__ __forceinline__ void row_inv2_body(const EvalArgs<T> &a, const int bi
                 fvw[q][s] = (T)1 / ((T)2 * (p > psi_floor ? p : psi_floor));
                 if (nl) {
                     const T xf = x > a.floor_ ? x : a.floor_;
-                    const T ra = dpow(xf, a.alpha);
-                    const T rb = (a.beta == a.alpha) ? ra : dpow(xf, a.beta);
+                    T ra, rb, kf;
+                    point_powers(a, xf, ra, rb, kf);
                     const T sa1 = ra / xf;
                     fa1[q][s] = a.alpha * sa1;
                     fb1[q][s] = a.beta * (rb / xf);
                     if (lwt) {
-                        const T kf = dcbrt((T)kThreePi2 * xf);
                         const bool inside = in_knot_range(a, xf, kf, sk[0], sk[M - 1], rlo, rhi);
                         const T kc = kf < sk[0] ? sk[0] : (kf > sk[M - 1] ? sk[M - 1] : kf);
-                        const int j = knot_interval(kc, sk, M);
+                        const int j = knot_interval_fast(kc, sk, M, ilr);
                         const T t = (kc - sk[j]) * sdk[j], idk = sdk[j];
                         jj[q][s] = j;
                         if (interp) {

@@ -39,6 +39,9 @@ template <> void recip_candidates<float>(int n, std::vector<KernelCand> &out) {
             // through the second round)
             add_recip<float, 128, 8, 4, 14, 2>(out);
             add_recip<float, 128, 8, 4, 28, 1>(out);
+            add_recip<float, 128, 16, 4, 14, 2>(out);
+            // 8 columns, 64 threads: a block barrier joins two warps
+            add_recip<float, 128, 16, 3, 8, 4>(out);
             break;
         case 64:
             add_recip<float, 64, 8, 6>(out);

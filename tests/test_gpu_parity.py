@@ -434,7 +434,7 @@ def _bulk_case(shape):
     return cell, pos, rho
 
 
-@pytest.mark.parametrize("pick", range(10))
+@pytest.mark.parametrize("pick", range(12))
 @pytest.mark.parametrize("shape", [(128, 18, 20), (64, 10, 12), (32, 6, 10)])
 def test_every_reciprocal_kernel_configuration_matches_oracle(shape, pick):
     """Each compiled configuration of the reciprocal-space pass for the shape's n0 (the
