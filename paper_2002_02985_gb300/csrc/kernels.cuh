@@ -10,6 +10,8 @@
 #include "eval.cuh"
 #include "gnl_fit.cuh"
 
+#include <type_traits>
+
 namespace ofdft {
 
 // ======================================================================= policies
@@ -159,6 +161,19 @@ template <typename T, bool MGP> __device__ __forceinline__ T kernel_value(const 
     T G = gnl(eta);
     if constexpr (MGP) G = a.mgp_1mx * G + a.mgp_3xy * mgp_j(a.mgp_tab, a.mgp_n, eta);
     return (T)kCWT * G;
+}
+
+// The FP32 kernel at eta > 2, exactly as kernel_value<float, false> gives it there, for a warp
+// whose every eta is known to lie above 2 (most G vectors of a bulk grid): the polynomial in
+// 1/eta^2 alone, without the other range's polynomial, the select and the closed-form test.
+__device__ __forceinline__ float kernel_value_large(float eta) {
+    return (float)kCWT * gnl_large_l(gdiv(1.0f, eta * eta));
+}
+// whether the calling warp may use kernel_value_large for every element whose |G| is at least
+// gmin (the caller's smallest |G|) at eta = |G| hk; always false for MGP and FP64 kernels
+template <typename T, bool MGP> __device__ __forceinline__ bool warp_all_large(T gmin, T hk) {
+    if constexpr (MGP || sizeof(T) != 4) return false;
+    else return __all_sync(__activemask(), gmin * hk > (T)2);
 }
 
 // ======================================================================= LDA exchange-correlation
@@ -557,16 +572,32 @@ __device__ __forceinline__ void pencil1_body(const EvalArgs<T> &a, const int bid
         const int ch = DIR < 0 ? a.col_ch[ci] : a.col_inv_ch[ci];
         return a.chan + (size_t)ch * a.NH;
     };
-    // (NT is a multiple of TW, so a thread's column w, hence the division, is loop invariant)
+    // With a compile-time policy NT is a multiple of TW, so a thread keeps one column w of
+    // every tile: its (k0, k2) is found once per tile with a 32-bit division (columns number
+    // fewer than 2^31) and each element adds only its row offset.
+    constexpr bool fixed_col = P::ct && P::B_ > 0 && (P::NT_ % (P::B_ > 0 ? P::B_ : 1) == 0);
+    auto col_offset = [&](long long c0, bool &ok) -> size_t {
+        const int c = (int)c0 + threadIdx.x % TW;
+        ok = c < ncols;
+        const int k0 = c / n2h, k2 = c - k0 * n2h;
+        return ok ? (size_t)k0 * plane + k2 : 0;
+    };
     auto prefetch = [&](int t, C *dst) {
         long long c0;
         const C *base = tile_base(t, c0);
-        for (int idx = threadIdx.x; idx < n * TW; idx += NT) {
-            const int w = idx % TW, i = idx / TW;
-            const long long c = c0 + w;
-            const long long k0 = c / n2h, k2 = c - k0 * n2h;
-            const bool ok = c < ncols;
-            cp_async<sizeof(C)>(dst + idx, base + (ok ? k0 * plane + (long long)i * n2h + k2 : 0), ok);
+        if constexpr (fixed_col) {
+            bool ok;
+            const C *src = base + col_offset(c0, ok);
+            for (int idx = threadIdx.x; idx < n * TW; idx += NT)
+                cp_async<sizeof(C)>(dst + idx, src + (ok ? (size_t)(idx / TW) * n2h : 0), ok);
+        } else {
+            for (int idx = threadIdx.x; idx < n * TW; idx += NT) {
+                const int w = idx % TW, i = idx / TW;
+                const long long c = c0 + w;
+                const long long k0 = c / n2h, k2 = c - k0 * n2h;
+                const bool ok = c < ncols;
+                cp_async<sizeof(C)>(dst + idx, base + (ok ? k0 * plane + (long long)i * n2h + k2 : 0), ok);
+            }
         }
         cp_async_commit();
     };
@@ -580,11 +611,18 @@ __device__ __forceinline__ void pencil1_body(const EvalArgs<T> &a, const int bid
         const C *res = P::template fft2<DIR>(cur, scr, a, tw);
         long long c0;
         C *base = tile_base(t, c0);
-        for (int idx = threadIdx.x; idx < n * TW; idx += NT) {
-            const int w = idx % TW, i = idx / TW;
-            const long long c = c0 + w;
-            const long long k0 = c / n2h, k2 = c - k0 * n2h;
-            if (c < ncols) base[k0 * plane + (long long)i * n2h + k2] = res[idx];
+        if constexpr (fixed_col) {
+            bool ok;
+            C *dstc = base + col_offset(c0, ok);
+            if (ok)
+                for (int idx = threadIdx.x; idx < n * TW; idx += NT) dstc[(size_t)(idx / TW) * n2h] = res[idx];
+        } else {
+            for (int idx = threadIdx.x; idx < n * TW; idx += NT) {
+                const int w = idx % TW, i = idx / TW;
+                const long long c = c0 + w;
+                const long long k0 = c / n2h, k2 = c - k0 * n2h;
+                if (c < ncols) base[k0 * plane + (long long)i * n2h + k2] = res[idx];
+            }
         }
     }
     cp_async_wait<0>();
@@ -691,6 +729,7 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a, const int bid, 
         else xa = p;
     };
     const T b0x = (T)a.bvec[0], b0y = (T)a.bvec[1], b0z = (T)a.bvec[2];
+    T gmin = (T)3.0e38;                       // the smallest |G| of this thread's elements
     for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
         const int w = idx % TW, i = idx / TW;
         const T m0 = (T)((i <= n / 2) ? i : i - n);
@@ -698,6 +737,7 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a, const int bid, 
         const T gy = cvec[w][1] + m0 * b0y;
         const T gz = cvec[w][2] + m0 * b0z;
         gn[idx] = dsqrt(gx * gx + gy * gy + gz * gz);
+        gmin = gn[idx] < gmin ? gn[idx] : gmin;
     }
     const T invN = (T)(1.0 / (double)a.N);
     double eH = 0.0, eV = 0.0, eP = 0.0, eN = 0.0;
@@ -776,15 +816,21 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a, const int bid, 
             C *S = fwd(slot(sl));
             set_slot(sl, S);
             Part<T, XS> fN;
-            for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
-                const int w = idx % TW;
-                const T K = kernel_value<T, MGP>(a, gn[idx] * hk);
-                const C Sa = cscale(S[idx], invN);
-                const C Rb = Rr[idx];
-                fN.add(cw[w] * K * (Sa.x * Rb.x + Sa.y * Rb.y));
-                Rr[idx] = cscale(Rb, K);
-                S[idx] = cscale(Sa, K);
-            }
+            auto wt = [&](auto large) {
+                for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
+                    const int w = idx % TW;
+                    T K;
+                    if constexpr (decltype(large)::value) K = kernel_value_large(gn[idx] * hk);
+                    else K = kernel_value<T, MGP>(a, gn[idx] * hk);
+                    const C Sa = cscale(S[idx], invN);
+                    const C Rb = Rr[idx];
+                    fN.add(cw[w] * K * (Sa.x * Rb.x + Sa.y * Rb.y));
+                    Rr[idx] = cscale(Rb, K);
+                    S[idx] = cscale(Sa, K);
+                }
+            };
+            if (warp_all_large<T, MGP>(gmin, hk)) wt(std::true_type{});
+            else wt(std::false_type{});
             eN += fN.value();
             __syncthreads();
             Rr = inv(Rr);
@@ -809,17 +855,23 @@ __device__ __forceinline__ void axis0_body(const EvalArgs<T> &a, const int bid, 
                     S = slot(sl);
                 }
                 Part<T, XS> fN;
-                for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
-                    const T K = kernel_value<T, MGP>(a, gn[idx] * hk);
-                    if (exact) {
-                        // E_NL += Omega sum_G w Re(conj(FFT[h_m rho^alpha]) K_m FFT[rho^beta])
-                        const C Sm = cscale(S[idx], invN);
-                        const C Rb = Rr[idx];
-                        fN.add(cw[idx % TW] * K * (Sm.x * Rb.x + Sm.y * Rb.y));
-                        A[idx] = cadd(A[idx], cscale(Sm, K));
+                auto knot = [&](auto large) {
+                    for (int idx = threadIdx.x; idx < NTILE; idx += NT) {
+                        T K;
+                        if constexpr (decltype(large)::value) K = kernel_value_large(gn[idx] * hk);
+                        else K = kernel_value<T, MGP>(a, gn[idx] * hk);
+                        if (exact) {
+                            // E_NL += Omega sum_G w Re(conj(FFT[h_m rho^alpha]) K_m FFT[rho^beta])
+                            const C Sm = cscale(S[idx], invN);
+                            const C Rb = Rr[idx];
+                            fN.add(cw[idx % TW] * K * (Sm.x * Rb.x + Sm.y * Rb.y));
+                            A[idx] = cadd(A[idx], cscale(Sm, K));
+                        }
+                        S[idx] = cscale(Rr[idx], K);
                     }
-                    S[idx] = cscale(Rr[idx], K);
-                }
+                };
+                if (warp_all_large<T, MGP>(gmin, hk)) knot(std::true_type{});
+                else knot(std::false_type{});
                 eN += fN.value();
                 __syncthreads();
                 S = inv(S);

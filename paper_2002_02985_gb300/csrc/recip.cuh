@@ -321,6 +321,9 @@ __device__ __forceinline__ void recip_body(const EvalArgs<T> &a, const RecipMaps
                     gn[q * RL + r] = dsqrt(gx * gx + gy * gy + gz * gz);
                 }
         }
+        T gmin = gn[0];                                      // the smallest |G| of the thread
+#pragma unroll
+        for (int i = 1; i < E; i++) gmin = gn[i] < gmin ? gn[i] : gmin;
 #pragma unroll
         for (int i = 0; i < E; i++) A[i] = cmake<C>((T)0, (T)0);
         for (int o = 0; o < nops; o++) {
@@ -335,9 +338,14 @@ __device__ __forceinline__ void recip_body(const EvalArgs<T> &a, const RecipMaps
                 // the kernel of this knot (WT: of the mean density's kF) at the thread's |G|
                 const T hk = kind == OP_WT ? (T)(0.5 / a.scal[S_KF_WT]) : (T)0.5 / sk[op.m];
                 Part<T, false> fN;
+                // (a warp whose every eta is above 2 takes the kernel from the large-eta
+                // polynomial alone: the same values, fewer instructions)
+                auto knot = [&](auto large) {
 #pragma unroll
                 for (int i = 0; i < E; i++) {
-                    const T K = kernel_value<T, MGP>(a, gn[i] * hk);
+                    T K;
+                    if constexpr (decltype(large)::value) K = kernel_value_large(gn[i] * hk);
+                    else K = kernel_value<T, MGP>(a, gn[i] * hk);
                     if (kind == OP_EX) {
                         // E_NL += Omega sum_G w Re(conj(FFT[h_m rho^alpha]) K_m FFT[rho^beta])
                         const C Sm = cscale(v[i], invN);
@@ -355,6 +363,9 @@ __device__ __forceinline__ void recip_body(const EvalArgs<T> &a, const RecipMaps
                         v[i] = cscale(Sa, K);
                     }
                 }
+                };
+                if (warp_all_large<T, MGP>(gmin, hk)) knot(std::true_type{});
+                else knot(std::false_type{});
                 eN += fN.value();
             } else if (kind == OP_HPP) {
                 if (a.rhohat_out && col < PL) {
