@@ -48,6 +48,13 @@ template <> void recip_candidates<float>(int n, std::vector<KernelCand> &out) {
             add_recip<float, 64, 4, 4, 16, 2>(out);
             break;
         case 32: add_recip<float, 32, 4, 8>(out); break;
+        case 1024:
+            // 4-column tiles (32-byte rows: the tensor copies' x stays a multiple of 16 bytes), one
+            // block per SM: 16 elements per thread (passes 16 16 4) or 8 (passes 8 8 8 2)
+            add_recip<float, 1024, 16, 4, 4, 1>(out);
+            add_recip<float, 1024, 16, 2, 4, 1>(out);
+            add_recip<float, 1024, 8, 4, 4, 1>(out);
+            break;
         default: break;
     }
 }
