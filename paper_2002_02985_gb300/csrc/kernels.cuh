@@ -235,7 +235,8 @@ template <typename T> __device__ __forceinline__ int knot_interval(T kc, const T
     return lo;
 }
 
-// Knot interval of a clamped kF for geometric knots made from the density (s1, reading 4):
+// Knot interval of a clamped kF for geometric knots made from the density (s1: the end
+// knots are kF of the minimum and maximum density):
 // j from ln(kF / k_1) / ln(r) (ilr = 1 / ln r, r the knot ratio), then one step up and one
 // down with the binary search's rule, which gives its result exactly whenever the guess is
 // within one interval (ln r >= 1e-4 keeps the guess's rounding below a hundredth of an

@@ -19,11 +19,11 @@
 // products are applied in registers and the inverse starts without an exchange.
 // With TW = 32 a warp touches one row of 32 consecutive columns and with TW = 16 two
 // rows of 16: every shared-memory access is conflict-free, and every global store
-// whole 128- or 256-byte segments.  TW = 14 or 28 (tiles that divide a 128 x 65 column
-// plane evenly over two rounds of the resident blocks) lets a warp's rows straddle
-// warps: a few exchange accesses take two wavefronts, and row segments start on
-// 16-byte boundaries (the tensor copies' x coordinate stays a multiple of 16 bytes).  rho^beta hat, the term-2 accumulator and |G| stay in
-// registers for the whole tile.
+// whole 128- or 256-byte segments.  With TW = 14 or 28 (tiles that divide a 128 x 65
+// column plane evenly over two rounds of the resident blocks) a warp spans parts of
+// several tile rows: some exchange accesses take two wavefronts, and row segments start
+// on 16-byte boundaries (the tensor copies' x coordinate stays a multiple of 16 bytes).
+// rho^beta hat, the term-2 accumulator and |G| stay in registers for the whole tile.
 #pragma once
 
 #include <cuda.h>
