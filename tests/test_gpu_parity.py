@@ -415,7 +415,7 @@ def test_channel_batched_and_per_channel_rows_agree(kw):
 
 
 # ---------------------------------------------------------------- persistent reciprocal-space kernel
-# n0 in {32, 64, 128} runs the register-resident, tensor-copy kernel: ragged last column tiles
+# n0 in {32, 64, 128, 1024} runs the register-resident, tensor-copy kernel: ragged last column tiles
 # (n1 (n2/2+1) not a multiple of 32), every NL mode, the MGP form; n1 (n2/2+1) odd keeps the
 # tile kernel (tensor maps need 16-byte row strides)
 RECIP_CASES = [((128, 18, 20), dict(n_knots=8)), ((64, 10, 12), dict(n_knots=8)), ((32, 6, 10), dict(n_knots=8)),
@@ -424,6 +424,7 @@ RECIP_CASES = [((128, 18, 20), dict(n_knots=8)), ((64, 10, 12), dict(n_knots=8))
                ((64, 10, 12), dict(n_knots=8, terms=L.TERMS_VALID))]
 
 
+@functools.lru_cache(maxsize=None)
 def _bulk_case(shape):
     cell = np.array([[0.25 * shape[0], 0.0, 0.0], [0.3, 0.45 * shape[1], 0.0], [-0.2, 0.1, 0.4 * shape[2]]])
     vol = abs(np.linalg.det(cell))
@@ -435,7 +436,7 @@ def _bulk_case(shape):
 
 
 @pytest.mark.parametrize("pick", range(12))
-@pytest.mark.parametrize("shape", [(128, 18, 20), (64, 10, 12), (32, 6, 10)])
+@pytest.mark.parametrize("shape", [(128, 18, 20), (64, 10, 12), (32, 6, 10), (1024, 6, 10)])
 def test_every_reciprocal_kernel_configuration_matches_oracle(shape, pick):
     """Each compiled configuration of the reciprocal-space pass for the shape's n0 (the
     autotuner's candidates, forced one at a time; indices past the list are skipped)."""
