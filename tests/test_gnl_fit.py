@@ -6,6 +6,7 @@ import os
 import re
 
 import numpy as np
+import pytest
 
 from oracle.lindhard import G_NL
 
@@ -45,3 +46,17 @@ def test_large_eta_polynomial_matches_g_nl():
     ref = G_NL(eta)
     assert np.max(np.abs(got - ref) / np.abs(ref)) < 1e-7
     assert abs(c[0] + 1.6) < 1e-6                       # G_NL(inf) = -8/5
+
+
+def test_generator_reproduces_the_compiled_header(tmp_path, monkeypatch):
+    """gen_gnl_fit.py (50-digit Chebyshev interpolation) writes exactly the committed header."""
+    pytest.importorskip("mpmath")
+    import importlib.util
+    gen = os.path.join(os.path.dirname(HDR), "..", "gen_gnl_fit.py")
+    spec = importlib.util.spec_from_file_location("gen_gnl_fit", gen)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    out = tmp_path / "gnl_fit.cuh"
+    monkeypatch.setattr(mod, "OUT", str(out))
+    mod.main()
+    assert out.read_text() == open(HDR).read()
